@@ -1,0 +1,298 @@
+"""Oracle: a plain, slow FP64 CPU restatement of the filtered time-domain
+Krylov eigensolver of Nannen & Wess, "A Krylov Eigenvalue Solver Based on
+Filtered Time Domain Solutions" (arXiv:2402.08515), Sec. 2.
+
+TEST INFRASTRUCTURE ONLY. Only tests/, __graft_entry__.smoke() and the CPU
+baseline / reference arm of bench.py import this module. The CUDA library
+never calls it, links it or shares code with it; the two meet only through
+the seeded inputs of ``fe_inputs``.
+
+Everything is float64 numpy; the sparse product S @ y is scipy's CSR matvec
+(a library primitive) and the small symmetric eigenproblem is LAPACK through
+numpy.linalg.eigh. Steps are taken in the paper's order and notation; where
+the paper is silent or garbled the reading taken is stated in the docstring.
+
+Readings used throughout (see the function docstrings):
+  * index range: ``L`` time steps give the L+1 samples y_0..y_L, weighted by
+    alpha_n = tau * alpha(n tau), n = 0..L, so the last sample is at t = T = L tau
+    (eq. disc_filtercoeff sums l = 0..L-1 with L-1 steps; the closed interval
+    (0, T] of eq. weightf is covered by taking L steps and L+1 terms);
+  * inner product: the M-inner product (x, y)_M = x^T M y with two full
+    classical Gram-Schmidt passes (Algorithm 2.4 uses the Euclidean product
+    and one modified pass); the projected problem eq. projevp then becomes a
+    standard symmetric eigenproblem because B^T M B = I;
+  * breakdown: stop when the M-norm after orthogonalisation is below 1e-10
+    times the M-norm before it (Algorithm 2.4 tests for an exact zero);
+  * Krylov dimension kmax = number of basis vectors b_0..b_{kmax-1}, which
+    takes kmax-1 filter applications;
+  * residual: rel_res = ||S x - theta M x||_2 / (theta ||M x||_2) with
+    x = B y, ||x||_M = 1; the absolute residual of eq. res is also returned.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "weight", "alpha_table", "q_values", "beta_tilde", "filter_apply",
+    "filter_apply_multi", "power_iteration", "m_inner", "m_norm",
+    "orthonormalize_cgs2", "rayleigh_ritz", "ritz_residuals", "krylov_solve",
+    "KrylovResult", "BREAKDOWN_RATIO",
+]
+
+BREAKDOWN_RATIO = 1e-10
+
+
+# --------------------------------------------------------------------------
+# weight function and weight table: eq. (weightf), eq. (disc_filtercoeff)
+# --------------------------------------------------------------------------
+
+def weight(t, omega_min: float, omega_max: float, T: float):
+    """alpha(t) of eq. (weightf).
+
+    alpha(0) = 2 (omega_max - omega_min) / pi; for 0 < t <= T
+    alpha(t) = 4/(pi t) sin(t (omega_max - omega_min)/2) cos(t (omega_max + omega_min)/2);
+    alpha(t) = 0 for t > T.
+    """
+    t = np.asarray(t, dtype=np.float64)
+    out = np.zeros_like(t)
+    zero = t == 0.0
+    inside = (t > 0.0) & (t <= T)
+    out[zero] = 2.0 * (omega_max - omega_min) / math.pi
+    ti = t[inside]
+    out[inside] = (4.0 / (math.pi * ti) * np.sin(0.5 * ti * (omega_max - omega_min))
+                   * np.cos(0.5 * ti * (omega_max + omega_min)))
+    return out
+
+
+def alpha_table(omega_min: float, omega_max: float, tau: float, L: int) -> np.ndarray:
+    """Rectangle-rule weights alpha_n = tau * alpha(n tau), n = 0..L, T = L tau
+    (eq. disc_filtercoeff with the L-steps / L+1-terms reading)."""
+    T = L * tau
+    n = np.arange(L + 1, dtype=np.float64)
+    return tau * weight(n * tau, omega_min, omega_max, T)
+
+
+# --------------------------------------------------------------------------
+# discrete filter: eq. (scalartimestep), eq. (fullydiscfilter)
+# --------------------------------------------------------------------------
+
+def q_values(omega, tau: float, L: int) -> np.ndarray:
+    """q_l(omega), l = 0..L, of the scalar recurrence eq. (scalartimestep):
+    q_{-1} = q_0 = 1, q_{l+1} = (2 - tau^2 omega^2) q_l - q_{l-1}.
+    Returns shape (L+1, len(omega))."""
+    omega = np.atleast_1d(np.asarray(omega, dtype=np.float64))
+    q = np.empty((L + 1, omega.size))
+    q_prev = np.ones_like(omega)
+    q_cur = np.ones_like(omega)
+    q[0] = q_cur
+    for l in range(L):
+        q_next = (2.0 - tau * tau * omega * omega) * q_cur - q_prev
+        q[l + 1] = q_next
+        q_prev, q_cur = q_cur, q_next
+    return q
+
+
+def beta_tilde(omega, alpha: np.ndarray, tau: float) -> np.ndarray:
+    """Fully discrete filter of eq. (fullydiscfilter):
+    beta~(omega) = sum_{n=0..L} alpha_n q_n(omega), alpha_n = tau alpha(n tau)."""
+    L = len(alpha) - 1
+    return alpha @ q_values(omega, tau, L)
+
+
+# --------------------------------------------------------------------------
+# filter application: eq. (2stepmethod) + eq. (disc_filtercoeff)
+# --------------------------------------------------------------------------
+
+def filter_apply(S, m: np.ndarray, r: np.ndarray, tau: float,
+                 alpha: np.ndarray) -> np.ndarray:
+    """C r = sum_{n=0..L} alpha_n y_n(r) (eq. disc_filtercoeff).
+
+    y_{-1} = y_0 = r and y_{l+1} = -tau^2 M^{-1} S y_l + 2 y_l - y_{l-1}
+    (eq. 2stepmethod), M = diag(m); the inner loop of Algorithm 2.4."""
+    L = len(alpha) - 1
+    y_prev = np.array(r, dtype=np.float64)
+    y = np.array(r, dtype=np.float64)
+    acc = alpha[0] * y
+    for l in range(L):
+        y_next = -tau * tau * (S @ y) / m + 2.0 * y - y_prev
+        acc = acc + alpha[l + 1] * y_next
+        y_prev, y = y, y_next
+    return acc
+
+
+def filter_apply_multi(S, m: np.ndarray, R: np.ndarray, tau: float,
+                       alphas: np.ndarray) -> np.ndarray:
+    """Several weight tables on one trajectory per start vector.
+
+    R: (b, n) start vectors; alphas: (F, L+1) weight tables sharing tau and L.
+    Returns (F, b, n) with out[f, j] = sum_n alphas[f, n] y_n(R[j])."""
+    R = np.atleast_2d(np.asarray(R, dtype=np.float64))
+    alphas = np.atleast_2d(np.asarray(alphas, dtype=np.float64))
+    F, Lp1 = alphas.shape
+    out = np.empty((F, R.shape[0], R.shape[1]))
+    for j in range(R.shape[0]):
+        y_prev = R[j].copy()
+        y = R[j].copy()
+        acc = [alphas[f, 0] * y for f in range(F)]
+        for l in range(Lp1 - 1):
+            y_next = -tau * tau * (S @ y) / m + 2.0 * y - y_prev
+            for f in range(F):
+                acc[f] = acc[f] + alphas[f, l + 1] * y_next
+            y_prev, y = y, y_next
+        for f in range(F):
+            out[f, j] = acc[f]
+    return out
+
+
+# --------------------------------------------------------------------------
+# power iteration for omega_max(S, M) (Sec. 3.1: the stable time step is
+# "determined using a power iteration")
+# --------------------------------------------------------------------------
+
+def power_iteration(S, m: np.ndarray, v0: np.ndarray, iters: int) -> float:
+    """Largest eigenfrequency of the pencil by power iteration on M^{-1} S.
+
+    v <- M^{-1} S v / ||M^{-1} S v||_2, ``iters`` times from v0/||v0||_2; the
+    estimate is sqrt of the Rayleigh quotient (v^T S v)/(v^T M v)."""
+    v = np.array(v0, dtype=np.float64)
+    v = v / np.linalg.norm(v)
+    for _ in range(iters):
+        w = (S @ v) / m
+        v = w / np.linalg.norm(w)
+    theta = (v @ (S @ v)) / (v @ (m * v))
+    return math.sqrt(theta)
+
+
+# --------------------------------------------------------------------------
+# Gram-Schmidt in the M-inner product (Algorithm 2.4, orthogonalisation loop)
+# --------------------------------------------------------------------------
+
+def m_inner(x: np.ndarray, y: np.ndarray, m: np.ndarray) -> float:
+    return float(np.sum(x * m * y))
+
+
+def m_norm(x: np.ndarray, m: np.ndarray) -> float:
+    return math.sqrt(m_inner(x, x, m))
+
+
+def orthonormalize_cgs2(B: np.ndarray, w: np.ndarray, m: np.ndarray):
+    """Two classical Gram-Schmidt passes of w against the columns of B in the
+    M-inner product, then M-normalisation.
+
+    B: (k, n) with M-orthonormal rows. Returns (b, norm_before, norm_after);
+    b is None on breakdown (norm_after < BREAKDOWN_RATIO * norm_before)."""
+    w = np.array(w, dtype=np.float64)
+    norm_before = m_norm(w, m)
+    for _ in range(2):
+        if B.shape[0]:
+            h = B @ (m * w)           # h_j = (w, b_j)_M
+            w = w - h @ B             # w -= sum_j h_j b_j
+    norm_after = m_norm(w, m)
+    if not norm_after > BREAKDOWN_RATIO * norm_before:
+        return None, norm_before, norm_after
+    return w / norm_after, norm_before, norm_after
+
+
+# --------------------------------------------------------------------------
+# Rayleigh-Ritz (eq. projevp) and residuals (eq. res)
+# --------------------------------------------------------------------------
+
+def rayleigh_ritz(S, B: np.ndarray):
+    """Eigenpairs of B^T S B y = theta B^T M B y with B^T M B = I.
+
+    B: (k, n), rows M-orthonormal. Returns ascending theta (k,) and Y (k, k)
+    with columns y_j. Negative theta from rounding is clamped to 0 (S PSD)."""
+    SB = np.stack([S @ b for b in B]) if B.shape[0] else np.zeros_like(B)
+    H = B @ SB.T                      # H[i, j] = b_i^T S b_j
+    H = 0.5 * (H + H.T)
+    theta, Y = np.linalg.eigh(H)
+    return np.maximum(theta, 0.0), Y
+
+
+def ritz_residuals(S, m: np.ndarray, B: np.ndarray, theta: np.ndarray,
+                   Y: np.ndarray):
+    """For each Ritz pair: x = B^T y (||x||_M = 1), the absolute residual
+    ||(S - theta M) x||_2 of eq. (res) and the relative one
+    ||S x - theta M x||_2 / (theta ||M x||_2). Returns (X (p, n), abs, rel)."""
+    X = Y.T @ B
+    abs_res = np.empty(len(theta))
+    rel_res = np.empty(len(theta))
+    for j, (th, x) in enumerate(zip(theta, X)):
+        r = S @ x - th * (m * x)
+        abs_res[j] = np.linalg.norm(r)
+        denom = th * np.linalg.norm(m * x)
+        rel_res[j] = abs_res[j] / denom if denom > 0 else math.inf
+    return X, abs_res, rel_res
+
+
+# --------------------------------------------------------------------------
+# the Krylov eigensolver (Algorithm 2.4 + eq. projevp + eq. res)
+# --------------------------------------------------------------------------
+
+@dataclass
+class KrylovResult:
+    omega2: np.ndarray            # accepted theta, ascending
+    omega: np.ndarray
+    rel_res: np.ndarray
+    abs_res: np.ndarray
+    vectors: np.ndarray           # (p, n)
+    k_used: int                   # basis size reached
+    time_steps: int               # leapfrog steps taken
+    breakdown: bool
+    ritz_theta: np.ndarray        # every Ritz value of the last projection
+    ritz_rel_res: np.ndarray      # rel. residual of the in-interval ones (nan elsewhere)
+    basis: np.ndarray             # (k_used, n)
+    history: list = field(default_factory=list)
+
+
+def krylov_solve(S, m: np.ndarray, r0: np.ndarray, omega_min: float,
+                 omega_max: float, tau: float, L: int, kmax: int, tol: float,
+                 check_every: int = 5, keep_basis: bool = True) -> KrylovResult:
+    """Krylov space of C from r0 (Algorithm 2.4), projected problem
+    (eq. projevp) and residual acceptance (eq. res).
+
+    b_0 = r0/||r0||_M; for k = 0.. : w = C b_k, CGS2 in the M-inner product,
+    stop on breakdown, b_{k+1} = w/||w||_M, until kmax basis vectors exist.
+    Every ``check_every`` new vectors and at the end the projected problem is
+    solved; pairs with omega = sqrt(theta) in [omega_min, omega_max] and
+    rel_res <= tol are accepted (the last projection is returned)."""
+    alpha = alpha_table(omega_min, omega_max, tau, L)
+    n = len(m)
+    B = np.zeros((kmax, n))
+    B[0] = r0 / m_norm(r0, m)
+    k = 1
+    steps = 0
+    breakdown = False
+    history = []
+
+    def project(k):
+        theta, Y = rayleigh_ritz(S, B[:k])
+        omega = np.sqrt(theta)
+        inside = (omega >= omega_min) & (omega <= omega_max)
+        rel_all = np.full(k, np.nan)
+        X, a, r = ritz_residuals(S, m, B[:k], theta[inside], Y[:, inside])
+        rel_all[inside] = r
+        acc = r <= tol
+        history.append(dict(k=k, n_inside=int(inside.sum()), n_acc=int(acc.sum())))
+        return theta, rel_all, theta[inside][acc], r[acc], a[acc], X[acc]
+
+    while k < kmax:
+        w = filter_apply(S, m, B[k - 1], tau, alpha)
+        steps += L
+        b, nb, na = orthonormalize_cgs2(B[:k], w, m)
+        if b is None:
+            breakdown = True
+            break
+        B[k] = b
+        k += 1
+        if k % check_every == 0 and k < kmax:
+            project(k)
+    theta, rel_all, th_acc, rel_acc, abs_acc, X_acc = project(k)
+    return KrylovResult(omega2=th_acc, omega=np.sqrt(th_acc), rel_res=rel_acc,
+                        abs_res=abs_acc, vectors=X_acc, k_used=k,
+                        time_steps=steps, breakdown=breakdown, ritz_theta=theta,
+                        ritz_rel_res=rel_all,
+                        basis=B[:k] if keep_basis else None, history=history)

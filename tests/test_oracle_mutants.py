@@ -1,0 +1,129 @@
+"""Plant plausible mistakes in the oracle (on the CPU, by monkeypatching) and
+check that the pins of tests/test_oracle_pins.py catch every one of them.
+
+A pin that keeps passing on a broken oracle would prove nothing; these tests
+show that each slip listed below breaks at least one pin.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.kes_oracle as K
+from tests import test_oracle_pins as pins
+
+
+def _patch(monkeypatch, name, fn):
+    monkeypatch.setattr(K, name, fn)
+    monkeypatch.setattr(oracle, name, fn)
+
+
+def _leapfrog(S, m, r, tau, alpha, *, start_prev=None, sign=-1.0, shift=1,
+              use_mass=True):
+    """filter_apply with one configurable slip."""
+    L = len(alpha) - 1
+    y_prev = np.array(r if start_prev is None else start_prev(r), dtype=np.float64)
+    y = np.array(r, dtype=np.float64)
+    acc = alpha[0] * y
+    for l in range(L):
+        sy = S @ y
+        if use_mass:
+            sy = sy / m
+        y_next = sign * tau * tau * sy + 2.0 * y - y_prev
+        acc = acc + alpha[min(l + shift, L)] * y_next
+        y_prev, y = y, y_next
+    return acc
+
+
+MUTANTS_FILTER = {
+    "zero_previous_state": dict(start_prev=np.zeros_like),
+    "wrong_sign_of_stiffness_term": dict(sign=+1.0),
+    "weights_shifted_by_one_step": dict(shift=0),
+    "mass_inverse_dropped": dict(use_mass=False),
+}
+
+
+@pytest.mark.parametrize("mutant", sorted(MUTANTS_FILTER))
+def test_filter_mutants_are_caught(monkeypatch, mutant):
+    kw = MUTANTS_FILTER[mutant]
+    _patch(monkeypatch, "filter_apply", lambda S, m, r, tau, a: _leapfrog(S, m, r, tau, a, **kw))
+    caught = 0
+    for kind in ["random", "box"]:
+        try:
+            pins.test_filter_maps_eigenvectors_by_beta_tilde(kind)
+        except AssertionError:
+            caught += 1
+    assert caught >= 1
+
+
+def test_weight_factor_mutant_is_caught(monkeypatch):
+    orig = K.weight
+
+    def halved(t, wmin, wmax, T):
+        return 0.5 * orig(t, wmin, wmax, T)
+    _patch(monkeypatch, "weight", halved)
+    with pytest.raises(AssertionError):
+        pins.test_beta_tilde_tends_to_indicator()
+
+
+def test_weight_sum_difference_mutant_is_caught(monkeypatch):
+    def swapped(t, wmin, wmax, T):   # sum and difference frequencies swapped
+        t = np.asarray(t, dtype=np.float64)
+        out = np.zeros_like(t)
+        out[t == 0] = 2 * (wmax - wmin) / math.pi
+        i = (t > 0) & (t <= T)
+        ti = t[i]
+        out[i] = 4 / (math.pi * ti) * np.sin(0.5 * ti * (wmax + wmin)) * np.cos(0.5 * ti * (wmax - wmin))
+        return out
+    _patch(monkeypatch, "weight", swapped)
+    with pytest.raises(AssertionError):
+        pins.test_weight_equals_sine_difference_form()
+
+
+def test_alpha_without_tau_is_caught(monkeypatch):
+    def no_tau(wmin, wmax, tau, L):
+        return K.weight(np.arange(L + 1) * tau, wmin, wmax, L * tau)
+    _patch(monkeypatch, "alpha_table", no_tau)
+    with pytest.raises(AssertionError):
+        pins.test_alpha_table_indexing()
+
+
+def test_recurrence_mutant_is_caught(monkeypatch):
+    def q_bad(omega, tau, L):       # q_{-1} = 0 instead of 1
+        omega = np.atleast_1d(np.asarray(omega, dtype=np.float64))
+        q = np.empty((L + 1, omega.size))
+        qp, qc = np.zeros_like(omega), np.ones_like(omega)
+        q[0] = qc
+        for l in range(L):
+            qn = (2 - tau * tau * omega * omega) * qc - qp
+            q[l + 1] = qn
+            qp, qc = qc, qn
+        return q
+    _patch(monkeypatch, "q_values", q_bad)
+    with pytest.raises(AssertionError):
+        pins.test_q_is_chebyshev_third_kind()
+
+
+def test_euclidean_gram_schmidt_is_caught(monkeypatch):
+    def cgs2_l2(B, w, m):
+        w = np.array(w, dtype=np.float64)
+        nb = np.linalg.norm(w)
+        for _ in range(2):
+            if B.shape[0]:
+                w = w - (B @ w) @ B
+        na = np.linalg.norm(w)
+        return w / na, nb, na
+    _patch(monkeypatch, "orthonormalize_cgs2", cgs2_l2)
+    with pytest.raises(AssertionError):
+        pins.test_cgs2_gives_m_orthonormal_basis()
+
+
+def test_residual_without_mass_is_caught(monkeypatch):
+    def res_bad(S, m, B, theta, Y):
+        X = Y.T @ B
+        a = np.array([np.linalg.norm(S @ x - th * x) for th, x in zip(theta, X)])
+        return X, a, a / np.maximum(theta, 1e-300)
+    _patch(monkeypatch, "ritz_residuals", res_bad)
+    with pytest.raises(AssertionError):
+        pins.test_krylov_finds_every_distinct_eigenvalue_in_interval()

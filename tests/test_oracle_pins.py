@@ -1,0 +1,297 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each pin is chosen so that a plausible slip in the oracle (a dropped factor,
+a wrong sign or start value, a shifted index, the wrong inner product) breaks
+at least one of them; tests/test_oracle_mutants.py plants such slips and
+checks that they are caught.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+import oracle as O
+from oracle import spectra
+from fe_inputs import box_grid, square_grid, start_vectors, flared_tube
+
+
+def random_pencil(n, seed, density=0.2):
+    """A random sparse symmetric PSD S (graph Laplacian with random positive
+    weights plus a positive shift on a few nodes) and positive lumped masses."""
+    rng = np.random.default_rng(seed)
+    A = sp.random(n, n, density=density, random_state=seed, format="csr")
+    A = abs(A + A.T)
+    A.setdiag(0)
+    A.eliminate_zeros()
+    Lap = sp.diags(np.asarray(A.sum(axis=1)).ravel()) - A
+    shift = np.zeros(n)
+    shift[rng.choice(n, size=max(1, n // 5), replace=False)] = rng.uniform(0.5, 2, max(1, n // 5))
+    S = (Lap + sp.diags(shift)).tocsr()
+    m = rng.uniform(0.5, 2.0, n)
+    return S, m
+
+
+def dense_pencil(S, m):
+    w2, V = sla.eigh(S.toarray(), np.diag(m))    # V^T M V = I
+    return np.maximum(w2, 0.0), V
+
+
+# ---------------------------------------------------------------- eq. weightf
+
+def test_weight_at_zero_is_the_limit_of_the_formula():
+    for wmin, wmax in [(20.0, 30.0), (0.0, 3.0), (40.0, 45.0), (12.2, 12.5)]:
+        a0 = O.weight(np.array([0.0]), wmin, wmax, 1.0)[0]
+        assert a0 == pytest.approx(2.0 * (wmax - wmin) / math.pi, rel=1e-15)
+        t = np.array([1e-7])
+        assert O.weight(t, wmin, wmax, 1.0)[0] == pytest.approx(a0, rel=1e-9)
+
+
+def test_weight_equals_sine_difference_form():
+    # 2 sin(a) cos(b) = sin(a+b) + sin(a-b) turns eq. weightf into
+    # 2/(pi t) (sin(t wmax) - sin(t wmin)): a different expression of the same function
+    wmin, wmax, T = 1.6, 2.3, 30.0
+    t = np.linspace(1e-3, T, 5001)
+    ref = 2.0 / (math.pi * t) * (np.sin(t * wmax) - np.sin(t * wmin))
+    np.testing.assert_allclose(O.weight(t, wmin, wmax, T), ref, rtol=0, atol=1e-13)
+
+
+def test_weight_support_is_closed_interval():
+    wmin, wmax, T = 2.0, 4.0, 5.0
+    vals = O.weight(np.array([T, T * (1 + 1e-12), 2 * T]), wmin, wmax, T)
+    assert vals[0] != 0.0
+    assert vals[1] == 0.0 and vals[2] == 0.0
+
+
+def test_alpha_table_indexing():
+    wmin, wmax, tau, L = 20.0, 30.0, 0.0099, 300
+    a = O.alpha_table(wmin, wmax, tau, L)
+    assert a.shape == (L + 1,)
+    assert a[0] == pytest.approx(tau * 2 * (wmax - wmin) / math.pi, rel=1e-15)
+    t = L * tau
+    last = tau * 2.0 / (math.pi * t) * (math.sin(t * wmax) - math.sin(t * wmin))
+    assert a[L] == pytest.approx(last, rel=1e-10, abs=1e-15)
+    t = 7 * tau
+    a7 = tau * 2.0 / (math.pi * t) * (math.sin(t * wmax) - math.sin(t * wmin))
+    assert a[7] == pytest.approx(a7, rel=1e-12)
+
+
+# ---------------------------------------------------------------- eq. scalartimestep
+
+def test_q_is_chebyshev_third_kind():
+    # q_l = cos((l + 1/2) theta) / cos(theta / 2), cos(theta) = 1 - tau^2 w^2 / 2
+    tau, L = 0.01, 400
+    w = np.linspace(0.5, 1.99 / tau, 97)
+    q = O.q_values(w, tau, L)
+    theta = np.arccos(1.0 - 0.5 * tau * tau * w * w)
+    l = np.arange(L + 1)[:, None]
+    ref = np.cos((l + 0.5) * theta) / np.cos(0.5 * theta)
+    np.testing.assert_allclose(q, ref, rtol=0, atol=1e-9 * np.abs(ref).max())
+
+
+def test_q_special_cases():
+    tau, L = 0.5, 200                    # tau^2 w^2 = 4 exactly at w = 4
+    q0 = O.q_values([0.0], tau, L)[:, 0]
+    np.testing.assert_array_equal(q0, np.ones(L + 1))
+    qe = O.q_values([2.0 / tau], tau, L)[:, 0]
+    l = np.arange(L + 1)
+    np.testing.assert_allclose(qe, (-1.0) ** l * (2 * l + 1), rtol=1e-12)
+
+
+def test_q_bounded_inside_cfl_and_growing_outside():
+    tau, L = 0.1, 500
+    inside = O.q_values([0.95 * 2 / tau], tau, L)[:, 0]
+    theta = math.acos(1 - 0.5 * (0.95 * 2) ** 2)
+    assert np.abs(inside).max() <= 1 / math.cos(theta / 2) + 1e-9
+    outside = O.q_values([1.05 * 2 / tau], tau, L)[:, 0]
+    assert abs(outside[-1]) > 1e20
+
+
+# ---------------------------------------------------------------- Lemma 2.1 limit
+
+def test_beta_tilde_tends_to_indicator():
+    # Lemma 2.1 with eq. weightf: beta -> chi_[wmin, wmax] (1/2 at the ends)
+    # as tau -> 0 and T -> infinity
+    wmin, wmax = 2.0, 4.0
+    tau, L = 0.002, 200000               # T = 400
+    a = O.alpha_table(wmin, wmax, tau, L)
+    w = np.array([0.5, 1.0, 1.5, 2.0, 2.5, 3.0, 3.5, 4.0, 4.5, 6.0, 10.0])
+    b = O.beta_tilde(w, a, tau)
+    expect = np.array([0, 0, 0, 0.5, 1, 1, 1, 0.5, 0, 0, 0])
+    # the ends sit on the transition (width ~ pi/T) and move with the
+    # O(tau^2 w^2) phase error of the leapfrog, hence the looser bound there
+    atol = np.where(expect == 0.5, 2e-2, 6e-3)
+    assert np.all(np.abs(b - expect) <= atol), b
+
+
+def test_beta_tilde_is_rectangle_rule_of_beta():
+    # for tau -> 0 with T fixed, beta~ tends to the integral of eq. filterfunc
+    wmin, wmax, T = 2.0, 4.0, 6.0
+    w = np.array([1.0, 3.0, 5.0])
+    ts = np.linspace(0, T, 2_000_001)
+    f = O.weight(ts, wmin, wmax, T)[:, None] * np.cos(ts[:, None] * w[None, :])
+    integral = np.trapezoid(f, ts, axis=0)
+    L = 60000
+    tau = T / L
+    b = O.beta_tilde(w, O.alpha_table(wmin, wmax, tau, L), tau)
+    # rectangle rule = trapezoid + tau/2 (f(0) + f(T)), plus O(tau^2) from q_l ~ cos
+    np.testing.assert_allclose(b, integral, atol=2e-3)
+
+
+# ---------------------------------------------------------------- Lemma 2.3
+
+@pytest.mark.parametrize("kind", ["square", "box", "random", "tube"])
+def test_filter_maps_eigenvectors_by_beta_tilde(kind):
+    if kind == "square":
+        p = square_grid(7); S, m = p.to_scipy(), p.m
+    elif kind == "box":
+        p = box_grid((5, 4, 6), extent=(1.0, 0.7, 1.3)); S, m = p.to_scipy(), p.m
+    elif kind == "tube":
+        p = flared_tube(0.125, length=1.0, r0=0.2, growth=0.8); S, m = p.to_scipy(), p.m
+    else:
+        S, m = random_pencil(40, seed=3)
+    w2, V = dense_pencil(S, m)
+    w = np.sqrt(w2)
+    tau = 0.95 * 2 / w.max()
+    L = 60
+    alpha = O.alpha_table(0.3 * w.max(), 0.45 * w.max(), tau, L)
+    bt = O.beta_tilde(w, alpha, tau)
+    scale = np.abs(alpha).sum() * 2
+    for j in range(len(w)):
+        c = O.filter_apply(S, m, V[:, j], tau, alpha)
+        err = np.abs(c - bt[j] * V[:, j]).max() / np.abs(V[:, j]).max()
+        assert err < 1e-12 * scale, (j, err)
+
+
+def test_filter_is_polynomial_in_minv_s():
+    # eq. polyFilter: C = beta~(M^-1 S) = V diag(beta~) V^T M for M-orthonormal V
+    S, m = random_pencil(30, seed=11)
+    w2, V = dense_pencil(S, m)
+    w = np.sqrt(w2)
+    tau = 0.9 * 2 / w.max()
+    alpha = O.alpha_table(0.2 * w.max(), 0.5 * w.max(), tau, 45)
+    r = start_vectors(30, 1, 5)[0]
+    ref = V @ (O.beta_tilde(w, alpha, tau) * (V.T @ (m * r)))
+    got = O.filter_apply(S, m, r, tau, alpha)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_filter_is_m_self_adjoint():
+    S, m = random_pencil(50, seed=7)
+    w2, _ = dense_pencil(S, m)
+    tau = 0.9 * 2 / math.sqrt(w2.max())
+    alpha = O.alpha_table(1.0, 2.0, tau, 80)
+    x, y = start_vectors(50, 2, 9)
+    cx = O.filter_apply(S, m, x, tau, alpha)
+    cy = O.filter_apply(S, m, y, tau, alpha)
+    lhs, rhs = O.m_inner(cx, y, m), O.m_inner(x, cy, m)
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + abs(rhs) + 1)
+
+
+def test_filter_multi_equals_separate_runs():
+    p = square_grid(9)
+    S, m = p.to_scipy(), p.m
+    tau = 0.9 * 2 / math.sqrt(spectra.box_spectrum(p.cells, p.h).max())
+    L = 40
+    alphas = np.stack([O.alpha_table(a, b, tau, L) for a, b in [(5, 9), (9, 14), (14, 20)]])
+    R = start_vectors(p.n, 2, 4)
+    out = O.filter_apply_multi(S, m, R, tau, alphas)
+    for f in range(3):
+        for j in range(2):
+            np.testing.assert_allclose(out[f, j], O.filter_apply(S, m, R[j], tau, alphas[f]),
+                                       rtol=0, atol=1e-15)
+
+
+# ---------------------------------------------------------------- closed-form spectra
+
+@pytest.mark.parametrize("cells,extent", [((8, 8), None), ((6, 9), (1.0, 2.0)),
+                                          ((4, 4, 4), None), ((5, 6, 7), (1.0, 1.3, 0.8))])
+def test_tensor_grid_spectrum_matches_dense(cells, extent):
+    p = box_grid(cells, extent)
+    w2, _ = dense_pencil(p.to_scipy(), p.m)
+    ref = spectra.box_spectrum(p.cells, p.h)
+    np.testing.assert_allclose(np.sort(w2), ref, rtol=1e-13)
+
+
+def test_tensor_grid_eigenvector_closed_form():
+    p = box_grid((7, 5, 6))
+    S = p.to_scipy()
+    lam = 4 * 49 * math.sin(2 * math.pi / 14) ** 2 + 4 * 25 * math.sin(3 * math.pi / 10) ** 2 \
+        + 4 * 36 * math.sin(1 * math.pi / 12) ** 2
+    v = spectra.box_eigenvector(p.cells, (2, 3, 1))
+    r = S @ v - lam * p.m * v
+    assert np.abs(r).max() < 1e-13 * lam * np.abs(p.m * v).max()
+
+
+# ---------------------------------------------------------------- power iteration
+
+def test_power_iteration_reaches_largest_frequency():
+    S, m = random_pencil(60, seed=2)
+    w2, _ = dense_pencil(S, m)
+    got = O.power_iteration(S, m, start_vectors(60, 1, 0)[0], 2000)
+    assert got == pytest.approx(math.sqrt(w2.max()), rel=1e-6)
+
+
+def test_power_iteration_underestimates_within_cfl_margin():
+    p = square_grid(64)
+    wmax = math.sqrt(spectra.box_spectrum(p.cells, p.h).max())
+    got = O.power_iteration(p.to_scipy(), p.m, start_vectors(p.n, 1, 0)[0], 300)
+    assert got <= wmax * (1 + 1e-12)
+    assert got >= wmax / 1.05          # tau = 0.9 * 2 / got stays below 2 / wmax
+
+
+# ---------------------------------------------------------------- Gram-Schmidt
+
+def test_cgs2_gives_m_orthonormal_basis():
+    p = square_grid(12)
+    m = p.m
+    X = start_vectors(p.n, 25, 1)
+    X[5] = X[2] + 1e-6 * start_vectors(p.n, 1, 99)[0]   # nearly dependent column
+    B = np.zeros((0, p.n))
+    for x in X:
+        b, nb, na = O.orthonormalize_cgs2(B, x, m)
+        assert b is not None
+        B = np.vstack([B, b])
+    G = B @ (m[:, None] * B.T)
+    np.testing.assert_allclose(G, np.eye(len(B)), atol=1e-14)
+
+
+def test_cgs2_reports_breakdown_for_dependent_vector():
+    p = square_grid(10)
+    X = start_vectors(p.n, 3, 1)
+    B = np.zeros((0, p.n))
+    for x in X:
+        B = np.vstack([B, O.orthonormalize_cgs2(B, x, p.m)[0]])
+    b, nb, na = O.orthonormalize_cgs2(B, 2.0 * B[0] - 3.0 * B[2], p.m)
+    assert b is None and na < O.BREAKDOWN_RATIO * nb
+
+
+# ---------------------------------------------------------------- full solver
+
+def test_krylov_finds_every_distinct_eigenvalue_in_interval():
+    p = square_grid(32)
+    S = p.to_scipy()
+    exact, mult = spectra.distinct(spectra.eigenvalues_in(p.cells, p.h, 20.0, 30.0))
+    wmax = math.sqrt(spectra.box_spectrum(p.cells, p.h).max())
+    tau = 0.9 * 2 / wmax
+    res = O.krylov_solve(S, p.m, start_vectors(p.n, 1, 0)[0], 20.0, 30.0, tau, 300, 60, 1e-8)
+    assert len(res.omega2) == len(exact)
+    np.testing.assert_allclose(res.omega2, exact, rtol=1e-10)
+    assert np.all(res.rel_res <= 1e-8)
+    # residual recomputed from the returned vectors
+    for th, x in zip(res.omega2, res.vectors):
+        assert np.linalg.norm(S @ x - th * p.m * x) <= 1e-8 * th * np.linalg.norm(p.m * x)
+        assert O.m_norm(x, p.m) == pytest.approx(1.0, rel=1e-12)
+    assert res.time_steps == 59 * 300
+
+
+def test_krylov_breakdown_on_eigenvector_start():
+    p = square_grid(16)
+    v = spectra.box_eigenvector(p.cells, (3, 2))
+    lam = 4 * 256 * (math.sin(3 * math.pi / 32) ** 2 + math.sin(2 * math.pi / 32) ** 2)
+    tau = 0.9 * 2 / math.sqrt(spectra.box_spectrum(p.cells, p.h).max())
+    res = O.krylov_solve(p.to_scipy(), p.m, v, 0.8 * math.sqrt(lam), 1.2 * math.sqrt(lam),
+                         tau, 100, 10, 1e-8)
+    assert res.breakdown and res.k_used == 1
+    assert res.omega2[0] == pytest.approx(lam, rel=1e-13)
