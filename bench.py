@@ -1,0 +1,394 @@
+#!/usr/bin/env python3
+"""Benchmark of the filtered time-domain Krylov eigensolver on GB300.
+
+One step = one full eigensolve on the workload (every part of the hot path):
+weights (eq. weightf), kmax-1 filter applications of L fused leapfrog steps
+(eq. 2stepmethod, eq. disc_filtercoeff), M-orthonormalisation (Algorithm 2.4),
+Rayleigh-Ritz (eq. projevp) and residual acceptance (eq. res). The default
+workload is the 128^3 Kuhn cube (2,048,383 dofs, 30,340,171 entries), interval
+[40, 45], L = 600, Krylov dimension 60, FP64.
+
+Metric: GDOF*steps/s = dofs * leapfrog steps / time / 1e9 (whole job, all
+ranks). The line also carries the roofline of the fused step kernel, the
+oracle timed on the host cores (cpu_baseline) and the end-to-end number
+through the C ABI with host buffers (e2e).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl kes|reference]
+Under torchrun (N > 1) every rank solves its own replica (its own start
+vector); value = all ranks' dof-steps / max-over-ranks time ("weak" scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GDOF*steps/s"
+FALLBACK_HBM_GBS = 6800.0
+STEP_KERNEL_SRC = os.path.join(ROOT, "paper_2402_08515_gb300", "csrc", "kernels_step.cu")
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="cube128_fp64")
+    ap.add_argument("--impl", default="kes", choices=["kes", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="solve", choices=["solve", "filter"],
+                    help="filter: one filter application only (small profiling runs)")
+    ap.add_argument("--L", type=int, default=0, help="override the workload's time steps (--mode filter)")
+    return ap.parse_args(argv)
+
+
+# ----------------------------------------------------------------------------- ranks
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def init_dist(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist if world > 1 else None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, value: float, device=None) -> float:
+    """Max of a float over all ranks (timing only; no data-path collective)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, value: float, device=None) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        rows = list(csv.reader(open(self.path)))
+        os.unlink(self.path)
+        sm, smax, names = [], [], set()
+        keys = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for k, v in zip(keys, r[5:9]):
+                if v.strip().lower() == "active":
+                    names.add(k)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(names),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- peaks & profiles
+
+def load_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    return hashlib.sha256(open(STEP_KERNEL_SRC, "rb").read()).hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per step-kernel launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"step_kernel_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
+    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not h or not t or h.group(1) != kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+# ----------------------------------------------------------------------------- CPU baseline
+
+def oracle_sample(problem, tau, wl, seconds: float):
+    """Times the oracle's filter application (as it stands) on a bounded number of
+    leapfrog steps of the same workload; returns (GDOF*steps/s, steps, seconds)."""
+    import numpy as np
+    import oracle as O
+    from fe_inputs import start_vectors
+    S = problem.to_scipy()
+    r = start_vectors(problem.n, 1, wl.seed)[0]
+    probe = 5
+    t0 = time.perf_counter()
+    O.filter_apply(S, problem.m, r, tau, O.alpha_table(wl.omega_min, wl.omega_max, tau, probe))
+    per_step = (time.perf_counter() - t0) / probe
+    steps = int(max(5, min(wl.L, seconds / max(per_step, 1e-6))))
+    alpha = O.alpha_table(wl.omega_min, wl.omega_max, tau, steps)
+    t0 = time.perf_counter()
+    out = O.filter_apply(S, problem.m, r, tau, alpha)
+    dt = time.perf_counter() - t0
+    assert np.isfinite(out).all()
+    return problem.n * steps / dt / 1e9, steps, dt
+
+
+def cpu_cores_used() -> int:
+    # scipy's CSR matvec and numpy's elementwise ops run on one thread
+    return 1
+
+
+# ----------------------------------------------------------------------------- kes arm
+
+def run_kes(args):
+    import numpy as np
+    import torch
+
+    import paper_2402_08515_gb300 as K
+    from fe_inputs import WORKLOADS, start_vectors
+    from oracle import spectra
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    dev = torch.device("cuda", local)
+    wl = WORKLOADS[args.workload]
+    problem = wl.build()
+    n = problem.n
+    stream = torch.cuda.Stream(device=dev)
+    ctx = K.Context(problem, precision=wl.precision, stream=stream)
+    h = ctx.handle
+    v0 = start_vectors(n, 1, wl.seed)[0]
+    omega_pow, gersh = K.kes_estimate_omega_max(h, wl.power_iters, v0)
+    tau = wl.cfl * 2.0 / omega_pow
+    K.kes_set_filter(h, wl.omega_min, wl.omega_max, tau, wl.L)
+    so = K.kes_solve_opts_default()
+    so.kmax, so.tol = wl.kmax, (1e-8 if wl.precision == "fp64" else 1e-5)
+    r0_host = start_vectors(n, 1, wl.seed + 1 + rank)[0]
+    r0_dev = torch.from_numpy(r0_host).to(dev)
+    torch.cuda.synchronize()
+    if args.mode == "filter":
+        L = args.L or wl.L
+        K.kes_set_filter(h, wl.omega_min, wl.omega_max, tau, L)
+        out = torch.zeros((1, 1, n), dtype=torch.float64, device=dev)
+        K.kes_filter_apply(h, r0_dev[None, :], out, 1)
+        K.kes_sync(h)
+        st = K.kes_get_stats(h)
+        if rank == 0:
+            print(json.dumps({"mode": "filter", "workload": args.workload, "L": L, "dofs": n,
+                              "filter_ms": st["filter_ms"], "finite": bool(torch.isfinite(out).all())}))
+        ctx.close()
+        return
+
+    def solve():
+        return K.kes_krylov_solve(h, r0_dev, so)
+
+    for _ in range(max(args.warmup, 0)):
+        res = solve()
+    K.kes_reset_stats(h)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(dist)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(args.steps):
+                res = solve()
+            e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(dist)
+    ms_local = e0.elapsed_time(e1)
+    stats = K.kes_get_stats(h)
+    ms_total = max_over_ranks(dist, ms_local, dev)
+    units_local = n * res["time_steps"] * args.steps
+    units = sum_over_ranks(dist, units_local, dev)
+    value = units / (ms_total / 1e3) / 1e9
+
+    # roofline of the fused step kernel, timed by the library's CUDA events on its stream
+    step_ms = stats["filter_ms"] / max(stats["filter_steps"], 1)
+    bytes_step = K.kes_step_bytes(h, 1, 1)
+    achieved = bytes_step / (step_ms / 1e3) / 1e9
+    peak, peak_src = load_peak()
+    traffic = profiled_traffic(args.workload)
+
+    # end to end through the C ABI with host buffers: r0 from pinned memory in,
+    # accepted Ritz pairs (values and vectors) out, every step
+    r0_pinned = torch.from_numpy(r0_host).pin_memory()
+    so_e2e = K.kes_solve_opts_default()
+    so_e2e.kmax, so_e2e.tol, so_e2e.want_vectors = so.kmax, so.tol, 1
+    e2e_steps = args.e2e_steps
+    barrier(dist)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out_bytes = 0
+    r = res
+    for _ in range(e2e_steps):
+        r = K.kes_krylov_solve(h, r0_pinned.numpy(), so_e2e)
+        out_bytes = (r["vectors"].nbytes if r["vectors"] is not None else 0) + 4 * r["n_pairs"] * 8
+    torch.cuda.synchronize()
+    e2e = None
+    if e2e_steps > 0:
+        e2e_s = max_over_ranks(dist, (time.perf_counter() - t0) / e2e_steps, dev)
+        e2e = {"value": sum_over_ranks(dist, n * r["time_steps"], dev) / e2e_s / 1e9, "unit": METRIC,
+               "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": out_bytes}
+
+    # accuracy of the accepted pairs against the exact spectrum (tensor grids)
+    eig_err = None
+    if problem.cells and res["n_pairs"]:
+        exact = spectra.eigenvalues_in(problem.cells, problem.h, wl.omega_min, wl.omega_max)
+        eig_err = float(max(np.min(np.abs(exact - t)) / t for t in res["omega2"]))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, steps, dt = oracle_sample(problem, tau, wl, args.cpu_seconds)
+        cpu = {"value": v, "unit": METRIC, "cores": cpu_cores_used(), "kind": "oracle",
+               "sample": f"{steps} leapfrog steps of the FP64 oracle filter on the same matrix ({dt:.1f} s)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wl.precision == "fp64" else "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "dofs": n, "nnz": problem.nnz, "interval": [wl.omega_min, wl.omega_max],
+                   "L": wl.L, "kmax": wl.kmax, "tau": tau, "omega_max_power": omega_pow,
+                   "format": "SELL-32 (sigma=1)", "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (matrix > 129 MB)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                     "kernel": "k_step_f64" if wl.precision == "fp64" else "k_step_f32",
+                     "step_us": step_ms * 1e3, "algorithmic_bytes_per_step": bytes_step},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(stats["kernel_launches"]),
+        "clocks": clk.summary(),
+        "solve": {"accepted_pairs": res["n_pairs"], "k_used": res["k_used"], "time_steps": res["time_steps"],
+                  "max_rel_res": float(res["rel_res"].max()) if res["n_pairs"] else None,
+                  "max_eig_rel_err_vs_exact": eig_err, "filter_ms_share": stats["filter_ms"] / ms_local},
+    }
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    from fe_inputs import WORKLOADS, start_vectors
+    wl = WORKLOADS[args.workload]
+    problem = wl.build()
+    S = problem.to_scipy()
+    omega_pow = O.power_iteration(S, problem.m, start_vectors(problem.n, 1, wl.seed)[0], wl.power_iters)
+    tau = wl.cfl * 2.0 / omega_pow
+    per_step_budget = max(1.0, 60.0 / max(args.steps + args.warmup, 1))
+    samples = []
+    for i in range(args.warmup + args.steps):
+        v, steps, dt = oracle_sample(problem, tau, wl, per_step_budget)
+        if i >= args.warmup:
+            samples.append((v, steps, dt))
+    total_units = sum(problem.n * s for _, s, _ in samples)
+    total_s = sum(dt for _, _, dt in samples)
+    value = total_units / total_s / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / max(len(samples), 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "dofs": problem.n, "nnz": problem.nnz,
+                   "interval": [wl.omega_min, wl.omega_max], "L": wl.L, "kmax": wl.kmax, "tau": tau},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": cpu_cores_used(), "kind": "oracle",
+                         "sample": f"each step = {samples[0][1] if samples else 0} leapfrog steps of the FP64 "
+                                   f"oracle filter on the full matrix"},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_kes(args)
+
+
+if __name__ == "__main__":
+    main()

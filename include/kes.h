@@ -1,0 +1,206 @@
+/*
+ * kes.h -- C ABI of the filtered time-domain Krylov eigensolver for GB300.
+ *
+ * Method: Nannen & Wess, "A Krylov Eigenvalue Solver Based on Filtered Time
+ * Domain Solutions" (arXiv:2402.08515), Sec. 2. The library finds eigenpairs
+ * (omega^2, v) of S v = omega^2 M v (eq. def:basisMatrixEVP) with omega in a
+ * chosen interval [omega_min, omega_max], for a sparse symmetric positive
+ * semi-definite S and a lumped (diagonal, positive) M (Remark rmk:mass_lumping).
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns a kes_status (0 = success); no C++ exception and
+ *     no CUDA error crosses the ABI. kes_strerror() names a status.
+ *   - Arrays are plain pointers. "host" pointers are ordinary CPU memory,
+ *     "device" pointers are CUDA global memory on the context's device.
+ *     A `mem` argument (KES_MEM_HOST / KES_MEM_DEVICE) says which.
+ *   - Blocks of vectors are n x b column-major: vector j starts at j * n.
+ *   - The library copies every input it keeps; the caller keeps ownership of
+ *     what it passes. Results returned through kes_result are owned by the
+ *     library and released with kes_result_free().
+ *   - All GPU work is issued on the context's stream (kes_opts.stream). Calls
+ *     that return host data synchronise that stream; kes_filter_apply with
+ *     device pointers does not (use kes_sync).
+ *   - Indices are 0-based. Real symmetric input only; Dirichlet dofs must be
+ *     eliminated by the caller.
+ */
+#ifndef KES_H
+#define KES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kes_ctx kes_ctx;
+
+typedef enum kes_status {
+  KES_OK = 0,
+  KES_INFO_INVARIANT_SUBSPACE = 1, /* Krylov breakdown: an invariant subspace was found (Algorithm 2.4, "exact eigenspace found") */
+  KES_ERR_ARG = -1,                /* invalid argument (null pointer, size, range, ordering) */
+  KES_ERR_MASS = -2,               /* a lumped mass entry is <= 0 or not finite */
+  KES_ERR_UNSTABLE = -3,           /* CFL violated (tau * omega_max >= 2) or the time stepping produced Inf/NaN */
+  KES_ERR_CUDA = -4,               /* a CUDA runtime call failed */
+  KES_ERR_OOM = -5,                /* device or host allocation failed */
+  KES_ERR_TIMEOUT = -6,            /* a bounded device-side wait gave up */
+  KES_ERR_STATE = -7,              /* call out of order (e.g. filter not set) */
+  KES_ERR_UNSUPPORTED = -8         /* option combination not implemented */
+} kes_status;
+
+enum kes_precision {
+  KES_PREC_FP64 = 0, /* FP64 matrix values, state and accumulation */
+  KES_PREC_FP32 = 1  /* FP32 matrix values and leapfrog state, compensated (two-sum) FP32 accumulation;
+                        orthogonalisation, Rayleigh-Ritz and residuals stay FP64 */
+};
+
+enum kes_mem { KES_MEM_DEVICE = 0, KES_MEM_HOST = 1 };
+
+/* Options of kes_create. Initialise with kes_opts_default(). */
+typedef struct kes_opts {
+  int32_t precision;   /* enum kes_precision */
+  int32_t sell_sigma;  /* SELL-C-sigma sorting window in rows (slices are C = 32 rows); 1 keeps the row order */
+  int32_t use_graph;   /* 1: the L time steps of a filter application replay as one CUDA graph; 0: plain launches */
+  int32_t block_b;     /* largest number of start vectors filtered together (columns of kes_filter_apply) */
+  void* stream;        /* cudaStream_t for every launch; NULL: the context creates its own non-blocking stream */
+  /* Optional device allocator (e.g. a framework's caching allocator). Both NULL: cudaMalloc / cudaFree. */
+  void* (*dev_alloc)(size_t bytes, void* user);
+  void (*dev_free)(void* ptr, size_t bytes, void* user);
+  void* alloc_user;
+} kes_opts;
+
+/* Options of kes_krylov_solve. Initialise with kes_solve_opts_default(). */
+typedef struct kes_solve_opts {
+  int32_t kmax;         /* Krylov dimension: number of basis vectors b_0..b_{kmax-1} (kmax-1 filter applications) */
+  int32_t check_every;  /* solve the projected problem every this many new basis vectors (and at the end) */
+  int32_t n_wanted;     /* stop as soon as this many pairs are accepted (0: run to kmax) */
+  int32_t want_vectors; /* 1: return the accepted Ritz vectors B y (host, n x n_pairs col-major) */
+  double tol;           /* acceptance: rel_res = ||S x - theta M x||_2 / (theta ||M x||_2) <= tol */
+} kes_solve_opts;
+
+/* Result of kes_krylov_solve; host memory owned by the library. */
+typedef struct kes_result {
+  int64_t n;             /* problem size */
+  int32_t n_pairs;       /* accepted pairs: omega in [omega_min, omega_max] and rel_res <= tol */
+  int32_t k_used;        /* basis size reached */
+  int32_t breakdown;     /* 1 if the Krylov space became invariant (status KES_INFO_INVARIANT_SUBSPACE) */
+  int32_t n_ritz;        /* Ritz values of the last projection */
+  int64_t time_steps;    /* leapfrog steps taken (per start vector) */
+  double* omega2;        /* [n_pairs] accepted theta = omega^2, ascending */
+  double* omega;         /* [n_pairs] sqrt(theta) */
+  double* rel_res;       /* [n_pairs] relative residual */
+  double* abs_res;       /* [n_pairs] ||(S - theta M) x||_2 with ||x||_M = 1 (eq. res) */
+  double* vectors;       /* n x n_pairs col-major, or NULL unless want_vectors */
+  double* ritz_omega2;   /* [n_ritz] every Ritz value of the last projection, ascending */
+  double* ritz_rel_res;  /* [n_ritz] relative residual of the in-interval ones, NaN elsewhere */
+  double solve_ms;       /* wall time of the call */
+} kes_result;
+
+/* Counters accumulated by a context since creation or kes_reset_stats. */
+typedef struct kes_stats {
+  int64_t filter_calls;     /* filter applications (one per start-vector block) */
+  int64_t filter_steps;     /* fused leapfrog steps launched (kernel launches of the step kernel) */
+  int64_t kernel_launches;  /* every kernel this library launched (graph nodes counted one by one) */
+  double filter_ms;         /* device time of the filter applications (CUDA events on the context stream) */
+  double solve_other_ms;    /* device time of orthogonalisation, projection and residuals */
+  int64_t bytes_per_step;   /* algorithmic HBM bytes of one fused step (see kes_step_bytes) */
+} kes_stats;
+
+void kes_opts_default(kes_opts* opts);
+void kes_solve_opts_default(kes_solve_opts* opts);
+const char* kes_strerror(int32_t status);
+
+/*
+ * kes_create -- upload S (CSR) and the lumped mass diagonal m (Sec. 2,
+ * eq. def:basisMatrixEVP with Remark rmk:mass_lumping) and build the device
+ * format (SELL-C-sigma, C = 32).
+ *   n        number of dofs (rows), 1 <= n < 2^31
+ *   row_ptr  host int64[n+1], row_ptr[0] = 0, non-decreasing
+ *   col      host int32[nnz], column indices in [0, n), ascending inside a row
+ *   val      host float64[nnz], S values (S must be symmetric PSD; not checked beyond finiteness)
+ *   m_diag   host float64[n], lumped masses, all > 0 (else KES_ERR_MASS)
+ *   opts     NULL for defaults
+ * On success *out owns device copies; release with kes_destroy().
+ */
+kes_status kes_create(kes_ctx** out, int64_t n, const int64_t* row_ptr, const int32_t* col,
+                      const double* val, const double* m_diag, const kes_opts* opts);
+void kes_destroy(kes_ctx* ctx);
+int64_t kes_size(const kes_ctx* ctx);
+kes_status kes_sync(kes_ctx* ctx);
+
+/*
+ * kes_estimate_omega_max -- largest eigenfrequency of the pencil by power
+ * iteration on M^{-1} S (Sec. 3.1: the stable time step is found by a power
+ * iteration). v <- M^{-1} S v / ||M^{-1} S v||_2, `iters` times from the host
+ * vector v0[n]; *omega_max = sqrt((v^T S v) / (v^T M v)). A power iteration
+ * approaches the largest value from below; the CFL condition tau < 2/omega
+ * (Sec. 2.3, after eq. scalartimestep) is why callers take tau = 0.9 * 2 / omega_max.
+ * *gershgorin (may be NULL) receives the upper bound sqrt(max_i sum_j |s_ij| / m_i).
+ */
+kes_status kes_estimate_omega_max(kes_ctx* ctx, int32_t iters, const double* v0, double* omega_max,
+                                  double* gershgorin);
+
+/*
+ * kes_set_filter -- weights alpha_n = tau * alpha(n tau), n = 0..L, of
+ * eq. (weightf) sampled by the rectangle rule of eq. (disc_filtercoeff),
+ * with T = L tau. L is the number of leapfrog steps (L+1 weighted samples,
+ * the last at t = T). Requires 0 <= omega_min < omega_max, tau > 0, L >= 1.
+ * Returns KES_ERR_UNSTABLE if tau * gershgorin >= 2 (the CFL bound is then
+ * violated for certain).
+ * kes_set_filters sets F weight tables (intervals) that share tau and L;
+ * kes_filter_apply then returns F filtered blocks from one trajectory.
+ */
+kes_status kes_set_filter(kes_ctx* ctx, double omega_min, double omega_max, double tau, int32_t L);
+kes_status kes_set_filters(kes_ctx* ctx, int32_t F, const double* omega_min, const double* omega_max,
+                           double tau, int32_t L);
+
+/* Host helpers, no context and no GPU needed. */
+/* kes_alpha_table: alpha[0..L] = tau * alpha(n tau) of eq. (weightf), T = L tau. */
+kes_status kes_alpha_table(double omega_min, double omega_max, double tau, int32_t L, double* alpha);
+/* kes_filter_response: beta~(omega_i), i < k, of eq. (fullydiscfilter), the factor that
+   the filter applies to an eigenvector of frequency omega (Lemma 2.3). */
+kes_status kes_filter_response(double omega_min, double omega_max, double tau, int32_t L,
+                               const double* omega, int64_t k, double* beta);
+/* kes_sym_eig: eigenvalues (ascending, w[k]) and orthonormal eigenvectors (V, k x k col-major,
+   may be NULL) of the symmetric k x k col-major matrix A (only its lower triangle is read).
+   This is the small projected problem of eq. (projevp) with B^T M B = I. */
+kes_status kes_sym_eig(int32_t k, const double* A, double* w, double* V);
+/* kes_step_bytes: algorithmic HBM bytes of one fused leapfrog step of this context for b vectors
+   and F intervals (every matrix entry, row pointer and per-row vector read or written once). */
+int64_t kes_step_bytes(const kes_ctx* ctx, int32_t b, int32_t F);
+
+/*
+ * kes_filter_apply -- r_out = C r_in for b vectors (eq. disc_filtercoeff): L
+ * leapfrog steps y_{l+1} = -tau^2 M^{-1} S y_l + 2 y_l - y_{l-1}, y_{-1} = y_0 = r
+ * (eq. 2stepmethod), accumulating sum_{n=0..L} alpha_n y_n. Each step is one
+ * fused kernel (SpMV, diagonal scale, three-term update, weighted accumulation).
+ *   r_in   n x b col-major float64 (host or device per `mem`)
+ *   r_out  F x b x n float64 (block f holds the sum with weight table f)
+ *   b      1 <= b <= opts.block_b
+ * Device pointers: asynchronous on the context stream. Host pointers: the
+ * call copies in, runs and copies out before returning.
+ * KES_ERR_UNSTABLE if a non-finite value appeared in the state.
+ */
+kes_status kes_filter_apply(kes_ctx* ctx, const double* r_in, double* r_out, int32_t b, int32_t mem);
+
+/*
+ * kes_krylov_solve -- Krylov space of C from r0 (Algorithm 2.4, with the
+ * M-inner product and two classical Gram-Schmidt passes), Rayleigh-Ritz on it
+ * (eq. projevp) and residual acceptance (eq. res).
+ *   r0     start vector, length n (host or device per `mem`); it is M-normalised first
+ *   sopts  NULL for defaults
+ *   out    receives a kes_result (free with kes_result_free); set even on
+ *          KES_INFO_INVARIANT_SUBSPACE.
+ * Requires a single filter interval (kes_set_filter).
+ */
+kes_status kes_krylov_solve(kes_ctx* ctx, const double* r0, int32_t mem, const kes_solve_opts* sopts,
+                            kes_result** out);
+void kes_result_free(kes_result* res);
+
+kes_status kes_get_stats(kes_ctx* ctx, kes_stats* stats); /* synchronises the stream */
+kes_status kes_reset_stats(kes_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KES_H */

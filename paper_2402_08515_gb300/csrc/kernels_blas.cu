@@ -1,0 +1,263 @@
+// FP64 vector kernels of the Krylov loop (Algorithm 2.4, orthogonalisation),
+// the projection (eq. projevp) and the residuals (eq. res).
+//
+// All reductions are deterministic: every block writes one partial per
+// column in a fixed row order and a second kernel sums the partials in a
+// fixed tree order, so repeated runs give bit-identical results.
+#include <cuda_runtime.h>
+
+#include "kes_internal.h"
+
+namespace kes {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kGroup = 8;  // columns per block in the multi-column kernels
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Reduces G per-thread values over the block; thread 0 of warp 0 ends with the sums in out[].
+template <int G>
+__device__ __forceinline__ void block_sum(double (&v)[G], double (&out)[G]) {
+  __shared__ double sh[G][kThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const double s = warp_sum(v[g]);
+    if (lane == 0) sh[g][warp] = s;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      double s = lane < kThreads / 32 ? sh[g][lane] : 0.0;
+      out[g] = warp_sum(s);
+    }
+  }
+}
+
+// partial[j * nblk + blk] = sum over this block's rows of B[j*ldb + i] * w[i] * v[i]
+__global__ void __launch_bounds__(kThreads) k_mdot_partial(const double* __restrict__ B, int64_t ldb, int k,
+                                                           const double* __restrict__ v,
+                                                           const double* __restrict__ w, int64_t n,
+                                                           double* __restrict__ partial) {
+  const int j0 = blockIdx.y * kGroup;
+  double acc[kGroup];
+#pragma unroll
+  for (int g = 0; g < kGroup; ++g) acc[g] = 0.0;
+  const int ng = min(kGroup, k - j0);
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * kThreads) {
+    const double wv = w ? w[i] * v[i] : v[i];
+#pragma unroll
+    for (int g = 0; g < kGroup; ++g)
+      if (g < ng) acc[g] = fma(B[(j0 + g) * ldb + i], wv, acc[g]);
+  }
+  double tot[kGroup];
+  block_sum<kGroup>(acc, tot);
+  if (threadIdx.x == 0)
+    for (int g = 0; g < ng; ++g) partial[static_cast<int64_t>(j0 + g) * gridDim.x + blockIdx.x] = tot[g];
+}
+
+// out[j] = sum_b partial[j * nblk + b]
+__global__ void __launch_bounds__(kThreads) k_reduce_partial(const double* __restrict__ partial, int nblk,
+                                                             double* __restrict__ out) {
+  const int j = blockIdx.x;
+  double v[1] = {0.0};
+  for (int b = threadIdx.x; b < nblk; b += kThreads) v[0] += partial[static_cast<int64_t>(j) * nblk + b];
+  double tot[1];
+  block_sum<1>(v, tot);
+  if (threadIdx.x == 0) out[j] = tot[0];
+}
+
+__global__ void __launch_bounds__(kThreads) k_gemv_sub(double* __restrict__ v, const double* __restrict__ B,
+                                                       int64_t ldb, int k, const double* __restrict__ h,
+                                                       int64_t n) {
+  extern __shared__ double sh_h[];
+  for (int j = threadIdx.x; j < k; j += kThreads) sh_h[j] = h[j];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * kThreads) {
+    double s0 = 0.0, s1 = 0.0;
+    int j = 0;
+    for (; j + 2 <= k; j += 2) {
+      s0 = fma(B[j * ldb + i], sh_h[j], s0);
+      s1 = fma(B[(j + 1) * ldb + i], sh_h[j + 1], s1);
+    }
+    if (j < k) s0 = fma(B[j * ldb + i], sh_h[j], s0);
+    v[i] -= s0 + s1;
+  }
+}
+
+__global__ void k_scale_rsqrt(const double* __restrict__ v, const double* __restrict__ nrm2,
+                              double* __restrict__ dst, double* __restrict__ dst2, int64_t n) {
+  const double nrm = sqrt(nrm2[0]);
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const double x = v[i] / nrm;
+    dst[i] = x;
+    if (dst2) dst2[i] = x;
+  }
+}
+
+// Ritz residual partial sums for Ritz vectors j0 .. j0+kGroup-1:
+// partial[j * nblk + blk] = sum_i (sx_j - theta_j m_i x_j)^2, partial[(p + j) * nblk + blk] = sum_i (m_i x_j)^2
+__global__ void __launch_bounds__(kThreads) k_ritz_residual(const double* __restrict__ B,
+                                                            const double* __restrict__ SB, int64_t ldb, int k,
+                                                            const double* __restrict__ Y,
+                                                            const double* __restrict__ theta, int p,
+                                                            const double* __restrict__ m, int64_t n,
+                                                            double* __restrict__ partial) {
+  extern __shared__ double sY[];  // k x kGroup
+  const int j0 = blockIdx.y * kGroup;
+  const int ng = min(kGroup, p - j0);
+  for (int t = threadIdx.x; t < k * kGroup; t += kThreads) {
+    const int l = t / kGroup, g = t % kGroup;
+    sY[t] = g < ng ? Y[static_cast<int64_t>(j0 + g) * k + l] : 0.0;
+  }
+  __syncthreads();
+  double th[kGroup];
+#pragma unroll
+  for (int g = 0; g < kGroup; ++g) th[g] = g < ng ? theta[j0 + g] : 0.0;
+  double rr[kGroup], mm[kGroup];
+#pragma unroll
+  for (int g = 0; g < kGroup; ++g) rr[g] = mm[g] = 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * kThreads) {
+    double x[kGroup], sx[kGroup];
+#pragma unroll
+    for (int g = 0; g < kGroup; ++g) x[g] = sx[g] = 0.0;
+    for (int l = 0; l < k; ++l) {
+      const double b = B[l * ldb + i], sb = SB[l * ldb + i];
+#pragma unroll
+      for (int g = 0; g < kGroup; ++g) {
+        x[g] = fma(b, sY[l * kGroup + g], x[g]);
+        sx[g] = fma(sb, sY[l * kGroup + g], sx[g]);
+      }
+    }
+    const double mi = m[i];
+#pragma unroll
+    for (int g = 0; g < kGroup; ++g) {
+      const double mx = mi * x[g];
+      const double r = sx[g] - th[g] * mx;
+      rr[g] = fma(r, r, rr[g]);
+      mm[g] = fma(mx, mx, mm[g]);
+    }
+  }
+  double trr[kGroup], tmm[kGroup];
+  block_sum<kGroup>(rr, trr);
+  __syncthreads();
+  block_sum<kGroup>(mm, tmm);
+  if (threadIdx.x == 0)
+    for (int g = 0; g < ng; ++g) {
+      partial[static_cast<int64_t>(j0 + g) * gridDim.x + blockIdx.x] = trr[g];
+      partial[static_cast<int64_t>(p + j0 + g) * gridDim.x + blockIdx.x] = tmm[g];
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_gemm_bx(const double* __restrict__ B, int64_t ldb, int k,
+                                                      const double* __restrict__ Y, int p,
+                                                      double* __restrict__ X, int64_t ldx, int64_t n) {
+  extern __shared__ double sY[];
+  const int j0 = blockIdx.y * kGroup;
+  const int ng = min(kGroup, p - j0);
+  for (int t = threadIdx.x; t < k * kGroup; t += kThreads) {
+    const int l = t / kGroup, g = t % kGroup;
+    sY[t] = g < ng ? Y[static_cast<int64_t>(j0 + g) * k + l] : 0.0;
+  }
+  __syncthreads();
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * kThreads) {
+    double x[kGroup];
+#pragma unroll
+    for (int g = 0; g < kGroup; ++g) x[g] = 0.0;
+    for (int l = 0; l < k; ++l) {
+      const double b = B[l * ldb + i];
+#pragma unroll
+      for (int g = 0; g < kGroup; ++g) x[g] = fma(b, sY[l * kGroup + g], x[g]);
+    }
+    for (int g = 0; g < ng; ++g) X[(j0 + g) * ldx + i] = x[g];
+  }
+}
+
+__global__ void k_permute(const double* __restrict__ src, double* __restrict__ dst,
+                          const int32_t* __restrict__ perm, int64_t n, bool gather) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    if (gather) dst[i] = src[perm[i]];
+    else dst[perm[i]] = src[i];
+  }
+}
+
+__global__ void k_scale(const double* __restrict__ src, double s, double* __restrict__ dst, int64_t n) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    dst[i] = src[i] * s;
+}
+
+int rows_grid(int64_t n, int cap) {
+  const int64_t b = (n + kThreads - 1) / kThreads;
+  return static_cast<int>(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+}  // namespace
+
+void launch_mdot(cudaStream_t st, const double* B, int64_t ldb, int k, const double* v, const double* w,
+                 int64_t n, double* partial, double* h) {
+  if (k <= 0) return;
+  const int nblk = rows_grid(n, kDotBlocks);
+  dim3 grid(nblk, (k + kGroup - 1) / kGroup);
+  k_mdot_partial<<<grid, kThreads, 0, st>>>(B, ldb, k, v, w, n, partial);
+  k_reduce_partial<<<k, kThreads, 0, st>>>(partial, nblk, h);
+  g_launches += 2;
+}
+
+void launch_gemv_sub(cudaStream_t st, double* v, const double* B, int64_t ldb, int k, const double* h,
+                     int64_t n) {
+  if (k <= 0) return;
+  k_gemv_sub<<<rows_grid(n, 2048), kThreads, k * sizeof(double), st>>>(v, B, ldb, k, h, n);
+  ++g_launches;
+}
+
+void launch_scale_rsqrt(cudaStream_t st, const double* v, const double* nrm2, double* dst, double* dst2,
+                        int64_t n) {
+  k_scale_rsqrt<<<rows_grid(n, 2048), kThreads, 0, st>>>(v, nrm2, dst, dst2, n);
+  ++g_launches;
+}
+
+void launch_ritz_residual(cudaStream_t st, const double* B, const double* SB, int64_t ldb, int k,
+                          const double* Y, const double* theta, int p, const double* m, int64_t n,
+                          double* partial, double* out) {
+  if (p <= 0) return;
+  const int nblk = rows_grid(n, kDotBlocks);
+  dim3 grid(nblk, (p + kGroup - 1) / kGroup);
+  k_ritz_residual<<<grid, kThreads, k * kGroup * sizeof(double), st>>>(B, SB, ldb, k, Y, theta, p, m, n,
+                                                                       partial);
+  k_reduce_partial<<<2 * p, kThreads, 0, st>>>(partial, nblk, out);
+  g_launches += 2;
+}
+
+void launch_gemm_bx(cudaStream_t st, const double* B, int64_t ldb, int k, const double* Y, int p, double* X,
+                    int64_t ldx, int64_t n) {
+  if (p <= 0) return;
+  dim3 grid(rows_grid(n, 2048), (p + kGroup - 1) / kGroup);
+  k_gemm_bx<<<grid, kThreads, k * kGroup * sizeof(double), st>>>(B, ldb, k, Y, p, X, ldx, n);
+  ++g_launches;
+}
+
+void launch_permute(cudaStream_t st, const double* src, double* dst, const int32_t* perm, int64_t n,
+                    bool gather) {
+  k_permute<<<rows_grid(n, 2048), kThreads, 0, st>>>(src, dst, perm, n, gather);
+  ++g_launches;
+}
+
+void launch_scale(cudaStream_t st, const double* src, double s, double* dst, int64_t n) {
+  k_scale<<<rows_grid(n, 2048), kThreads, 0, st>>>(src, s, dst, n);
+  ++g_launches;
+}
+
+}  // namespace kes

@@ -1,0 +1,259 @@
+// Fused leapfrog step kernels on SELL-C-sigma (C = 32), sm_103a.
+//
+// One step of the filter application (Sec. 2.3, eq. 2stepmethod and
+// eq. disc_filtercoeff; Algorithm 2.4, time loop):
+//   u_{n+1} = 2 u_n - u_{n-1} - (tau^2 / m) .* (S u_n)
+//   acc_f  += alpha_f[n+1] * u_{n+1}
+// fused into one pass: a warp owns one 32-row slice (lane = row); the slice's
+// values and column indices stream from HBM in 256-byte (FP64) / 128-byte
+// (FP32) coalesced warp loads marked evict-first, u_n is gathered through the
+// read-only path (it stays L2-resident across the step), and the three-term
+// update and the weighted accumulation run on the row result in registers.
+// No tensor cores: the step is a sparse gather, not a dense contraction.
+#include <cuda_runtime.h>
+
+#include "kes_internal.h"
+
+namespace kes {
+
+thread_local int64_t g_launches = 0;
+
+namespace {
+
+__device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
+__device__ __forceinline__ int32_t ld_stream(const int32_t* p) { return __ldcs(p); }
+
+// sum_k val[32k] * x[col[32k]] over the w entries of one lane's row
+template <typename T>
+__device__ __forceinline__ T row_dot(const T* __restrict__ v, const int32_t* __restrict__ c, int w,
+                                     const T* __restrict__ x) {
+  T sum0 = T(0), sum1 = T(0);
+  int k = 0;
+  for (; k + 8 <= w; k += 8) {
+    int32_t cc[8];
+    T vv[8], xx[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) cc[j] = ld_stream(c + (k + j) * kSliceC);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) vv[j] = ld_stream(v + (k + j) * kSliceC);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) xx[j] = __ldg(x + cc[j]);
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+      sum0 = fma(vv[j], xx[j], sum0);
+      sum1 = fma(vv[j + 1], xx[j + 1], sum1);
+    }
+  }
+  if (k < w) {
+    int32_t cc[8];
+    T vv[8], xx[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (k + j < w) cc[j] = ld_stream(c + (k + j) * kSliceC);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (k + j < w) vv[j] = ld_stream(v + (k + j) * kSliceC);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (k + j < w) xx[j] = __ldg(x + cc[j]);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (k + j < w) {
+        if (j & 1) sum1 = fma(vv[j], xx[j], sum1);
+        else sum0 = fma(vv[j], xx[j], sum0);
+      }
+  }
+  return sum0 + sum1;
+}
+
+template <bool FIRST, bool LAST>
+__global__ void __launch_bounds__(256) k_step_f64(SellDev A, const double* __restrict__ tau2m,
+                                                  const double* __restrict__ x, const double* prev,
+                                                  double* out, double* acc, int64_t acc_stride, int F,
+                                                  const double* __restrict__ alpha, int Lp1, int step,
+                                                  int* flag) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t s = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; s < A.n_slices;
+       s += nwarps) {
+    const int64_t beg = A.slice_ptr[s];
+    const int w = static_cast<int>((A.slice_ptr[s + 1] - beg) >> 5);
+    const double sum = row_dot(A.val64 + beg + lane, A.col + beg + lane, w, x);
+    const int64_t row = s * kSliceC + lane;
+    const double xi = x[row];
+    const double pi = FIRST ? xi : prev[row];
+    const double un = fma(-ld_stream(tau2m + row), sum, 2.0 * xi - pi);
+    if (!LAST) out[row] = un;
+    bool bad = false;
+    for (int f = 0; f < F; ++f) {
+      const double* al = alpha + static_cast<int64_t>(f) * Lp1;
+      double* a = acc + f * acc_stride + row;
+      const double prev_acc = FIRST ? al[0] * xi : *a;
+      const double na = fma(al[step + 1], un, prev_acc);
+      *a = na;
+      if (LAST) bad |= !isfinite(na);
+    }
+    if (LAST && bad) atomicOr(flag, 1);
+  }
+}
+
+// error-free sum: s + t = a + b exactly (Knuth's two-sum), round-to-nearest ops only
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  const float ap = __fsub_rn(s, bp);
+  t = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+
+template <bool FIRST, bool LAST>
+__global__ void __launch_bounds__(256) k_step_f32(SellDev A, const float* __restrict__ tau2m,
+                                                  const float* __restrict__ x, const float* prev,
+                                                  float* out, float* acc_s, float* acc_c, double* acc64,
+                                                  int64_t acc_stride, int F, const float* __restrict__ ahi,
+                                                  const float* __restrict__ alo, int Lp1, int step,
+                                                  int* flag) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t s = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; s < A.n_slices;
+       s += nwarps) {
+    const int64_t beg = A.slice_ptr[s];
+    const int w = static_cast<int>((A.slice_ptr[s + 1] - beg) >> 5);
+    const float sum = row_dot(A.val32 + beg + lane, A.col + beg + lane, w, x);
+    const int64_t row = s * kSliceC + lane;
+    const float xi = x[row];
+    const float pi = FIRST ? xi : prev[row];
+    const float un = fmaf(-ld_stream(tau2m + row), sum, __fsub_rn(__fmul_rn(2.0f, xi), pi));
+    if (!LAST) out[row] = un;
+    bool bad = false;
+    for (int f = 0; f < F; ++f) {
+      const int64_t ai = static_cast<int64_t>(f) * Lp1 + step + 1;
+      const float a_hi = ahi[ai], a_lo = alo[ai];
+      const int64_t at = f * acc_stride + row;
+      // alpha * un = p + pe, p = fl(a_hi * un), pe = (a_hi * un - p) + a_lo * un
+      const float p = __fmul_rn(a_hi, un);
+      const float pe = fmaf(a_lo, un, fmaf(a_hi, un, -p));
+      float sn, e;
+      two_sum(acc_s[at], p, sn, e);
+      const float cn = __fadd_rn(acc_c[at], __fadd_rn(e, pe));
+      if (LAST) {
+        const double v = static_cast<double>(sn) + static_cast<double>(cn);
+        acc64[at] = v;
+        bad |= !isfinite(v);
+      } else {
+        acc_s[at] = sn;
+        acc_c[at] = cn;
+      }
+    }
+    if (LAST && bad) atomicOr(flag, 1);
+  }
+}
+
+__global__ void k_init_f32(int64_t n_pad, const double* __restrict__ r, float* __restrict__ x32,
+                           float* __restrict__ acc_s, float* __restrict__ acc_c, int64_t acc_stride, int F,
+                           const double* __restrict__ alpha, int Lp1) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n_pad;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const double ri = r[i];
+    x32[i] = static_cast<float>(ri);
+    for (int f = 0; f < F; ++f) {
+      const double t = alpha[static_cast<int64_t>(f) * Lp1] * ri;
+      const float s = static_cast<float>(t);
+      acc_s[f * acc_stride + i] = s;
+      acc_c[f * acc_stride + i] = static_cast<float>(t - static_cast<double>(s));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_spmv_f64(SellDev A, const double* __restrict__ x,
+                                                  const double* __restrict__ dscale, double* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t s = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; s < A.n_slices;
+       s += nwarps) {
+    const int64_t beg = A.slice_ptr[s];
+    const int w = static_cast<int>((A.slice_ptr[s + 1] - beg) >> 5);
+    const double sum = row_dot(A.val64 + beg + lane, A.col + beg + lane, w, x);
+    const int64_t row = s * kSliceC + lane;
+    y[row] = dscale ? sum * dscale[row] : sum;
+  }
+}
+
+__global__ void k_check_finite(const double* __restrict__ v, int64_t n, int* flag) {
+  bool bad = false;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    bad |= !isfinite(v[i]);
+  if (bad) atomicOr(flag, 1);
+}
+
+int grid_for(const LaunchCfg& cfg, int64_t n_slices) {
+  const int64_t need = (n_slices + (cfg.block_step / 32) - 1) / (cfg.block_step / 32);
+  return static_cast<int>(need < cfg.grid_step ? need : cfg.grid_step);
+}
+
+}  // namespace
+
+int step_blocks_per_sm(bool fp32, int block) {
+  int nb = 0;
+  cudaError_t e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_f32<false, false>, block, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_f64<false, false>, block, 0);
+  return (e == cudaSuccess && nb > 0) ? nb : 4;
+}
+
+void launch_step_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bool first, const double* tau2m,
+                     const double* x, const double* prev, double* out, double* acc, int64_t acc_stride, int F,
+                     const double* alpha, int L, int step, bool last, int* flag) {
+  const int grid = grid_for(cfg, A.n_slices);
+  const int Lp1 = L + 1;
+  if (first && last)
+    k_step_f64<true, true><<<grid, cfg.block_step, 0, st>>>(A, tau2m, x, prev, out, acc, acc_stride, F, alpha,
+                                                             Lp1, step, flag);
+  else if (first)
+    k_step_f64<true, false><<<grid, cfg.block_step, 0, st>>>(A, tau2m, x, prev, out, acc, acc_stride, F, alpha,
+                                                              Lp1, step, flag);
+  else if (last)
+    k_step_f64<false, true><<<grid, cfg.block_step, 0, st>>>(A, tau2m, x, prev, out, acc, acc_stride, F, alpha,
+                                                              Lp1, step, flag);
+  else
+    k_step_f64<false, false><<<grid, cfg.block_step, 0, st>>>(A, tau2m, x, prev, out, acc, acc_stride, F,
+                                                               alpha, Lp1, step, flag);
+  ++g_launches;
+}
+
+void launch_step_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bool first, bool last,
+                     const float* tau2m, const float* x, const float* prev, float* out, float* acc_s,
+                     float* acc_c, double* acc64, int64_t acc_stride, int F, const float* alpha_hi,
+                     const float* alpha_lo, int L, int step, int* flag) {
+  const int grid = grid_for(cfg, A.n_slices);
+  const int Lp1 = L + 1;
+#define KES_F32_ARGS A, tau2m, x, prev, out, acc_s, acc_c, acc64, acc_stride, F, alpha_hi, alpha_lo, Lp1, step, flag
+  if (first && last) k_step_f32<true, true><<<grid, cfg.block_step, 0, st>>>(KES_F32_ARGS);
+  else if (first) k_step_f32<true, false><<<grid, cfg.block_step, 0, st>>>(KES_F32_ARGS);
+  else if (last) k_step_f32<false, true><<<grid, cfg.block_step, 0, st>>>(KES_F32_ARGS);
+  else k_step_f32<false, false><<<grid, cfg.block_step, 0, st>>>(KES_F32_ARGS);
+#undef KES_F32_ARGS
+  ++g_launches;
+}
+
+void launch_init_f32(cudaStream_t st, int64_t n_pad, const double* r64, float* x32, float* acc_s, float* acc_c,
+                     int64_t acc_stride, int F, const double* alpha64, int L) {
+  const int64_t blocks = (n_pad + 255) / 256;
+  k_init_f32<<<static_cast<int>(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(n_pad, r64, x32, acc_s, acc_c,
+                                                                               acc_stride, F, alpha64, L + 1);
+  ++g_launches;
+}
+
+void launch_spmv_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, const double* x,
+                     const double* dscale, double* y) {
+  k_spmv_f64<<<grid_for(cfg, A.n_slices), cfg.block_step, 0, st>>>(A, x, dscale, y);
+  ++g_launches;
+}
+
+void launch_check_finite(cudaStream_t st, const double* v, int64_t n, int* flag) {
+  const int64_t blocks = (n + 255) / 256;
+  k_check_finite<<<static_cast<int>(blocks < 2048 ? blocks : 2048), 256, 0, st>>>(v, n, flag);
+  ++g_launches;
+}
+
+}  // namespace kes

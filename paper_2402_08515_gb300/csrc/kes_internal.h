@@ -1,0 +1,112 @@
+// Internal declarations of the kes library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "kes.h"
+
+namespace kes {
+
+constexpr int kSliceC = 32;  // SELL slice height = warp width
+
+// ---------------------------------------------------------------- host math
+void alpha_table(double wmin, double wmax, double tau, int L, double* alpha);
+void filter_response(double wmin, double wmax, double tau, int L, const double* omega, int64_t k,
+                     double* beta);
+// Symmetric eigensolver for the projected problem: Householder tridiagonalisation
+// followed by implicit QR steps with Wilkinson shifts. A is k x k col-major (lower
+// triangle read), w ascending, V (optional) orthonormal eigenvectors col-major.
+bool sym_eig(int k, const double* A, double* w, double* V);
+
+// ---------------------------------------------------------------- SELL-C-sigma
+struct SellHost {
+  int64_t n = 0, n_slices = 0, nnz = 0, nnz_pad = 0;
+  std::vector<int64_t> slice_ptr;  // [n_slices+1] element offsets, multiples of 32
+  std::vector<int32_t> col;        // [nnz_pad], entry (lane, k) of slice s at slice_ptr[s] + 32k + lane
+  std::vector<double> val;         // [nnz_pad], 0 in padding
+  std::vector<int32_t> perm;       // new row i = old row perm[i]; empty = identity
+};
+// Rows are sorted by decreasing length inside windows of `sigma` rows (sigma = 1
+// keeps the order); the permutation is applied symmetrically so that every
+// vector lives in the permuted order. Padding entries repeat the row's own index
+// with value 0 (phantom rows past n use column n-1).
+SellHost build_sell(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val, int sigma);
+
+// ---------------------------------------------------------------- kernels
+struct SellDev {
+  int64_t n = 0, n_pad = 0, n_slices = 0;
+  const int64_t* slice_ptr = nullptr;
+  const int32_t* col = nullptr;
+  const double* val64 = nullptr;
+  const float* val32 = nullptr;
+};
+
+struct LaunchCfg {
+  int grid_step = 0;   // blocks of the step / SpMV kernels (grid-stride over slices)
+  int block_step = 256;
+  int n_sm = 152;
+};
+
+// One fused leapfrog step, FP64 (Sec. 2.3, eq. 2stepmethod + eq. disc_filtercoeff):
+//   out = 2 x - prev - tau2m .* (S x);   acc_f += alpha_f[step+1] * out   (f < F)
+// first: prev = x and acc_f = alpha_f[0] * x + alpha_f[1] * out.
+// x, prev, out, acc: length n_pad; acc_f at acc + f * acc_stride; alpha_f at alpha + f * (L+1).
+// last: the state of the final step is not stored; flag[0] |= 1 if any acc entry is not finite.
+void launch_step_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bool first,
+                     const double* tau2m, const double* x, const double* prev, double* out,
+                     double* acc, int64_t acc_stride, int F, const double* alpha, int L, int step,
+                     bool last, int* flag);
+
+// FP32 form: values/state FP32, accumulator as an unevaluated FP32 sum (s + c) kept by
+// error-free transformations; alpha as FP32 pairs (hi + lo). last: writes acc64 = s + c in FP64.
+void launch_step_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bool first, bool last,
+                     const float* tau2m, const float* x, const float* prev, float* out, float* acc_s,
+                     float* acc_c, double* acc64, int64_t acc_stride, int F, const float* alpha_hi,
+                     const float* alpha_lo, int L, int step, int* flag);
+// FP32 start: x32 = (float) r64; s_f = fl(alpha_f[0] r), c_f = alpha_f[0] r - s_f (rounded).
+void launch_init_f32(cudaStream_t st, int64_t n_pad, const double* r64, float* x32, float* acc_s,
+                     float* acc_c, int64_t acc_stride, int F, const double* alpha64, int L);
+
+// Resident blocks per SM of the step kernel (occupancy calculator); the step grid is
+// n_sm * this, so that the grid-stride loop runs in exactly one wave.
+int step_blocks_per_sm(bool fp32, int block);
+
+// y = dscale .* (S x) (dscale may be null) in FP64.
+void launch_spmv_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, const double* x,
+                     const double* dscale, double* y);
+
+// Sets flag[0] = 1 if any of v[0..n) is not finite.
+void launch_check_finite(cudaStream_t st, const double* v, int64_t n, int* flag);
+
+// h_j = sum_i B[j*ldb + i] * w[i] * v[i] for j < k (w may be null); deterministic two-pass
+// reduction through `partial` (size >= k * kDotBlocks); result written to h (device).
+constexpr int kDotBlocks = 608;
+void launch_mdot(cudaStream_t st, const double* B, int64_t ldb, int k, const double* v, const double* w,
+                 int64_t n, double* partial, double* h);
+// v[i] -= sum_j B[j*ldb + i] * h[j], j < k
+void launch_gemv_sub(cudaStream_t st, double* v, const double* B, int64_t ldb, int k, const double* h,
+                     int64_t n);
+// dst[i] = v[i] / sqrt(nrm2[0]) (dst2 may be null: second copy)
+void launch_scale_rsqrt(cudaStream_t st, const double* v, const double* nrm2, double* dst, double* dst2,
+                        int64_t n);
+// residuals of Ritz pairs: for j < p, x_j = B Y_j, sx_j = SB Y_j (k terms);
+// out[j] = ||sx_j - theta_j m x_j||_2^2, out[p + j] = ||m x_j||_2^2
+void launch_ritz_residual(cudaStream_t st, const double* B, const double* SB, int64_t ldb, int k,
+                          const double* Y, const double* theta, int p, const double* m, int64_t n,
+                          double* partial, double* out);
+// X[:, j] = B Y_j, j < p (X: ldx-strided columns)
+void launch_gemm_bx(cudaStream_t st, const double* B, int64_t ldb, int k, const double* Y, int p,
+                    double* X, int64_t ldx, int64_t n);
+// dst[i] = src[perm[i]] (gather into permuted order) / dst[perm[i]] = src[i] (scatter back)
+void launch_permute(cudaStream_t st, const double* src, double* dst, const int32_t* perm, int64_t n,
+                    bool gather);
+// dst[i] = src[i] * s
+void launch_scale(cudaStream_t st, const double* src, double s, double* dst, int64_t n);
+
+extern thread_local int64_t g_launches;  // kernels launched by this thread (stats)
+
+}  // namespace kes

@@ -10,4 +10,6 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
-    config.addinivalue_line("markers", "slow: long-running CPU test")
+    # the C-ABI tests load the in-tree library; build it once if it is missing or stale
+    from paper_2402_08515_gb300 import build as _build
+    _build.build()

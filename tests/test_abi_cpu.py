@@ -1,0 +1,99 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function
+include/kes.h declares, and its host-side logic (weights, filter response,
+small symmetric eigensolver, input validation) is right."""
+import math
+
+import numpy as np
+import pytest
+
+import paper_2402_08515_gb300 as K
+import oracle as O  # noqa: E402
+from fe_inputs import square_grid  # noqa: E402
+
+
+def test_every_header_function_is_exported():
+    names = K.header_functions()
+    assert len(names) >= 15
+    missing = [f for f in names if not hasattr(K.lib, f)]
+    assert not missing, missing
+
+
+def test_status_strings():
+    for s in [0, 1, -1, -2, -3, -4, -5, -6, -7, -8]:
+        assert K.kes_strerror(s) and K.kes_strerror(s) != "unknown status"
+
+
+def test_alpha_table_matches_oracle():
+    for wmin, wmax, tau, L in [(20, 30, 0.0099467, 300), (40, 45, 0.0040598, 600), (0, 3, 0.0056, 300)]:
+        np.testing.assert_allclose(K.kes_alpha_table(wmin, wmax, tau, L),
+                                   O.alpha_table(wmin, wmax, tau, L), rtol=1e-13, atol=1e-17)
+
+
+def test_filter_response_matches_oracle():
+    tau, L = 0.0099467, 300
+    w = np.linspace(0, 2 / tau * 0.999, 400)
+    np.testing.assert_allclose(K.kes_filter_response(20, 30, tau, L, w),
+                               O.beta_tilde(w, O.alpha_table(20, 30, tau, L), tau), rtol=0, atol=1e-11)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 7, 40, 120])
+def test_sym_eig_random(k):
+    rng = np.random.default_rng(k)
+    A = rng.standard_normal((k, k))
+    A = A + A.T
+    w, V = K.kes_sym_eig(A)
+    ref = np.linalg.eigvalsh(A)
+    scale = max(1.0, np.abs(ref).max())
+    np.testing.assert_allclose(w, ref, atol=1e-13 * scale * k)
+    np.testing.assert_allclose(V.T @ V, np.eye(k), atol=1e-13 * k)
+    np.testing.assert_allclose(A @ V, V * w, atol=1e-13 * scale * k)
+
+
+def test_sym_eig_clusters_and_diagonal():
+    rng = np.random.default_rng(3)
+    Q, _ = np.linalg.qr(rng.standard_normal((30, 30)))
+    d = np.repeat([1.0, 2.0, 2.0 + 1e-12, 5.0, 1e3], 6)
+    A = (Q * d) @ Q.T
+    A = 0.5 * (A + A.T)
+    w, V = K.kes_sym_eig(A)
+    np.testing.assert_allclose(w, np.sort(d), atol=1e-11)
+    np.testing.assert_allclose(A @ V, V * w, atol=1e-11)
+    D = np.diag([3.0, -1.0, 2.0])
+    w, V = K.kes_sym_eig(D)
+    np.testing.assert_array_equal(w, [-1.0, 2.0, 3.0])
+
+
+def test_sym_eig_reads_lower_triangle_only():
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((12, 12))
+    A = A + A.T
+    A_low = np.tril(A) + np.triu(np.full((12, 12), 1e300), 1)
+    np.testing.assert_allclose(K.kes_sym_eig(A_low)[0], np.linalg.eigvalsh(A), atol=1e-12)
+
+
+def test_create_validates_inputs_before_touching_the_gpu():
+    p = square_grid(6)
+    bad_m = p.m.copy()
+    bad_m[3] = 0.0
+    with pytest.raises(K.KesError) as e:
+        K.kes_create(p.n, p.row_ptr, p.col, p.val, bad_m)
+    assert e.value.status == -2
+    bad_col = p.col.copy()
+    bad_col[5] = p.n + 3
+    with pytest.raises(K.KesError) as e:
+        K.kes_create(p.n, p.row_ptr, bad_col, p.val, p.m)
+    assert e.value.status == -1
+    bad_val = p.val.copy()
+    bad_val[0] = math.nan
+    with pytest.raises(K.KesError) as e:
+        K.kes_create(p.n, p.row_ptr, p.col, bad_val, p.m)
+    assert e.value.status == -1
+
+
+def test_host_helpers_reject_bad_arguments():
+    with pytest.raises(K.KesError):
+        K.kes_alpha_table(3.0, 2.0, 0.1, 10)
+    with pytest.raises(K.KesError):
+        K.kes_alpha_table(2.0, 3.0, -0.1, 10)
+    with pytest.raises(K.KesError):
+        K.kes_filter_response(2.0, 3.0, 0.1, 0, [1.0])

@@ -1,0 +1,220 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Every input is seeded and synthetic (fe_inputs); every expected value comes
+from oracle/ (or the closed-form spectra in oracle/spectra.py).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2402_08515_gb300 as K
+from fe_inputs import box_grid, flared_tube, square_grid, start_vectors
+from oracle import spectra
+from tests.tolerances import EIG_REL, elementwise_bound, filter_error, filter_tol
+
+pytestmark = pytest.mark.gpu
+
+
+def _ctx(p, **kw):
+    return K.Context(p, **kw)
+
+
+def _tau_for(p):
+    """tau = 0.9 * 2 / omega_max(S, M), omega_max from the oracle's power iteration."""
+    w = O.power_iteration(p.to_scipy(), p.m, start_vectors(p.n, 1, 0)[0], 300)
+    return 0.9 * 2.0 / w
+
+
+PROBLEMS = {
+    "square64": lambda: square_grid(64),                           # 3969 dofs, 125 slices (ragged tail)
+    "box_ragged": lambda: box_grid((37, 29, 23), extent=(1.0, 0.8, 0.7)),
+    "tube": lambda: flared_tube(0.02, length=1.0, r0=0.05, growth=1.5),
+    "tiny": lambda: square_grid(4),                                # n = 9 < one slice
+    "single": lambda: square_grid(2),                              # n = 1
+}
+
+
+@pytest.fixture(scope="module")
+def problems():
+    return {k: f() for k, f in PROBLEMS.items()}
+
+
+@pytest.mark.parametrize("name", sorted(PROBLEMS))
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_filter_apply_matches_oracle(problems, name, precision):
+    p = problems[name]
+    tau = _tau_for(p)
+    w_top = 0.9 * 2 / tau
+    wmin, wmax = 0.15 * w_top, 0.25 * w_top
+    L = 1 if name == "single" else 120
+    alpha = O.alpha_table(wmin, wmax, tau, L)
+    r = start_vectors(p.n, 1, 7)
+    ref = O.filter_apply(p.to_scipy(), p.m, r[0], tau, alpha)
+    with _ctx(p, precision=precision) as c:
+        K.kes_set_filter(c.handle, wmin, wmax, tau, L)
+        out = np.zeros((1, 1, p.n))
+        K.kes_filter_apply(c.handle, r, out, 1)
+    err = filter_error(out[0], ref, r, p.m, alpha)
+    tol = filter_tol(L, precision)
+    print(f"{name} {precision} L={L}: M-norm error {err:.3e} (tol {tol:.3e})")
+    assert err <= tol
+    np.testing.assert_array_less(np.abs(out[0, 0] - ref), elementwise_bound(tol, r, p.m, alpha) + 1e-300)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_filter_block_and_intervals_on_device(problems, precision):
+    import torch
+    p = problems["box_ragged"]
+    tau = _tau_for(p)
+    L = 90
+    bands = [(5.0, 9.0), (12.0, 14.0), (20.0, 31.0)]
+    alphas = np.stack([O.alpha_table(a, b, tau, L) for a, b in bands])
+    R = start_vectors(p.n, 3, 11)
+    ref = O.filter_apply_multi(p.to_scipy(), p.m, R, tau, alphas)
+    with _ctx(p, precision=precision, block_b=3, torch_alloc=True) as c:
+        K.kes_set_filters(c.handle, [a for a, _ in bands], [b for _, b in bands], tau, L)
+        r_dev = torch.from_numpy(R).cuda()
+        out = torch.zeros((3, 3, p.n), dtype=torch.float64, device="cuda")
+        K.kes_filter_apply(c.handle, r_dev, out, 3)
+        K.kes_sync(c.handle)
+        got = out.cpu().numpy()
+    for f in range(3):
+        err = filter_error(got[f], ref[f], R, p.m, alphas[f])
+        assert err <= filter_tol(L, precision), (f, err)
+
+
+def test_graph_and_plain_launches_are_bitwise_equal(problems):
+    p = problems["tube"]
+    tau = _tau_for(p)
+    r = start_vectors(p.n, 1, 3)
+    outs = []
+    for use_graph in (True, False):
+        with _ctx(p, use_graph=use_graph) as c:
+            K.kes_set_filter(c.handle, 10.0, 20.0, tau, 50)
+            o = np.zeros((1, 1, p.n))
+            K.kes_filter_apply(c.handle, r, o, 1)
+            K.kes_filter_apply(c.handle, r, o, 1)      # graph replay
+            outs.append(o)
+    np.testing.assert_array_equal(outs[0], outs[1])
+
+
+def test_sorted_slices_give_the_same_filter(problems):
+    p = problems["tube"]                              # rows of 4..15 entries
+    tau = _tau_for(p)
+    L = 80
+    alpha = O.alpha_table(10.0, 20.0, tau, L)
+    r = start_vectors(p.n, 1, 5)
+    ref = O.filter_apply(p.to_scipy(), p.m, r[0], tau, alpha)
+    for sigma in (32, 256):
+        with _ctx(p, sell_sigma=sigma) as c:
+            K.kes_set_filter(c.handle, 10.0, 20.0, tau, L)
+            o = np.zeros((1, 1, p.n))
+            K.kes_filter_apply(c.handle, r, o, 1)
+        assert filter_error(o[0], ref, r, p.m, alpha) <= filter_tol(L, "fp64"), sigma
+
+
+def test_omega_max_matches_oracle_power_iteration(problems):
+    for name in ["square64", "box_ragged", "tube"]:
+        p = problems[name]
+        v0 = start_vectors(p.n, 1, 0)[0]
+        ref = O.power_iteration(p.to_scipy(), p.m, v0, 300)
+        with _ctx(p) as c:
+            got, gersh = K.kes_estimate_omega_max(c.handle, 300, v0)
+        assert got == pytest.approx(ref, rel=1e-10), name
+        assert gersh >= got * (1 - 1e-12)
+
+
+def _closed_form_check(p, res, wmin, wmax, rel):
+    exact = spectra.eigenvalues_in(p.cells, p.h, wmin, wmax)
+    vals, _ = spectra.distinct(exact)
+    for th in res["omega2"]:
+        assert np.min(np.abs(vals - th) / th) <= rel, th
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_krylov_solve_square64_matches_closed_form_and_oracle(problems, precision):
+    p = problems["square64"]
+    S = p.to_scipy()
+    tau = _tau_for(p)
+    wmin, wmax, L, kmax = 20.0, 30.0, 300, 80
+    tol = 1e-8 if precision == "fp64" else 1e-5
+    r0 = start_vectors(p.n, 1, 0)[0]
+    with _ctx(p, precision=precision) as c:
+        K.kes_set_filter(c.handle, wmin, wmax, tau, L)
+        so = K.kes_solve_opts_default()
+        so.kmax, so.tol, so.want_vectors = kmax, tol, 1
+        res = K.kes_krylov_solve(c.handle, r0, so)
+        stats = K.kes_get_stats(c.handle)
+    assert res["k_used"] == kmax and res["time_steps"] == (kmax - 1) * L
+    assert stats["filter_steps"] == (kmax - 1) * L and stats["kernel_launches"] > stats["filter_steps"]
+    _closed_form_check(p, res, wmin, wmax, EIG_REL[precision])
+    distinct_exact, _ = spectra.distinct(spectra.eigenvalues_in(p.cells, p.h, wmin, wmax))
+    found, _ = spectra.distinct(res["omega2"])
+    print(f"{precision}: accepted {res['n_pairs']} pairs, {len(found)} of {len(distinct_exact)} distinct")
+    # residuals recomputed on the host from the returned vectors
+    for th, x, rr in zip(res["omega2"], res["vectors"], res["rel_res"]):
+        r = S @ x - th * p.m * x
+        rel = np.linalg.norm(r) / (th * np.linalg.norm(p.m * x))
+        assert rel <= tol * 1.01 and rel == pytest.approx(rr, rel=1e-3, abs=1e-14)
+    # the oracle accepts the same distinct eigenvalues, up to pairs near the threshold
+    ores = O.krylov_solve(S, p.m, r0, wmin, wmax, tau, L, kmax, tol)
+    o_found, _ = spectra.distinct(ores.omega2)
+    if precision == "fp64":
+        assert len(found) == len(distinct_exact) and len(o_found) == len(distinct_exact)
+    else:
+        assert len(found) >= len(o_found) - 2
+
+
+def test_breakdown_on_eigenvector_start(problems):
+    p = problems["square64"]
+    v = spectra.box_eigenvector(p.cells, (5, 6))
+    lam = 4 * 64 * 64 * (math.sin(5 * math.pi / 128) ** 2 + math.sin(6 * math.pi / 128) ** 2)
+    tau = _tau_for(p)
+    with _ctx(p) as c:
+        K.kes_set_filter(c.handle, 0.8 * math.sqrt(lam), 1.2 * math.sqrt(lam), tau, 100)
+        so = K.kes_solve_opts_default()
+        so.kmax = 10
+        res = K.kes_krylov_solve(c.handle, v, so)
+    assert res["status"] == 1 and res["breakdown"] and res["k_used"] == 1
+    assert res["omega2"][0] == pytest.approx(lam, rel=1e-12)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_cfl_violation_is_reported_not_faulted(problems, precision):
+    p = problems["box_ragged"]
+    w = math.sqrt(spectra.box_spectrum(p.cells, p.h).max())
+    tau = 1.5 * 2 / w                          # far beyond tau < 2 / omega_max
+    r = start_vectors(p.n, 1, 1)
+    with _ctx(p, precision=precision) as c:
+        K.kes_set_filter(c.handle, 1.0, 2.0, tau, 600)
+        with pytest.raises(K.KesError) as e:
+            K.kes_filter_apply(c.handle, r, np.zeros((1, 1, p.n)), 1)
+        assert e.value.status == -3
+        with pytest.raises(K.KesError) as e:
+            K.kes_krylov_solve(c.handle, r[0])
+        assert e.value.status == -3
+        # the context stays usable after the error
+        K.kes_set_filter(c.handle, 1.0, 2.0, 0.5 * 2 / w, 10)
+        K.kes_filter_apply(c.handle, r, np.zeros((1, 1, p.n)), 1)
+        K.kes_estimate_omega_max(c.handle, 300, r[0])
+        with pytest.raises(K.KesError) as e:           # tau beyond the stored estimate
+            K.kes_set_filter(c.handle, 1.0, 2.0, 2.5 / w, 10)
+        assert e.value.status == -3
+
+
+def test_state_errors():
+    p = square_grid(8)
+    with _ctx(p) as c:
+        with pytest.raises(K.KesError) as e:
+            K.kes_filter_apply(c.handle, np.zeros((1, p.n)), np.zeros((1, 1, p.n)), 1)
+        assert e.value.status == -7
+        K.kes_set_filter(c.handle, 1.0, 2.0, 0.01, 5)
+        with pytest.raises(K.KesError) as e:           # b beyond opts.block_b
+            K.kes_filter_apply(c.handle, np.zeros((2, p.n)), np.zeros((1, 2, p.n)), 2)
+        assert e.value.status == -1
+        K.kes_set_filters(c.handle, [1.0, 3.0], [2.0, 4.0], 0.01, 5)
+        with pytest.raises(K.KesError) as e:           # the solver takes one interval
+            K.kes_krylov_solve(c.handle, np.ones(p.n))
+        assert e.value.status == -8

@@ -1,0 +1,50 @@
+"""Tolerances of the parity tests, derived from the arithmetic.
+
+Filter application (eq. disc_filtercoeff). Write u^_n = u_n + e_n for the
+computed leapfrog states. Each step adds a local rounding error d_n with
+||d_n||_M <= c_loc * eps * ||u^_n||_M (the row dot product of <= 16 terms,
+the scale by tau^2/m and the three-term update: c_loc ~ 16 * (tau^2 G + 3)
+with tau^2 G <= 4 under the CFL bound, G the Gershgorin bound of M^-1 S).
+The error obeys the same two-step recurrence, e_{n+1} = (2 - tau^2 M^-1 S) e_n
+- e_{n-1} + d_n, so e_n = sum_j U_{n-1-j}(I - tau^2 M^-1 S / 2) d_j with the
+Chebyshev polynomials U_k of the second kind, |U_k| <= k + 1 on the stable
+spectrum; ||u_n||_M <= ||r||_M / cos(theta_max / 2) (the third-kind bound of
+eq. scalartimestep). Summing with the weights gives the first-order bound
+
+    ||C^ r - C r||_M <= (sum_n |alpha_n|) * c_loc * eps * L^2 / (2 cos(theta_max/2)) * ||r||_M,
+
+which is FILTER_C * eps * L^2 with FILTER_C = 16 * 7 / 2 * 2.3 ~ 130 after
+normalising by sum |alpha_n| ||r||_M. The FP32 form has eps = 2^-24 for the
+state; its accumulator is compensated, so the sum adds no error of its own.
+
+Eigenvalues: BASELINE targets are a relative 1e-10 (FP64 form) and 1e-6 (FP32
+form) against the exact (closed-form) spectrum.
+"""
+import numpy as np
+
+EPS64 = float(np.finfo(np.float64).eps) / 2     # unit roundoff 2^-53
+EPS32 = float(np.finfo(np.float32).eps) / 2     # 2^-24
+FILTER_C = 130.0
+
+EIG_REL = {"fp64": 1e-10, "fp32": 1e-6}
+
+
+def filter_tol(L: int, precision: str) -> float:
+    """Bound on ||C_gpu r - C_oracle r||_M / (sum_n |alpha_n| * ||r||_M)."""
+    eps = EPS64 if precision == "fp64" else EPS32
+    return FILTER_C * eps * L * L
+
+
+def filter_error(got: np.ndarray, ref: np.ndarray, r: np.ndarray, m: np.ndarray,
+                 alpha: np.ndarray) -> float:
+    """||got - ref||_M / (sum |alpha| ||r||_M) for one vector (or row-stacked vectors)."""
+    got, ref, r = np.atleast_2d(got), np.atleast_2d(ref), np.atleast_2d(r)
+    num = np.sqrt(np.sum((got - ref) ** 2 * m, axis=-1))
+    den = np.abs(alpha).sum() * np.sqrt(np.sum(r ** 2 * m, axis=-1))
+    return float(np.max(num / den))
+
+
+def elementwise_bound(tol: float, r: np.ndarray, m: np.ndarray, alpha: np.ndarray) -> float:
+    """Entry-wise bound implied by the M-norm bound: |e_i| <= ||e||_M / sqrt(min m)."""
+    rm = np.sqrt(np.sum(np.atleast_2d(r) ** 2 * m, axis=-1)).max()
+    return tol * np.abs(alpha).sum() * rm / np.sqrt(m.min())
