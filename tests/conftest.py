@@ -11,5 +11,5 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     # the C-ABI tests load the in-tree library; build it once if it is missing or stale
-    from paper_2402_08515_gb300 import build as _build
-    _build.build()
+    import __graft_entry__
+    __graft_entry__.build()
