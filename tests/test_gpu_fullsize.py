@@ -105,9 +105,18 @@ def test_krylov_solve_full_size_matches_exact_spectrum(cube, precision):
         so.kmax, so.tol = WL.kmax, tol
         res = K.kes_krylov_solve(c.handle, v0, so)
     exact, _ = spectra.distinct(spectra.eigenvalues_in(p.cells, p.h, WL.omega_min, WL.omega_max))
+    everything = spectra.box_spectrum(p.cells, p.h)
     print(f"{precision}: {res['n_pairs']} accepted of {exact.size} distinct, k={res['k_used']}, "
           f"{res['solve_ms']:.0f} ms")
-    assert res["n_pairs"] >= 1
+    assert res["k_used"] == WL.kmax and res["time_steps"] == (WL.kmax - 1) * WL.L
     assert np.all(res["rel_res"] <= tol)
     for th in res["omega2"]:
         assert np.min(np.abs(exact - th) / th) <= EIG_REL[precision]
+    # Every Ritz pair in the interval, converged or not, obeys the residual bound of a
+    # symmetric definite pencil: some eigenvalue lies within ||(S - theta M) x||_{M^-1}
+    # of theta (||x||_M = 1); with M = h^3 I that radius is rel_res * theta.
+    inside = ~np.isnan(res["ritz_rel_res"])
+    assert inside.any()
+    for th, rel in zip(res["ritz_omega2"][inside], res["ritz_rel_res"][inside]):
+        gap = np.min(np.abs(everything - th))
+        assert gap <= rel * th * (1 + 1e-6) + 1e-12 * th, (th, rel, gap)

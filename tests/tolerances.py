@@ -13,9 +13,25 @@ eq. scalartimestep). Summing with the weights gives the first-order bound
 
     ||C^ r - C r||_M <= (sum_n |alpha_n|) * c_loc * eps * L^2 / (2 cos(theta_max/2)) * ||r||_M,
 
-which is FILTER_C * eps * L^2 with FILTER_C = 16 * 7 / 2 * 2.3 ~ 130 after
-normalising by sum |alpha_n| ||r||_M. The FP32 form has eps = 2^-24 for the
-state; its accumulator is compensated, so the sum adds no error of its own.
+i.e. about 130 * eps * L^2 after normalising by sum |alpha_n| ||r||_M. That
+worst case assumes every rounding error has the same sign and the largest
+size. The tests use the probabilistic form of the same analysis (Higham &
+Mary, SIAM J. Sci. Comput. 2019: independent, zero-mean rounding errors
+accumulate like a random walk, with the same bound up to a small constant
+holding with overwhelming probability):
+  * a row's local error is the sum of ~w + 3 independent roundings (w <= 16
+    products and sums of the row, the scale and the three-term update) of
+    terms whose sizes add up to at most (tau^2 G + 3) |u| <= 7 |u|; spread over
+    ~18 roundings that is a standard deviation of ~7/sqrt(18) ~ 1.7 eps |u|,
+    and c_loc = 4 also covers the partial sums carried through the row;
+  * the weighted sum sum_n alpha_n e_n = sum_j G_j d_j, where
+    G_j = sum_{n>j} alpha_n U_{n-1-j} is bounded by sum |alpha_n| / sin(theta)
+    and sin(theta) >= tau omega_min / 2 keeps it within a factor ~ 2 on the
+    meshes used here; L independent terms then add to
+    ~ 2 c_loc eps sqrt(L) sum |alpha_n| ||r||_M.
+FILTER_TOL_C = 32 = 2 * c_loc * (safety factor 4). The FP32 form has
+eps = 2^-24 for values and state; its accumulator is compensated (two-sum and
+two-product), so the sum adds no error of its own.
 
 Eigenvalues: BASELINE targets are a relative 1e-10 (FP64 form) and 1e-6 (FP32
 form) against the exact (closed-form) spectrum.
@@ -24,15 +40,22 @@ import numpy as np
 
 EPS64 = float(np.finfo(np.float64).eps) / 2     # unit roundoff 2^-53
 EPS32 = float(np.finfo(np.float32).eps) / 2     # 2^-24
-FILTER_C = 130.0
+FILTER_WORST_C = 130.0
+FILTER_TOL_C = 32.0
 
 EIG_REL = {"fp64": 1e-10, "fp32": 1e-6}
 
 
 def filter_tol(L: int, precision: str) -> float:
-    """Bound on ||C_gpu r - C_oracle r||_M / (sum_n |alpha_n| * ||r||_M)."""
+    """Tolerance on ||C_gpu r - C_oracle r||_M / (sum_n |alpha_n| * ||r||_M)."""
     eps = EPS64 if precision == "fp64" else EPS32
-    return FILTER_C * eps * L * L
+    return FILTER_TOL_C * eps * (L + 1) ** 0.5
+
+
+def filter_worst_bound(L: int, precision: str) -> float:
+    """First-order worst-case bound (every rounding error aligned)."""
+    eps = EPS64 if precision == "fp64" else EPS32
+    return FILTER_WORST_C * eps * L * L
 
 
 def filter_error(got: np.ndarray, ref: np.ndarray, r: np.ndarray, m: np.ndarray,
