@@ -3,7 +3,7 @@
 
 One step = one full eigensolve on the workload (every part of the hot path):
 weights (eq. weightf), kmax-1 filter applications of L fused leapfrog steps
-(eq. 2stepmethod, eq. disc_filtercoeff), M-orthonormalisation (Algorithm 2.4),
+(eq. 2stepmethod, eq. disc_filtercoeff), M-orthonormalisation (Algorithm 2.5),
 Rayleigh-Ritz (eq. projevp) and residual acceptance (eq. res). The default
 workload is the 128^3 Kuhn cube (2,048,383 dofs, 30,340,171 entries), interval
 [40, 45], L = 600, Krylov dimension 60, FP64.

@@ -5,7 +5,7 @@
  * Domain Solutions" (arXiv:2402.08515), Sec. 2. The library finds eigenpairs
  * (omega^2, v) of S v = omega^2 M v (eq. def:basisMatrixEVP) with omega in a
  * chosen interval [omega_min, omega_max], for a sparse symmetric positive
- * semi-definite S and a lumped (diagonal, positive) M (Remark rmk:mass_lumping).
+ * semi-definite S and a lumped (diagonal, positive) M (Remark 2.1).
  *
  * Conventions shared by every entry point:
  *   - Every function returns a kes_status (0 = success); no C++ exception and
@@ -37,7 +37,7 @@ typedef struct kes_ctx kes_ctx;
 
 typedef enum kes_status {
   KES_OK = 0,
-  KES_INFO_INVARIANT_SUBSPACE = 1, /* Krylov breakdown: an invariant subspace was found (Algorithm 2.4, "exact eigenspace found") */
+  KES_INFO_INVARIANT_SUBSPACE = 1, /* Krylov breakdown: an invariant subspace was found (Algorithm 2.5, "exact eigenspace found") */
   KES_ERR_ARG = -1,                /* invalid argument (null pointer, size, range, ordering) */
   KES_ERR_MASS = -2,               /* a lumped mass entry is <= 0 or not finite */
   KES_ERR_UNSTABLE = -3,           /* CFL violated (tau * omega_max >= 2) or the time stepping produced Inf/NaN */
@@ -62,6 +62,9 @@ typedef struct kes_opts {
   int32_t sell_sigma;  /* SELL-C-sigma sorting window in rows (slices are C = 32 rows); 1 keeps the row order */
   int32_t use_graph;   /* 1: the L time steps of a filter application replay as one CUDA graph; 0: plain launches */
   int32_t block_b;     /* largest number of start vectors filtered together (columns of kes_filter_apply) */
+  int32_t autotune;    /* 1: kes_create times every launch shape of the step kernel on this matrix and keeps the
+                          fastest (results do not depend on the choice); 0: the first shape */
+  int32_t reserved;    /* set to 0 */
   void* stream;        /* cudaStream_t for every launch; NULL: the context creates its own non-blocking stream */
   /* Optional device allocator (e.g. a framework's caching allocator). Both NULL: cudaMalloc / cudaFree. */
   void* (*dev_alloc)(size_t bytes, void* user);
@@ -104,6 +107,8 @@ typedef struct kes_stats {
   double filter_ms;         /* device time of the filter applications (CUDA events on the context stream) */
   double solve_other_ms;    /* device time of orthogonalisation, projection and residuals */
   int64_t bytes_per_step;   /* algorithmic HBM bytes of one fused step (see kes_step_bytes) */
+  int32_t step_variant;     /* launch shape of the step kernel in use */
+  int32_t step_grid;        /* its grid size (blocks of 256 threads) */
 } kes_stats;
 
 void kes_opts_default(kes_opts* opts);
@@ -112,7 +117,7 @@ const char* kes_strerror(int32_t status);
 
 /*
  * kes_create -- upload S (CSR) and the lumped mass diagonal m (Sec. 2,
- * eq. def:basisMatrixEVP with Remark rmk:mass_lumping) and build the device
+ * eq. def:basisMatrixEVP with Remark 2.1) and build the device
  * format (SELL-C-sigma, C = 32).
  *   n        number of dofs (rows), 1 <= n < 2^31
  *   row_ptr  host int64[n+1], row_ptr[0] = 0, non-decreasing
@@ -184,7 +189,7 @@ int64_t kes_step_bytes(const kes_ctx* ctx, int32_t b, int32_t F);
 kes_status kes_filter_apply(kes_ctx* ctx, const double* r_in, double* r_out, int32_t b, int32_t mem);
 
 /*
- * kes_krylov_solve -- Krylov space of C from r0 (Algorithm 2.4, with the
+ * kes_krylov_solve -- Krylov space of C from r0 (Algorithm 2.5, with the
  * M-inner product and two classical Gram-Schmidt passes), Rayleigh-Ritz on it
  * (eq. projevp) and residual acceptance (eq. res).
  *   r0     start vector, length n (host or device per `mem`); it is M-normalised first

@@ -18,11 +18,11 @@ Readings used throughout (see the function docstrings):
     (eq. disc_filtercoeff sums l = 0..L-1 with L-1 steps; the closed interval
     (0, T] of eq. weightf is covered by taking L steps and L+1 terms);
   * inner product: the M-inner product (x, y)_M = x^T M y with two full
-    classical Gram-Schmidt passes (Algorithm 2.4 uses the Euclidean product
+    classical Gram-Schmidt passes (Algorithm 2.5 uses the Euclidean product
     and one modified pass); the projected problem eq. projevp then becomes a
     standard symmetric eigenproblem because B^T M B = I;
   * breakdown: stop when the M-norm after orthogonalisation is below 1e-10
-    times the M-norm before it (Algorithm 2.4 tests for an exact zero);
+    times the M-norm before it (Algorithm 2.5 tests for an exact zero);
   * Krylov dimension kmax = number of basis vectors b_0..b_{kmax-1}, which
     takes kmax-1 filter applications;
   * residual: rel_res = ||S x - theta M x||_2 / (theta ||M x||_2) with
@@ -111,7 +111,7 @@ def filter_apply(S, m: np.ndarray, r: np.ndarray, tau: float,
     """C r = sum_{n=0..L} alpha_n y_n(r) (eq. disc_filtercoeff).
 
     y_{-1} = y_0 = r and y_{l+1} = -tau^2 M^{-1} S y_l + 2 y_l - y_{l-1}
-    (eq. 2stepmethod), M = diag(m); the inner loop of Algorithm 2.4."""
+    (eq. 2stepmethod), M = diag(m); the inner loop of Algorithm 2.5."""
     L = len(alpha) - 1
     y_prev = np.array(r, dtype=np.float64)
     y = np.array(r, dtype=np.float64)
@@ -167,7 +167,7 @@ def power_iteration(S, m: np.ndarray, v0: np.ndarray, iters: int) -> float:
 
 
 # --------------------------------------------------------------------------
-# Gram-Schmidt in the M-inner product (Algorithm 2.4, orthogonalisation loop)
+# Gram-Schmidt in the M-inner product (Algorithm 2.5, orthogonalisation loop)
 # --------------------------------------------------------------------------
 
 def m_inner(x: np.ndarray, y: np.ndarray, m: np.ndarray) -> float:
@@ -229,7 +229,7 @@ def ritz_residuals(S, m: np.ndarray, B: np.ndarray, theta: np.ndarray,
 
 
 # --------------------------------------------------------------------------
-# the Krylov eigensolver (Algorithm 2.4 + eq. projevp + eq. res)
+# the Krylov eigensolver (Algorithm 2.5 + eq. projevp + eq. res)
 # --------------------------------------------------------------------------
 
 @dataclass
@@ -251,7 +251,7 @@ class KrylovResult:
 def krylov_solve(S, m: np.ndarray, r0: np.ndarray, omega_min: float,
                  omega_max: float, tau: float, L: int, kmax: int, tol: float,
                  check_every: int = 5, keep_basis: bool = True) -> KrylovResult:
-    """Krylov space of C from r0 (Algorithm 2.4), projected problem
+    """Krylov space of C from r0 (Algorithm 2.5), projected problem
     (eq. projevp) and residual acceptance (eq. res).
 
     b_0 = r0/||r0||_M; for k = 0.. : w = C b_k, CGS2 in the M-inner product,

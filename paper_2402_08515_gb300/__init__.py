@@ -31,7 +31,7 @@ LIB_PATH = os.path.join(HERE, "libkes.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "kes.h")
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2402_08515_gb300.build` "
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_2402_08515_gb300/build.py` "
                       "(no CPU fallback exists)")
 lib = C.CDLL(LIB_PATH)
 
@@ -52,7 +52,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
 
 class KesOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("sell_sigma", C.c_int32), ("use_graph", C.c_int32),
-                ("block_b", C.c_int32), ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN),
+                ("block_b", C.c_int32), ("autotune", C.c_int32), ("reserved", C.c_int32), ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN),
                 ("dev_free", FREE_FN), ("alloc_user", C.c_void_p)]
 
 
@@ -72,7 +72,8 @@ class KesResult(C.Structure):
 
 class KesStats(C.Structure):
     _fields_ = [("filter_calls", C.c_int64), ("filter_steps", C.c_int64), ("kernel_launches", C.c_int64),
-                ("filter_ms", C.c_double), ("solve_other_ms", C.c_double), ("bytes_per_step", C.c_int64)]
+                ("filter_ms", C.c_double), ("solve_other_ms", C.c_double), ("bytes_per_step", C.c_int64),
+                ("step_variant", C.c_int32), ("step_grid", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -274,8 +275,9 @@ class Context:
     ``torch_alloc`` is set, launches on ``stream`` (a torch.cuda.Stream or None)."""
 
     def __init__(self, problem, precision: str = "fp64", sell_sigma: int = 1, use_graph: bool = True,
-                 block_b: int = 1, stream=None, torch_alloc: bool = False):
+                 block_b: int = 1, stream=None, torch_alloc: bool = False, autotune: bool = True):
         o = kes_opts_default()
+        o.autotune = 1 if autotune else 0
         o.precision = KES_PREC_FP32 if precision == "fp32" else KES_PREC_FP64
         o.sell_sigma = sell_sigma
         o.use_graph = 1 if use_graph else 0

@@ -3,7 +3,7 @@
 Each translation unit is compiled by its own nvcc process (in parallel) and
 linked into ``paper_2402_08515_gb300/libkes.so`` with the CUDA runtime linked
 statically, so the library loads on a machine without a GPU (its CUDA calls
-then fail with KES_ERR_CUDA). Run ``python -m paper_2402_08515_gb300.build``.
+then fail with KES_ERR_CUDA). Run ``python paper_2402_08515_gb300/build.py`` (the package itself needs the library).
 """
 from __future__ import annotations
 

@@ -1,4 +1,4 @@
-// FP64 vector kernels of the Krylov loop (Algorithm 2.4, orthogonalisation),
+// FP64 vector kernels of the Krylov loop (Algorithm 2.5, orthogonalisation),
 // the projection (eq. projevp) and the residuals (eq. res).
 //
 // All reductions are deterministic: every block writes one partial per

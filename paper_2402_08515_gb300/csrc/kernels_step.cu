@@ -1,7 +1,7 @@
 // Fused leapfrog step kernels on SELL-C-sigma (C = 32), sm_103a.
 //
 // One step of the filter application (Sec. 2.3, eq. 2stepmethod and
-// eq. disc_filtercoeff; Algorithm 2.4, time loop):
+// eq. disc_filtercoeff; Algorithm 2.5, time loop):
 //   u_{n+1} = 2 u_n - u_{n-1} - (tau^2 / m) .* (S u_n)
 //   acc_f  += alpha_f[n+1] * u_{n+1}
 // fused into one pass: a warp owns one 32-row slice (lane = row); the slice's
@@ -24,41 +24,44 @@ __device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p);
 __device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
 __device__ __forceinline__ int32_t ld_stream(const int32_t* p) { return __ldcs(p); }
 
-// sum_k val[32k] * x[col[32k]] over the w entries of one lane's row
-template <typename T>
+// sum_k val[32k] * x[col[32k]] over the w entries of one lane's row. Loads are issued
+// BATCH entries at a time (memory-level parallelism); even entries go to sum0 and odd
+// ones to sum1 whatever BATCH is, so every variant rounds identically.
+template <typename T, int BATCH>
 __device__ __forceinline__ T row_dot(const T* __restrict__ v, const int32_t* __restrict__ c, int w,
                                      const T* __restrict__ x) {
+  static_assert(BATCH % 2 == 0, "BATCH must be even");
   T sum0 = T(0), sum1 = T(0);
   int k = 0;
-  for (; k + 8 <= w; k += 8) {
-    int32_t cc[8];
-    T vv[8], xx[8];
+  for (; k + BATCH <= w; k += BATCH) {
+    int32_t cc[BATCH];
+    T vv[BATCH], xx[BATCH];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) cc[j] = ld_stream(c + (k + j) * kSliceC);
+    for (int j = 0; j < BATCH; ++j) cc[j] = ld_stream(c + (k + j) * kSliceC);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) vv[j] = ld_stream(v + (k + j) * kSliceC);
+    for (int j = 0; j < BATCH; ++j) vv[j] = ld_stream(v + (k + j) * kSliceC);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) xx[j] = __ldg(x + cc[j]);
+    for (int j = 0; j < BATCH; ++j) xx[j] = __ldg(x + cc[j]);
 #pragma unroll
-    for (int j = 0; j < 8; j += 2) {
+    for (int j = 0; j < BATCH; j += 2) {
       sum0 = fma(vv[j], xx[j], sum0);
       sum1 = fma(vv[j + 1], xx[j + 1], sum1);
     }
   }
   if (k < w) {
-    int32_t cc[8];
-    T vv[8], xx[8];
+    int32_t cc[BATCH];
+    T vv[BATCH], xx[BATCH];
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
+    for (int j = 0; j < BATCH; ++j)
       if (k + j < w) cc[j] = ld_stream(c + (k + j) * kSliceC);
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
+    for (int j = 0; j < BATCH; ++j)
       if (k + j < w) vv[j] = ld_stream(v + (k + j) * kSliceC);
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
+    for (int j = 0; j < BATCH; ++j)
       if (k + j < w) xx[j] = __ldg(x + cc[j]);
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
+    for (int j = 0; j < BATCH; ++j)
       if (k + j < w) {
         if (j & 1) sum1 = fma(vv[j], xx[j], sum1);
         else sum0 = fma(vv[j], xx[j], sum0);
@@ -67,8 +70,8 @@ __device__ __forceinline__ T row_dot(const T* __restrict__ v, const int32_t* __r
   return sum0 + sum1;
 }
 
-template <bool FIRST, bool LAST>
-__global__ void __launch_bounds__(256) k_step_f64(SellDev A, const double* __restrict__ tau2m,
+template <bool FIRST, bool LAST, int BATCH, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_step_f64(SellDev A, const double* __restrict__ tau2m,
                                                   const double* __restrict__ x, const double* prev,
                                                   double* out, double* acc, int64_t acc_stride, int F,
                                                   const double* __restrict__ alpha, int Lp1, int step,
@@ -79,7 +82,7 @@ __global__ void __launch_bounds__(256) k_step_f64(SellDev A, const double* __res
        s += nwarps) {
     const int64_t beg = A.slice_ptr[s];
     const int w = static_cast<int>((A.slice_ptr[s + 1] - beg) >> 5);
-    const double sum = row_dot(A.val64 + beg + lane, A.col + beg + lane, w, x);
+    const double sum = row_dot<double, BATCH>(A.val64 + beg + lane, A.col + beg + lane, w, x);
     const int64_t row = s * kSliceC + lane;
     const double xi = x[row];
     const double pi = FIRST ? xi : prev[row];
@@ -106,8 +109,8 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
   t = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
 }
 
-template <bool FIRST, bool LAST>
-__global__ void __launch_bounds__(256) k_step_f32(SellDev A, const float* __restrict__ tau2m,
+template <bool FIRST, bool LAST, int BATCH, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_step_f32(SellDev A, const float* __restrict__ tau2m,
                                                   const float* __restrict__ x, const float* prev,
                                                   float* out, float* acc_s, float* acc_c, double* acc64,
                                                   int64_t acc_stride, int F, const float* __restrict__ ahi,
@@ -119,7 +122,7 @@ __global__ void __launch_bounds__(256) k_step_f32(SellDev A, const float* __rest
        s += nwarps) {
     const int64_t beg = A.slice_ptr[s];
     const int w = static_cast<int>((A.slice_ptr[s + 1] - beg) >> 5);
-    const float sum = row_dot(A.val32 + beg + lane, A.col + beg + lane, w, x);
+    const float sum = row_dot<float, BATCH>(A.val32 + beg + lane, A.col + beg + lane, w, x);
     const int64_t row = s * kSliceC + lane;
     const float xi = x[row];
     const float pi = FIRST ? xi : prev[row];
@@ -173,7 +176,7 @@ __global__ void __launch_bounds__(256) k_spmv_f64(SellDev A, const double* __res
        s += nwarps) {
     const int64_t beg = A.slice_ptr[s];
     const int w = static_cast<int>((A.slice_ptr[s + 1] - beg) >> 5);
-    const double sum = row_dot(A.val64 + beg + lane, A.col + beg + lane, w, x);
+    const double sum = row_dot<double, 8>(A.val64 + beg + lane, A.col + beg + lane, w, x);
     const int64_t row = s * kSliceC + lane;
     y[row] = dscale ? sum * dscale[row] : sum;
   }
@@ -192,32 +195,82 @@ int grid_for(const LaunchCfg& cfg, int64_t n_slices) {
   return static_cast<int>(need < cfg.grid_step ? need : cfg.grid_step);
 }
 
+// Launch shapes of the step kernels: (load batch, minimum resident blocks of 256
+// threads per SM, which caps the registers). Every variant computes the same sums.
+#define KES_STEP_VARIANTS(X) \
+  X(0, 8, 1) X(1, 8, 3) X(2, 8, 4) X(3, 4, 4) X(4, 4, 5) X(5, 4, 6) X(6, 2, 6) X(7, 2, 8)
+
+template <int BATCH, int MINB>
+void step_f64_impl(int grid, int block, cudaStream_t st, bool first, bool last, const SellDev& A,
+                   const double* tau2m, const double* x, const double* prev, double* out, double* acc,
+                   int64_t acc_stride, int F, const double* alpha, int Lp1, int step, int* flag) {
+  if (first && last)
+    k_step_f64<true, true, BATCH, MINB><<<grid, block, 0, st>>>(A, tau2m, x, prev, out, acc, acc_stride, F,
+                                                                 alpha, Lp1, step, flag);
+  else if (first)
+    k_step_f64<true, false, BATCH, MINB><<<grid, block, 0, st>>>(A, tau2m, x, prev, out, acc, acc_stride, F,
+                                                                  alpha, Lp1, step, flag);
+  else if (last)
+    k_step_f64<false, true, BATCH, MINB><<<grid, block, 0, st>>>(A, tau2m, x, prev, out, acc, acc_stride, F,
+                                                                  alpha, Lp1, step, flag);
+  else
+    k_step_f64<false, false, BATCH, MINB><<<grid, block, 0, st>>>(A, tau2m, x, prev, out, acc, acc_stride, F,
+                                                                   alpha, Lp1, step, flag);
+}
+
+template <int BATCH, int MINB>
+void step_f32_impl(int grid, int block, cudaStream_t st, bool first, bool last, const SellDev& A,
+                   const float* tau2m, const float* x, const float* prev, float* out, float* acc_s, float* acc_c,
+                   double* acc64, int64_t acc_stride, int F, const float* ahi, const float* alo, int Lp1,
+                   int step, int* flag) {
+#define KES_F32_ARGS A, tau2m, x, prev, out, acc_s, acc_c, acc64, acc_stride, F, ahi, alo, Lp1, step, flag
+  if (first && last) k_step_f32<true, true, BATCH, MINB><<<grid, block, 0, st>>>(KES_F32_ARGS);
+  else if (first) k_step_f32<true, false, BATCH, MINB><<<grid, block, 0, st>>>(KES_F32_ARGS);
+  else if (last) k_step_f32<false, true, BATCH, MINB><<<grid, block, 0, st>>>(KES_F32_ARGS);
+  else k_step_f32<false, false, BATCH, MINB><<<grid, block, 0, st>>>(KES_F32_ARGS);
+#undef KES_F32_ARGS
+}
+
 }  // namespace
 
-int step_blocks_per_sm(bool fp32, int block) {
+int step_variant_count() {
+  int n = 0;
+#define X(ID, B, M) ++n;
+  KES_STEP_VARIANTS(X)
+#undef X
+  return n;
+}
+
+int step_blocks_per_sm(bool fp32, int variant, int block) {
   int nb = 0;
-  cudaError_t e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_f32<false, false>, block, 0)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_f64<false, false>, block, 0);
-  return (e == cudaSuccess && nb > 0) ? nb : 4;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (variant) {
+#define X(ID, B, M)                                                                                      \
+  case ID:                                                                                               \
+    e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_f32<false, false, B, M>, block, 0) \
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_f64<false, false, B, M>, block, 0); \
+    break;
+    KES_STEP_VARIANTS(X)
+#undef X
+    default: break;
+  }
+  return (e == cudaSuccess && nb > 0) ? nb : 2;
 }
 
 void launch_step_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bool first, const double* tau2m,
                      const double* x, const double* prev, double* out, double* acc, int64_t acc_stride, int F,
                      const double* alpha, int L, int step, bool last, int* flag) {
   const int grid = grid_for(cfg, A.n_slices);
-  const int Lp1 = L + 1;
-  if (first && last)
-    k_step_f64<true, true><<<grid, cfg.block_step, 0, st>>>(A, tau2m, x, prev, out, acc, acc_stride, F, alpha,
-                                                             Lp1, step, flag);
-  else if (first)
-    k_step_f64<true, false><<<grid, cfg.block_step, 0, st>>>(A, tau2m, x, prev, out, acc, acc_stride, F, alpha,
-                                                              Lp1, step, flag);
-  else if (last)
-    k_step_f64<false, true><<<grid, cfg.block_step, 0, st>>>(A, tau2m, x, prev, out, acc, acc_stride, F, alpha,
-                                                              Lp1, step, flag);
-  else
-    k_step_f64<false, false><<<grid, cfg.block_step, 0, st>>>(A, tau2m, x, prev, out, acc, acc_stride, F,
-                                                               alpha, Lp1, step, flag);
+  switch (cfg.variant) {
+#define X(ID, B, M)                                                                                        \
+  case ID:                                                                                                 \
+    step_f64_impl<B, M>(grid, cfg.block_step, st, first, last, A, tau2m, x, prev, out, acc, acc_stride, F, \
+                        alpha, L + 1, step, flag);                                                         \
+    break;
+    KES_STEP_VARIANTS(X)
+#undef X
+    default: break;
+  }
   ++g_launches;
 }
 
@@ -226,13 +279,16 @@ void launch_step_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bo
                      float* acc_c, double* acc64, int64_t acc_stride, int F, const float* alpha_hi,
                      const float* alpha_lo, int L, int step, int* flag) {
   const int grid = grid_for(cfg, A.n_slices);
-  const int Lp1 = L + 1;
-#define KES_F32_ARGS A, tau2m, x, prev, out, acc_s, acc_c, acc64, acc_stride, F, alpha_hi, alpha_lo, Lp1, step, flag
-  if (first && last) k_step_f32<true, true><<<grid, cfg.block_step, 0, st>>>(KES_F32_ARGS);
-  else if (first) k_step_f32<true, false><<<grid, cfg.block_step, 0, st>>>(KES_F32_ARGS);
-  else if (last) k_step_f32<false, true><<<grid, cfg.block_step, 0, st>>>(KES_F32_ARGS);
-  else k_step_f32<false, false><<<grid, cfg.block_step, 0, st>>>(KES_F32_ARGS);
-#undef KES_F32_ARGS
+  switch (cfg.variant) {
+#define X(ID, B, M)                                                                                        \
+  case ID:                                                                                                 \
+    step_f32_impl<B, M>(grid, cfg.block_step, st, first, last, A, tau2m, x, prev, out, acc_s, acc_c, acc64, \
+                        acc_stride, F, alpha_hi, alpha_lo, L + 1, step, flag);                             \
+    break;
+    KES_STEP_VARIANTS(X)
+#undef X
+    default: break;
+  }
   ++g_launches;
 }
 

@@ -276,6 +276,8 @@ void ensure_stage_out(kes_ctx* c, int F) {
     c->dfree(c->acc_c);
     c->acc_s = c->dalloc_n<float>(static_cast<int64_t>(F) * c->n_pad);
     c->acc_c = c->dalloc_n<float>(static_cast<int64_t>(F) * c->n_pad);
+    KES_CUDA(cudaMemsetAsync(c->acc_s, 0, static_cast<size_t>(F) * c->n_pad * sizeof(float), c->stream));
+    KES_CUDA(cudaMemsetAsync(c->acc_c, 0, static_cast<size_t>(F) * c->n_pad * sizeof(float), c->stream));
   }
   c->stage_out_F = F;
   if (c->gexec) {  // buffers moved: recapture
@@ -310,6 +312,58 @@ void ensure_krylov(kes_ctx* c, int kmax) {
   KES_CUDA(cudaMemsetAsync(c->Hd, 0, sizeof(double) * kmax * kmax, c->stream));
 }
 
+// Times every launch shape of the step kernel on this matrix (a few steps on zeroed
+// scratch state, CUDA events) and keeps the fastest. All shapes compute the same sums.
+void tune_step(kes_ctx* c) {
+  const bool fp32 = c->opts.precision == KES_PREC_FP32;
+  const int nv = step_variant_count();
+  ensure_stage_out(c, 1);
+  double* a64 = c->dalloc_n<double>(8);
+  float* a32 = c->dalloc_n<float>(8);
+  KES_CUDA(cudaMemsetAsync(a64, 0, 8 * sizeof(double), c->stream));
+  KES_CUDA(cudaMemsetAsync(a32, 0, 8 * sizeof(float), c->stream));
+  cudaEvent_t e0 = c->get_event(), e1 = c->get_event();
+  auto steps = [&](int count) {
+    for (int i = 0; i < count; ++i) {
+      if (fp32)
+        launch_step_f32(c->A, c->cfg, c->stream, false, false, c->tau2m32, c->U32[0], c->U32[1], c->U32[1],
+                        c->acc_s, c->acc_c, c->stage_out, c->n_pad, 1, a32, a32, 7, 1, c->d_flag);
+      else
+        launch_step_f64(c->A, c->cfg, c->stream, false, c->tau2m64, c->U64[0], c->U64[1], c->U64[1],
+                        c->stage_out, c->n_pad, 1, a64, 7, 1, false, c->d_flag);
+    }
+  };
+  int best = 0;
+  float best_ms = 3.0e38f;
+  for (int v = 0; v < nv; ++v) {
+    c->cfg.variant = v;
+    c->cfg.grid_step = c->cfg.n_sm * step_blocks_per_sm(fp32, v, c->cfg.block_step);
+    steps(2);
+    float ms_v = 3.0e38f;
+    for (int rep = 0; rep < 2; ++rep) {
+      KES_CUDA(cudaEventRecord(e0, c->stream));
+      steps(6);
+      KES_CUDA(cudaEventRecord(e1, c->stream));
+      KES_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      KES_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      ms_v = std::min(ms_v, ms);
+    }
+    KES_CHECK_LAUNCH();
+    if (ms_v < best_ms) {
+      best_ms = ms_v;
+      best = v;
+    }
+  }
+  c->ev_pool.push_back(e0);
+  c->ev_pool.push_back(e1);
+  c->cfg.variant = best;
+  c->cfg.grid_step = c->cfg.n_sm * step_blocks_per_sm(fp32, best, c->cfg.block_step);
+  c->sync();
+  c->dfree(a64);
+  c->dfree(a32);
+}
+
 void validate_csr(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val, const double* m) {
   if (n <= 0 || n >= (int64_t(1) << 31) || !row_ptr || !col || !val || !m) throw KesError{KES_ERR_ARG};
   if (row_ptr[0] != 0) throw KesError{KES_ERR_ARG};
@@ -339,6 +393,7 @@ void kes_opts_default(kes_opts* o) {
   o->sell_sigma = 1;
   o->use_graph = 1;
   o->block_b = 1;
+  o->autotune = 1;
 }
 
 void kes_solve_opts_default(kes_solve_opts* o) {
@@ -459,12 +514,17 @@ kes_status kes_create(kes_ctx** out, int64_t n, const int64_t* row_ptr, const in
     KES_CUDA(cudaMemsetAsync(c->stage_in, 0, c->n_pad * sizeof(double), c->stream));
     c->d_flag = c->dalloc_n<int>(4);
     KES_CUDA(cudaMemsetAsync(c->d_flag, 0, 4 * sizeof(int), c->stream));
+    if (c->tau2m32) KES_CUDA(cudaMemsetAsync(c->tau2m32, 0, c->n_pad * sizeof(float), c->stream));
     // grid-stride launch shape: one full wave of resident 256-thread blocks
     c->cfg.n_sm = n_sm;
     c->cfg.block_step = 256;
-    c->cfg.grid_step = n_sm * step_blocks_per_sm(c->opts.precision == KES_PREC_FP32, c->cfg.block_step);
+    c->cfg.variant = 0;
+    c->cfg.grid_step = n_sm * step_blocks_per_sm(c->opts.precision == KES_PREC_FP32, 0, c->cfg.block_step);
+    if (c->opts.autotune) tune_step(c);
     c->sync();
     c->stats.bytes_per_step = kes_step_bytes(c, 1, 1);
+    c->stats.step_variant = c->cfg.variant;
+    c->stats.step_grid = c->cfg.grid_step;
     return KES_OK;
   });
   if (st != KES_OK) {
@@ -852,6 +912,8 @@ kes_status kes_reset_stats(kes_ctx* c) {
     const int64_t bps = c->stats.bytes_per_step;
     c->stats = kes_stats{};
     c->stats.bytes_per_step = bps;
+    c->stats.step_variant = c->cfg.variant;
+    c->stats.step_grid = c->cfg.grid_step;
     return KES_OK;
   });
 }

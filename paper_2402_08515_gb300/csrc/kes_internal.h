@@ -49,6 +49,7 @@ struct LaunchCfg {
   int grid_step = 0;   // blocks of the step / SpMV kernels (grid-stride over slices)
   int block_step = 256;
   int n_sm = 152;
+  int variant = 0;     // step-kernel launch shape (load batch, register cap), see step_variant_count
 };
 
 // One fused leapfrog step, FP64 (Sec. 2.3, eq. 2stepmethod + eq. disc_filtercoeff):
@@ -71,9 +72,11 @@ void launch_step_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bo
 void launch_init_f32(cudaStream_t st, int64_t n_pad, const double* r64, float* x32, float* acc_s,
                      float* acc_c, int64_t acc_stride, int F, const double* alpha64, int L);
 
-// Resident blocks per SM of the step kernel (occupancy calculator); the step grid is
-// n_sm * this, so that the grid-stride loop runs in exactly one wave.
-int step_blocks_per_sm(bool fp32, int block);
+// Launch-shape variants of the step kernels (same arithmetic, different load batch and
+// register cap) and the resident blocks per SM of one variant (occupancy calculator);
+// the step grid is n_sm * that, so that the grid-stride loop runs in one wave.
+int step_variant_count();
+int step_blocks_per_sm(bool fp32, int variant, int block);
 
 // y = dscale .* (S x) (dscale may be null) in FP64.
 void launch_spmv_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, const double* x,

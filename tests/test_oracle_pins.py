@@ -108,10 +108,10 @@ def test_q_bounded_inside_cfl_and_growing_outside():
     assert abs(outside[-1]) > 1e20
 
 
-# ---------------------------------------------------------------- Lemma 2.1 limit
+# ---------------------------------------------------------------- Lemma 2.2 limit
 
 def test_beta_tilde_tends_to_indicator():
-    # Lemma 2.1 with eq. weightf: beta -> chi_[wmin, wmax] (1/2 at the ends)
+    # Lemma 2.2 with eq. weightf: beta -> chi_[wmin, wmax] (1/2 at the ends)
     # as tau -> 0 and T -> infinity
     wmin, wmax = 2.0, 4.0
     tau, L = 0.002, 200000               # T = 400
