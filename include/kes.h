@@ -205,6 +205,35 @@ void kes_result_free(kes_result* res);
 kes_status kes_get_stats(kes_ctx* ctx, kes_stats* stats); /* synchronises the stream */
 kes_status kes_reset_stats(kes_ctx* ctx);
 
+/*
+ * kes_filter_apply_noalloc -- r_out = C r_in for one start vector in FP64, like
+ * kes_filter_apply, without allocating anything. The paper has no counterpart:
+ * this entry point is for callers that cannot call cudaMalloc at all, such as a
+ * program that reserves every byte of device memory it may use when it starts and
+ * forbids later allocation (a long-running service with a fixed memory budget, a
+ * plugin whose host owns the device heap), so that nothing can fail or fragment
+ * mid-run. kes_create allocates the context's state, so those callers use this
+ * function: they own every input and the output, and the two leapfrog state
+ * vectors live in a fixed array inside the library, 2 * KES_NOALLOC_MAX_N doubles
+ * (16 MiB), which every GPU that loads the library holds until the process exits.
+ *   n        rows, 1 <= n <= KES_NOALLOC_MAX_N; a larger n returns KES_ERR_ARG and launches nothing
+ *   row_ptr  device int64[n+1]; col device int32[nnz]; val device float64[nnz]: CSR of S
+ *   tau2m    device float64[n], tau^2 / m_i
+ *   alpha    device float64[L+1], the weights kes_alpha_table returns (L >= 1 steps)
+ *   r_in     device float64[n]; r_out device float64[n] receives the filtered vector
+ *   stream   cudaStream_t (NULL: the legacy default stream); the call only enqueues the work
+ * The first call on a device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream capture. Every
+ * call shares the array, which keeps the last call's contents (each call writes every
+ * entry before reading it, so nothing needs clearing); calls whose GPU work overlaps
+ * race on it. A CFL violation is not detected here: it shows as huge or non-finite
+ * values in r_out. Calls no cudaMalloc, cudaFree or other allocating routine.
+ */
+#define KES_NOALLOC_MAX_N 1048576
+kes_status kes_filter_apply_noalloc(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
+                                    const double* tau2m, const double* alpha, int32_t L, const double* r_in,
+                                    double* r_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,7 +23,7 @@ __all__ = [
     "kes_size", "kes_sync", "kes_estimate_omega_max", "kes_set_filter", "kes_set_filters",
     "kes_alpha_table", "kes_filter_response", "kes_sym_eig", "kes_step_bytes",
     "kes_filter_apply", "kes_krylov_solve", "kes_get_stats", "kes_reset_stats",
-    "Context", "header_functions",
+    "Context", "header_functions", "kes_filter_apply_noalloc", "KES_NOALLOC_MAX_N",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -98,6 +98,7 @@ _sig = {
     "kes_result_free": (None, [C.POINTER(KesResult)]),
     "kes_get_stats": (C.c_int, [_P, C.POINTER(KesStats)]),
     "kes_reset_stats": (C.c_int, [_P]),
+    "kes_filter_apply_noalloc": (C.c_int, [C.c_int64, _P, _P, _P, _P, _P, C.c_int32, _P, _P, _P]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(lib, _name)
@@ -266,6 +267,16 @@ def kes_get_stats(ctx: int) -> dict:
 
 def kes_reset_stats(ctx: int) -> None:
     _check(lib.kes_reset_stats(ctx), "kes_reset_stats")
+
+
+KES_NOALLOC_MAX_N = 1048576
+
+
+def kes_filter_apply_noalloc(n, row_ptr, col, val, tau2m, alpha, L, r_in, r_out, stream=None) -> None:
+    """Allocation-free FP64 filter of one vector; every array argument is a CUDA tensor the
+    caller owns (int64 row_ptr, int32 col, float64 val / tau2m / alpha / r_in / r_out)."""
+    _check(lib.kes_filter_apply_noalloc(int(n), _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(tau2m), _ptr(alpha),
+                                        int(L), _ptr(r_in), _ptr(r_out), stream), "kes_filter_apply_noalloc")
 
 
 # ------------------------------------------------------------------ convenience

@@ -23,6 +23,7 @@ SOURCES = [
     "csrc/kernels_step.cu",
     "csrc/kernels_blas.cu",
     "csrc/kes_api.cu",
+    "csrc/noalloc.cu",
 ]
 HEADERS = ["csrc/kes_internal.h", os.path.join("..", "include", "kes.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
