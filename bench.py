@@ -55,6 +55,8 @@ def parse_args(argv=None):
     ap.add_argument("--mode", default="solve", choices=["solve", "filter"],
                     help="filter: one filter application only (small profiling runs)")
     ap.add_argument("--L", type=int, default=0, help="override the workload's time steps (--mode filter)")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="fixed step-kernel launch shape instead of the autotuner's choice")
     return ap.parse_args(argv)
 
 
@@ -230,7 +232,7 @@ def run_kes(args):
     problem = wl.build()
     n = problem.n
     stream = torch.cuda.Stream(device=dev)
-    ctx = K.Context(problem, precision=wl.precision, stream=stream)
+    ctx = K.Context(problem, precision=wl.precision, stream=stream, step_variant=args.variant)
     h = ctx.handle
     v0 = start_vectors(n, 1, wl.seed)[0]
     omega_pow, gersh = K.kes_estimate_omega_max(h, wl.power_iters, v0)
@@ -250,7 +252,8 @@ def run_kes(args):
         st = K.kes_get_stats(h)
         if rank == 0:
             print(json.dumps({"mode": "filter", "workload": args.workload, "L": L, "dofs": n,
-                              "filter_ms": st["filter_ms"], "finite": bool(torch.isfinite(out).all())}))
+                              "filter_ms": st["filter_ms"], "step_variant": st["step_variant"],
+                              "finite": bool(torch.isfinite(out).all())}))
         ctx.close()
         return
 
@@ -330,6 +333,7 @@ def run_kes(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
                      "kernel": "k_step_f64" if wl.precision == "fp64" else "k_step_f32",
+                     "step_variant": stats["step_variant"], "step_grid": stats["step_grid"],
                      "step_us": step_ms * 1e3, "algorithmic_bytes_per_step": bytes_step},
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -63,8 +63,8 @@ typedef struct kes_opts {
   int32_t use_graph;   /* 1: the L time steps of a filter application replay as one CUDA graph; 0: plain launches */
   int32_t block_b;     /* largest number of start vectors filtered together (columns of kes_filter_apply) */
   int32_t autotune;    /* 1: kes_create times every launch shape of the step kernel on this matrix and keeps the
-                          fastest (results do not depend on the choice); 0: the first shape */
-  int32_t reserved;    /* set to 0 */
+                          fastest (results do not depend on the choice); 0: use step_variant */
+  int32_t step_variant; /* launch shape used when autotune is 0 (0 .. number of shapes - 1) */
   void* stream;        /* cudaStream_t for every launch; NULL: the context creates its own non-blocking stream */
   /* Optional device allocator (e.g. a framework's caching allocator). Both NULL: cudaMalloc / cudaFree. */
   void* (*dev_alloc)(size_t bytes, void* user);

@@ -52,7 +52,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
 
 class KesOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("sell_sigma", C.c_int32), ("use_graph", C.c_int32),
-                ("block_b", C.c_int32), ("autotune", C.c_int32), ("reserved", C.c_int32), ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN),
+                ("block_b", C.c_int32), ("autotune", C.c_int32), ("step_variant", C.c_int32), ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN),
                 ("dev_free", FREE_FN), ("alloc_user", C.c_void_p)]
 
 
@@ -286,9 +286,11 @@ class Context:
     ``torch_alloc`` is set, launches on ``stream`` (a torch.cuda.Stream or None)."""
 
     def __init__(self, problem, precision: str = "fp64", sell_sigma: int = 1, use_graph: bool = True,
-                 block_b: int = 1, stream=None, torch_alloc: bool = False, autotune: bool = True):
+                 block_b: int = 1, stream=None, torch_alloc: bool = False, autotune: bool = True,
+                 step_variant: int | None = None):
         o = kes_opts_default()
-        o.autotune = 1 if autotune else 0
+        o.autotune = 1 if (autotune and step_variant is None) else 0
+        o.step_variant = step_variant or 0
         o.precision = KES_PREC_FP32 if precision == "fp32" else KES_PREC_FP64
         o.sell_sigma = sell_sigma
         o.use_graph = 1 if use_graph else 0

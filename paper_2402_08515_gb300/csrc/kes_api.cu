@@ -518,8 +518,10 @@ kes_status kes_create(kes_ctx** out, int64_t n, const int64_t* row_ptr, const in
     // grid-stride launch shape: one full wave of resident 256-thread blocks
     c->cfg.n_sm = n_sm;
     c->cfg.block_step = 256;
-    c->cfg.variant = 0;
-    c->cfg.grid_step = n_sm * step_blocks_per_sm(c->opts.precision == KES_PREC_FP32, 0, c->cfg.block_step);
+    if (c->opts.step_variant < 0 || c->opts.step_variant >= step_variant_count()) throw KesError{KES_ERR_ARG};
+    c->cfg.variant = c->opts.step_variant;
+    c->cfg.grid_step =
+        n_sm * step_blocks_per_sm(c->opts.precision == KES_PREC_FP32, c->cfg.variant, c->cfg.block_step);
     if (c->opts.autotune) tune_step(c);
     c->sync();
     c->stats.bytes_per_step = kes_step_bytes(c, 1, 1);
