@@ -61,7 +61,9 @@ typedef struct kes_opts {
   int32_t precision;   /* enum kes_precision */
   int32_t sell_sigma;  /* SELL-C-sigma sorting window in rows (slices are C = 32 rows); 1 keeps the row order */
   int32_t use_graph;   /* 1: the L time steps of a filter application replay as one CUDA graph; 0: plain launches */
-  int32_t block_b;     /* largest number of start vectors filtered together (columns of kes_filter_apply) */
+  int32_t block_b;     /* largest number of start vectors filtered together (columns of kes_filter_apply and
+                          the block size of kes_block_krylov_solve), 1..8; blocks of 2, 4 or 8 columns run
+                          as one SpMM step (row-major state), other sizes are padded to the next of them */
   int32_t autotune;    /* 1: kes_create times every launch shape of the step kernel on this matrix and keeps the
                           fastest (results do not depend on the choice); 0: use step_variant */
   int32_t step_variant; /* launch shape used when autotune is 0 (0 .. number of shapes - 1) */
@@ -130,8 +132,23 @@ const char* kes_strerror(int32_t status);
 kes_status kes_create(kes_ctx** out, int64_t n, const int64_t* row_ptr, const int32_t* col,
                       const double* val, const double* m_diag, const kes_opts* opts);
 void kes_destroy(kes_ctx* ctx);
-int64_t kes_size(const kes_ctx* ctx);
+int64_t kes_size(const kes_ctx* ctx);   /* n_total: rows of all meshes */
+int32_t kes_mesh_count(const kes_ctx* ctx);
 kes_status kes_sync(kes_ctx* ctx);
+
+/*
+ * kes_create_batch -- several independent pencils ("meshes") in one context. They
+ * are stacked block-diagonally in one SELL-C-sigma matrix, each mesh starting on a
+ * slice boundary, so that every fused-step launch (and the one CUDA graph of a
+ * filter application) advances all meshes at once; each mesh keeps its own tau,
+ * weight tables, Krylov basis and projected problem. Arguments per mesh j < n_mesh
+ * as in kes_create (host arrays: n[j], row_ptr[j], col[j], val[j], m_diag[j]).
+ * Every vector passed to the other calls concatenates the meshes in this order,
+ * n_total = sum_j n[j] rows per column. kes_create is the n_mesh = 1 case.
+ */
+kes_status kes_create_batch(kes_ctx** out, int32_t n_mesh, const int64_t* n, const int64_t* const* row_ptr,
+                            const int32_t* const* col, const double* const* val, const double* const* m_diag,
+                            const kes_opts* opts);
 
 /*
  * kes_estimate_omega_max -- largest eigenfrequency of the pencil by power
@@ -144,6 +161,11 @@ kes_status kes_sync(kes_ctx* ctx);
  */
 kes_status kes_estimate_omega_max(kes_ctx* ctx, int32_t iters, const double* v0, double* omega_max,
                                   double* gershgorin);
+/* The same power iteration for every mesh of a batch at once (each mesh normalised on
+   its own rows): v0[n_total], omega_max[n_mesh], gershgorin[n_mesh] (may be NULL).
+   kes_estimate_omega_max requires a single mesh (else KES_ERR_UNSUPPORTED). */
+kes_status kes_estimate_omega_max_batch(kes_ctx* ctx, int32_t iters, const double* v0, double* omega_max,
+                                        double* gershgorin);
 
 /*
  * kes_set_filter -- weights alpha_n = tau * alpha(n tau), n = 0..L, of
@@ -158,6 +180,11 @@ kes_status kes_estimate_omega_max(kes_ctx* ctx, int32_t iters, const double* v0,
 kes_status kes_set_filter(kes_ctx* ctx, double omega_min, double omega_max, double tau, int32_t L);
 kes_status kes_set_filters(kes_ctx* ctx, int32_t F, const double* omega_min, const double* omega_max,
                            double tau, int32_t L);
+/* Per-mesh filters of a batch: omega_min/omega_max[n_mesh * F] (mesh-major), tau[n_mesh];
+   all meshes share L (one launch per step advances them together). kes_set_filter(s)
+   give every mesh the same intervals and tau. */
+kes_status kes_set_filters_batch(kes_ctx* ctx, int32_t F, const double* omega_min, const double* omega_max,
+                                 const double* tau, int32_t L);
 
 /* Host helpers, no context and no GPU needed. */
 /* kes_alpha_table: alpha[0..L] = tau * alpha(n tau) of eq. (weightf), T = L tau. */
@@ -179,9 +206,9 @@ int64_t kes_step_bytes(const kes_ctx* ctx, int32_t b, int32_t F);
  * leapfrog steps y_{l+1} = -tau^2 M^{-1} S y_l + 2 y_l - y_{l-1}, y_{-1} = y_0 = r
  * (eq. 2stepmethod), accumulating sum_{n=0..L} alpha_n y_n. Each step is one
  * fused kernel (SpMV, diagonal scale, three-term update, weighted accumulation).
- *   r_in   n x b col-major float64 (host or device per `mem`)
- *   r_out  F x b x n float64 (block f holds the sum with weight table f)
- *   b      1 <= b <= opts.block_b
+ *   r_in   n_total x b col-major float64 (host or device per `mem`)
+ *   r_out  F x b x n_total float64 (block f holds the sum with weight table f)
+ *   b      1 <= b <= opts.block_b; the b vectors share one trajectory (SpMM step)
  * Device pointers: asynchronous on the context stream. Host pointers: the
  * call copies in, runs and copies out before returning.
  * KES_ERR_UNSTABLE if a non-finite value appeared in the state.
@@ -196,10 +223,30 @@ kes_status kes_filter_apply(kes_ctx* ctx, const double* r_in, double* r_out, int
  *   sopts  NULL for defaults
  *   out    receives a kes_result (free with kes_result_free); set even on
  *          KES_INFO_INVARIANT_SUBSPACE.
- * Requires a single filter interval (kes_set_filter).
+ * Requires a single mesh and a single filter interval (kes_set_filter).
  */
 kes_status kes_krylov_solve(kes_ctx* ctx, const double* r0, int32_t mem, const kes_solve_opts* sopts,
                             kes_result** out);
+
+/*
+ * kes_block_krylov_solve -- the block version of the Krylov space (Sec. 4: start
+ * from b M-orthonormalised random vectors and orthonormalise every filtered block),
+ * for every mesh of the context at once. Each block step filters the b newest basis
+ * vectors of every mesh in one SpMM trajectory, then orthogonalises each filtered
+ * vector (two classical passes, M-inner product) into its mesh's basis; dependent
+ * vectors are dropped, and a mesh whose whole block is dependent stops (invariant
+ * subspace). The projected problem and the residual acceptance are those of
+ * kes_krylov_solve, per mesh. A block of b vectors resolves eigenvalues of
+ * multiplicity up to b.
+ *   R0     n_total x b col-major start vectors (host or device per `mem`)
+ *   b      1 <= b <= opts.block_b
+ *   sopts  kmax counts basis vectors per mesh (kmax >= b)
+ *   out    array of kes_mesh_count(ctx) result pointers, one per mesh (free each with
+ *          kes_result_free); set on KES_OK and KES_INFO_INVARIANT_SUBSPACE
+ * Requires a single filter interval per mesh.
+ */
+kes_status kes_block_krylov_solve(kes_ctx* ctx, const double* R0, int32_t b, int32_t mem,
+                                  const kes_solve_opts* sopts, kes_result** out);
 void kes_result_free(kes_result* res);
 
 kes_status kes_get_stats(kes_ctx* ctx, kes_stats* stats); /* synchronises the stream */

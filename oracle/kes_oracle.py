@@ -39,7 +39,7 @@ __all__ = [
     "weight", "alpha_table", "q_values", "beta_tilde", "filter_apply",
     "filter_apply_multi", "power_iteration", "m_inner", "m_norm",
     "orthonormalize_cgs2", "rayleigh_ritz", "ritz_residuals", "krylov_solve",
-    "KrylovResult", "BREAKDOWN_RATIO",
+    "block_krylov_solve", "KrylovResult", "BREAKDOWN_RATIO",
 ]
 
 BREAKDOWN_RATIO = 1e-10
@@ -290,6 +290,78 @@ def krylov_solve(S, m: np.ndarray, r0: np.ndarray, omega_min: float,
         k += 1
         if k % check_every == 0 and k < kmax:
             project(k)
+    theta, rel_all, th_acc, rel_acc, abs_acc, X_acc = project(k)
+    return KrylovResult(omega2=th_acc, omega=np.sqrt(th_acc), rel_res=rel_acc,
+                        abs_res=abs_acc, vectors=X_acc, k_used=k,
+                        time_steps=steps, breakdown=breakdown, ritz_theta=theta,
+                        ritz_rel_res=rel_all,
+                        basis=B[:k] if keep_basis else None, history=history)
+
+
+def block_krylov_solve(S, m: np.ndarray, R0: np.ndarray, omega_min: float,
+                       omega_max: float, tau: float, L: int, kmax: int, tol: float,
+                       check_every: int = 5, keep_basis: bool = True) -> KrylovResult:
+    """Block version of the Krylov space (Sec. 4, eigenvalue solver): start from b
+    M-orthonormalised random vectors and orthonormalise every filtered block.
+
+    R0: (b, n). The b start vectors are orthonormalised in order (CGS2, dependent
+    ones dropped). Each block step filters the b newest basis vectors, one after the
+    other orthogonalises each filtered vector into the basis and appends it unless it
+    is dependent, stopping at kmax vectors; a step that appends nothing is a
+    breakdown. The projected problem and the acceptance are those of krylov_solve,
+    solved whenever the basis size passes a multiple of check_every and at the end."""
+    R0 = np.atleast_2d(np.asarray(R0, dtype=np.float64))
+    b = R0.shape[0]
+    alpha = alpha_table(omega_min, omega_max, tau, L)
+    n = len(m)
+    B = np.zeros((kmax, n))
+    k = 0
+    for r in R0:
+        if k >= kmax:
+            break
+        v, nb, na = orthonormalize_cgs2(B[:k], r, m)
+        if v is not None:
+            B[k] = v
+            k += 1
+    steps = 0
+    breakdown = k == 0
+    history = []
+    next_check = check_every
+
+    def project(kk):
+        theta, Y = rayleigh_ritz(S, B[:kk])
+        omega = np.sqrt(theta)
+        inside = (omega >= omega_min) & (omega <= omega_max)
+        rel_all = np.full(kk, np.nan)
+        X, a, r = ritz_residuals(S, m, B[:kk], theta[inside], Y[:, inside])
+        rel_all[inside] = r
+        acc = r <= tol
+        history.append(dict(k=kk, n_inside=int(inside.sum()), n_acc=int(acc.sum())))
+        return theta, rel_all, theta[inside][acc], r[acc], a[acc], X[acc]
+
+    kproj = -1
+    while not breakdown and k < kmax:
+        newest = [B[j] if j >= 0 else np.zeros(n) for j in range(k - b, k)]
+        W = [filter_apply(S, m, v, tau, alpha) for v in newest]
+        steps += L
+        added = 0
+        for w in W:
+            if k >= kmax:
+                break
+            v, nb, na = orthonormalize_cgs2(B[:k], w, m)
+            if v is None:
+                continue
+            B[k] = v
+            k += 1
+            added += 1
+        if added == 0:
+            breakdown = True
+            break
+        if k >= next_check and k < kmax:
+            while next_check <= k:
+                next_check += check_every
+            project(k)
+            kproj = k
     theta, rel_all, th_acc, rel_acc, abs_acc, X_acc = project(k)
     return KrylovResult(omega2=th_acc, omega=np.sqrt(th_acc), rel_res=rel_acc,
                         abs_res=abs_acc, vectors=X_acc, k_used=k,

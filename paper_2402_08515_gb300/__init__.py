@@ -24,6 +24,8 @@ __all__ = [
     "kes_alpha_table", "kes_filter_response", "kes_sym_eig", "kes_step_bytes",
     "kes_filter_apply", "kes_krylov_solve", "kes_get_stats", "kes_reset_stats",
     "Context", "header_functions", "kes_filter_apply_noalloc", "KES_NOALLOC_MAX_N",
+    "kes_create_batch", "kes_mesh_count", "kes_estimate_omega_max_batch", "kes_set_filters_batch",
+    "kes_block_krylov_solve",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -99,6 +101,12 @@ _sig = {
     "kes_get_stats": (C.c_int, [_P, C.POINTER(KesStats)]),
     "kes_reset_stats": (C.c_int, [_P]),
     "kes_filter_apply_noalloc": (C.c_int, [C.c_int64, _P, _P, _P, _P, _P, C.c_int32, _P, _P, _P]),
+    "kes_create_batch": (C.c_int, [C.POINTER(_P), C.c_int32, _P, _P, _P, _P, _P, C.POINTER(KesOpts)]),
+    "kes_mesh_count": (C.c_int32, [_P]),
+    "kes_estimate_omega_max_batch": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
+    "kes_set_filters_batch": (C.c_int, [_P, C.c_int32, _P, _P, _P, C.c_int32]),
+    "kes_block_krylov_solve": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.POINTER(KesSolveOpts),
+                                         C.POINTER(C.POINTER(KesResult))]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(lib, _name)
@@ -236,14 +244,7 @@ def _arr(p, k):
     return np.ctypeslib.as_array(p, shape=(k,)).copy() if k > 0 else np.zeros(0)
 
 
-def kes_krylov_solve(ctx: int, r0, sopts: KesSolveOpts | None = None) -> dict:
-    dev = _is_device(r0)
-    if not dev:
-        r0 = _f64_host(r0)
-    rp = C.POINTER(KesResult)()
-    st = lib.kes_krylov_solve(ctx, _ptr(r0), KES_MEM_DEVICE if dev else KES_MEM_HOST,
-                              C.byref(sopts) if sopts is not None else None, C.byref(rp))
-    _check(st, "kes_krylov_solve", allow_info=True)
+def _result_dict(rp, st) -> dict:
     r = rp.contents
     try:
         p = r.n_pairs
@@ -257,6 +258,73 @@ def kes_krylov_solve(ctx: int, r0, sopts: KesSolveOpts | None = None) -> dict:
     finally:
         lib.kes_result_free(rp)
     return out
+
+
+def kes_krylov_solve(ctx: int, r0, sopts: KesSolveOpts | None = None) -> dict:
+    dev = _is_device(r0)
+    if not dev:
+        r0 = _f64_host(r0)
+    rp = C.POINTER(KesResult)()
+    st = lib.kes_krylov_solve(ctx, _ptr(r0), KES_MEM_DEVICE if dev else KES_MEM_HOST,
+                              C.byref(sopts) if sopts is not None else None, C.byref(rp))
+    _check(st, "kes_krylov_solve", allow_info=True)
+    return _result_dict(rp, st)
+
+
+def kes_block_krylov_solve(ctx: int, R0, b: int, sopts: KesSolveOpts | None = None) -> list[dict]:
+    """R0: (b, n_total) start vectors (numpy or CUDA tensor); one result dict per mesh."""
+    dev = _is_device(R0)
+    if not dev:
+        R0 = _f64_host(R0)
+    nm = lib.kes_mesh_count(ctx)
+    arr = (C.POINTER(KesResult) * nm)()
+    st = lib.kes_block_krylov_solve(ctx, _ptr(R0), int(b), KES_MEM_DEVICE if dev else KES_MEM_HOST,
+                                    C.byref(sopts) if sopts is not None else None,
+                                    C.cast(arr, C.POINTER(C.POINTER(KesResult))))
+    _check(st, "kes_block_krylov_solve", allow_info=True)
+    return [_result_dict(arr[j], st) for j in range(nm)]
+
+
+def kes_mesh_count(ctx: int) -> int:
+    return lib.kes_mesh_count(ctx)
+
+
+def kes_create_batch(problems, opts: KesOpts | None = None) -> int:
+    """problems: sequence of objects with n, row_ptr, col, val, m (host arrays)."""
+    keep = []
+    nm = len(problems)
+    n = np.array([p.n for p in problems], dtype=np.int64)
+    ptrs = {k: (C.c_void_p * nm)() for k in ("row_ptr", "col", "val", "m")}
+    for j, p in enumerate(problems):
+        arrs = dict(row_ptr=np.ascontiguousarray(p.row_ptr, dtype=np.int64),
+                    col=np.ascontiguousarray(p.col, dtype=np.int32), val=_f64_host(p.val), m=_f64_host(p.m))
+        keep.append(arrs)
+        for k, a in arrs.items():
+            ptrs[k][j] = a.ctypes.data
+    h = C.c_void_p()
+    _check(lib.kes_create_batch(C.byref(h), nm, n.ctypes.data, C.cast(ptrs["row_ptr"], C.c_void_p),
+                                C.cast(ptrs["col"], C.c_void_p), C.cast(ptrs["val"], C.c_void_p),
+                                C.cast(ptrs["m"], C.c_void_p), C.byref(opts) if opts is not None else None),
+           "kes_create_batch")
+    return h.value
+
+
+def kes_estimate_omega_max_batch(ctx: int, iters: int, v0) -> tuple[np.ndarray, np.ndarray]:
+    v0 = _f64_host(v0)
+    nm = lib.kes_mesh_count(ctx)
+    om, g = np.zeros(nm), np.zeros(nm)
+    _check(lib.kes_estimate_omega_max_batch(ctx, int(iters), _ptr(v0), om.ctypes.data, g.ctypes.data),
+           "kes_estimate_omega_max_batch")
+    return om, g
+
+
+def kes_set_filters_batch(ctx: int, omega_min, omega_max, tau, L: int) -> None:
+    """omega_min/omega_max: (n_mesh, F); tau: (n_mesh,)."""
+    a = np.ascontiguousarray(np.atleast_2d(omega_min), dtype=np.float64)
+    b = np.ascontiguousarray(np.atleast_2d(omega_max), dtype=np.float64)
+    t = _f64_host(np.atleast_1d(tau))
+    _check(lib.kes_set_filters_batch(ctx, a.shape[1], a.ctypes.data, b.ctypes.data, t.ctypes.data, int(L)),
+           "kes_set_filters_batch")
 
 
 def kes_get_stats(ctx: int) -> dict:
@@ -311,8 +379,12 @@ class Context:
             a, f = ALLOC_FN(_alloc), FREE_FN(_free)
             self._keep += [a, f]
             o.dev_alloc, o.dev_free = a, f
-        self.n = problem.n
-        self.handle = kes_create(problem.n, problem.row_ptr, problem.col, problem.val, problem.m, o)
+        if isinstance(problem, (list, tuple)):
+            self.n = sum(p.n for p in problem)
+            self.handle = kes_create_batch(problem, o)
+        else:
+            self.n = problem.n
+            self.handle = kes_create(problem.n, problem.row_ptr, problem.col, problem.val, problem.m, o)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -22,6 +22,7 @@ SOURCES = [
     "csrc/sell.cpp",
     "csrc/kernels_step.cu",
     "csrc/kernels_blas.cu",
+    "csrc/kernels_block.cu",
     "csrc/kes_api.cu",
     "csrc/noalloc.cu",
 ]

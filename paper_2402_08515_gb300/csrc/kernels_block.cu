@@ -1,0 +1,325 @@
+// Block (SpMM) form of the fused leapfrog step: NB start vectors advance together,
+// so each stored matrix entry streamed from HBM serves NB products (Sec. 4, block
+// version of the Krylov space; eq. 2stepmethod and eq. disc_filtercoeff per column).
+//
+// State, previous state, output and accumulators are row-major n_pad x NB: the NB
+// values of a row are contiguous (32 B for FP32 and NB = 8, one sector), so the
+// gather of x at a column index is one or a few 16-byte vector loads per lane.
+// A warp owns a 32-row SELL slice exactly as in the single-vector kernels; the
+// values and columns stream evict-first, and every column's sum is formed in the
+// same order as the single-vector kernel forms it.
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "kes_internal.h"
+
+namespace kes {
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T ld_cs(const T* p) { return __ldcs(p); }
+
+// NB contiguous values at p (16-byte aligned for NB * sizeof(T) >= 16) through the read-only path.
+template <int NB>
+__device__ __forceinline__ void load_row(const float* __restrict__ p, float (&v)[NB]) {
+  if constexpr (NB >= 4) {
+#pragma unroll
+    for (int q = 0; q < NB / 4; ++q) {
+      const float4 t = __ldg(reinterpret_cast<const float4*>(p) + q);
+      v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+    }
+  } else {
+    const float2 t = __ldg(reinterpret_cast<const float2*>(p));
+    v[0] = t.x; v[1] = t.y;
+  }
+}
+template <int NB>
+__device__ __forceinline__ void load_row(const double* __restrict__ p, double (&v)[NB]) {
+#pragma unroll
+  for (int q = 0; q < NB / 2; ++q) {
+    const double2 t = __ldg(reinterpret_cast<const double2*>(p) + q);
+    v[2 * q] = t.x; v[2 * q + 1] = t.y;
+  }
+}
+// plain (coherent) loads and stores of a row
+template <typename T, int NB>
+__device__ __forceinline__ void load_plain(const T* p, T (&v)[NB]) {
+#pragma unroll
+  for (int j = 0; j < NB; ++j) v[j] = p[j];
+}
+template <typename T, int NB>
+__device__ __forceinline__ void store_row(T* p, const T (&v)[NB]) {
+#pragma unroll
+  for (int j = 0; j < NB; ++j) p[j] = v[j];
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  const float ap = __fsub_rn(s, bp);
+  t = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+
+template <typename T, int NB, bool FIRST, bool LAST, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+    k_step_blk(SellDev A, const T* __restrict__ tau2m, const T* __restrict__ x, const T* prev, T* out, T* acc_s,
+               T* acc_c, double* acc64, int64_t acc_stride, int F, const T* __restrict__ ahi,
+               const T* __restrict__ alo, int Lp1, int step, int* flag) {
+  constexpr bool kF32 = std::is_same<T, float>::value;
+  const T* val;
+  if constexpr (kF32) val = A.val32;
+  else val = A.val64;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t s = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; s < A.n_slices;
+       s += nwarps) {
+    const int64_t beg = A.slice_ptr[s];
+    const int w = static_cast<int>((A.slice_ptr[s + 1] - beg) >> 5);
+    const int64_t mesh = A.slice_mesh ? A.slice_mesh[s] : 0;
+    const T* vp = val + beg + lane;
+    const int32_t* cp = A.col + beg + lane;
+    // even entries into sum0, odd into sum1 (the order of the single-vector kernels)
+    T sum0[NB], sum1[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) sum0[j] = sum1[j] = T(0);
+    int k = 0;
+    for (; k + 2 <= w; k += 2) {
+      const int32_t c0 = ld_cs(cp + k * kSliceC), c1 = ld_cs(cp + (k + 1) * kSliceC);
+      const T v0 = ld_cs(vp + k * kSliceC), v1 = ld_cs(vp + (k + 1) * kSliceC);
+      T x0[NB], x1[NB];
+      load_row<NB>(x + static_cast<int64_t>(c0) * NB, x0);
+      load_row<NB>(x + static_cast<int64_t>(c1) * NB, x1);
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        sum0[j] = fma(v0, x0[j], sum0[j]);
+        sum1[j] = fma(v1, x1[j], sum1[j]);
+      }
+    }
+    if (k < w) {
+      const int32_t c0 = ld_cs(cp + k * kSliceC);
+      const T v0 = ld_cs(vp + k * kSliceC);
+      T x0[NB];
+      load_row<NB>(x + static_cast<int64_t>(c0) * NB, x0);
+#pragma unroll
+      for (int j = 0; j < NB; ++j) sum0[j] = fma(v0, x0[j], sum0[j]);
+    }
+    const int64_t row = s * kSliceC + lane;
+    const T t2m = ld_cs(tau2m + row);
+    T xi[NB], pi[NB], un[NB];
+    load_plain<T, NB>(x + row * NB, xi);
+    if constexpr (FIRST) {
+#pragma unroll
+      for (int j = 0; j < NB; ++j) pi[j] = xi[j];
+    } else {
+      load_plain<T, NB>(prev + row * NB, pi);
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      if constexpr (kF32) un[j] = fmaf(-t2m, sum0[j] + sum1[j], __fsub_rn(__fmul_rn(2.0f, xi[j]), pi[j]));
+      else un[j] = fma(-t2m, sum0[j] + sum1[j], 2.0 * xi[j] - pi[j]);
+    }
+    if (!LAST) store_row<T, NB>(out + row * NB, un);
+    bool bad = false;
+    for (int f = 0; f < F; ++f) {
+      const int64_t ai = (mesh * F + f) * Lp1;
+      const int64_t at = f * acc_stride + row * NB;
+      if constexpr (kF32) {
+        const float a_hi = ahi[ai + step + 1], a_lo = alo[ai + step + 1];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+          const float p = __fmul_rn(a_hi, un[j]);
+          const float pe = fmaf(a_lo, un[j], fmaf(a_hi, un[j], -p));
+          float sn, e;
+          two_sum(acc_s[at + j], p, sn, e);
+          const float cn = __fadd_rn(acc_c[at + j], __fadd_rn(e, pe));
+          if (LAST) {
+            const double v = static_cast<double>(sn) + static_cast<double>(cn);
+            acc64[at + j] = v;
+            bad |= !isfinite(v);
+          } else {
+            acc_s[at + j] = sn;
+            acc_c[at + j] = cn;
+          }
+        }
+      } else {
+        const double a1 = ahi[ai + step + 1];
+        const double a0 = FIRST ? ahi[ai] : 0.0;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+          const double na = fma(a1, un[j], FIRST ? a0 * xi[j] : acc_s[at + j]);
+          acc_s[at + j] = na;
+          if (LAST) bad |= !isfinite(na);
+        }
+      }
+    }
+    if (LAST && bad) atomicOr(flag, 1);
+  }
+}
+
+// Launch shapes of the block kernels: minimum resident 256-thread blocks per SM.
+#define KES_BLK_VARIANTS(X) X(0, 1) X(1, 2) X(2, 3) X(3, 4)
+
+template <typename T, int NB, int MINB>
+void blk_impl(int grid, int block, cudaStream_t st, bool first, bool last, const SellDev& A, const T* tau2m,
+              const T* x, const T* prev, T* out, T* acc_s, T* acc_c, double* acc64, int64_t acc_stride, int F,
+              const T* ahi, const T* alo, int Lp1, int step, int* flag) {
+#define KES_BLK_ARGS A, tau2m, x, prev, out, acc_s, acc_c, acc64, acc_stride, F, ahi, alo, Lp1, step, flag
+  if (first && last) k_step_blk<T, NB, true, true, MINB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
+  else if (first) k_step_blk<T, NB, true, false, MINB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
+  else if (last) k_step_blk<T, NB, false, true, MINB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
+  else k_step_blk<T, NB, false, false, MINB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
+#undef KES_BLK_ARGS
+}
+
+template <typename T>
+void blk_dispatch(const LaunchCfg& cfg, int NB, cudaStream_t st, bool first, bool last, const SellDev& A,
+                  const T* tau2m, const T* x, const T* prev, T* out, T* acc_s, T* acc_c, double* acc64,
+                  int64_t acc_stride, int F, const T* ahi, const T* alo, int Lp1, int step, int* flag) {
+  const int64_t need = (A.n_slices + 7) / 8;
+  const int grid = static_cast<int>(need < cfg.grid_blk ? need : cfg.grid_blk);
+#define KES_CALL(NBV, M)                                                                                   \
+  blk_impl<T, NBV, M>(grid, 256, st, first, last, A, tau2m, x, prev, out, acc_s, acc_c, acc64, acc_stride, F, \
+                      ahi, alo, Lp1, step, flag)
+#define X(ID, M)                         \
+  case ID:                               \
+    if (NB == 2) KES_CALL(2, M);         \
+    else if (NB == 4) KES_CALL(4, M);    \
+    else KES_CALL(8, M);                 \
+    break;
+  switch (cfg.variant_blk) {
+    KES_BLK_VARIANTS(X)
+    default: break;
+  }
+#undef X
+#undef KES_CALL
+}
+
+template <typename T, int NB, int M>
+int occ_one(int block) {
+  int nb = 0;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_blk<T, NB, false, false, M>, block, 0) ==
+                 cudaSuccess
+             ? nb
+             : 0;
+}
+
+__global__ void k_gather_rows(const double* __restrict__ src, int64_t ld_src, int ncols,
+                              const int32_t* __restrict__ row_src, int64_t n_valid, double* __restrict__ dst,
+                              int NB, int64_t n_pad) {
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < n_pad * NB;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = t / NB;
+    const int j = static_cast<int>(t % NB);
+    const int64_t r = row_src ? row_src[i] : (i < n_valid ? i : -1);
+    dst[t] = (j < ncols && r >= 0) ? src[j * ld_src + r] : 0.0;
+  }
+}
+
+__global__ void k_scatter_rows(const double* __restrict__ src, int NB, int ncols,
+                               const int32_t* __restrict__ row_src, int64_t n_valid, double* __restrict__ dst,
+                               int64_t ld_dst, int64_t n_pad) {
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < n_pad * NB;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = t / NB;
+    const int j = static_cast<int>(t % NB);
+    const int64_t r = row_src ? row_src[i] : (i < n_valid ? i : -1);
+    if (j < ncols && r >= 0) dst[j * ld_dst + r] = src[t];
+  }
+}
+
+__global__ void k_pack_basis(const double* __restrict__ B, int64_t ldb, const int32_t* __restrict__ colsel,
+                             const int32_t* __restrict__ slice_mesh, double* __restrict__ stage, int NB,
+                             int64_t n_pad) {
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < n_pad * NB;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = t / NB;
+    const int j = static_cast<int>(t % NB);
+    const int mesh = slice_mesh ? slice_mesh[i / kSliceC] : 0;
+    const int c = colsel[mesh * NB + j];
+    stage[t] = c >= 0 ? B[c * ldb + i] : 0.0;
+  }
+}
+
+__global__ void k_unpack_block(const double* __restrict__ stage, int NB, double* __restrict__ Wc, int64_t n_pad) {
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < n_pad * NB;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = t / NB;
+    const int j = static_cast<int>(t % NB);
+    Wc[j * n_pad + i] = stage[t];
+  }
+}
+
+int elem_grid(int64_t count) {
+  const int64_t b = (count + 255) / 256;
+  return static_cast<int>(b < 4096 ? (b > 0 ? b : 1) : 4096);
+}
+
+}  // namespace
+
+int blk_variant_count() {
+  int n = 0;
+#define X(ID, M) ++n;
+  KES_BLK_VARIANTS(X)
+#undef X
+  return n;
+}
+
+int blk_blocks_per_sm(bool fp32, int NB, int variant, int block) {
+  int nb = 0;
+#define X(ID, M)                                                                                  \
+  case ID:                                                                                        \
+    if (fp32) nb = NB == 2 ? occ_one<float, 2, M>(block) : NB == 4 ? occ_one<float, 4, M>(block)   \
+                                                                   : occ_one<float, 8, M>(block);  \
+    else nb = NB == 2 ? occ_one<double, 2, M>(block) : NB == 4 ? occ_one<double, 4, M>(block)      \
+                                                               : occ_one<double, 8, M>(block);     \
+    break;
+  switch (variant) {
+    KES_BLK_VARIANTS(X)
+    default: break;
+  }
+#undef X
+  return nb > 0 ? nb : 1;
+}
+
+void launch_step_blk_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, int NB, bool first, bool last,
+                         const double* tau2m, const double* x, const double* prev, double* out, double* acc,
+                         int64_t acc_stride, int F, const double* alpha, int L, int step, int* flag) {
+  blk_dispatch<double>(cfg, NB, st, first, last, A, tau2m, x, prev, out, acc, nullptr, nullptr, acc_stride, F, alpha,
+                       nullptr, L + 1, step, flag);
+  ++g_launches;
+}
+
+void launch_step_blk_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, int NB, bool first, bool last,
+                         const float* tau2m, const float* x, const float* prev, float* out, float* acc_s,
+                         float* acc_c, double* acc64, int64_t acc_stride, int F, const float* alpha_hi,
+                         const float* alpha_lo, int L, int step, int* flag) {
+  blk_dispatch<float>(cfg, NB, st, first, last, A, tau2m, x, prev, out, acc_s, acc_c, acc64, acc_stride, F,
+                      alpha_hi, alpha_lo, L + 1, step, flag);
+  ++g_launches;
+}
+
+void launch_gather_rows(cudaStream_t st, const double* src, int64_t ld_src, int ncols, const int32_t* row_src,
+                        int64_t n_valid, double* dst, int NB, int64_t n_pad) {
+  k_gather_rows<<<elem_grid(n_pad * NB), 256, 0, st>>>(src, ld_src, ncols, row_src, n_valid, dst, NB, n_pad);
+  ++g_launches;
+}
+
+void launch_scatter_rows(cudaStream_t st, const double* src, int NB, int ncols, const int32_t* row_src,
+                         int64_t n_valid, double* dst, int64_t ld_dst, int64_t n_pad) {
+  k_scatter_rows<<<elem_grid(n_pad * NB), 256, 0, st>>>(src, NB, ncols, row_src, n_valid, dst, ld_dst, n_pad);
+  ++g_launches;
+}
+
+void launch_pack_basis(cudaStream_t st, const double* B, int64_t ldb, const int32_t* colsel,
+                       const int32_t* slice_mesh, double* stage, int NB, int64_t n_pad) {
+  k_pack_basis<<<elem_grid(n_pad * NB), 256, 0, st>>>(B, ldb, colsel, slice_mesh, stage, NB, n_pad);
+  ++g_launches;
+}
+
+void launch_unpack_block(cudaStream_t st, const double* stage, int NB, double* Wc, int64_t n_pad) {
+  k_unpack_block<<<elem_grid(n_pad * NB), 256, 0, st>>>(stage, NB, Wc, n_pad);
+  ++g_launches;
+}
+
+}  // namespace kes

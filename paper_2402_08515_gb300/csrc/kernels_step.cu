@@ -84,13 +84,14 @@ __global__ void __launch_bounds__(256, MINB) k_step_f64(SellDev A, const double*
     const int w = static_cast<int>((A.slice_ptr[s + 1] - beg) >> 5);
     const double sum = row_dot<double, BATCH>(A.val64 + beg + lane, A.col + beg + lane, w, x);
     const int64_t row = s * kSliceC + lane;
+    const int64_t mesh = A.slice_mesh ? A.slice_mesh[s] : 0;
     const double xi = x[row];
     const double pi = FIRST ? xi : prev[row];
     const double un = fma(-ld_stream(tau2m + row), sum, 2.0 * xi - pi);
     if (!LAST) out[row] = un;
     bool bad = false;
     for (int f = 0; f < F; ++f) {
-      const double* al = alpha + static_cast<int64_t>(f) * Lp1;
+      const double* al = alpha + (mesh * F + f) * Lp1;
       double* a = acc + f * acc_stride + row;
       const double prev_acc = FIRST ? al[0] * xi : *a;
       const double na = fma(al[step + 1], un, prev_acc);
@@ -124,13 +125,14 @@ __global__ void __launch_bounds__(256, MINB) k_step_f32(SellDev A, const float* 
     const int w = static_cast<int>((A.slice_ptr[s + 1] - beg) >> 5);
     const float sum = row_dot<float, BATCH>(A.val32 + beg + lane, A.col + beg + lane, w, x);
     const int64_t row = s * kSliceC + lane;
+    const int64_t mesh = A.slice_mesh ? A.slice_mesh[s] : 0;
     const float xi = x[row];
     const float pi = FIRST ? xi : prev[row];
     const float un = fmaf(-ld_stream(tau2m + row), sum, __fsub_rn(__fmul_rn(2.0f, xi), pi));
     if (!LAST) out[row] = un;
     bool bad = false;
     for (int f = 0; f < F; ++f) {
-      const int64_t ai = static_cast<int64_t>(f) * Lp1 + step + 1;
+      const int64_t ai = (mesh * F + f) * Lp1 + step + 1;
       const float a_hi = ahi[ai], a_lo = alo[ai];
       const int64_t at = f * acc_stride + row;
       // alpha * un = p + pe, p = fl(a_hi * un), pe = (a_hi * un - p) + a_lo * un
@@ -152,15 +154,18 @@ __global__ void __launch_bounds__(256, MINB) k_step_f32(SellDev A, const float* 
   }
 }
 
-__global__ void k_init_f32(int64_t n_pad, const double* __restrict__ r, float* __restrict__ x32,
+// FP32 start for nb columns (row-major, nb values per row): x32 = (float) r64 and the
+// compensated accumulator of weight table f set to alpha_f[0] r, split as s + c.
+__global__ void k_init_f32(int64_t count, int nb, const double* __restrict__ r, float* __restrict__ x32,
                            float* __restrict__ acc_s, float* __restrict__ acc_c, int64_t acc_stride, int F,
-                           const double* __restrict__ alpha, int Lp1) {
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n_pad;
+                           const double* __restrict__ alpha, int Lp1, const int32_t* __restrict__ slice_mesh) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < count;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const double ri = r[i];
+    const int64_t mesh = slice_mesh ? slice_mesh[(i / nb) / kSliceC] : 0;
     x32[i] = static_cast<float>(ri);
     for (int f = 0; f < F; ++f) {
-      const double t = alpha[static_cast<int64_t>(f) * Lp1] * ri;
+      const double t = alpha[(mesh * F + f) * Lp1] * ri;
       const float s = static_cast<float>(t);
       acc_s[f * acc_stride + i] = s;
       acc_c[f * acc_stride + i] = static_cast<float>(t - static_cast<double>(s));
@@ -292,11 +297,12 @@ void launch_step_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bo
   ++g_launches;
 }
 
-void launch_init_f32(cudaStream_t st, int64_t n_pad, const double* r64, float* x32, float* acc_s, float* acc_c,
-                     int64_t acc_stride, int F, const double* alpha64, int L) {
-  const int64_t blocks = (n_pad + 255) / 256;
-  k_init_f32<<<static_cast<int>(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(n_pad, r64, x32, acc_s, acc_c,
-                                                                               acc_stride, F, alpha64, L + 1);
+void launch_init_f32(cudaStream_t st, const SellDev& A, int nb, const double* r64, float* x32, float* acc_s,
+                     float* acc_c, int64_t acc_stride, int F, const double* alpha64, int L) {
+  const int64_t count = A.n_pad * nb;
+  const int64_t blocks = (count + 255) / 256;
+  k_init_f32<<<static_cast<int>(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(
+      count, nb, r64, x32, acc_s, acc_c, acc_stride, F, alpha64, L + 1, A.slice_mesh);
   ++g_launches;
 }
 

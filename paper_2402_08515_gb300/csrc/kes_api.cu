@@ -1,5 +1,12 @@
 // C ABI of the kes library: context, filter application and the Krylov
-// eigensolver (Nannen & Wess, arXiv:2402.08515, Sec. 2).
+// eigensolver (Nannen & Wess, arXiv:2402.08515, Sec. 2 and the block version of
+// Sec. 4).
+//
+// A context holds one or several meshes (independent pencils) stacked
+// block-diagonally: every mesh occupies a 32-row-aligned range of padded rows
+// and of SELL slices, so that one launch per time step advances all of them.
+// Each mesh keeps its own time step, weight tables, Krylov basis and
+// projected problem.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,13 +29,13 @@ struct KesError {
   kes_status status;
 };
 
-#define KES_CUDA(call)                                              \
-  do {                                                              \
-    cudaError_t e_ = (call);                                        \
-    if (e_ != cudaSuccess) {                                        \
-      throw KesError{e_ == cudaErrorMemoryAllocation ? KES_ERR_OOM  \
+#define KES_CUDA(call)                                                \
+  do {                                                                \
+    cudaError_t e_ = (call);                                          \
+    if (e_ != cudaSuccess) {                                          \
+      throw KesError{e_ == cudaErrorMemoryAllocation ? KES_ERR_OOM    \
                                                      : KES_ERR_CUDA}; \
-    }                                                               \
+    }                                                                 \
   } while (0)
 
 #define KES_CHECK_LAUNCH() KES_CUDA(cudaGetLastError())
@@ -46,6 +53,36 @@ kes_status guarded(F&& f) {
   }
 }
 
+struct MeshInfo {
+  int64_t n = 0;          // dofs of this mesh
+  int64_t n_pad = 0;      // its padded rows (multiple of 32)
+  int64_t row_off = 0;    // first padded row in the context
+  int64_t src_off = 0;    // first row in the caller's concatenated vectors
+  int64_t slice_off = 0;  // first SELL slice
+  int64_t n_slices = 0;
+  int64_t nnz = 0;
+  double gershgorin = 0;  // sqrt(max_i sum_j |s_ij| / m_i) >= omega_max
+  double omega_est = 0;   // last power-iteration estimate (0: none)
+  double tau = 0;
+  std::vector<double> wmin, wmax;
+};
+
+// Adds the kernels launched while it lives (this thread) to the context's counter.
+struct LaunchCount {
+  kes_stats* stats;
+  int64_t start;
+  explicit LaunchCount(kes_stats* s) : stats(s), start(g_launches) {}
+  ~LaunchCount() { stats->kernel_launches += g_launches - start; }
+};
+
+struct GraphEntry {
+  int NB = 0;
+  cudaGraphExec_t exec = nullptr;
+  int64_t nodes = 0;
+};
+
+int nb_for(int b) { return b <= 1 ? 1 : b <= 2 ? 2 : b <= 4 ? 4 : 8; }
+
 }  // namespace
 
 struct kes_ctx {
@@ -53,56 +90,56 @@ struct kes_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int device = 0;
-  int64_t n = 0, n_pad = 0, nnz = 0;
-  double gershgorin = 0.0;    // sqrt(max_i sum_j |s_ij| / m_i) >= omega_max(S, M)
-  double omega_est = 0.0;     // last power-iteration estimate (0: none)
+  std::vector<MeshInfo> meshes;
+  int64_t n = 0, n_pad = 0, nnz = 0, nnz_pad = 0;
   std::vector<std::pair<void*, size_t>> allocs;
   SellDev A;
   LaunchCfg cfg;
-  int64_t nnz_pad = 0;
-  int32_t* perm = nullptr;    // device; null = identity order
-  double* m64 = nullptr;      // lumped mass (n_pad, zero padded)
-  double* minv64 = nullptr;   // 1 / m (n_pad, zero padded)
-  double* tau2m64 = nullptr;  // tau^2 / m (FP64 form)
-  float* tau2m32 = nullptr;   // tau^2 / m (FP32 form)
+  int NBcap = 1;
+  int32_t* row_src = nullptr;     // padded row -> caller row (-1: padding); null: identity
+  int32_t* slice_mesh = nullptr;  // slice -> mesh (null: one mesh)
+  double* m64 = nullptr;          // lumped mass (n_pad, zero padded)
+  double* minv64 = nullptr;       // 1 / m
+  double* tau2m64 = nullptr;      // tau^2 / m with the tau of the row's mesh
+  float* tau2m32 = nullptr;
   // filter
   bool filter_set = false;
   int F = 0, L = 0;
-  double tau = 0.0;
-  std::vector<double> wmin, wmax, h_alpha;
-  double* alpha64 = nullptr;
+  double* alpha64 = nullptr;  // [n_mesh][F][L+1]
   float* alpha_hi = nullptr;
   float* alpha_lo = nullptr;
   size_t alpha_cap = 0;
-  // filter work
-  double* stage_in = nullptr;   // n_pad, permuted start vector of the trajectory
-  double* stage_out = nullptr;  // F x n_pad, filtered vectors (FP64)
+  // filter work (capacity NBcap columns)
+  double* stage_in = nullptr;   // n_pad x NB row-major: the start block of the trajectory
+  double* stage_out = nullptr;  // F x (n_pad x NB): filtered blocks (FP64)
   int stage_out_F = 0;
   double* U64[2] = {nullptr, nullptr};
   float* U32[3] = {nullptr, nullptr, nullptr};
   float* acc_s = nullptr;
   float* acc_c = nullptr;
-  double* tmp = nullptr;        // n_pad scratch for host transfers / permutation
+  double* tmp_user = nullptr;  // n x NBcap, caller layout
   int* d_flag = nullptr;
-  // graph of one filter application
-  cudaGraphExec_t gexec = nullptr;
+  std::vector<GraphEntry> graphs;
   int g_F = -1, g_L = -1;
-  int64_t g_nodes = 0;
   // Krylov workspace
   int kcap = 0;
-  double* B = nullptr;
+  double* B = nullptr;   // n_pad x kcap, column-major; mesh j uses rows row_off_j ..
   double* SB = nullptr;
-  double* Hd = nullptr;         // kcap x kcap col-major, column j holds b_i^T S b_j for i <= j
+  double* Hd = nullptr;  // n_mesh x kcap x kcap; column k of mesh j holds b_i^T S b_k, i <= k
   double* partial = nullptr;
-  double* scal = nullptr;       // device scalars
+  double* scal = nullptr;  // per mesh: 2 * kcap + kScal device scalars
   double* Yd = nullptr;
   double* thd = nullptr;
   double* Xd = nullptr;
   size_t Xd_cap = 0;
+  double* Wc = nullptr;       // n_pad x NBcap column-major (filtered block, unpacked)
+  int32_t* colsel = nullptr;  // n_mesh x 8
   // stats
   kes_stats stats{};
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_filter, ev_other;
   std::vector<cudaEvent_t> ev_pool;
+
+  int n_mesh() const { return static_cast<int>(meshes.size()); }
 
   void* dalloc(size_t bytes) {
     if (bytes == 0) bytes = 16;
@@ -131,7 +168,15 @@ struct kes_ctx {
       }
   }
   template <typename T>
-  T* dalloc_n(int64_t count) { return static_cast<T*>(dalloc(static_cast<size_t>(count) * sizeof(T))); }
+  T* dalloc_n(int64_t count) {
+    return static_cast<T*>(dalloc(static_cast<size_t>(count) * sizeof(T)));
+  }
+  template <typename T>
+  T* dzero_n(int64_t count) {
+    T* p = dalloc_n<T>(count);
+    KES_CUDA(cudaMemsetAsync(p, 0, static_cast<size_t>(count) * sizeof(T), stream));
+    return p;
+  }
 
   cudaEvent_t get_event() {
     if (!ev_pool.empty()) {
@@ -162,14 +207,21 @@ struct kes_ctx {
     KES_CUDA(cudaStreamSynchronize(stream));
     harvest_events();
   }
+  void drop_graphs() {
+    for (auto& g : graphs)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+    graphs.clear();
+  }
 };
 
 namespace {
 
+constexpr int kScal = 16;  // device scalars per mesh ahead of the Gram-Schmidt coefficients
+
 void release(kes_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
-  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->drop_graphs();
   c->harvest_events();
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   while (!c->allocs.empty()) c->dfree(c->allocs.back().first);
@@ -178,86 +230,93 @@ void release(kes_ctx* c) {
 }
 
 // --------------------------------------------------------------- transfers
-// Brings a length-n user vector (host or device, original order) into dst (n_pad, permuted order).
-void vec_in(kes_ctx* c, const double* src, int32_t mem, double* dst) {
-  double* target = c->perm ? c->tmp : dst;
-  if (mem == KES_MEM_HOST)
-    KES_CUDA(cudaMemcpyAsync(target, src, c->n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  else
-    KES_CUDA(cudaMemcpyAsync(target, src, c->n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-  if (c->perm) {
-    launch_permute(c->stream, c->tmp, dst, c->perm, c->n, true);
-    KES_CHECK_LAUNCH();
-  }
+// Caller block (n x nb column-major, host or device) -> row-major n_pad x NB block.
+void block_in(kes_ctx* c, const double* src, int nb, int32_t mem, int NB, double* dst) {
+  const size_t bytes = static_cast<size_t>(c->n) * nb * sizeof(double);
+  KES_CUDA(cudaMemcpyAsync(c->tmp_user, src, bytes,
+                           mem == KES_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
+  launch_gather_rows(c->stream, c->tmp_user, c->n, nb, c->row_src, c->n, dst, NB, c->n_pad);
+  KES_CHECK_LAUNCH();
 }
 
-// Copies src (n_pad, permuted order) out to a length-n user vector (host or device).
-void vec_out(kes_ctx* c, const double* src, double* dst, int32_t mem) {
-  const double* from = src;
-  if (c->perm) {
-    launch_permute(c->stream, src, c->tmp, c->perm, c->n, false);
-    KES_CHECK_LAUNCH();
-    from = c->tmp;
-  }
-  KES_CUDA(cudaMemcpyAsync(dst, from, c->n * sizeof(double),
+// Row-major n_pad x NB block (first nb columns) -> caller block (n x nb column-major).
+void block_out(kes_ctx* c, const double* src, int NB, int nb, double* dst, int32_t mem) {
+  launch_scatter_rows(c->stream, src, NB, nb, c->row_src, c->n, c->tmp_user, c->n, c->n_pad);
+  KES_CHECK_LAUNCH();
+  KES_CUDA(cudaMemcpyAsync(dst, c->tmp_user, static_cast<size_t>(c->n) * nb * sizeof(double),
                            mem == KES_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream));
 }
 
 // --------------------------------------------------------------- filter
-// Issues the L fused steps of one filter application on c->stream:
-// stage_in (one permuted vector) -> stage_out (F filtered vectors).
-int64_t issue_filter_steps(kes_ctx* c) {
+// Issues the L fused steps of one filter application of an NB-column block on the
+// context stream: stage_in -> stage_out (F filtered blocks).
+int64_t issue_filter_steps(kes_ctx* c, int NB) {
   const int64_t before = g_launches;
   const int L = c->L, F = c->F;
+  const int64_t stride = c->n_pad * NB;
   if (c->opts.precision == KES_PREC_FP64) {
     for (int s = 0; s < L; ++s) {
       const bool first = s == 0, last = s == L - 1;
       const double* x = s == 0 ? c->stage_in : c->U64[(s - 1) & 1];
       const double* prev = s <= 1 ? c->stage_in : c->U64[s & 1];
       double* out = c->U64[s & 1];
-      launch_step_f64(c->A, c->cfg, c->stream, first, c->tau2m64, x, prev, out, c->stage_out, c->n_pad, F,
-                      c->alpha64, L, s, last, c->d_flag);
+      if (NB == 1)
+        launch_step_f64(c->A, c->cfg, c->stream, first, c->tau2m64, x, prev, out, c->stage_out, stride, F, c->alpha64,
+                        L, s, last, c->d_flag);
+      else
+        launch_step_blk_f64(c->A, c->cfg, c->stream, NB, first, last, c->tau2m64, x, prev, out, c->stage_out, stride,
+                            F, c->alpha64, L, s, c->d_flag);
     }
   } else {
-    launch_init_f32(c->stream, c->n_pad, c->stage_in, c->U32[2], c->acc_s, c->acc_c, c->n_pad, F, c->alpha64, L);
+    launch_init_f32(c->stream, c->A, NB, c->stage_in, c->U32[2], c->acc_s, c->acc_c, stride, F, c->alpha64, L);
     for (int s = 0; s < L; ++s) {
       const bool first = s == 0, last = s == L - 1;
       const float* x = s == 0 ? c->U32[2] : c->U32[(s - 1) & 1];
       const float* prev = s <= 1 ? c->U32[2] : c->U32[s & 1];
       float* out = c->U32[s & 1];
-      launch_step_f32(c->A, c->cfg, c->stream, first, last, c->tau2m32, x, prev, out, c->acc_s, c->acc_c,
-                      c->stage_out, c->n_pad, F, c->alpha_hi, c->alpha_lo, L, s, c->d_flag);
+      if (NB == 1)
+        launch_step_f32(c->A, c->cfg, c->stream, first, last, c->tau2m32, x, prev, out, c->acc_s, c->acc_c,
+                        c->stage_out, stride, F, c->alpha_hi, c->alpha_lo, L, s, c->d_flag);
+      else
+        launch_step_blk_f32(c->A, c->cfg, c->stream, NB, first, last, c->tau2m32, x, prev, out, c->acc_s, c->acc_c,
+                            c->stage_out, stride, F, c->alpha_hi, c->alpha_lo, L, s, c->d_flag);
     }
   }
   return g_launches - before;
 }
 
-void run_filter(kes_ctx* c) {
+void run_filter(kes_ctx* c, int NB) {
   cudaEvent_t e0 = c->get_event(), e1 = c->get_event();
   KES_CUDA(cudaEventRecord(e0, c->stream));
   if (c->opts.use_graph) {
-    if (!c->gexec || c->g_F != c->F || c->g_L != c->L) {
-      if (c->gexec) {
-        cudaGraphExecDestroy(c->gexec);
-        c->gexec = nullptr;
-      }
+    if (c->g_F != c->F || c->g_L != c->L) {
+      c->drop_graphs();
+      c->g_F = c->F;
+      c->g_L = c->L;
+    }
+    GraphEntry* ge = nullptr;
+    for (auto& g : c->graphs)
+      if (g.NB == NB) ge = &g;
+    if (!ge) {
       cudaGraph_t graph;
       KES_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-      const int64_t nodes = issue_filter_steps(c);
+      const int64_t nodes = issue_filter_steps(c, NB);
       cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
       g_launches -= nodes;  // captured, not launched
       KES_CUDA(ce);
-      ce = cudaGraphInstantiate(&c->gexec, graph, 0);
+      GraphEntry g;
+      g.NB = NB;
+      g.nodes = nodes;
+      ce = cudaGraphInstantiate(&g.exec, graph, 0);
       cudaGraphDestroy(graph);
       KES_CUDA(ce);
-      c->g_F = c->F;
-      c->g_L = c->L;
-      c->g_nodes = nodes;
+      c->graphs.push_back(g);
+      ge = &c->graphs.back();
     }
-    KES_CUDA(cudaGraphLaunch(c->gexec, c->stream));
-    c->stats.kernel_launches += c->g_nodes;
+    KES_CUDA(cudaGraphLaunch(ge->exec, c->stream));
+    g_launches += ge->nodes;  // every node of the replayed graph is a kernel launch
   } else {
-    c->stats.kernel_launches += issue_filter_steps(c);
+    issue_filter_steps(c, NB);
     KES_CHECK_LAUNCH();
   }
   KES_CUDA(cudaEventRecord(e1, c->stream));
@@ -268,22 +327,17 @@ void run_filter(kes_ctx* c) {
 
 void ensure_stage_out(kes_ctx* c, int F) {
   if (c->stage_out_F >= F) return;
+  const int64_t cnt = static_cast<int64_t>(F) * c->n_pad * c->NBcap;
   c->dfree(c->stage_out);
-  c->stage_out = c->dalloc_n<double>(static_cast<int64_t>(F) * c->n_pad);
-  KES_CUDA(cudaMemsetAsync(c->stage_out, 0, static_cast<size_t>(F) * c->n_pad * sizeof(double), c->stream));
+  c->stage_out = c->dzero_n<double>(cnt);
   if (c->opts.precision == KES_PREC_FP32) {
     c->dfree(c->acc_s);
     c->dfree(c->acc_c);
-    c->acc_s = c->dalloc_n<float>(static_cast<int64_t>(F) * c->n_pad);
-    c->acc_c = c->dalloc_n<float>(static_cast<int64_t>(F) * c->n_pad);
-    KES_CUDA(cudaMemsetAsync(c->acc_s, 0, static_cast<size_t>(F) * c->n_pad * sizeof(float), c->stream));
-    KES_CUDA(cudaMemsetAsync(c->acc_c, 0, static_cast<size_t>(F) * c->n_pad * sizeof(float), c->stream));
+    c->acc_s = c->dzero_n<float>(cnt);
+    c->acc_c = c->dzero_n<float>(cnt);
   }
   c->stage_out_F = F;
-  if (c->gexec) {  // buffers moved: recapture
-    cudaGraphExecDestroy(c->gexec);
-    c->gexec = nullptr;
-  }
+  c->drop_graphs();  // buffers moved: recapture
 }
 
 kes_status check_flag(kes_ctx* c) {
@@ -301,64 +355,106 @@ kes_status check_flag(kes_ctx* c) {
 void ensure_krylov(kes_ctx* c, int kmax) {
   if (c->kcap >= kmax) return;
   for (double* p : {c->B, c->SB, c->Hd, c->partial, c->scal, c->Yd, c->thd}) c->dfree(p);
+  const int nm = c->n_mesh();
   c->kcap = kmax;
-  c->B = c->dalloc_n<double>(static_cast<int64_t>(kmax) * c->n_pad);
-  c->SB = c->dalloc_n<double>(static_cast<int64_t>(kmax) * c->n_pad);
-  c->Hd = c->dalloc_n<double>(static_cast<int64_t>(kmax) * kmax);
+  c->B = c->dzero_n<double>(static_cast<int64_t>(kmax) * c->n_pad);
+  c->SB = c->dzero_n<double>(static_cast<int64_t>(kmax) * c->n_pad);
+  c->Hd = c->dzero_n<double>(static_cast<int64_t>(nm) * kmax * kmax);
   c->partial = c->dalloc_n<double>(static_cast<int64_t>(kDotBlocks) * (2 * kmax + 8));
-  c->scal = c->dalloc_n<double>(2 * kmax + 16);
+  c->scal = c->dzero_n<double>(static_cast<int64_t>(nm) * (2 * kmax + kScal));
   c->Yd = c->dalloc_n<double>(static_cast<int64_t>(kmax) * kmax);
   c->thd = c->dalloc_n<double>(kmax);
-  KES_CUDA(cudaMemsetAsync(c->Hd, 0, sizeof(double) * kmax * kmax, c->stream));
 }
 
-// Times every launch shape of the step kernel on this matrix (a few steps on zeroed
+double* mesh_scal(kes_ctx* c, int j) { return c->scal + static_cast<int64_t>(j) * (2 * c->kcap + kScal); }
+
+// The slices of one mesh as a matrix of its own (columns stay global row indices).
+SellDev mesh_sell(const kes_ctx* c, const MeshInfo& m) {
+  SellDev a = c->A;
+  a.slice_ptr = c->A.slice_ptr + m.slice_off;
+  a.n_slices = m.n_slices;
+  a.n = m.n;
+  a.n_pad = m.n_pad;
+  a.slice_mesh = nullptr;
+  return a;
+}
+
+// Times every launch shape of the step kernels on this matrix (a few steps on zeroed
 // scratch state, CUDA events) and keeps the fastest. All shapes compute the same sums.
-void tune_step(kes_ctx* c) {
+void tune_steps(kes_ctx* c) {
   const bool fp32 = c->opts.precision == KES_PREC_FP32;
-  const int nv = step_variant_count();
   ensure_stage_out(c, 1);
-  double* a64 = c->dalloc_n<double>(8);
-  float* a32 = c->dalloc_n<float>(8);
-  KES_CUDA(cudaMemsetAsync(a64, 0, 8 * sizeof(double), c->stream));
-  KES_CUDA(cudaMemsetAsync(a32, 0, 8 * sizeof(float), c->stream));
+  const int64_t na = static_cast<int64_t>(c->n_mesh()) * 8;
+  double* a64 = c->dzero_n<double>(na);
+  float* a32 = c->dzero_n<float>(na);
   cudaEvent_t e0 = c->get_event(), e1 = c->get_event();
-  auto steps = [&](int count) {
-    for (int i = 0; i < count; ++i) {
-      if (fp32)
-        launch_step_f32(c->A, c->cfg, c->stream, false, false, c->tau2m32, c->U32[0], c->U32[1], c->U32[1],
-                        c->acc_s, c->acc_c, c->stage_out, c->n_pad, 1, a32, a32, 7, 1, c->d_flag);
-      else
-        launch_step_f64(c->A, c->cfg, c->stream, false, c->tau2m64, c->U64[0], c->U64[1], c->U64[1],
-                        c->stage_out, c->n_pad, 1, a64, 7, 1, false, c->d_flag);
-    }
-  };
-  int best = 0;
-  float best_ms = 3.0e38f;
-  for (int v = 0; v < nv; ++v) {
-    c->cfg.variant = v;
-    c->cfg.grid_step = c->cfg.n_sm * step_blocks_per_sm(fp32, v, c->cfg.block_step);
-    steps(2);
-    float ms_v = 3.0e38f;
+  auto timed = [&](auto&& launch) {
+    launch(2);
+    float best = 3.0e38f;
     for (int rep = 0; rep < 2; ++rep) {
       KES_CUDA(cudaEventRecord(e0, c->stream));
-      steps(6);
+      launch(6);
       KES_CUDA(cudaEventRecord(e1, c->stream));
       KES_CUDA(cudaEventSynchronize(e1));
       float ms = 0.f;
       KES_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-      ms_v = std::min(ms_v, ms);
+      best = std::min(best, ms);
     }
     KES_CHECK_LAUNCH();
-    if (ms_v < best_ms) {
-      best_ms = ms_v;
+    return best;
+  };
+  // single-vector kernel
+  int best = 0;
+  float best_ms = 3.0e38f;
+  for (int v = 0; v < step_variant_count(); ++v) {
+    c->cfg.variant = v;
+    c->cfg.grid_step = c->cfg.n_sm * step_blocks_per_sm(fp32, v, c->cfg.block_step);
+    const float ms = timed([&](int count) {
+      for (int i = 0; i < count; ++i) {
+        if (fp32)
+          launch_step_f32(c->A, c->cfg, c->stream, false, false, c->tau2m32, c->U32[0], c->U32[1], c->U32[1],
+                          c->acc_s, c->acc_c, c->stage_out, c->n_pad, 1, a32, a32, 7, 1, c->d_flag);
+        else
+          launch_step_f64(c->A, c->cfg, c->stream, false, c->tau2m64, c->U64[0], c->U64[1], c->U64[1], c->stage_out,
+                          c->n_pad, 1, a64, 7, 1, false, c->d_flag);
+      }
+    });
+    if (ms < best_ms) {
+      best_ms = ms;
       best = v;
     }
   }
-  c->ev_pool.push_back(e0);
-  c->ev_pool.push_back(e1);
   c->cfg.variant = best;
   c->cfg.grid_step = c->cfg.n_sm * step_blocks_per_sm(fp32, best, c->cfg.block_step);
+  // block kernel at the context's block width
+  if (c->NBcap > 1) {
+    const int NB = c->NBcap;
+    best = 0;
+    best_ms = 3.0e38f;
+    for (int v = 0; v < blk_variant_count(); ++v) {
+      c->cfg.variant_blk = v;
+      c->cfg.grid_blk = c->cfg.n_sm * blk_blocks_per_sm(fp32, NB, v, c->cfg.block_step);
+      const float ms = timed([&](int count) {
+        for (int i = 0; i < count; ++i) {
+          if (fp32)
+            launch_step_blk_f32(c->A, c->cfg, c->stream, NB, false, false, c->tau2m32, c->U32[0], c->U32[1],
+                                c->U32[1], c->acc_s, c->acc_c, c->stage_out, c->n_pad * NB, 1, a32, a32, 7, 1,
+                                c->d_flag);
+          else
+            launch_step_blk_f64(c->A, c->cfg, c->stream, NB, false, false, c->tau2m64, c->U64[0], c->U64[1],
+                                c->U64[1], c->stage_out, c->n_pad * NB, 1, a64, 7, 1, c->d_flag);
+        }
+      });
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = v;
+      }
+    }
+    c->cfg.variant_blk = best;
+    c->cfg.grid_blk = c->cfg.n_sm * blk_blocks_per_sm(fp32, NB, best, c->cfg.block_step);
+  }
+  c->ev_pool.push_back(e0);
+  c->ev_pool.push_back(e1);
   c->sync();
   c->dfree(a64);
   c->dfree(a32);
@@ -377,6 +473,568 @@ void validate_csr(int64_t n, const int64_t* row_ptr, const int32_t* col, const d
     }
     if (!(m[i] > 0.0) || !std::isfinite(m[i])) throw KesError{KES_ERR_MASS};
   }
+}
+
+// Builds the block-diagonal device matrix and the per-row vectors of all meshes.
+void build_context(kes_ctx* c, int nm, const int64_t* n, const int64_t* const* row_ptr, const int32_t* const* col,
+                   const double* const* val, const double* const* m_diag) {
+  std::vector<SellHost> sells(nm);
+  int64_t row_off = 0, src_off = 0, slice_off = 0, nnz_pad = 0;
+  for (int j = 0; j < nm; ++j) {  // inputs were validated by the caller
+    MeshInfo mi;
+    mi.n = n[j];
+    mi.nnz = row_ptr[j][n[j]];
+    double g = 0.0;
+    for (int64_t i = 0; i < n[j]; ++i) {
+      double s = 0.0;
+      for (int64_t p = row_ptr[j][i]; p < row_ptr[j][i + 1]; ++p) s += std::fabs(val[j][p]);
+      g = std::max(g, s / m_diag[j][i]);
+    }
+    mi.gershgorin = std::sqrt(g);
+    sells[j] = build_sell(n[j], row_ptr[j], col[j], val[j], c->opts.sell_sigma);
+    mi.n_slices = sells[j].n_slices;
+    mi.n_pad = sells[j].n_slices * kSliceC;
+    mi.row_off = row_off;
+    mi.src_off = src_off;
+    mi.slice_off = slice_off;
+    row_off += mi.n_pad;
+    src_off += mi.n;
+    slice_off += mi.n_slices;
+    nnz_pad += sells[j].nnz_pad;
+    c->nnz += mi.nnz;
+    c->meshes.push_back(mi);
+  }
+  c->n = src_off;
+  c->n_pad = row_off;
+  c->nnz_pad = nnz_pad;
+  if (c->n >= (int64_t(1) << 31) || c->n_pad >= (int64_t(1) << 31)) throw KesError{KES_ERR_ARG};
+  const int64_t n_slices = slice_off;
+  // concatenate the slices; columns shift by the mesh's row offset
+  std::vector<int64_t> sp(n_slices + 1);
+  std::vector<int32_t> cols(nnz_pad);
+  std::vector<double> vals(nnz_pad);
+  std::vector<int32_t> smesh(n_slices), rsrc(c->n_pad, -1);
+  std::vector<double> mp(c->n_pad, 0.0), minv(c->n_pad, 0.0);
+  bool identity = nm == 1;
+  int64_t at = 0;
+  for (int j = 0; j < nm; ++j) {
+    const MeshInfo& mi = c->meshes[j];
+    const SellHost& sh = sells[j];
+    for (int64_t s = 0; s < sh.n_slices; ++s) {
+      sp[mi.slice_off + s] = at + sh.slice_ptr[s];
+      smesh[mi.slice_off + s] = j;
+    }
+    for (int64_t e = 0; e < sh.nnz_pad; ++e) {
+      cols[at + e] = static_cast<int32_t>(sh.col[e] + mi.row_off);
+      vals[at + e] = sh.val[e];
+    }
+    at += sh.nnz_pad;
+    for (int64_t i = 0; i < mi.n; ++i) {
+      const int64_t o = sh.perm.empty() ? i : sh.perm[i];
+      rsrc[mi.row_off + i] = static_cast<int32_t>(mi.src_off + o);
+      if (mi.row_off + i != mi.src_off + o) identity = false;
+      mp[mi.row_off + i] = m_diag[j][o];
+      minv[mi.row_off + i] = 1.0 / m_diag[j][o];
+    }
+  }
+  sp[n_slices] = at;
+  sells.clear();
+  int64_t* d_sp = c->dalloc_n<int64_t>(n_slices + 1);
+  int32_t* d_col = c->dalloc_n<int32_t>(nnz_pad);
+  double* d_val = c->dalloc_n<double>(nnz_pad);
+  KES_CUDA(cudaMemcpyAsync(d_sp, sp.data(), (n_slices + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+  KES_CUDA(cudaMemcpyAsync(d_col, cols.data(), nnz_pad * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+  KES_CUDA(cudaMemcpyAsync(d_val, vals.data(), nnz_pad * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  c->A.n = c->n;
+  c->A.n_pad = c->n_pad;
+  c->A.n_slices = n_slices;
+  c->A.slice_ptr = d_sp;
+  c->A.col = d_col;
+  c->A.val64 = d_val;  // FP64 values are always kept: the Krylov basis needs S b_k in FP64
+  if (c->opts.precision == KES_PREC_FP32) {
+    std::vector<float> v32(vals.begin(), vals.end());
+    float* d32 = c->dalloc_n<float>(nnz_pad);
+    KES_CUDA(cudaMemcpyAsync(d32, v32.data(), nnz_pad * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    c->A.val32 = d32;
+    c->sync();
+  }
+  if (nm > 1) {
+    c->slice_mesh = c->dalloc_n<int32_t>(n_slices);
+    KES_CUDA(cudaMemcpyAsync(c->slice_mesh, smesh.data(), n_slices * sizeof(int32_t), cudaMemcpyHostToDevice,
+                             c->stream));
+    c->A.slice_mesh = c->slice_mesh;
+  }
+  if (!identity) {
+    c->row_src = c->dalloc_n<int32_t>(c->n_pad);
+    KES_CUDA(
+        cudaMemcpyAsync(c->row_src, rsrc.data(), c->n_pad * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+  }
+  c->m64 = c->dalloc_n<double>(c->n_pad);
+  c->minv64 = c->dalloc_n<double>(c->n_pad);
+  KES_CUDA(cudaMemcpyAsync(c->m64, mp.data(), c->n_pad * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  KES_CUDA(cudaMemcpyAsync(c->minv64, minv.data(), c->n_pad * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  c->sync();
+}
+
+kes_status create_impl(kes_ctx** out, int32_t nm, const int64_t* n, const int64_t* const* row_ptr,
+                       const int32_t* const* col, const double* const* val, const double* const* m_diag,
+                       const kes_opts* opts) {
+  if (!out) return KES_ERR_ARG;
+  *out = nullptr;
+  if (nm < 1 || !n || !row_ptr || !col || !val || !m_diag) return KES_ERR_ARG;
+  kes_ctx* c = nullptr;
+  kes_status st = guarded([&]() -> kes_status {
+    c = new kes_ctx();
+    if (opts) c->opts = *opts;
+    else kes_opts_default(&c->opts);
+    if (c->opts.precision != KES_PREC_FP64 && c->opts.precision != KES_PREC_FP32) throw KesError{KES_ERR_ARG};
+    if (c->opts.sell_sigma < 1) c->opts.sell_sigma = 1;
+    if (c->opts.block_b < 1) c->opts.block_b = 1;
+    if (c->opts.block_b > 8) throw KesError{KES_ERR_UNSUPPORTED};
+    if ((c->opts.dev_alloc == nullptr) != (c->opts.dev_free == nullptr)) throw KesError{KES_ERR_ARG};
+    if (c->opts.step_variant < 0 || c->opts.step_variant >= step_variant_count()) throw KesError{KES_ERR_ARG};
+    // host-side validation first: a bad input never reaches the GPU
+    for (int j = 0; j < nm; ++j) {
+      if (!row_ptr[j] || !col[j] || !val[j] || !m_diag[j]) throw KesError{KES_ERR_ARG};
+      validate_csr(n[j], row_ptr[j], col[j], val[j], m_diag[j]);
+    }
+    c->NBcap = nb_for(c->opts.block_b);
+    KES_CUDA(cudaGetDevice(&c->device));
+    int n_sm = 0;
+    KES_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, c->device));
+    if (c->opts.stream) {
+      c->stream = static_cast<cudaStream_t>(c->opts.stream);
+    } else {
+      KES_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+      c->own_stream = true;
+    }
+    build_context(c, nm, n, row_ptr, col, val, m_diag);
+    const int64_t np = c->n_pad, nb = c->NBcap;
+    c->tau2m64 = c->dzero_n<double>(np);
+    if (c->opts.precision == KES_PREC_FP32) {
+      c->tau2m32 = c->dzero_n<float>(np);
+      for (int j = 0; j < 3; ++j) c->U32[j] = c->dzero_n<float>(np * nb);
+    } else {
+      for (int j = 0; j < 2; ++j) c->U64[j] = c->dzero_n<double>(np * nb);
+    }
+    c->stage_in = c->dzero_n<double>(np * nb);
+    c->tmp_user = c->dzero_n<double>(c->n * nb);
+    c->Wc = c->dzero_n<double>(np * nb);
+    c->colsel = c->dalloc_n<int32_t>(static_cast<int64_t>(nm) * 8);
+    c->d_flag = c->dzero_n<int>(4);
+    // grid-stride launch shapes: one full wave of resident 256-thread blocks
+    const bool fp32 = c->opts.precision == KES_PREC_FP32;
+    c->cfg.n_sm = n_sm;
+    c->cfg.block_step = 256;
+    c->cfg.variant = c->opts.step_variant;
+    c->cfg.grid_step = n_sm * step_blocks_per_sm(fp32, c->cfg.variant, c->cfg.block_step);
+    c->cfg.variant_blk = 0;
+    c->cfg.grid_blk = n_sm * blk_blocks_per_sm(fp32, c->NBcap > 1 ? c->NBcap : 2, 0, c->cfg.block_step);
+    if (c->opts.autotune) tune_steps(c);
+    c->sync();
+    c->stats.bytes_per_step = kes_step_bytes(c, 1, 1);
+    c->stats.step_variant = c->cfg.variant;
+    c->stats.step_grid = c->cfg.grid_step;
+    return KES_OK;
+  });
+  if (st != KES_OK) {
+    release(c);
+    return st;
+  }
+  *out = c;
+  return KES_OK;
+}
+
+kes_status set_filters_impl(kes_ctx* c, int32_t F, const double* wmin, const double* wmax, const double* tau,
+                            int32_t L) {
+  const int nm = c->n_mesh();
+  for (int j = 0; j < nm; ++j) {
+    if (!(tau[j] > 0.0) || !std::isfinite(tau[j])) return KES_ERR_ARG;
+    for (int f = 0; f < F; ++f) {
+      const double a = wmin[j * F + f], b = wmax[j * F + f];
+      if (!(a >= 0.0) || !(b > a) || !std::isfinite(b)) return KES_ERR_ARG;
+    }
+    if (c->meshes[j].omega_est > 0.0 && tau[j] * c->meshes[j].omega_est >= 2.0) return KES_ERR_UNSTABLE;
+  }
+  return guarded([&]() -> kes_status {
+    const size_t need = static_cast<size_t>(nm) * F * (L + 1);
+    std::vector<double> a64(need, 0.0);
+    for (int j = 0; j < nm; ++j)
+      for (int f = 0; f < F; ++f)
+        alpha_table(wmin[j * F + f], wmax[j * F + f], tau[j], L,
+                    a64.data() + (static_cast<size_t>(j) * F + f) * (L + 1));
+    c->sync();
+    if (need > c->alpha_cap) {
+      c->dfree(c->alpha64);
+      c->dfree(c->alpha_hi);
+      c->dfree(c->alpha_lo);
+      c->alpha64 = c->dalloc_n<double>(need);
+      c->alpha_hi = c->dalloc_n<float>(need);
+      c->alpha_lo = c->dalloc_n<float>(need);
+      c->alpha_cap = need;
+      c->drop_graphs();
+    }
+    std::vector<float> hi(need), lo(need);
+    for (size_t i = 0; i < need; ++i) {
+      hi[i] = static_cast<float>(a64[i]);
+      lo[i] = static_cast<float>(a64[i] - static_cast<double>(hi[i]));
+    }
+    KES_CUDA(cudaMemcpyAsync(c->alpha64, a64.data(), need * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    KES_CUDA(cudaMemcpyAsync(c->alpha_hi, hi.data(), need * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    KES_CUDA(cudaMemcpyAsync(c->alpha_lo, lo.data(), need * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    // tau^2 / m with each mesh's tau, in the padded (permuted) order
+    std::vector<double> m(c->n_pad);
+    KES_CUDA(cudaMemcpyAsync(m.data(), c->m64, c->n_pad * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    c->sync();
+    std::vector<double> t2m(c->n_pad, 0.0);
+    for (int j = 0; j < nm; ++j) {
+      const MeshInfo& mi = c->meshes[j];
+      for (int64_t i = 0; i < mi.n; ++i) t2m[mi.row_off + i] = tau[j] * tau[j] / m[mi.row_off + i];
+    }
+    KES_CUDA(cudaMemcpyAsync(c->tau2m64, t2m.data(), c->n_pad * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (c->tau2m32) {
+      std::vector<float> t32(t2m.begin(), t2m.end());
+      KES_CUDA(cudaMemcpyAsync(c->tau2m32, t32.data(), c->n_pad * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+      c->sync();
+    }
+    ensure_stage_out(c, F);
+    c->sync();
+    c->F = F;
+    c->L = L;
+    for (int j = 0; j < nm; ++j) {
+      c->meshes[j].tau = tau[j];
+      c->meshes[j].wmin.assign(wmin + j * F, wmin + (j + 1) * F);
+      c->meshes[j].wmax.assign(wmax + j * F, wmax + (j + 1) * F);
+    }
+    c->filter_set = true;
+    return KES_OK;
+  });
+}
+
+kes_status omega_impl(kes_ctx* c, int32_t iters, const double* v0, double* omega, double* gersh) {
+  LaunchCount lc(&c->stats);
+  return guarded([&]() -> kes_status {
+    const int nm = c->n_mesh();
+    ensure_krylov(c, 2);
+    double* v = c->B;  // scratch n_pad vectors
+    double* w = c->SB;
+    cudaStream_t s = c->stream;
+    block_in(c, v0, 1, KES_MEM_HOST, 1, w);
+    for (int j = 0; j < nm; ++j) {
+      const MeshInfo& mi = c->meshes[j];
+      double* sc = mesh_scal(c, j);
+      launch_mdot(s, w + mi.row_off, 0, 1, w + mi.row_off, nullptr, mi.n_pad, c->partial, sc);
+      launch_scale_rsqrt(s, w + mi.row_off, sc, v + mi.row_off, nullptr, mi.n_pad);
+    }
+    for (int it = 0; it < iters; ++it) {
+      launch_spmv_f64(c->A, c->cfg, s, v, c->minv64, w);
+      for (int j = 0; j < nm; ++j) {
+        const MeshInfo& mi = c->meshes[j];
+        double* sc = mesh_scal(c, j);
+        launch_mdot(s, w + mi.row_off, 0, 1, w + mi.row_off, nullptr, mi.n_pad, c->partial, sc);
+        launch_scale_rsqrt(s, w + mi.row_off, sc, v + mi.row_off, nullptr, mi.n_pad);
+      }
+    }
+    launch_spmv_f64(c->A, c->cfg, s, v, nullptr, w);
+    std::vector<double> h(2 * nm);
+    for (int j = 0; j < nm; ++j) {
+      const MeshInfo& mi = c->meshes[j];
+      double* sc = mesh_scal(c, j);
+      launch_mdot(s, v + mi.row_off, 0, 1, w + mi.row_off, nullptr, mi.n_pad, c->partial, sc);  // v^T S v
+      launch_mdot(s, v + mi.row_off, 0, 1, v + mi.row_off, c->m64 + mi.row_off, mi.n_pad, c->partial,
+                  sc + 1);  // v^T M v
+      KES_CUDA(cudaMemcpyAsync(&h[2 * j], sc, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    KES_CHECK_LAUNCH();
+    c->sync();
+    for (int j = 0; j < nm; ++j) {
+      omega[j] = std::sqrt(std::max(h[2 * j], 0.0) / h[2 * j + 1]);
+      c->meshes[j].omega_est = omega[j];
+      if (gersh) gersh[j] = c->meshes[j].gershgorin;
+    }
+    return KES_OK;
+  });
+}
+
+// ------------------------------------------------------------------ block Krylov solver
+struct MeshSolve {
+  int k = 0;            // basis vectors
+  bool done = false;    // no further blocks for this mesh
+  bool breakdown = false;
+  int kproj = -1;       // basis size at the last projection
+  std::vector<double> last_theta, last_rel;
+  std::vector<double> acc_theta, acc_rel, acc_abs, acc_Y;
+};
+
+double* hdup(const std::vector<double>& v) {
+  double* d = static_cast<double*>(std::malloc(std::max<size_t>(1, v.size()) * sizeof(double)));
+  if (!d) throw std::bad_alloc();
+  if (!v.empty()) std::memcpy(d, v.data(), v.size() * sizeof(double));
+  return d;
+}
+
+kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, const kes_solve_opts& so,
+                            kes_result** out) {
+  const int nm = c->n_mesh();
+  const int kmax = so.kmax;
+  const int NB = nb_for(b);
+  std::vector<MeshSolve> ms(nm);
+  std::vector<kes_result*> res(nm, nullptr);
+  for (int j = 0; j < nm; ++j) {
+    res[j] = static_cast<kes_result*>(std::calloc(1, sizeof(kes_result)));
+    if (!res[j]) {
+      for (auto* r : res) kes_result_free(r);
+      return KES_ERR_OOM;
+    }
+  }
+  const auto t_start = std::chrono::steady_clock::now();
+  LaunchCount lc(&c->stats);
+  kes_status st = guarded([&]() -> kes_status {
+    ensure_krylov(c, kmax);
+    const int64_t np = c->n_pad;
+    cudaStream_t s = c->stream;
+    double* B = c->B;
+    double* SB = c->SB;
+    auto other_begin = [&]() {
+      cudaEvent_t e0 = c->get_event();
+      KES_CUDA(cudaEventRecord(e0, s));
+      return e0;
+    };
+    auto other_end = [&](cudaEvent_t e0) {
+      cudaEvent_t e1 = c->get_event();
+      KES_CUDA(cudaEventRecord(e1, s));
+      c->ev_other.emplace_back(e0, e1);
+    };
+    auto Hcol = [&](int j, int k) { return c->Hd + (static_cast<int64_t>(j) * c->kcap + k) * c->kcap; };
+
+    // Orthogonalise column jj of Wc against each mesh's basis (two classical passes in
+    // the M-inner product) and append the vectors that are not dependent (Algorithm 2.5).
+    auto append_column = [&](int jj) {
+      cudaEvent_t ev = other_begin();
+      std::vector<char> active(nm, 0);
+      for (int j = 0; j < nm; ++j) {
+        if (ms[j].done || ms[j].k >= kmax) continue;
+        active[j] = 1;
+        const MeshInfo& mi = c->meshes[j];
+        double* w = c->Wc + static_cast<int64_t>(jj) * np + mi.row_off;
+        const double* Bj = B + mi.row_off;
+        const double* mj = c->m64 + mi.row_off;
+        double* sc = mesh_scal(c, j);
+        launch_mdot(s, w, 0, 1, w, mj, mi.n_pad, c->partial, sc);  // ||w||_M^2 before
+        for (int pass = 0; pass < 2 && ms[j].k > 0; ++pass) {
+          launch_mdot(s, Bj, np, ms[j].k, w, mj, mi.n_pad, c->partial, sc + kScal);  // h = B^T M w
+          launch_gemv_sub(s, w, Bj, np, ms[j].k, sc + kScal, mi.n_pad);             // w -= B h
+        }
+        launch_mdot(s, w, 0, 1, w, mj, mi.n_pad, c->partial, sc + 1);  // ||w||_M^2 after
+      }
+      KES_CHECK_LAUNCH();
+      std::vector<double> nrm(2 * nm, 0.0);
+      for (int j = 0; j < nm; ++j)
+        if (active[j])
+          KES_CUDA(cudaMemcpyAsync(&nrm[2 * j], mesh_scal(c, j), 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      int flag = 0;
+      KES_CUDA(cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+      other_end(ev);
+      c->sync();
+      if (flag) {
+        KES_CUDA(cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
+        throw KesError{KES_ERR_UNSTABLE};
+      }
+      ev = other_begin();
+      std::vector<char> added(nm, 0);
+      for (int j = 0; j < nm; ++j) {
+        if (!active[j]) continue;
+        if (!(std::sqrt(nrm[2 * j + 1]) > 1e-10 * std::sqrt(nrm[2 * j]))) continue;  // dependent vector
+        const MeshInfo& mi = c->meshes[j];
+        const int k = ms[j].k;
+        double* w = c->Wc + static_cast<int64_t>(jj) * np + mi.row_off;
+        double* bk = B + static_cast<int64_t>(k) * np + mi.row_off;
+        double* sbk = SB + static_cast<int64_t>(k) * np + mi.row_off;
+        launch_scale_rsqrt(s, w, mesh_scal(c, j) + 1, bk, nullptr, mi.n_pad);  // b_k
+        launch_spmv_f64(mesh_sell(c, mi), c->cfg, s, B + static_cast<int64_t>(k) * np, nullptr, sbk);  // S b_k
+        launch_mdot(s, B + mi.row_off, np, k + 1, sbk, nullptr, mi.n_pad, c->partial, Hcol(j, k));
+        ms[j].k = k + 1;
+        added[j] = 1;
+      }
+      KES_CHECK_LAUNCH();
+      other_end(ev);
+      return added;
+    };
+
+    auto project = [&](int j) {
+      MeshSolve& m = ms[j];
+      const MeshInfo& mi = c->meshes[j];
+      const int kk = m.k;
+      m.kproj = kk;
+      std::vector<double> Hh(static_cast<size_t>(kk) * kk, 0.0);
+      KES_CUDA(cudaMemcpy2DAsync(Hh.data(), kk * sizeof(double), Hcol(j, 0), c->kcap * sizeof(double),
+                                 kk * sizeof(double), kk, cudaMemcpyDeviceToHost, s));
+      c->sync();
+      // column i holds rows 0..i (upper triangle); mirror it into the lower triangle
+      for (int i = 0; i < kk; ++i)
+        for (int r = i + 1; r < kk; ++r) Hh[static_cast<size_t>(i) * kk + r] = Hh[static_cast<size_t>(r) * kk + i];
+      std::vector<double> theta(kk), Y(static_cast<size_t>(kk) * kk);
+      if (!sym_eig(kk, Hh.data(), theta.data(), Y.data())) throw KesError{KES_ERR_CUDA};
+      for (double& t : theta) t = std::max(t, 0.0);
+      const double wmin = mi.wmin[0], wmax = mi.wmax[0];
+      std::vector<int> inside;
+      for (int q = 0; q < kk; ++q) {
+        const double om = std::sqrt(theta[q]);
+        if (om >= wmin && om <= wmax) inside.push_back(q);
+      }
+      const int p = static_cast<int>(inside.size());
+      m.last_theta = theta;
+      m.last_rel.assign(kk, std::numeric_limits<double>::quiet_NaN());
+      m.acc_theta.clear();
+      m.acc_rel.clear();
+      m.acc_abs.clear();
+      m.acc_Y.clear();
+      if (p == 0) return;
+      std::vector<double> Ysel(static_cast<size_t>(kk) * p), thsel(p);
+      for (int q = 0; q < p; ++q) {
+        thsel[q] = theta[inside[q]];
+        std::memcpy(&Ysel[static_cast<size_t>(q) * kk], &Y[static_cast<size_t>(inside[q]) * kk], kk * sizeof(double));
+      }
+      cudaEvent_t ev = other_begin();
+      double* sc = mesh_scal(c, j);
+      KES_CUDA(cudaMemcpyAsync(c->Yd, Ysel.data(), Ysel.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+      KES_CUDA(cudaMemcpyAsync(c->thd, thsel.data(), p * sizeof(double), cudaMemcpyHostToDevice, s));
+      launch_ritz_residual(s, B + mi.row_off, SB + mi.row_off, np, kk, c->Yd, c->thd, p, c->m64 + mi.row_off,
+                           mi.n_pad, c->partial, sc + kScal);
+      KES_CHECK_LAUNCH();
+      std::vector<double> rr(2 * p);
+      KES_CUDA(cudaMemcpyAsync(rr.data(), sc + kScal, 2 * p * sizeof(double), cudaMemcpyDeviceToHost, s));
+      other_end(ev);
+      c->sync();
+      for (int q = 0; q < p; ++q) {
+        const double a = std::sqrt(std::max(rr[q], 0.0));
+        const double den = thsel[q] * std::sqrt(std::max(rr[p + q], 0.0));
+        const double rel = den > 0.0 ? a / den : std::numeric_limits<double>::infinity();
+        m.last_rel[inside[q]] = rel;
+        if (rel <= so.tol) {
+          m.acc_theta.push_back(thsel[q]);
+          m.acc_rel.push_back(rel);
+          m.acc_abs.push_back(a);
+          m.acc_Y.insert(m.acc_Y.end(), Ysel.begin() + static_cast<size_t>(q) * kk,
+                         Ysel.begin() + static_cast<size_t>(q + 1) * kk);
+        }
+      }
+    };
+
+    // start block: the b start vectors, M-orthonormalised in order
+    {
+      cudaEvent_t ev = other_begin();
+      block_in(c, R0, b, mem, NB, c->stage_in);
+      launch_unpack_block(s, c->stage_in, NB, c->Wc, np);
+      KES_CHECK_LAUNCH();
+      other_end(ev);
+      for (int jj = 0; jj < b; ++jj) append_column(jj);
+      for (int j = 0; j < nm; ++j)
+        if (ms[j].k == 0) ms[j].done = ms[j].breakdown = true;
+    }
+    int64_t steps = 0;
+    std::vector<int> next_check(nm, so.check_every);
+    std::vector<int32_t> colsel(static_cast<size_t>(nm) * NB, -1);
+    for (;;) {
+      bool any = false;
+      std::fill(colsel.begin(), colsel.end(), -1);
+      for (int j = 0; j < nm; ++j) {
+        MeshSolve& m = ms[j];
+        if (m.done || m.k >= kmax) continue;
+        any = true;
+        // filter the b newest basis vectors (Algorithm 2.5 filters the newest one)
+        for (int jj = 0; jj < b; ++jj) {
+          const int col = m.k - b + jj;
+          colsel[j * NB + jj] = col >= 0 ? col : -1;
+        }
+      }
+      if (!any) break;
+      KES_CUDA(cudaMemcpyAsync(c->colsel, colsel.data(), colsel.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      launch_pack_basis(s, B, np, c->colsel, c->slice_mesh, c->stage_in, NB, np);
+      KES_CHECK_LAUNCH();
+      run_filter(c, NB);  // stage_in -> stage_out
+      steps += c->L;
+      launch_unpack_block(s, c->stage_out, NB, c->Wc, np);
+      KES_CHECK_LAUNCH();
+      std::vector<int> added(nm, 0);
+      for (int jj = 0; jj < b; ++jj) {
+        std::vector<char> a = append_column(jj);
+        for (int j = 0; j < nm; ++j) added[j] += a[j];
+      }
+      for (int j = 0; j < nm; ++j) {
+        MeshSolve& m = ms[j];
+        if (m.done) continue;
+        if (added[j] == 0 && m.k < kmax) {  // the whole block was dependent: invariant subspace
+          m.done = m.breakdown = true;
+          continue;
+        }
+        if (m.k >= next_check[j] && m.k < kmax) {
+          while (next_check[j] <= m.k) next_check[j] += so.check_every;
+          project(j);
+          if (so.n_wanted > 0 && static_cast<int>(m.acc_theta.size()) >= so.n_wanted) m.done = true;
+        }
+      }
+    }
+    // final projection and results
+    bool any_breakdown = false;
+    for (int j = 0; j < nm; ++j) {
+      MeshSolve& m = ms[j];
+      const MeshInfo& mi = c->meshes[j];
+      if (m.kproj != m.k) project(j);
+      any_breakdown |= m.breakdown;
+      kes_result* r = res[j];
+      const int p = static_cast<int>(m.acc_theta.size());
+      r->n = mi.n;
+      r->n_pairs = p;
+      r->k_used = m.k;
+      r->breakdown = m.breakdown ? 1 : 0;
+      r->n_ritz = static_cast<int32_t>(m.last_theta.size());
+      r->time_steps = steps;
+      r->omega2 = hdup(m.acc_theta);
+      std::vector<double> om(p);
+      for (int q = 0; q < p; ++q) om[q] = std::sqrt(m.acc_theta[q]);
+      r->omega = hdup(om);
+      r->rel_res = hdup(m.acc_rel);
+      r->abs_res = hdup(m.acc_abs);
+      r->ritz_omega2 = hdup(m.last_theta);
+      r->ritz_rel_res = hdup(m.last_rel);
+      if (so.want_vectors && p > 0) {
+        const size_t need = static_cast<size_t>(p) * np;
+        if (need > c->Xd_cap) {
+          c->dfree(c->Xd);
+          c->Xd = c->dalloc_n<double>(need);
+          c->Xd_cap = need;
+        }
+        KES_CUDA(cudaMemsetAsync(c->Xd, 0, need * sizeof(double), s));
+        KES_CUDA(cudaMemcpyAsync(c->Yd, m.acc_Y.data(), m.acc_Y.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        launch_gemm_bx(s, B + mi.row_off, np, m.k, c->Yd, p, c->Xd + mi.row_off, np, mi.n_pad);
+        KES_CHECK_LAUNCH();
+        r->vectors = static_cast<double*>(std::malloc(static_cast<size_t>(p) * mi.n * sizeof(double)));
+        if (!r->vectors) throw std::bad_alloc();
+        // scatter each Ritz vector to the caller's order and keep this mesh's rows
+        for (int q = 0; q < p; ++q) {
+          launch_scatter_rows(s, c->Xd + static_cast<int64_t>(q) * np, 1, 1, c->row_src, c->n, c->tmp_user, c->n,
+                              np);
+          KES_CHECK_LAUNCH();
+          KES_CUDA(cudaMemcpyAsync(r->vectors + static_cast<size_t>(q) * mi.n, c->tmp_user + mi.src_off,
+                                   mi.n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        }
+        c->sync();
+      }
+    }
+    c->sync();
+    return any_breakdown ? KES_INFO_INVARIANT_SUBSPACE : KES_OK;
+  });
+  const double ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  if (st != KES_OK && st != KES_INFO_INVARIANT_SUBSPACE) {
+    for (auto* r : res) kes_result_free(r);
+    return st;
+  }
+  for (int j = 0; j < nm; ++j) {
+    res[j]->solve_ms = ms_total;
+    out[j] = res[j];
+  }
+  return st;
 }
 
 }  // namespace
@@ -424,122 +1082,20 @@ const char* kes_strerror(int32_t s) {
 
 kes_status kes_create(kes_ctx** out, int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
                       const double* m_diag, const kes_opts* opts) {
-  if (!out) return KES_ERR_ARG;
-  *out = nullptr;
-  kes_ctx* c = nullptr;
-  kes_status st = guarded([&]() -> kes_status {
-    validate_csr(n, row_ptr, col, val, m_diag);
-    c = new kes_ctx();
-    if (opts) c->opts = *opts;
-    else kes_opts_default(&c->opts);
-    if (c->opts.precision != KES_PREC_FP64 && c->opts.precision != KES_PREC_FP32) throw KesError{KES_ERR_ARG};
-    if (c->opts.sell_sigma < 1) c->opts.sell_sigma = 1;
-    if (c->opts.block_b < 1) c->opts.block_b = 1;
-    if ((c->opts.dev_alloc == nullptr) != (c->opts.dev_free == nullptr)) throw KesError{KES_ERR_ARG};
-    KES_CUDA(cudaGetDevice(&c->device));
-    int n_sm = 0;
-    KES_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, c->device));
-    if (c->opts.stream) {
-      c->stream = static_cast<cudaStream_t>(c->opts.stream);
-    } else {
-      KES_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
-      c->own_stream = true;
-    }
-    c->n = n;
-    c->nnz = row_ptr[n];
-    // Gershgorin bound of M^{-1} S
-    double g = 0.0;
-    for (int64_t i = 0; i < n; ++i) {
-      double s = 0.0;
-      for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) s += std::fabs(val[p]);
-      g = std::max(g, s / m_diag[i]);
-    }
-    c->gershgorin = std::sqrt(g);
+  return create_impl(out, 1, &n, &row_ptr, &col, &val, &m_diag, opts);
+}
 
-    SellHost sh = build_sell(n, row_ptr, col, val, c->opts.sell_sigma);
-    c->n_pad = sh.n_slices * kSliceC;
-    c->nnz_pad = sh.nnz_pad;
-    int64_t* sp = c->dalloc_n<int64_t>(sh.n_slices + 1);
-    int32_t* dc = c->dalloc_n<int32_t>(sh.nnz_pad);
-    KES_CUDA(cudaMemcpyAsync(sp, sh.slice_ptr.data(), (sh.n_slices + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
-                             c->stream));
-    KES_CUDA(cudaMemcpyAsync(dc, sh.col.data(), sh.nnz_pad * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
-    c->A.n = n;
-    c->A.n_pad = c->n_pad;
-    c->A.n_slices = sh.n_slices;
-    c->A.slice_ptr = sp;
-    c->A.col = dc;
-    // FP64 values are always kept: the Krylov basis needs S b_k in FP64
-    double* dv = c->dalloc_n<double>(sh.nnz_pad);
-    KES_CUDA(cudaMemcpyAsync(dv, sh.val.data(), sh.nnz_pad * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    c->A.val64 = dv;
-    if (c->opts.precision == KES_PREC_FP32) {
-      std::vector<float> v32(sh.val.begin(), sh.val.end());
-      float* dv32 = c->dalloc_n<float>(sh.nnz_pad);
-      KES_CUDA(cudaMemcpyAsync(dv32, v32.data(), sh.nnz_pad * sizeof(float), cudaMemcpyHostToDevice, c->stream));
-      c->A.val32 = dv32;
-      c->sync();  // v32 goes out of scope
-    }
-    if (!sh.perm.empty()) {
-      c->perm = c->dalloc_n<int32_t>(n);
-      KES_CUDA(cudaMemcpyAsync(c->perm, sh.perm.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
-    }
-    // per-row vectors in permuted order, zero padded
-    std::vector<double> mp(c->n_pad, 0.0), minv(c->n_pad, 0.0);
-    for (int64_t i = 0; i < n; ++i) {
-      const int64_t o = sh.perm.empty() ? i : sh.perm[i];
-      mp[i] = m_diag[o];
-      minv[i] = 1.0 / m_diag[o];
-    }
-    c->m64 = c->dalloc_n<double>(c->n_pad);
-    c->minv64 = c->dalloc_n<double>(c->n_pad);
-    KES_CUDA(cudaMemcpyAsync(c->m64, mp.data(), c->n_pad * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    KES_CUDA(cudaMemcpyAsync(c->minv64, minv.data(), c->n_pad * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    c->tau2m64 = c->dalloc_n<double>(c->n_pad);
-    KES_CUDA(cudaMemsetAsync(c->tau2m64, 0, c->n_pad * sizeof(double), c->stream));
-    if (c->opts.precision == KES_PREC_FP32) {
-      c->tau2m32 = c->dalloc_n<float>(c->n_pad);
-      for (int j = 0; j < 3; ++j) {
-        c->U32[j] = c->dalloc_n<float>(c->n_pad);
-        KES_CUDA(cudaMemsetAsync(c->U32[j], 0, c->n_pad * sizeof(float), c->stream));
-      }
-    } else {
-      for (int j = 0; j < 2; ++j) {
-        c->U64[j] = c->dalloc_n<double>(c->n_pad);
-        KES_CUDA(cudaMemsetAsync(c->U64[j], 0, c->n_pad * sizeof(double), c->stream));
-      }
-    }
-    c->stage_in = c->dalloc_n<double>(c->n_pad);
-    c->tmp = c->dalloc_n<double>(c->n_pad);
-    KES_CUDA(cudaMemsetAsync(c->stage_in, 0, c->n_pad * sizeof(double), c->stream));
-    c->d_flag = c->dalloc_n<int>(4);
-    KES_CUDA(cudaMemsetAsync(c->d_flag, 0, 4 * sizeof(int), c->stream));
-    if (c->tau2m32) KES_CUDA(cudaMemsetAsync(c->tau2m32, 0, c->n_pad * sizeof(float), c->stream));
-    // grid-stride launch shape: one full wave of resident 256-thread blocks
-    c->cfg.n_sm = n_sm;
-    c->cfg.block_step = 256;
-    if (c->opts.step_variant < 0 || c->opts.step_variant >= step_variant_count()) throw KesError{KES_ERR_ARG};
-    c->cfg.variant = c->opts.step_variant;
-    c->cfg.grid_step =
-        n_sm * step_blocks_per_sm(c->opts.precision == KES_PREC_FP32, c->cfg.variant, c->cfg.block_step);
-    if (c->opts.autotune) tune_step(c);
-    c->sync();
-    c->stats.bytes_per_step = kes_step_bytes(c, 1, 1);
-    c->stats.step_variant = c->cfg.variant;
-    c->stats.step_grid = c->cfg.grid_step;
-    return KES_OK;
-  });
-  if (st != KES_OK) {
-    release(c);
-    return st;
-  }
-  *out = c;
-  return KES_OK;
+kes_status kes_create_batch(kes_ctx** out, int32_t n_mesh, const int64_t* n, const int64_t* const* row_ptr,
+                            const int32_t* const* col, const double* const* val, const double* const* m_diag,
+                            const kes_opts* opts) {
+  return create_impl(out, n_mesh, n, row_ptr, col, val, m_diag, opts);
 }
 
 void kes_destroy(kes_ctx* ctx) { release(ctx); }
 
 int64_t kes_size(const kes_ctx* ctx) { return ctx ? ctx->n : -1; }
+
+int32_t kes_mesh_count(const kes_ctx* ctx) { return ctx ? ctx->n_mesh() : -1; }
 
 kes_status kes_sync(kes_ctx* ctx) {
   if (!ctx) return KES_ERR_ARG;
@@ -548,8 +1104,8 @@ kes_status kes_sync(kes_ctx* ctx) {
 
 int64_t kes_step_bytes(const kes_ctx* c, int32_t b, int32_t F) {
   if (!c || b < 1 || F < 1) return -1;
-  // matrix: value + int32 column per stored entry; per row and vector: gather of u_n once,
-  // tau^2/m, u_{n-1} read, u_{n+1} written, F accumulators read and written.
+  // matrix: value + int32 column per stored entry; per row: tau^2/m once; per row and
+  // vector: gather of u_n once, u_{n-1} read, u_{n+1} written, F accumulators read and written.
   if (c->opts.precision == KES_PREC_FP64)
     return 12 * c->nnz + 4 * (c->n + 1) + c->n * (8 + int64_t(b) * (8 + 8 + 8 + 16 * F));
   return 8 * c->nnz + c->n * (4 + int64_t(b) * (4 + 4 + 4 + 16 * F));
@@ -558,93 +1114,36 @@ int64_t kes_step_bytes(const kes_ctx* c, int32_t b, int32_t F) {
 kes_status kes_estimate_omega_max(kes_ctx* c, int32_t iters, const double* v0, double* omega_max,
                                   double* gershgorin) {
   if (!c || !v0 || !omega_max || iters < 0) return KES_ERR_ARG;
-  return guarded([&]() -> kes_status {
-    const int64_t launches0 = g_launches;
-    ensure_krylov(c, 2);
-    double* v = c->U64[0] ? c->U64[0] : c->B;  // scratch n_pad vectors
-    double* w = c->U64[1] ? c->U64[1] : c->SB;
-    KES_CUDA(cudaMemsetAsync(v, 0, c->n_pad * sizeof(double), c->stream));
-    KES_CUDA(cudaMemsetAsync(w, 0, c->n_pad * sizeof(double), c->stream));
-    vec_in(c, v0, KES_MEM_HOST, w);
-    launch_mdot(c->stream, w, 0, 1, w, nullptr, c->n_pad, c->partial, c->scal);
-    launch_scale_rsqrt(c->stream, w, c->scal, v, nullptr, c->n_pad);
-    for (int it = 0; it < iters; ++it) {
-      launch_spmv_f64(c->A, c->cfg, c->stream, v, c->minv64, w);
-      launch_mdot(c->stream, w, 0, 1, w, nullptr, c->n_pad, c->partial, c->scal);
-      launch_scale_rsqrt(c->stream, w, c->scal, v, nullptr, c->n_pad);
-    }
-    launch_spmv_f64(c->A, c->cfg, c->stream, v, nullptr, w);
-    launch_mdot(c->stream, v, 0, 1, w, nullptr, c->n_pad, c->partial, c->scal);          // v^T S v
-    launch_mdot(c->stream, v, 0, 1, v, c->m64, c->n_pad, c->partial, c->scal + 1);      // v^T M v
-    KES_CHECK_LAUNCH();
-    double h[2];
-    KES_CUDA(cudaMemcpyAsync(h, c->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    c->sync();
-    c->stats.kernel_launches += g_launches - launches0;
-    *omega_max = std::sqrt(std::max(h[0], 0.0) / h[1]);
-    c->omega_est = *omega_max;
-    if (gershgorin) *gershgorin = c->gershgorin;
-    return KES_OK;
-  });
+  if (c->n_mesh() != 1) return KES_ERR_UNSUPPORTED;
+  return omega_impl(c, iters, v0, omega_max, gershgorin);
+}
+
+kes_status kes_estimate_omega_max_batch(kes_ctx* c, int32_t iters, const double* v0, double* omega_max,
+                                        double* gershgorin) {
+  if (!c || !v0 || !omega_max || iters < 0) return KES_ERR_ARG;
+  return omega_impl(c, iters, v0, omega_max, gershgorin);
 }
 
 kes_status kes_set_filters(kes_ctx* c, int32_t F, const double* wmin, const double* wmax, double tau, int32_t L) {
-  if (!c || F < 1 || !wmin || !wmax || !(tau > 0.0) || L < 1 || !std::isfinite(tau)) return KES_ERR_ARG;
-  for (int f = 0; f < F; ++f)
-    if (!(wmin[f] >= 0.0) || !(wmax[f] > wmin[f]) || !std::isfinite(wmax[f])) return KES_ERR_ARG;
-  if (c->omega_est > 0.0 && tau * c->omega_est >= 2.0) return KES_ERR_UNSTABLE;
-  return guarded([&]() -> kes_status {
-    const size_t need = static_cast<size_t>(F) * (L + 1);
-    c->h_alpha.assign(need, 0.0);
-    for (int f = 0; f < F; ++f) alpha_table(wmin[f], wmax[f], tau, L, c->h_alpha.data() + f * (L + 1));
-    c->sync();
-    if (need > c->alpha_cap) {
-      c->dfree(c->alpha64);
-      c->dfree(c->alpha_hi);
-      c->dfree(c->alpha_lo);
-      c->alpha64 = c->dalloc_n<double>(need);
-      c->alpha_hi = c->dalloc_n<float>(need);
-      c->alpha_lo = c->dalloc_n<float>(need);
-      c->alpha_cap = need;
-      if (c->gexec) {
-        cudaGraphExecDestroy(c->gexec);
-        c->gexec = nullptr;
-      }
+  if (!c || F < 1 || !wmin || !wmax || L < 1) return KES_ERR_ARG;
+  const int nm = c->n_mesh();
+  std::vector<double> a(static_cast<size_t>(nm) * F), b(a.size()), t(nm, tau);
+  for (int j = 0; j < nm; ++j)
+    for (int f = 0; f < F; ++f) {
+      a[j * F + f] = wmin[f];
+      b[j * F + f] = wmax[f];
     }
-    std::vector<float> hi(need), lo(need);
-    for (size_t i = 0; i < need; ++i) {
-      hi[i] = static_cast<float>(c->h_alpha[i]);
-      lo[i] = static_cast<float>(c->h_alpha[i] - static_cast<double>(hi[i]));
-    }
-    KES_CUDA(cudaMemcpyAsync(c->alpha64, c->h_alpha.data(), need * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    KES_CUDA(cudaMemcpyAsync(c->alpha_hi, hi.data(), need * sizeof(float), cudaMemcpyHostToDevice, c->stream));
-    KES_CUDA(cudaMemcpyAsync(c->alpha_lo, lo.data(), need * sizeof(float), cudaMemcpyHostToDevice, c->stream));
-    // tau^2 / m in permuted order
-    std::vector<double> m(c->n_pad);
-    KES_CUDA(cudaMemcpyAsync(m.data(), c->m64, c->n_pad * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    c->sync();
-    std::vector<double> t2m(c->n_pad, 0.0);
-    for (int64_t i = 0; i < c->n; ++i) t2m[i] = tau * tau / m[i];
-    KES_CUDA(cudaMemcpyAsync(c->tau2m64, t2m.data(), c->n_pad * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    if (c->tau2m32) {
-      std::vector<float> t32(t2m.begin(), t2m.end());
-      KES_CUDA(cudaMemcpyAsync(c->tau2m32, t32.data(), c->n_pad * sizeof(float), cudaMemcpyHostToDevice, c->stream));
-      c->sync();
-    }
-    ensure_stage_out(c, F);
-    c->sync();
-    c->F = F;
-    c->L = L;
-    c->tau = tau;
-    c->wmin.assign(wmin, wmin + F);
-    c->wmax.assign(wmax, wmax + F);
-    c->filter_set = true;
-    return KES_OK;
-  });
+  return set_filters_impl(c, F, a.data(), b.data(), t.data(), L);
 }
 
 kes_status kes_set_filter(kes_ctx* c, double wmin, double wmax, double tau, int32_t L) {
   return kes_set_filters(c, 1, &wmin, &wmax, tau, L);
+}
+
+kes_status kes_set_filters_batch(kes_ctx* c, int32_t F, const double* wmin, const double* wmax, const double* tau,
+                                 int32_t L) {
+  if (!c || F < 1 || !wmin || !wmax || !tau || L < 1) return KES_ERR_ARG;
+  return set_filters_impl(c, F, wmin, wmax, tau, L);
 }
 
 kes_status kes_alpha_table(double wmin, double wmax, double tau, int32_t L, double* alpha) {
@@ -669,14 +1168,14 @@ kes_status kes_filter_apply(kes_ctx* c, const double* r_in, double* r_out, int32
   if (!c || !r_in || !r_out || b < 1 || b > c->opts.block_b || (mem != KES_MEM_HOST && mem != KES_MEM_DEVICE))
     return KES_ERR_ARG;
   if (!c->filter_set) return KES_ERR_STATE;
+  LaunchCount lc(&c->stats);
   return guarded([&]() -> kes_status {
-    for (int j = 0; j < b; ++j) {
-      vec_in(c, r_in + static_cast<int64_t>(j) * c->n, mem, c->stage_in);
-      run_filter(c);
-      for (int f = 0; f < c->F; ++f)
-        vec_out(c, c->stage_out + static_cast<int64_t>(f) * c->n_pad,
-                r_out + (static_cast<int64_t>(f) * b + j) * c->n, mem);
-    }
+    const int NB = nb_for(b);
+    block_in(c, r_in, b, mem, NB, c->stage_in);
+    run_filter(c, NB);
+    for (int f = 0; f < c->F; ++f)
+      block_out(c, c->stage_out + static_cast<int64_t>(f) * c->n_pad * NB, NB, b,
+                r_out + static_cast<int64_t>(f) * b * c->n, mem);
     KES_CHECK_LAUNCH();
     if (mem == KES_MEM_HOST) return check_flag(c);
     return KES_OK;
@@ -700,202 +1199,26 @@ kes_status kes_krylov_solve(kes_ctx* c, const double* r0, int32_t mem, const kes
   if (!c || !r0 || !out || (mem != KES_MEM_HOST && mem != KES_MEM_DEVICE)) return KES_ERR_ARG;
   *out = nullptr;
   if (!c->filter_set) return KES_ERR_STATE;
-  if (c->F != 1) return KES_ERR_UNSUPPORTED;
+  if (c->F != 1 || c->n_mesh() != 1) return KES_ERR_UNSUPPORTED;
   kes_solve_opts so;
   if (so_in) so = *so_in;
   else kes_solve_opts_default(&so);
   if (so.kmax < 1 || so.check_every < 1 || !(so.tol > 0.0)) return KES_ERR_ARG;
-  const auto t_start = std::chrono::steady_clock::now();
-  kes_result* res = static_cast<kes_result*>(std::calloc(1, sizeof(kes_result)));
-  if (!res) return KES_ERR_OOM;
-  kes_status st = guarded([&]() -> kes_status {
-    const int kmax = so.kmax;
-    ensure_krylov(c, kmax);
-    const int64_t np = c->n_pad;
-    const double wmin = c->wmin[0], wmax = c->wmax[0];
-    cudaStream_t s = c->stream;
-    double* B = c->B;
-    double* SB = c->SB;
-    double* w = c->stage_out;  // the filtered vector is orthogonalised in place
-    auto other_begin = [&]() {
-      cudaEvent_t e0 = c->get_event();
-      KES_CUDA(cudaEventRecord(e0, s));
-      return e0;
-    };
-    auto other_end = [&](cudaEvent_t e0) {
-      cudaEvent_t e1 = c->get_event();
-      KES_CUDA(cudaEventRecord(e1, s));
-      c->ev_other.emplace_back(e0, e1);
-    };
-    const int64_t launches0 = g_launches;
+  return block_solve_impl(c, r0, 1, mem, so, out);
+}
 
-    // b_0 = r0 / ||r0||_M ; S b_0 ; H(0,0)
-    cudaEvent_t e0 = other_begin();
-    vec_in(c, r0, mem, c->stage_in);
-    launch_mdot(s, c->stage_in, 0, 1, c->stage_in, c->m64, np, c->partial, c->scal);
-    launch_scale_rsqrt(s, c->stage_in, c->scal, B, c->stage_in, np);
-    launch_spmv_f64(c->A, c->cfg, s, B, nullptr, SB);
-    launch_mdot(s, B, np, 1, SB, nullptr, np, c->partial, c->Hd);
-    KES_CHECK_LAUNCH();
-    other_end(e0);
-
-    std::vector<double> Hh, theta, Y, rr;
-    int k = 1;
-    bool breakdown = false;
-    int64_t steps = 0;
-    // projection state of the last solve of eq. (projevp)
-    std::vector<double> last_theta, last_rel;
-    std::vector<int> acc_idx;
-    std::vector<double> acc_theta, acc_rel, acc_abs, acc_Y;
-
-    auto project = [&](int kk) {
-      Hh.assign(static_cast<size_t>(kk) * kk, 0.0);
-      KES_CUDA(cudaMemcpy2DAsync(Hh.data(), kk * sizeof(double), c->Hd, c->kcap * sizeof(double),
-                                 kk * sizeof(double), kk, cudaMemcpyDeviceToHost, s));
-      c->sync();
-      // column j holds rows 0..j (upper triangle); mirror it into the lower triangle
-      for (int j = 0; j < kk; ++j)
-        for (int i = j + 1; i < kk; ++i) Hh[static_cast<size_t>(j) * kk + i] = Hh[static_cast<size_t>(i) * kk + j];
-      theta.assign(kk, 0.0);
-      Y.assign(static_cast<size_t>(kk) * kk, 0.0);
-      if (!sym_eig(kk, Hh.data(), theta.data(), Y.data())) throw KesError{KES_ERR_CUDA};
-      for (double& t : theta) t = std::max(t, 0.0);
-      std::vector<int> inside;
-      for (int j = 0; j < kk; ++j) {
-        const double om = std::sqrt(theta[j]);
-        if (om >= wmin && om <= wmax) inside.push_back(j);
-      }
-      const int p = static_cast<int>(inside.size());
-      last_theta = theta;
-      last_rel.assign(kk, std::numeric_limits<double>::quiet_NaN());
-      acc_idx.clear();
-      acc_theta.clear();
-      acc_rel.clear();
-      acc_abs.clear();
-      acc_Y.clear();
-      if (p == 0) return;
-      std::vector<double> Ysel(static_cast<size_t>(kk) * p), thsel(p);
-      for (int q = 0; q < p; ++q) {
-        thsel[q] = theta[inside[q]];
-        std::memcpy(&Ysel[static_cast<size_t>(q) * kk], &Y[static_cast<size_t>(inside[q]) * kk], kk * sizeof(double));
-      }
-      if (p > c->kcap) throw KesError{KES_ERR_ARG};
-      cudaEvent_t ev = other_begin();
-      KES_CUDA(cudaMemcpyAsync(c->Yd, Ysel.data(), Ysel.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-      KES_CUDA(cudaMemcpyAsync(c->thd, thsel.data(), p * sizeof(double), cudaMemcpyHostToDevice, s));
-      launch_ritz_residual(s, B, SB, np, kk, c->Yd, c->thd, p, c->m64, np, c->partial, c->scal);
-      KES_CHECK_LAUNCH();
-      rr.assign(2 * p, 0.0);
-      KES_CUDA(cudaMemcpyAsync(rr.data(), c->scal, 2 * p * sizeof(double), cudaMemcpyDeviceToHost, s));
-      other_end(ev);
-      c->sync();
-      for (int q = 0; q < p; ++q) {
-        const double a = std::sqrt(std::max(rr[q], 0.0));
-        const double den = thsel[q] * std::sqrt(std::max(rr[p + q], 0.0));
-        const double rel = den > 0.0 ? a / den : std::numeric_limits<double>::infinity();
-        last_rel[inside[q]] = rel;
-        if (rel <= so.tol) {
-          acc_idx.push_back(inside[q]);
-          acc_theta.push_back(thsel[q]);
-          acc_rel.push_back(rel);
-          acc_abs.push_back(a);
-          acc_Y.insert(acc_Y.end(), Ysel.begin() + static_cast<size_t>(q) * kk,
-                       Ysel.begin() + static_cast<size_t>(q + 1) * kk);
-        }
-      }
-    };
-
-    int kproj = 0;
-    while (k < kmax) {
-      run_filter(c);  // stage_in = b_{k-1} -> w = C b_{k-1}
-      steps += c->L;
-      cudaEvent_t ev = other_begin();
-      double* sc = c->scal;
-      launch_mdot(s, w, 0, 1, w, c->m64, np, c->partial, sc);          // ||w||_M^2 before
-      for (int pass = 0; pass < 2; ++pass) {
-        launch_mdot(s, B, np, k, w, c->m64, np, c->partial, sc + 4);   // h = B^T M w
-        launch_gemv_sub(s, w, B, np, k, sc + 4, np);                   // w -= B h
-      }
-      launch_mdot(s, w, 0, 1, w, c->m64, np, c->partial, sc + 1);      // ||w||_M^2 after
-      KES_CHECK_LAUNCH();
-      double nrm[2];
-      int flag = 0;
-      KES_CUDA(cudaMemcpyAsync(nrm, sc, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-      KES_CUDA(cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-      other_end(ev);
-      c->sync();
-      if (flag) {
-        KES_CUDA(cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
-        throw KesError{KES_ERR_UNSTABLE};
-      }
-      if (!(std::sqrt(nrm[1]) > 1e-10 * std::sqrt(nrm[0]))) {
-        breakdown = true;
-        break;
-      }
-      ev = other_begin();
-      double* bk = B + static_cast<int64_t>(k) * np;
-      double* sbk = SB + static_cast<int64_t>(k) * np;
-      launch_scale_rsqrt(s, w, sc + 1, bk, c->stage_in, np);            // b_k, next filter input
-      launch_spmv_f64(c->A, c->cfg, s, bk, nullptr, sbk);               // S b_k
-      launch_mdot(s, B, np, k + 1, sbk, nullptr, np, c->partial, c->Hd + static_cast<int64_t>(k) * c->kcap);
-      KES_CHECK_LAUNCH();
-      other_end(ev);
-      ++k;
-      if (k % so.check_every == 0 && k < kmax) {
-        project(k);
-        kproj = k;
-        if (so.n_wanted > 0 && static_cast<int>(acc_idx.size()) >= so.n_wanted) break;
-      }
-    }
-    if (kproj != k) project(k);
-
-    const int p = static_cast<int>(acc_idx.size());
-    res->n = c->n;
-    res->n_pairs = p;
-    res->k_used = k;
-    res->breakdown = breakdown ? 1 : 0;
-    res->n_ritz = k;
-    res->time_steps = steps;
-    auto hdup = [](const std::vector<double>& v) {
-      double* d = static_cast<double*>(std::malloc(std::max<size_t>(1, v.size()) * sizeof(double)));
-      if (!d) throw std::bad_alloc();
-      if (!v.empty()) std::memcpy(d, v.data(), v.size() * sizeof(double));
-      return d;
-    };
-    res->omega2 = hdup(acc_theta);
-    std::vector<double> om(p);
-    for (int q = 0; q < p; ++q) om[q] = std::sqrt(acc_theta[q]);
-    res->omega = hdup(om);
-    res->rel_res = hdup(acc_rel);
-    res->abs_res = hdup(acc_abs);
-    res->ritz_omega2 = hdup(last_theta);
-    res->ritz_rel_res = hdup(last_rel);
-    if (so.want_vectors && p > 0) {
-      const size_t need = static_cast<size_t>(p) * np;
-      if (need > c->Xd_cap) {
-        c->dfree(c->Xd);
-        c->Xd = c->dalloc_n<double>(need);
-        c->Xd_cap = need;
-      }
-      KES_CUDA(cudaMemcpyAsync(c->Yd, acc_Y.data(), acc_Y.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-      launch_gemm_bx(s, B, np, k, c->Yd, p, c->Xd, np, np);
-      KES_CHECK_LAUNCH();
-      res->vectors = static_cast<double*>(std::malloc(static_cast<size_t>(p) * c->n * sizeof(double)));
-      if (!res->vectors) throw std::bad_alloc();
-      for (int q = 0; q < p; ++q) vec_out(c, c->Xd + static_cast<int64_t>(q) * np, res->vectors + q * c->n, KES_MEM_HOST);
-    }
-    c->sync();
-    c->stats.kernel_launches += g_launches - launches0;
-    return breakdown ? KES_INFO_INVARIANT_SUBSPACE : KES_OK;
-  });
-  res->solve_ms =
-      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
-  if (st != KES_OK && st != KES_INFO_INVARIANT_SUBSPACE) {
-    kes_result_free(res);
-    return st;
-  }
-  *out = res;
-  return st;
+kes_status kes_block_krylov_solve(kes_ctx* c, const double* R0, int32_t b, int32_t mem, const kes_solve_opts* so_in,
+                                  kes_result** out) {
+  if (!c || !R0 || !out || b < 1 || b > c->opts.block_b || (mem != KES_MEM_HOST && mem != KES_MEM_DEVICE))
+    return KES_ERR_ARG;
+  for (int j = 0; j < c->n_mesh(); ++j) out[j] = nullptr;
+  if (!c->filter_set) return KES_ERR_STATE;
+  if (c->F != 1) return KES_ERR_UNSUPPORTED;
+  kes_solve_opts so;
+  if (so_in) so = *so_in;
+  else kes_solve_opts_default(&so);
+  if (so.kmax < b || so.check_every < 1 || !(so.tol > 0.0)) return KES_ERR_ARG;
+  return block_solve_impl(c, R0, b, mem, so, out);
 }
 
 kes_status kes_get_stats(kes_ctx* c, kes_stats* s) {

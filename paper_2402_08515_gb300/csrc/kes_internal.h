@@ -43,6 +43,9 @@ struct SellDev {
   const int32_t* col = nullptr;
   const double* val64 = nullptr;
   const float* val32 = nullptr;
+  // mesh of each slice when several meshes are stacked block-diagonally (null: one mesh).
+  // Weight tables are indexed (mesh * F + f) * (L + 1) + n.
+  const int32_t* slice_mesh = nullptr;
 };
 
 struct LaunchCfg {
@@ -50,6 +53,8 @@ struct LaunchCfg {
   int block_step = 256;
   int n_sm = 152;
   int variant = 0;     // step-kernel launch shape (load batch, register cap), see step_variant_count
+  int grid_blk = 0;    // blocks of the block (SpMM) step kernels
+  int variant_blk = 0; // their launch shape (register cap), see blk_variant_count
 };
 
 // One fused leapfrog step, FP64 (Sec. 2.3, eq. 2stepmethod + eq. disc_filtercoeff):
@@ -68,9 +73,37 @@ void launch_step_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bo
                      const float* tau2m, const float* x, const float* prev, float* out, float* acc_s,
                      float* acc_c, double* acc64, int64_t acc_stride, int F, const float* alpha_hi,
                      const float* alpha_lo, int L, int step, int* flag);
-// FP32 start: x32 = (float) r64; s_f = fl(alpha_f[0] r), c_f = alpha_f[0] r - s_f (rounded).
-void launch_init_f32(cudaStream_t st, int64_t n_pad, const double* r64, float* x32, float* acc_s,
+// FP32 start over n_pad x nb row-major values: x32 = (float) r64; s_f = fl(alpha_f[0] r),
+// c_f = alpha_f[0] r - s_f (rounded), with the weight table of each row's mesh.
+void launch_init_f32(cudaStream_t st, const SellDev& A, int nb, const double* r64, float* x32, float* acc_s,
                      float* acc_c, int64_t acc_stride, int F, const double* alpha64, int L);
+
+// Block step (SpMM form) for NB in {2, 4, 8} columns, row-major n_pad x NB state
+// (row i's NB values contiguous). Same arithmetic per column as the single-vector
+// kernels; acc_stride = n_pad * NB elements per weight table.
+void launch_step_blk_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, int NB, bool first, bool last,
+                         const double* tau2m, const double* x, const double* prev, double* out, double* acc,
+                         int64_t acc_stride, int F, const double* alpha, int L, int step, int* flag);
+void launch_step_blk_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, int NB, bool first, bool last,
+                         const float* tau2m, const float* x, const float* prev, float* out, float* acc_s,
+                         float* acc_c, double* acc64, int64_t acc_stride, int F, const float* alpha_hi,
+                         const float* alpha_lo, int L, int step, int* flag);
+int blk_variant_count();
+int blk_blocks_per_sm(bool fp32, int NB, int variant, int block);
+
+// Row-major block <-> user / basis layouts.
+//   gather_rows: dst[i*NB + j] = src[j*ld_src + row_src[i]] for j < ncols and row_src[i] >= 0, else 0
+//   scatter_rows: dst[j*ld_dst + row_src[i]] = src[i*NB + j] for j < ncols, row_src[i] >= 0
+//   (row_src null: the identity for i < n_valid)
+void launch_gather_rows(cudaStream_t st, const double* src, int64_t ld_src, int ncols, const int32_t* row_src,
+                        int64_t n_valid, double* dst, int NB, int64_t n_pad);
+void launch_scatter_rows(cudaStream_t st, const double* src, int NB, int ncols, const int32_t* row_src,
+                         int64_t n_valid, double* dst, int64_t ld_dst, int64_t n_pad);
+//   pack_basis: stage[i*NB + j] = B[colsel[mesh(i)*NB + j] * ldb + i] (colsel < 0: 0)
+//   unpack_block: Wc[j*n_pad + i] = stage[i*NB + j]
+void launch_pack_basis(cudaStream_t st, const double* B, int64_t ldb, const int32_t* colsel,
+                       const int32_t* slice_mesh, double* stage, int NB, int64_t n_pad);
+void launch_unpack_block(cudaStream_t st, const double* stage, int NB, double* Wc, int64_t n_pad);
 
 // Launch-shape variants of the step kernels (same arithmetic, different load batch and
 // register cap) and the resident blocks per SM of one variant (occupancy calculator);

@@ -1,0 +1,145 @@
+"""Block (SpMM) filter, multi-mesh batches and the block Krylov solver (Sec. 4,
+block version) of the CUDA path against the FP64 oracle and the exact spectra."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2402_08515_gb300 as K
+from fe_inputs import box_grid, flared_tube, square_grid, start_vectors
+from oracle import spectra
+from tests.tolerances import EIG_REL, filter_error, filter_tol
+
+pytestmark = pytest.mark.gpu
+
+
+def _tau(p):
+    return 0.9 * 2 / O.power_iteration(p.to_scipy(), p.m, start_vectors(p.n, 1, 0)[0], 300)
+
+
+@pytest.fixture(scope="module")
+def meshes():
+    return [square_grid(40), box_grid((23, 19, 17), extent=(1.0, 0.9, 0.8)),
+            flared_tube(0.03, length=1.0, r0=0.06, growth=1.2)]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("b", [2, 3, 4, 8])
+def test_block_filter_matches_oracle(meshes, precision, b):
+    p = meshes[1]
+    tau = _tau(p)
+    L = 80
+    bands = [(6.0, 10.0), (14.0, 18.0)]
+    alphas = np.stack([O.alpha_table(a, c, tau, L) for a, c in bands])
+    R = start_vectors(p.n, b, 17)
+    ref = O.filter_apply_multi(p.to_scipy(), p.m, R, tau, alphas)
+    with K.Context(p, precision=precision, block_b=b) as c:
+        K.kes_set_filters(c.handle, [a for a, _ in bands], [x for _, x in bands], tau, L)
+        out = np.zeros((2, b, p.n))
+        K.kes_filter_apply(c.handle, R, out, b)
+    for f in range(2):
+        err = filter_error(out[f], ref[f], R, p.m, alphas[f])
+        assert err <= filter_tol(L, precision), (f, err)
+
+
+def test_block_columns_equal_single_vector_runs(meshes):
+    # every column of the SpMM step rounds like the single-vector kernel
+    p = meshes[2]
+    tau = _tau(p)
+    R = start_vectors(p.n, 4, 2)
+    with K.Context(p, block_b=4) as c:
+        K.kes_set_filter(c.handle, 8.0, 12.0, tau, 60)
+        blk = np.zeros((1, 4, p.n))
+        K.kes_filter_apply(c.handle, R, blk, 4)
+        for j in range(4):
+            one = np.zeros((1, 1, p.n))
+            K.kes_filter_apply(c.handle, R[j:j + 1], one, 1)
+            np.testing.assert_array_equal(one[0, 0], blk[0, j])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batched_meshes_filter_matches_oracle(meshes, precision):
+    taus = np.array([_tau(p) for p in meshes])
+    L = 70
+    wmin = np.array([[10.0, 20.0], [5.0, 9.0], [4.0, 7.0]])
+    wmax = np.array([[15.0, 26.0], [8.0, 13.0], [6.0, 9.0]])
+    b = 2
+    Rs = [start_vectors(p.n, b, 30 + j) for j, p in enumerate(meshes)]
+    R = np.concatenate(Rs, axis=1)                       # (b, n_total)
+    with K.Context(meshes, precision=precision, block_b=b) as c:
+        assert K.kes_mesh_count(c.handle) == 3 and K.kes_size(c.handle) == R.shape[1]
+        K.kes_set_filters_batch(c.handle, wmin, wmax, taus, L)
+        out = np.zeros((2, b, R.shape[1]))
+        K.kes_filter_apply(c.handle, R, out, b)
+    off = 0
+    for j, p in enumerate(meshes):
+        alphas = np.stack([O.alpha_table(wmin[j, f], wmax[j, f], taus[j], L) for f in range(2)])
+        ref = O.filter_apply_multi(p.to_scipy(), p.m, Rs[j], taus[j], alphas)
+        for f in range(2):
+            err = filter_error(out[f, :, off:off + p.n], ref[f], Rs[j], p.m, alphas[f])
+            assert err <= filter_tol(L, precision), (j, f, err)
+        off += p.n
+
+
+def test_block_solver_b1_equals_single_vector_solver():
+    p = square_grid(48)
+    tau = _tau(p)
+    r0 = start_vectors(p.n, 1, 0)
+    so = K.kes_solve_opts_default()
+    so.kmax, so.tol = 40, 1e-8
+    with K.Context(p) as c:
+        K.kes_set_filter(c.handle, 15.0, 25.0, tau, 200)
+        a = K.kes_krylov_solve(c.handle, r0[0], so)
+        b = K.kes_block_krylov_solve(c.handle, r0, 1, so)[0]
+    np.testing.assert_array_equal(a["ritz_omega2"], b["ritz_omega2"])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_block_solver_resolves_multiplicity_like_the_oracle(precision):
+    p = square_grid(32)
+    S = p.to_scipy()
+    tau = _tau(p)
+    exact = spectra.eigenvalues_in(p.cells, p.h, 20.0, 30.0)
+    R = start_vectors(p.n, 2, 3)
+    tol = 1e-8 if precision == "fp64" else 1e-5
+    so = K.kes_solve_opts_default()
+    so.kmax, so.tol, so.want_vectors = 100, tol, 1
+    with K.Context(p, precision=precision, block_b=2) as c:
+        K.kes_set_filter(c.handle, 20.0, 30.0, tau, 300)
+        res = K.kes_block_krylov_solve(c.handle, R, 2, so)[0]
+    ores = O.block_krylov_solve(S, p.m, R, 20.0, 30.0, tau, 300, 100, tol)
+    print(f"{precision}: GPU accepted {res['n_pairs']}, oracle {len(ores.omega2)}, exact {len(exact)}")
+    for th in res["omega2"]:
+        assert np.min(np.abs(exact - th)) <= EIG_REL[precision] * th
+    if precision == "fp64":
+        assert res["n_pairs"] == len(exact) == len(ores.omega2)
+        np.testing.assert_allclose(np.sort(res["omega2"]), exact, rtol=1e-10)
+    else:
+        assert res["n_pairs"] >= len(exact) - 4
+    for th, x in zip(res["omega2"], res["vectors"]):
+        r = S @ x - th * p.m * x
+        assert np.linalg.norm(r) <= tol * 1.01 * th * np.linalg.norm(p.m * x)
+
+
+def test_batched_block_solver_per_mesh(meshes):
+    sq, box = meshes[0], meshes[1]
+    taus = np.array([_tau(sq), _tau(box)])
+    wmin = np.array([[14.0], [7.0]])
+    wmax = np.array([[20.0], [10.0]])
+    b = 2
+    Rs = [start_vectors(sq.n, b, 5), start_vectors(box.n, b, 6)]
+    R = np.concatenate(Rs, axis=1)
+    so = K.kes_solve_opts_default()
+    so.kmax, so.tol = 80, 1e-8
+    with K.Context([sq, box], block_b=b) as c:
+        K.kes_set_filters_batch(c.handle, wmin, wmax, taus, 250)
+        res = K.kes_block_krylov_solve(c.handle, R, b, so)
+    for j, (p, r) in enumerate(zip([sq, box], res)):
+        exact = spectra.eigenvalues_in(p.cells, p.h, wmin[j, 0], wmax[j, 0])
+        print(f"mesh {j}: accepted {r['n_pairs']} of {len(exact)}")
+        assert r["n_pairs"] >= 1 and r["k_used"] <= 80
+        for th in r["omega2"]:
+            assert np.min(np.abs(exact - th)) <= 1e-10 * th
+        oref = O.block_krylov_solve(p.to_scipy(), p.m, Rs[j], wmin[j, 0], wmax[j, 0], taus[j], 250, 80, 1e-8)
+        assert abs(r["n_pairs"] - len(oref.omega2)) <= 2

@@ -295,3 +295,30 @@ def test_krylov_breakdown_on_eigenvector_start():
                          tau, 100, 10, 1e-8)
     assert res.breakdown and res.k_used == 1
     assert res.omega2[0] == pytest.approx(lam, rel=1e-13)
+
+
+# ---------------------------------------------------------------- block version (Sec. 4)
+
+def test_block_solver_with_one_vector_is_the_krylov_solver():
+    p = square_grid(24)
+    S = p.to_scipy()
+    tau = 0.9 * 2 / math.sqrt(spectra.box_spectrum(p.cells, p.h).max())
+    r = start_vectors(p.n, 1, 4)
+    a = O.krylov_solve(S, p.m, r[0], 15.0, 25.0, tau, 200, 40, 1e-8)
+    b = O.block_krylov_solve(S, p.m, r, 15.0, 25.0, tau, 200, 40, 1e-8)
+    np.testing.assert_array_equal(a.omega2, b.omega2)
+    np.testing.assert_array_equal(a.basis, b.basis)
+
+
+def test_block_solver_resolves_multiple_eigenvalues():
+    # the square has double eigenvalues (k1, k2) ~ (k2, k1); one start vector sees one
+    # vector per eigenspace (Lemma 2.2), a block of two sees both copies
+    p = square_grid(32)
+    S = p.to_scipy()
+    tau = 0.9 * 2 / math.sqrt(spectra.box_spectrum(p.cells, p.h).max())
+    exact = spectra.eigenvalues_in(p.cells, p.h, 20.0, 30.0)
+    res = O.block_krylov_solve(S, p.m, start_vectors(p.n, 2, 3), 20.0, 30.0, tau, 300, 100, 1e-8)
+    assert len(res.omega2) == len(exact) == 36
+    np.testing.assert_allclose(np.sort(res.omega2), exact, rtol=1e-10)
+    G = res.vectors @ (p.m[:, None] * res.vectors.T)     # accepted vectors M-orthonormal
+    np.testing.assert_allclose(G, np.eye(len(exact)), atol=1e-8)
