@@ -188,20 +188,21 @@ def profiled_traffic(workload: str):
 
 # ----------------------------------------------------------------------------- CPU baseline
 
-def oracle_sample(problem, tau, wl, seconds: float):
+def oracle_sample(problem, tau, wl, seconds: float, interval=None):
     """Times the oracle's filter application (as it stands) on a bounded number of
     leapfrog steps of the same workload; returns (GDOF*steps/s, steps, seconds)."""
     import numpy as np
     import oracle as O
     from fe_inputs import start_vectors
+    wmin, wmax = interval or (wl.omega_min, wl.omega_max)
     S = problem.to_scipy()
     r = start_vectors(problem.n, 1, wl.seed)[0]
-    probe = 5
+    probe = 3
     t0 = time.perf_counter()
-    O.filter_apply(S, problem.m, r, tau, O.alpha_table(wl.omega_min, wl.omega_max, tau, probe))
+    O.filter_apply(S, problem.m, r, tau, O.alpha_table(wmin, wmax, tau, probe))
     per_step = (time.perf_counter() - t0) / probe
-    steps = int(max(5, min(wl.L, seconds / max(per_step, 1e-6))))
-    alpha = O.alpha_table(wl.omega_min, wl.omega_max, tau, steps)
+    steps = int(max(3, min(wl.L, seconds / max(per_step, 1e-6))))
+    alpha = O.alpha_table(wmin, wmax, tau, steps)
     t0 = time.perf_counter()
     out = O.filter_apply(S, problem.m, r, tau, alpha)
     dt = time.perf_counter() - t0
@@ -214,6 +215,19 @@ def cpu_cores_used() -> int:
     return 1
 
 
+def workload_problems(wl):
+    built = wl.build()
+    return (built if isinstance(built, list) else [built]), isinstance(built, list)
+
+
+def start_block(problems, b, seed):
+    """(b, n_total) start vectors: each mesh draws its own seeded block."""
+    import numpy as np
+    from fe_inputs import start_vectors
+    return np.ascontiguousarray(np.concatenate(
+        [start_vectors(p.n, b, seed + 97 * j) for j, p in enumerate(problems)], axis=1))
+
+
 # ----------------------------------------------------------------------------- kes arm
 
 def run_kes(args):
@@ -221,7 +235,7 @@ def run_kes(args):
     import torch
 
     import paper_2402_08515_gb300 as K
-    from fe_inputs import WORKLOADS, start_vectors
+    from fe_inputs import WORKLOADS
     from oracle import spectra
 
     rank, world, local = dist_env()
@@ -229,36 +243,45 @@ def run_kes(args):
     dist = init_dist(world, "nccl")
     dev = torch.device("cuda", local)
     wl = WORKLOADS[args.workload]
-    problem = wl.build()
-    n = problem.n
+    problems, batch = workload_problems(wl)
+    n = sum(p.n for p in problems)
+    nnz = sum(p.nnz for p in problems)
+    b = wl.b
     stream = torch.cuda.Stream(device=dev)
-    ctx = K.Context(problem, precision=wl.precision, stream=stream, step_variant=args.variant)
+    ctx = K.Context(problems if batch else problems[0], precision=wl.precision, stream=stream,
+                    step_variant=args.variant, block_b=b)
     h = ctx.handle
-    v0 = start_vectors(n, 1, wl.seed)[0]
-    omega_pow, gersh = K.kes_estimate_omega_max(h, wl.power_iters, v0)
-    tau = wl.cfl * 2.0 / omega_pow
-    K.kes_set_filter(h, wl.omega_min, wl.omega_max, tau, wl.L)
+    v0 = start_block(problems, 1, wl.seed)[0]
+    omega_pow, gersh = K.kes_estimate_omega_max_batch(h, wl.power_iters, v0)
+    taus = wl.cfl * 2.0 / omega_pow
+    ivs = [wl.mesh_intervals(p) for p in problems]
+    F = len(ivs[0])
+    wmin1 = np.array([[iv[0][0]] for iv in ivs])
+    wmax1 = np.array([[iv[0][1]] for iv in ivs])
+    K.kes_set_filters_batch(h, wmin1, wmax1, taus, wl.L)
     so = K.kes_solve_opts_default()
-    so.kmax, so.tol = wl.kmax, (1e-8 if wl.precision == "fp64" else 1e-5)
-    r0_host = start_vectors(n, 1, wl.seed + 1 + rank)[0]
-    r0_dev = torch.from_numpy(r0_host).to(dev)
+    so.kmax, so.tol, so.check_every = wl.kmax, wl.acceptance(), wl.check_every
+    R0_host = start_block(problems, b, wl.seed + 1 + 1000 * rank)
+    R0_dev = torch.from_numpy(R0_host).to(dev)
     torch.cuda.synchronize()
     if args.mode == "filter":
         L = args.L or wl.L
-        K.kes_set_filter(h, wl.omega_min, wl.omega_max, tau, L)
-        out = torch.zeros((1, 1, n), dtype=torch.float64, device=dev)
-        K.kes_filter_apply(h, r0_dev[None, :], out, 1)
+        K.kes_set_filters_batch(h, wmin1, wmax1, taus, L)
+        out = torch.zeros((1, b, n), dtype=torch.float64, device=dev)
+        K.kes_filter_apply(h, R0_dev, out, b)
         K.kes_sync(h)
         st = K.kes_get_stats(h)
         if rank == 0:
-            print(json.dumps({"mode": "filter", "workload": args.workload, "L": L, "dofs": n,
+            print(json.dumps({"mode": "filter", "workload": args.workload, "L": L, "dofs": n, "b": b,
                               "filter_ms": st["filter_ms"], "step_variant": st["step_variant"],
                               "finite": bool(torch.isfinite(out).all())}))
         ctx.close()
         return
 
     def solve():
-        return K.kes_krylov_solve(h, r0_dev, so)
+        if b == 1 and not batch:
+            return [K.kes_krylov_solve(h, R0_dev[0], so)]
+        return K.kes_block_krylov_solve(h, R0_dev, b, so)
 
     for _ in range(max(args.warmup, 0)):
         res = solve()
@@ -277,22 +300,44 @@ def run_kes(args):
     ms_local = e0.elapsed_time(e1)
     stats = K.kes_get_stats(h)
     ms_total = max_over_ranks(dist, ms_local, dev)
-    units_local = n * res["time_steps"] * args.steps
+    steps_per_solve = res[0]["time_steps"]
+    units_local = n * b * steps_per_solve * args.steps
     units = sum_over_ranks(dist, units_local, dev)
     value = units / (ms_total / 1e3) / 1e9
 
     # roofline of the fused step kernel, timed by the library's CUDA events on its stream
     step_ms = stats["filter_ms"] / max(stats["filter_steps"], 1)
-    bytes_step = K.kes_step_bytes(h, 1, 1)
+    bytes_step = K.kes_step_bytes(h, b, 1)
     achieved = bytes_step / (step_ms / 1e3) / 1e9
     peak, peak_src = load_peak()
-    traffic = profiled_traffic(args.workload)
+    traffic = profiled_traffic(args.workload) if b == 1 and not batch else None
 
-    # end to end through the C ABI with host buffers: r0 from pinned memory in,
+    # several intervals from one trajectory: the same block filtered with F weight tables
+    multi = None
+    if F > 1:
+        K.kes_set_filters_batch(h, np.array([[a for a, _ in iv] for iv in ivs]),
+                                np.array([[c for _, c in iv] for iv in ivs]), taus, wl.L)
+        out = torch.zeros((F, b, n), dtype=torch.float64, device=dev)
+        K.kes_filter_apply(h, R0_dev, out, b)
+        K.kes_sync(h)
+        K.kes_reset_stats(h)
+        reps = 3
+        for _ in range(reps):
+            K.kes_filter_apply(h, R0_dev, out, b)
+        st = K.kes_get_stats(h)
+        fms = st["filter_ms"] / reps
+        bF = K.kes_step_bytes(h, b, F)
+        multi = {"F": F, "b": b, "L": wl.L, "ms_per_filter": fms,
+                 "value": n * b * wl.L / (fms / 1e3) / 1e9, "unit": METRIC,
+                 "step_us": 1e3 * fms / wl.L, "achieved_gbs": bF / (fms / wl.L / 1e3) / 1e9,
+                 "algorithmic_bytes_per_step": bF}
+        K.kes_set_filters_batch(h, wmin1, wmax1, taus, wl.L)
+
+    # end to end through the C ABI with host buffers: start block from pinned memory in,
     # accepted Ritz pairs (values and vectors) out, every step
-    r0_pinned = torch.from_numpy(r0_host).pin_memory()
+    R0_pinned = torch.from_numpy(R0_host).pin_memory()
     so_e2e = K.kes_solve_opts_default()
-    so_e2e.kmax, so_e2e.tol, so_e2e.want_vectors = so.kmax, so.tol, 1
+    so_e2e.kmax, so_e2e.tol, so_e2e.want_vectors, so_e2e.check_every = so.kmax, so.tol, 1, so.check_every
     e2e_steps = args.e2e_steps
     barrier(dist)
     torch.cuda.synchronize()
@@ -300,49 +345,62 @@ def run_kes(args):
     out_bytes = 0
     r = res
     for _ in range(e2e_steps):
-        r = K.kes_krylov_solve(h, r0_pinned.numpy(), so_e2e)
-        out_bytes = (r["vectors"].nbytes if r["vectors"] is not None else 0) + 4 * r["n_pairs"] * 8
+        if b == 1 and not batch:
+            r = [K.kes_krylov_solve(h, R0_pinned.numpy()[0], so_e2e)]
+        else:
+            r = K.kes_block_krylov_solve(h, R0_pinned.numpy(), b, so_e2e)
+        out_bytes = sum((x["vectors"].nbytes if x["vectors"] is not None else 0) + 4 * x["n_pairs"] * 8 for x in r)
     torch.cuda.synchronize()
     e2e = None
     if e2e_steps > 0:
         e2e_s = max_over_ranks(dist, (time.perf_counter() - t0) / e2e_steps, dev)
-        e2e = {"value": sum_over_ranks(dist, n * r["time_steps"], dev) / e2e_s / 1e9, "unit": METRIC,
-               "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": out_bytes}
+        e2e = {"value": sum_over_ranks(dist, n * b * r[0]["time_steps"], dev) / e2e_s / 1e9, "unit": METRIC,
+               "h2d_bytes_per_step": 8 * n * b, "d2h_bytes_per_step": out_bytes}
 
     # accuracy of the accepted pairs against the exact spectrum (tensor grids)
     eig_err = None
-    if problem.cells and res["n_pairs"]:
-        exact = spectra.eigenvalues_in(problem.cells, problem.h, wl.omega_min, wl.omega_max)
-        eig_err = float(max(np.min(np.abs(exact - t)) / t for t in res["omega2"]))
+    for p, rr, iv in zip(problems, res, ivs):
+        if p.cells and not p.meta.get("length") and rr["n_pairs"]:
+            exact = spectra.eigenvalues_in(p.cells, p.h, iv[0][0], iv[0][1])
+            e = float(max(np.min(np.abs(exact - t)) / t for t in rr["omega2"]))
+            eig_err = e if eig_err is None else max(eig_err, e)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, steps, dt = oracle_sample(problem, tau, wl, args.cpu_seconds)
+        big = max(range(len(problems)), key=lambda j: problems[j].n)
+        v, steps, dt = oracle_sample(problems[big], taus[big], wl, args.cpu_seconds, ivs[big][0])
         cpu = {"value": v, "unit": METRIC, "cores": cpu_cores_used(), "kind": "oracle",
-               "sample": f"{steps} leapfrog steps of the FP64 oracle filter on the same matrix ({dt:.1f} s)"}
+               "sample": f"{steps} leapfrog steps of the FP64 oracle filter, one vector, on "
+                         f"{problems[big].name} ({problems[big].n} dofs, {dt:.1f} s)"}
 
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wl.precision == "fp64" else "f32",
         "data": "synthetic",
-        "config": {"workload": args.workload, "dofs": n, "nnz": problem.nnz, "interval": [wl.omega_min, wl.omega_max],
-                   "L": wl.L, "kmax": wl.kmax, "tau": tau, "omega_max_power": omega_pow,
+        "config": {"workload": args.workload, "meshes": len(problems), "dofs": n, "nnz": nnz, "b": b,
+                   "interval": [float(wmin1[0, 0]), float(wmax1[0, 0])] if not batch else "per mesh",
+                   "L": wl.L, "kmax": wl.kmax, "tau": float(taus[0]) if not batch else "per mesh",
+                   "omega_max_power": float(omega_pow[0]) if not batch else "per mesh",
                    "format": "SELL-32 (sigma=1)", "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (matrix > 129 MB)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-                     "kernel": "k_step_f64" if wl.precision == "fp64" else "k_step_f32",
+                     "kernel": ("k_step_f64" if wl.precision == "fp64" else "k_step_f32") if b == 1
+                     else ("k_step_blk<double>" if wl.precision == "fp64" else "k_step_blk<float>"),
                      "step_variant": stats["step_variant"], "step_grid": stats["step_grid"],
                      "step_us": step_ms * 1e3, "algorithmic_bytes_per_step": bytes_step},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(stats["kernel_launches"]),
         "clocks": clk.summary(),
-        "solve": {"accepted_pairs": res["n_pairs"], "k_used": res["k_used"], "time_steps": res["time_steps"],
-                  "max_rel_res": float(res["rel_res"].max()) if res["n_pairs"] else None,
+        "solve": {"accepted_pairs": [x["n_pairs"] for x in res] if batch else res[0]["n_pairs"],
+                  "k_used": res[0]["k_used"], "time_steps": steps_per_solve,
+                  "max_rel_res": max((float(x["rel_res"].max()) for x in res if x["n_pairs"]), default=None),
                   "max_eig_rel_err_vs_exact": eig_err, "filter_ms_share": stats["filter_ms"] / ms_local},
     }
+    if multi:
+        line["filter_multi_interval"] = multi
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -357,16 +415,19 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle as O
-    from fe_inputs import WORKLOADS, start_vectors
+    from fe_inputs import WORKLOADS
     wl = WORKLOADS[args.workload]
-    problem = wl.build()
+    problems, _ = workload_problems(wl)
+    big = max(range(len(problems)), key=lambda j: problems[j].n)
+    problem = problems[big]
+    iv = wl.mesh_intervals(problem)[0]
     S = problem.to_scipy()
-    omega_pow = O.power_iteration(S, problem.m, start_vectors(problem.n, 1, wl.seed)[0], wl.power_iters)
+    omega_pow = O.power_iteration(S, problem.m, start_block([problem], 1, wl.seed)[0], wl.power_iters)
     tau = wl.cfl * 2.0 / omega_pow
     per_step_budget = max(1.0, 60.0 / max(args.steps + args.warmup, 1))
     samples = []
     for i in range(args.warmup + args.steps):
-        v, steps, dt = oracle_sample(problem, tau, wl, per_step_budget)
+        v, steps, dt = oracle_sample(problem, tau, wl, per_step_budget, iv)
         if i >= args.warmup:
             samples.append((v, steps, dt))
     total_units = sum(problem.n * s for _, s, _ in samples)
@@ -377,10 +438,10 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / max(len(samples), 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "dofs": problem.n, "nnz": problem.nnz,
-                   "interval": [wl.omega_min, wl.omega_max], "L": wl.L, "kmax": wl.kmax, "tau": tau},
+                   "interval": list(iv), "L": wl.L, "kmax": wl.kmax, "tau": tau},
         "cpu_baseline": {"value": value, "unit": METRIC, "cores": cpu_cores_used(), "kind": "oracle",
                          "sample": f"each step = {samples[0][1] if samples else 0} leapfrog steps of the FP64 "
-                                   f"oracle filter on the full matrix"},
+                                   f"oracle filter on {problem.name}"},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

@@ -3,7 +3,7 @@
 This module defines the *problem*, never the eigensolver: it assembles the
 pencil ``S v = omega^2 M v`` of Sec. 2 (eq. def:basisMatrixEVP) for first-order
 (P1) finite elements on voxel domains split into Kuhn simplices, with the mass
-matrix lumped to its row sums (Remark rmk:mass_lumping), and it draws seeded
+matrix lumped to its row sums (Remark 2.1), and it draws seeded
 N(0,1) start vectors. No filter weight, time step, orthogonalisation or
 Rayleigh-Ritz arithmetic lives here.
 
@@ -288,17 +288,50 @@ def start_vectors(n: int, b: int = 1, seed: int = 0) -> np.ndarray:
 
 @dataclass(frozen=True)
 class Workload:
+    """A measured configuration: the problem(s), the filter and the solver sizes.
+
+    ``build`` returns one Problem or a list of them (a batch of meshes solved in one
+    context). ``intervals(problem)`` gives the F filter intervals [(wmin, wmax), ...]
+    of a mesh; the solver uses the first one."""
     name: str
-    build: object                 # () -> Problem
+    build: object                 # () -> Problem | list[Problem]
     omega_min: float
     omega_max: float
     L: int
     kmax: int
     precision: str = "fp64"       # "fp64" | "fp32"
-    b: int = 1
+    b: int = 1                    # block size (start vectors per mesh)
     cfl: float = 0.9              # tau = cfl * 2 / omega_max(S, M)
     power_iters: int = 300
     seed: int = 0
+    intervals: object = None      # (Problem) -> list of (wmin, wmax); None: [(omega_min, omega_max)]
+    check_every: int = 5
+    tol: float = 0.0              # acceptance; 0: 1e-8 (fp64) / 1e-5 (fp32)
+
+    def mesh_intervals(self, p: Problem):
+        return self.intervals(p) if self.intervals else [(self.omega_min, self.omega_max)]
+
+    def acceptance(self) -> float:
+        return self.tol or (1e-8 if self.precision == "fp64" else 1e-5)
+
+
+# 12 boxes of uneven size, uniform spacing h = 1/64 (extent = cells / 64): 29,791 ..
+# 857,375 dofs, 3.13 M in total
+BATCH12_CELLS = [(32, 32, 32), (40, 40, 40), (48, 40, 32), (48, 48, 48), (56, 48, 40), (64, 48, 48),
+                 (64, 64, 64), (72, 64, 56), (80, 64, 64), (80, 80, 80), (88, 80, 72), (96, 96, 96)]
+
+
+def batch12():
+    return [box_grid(c, extent=tuple(x / 64.0 for x in c), name="box_" + "x".join(map(str, c)))
+            for c in BATCH12_CELLS]
+
+
+def weyl_intervals(p: Problem, counts=(100, 200, 300, 400), width: int = 15):
+    """Four disjoint intervals in the lower spectrum of a box, each expected to hold
+    ~``width`` eigenvalues by Weyl's law N(omega) ~ V omega^3 / (6 pi^2)."""
+    V = float(np.prod(p.meta.get("extent", (1.0,) * len(p.cells))))
+    w = lambda N: (6.0 * math.pi ** 2 * N / V) ** (1.0 / 3.0)
+    return [(w(c), w(c + width)) for c in counts]
 
 
 WORKLOADS = {
@@ -310,4 +343,10 @@ WORKLOADS = {
                              40.0, 45.0, L=600, kmax=60),
     "cube128_fp32": Workload("cube128_fp32", lambda: box_grid((128, 128, 128)),
                              40.0, 45.0, L=600, kmax=60, precision="fp32"),
+    # 12 uneven boxes in one context, blocks of 8 start vectors, 4 intervals per mesh
+    "batch12_fp32": Workload("batch12_fp32", batch12, 0.0, 0.0, L=600, kmax=64, precision="fp32",
+                             b=8, intervals=weyl_intervals, check_every=16),
+    # voxelised flared tube r = 0.02 exp(3x), x in [0, 1], h = 1.74e-3 (~16 M dofs)
+    "horn16m_fp32": Workload("horn16m_fp32", lambda: flared_tube(1.74e-3), 60.0, 66.0, L=1000,
+                             kmax=200, precision="fp32", b=8, check_every=40),
 }

@@ -81,6 +81,10 @@ typedef struct kes_solve_opts {
   int32_t n_wanted;     /* stop as soon as this many pairs are accepted (0: run to kmax) */
   int32_t want_vectors; /* 1: return the accepted Ritz vectors B y (host, n x n_pairs col-major) */
   double tol;           /* acceptance: rel_res = ||S x - theta M x||_2 / (theta ||M x||_2) <= tol */
+  int32_t refine_sweeps; /* after the Krylov phase: sweeps of FP64 filtered subspace iteration on the
+                            in-interval Ritz vectors (X <- C X with the FP64 step kernels, then
+                            Rayleigh-Ritz); lifts FP32-form pairs to FP64 residuals. 0: none */
+  int32_t reserved;      /* set to 0 */
 } kes_solve_opts;
 
 /* Result of kes_krylov_solve; host memory owned by the library. */
@@ -99,6 +103,7 @@ typedef struct kes_result {
   double* ritz_omega2;   /* [n_ritz] every Ritz value of the last projection, ascending */
   double* ritz_rel_res;  /* [n_ritz] relative residual of the in-interval ones, NaN elsewhere */
   double solve_ms;       /* wall time of the call */
+  int64_t refine_steps;  /* FP64 leapfrog steps of the refinement sweeps (per filtered block) */
 } kes_result;
 
 /* Counters accumulated by a context since creation or kes_reset_stats. */

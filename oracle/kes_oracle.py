@@ -39,7 +39,7 @@ __all__ = [
     "weight", "alpha_table", "q_values", "beta_tilde", "filter_apply",
     "filter_apply_multi", "power_iteration", "m_inner", "m_norm",
     "orthonormalize_cgs2", "rayleigh_ritz", "ritz_residuals", "krylov_solve",
-    "block_krylov_solve", "KrylovResult", "BREAKDOWN_RATIO",
+    "block_krylov_solve", "refine_subspace", "KrylovResult", "BREAKDOWN_RATIO",
 ]
 
 BREAKDOWN_RATIO = 1e-10
@@ -368,3 +368,33 @@ def block_krylov_solve(S, m: np.ndarray, R0: np.ndarray, omega_min: float,
                         time_steps=steps, breakdown=breakdown, ritz_theta=theta,
                         ritz_rel_res=rel_all,
                         basis=B[:k] if keep_basis else None, history=history)
+
+
+def refine_subspace(S, m: np.ndarray, X: np.ndarray, omega_min: float, omega_max: float,
+                    tau: float, L: int, tol: float, sweeps: int = 1):
+    """Filtered subspace iteration on the rows of X (the fixed-dimension, FEAST-like
+    use of the filter mentioned in Sec. 4): each sweep filters every vector (X <- C X),
+    M-orthonormalises the result (CGS2, dependent vectors dropped), solves the
+    projected problem (eq. projevp) and keeps the Ritz vectors with omega in the
+    interval for the next sweep. Returns (theta_acc, rel_acc, X_acc, theta_inside,
+    rel_inside) of the last sweep, acceptance rel_res <= tol."""
+    alpha = alpha_table(omega_min, omega_max, tau, L)
+    X = np.atleast_2d(np.asarray(X, dtype=np.float64))
+    th_in = rel_in = np.zeros(0)
+    th_acc = rel_acc = np.zeros(0)
+    X_acc = np.zeros((0, X.shape[1]))
+    for _ in range(sweeps):
+        B = np.zeros((0, X.shape[1]))
+        for x in X:
+            v, nb, na = orthonormalize_cgs2(B, filter_apply(S, m, x, tau, alpha), m)
+            if v is not None:
+                B = np.vstack([B, v])
+        theta, Y = rayleigh_ritz(S, B)
+        omega = np.sqrt(theta)
+        inside = (omega >= omega_min) & (omega <= omega_max)
+        Xi, a, r = ritz_residuals(S, m, B, theta[inside], Y[:, inside])
+        th_in, rel_in = theta[inside], r
+        acc = r <= tol
+        th_acc, rel_acc, X_acc = th_in[acc], r[acc], Xi[acc]
+        X = Xi
+    return th_acc, rel_acc, X_acc, th_in, rel_in

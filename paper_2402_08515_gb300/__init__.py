@@ -60,7 +60,8 @@ class KesOpts(C.Structure):
 
 class KesSolveOpts(C.Structure):
     _fields_ = [("kmax", C.c_int32), ("check_every", C.c_int32), ("n_wanted", C.c_int32),
-                ("want_vectors", C.c_int32), ("tol", C.c_double)]
+                ("want_vectors", C.c_int32), ("tol", C.c_double), ("refine_sweeps", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class KesResult(C.Structure):
@@ -69,7 +70,7 @@ class KesResult(C.Structure):
                 ("omega", C.POINTER(C.c_double)), ("rel_res", C.POINTER(C.c_double)),
                 ("abs_res", C.POINTER(C.c_double)), ("vectors", C.POINTER(C.c_double)),
                 ("ritz_omega2", C.POINTER(C.c_double)), ("ritz_rel_res", C.POINTER(C.c_double)),
-                ("solve_ms", C.c_double)]
+                ("solve_ms", C.c_double), ("refine_steps", C.c_int64)]
 
 
 class KesStats(C.Structure):
@@ -252,7 +253,7 @@ def _result_dict(rp, st) -> dict:
                    time_steps=r.time_steps, omega2=_arr(r.omega2, p), omega=_arr(r.omega, p),
                    rel_res=_arr(r.rel_res, p), abs_res=_arr(r.abs_res, p),
                    ritz_omega2=_arr(r.ritz_omega2, r.n_ritz), ritz_rel_res=_arr(r.ritz_rel_res, r.n_ritz),
-                   solve_ms=r.solve_ms, vectors=None)
+                   solve_ms=r.solve_ms, refine_steps=r.refine_steps, vectors=None)
         if r.vectors and p > 0:
             out["vectors"] = np.ctypeslib.as_array(r.vectors, shape=(p * r.n,)).copy().reshape(p, r.n)
     finally:

@@ -42,16 +42,44 @@ __device__ __forceinline__ void load_row(const double* __restrict__ p, double (&
     v[2 * q] = t.x; v[2 * q + 1] = t.y;
   }
 }
-// plain (coherent) loads and stores of a row
-template <typename T, int NB>
-__device__ __forceinline__ void load_plain(const T* p, T (&v)[NB]) {
+// Coherent loads and stores of one row's NB contiguous values with 8- or 16-byte
+// vector accesses (rows are NB * sizeof(T) aligned): a lane moves its whole row in
+// 1-4 instructions instead of NB scalar ones that each touch a separate sector.
+template <int NB>
+__device__ __forceinline__ void load_plain(const float* p, float (&v)[NB]) {
+  if constexpr (NB >= 4) {
 #pragma unroll
-  for (int j = 0; j < NB; ++j) v[j] = p[j];
+    for (int q = 0; q < NB / 4; ++q) {
+      const float4 t = reinterpret_cast<const float4*>(p)[q];
+      v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+    }
+  } else {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    v[0] = t.x; v[1] = t.y;
+  }
 }
-template <typename T, int NB>
-__device__ __forceinline__ void store_row(T* p, const T (&v)[NB]) {
+template <int NB>
+__device__ __forceinline__ void load_plain(const double* p, double (&v)[NB]) {
 #pragma unroll
-  for (int j = 0; j < NB; ++j) p[j] = v[j];
+  for (int q = 0; q < NB / 2; ++q) {
+    const double2 t = reinterpret_cast<const double2*>(p)[q];
+    v[2 * q] = t.x; v[2 * q + 1] = t.y;
+  }
+}
+template <int NB>
+__device__ __forceinline__ void store_row(float* p, const float (&v)[NB]) {
+  if constexpr (NB >= 4) {
+#pragma unroll
+    for (int q = 0; q < NB / 4; ++q)
+      reinterpret_cast<float4*>(p)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  } else {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  }
+}
+template <int NB>
+__device__ __forceinline__ void store_row(double* p, const double (&v)[NB]) {
+#pragma unroll
+  for (int q = 0; q < NB / 2; ++q) reinterpret_cast<double2*>(p)[q] = make_double2(v[2 * q], v[2 * q + 1]);
 }
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
@@ -107,50 +135,63 @@ __global__ void __launch_bounds__(256, MINB)
     const int64_t row = s * kSliceC + lane;
     const T t2m = ld_cs(tau2m + row);
     T xi[NB], pi[NB], un[NB];
-    load_plain<T, NB>(x + row * NB, xi);
+    load_plain<NB>(x + row * NB, xi);
     if constexpr (FIRST) {
 #pragma unroll
       for (int j = 0; j < NB; ++j) pi[j] = xi[j];
     } else {
-      load_plain<T, NB>(prev + row * NB, pi);
+      load_plain<NB>(prev + row * NB, pi);
     }
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
       if constexpr (kF32) un[j] = fmaf(-t2m, sum0[j] + sum1[j], __fsub_rn(__fmul_rn(2.0f, xi[j]), pi[j]));
       else un[j] = fma(-t2m, sum0[j] + sum1[j], 2.0 * xi[j] - pi[j]);
     }
-    if (!LAST) store_row<T, NB>(out + row * NB, un);
+    if (!LAST) store_row<NB>(out + row * NB, un);
     bool bad = false;
     for (int f = 0; f < F; ++f) {
       const int64_t ai = (mesh * F + f) * Lp1;
       const int64_t at = f * acc_stride + row * NB;
       if constexpr (kF32) {
         const float a_hi = ahi[ai + step + 1], a_lo = alo[ai + step + 1];
+        float as[NB], ac[NB];
+        load_plain<NB>(acc_s + at, as);
+        load_plain<NB>(acc_c + at, ac);
+        double v64[NB];
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
           const float p = __fmul_rn(a_hi, un[j]);
           const float pe = fmaf(a_lo, un[j], fmaf(a_hi, un[j], -p));
           float sn, e;
-          two_sum(acc_s[at + j], p, sn, e);
-          const float cn = __fadd_rn(acc_c[at + j], __fadd_rn(e, pe));
-          if (LAST) {
-            const double v = static_cast<double>(sn) + static_cast<double>(cn);
-            acc64[at + j] = v;
-            bad |= !isfinite(v);
-          } else {
-            acc_s[at + j] = sn;
-            acc_c[at + j] = cn;
-          }
+          two_sum(as[j], p, sn, e);
+          const float cn = __fadd_rn(ac[j], __fadd_rn(e, pe));
+          as[j] = sn;
+          ac[j] = cn;
+          v64[j] = static_cast<double>(sn) + static_cast<double>(cn);
+          if (LAST) bad |= !isfinite(v64[j]);
+        }
+        if (LAST) {
+          store_row<NB>(acc64 + at, v64);
+        } else {
+          store_row<NB>(acc_s + at, as);
+          store_row<NB>(acc_c + at, ac);
         }
       } else {
         const double a1 = ahi[ai + step + 1];
         const double a0 = FIRST ? ahi[ai] : 0.0;
+        double na[NB];
+        if constexpr (FIRST) {
+#pragma unroll
+          for (int j = 0; j < NB; ++j) na[j] = a0 * xi[j];
+        } else {
+          load_plain<NB>(acc_s + at, na);
+        }
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
-          const double na = fma(a1, un[j], FIRST ? a0 * xi[j] : acc_s[at + j]);
-          acc_s[at + j] = na;
-          if (LAST) bad |= !isfinite(na);
+          na[j] = fma(a1, un[j], na[j]);
+          if (LAST) bad |= !isfinite(na[j]);
         }
+        store_row<NB>(acc_s + at, na);
       }
     }
     if (LAST && bad) atomicOr(flag, 1);

@@ -77,6 +77,7 @@ struct LaunchCount {
 
 struct GraphEntry {
   int NB = 0;
+  bool fp64 = true;
   cudaGraphExec_t exec = nullptr;
   int64_t nodes = 0;
 };
@@ -250,21 +251,28 @@ void block_out(kes_ctx* c, const double* src, int NB, int nb, double* dst, int32
 // --------------------------------------------------------------- filter
 // Issues the L fused steps of one filter application of an NB-column block on the
 // context stream: stage_in -> stage_out (F filtered blocks).
-int64_t issue_filter_steps(kes_ctx* c, int NB) {
+int64_t issue_filter_steps(kes_ctx* c, int NB, bool fp64) {
   const int64_t before = g_launches;
   const int L = c->L, F = c->F;
   const int64_t stride = c->n_pad * NB;
-  if (c->opts.precision == KES_PREC_FP64) {
+  if (fp64) {
+    // in a context of the FP32 form the launch shape was tuned for the FP32 kernels:
+    // the FP64 steps of the refinement take a fixed register-staged shape
+    LaunchCfg cfg = c->cfg;
+    if (c->opts.precision != KES_PREC_FP64) {
+      cfg.variant = 3;
+      cfg.grid_step = cfg.n_sm * step_blocks_per_sm(false, 3, cfg.block_step);
+    }
     for (int s = 0; s < L; ++s) {
       const bool first = s == 0, last = s == L - 1;
       const double* x = s == 0 ? c->stage_in : c->U64[(s - 1) & 1];
       const double* prev = s <= 1 ? c->stage_in : c->U64[s & 1];
       double* out = c->U64[s & 1];
       if (NB == 1)
-        launch_step_f64(c->A, c->cfg, c->stream, first, c->tau2m64, x, prev, out, c->stage_out, stride, F, c->alpha64,
+        launch_step_f64(c->A, cfg, c->stream, first, c->tau2m64, x, prev, out, c->stage_out, stride, F, c->alpha64,
                         L, s, last, c->d_flag);
       else
-        launch_step_blk_f64(c->A, c->cfg, c->stream, NB, first, last, c->tau2m64, x, prev, out, c->stage_out, stride,
+        launch_step_blk_f64(c->A, cfg, c->stream, NB, first, last, c->tau2m64, x, prev, out, c->stage_out, stride,
                             F, c->alpha64, L, s, c->d_flag);
     }
   } else {
@@ -285,7 +293,14 @@ int64_t issue_filter_steps(kes_ctx* c, int NB) {
   return g_launches - before;
 }
 
-void run_filter(kes_ctx* c, int NB) {
+// The FP64 step kernels in a context of the FP32 form (used by the FP64 refinement).
+void ensure_fp64_state(kes_ctx* c) {
+  if (c->U64[0]) return;
+  for (int j = 0; j < 2; ++j) c->U64[j] = c->dzero_n<double>(c->n_pad * c->NBcap);
+}
+
+void run_filter(kes_ctx* c, int NB, bool fp64) {
+  if (fp64) ensure_fp64_state(c);
   cudaEvent_t e0 = c->get_event(), e1 = c->get_event();
   KES_CUDA(cudaEventRecord(e0, c->stream));
   if (c->opts.use_graph) {
@@ -296,16 +311,17 @@ void run_filter(kes_ctx* c, int NB) {
     }
     GraphEntry* ge = nullptr;
     for (auto& g : c->graphs)
-      if (g.NB == NB) ge = &g;
+      if (g.NB == NB && g.fp64 == fp64) ge = &g;
     if (!ge) {
       cudaGraph_t graph;
       KES_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-      const int64_t nodes = issue_filter_steps(c, NB);
+      const int64_t nodes = issue_filter_steps(c, NB, fp64);
       cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
       g_launches -= nodes;  // captured, not launched
       KES_CUDA(ce);
       GraphEntry g;
       g.NB = NB;
+      g.fp64 = fp64;
       g.nodes = nodes;
       ce = cudaGraphInstantiate(&g.exec, graph, 0);
       cudaGraphDestroy(graph);
@@ -316,7 +332,7 @@ void run_filter(kes_ctx* c, int NB) {
     KES_CUDA(cudaGraphLaunch(ge->exec, c->stream));
     g_launches += ge->nodes;  // every node of the replayed graph is a kernel launch
   } else {
-    issue_filter_steps(c, NB);
+    issue_filter_steps(c, NB, fp64);
     KES_CHECK_LAUNCH();
   }
   KES_CUDA(cudaEventRecord(e1, c->stream));
@@ -346,7 +362,7 @@ kes_status check_flag(kes_ctx* c) {
   c->sync();
   if (flag) {
     KES_CUDA(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
-    return KES_ERR_UNSTABLE;
+    return (flag & 2) ? KES_ERR_TIMEOUT : KES_ERR_UNSTABLE;
   }
   return KES_OK;
 }
@@ -379,6 +395,21 @@ SellDev mesh_sell(const kes_ctx* c, const MeshInfo& m) {
   return a;
 }
 
+// Makes launch shape v of the single-vector step kernel current; false if it cannot run
+// on this matrix (a TMA shape whose stage would not fit in shared memory).
+bool select_variant(kes_ctx* c, int v) {
+  const bool fp32 = c->opts.precision == KES_PREC_FP32;
+  if (v >= kRegStepVariants) {
+    const TmaShape sh = tma_variant_shape(v, c->cfg.tma.wmax);
+    if (!tma_shape_fits(fp32, sh)) return false;
+    KES_CUDA(tma_prepare(fp32, sh));
+    c->cfg.tma = sh;
+  }
+  c->cfg.variant = v;
+  c->cfg.grid_step = c->cfg.n_sm * step_blocks_per_sm(fp32, v, c->cfg.block_step);
+  return true;
+}
+
 // Times every launch shape of the step kernels on this matrix (a few steps on zeroed
 // scratch state, CUDA events) and keeps the fastest. All shapes compute the same sums.
 void tune_steps(kes_ctx* c) {
@@ -389,11 +420,11 @@ void tune_steps(kes_ctx* c) {
   float* a32 = c->dzero_n<float>(na);
   cudaEvent_t e0 = c->get_event(), e1 = c->get_event();
   auto timed = [&](auto&& launch) {
-    launch(2);
+    launch(3);
     float best = 3.0e38f;
-    for (int rep = 0; rep < 2; ++rep) {
+    for (int rep = 0; rep < 3; ++rep) {
       KES_CUDA(cudaEventRecord(e0, c->stream));
-      launch(6);
+      launch(16);
       KES_CUDA(cudaEventRecord(e1, c->stream));
       KES_CUDA(cudaEventSynchronize(e1));
       float ms = 0.f;
@@ -407,8 +438,7 @@ void tune_steps(kes_ctx* c) {
   int best = 0;
   float best_ms = 3.0e38f;
   for (int v = 0; v < step_variant_count(); ++v) {
-    c->cfg.variant = v;
-    c->cfg.grid_step = c->cfg.n_sm * step_blocks_per_sm(fp32, v, c->cfg.block_step);
+    if (!select_variant(c, v)) continue;
     const float ms = timed([&](int count) {
       for (int i = 0; i < count; ++i) {
         if (fp32)
@@ -424,8 +454,7 @@ void tune_steps(kes_ctx* c) {
       best = v;
     }
   }
-  c->cfg.variant = best;
-  c->cfg.grid_step = c->cfg.n_sm * step_blocks_per_sm(fp32, best, c->cfg.block_step);
+  select_variant(c, best);
   // block kernel at the context's block width
   if (c->NBcap > 1) {
     const int NB = c->NBcap;
@@ -538,6 +567,9 @@ void build_context(kes_ctx* c, int nm, const int64_t* n, const int64_t* const* r
     }
   }
   sp[n_slices] = at;
+  int64_t wmax = 0;
+  for (int64_t sl = 0; sl < n_slices; ++sl) wmax = std::max(wmax, (sp[sl + 1] - sp[sl]) / kSliceC);
+  c->cfg.tma.wmax = static_cast<int>(wmax);
   sells.clear();
   int64_t* d_sp = c->dalloc_n<int64_t>(n_slices + 1);
   int32_t* d_col = c->dalloc_n<int32_t>(nnz_pad);
@@ -626,8 +658,7 @@ kes_status create_impl(kes_ctx** out, int32_t nm, const int64_t* n, const int64_
     const bool fp32 = c->opts.precision == KES_PREC_FP32;
     c->cfg.n_sm = n_sm;
     c->cfg.block_step = 256;
-    c->cfg.variant = c->opts.step_variant;
-    c->cfg.grid_step = n_sm * step_blocks_per_sm(fp32, c->cfg.variant, c->cfg.block_step);
+    if (!select_variant(c, c->opts.step_variant)) throw KesError{KES_ERR_UNSUPPORTED};
     c->cfg.variant_blk = 0;
     c->cfg.grid_blk = n_sm * blk_blocks_per_sm(fp32, c->NBcap > 1 ? c->NBcap : 2, 0, c->cfg.block_step);
     if (c->opts.autotune) tune_steps(c);
@@ -809,11 +840,12 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
 
     // Orthogonalise column jj of Wc against each mesh's basis (two classical passes in
     // the M-inner product) and append the vectors that are not dependent (Algorithm 2.5).
+    std::vector<char> want(nm, 1);  // meshes taking part in the current block step
     auto append_column = [&](int jj) {
       cudaEvent_t ev = other_begin();
       std::vector<char> active(nm, 0);
       for (int j = 0; j < nm; ++j) {
-        if (ms[j].done || ms[j].k >= kmax) continue;
+        if (!want[j] || ms[j].done || ms[j].k >= kmax) continue;
         active[j] = 1;
         const MeshInfo& mi = c->meshes[j];
         double* w = c->Wc + static_cast<int64_t>(jj) * np + mi.row_off;
@@ -838,7 +870,7 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
       c->sync();
       if (flag) {
         KES_CUDA(cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
-        throw KesError{KES_ERR_UNSTABLE};
+        throw KesError{(flag & 2) ? KES_ERR_TIMEOUT : KES_ERR_UNSTABLE};
       }
       ev = other_begin();
       std::vector<char> added(nm, 0);
@@ -952,7 +984,7 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
       KES_CUDA(cudaMemcpyAsync(c->colsel, colsel.data(), colsel.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
       launch_pack_basis(s, B, np, c->colsel, c->slice_mesh, c->stage_in, NB, np);
       KES_CHECK_LAUNCH();
-      run_filter(c, NB);  // stage_in -> stage_out
+      run_filter(c, NB, c->opts.precision == KES_PREC_FP64);  // stage_in -> stage_out
       steps += c->L;
       launch_unpack_block(s, c->stage_out, NB, c->Wc, np);
       KES_CHECK_LAUNCH();
@@ -975,12 +1007,90 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
         }
       }
     }
-    // final projection and results
+    for (int j = 0; j < nm; ++j)
+      if (ms[j].kproj != ms[j].k) project(j);
+
+    // FP64 refinement: sweeps of filtered subspace iteration on the in-interval Ritz
+    // vectors (Sec. 4 mentions fixed-dimension, FEAST-like use of the filter): X <- C X
+    // with the FP64 step kernels, M-orthonormalise, Rayleigh-Ritz, residuals.
+    int64_t refine_steps = 0;
+    for (int sweep = 0; sweep < so.refine_sweeps; ++sweep) {
+      std::vector<int> pcount(nm, 0);
+      int pmax = 0;
+      for (int j = 0; j < nm; ++j) {
+        MeshSolve& m = ms[j];
+        int p = 0;
+        for (size_t q = 0; q < m.last_rel.size(); ++q) p += std::isnan(m.last_rel[q]) ? 0 : 1;
+        pcount[j] = p;
+        pmax = std::max(pmax, p);
+      }
+      if (pmax == 0) break;
+      const size_t need = static_cast<size_t>(pmax) * np;
+      if (need > c->Xd_cap) {
+        c->dfree(c->Xd);
+        c->Xd = c->dalloc_n<double>(need);
+        c->Xd_cap = need;
+      }
+      KES_CUDA(cudaMemsetAsync(c->Xd, 0, need * sizeof(double), s));
+      // Ritz vectors of every in-interval Ritz value: Xd[:, q] = B y_q on the mesh's rows
+      for (int j = 0; j < nm; ++j) {
+        if (pcount[j] == 0) continue;
+        MeshSolve& m = ms[j];
+        const MeshInfo& mi = c->meshes[j];
+        const int kk = m.k;
+        std::vector<double> Hh(static_cast<size_t>(kk) * kk, 0.0);
+        KES_CUDA(cudaMemcpy2DAsync(Hh.data(), kk * sizeof(double), Hcol(j, 0), c->kcap * sizeof(double),
+                                   kk * sizeof(double), kk, cudaMemcpyDeviceToHost, s));
+        c->sync();
+        for (int i = 0; i < kk; ++i)
+          for (int r = i + 1; r < kk; ++r)
+            Hh[static_cast<size_t>(i) * kk + r] = Hh[static_cast<size_t>(r) * kk + i];
+        std::vector<double> theta(kk), Y(static_cast<size_t>(kk) * kk), Ysel;
+        if (!sym_eig(kk, Hh.data(), theta.data(), Y.data())) throw KesError{KES_ERR_CUDA};
+        for (int q = 0; q < kk; ++q)
+          if (!std::isnan(m.last_rel[q]))
+            Ysel.insert(Ysel.end(), Y.begin() + static_cast<size_t>(q) * kk, Y.begin() + static_cast<size_t>(q + 1) * kk);
+        KES_CUDA(cudaMemcpyAsync(c->Yd, Ysel.data(), Ysel.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        launch_gemm_bx(s, B + mi.row_off, np, kk, c->Yd, pcount[j], c->Xd + mi.row_off, np, mi.n_pad);
+        KES_CHECK_LAUNCH();
+        c->sync();  // Yd is reused by the next mesh
+      }
+      // filter them with the FP64 kernels, NB at a time, into fresh bases
+      const int NBr = c->NBcap;
+      for (int j = 0; j < nm; ++j) {
+        want[j] = pcount[j] > 0;
+        if (want[j]) {
+          ms[j].k = 0;
+          ms[j].done = false;
+        }
+      }
+      std::vector<int32_t> csel(static_cast<size_t>(nm) * NBr, -1);
+      for (int q0 = 0; q0 < pmax; q0 += NBr) {
+        for (int j = 0; j < nm; ++j)
+          for (int jj = 0; jj < NBr; ++jj) csel[j * NBr + jj] = (q0 + jj < pcount[j]) ? q0 + jj : -1;
+        KES_CUDA(cudaMemcpyAsync(c->colsel, csel.data(), csel.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        launch_pack_basis(s, c->Xd, np, c->colsel, c->slice_mesh, c->stage_in, NBr, np);
+        KES_CHECK_LAUNCH();
+        run_filter(c, NBr, true);
+        refine_steps += c->L;
+        launch_unpack_block(s, c->stage_out, NBr, c->Wc, np);
+        KES_CHECK_LAUNCH();
+        for (int jj = 0; jj < NBr && q0 + jj < pmax; ++jj) {
+          for (int j = 0; j < nm; ++j) want[j] = q0 + jj < pcount[j];
+          append_column(jj);
+        }
+      }
+      for (int j = 0; j < nm; ++j) {
+        if (pcount[j] > 0) project(j);
+        want[j] = 1;
+      }
+    }
+
+    // results
     bool any_breakdown = false;
     for (int j = 0; j < nm; ++j) {
       MeshSolve& m = ms[j];
       const MeshInfo& mi = c->meshes[j];
-      if (m.kproj != m.k) project(j);
       any_breakdown |= m.breakdown;
       kes_result* r = res[j];
       const int p = static_cast<int>(m.acc_theta.size());
@@ -990,6 +1100,7 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
       r->breakdown = m.breakdown ? 1 : 0;
       r->n_ritz = static_cast<int32_t>(m.last_theta.size());
       r->time_steps = steps;
+      r->refine_steps = refine_steps;
       r->omega2 = hdup(m.acc_theta);
       std::vector<double> om(p);
       for (int q = 0; q < p; ++q) om[q] = std::sqrt(m.acc_theta[q]);
@@ -1172,7 +1283,7 @@ kes_status kes_filter_apply(kes_ctx* c, const double* r_in, double* r_out, int32
   return guarded([&]() -> kes_status {
     const int NB = nb_for(b);
     block_in(c, r_in, b, mem, NB, c->stage_in);
-    run_filter(c, NB);
+    run_filter(c, NB, c->opts.precision == KES_PREC_FP64);
     for (int f = 0; f < c->F; ++f)
       block_out(c, c->stage_out + static_cast<int64_t>(f) * c->n_pad * NB, NB, b,
                 r_out + static_cast<int64_t>(f) * b * c->n, mem);
@@ -1203,7 +1314,7 @@ kes_status kes_krylov_solve(kes_ctx* c, const double* r0, int32_t mem, const kes
   kes_solve_opts so;
   if (so_in) so = *so_in;
   else kes_solve_opts_default(&so);
-  if (so.kmax < 1 || so.check_every < 1 || !(so.tol > 0.0)) return KES_ERR_ARG;
+  if (so.kmax < 1 || so.check_every < 1 || !(so.tol > 0.0) || so.refine_sweeps < 0) return KES_ERR_ARG;
   return block_solve_impl(c, r0, 1, mem, so, out);
 }
 
@@ -1217,7 +1328,7 @@ kes_status kes_block_krylov_solve(kes_ctx* c, const double* R0, int32_t b, int32
   kes_solve_opts so;
   if (so_in) so = *so_in;
   else kes_solve_opts_default(&so);
-  if (so.kmax < b || so.check_every < 1 || !(so.tol > 0.0)) return KES_ERR_ARG;
+  if (so.kmax < b || so.check_every < 1 || !(so.tol > 0.0) || so.refine_sweeps < 0) return KES_ERR_ARG;
   return block_solve_impl(c, R0, b, mem, so, out);
 }
 

@@ -143,3 +143,27 @@ def test_batched_block_solver_per_mesh(meshes):
             assert np.min(np.abs(exact - th)) <= 1e-10 * th
         oref = O.block_krylov_solve(p.to_scipy(), p.m, Rs[j], wmin[j, 0], wmax[j, 0], taus[j], 250, 80, 1e-8)
         assert abs(r["n_pairs"] - len(oref.omega2)) <= 2
+
+
+@pytest.mark.parametrize("b", [1, 2])
+def test_fp32_solve_with_fp64_refinement_reaches_fp64_residuals(b):
+    p = square_grid(32)
+    S = p.to_scipy()
+    tau = _tau(p)
+    exact = spectra.eigenvalues_in(p.cells, p.h, 20.0, 30.0)
+    R = start_vectors(p.n, b, 3)
+    so = K.kes_solve_opts_default()
+    so.kmax, so.tol, so.want_vectors, so.refine_sweeps = 100, 1e-8, 1, 2
+    with K.Context(p, precision="fp32", block_b=b) as c:
+        K.kes_set_filter(c.handle, 20.0, 30.0, tau, 300)
+        res = K.kes_block_krylov_solve(c.handle, R, b, so)[0]
+    distinct, _ = spectra.distinct(exact)
+    found, _ = spectra.distinct(res["omega2"])
+    print(f"b={b}: refined FP32 accepted {res['n_pairs']} pairs ({len(found)} of {len(distinct)} distinct) "
+          f"after {res['refine_steps']} FP64 steps")
+    assert res["refine_steps"] > 0
+    assert len(found) >= len(distinct) - 1
+    for th, x in zip(res["omega2"], res["vectors"]):
+        assert np.min(np.abs(exact - th)) <= 1e-10 * th
+        r = S @ x - th * p.m * x
+        assert np.linalg.norm(r) <= 1.01e-8 * th * np.linalg.norm(p.m * x)

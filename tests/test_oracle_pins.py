@@ -322,3 +322,36 @@ def test_block_solver_resolves_multiple_eigenvalues():
     np.testing.assert_allclose(np.sort(res.omega2), exact, rtol=1e-10)
     G = res.vectors @ (p.m[:, None] * res.vectors.T)     # accepted vectors M-orthonormal
     np.testing.assert_allclose(G, np.eye(len(exact)), atol=1e-8)
+
+
+# ---------------------------------------------------------------- FP64 refinement
+
+def test_refinement_keeps_exact_eigenvectors():
+    p = square_grid(20)
+    S = p.to_scipy()
+    tau = 0.9 * 2 / math.sqrt(spectra.box_spectrum(p.cells, p.h).max())
+    modes = [(2, 3), (3, 2), (4, 1)]
+    X = np.stack([spectra.box_eigenvector(p.cells, k) for k in modes])
+    lam = sorted(4 * 400 * (math.sin(a * math.pi / 40) ** 2 + math.sin(b * math.pi / 40) ** 2) for a, b in modes)
+    th, rel, Xa, thi, reli = O.refine_subspace(S, p.m, X, 0.9 * math.sqrt(lam[0]), 1.1 * math.sqrt(lam[-1]),
+                                               tau, 150, 1e-10)
+    np.testing.assert_allclose(np.sort(th), lam, rtol=1e-12)
+    assert np.all(rel < 1e-12)
+
+
+def test_refinement_damps_noise_by_the_filter_contrast():
+    p = square_grid(24)
+    S = p.to_scipy()
+    tau = 0.9 * 2 / math.sqrt(spectra.box_spectrum(p.cells, p.h).max())
+    k = (3, 5)
+    v = spectra.box_eigenvector(p.cells, k)
+    lam = 4 * 576 * (math.sin(3 * math.pi / 48) ** 2 + math.sin(5 * math.pi / 48) ** 2)
+    noisy = v + 1e-5 * np.abs(v).max() * start_vectors(p.n, 1, 8)[0]
+    rq = (noisy @ (S @ noisy)) / (noisy @ (p.m * noisy))
+    rel0 = np.linalg.norm(S @ noisy - rq * p.m * noisy) / (rq * np.linalg.norm(p.m * noisy))
+    # neighbours at omega = 17.57 and 18.64: a narrow interval and a long filter isolate
+    # omega = 18.05 (its twin (5, 3) is the same eigenvalue, so its noise is harmless)
+    th, rel, Xa, thi, reli = O.refine_subspace(S, p.m, noisy[None, :], 17.8, 18.3, tau, 2000, 1e-8)
+    # the largest |beta~| outside the interval is ~0.08 against ~0.95 inside
+    assert len(thi) == 1 and thi[0] == pytest.approx(lam, rel=1e-12)
+    assert reli[0] < 1e-3 * rel0
