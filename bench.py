@@ -52,8 +52,11 @@ def parse_args(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="solve", choices=["solve", "filter"],
-                    help="filter: one filter application only (small profiling runs)")
+    ap.add_argument("--mode", default="solve", choices=["solve", "filter", "tts"],
+                    help="filter: one filter application only (small profiling runs); tts: time to "
+                         "converged eigenpairs at residual 1e-8, FP64 form against the FP32 forms with FP64 "
+                         "refinement")
+    ap.add_argument("--kmax", type=int, default=200, help="Krylov dimension of --mode tts")
     ap.add_argument("--L", type=int, default=0, help="override the workload's time steps (--mode filter)")
     ap.add_argument("--variant", type=int, default=None,
                     help="fixed step-kernel launch shape instead of the autotuner's choice")
@@ -447,8 +450,51 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_tts(args):
+    """Time to eigenpairs with rel_res <= 1e-8 on the cube: the plain FP64 form and the
+    FP32 forms (single vector and blocks of 8) followed by FP64 refinement sweeps."""
+    import numpy as np
+    import torch
+
+    import paper_2402_08515_gb300 as K
+    from fe_inputs import WORKLOADS, start_vectors
+    from oracle import spectra
+
+    wl = WORKLOADS["cube128_fp64"]
+    p = wl.build()
+    exact = spectra.eigenvalues_in(p.cells, p.h, wl.omega_min, wl.omega_max)
+    distinct, _ = spectra.distinct(exact)
+    v0 = start_vectors(p.n, 1, wl.seed)[0]
+    runs = []
+    for name, prec, b, refine in (("fp64", "fp64", 1, 0), ("fp32+refine", "fp32", 1, 2),
+                                  ("fp32_block8+refine", "fp32", 8, 2)):
+        with K.Context(p, precision=prec, block_b=b) as c:
+            w, _ = K.kes_estimate_omega_max(c.handle, wl.power_iters, v0)
+            K.kes_set_filter(c.handle, wl.omega_min, wl.omega_max, wl.cfl * 2 / w, wl.L)
+            so = K.kes_solve_opts_default()
+            so.kmax, so.tol, so.check_every, so.refine_sweeps, so.want_vectors = args.kmax, 1e-8, 20, refine, 0
+            R = start_vectors(p.n, b, wl.seed + 1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = K.kes_block_krylov_solve(c.handle, R, b, so)[0]
+            dt = time.perf_counter() - t0
+            found, _ = spectra.distinct(res["omega2"])
+            err = max((float(np.min(np.abs(exact - t)) / t) for t in res["omega2"]), default=None)
+            runs.append({"form": name, "b": b, "kmax": args.kmax, "seconds": dt, "accepted_pairs": res["n_pairs"],
+                         "accepted_distinct": len(found), "distinct_in_interval": len(distinct),
+                         "max_rel_res": float(res["rel_res"].max()) if res["n_pairs"] else None,
+                         "max_eig_rel_err_vs_exact": err, "leapfrog_steps": res["time_steps"],
+                         "fp64_refine_steps": res["refine_steps"]})
+            print(json.dumps(runs[-1]), file=sys.stderr, flush=True)
+    print(json.dumps({"mode": "tts", "workload": "cube128", "interval": [wl.omega_min, wl.omega_max], "L": wl.L,
+                      "tol": 1e-8, "runs": runs}), flush=True)
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.mode == "tts":
+        run_tts(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -91,7 +91,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
 
 template <typename T, int NB, bool FIRST, bool LAST, int MINB>
 __global__ void __launch_bounds__(256, MINB)
-    k_step_blk(SellDev A, const T* __restrict__ tau2m, const T* __restrict__ x, const T* prev, T* out, T* acc_s,
+    k_step_blk(SellDev A, const T* __restrict__ x, const T* prev, T* out, T* acc_s,
                T* acc_c, double* acc64, int64_t acc_stride, int F, const T* __restrict__ ahi,
                const T* __restrict__ alo, int Lp1, int step, int* flag) {
   constexpr bool kF32 = std::is_same<T, float>::value;
@@ -107,33 +107,7 @@ __global__ void __launch_bounds__(256, MINB)
     const int64_t mesh = A.slice_mesh ? A.slice_mesh[s] : 0;
     const T* vp = val + beg + lane;
     const int32_t* cp = A.col + beg + lane;
-    // even entries into sum0, odd into sum1 (the order of the single-vector kernels)
-    T sum0[NB], sum1[NB];
-#pragma unroll
-    for (int j = 0; j < NB; ++j) sum0[j] = sum1[j] = T(0);
-    int k = 0;
-    for (; k + 2 <= w; k += 2) {
-      const int32_t c0 = ld_cs(cp + k * kSliceC), c1 = ld_cs(cp + (k + 1) * kSliceC);
-      const T v0 = ld_cs(vp + k * kSliceC), v1 = ld_cs(vp + (k + 1) * kSliceC);
-      T x0[NB], x1[NB];
-      load_row<NB>(x + static_cast<int64_t>(c0) * NB, x0);
-      load_row<NB>(x + static_cast<int64_t>(c1) * NB, x1);
-#pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        sum0[j] = fma(v0, x0[j], sum0[j]);
-        sum1[j] = fma(v1, x1[j], sum1[j]);
-      }
-    }
-    if (k < w) {
-      const int32_t c0 = ld_cs(cp + k * kSliceC);
-      const T v0 = ld_cs(vp + k * kSliceC);
-      T x0[NB];
-      load_row<NB>(x + static_cast<int64_t>(c0) * NB, x0);
-#pragma unroll
-      for (int j = 0; j < NB; ++j) sum0[j] = fma(v0, x0[j], sum0[j]);
-    }
     const int64_t row = s * kSliceC + lane;
-    const T t2m = ld_cs(tau2m + row);
     T xi[NB], pi[NB], un[NB];
     load_plain<NB>(x + row * NB, xi);
     if constexpr (FIRST) {
@@ -142,10 +116,30 @@ __global__ void __launch_bounds__(256, MINB)
     } else {
       load_plain<NB>(prev + row * NB, pi);
     }
+    // u_{n+1} = (2 u_n - u_{n-1}) + A u_n: one FMA chain per column in entry order,
+    // seeded like the single-vector kernels, so every column rounds like them
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
-      if constexpr (kF32) un[j] = fmaf(-t2m, sum0[j] + sum1[j], __fsub_rn(__fmul_rn(2.0f, xi[j]), pi[j]));
-      else un[j] = fma(-t2m, sum0[j] + sum1[j], 2.0 * xi[j] - pi[j]);
+      if constexpr (kF32) un[j] = __fsub_rn(__fmul_rn(2.0f, xi[j]), pi[j]);
+      else un[j] = 2.0 * xi[j] - pi[j];
+    }
+    int k = 0;
+    for (; k + 2 <= w; k += 2) {
+      const int32_t c0 = ld_cs(cp + k * kSliceC), c1 = ld_cs(cp + (k + 1) * kSliceC);
+      const T v0 = ld_cs(vp + k * kSliceC), v1 = ld_cs(vp + (k + 1) * kSliceC);
+      T x0[NB], x1[NB];
+      load_row<NB>(x + static_cast<int64_t>(c0) * NB, x0);
+      load_row<NB>(x + static_cast<int64_t>(c1) * NB, x1);
+#pragma unroll
+      for (int j = 0; j < NB; ++j) un[j] = fma(v1, x1[j], fma(v0, x0[j], un[j]));
+    }
+    if (k < w) {
+      const int32_t c0 = ld_cs(cp + k * kSliceC);
+      const T v0 = ld_cs(vp + k * kSliceC);
+      T x0[NB];
+      load_row<NB>(x + static_cast<int64_t>(c0) * NB, x0);
+#pragma unroll
+      for (int j = 0; j < NB; ++j) un[j] = fma(v0, x0[j], un[j]);
     }
     if (!LAST) store_row<NB>(out + row * NB, un);
     bool bad = false;
@@ -202,10 +196,10 @@ __global__ void __launch_bounds__(256, MINB)
 #define KES_BLK_VARIANTS(X) X(0, 1) X(1, 2) X(2, 3) X(3, 4)
 
 template <typename T, int NB, int MINB>
-void blk_impl(int grid, int block, cudaStream_t st, bool first, bool last, const SellDev& A, const T* tau2m,
-              const T* x, const T* prev, T* out, T* acc_s, T* acc_c, double* acc64, int64_t acc_stride, int F,
-              const T* ahi, const T* alo, int Lp1, int step, int* flag) {
-#define KES_BLK_ARGS A, tau2m, x, prev, out, acc_s, acc_c, acc64, acc_stride, F, ahi, alo, Lp1, step, flag
+void blk_impl(int grid, int block, cudaStream_t st, bool first, bool last, const SellDev& A, const T* x,
+              const T* prev, T* out, T* acc_s, T* acc_c, double* acc64, int64_t acc_stride, int F, const T* ahi,
+              const T* alo, int Lp1, int step, int* flag) {
+#define KES_BLK_ARGS A, x, prev, out, acc_s, acc_c, acc64, acc_stride, F, ahi, alo, Lp1, step, flag
   if (first && last) k_step_blk<T, NB, true, true, MINB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
   else if (first) k_step_blk<T, NB, true, false, MINB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
   else if (last) k_step_blk<T, NB, false, true, MINB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
@@ -215,12 +209,12 @@ void blk_impl(int grid, int block, cudaStream_t st, bool first, bool last, const
 
 template <typename T>
 void blk_dispatch(const LaunchCfg& cfg, int NB, cudaStream_t st, bool first, bool last, const SellDev& A,
-                  const T* tau2m, const T* x, const T* prev, T* out, T* acc_s, T* acc_c, double* acc64,
-                  int64_t acc_stride, int F, const T* ahi, const T* alo, int Lp1, int step, int* flag) {
+                  const T* x, const T* prev, T* out, T* acc_s, T* acc_c, double* acc64, int64_t acc_stride, int F,
+                  const T* ahi, const T* alo, int Lp1, int step, int* flag) {
   const int64_t need = (A.n_slices + 7) / 8;
   const int grid = static_cast<int>(need < cfg.grid_blk ? need : cfg.grid_blk);
 #define KES_CALL(NBV, M)                                                                                   \
-  blk_impl<T, NBV, M>(grid, 256, st, first, last, A, tau2m, x, prev, out, acc_s, acc_c, acc64, acc_stride, F, \
+  blk_impl<T, NBV, M>(grid, 256, st, first, last, A, x, prev, out, acc_s, acc_c, acc64, acc_stride, F,        \
                       ahi, alo, Lp1, step, flag)
 #define X(ID, M)                         \
   case ID:                               \
@@ -324,19 +318,19 @@ int blk_blocks_per_sm(bool fp32, int NB, int variant, int block) {
 }
 
 void launch_step_blk_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, int NB, bool first, bool last,
-                         const double* tau2m, const double* x, const double* prev, double* out, double* acc,
-                         int64_t acc_stride, int F, const double* alpha, int L, int step, int* flag) {
-  blk_dispatch<double>(cfg, NB, st, first, last, A, tau2m, x, prev, out, acc, nullptr, nullptr, acc_stride, F, alpha,
+                         const double* x, const double* prev, double* out, double* acc, int64_t acc_stride, int F,
+                         const double* alpha, int L, int step, int* flag) {
+  blk_dispatch<double>(cfg, NB, st, first, last, A, x, prev, out, acc, nullptr, nullptr, acc_stride, F, alpha,
                        nullptr, L + 1, step, flag);
   ++g_launches;
 }
 
 void launch_step_blk_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, int NB, bool first, bool last,
-                         const float* tau2m, const float* x, const float* prev, float* out, float* acc_s,
-                         float* acc_c, double* acc64, int64_t acc_stride, int F, const float* alpha_hi,
-                         const float* alpha_lo, int L, int step, int* flag) {
-  blk_dispatch<float>(cfg, NB, st, first, last, A, tau2m, x, prev, out, acc_s, acc_c, acc64, acc_stride, F,
-                      alpha_hi, alpha_lo, L + 1, step, flag);
+                         const float* x, const float* prev, float* out, float* acc_s, float* acc_c, double* acc64,
+                         int64_t acc_stride, int F, const float* alpha_hi, const float* alpha_lo, int L, int step,
+                         int* flag) {
+  blk_dispatch<float>(cfg, NB, st, first, last, A, x, prev, out, acc_s, acc_c, acc64, acc_stride, F, alpha_hi,
+                      alpha_lo, L + 1, step, flag);
   ++g_launches;
 }
 

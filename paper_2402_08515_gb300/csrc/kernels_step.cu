@@ -2,13 +2,15 @@
 //
 // One step of the filter application (Sec. 2.3, eq. 2stepmethod and
 // eq. disc_filtercoeff; Algorithm 2.5, time loop):
-//   u_{n+1} = 2 u_n - u_{n-1} - (tau^2 / m) .* (S u_n)
+//   u_{n+1} = 2 u_n - u_{n-1} - tau^2 M^{-1} S u_n = (2 u_n - u_{n-1}) + A u_n
 //   acc_f  += alpha_f[n+1] * u_{n+1}
-// fused into one pass: a warp owns one 32-row slice (lane = row); the slice's
-// values and column indices stream from HBM in 256-byte (FP64) / 128-byte
-// (FP32) coalesced warp loads marked evict-first, u_n is gathered through the
-// read-only path (it stays L2-resident across the step), and the three-term
-// update and the weighted accumulation run on the row result in registers.
+// with A = -tau^2 M^{-1} S stored once per kes_set_filter (the diagonal scale is
+// folded into the values), fused into one pass: a warp owns one 32-row slice
+// (lane = row); the slice's values and column indices stream from HBM in
+// 256-byte (FP64) / 128-byte (FP32) coalesced warp loads marked evict-first, u_n
+// is gathered through the read-only path (it stays L2-resident across the step),
+// and each row is one FMA chain seeded with 2 u_n - u_{n-1}, followed by the
+// weighted accumulation in registers.
 // No tensor cores: the step is a sparse gather, not a dense contraction.
 #include <cuda_runtime.h>
 
@@ -24,14 +26,12 @@ __device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p);
 __device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
 __device__ __forceinline__ int32_t ld_stream(const int32_t* p) { return __ldcs(p); }
 
-// sum_k val[32k] * x[col[32k]] over the w entries of one lane's row. Loads are issued
-// BATCH entries at a time (memory-level parallelism); even entries go to sum0 and odd
-// ones to sum1 whatever BATCH is, so every variant rounds identically.
+// init + sum_k val[32k] * x[col[32k]] over the w entries of one lane's row, one FMA
+// chain in entry order (every step kernel forms it the same way, so all launch
+// shapes round identically). Loads are issued BATCH entries at a time.
 template <typename T, int BATCH>
-__device__ __forceinline__ T row_dot(const T* __restrict__ v, const int32_t* __restrict__ c, int w,
+__device__ __forceinline__ T row_dot(T acc, const T* __restrict__ v, const int32_t* __restrict__ c, int w,
                                      const T* __restrict__ x) {
-  static_assert(BATCH % 2 == 0, "BATCH must be even");
-  T sum0 = T(0), sum1 = T(0);
   int k = 0;
   for (; k + BATCH <= w; k += BATCH) {
     int32_t cc[BATCH];
@@ -43,10 +43,7 @@ __device__ __forceinline__ T row_dot(const T* __restrict__ v, const int32_t* __r
 #pragma unroll
     for (int j = 0; j < BATCH; ++j) xx[j] = __ldg(x + cc[j]);
 #pragma unroll
-    for (int j = 0; j < BATCH; j += 2) {
-      sum0 = fma(vv[j], xx[j], sum0);
-      sum1 = fma(vv[j + 1], xx[j + 1], sum1);
-    }
+    for (int j = 0; j < BATCH; ++j) acc = fma(vv[j], xx[j], acc);
   }
   if (k < w) {
     int32_t cc[BATCH];
@@ -62,17 +59,13 @@ __device__ __forceinline__ T row_dot(const T* __restrict__ v, const int32_t* __r
       if (k + j < w) xx[j] = __ldg(x + cc[j]);
 #pragma unroll
     for (int j = 0; j < BATCH; ++j)
-      if (k + j < w) {
-        if (j & 1) sum1 = fma(vv[j], xx[j], sum1);
-        else sum0 = fma(vv[j], xx[j], sum0);
-      }
+      if (k + j < w) acc = fma(vv[j], xx[j], acc);
   }
-  return sum0 + sum1;
+  return acc;
 }
 
 template <bool FIRST, bool LAST, int BATCH, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_step_f64(SellDev A, const double* __restrict__ tau2m,
-                                                  const double* __restrict__ x, const double* prev,
+__global__ void __launch_bounds__(256, MINB) k_step_f64(SellDev A, const double* __restrict__ x, const double* prev,
                                                   double* out, double* acc, int64_t acc_stride, int F,
                                                   const double* __restrict__ alpha, int Lp1, int step,
                                                   int* flag) {
@@ -82,12 +75,11 @@ __global__ void __launch_bounds__(256, MINB) k_step_f64(SellDev A, const double*
        s += nwarps) {
     const int64_t beg = A.slice_ptr[s];
     const int w = static_cast<int>((A.slice_ptr[s + 1] - beg) >> 5);
-    const double sum = row_dot<double, BATCH>(A.val64 + beg + lane, A.col + beg + lane, w, x);
     const int64_t row = s * kSliceC + lane;
     const int64_t mesh = A.slice_mesh ? A.slice_mesh[s] : 0;
     const double xi = x[row];
     const double pi = FIRST ? xi : prev[row];
-    const double un = fma(-ld_stream(tau2m + row), sum, 2.0 * xi - pi);
+    const double un = row_dot<double, BATCH>(2.0 * xi - pi, A.val64 + beg + lane, A.col + beg + lane, w, x);
     if (!LAST) out[row] = un;
     bool bad = false;
     for (int f = 0; f < F; ++f) {
@@ -111,8 +103,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
 }
 
 template <bool FIRST, bool LAST, int BATCH, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_step_f32(SellDev A, const float* __restrict__ tau2m,
-                                                  const float* __restrict__ x, const float* prev,
+__global__ void __launch_bounds__(256, MINB) k_step_f32(SellDev A, const float* __restrict__ x, const float* prev,
                                                   float* out, float* acc_s, float* acc_c, double* acc64,
                                                   int64_t acc_stride, int F, const float* __restrict__ ahi,
                                                   const float* __restrict__ alo, int Lp1, int step,
@@ -123,12 +114,12 @@ __global__ void __launch_bounds__(256, MINB) k_step_f32(SellDev A, const float* 
        s += nwarps) {
     const int64_t beg = A.slice_ptr[s];
     const int w = static_cast<int>((A.slice_ptr[s + 1] - beg) >> 5);
-    const float sum = row_dot<float, BATCH>(A.val32 + beg + lane, A.col + beg + lane, w, x);
     const int64_t row = s * kSliceC + lane;
     const int64_t mesh = A.slice_mesh ? A.slice_mesh[s] : 0;
     const float xi = x[row];
     const float pi = FIRST ? xi : prev[row];
-    const float un = fmaf(-ld_stream(tau2m + row), sum, __fsub_rn(__fmul_rn(2.0f, xi), pi));
+    const float un = row_dot<float, BATCH>(__fsub_rn(__fmul_rn(2.0f, xi), pi), A.val32 + beg + lane,
+                                           A.col + beg + lane, w, x);
     if (!LAST) out[row] = un;
     bool bad = false;
     for (int f = 0; f < F; ++f) {
@@ -181,9 +172,26 @@ __global__ void __launch_bounds__(256) k_spmv_f64(SellDev A, const double* __res
        s += nwarps) {
     const int64_t beg = A.slice_ptr[s];
     const int w = static_cast<int>((A.slice_ptr[s + 1] - beg) >> 5);
-    const double sum = row_dot<double, 8>(A.val64 + beg + lane, A.col + beg + lane, w, x);
+    const double sum = row_dot<double, 8>(0.0, A.val64 + beg + lane, A.col + beg + lane, w, x);
     const int64_t row = s * kSliceC + lane;
     y[row] = dscale ? sum * dscale[row] : sum;
+  }
+}
+
+// A = -tau^2 M^{-1} S in the SELL layout: out[e] = -tau2m[row(e)] * val64[e]
+__global__ void k_scale_values(SellDev A, const double* __restrict__ tau2m, double* __restrict__ out64,
+                               float* __restrict__ out32) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t s = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; s < A.n_slices;
+       s += nwarps) {
+    const int64_t beg = A.slice_ptr[s], end = A.slice_ptr[s + 1];
+    const double t = -tau2m[s * kSliceC + lane];
+    for (int64_t e = beg + lane; e < end; e += kSliceC) {
+      const double a = t * A.val64[e];
+      if (out64) out64[e] = a;
+      if (out32) out32[e] = static_cast<float>(a);
+    }
   }
 }
 
@@ -206,29 +214,22 @@ int grid_for(const LaunchCfg& cfg, int64_t n_slices) {
   X(0, 8, 1) X(1, 8, 3) X(2, 8, 4) X(3, 4, 4) X(4, 4, 5) X(5, 4, 6) X(6, 2, 6) X(7, 2, 8)
 
 template <int BATCH, int MINB>
-void step_f64_impl(int grid, int block, cudaStream_t st, bool first, bool last, const SellDev& A,
-                   const double* tau2m, const double* x, const double* prev, double* out, double* acc,
-                   int64_t acc_stride, int F, const double* alpha, int Lp1, int step, int* flag) {
-  if (first && last)
-    k_step_f64<true, true, BATCH, MINB><<<grid, block, 0, st>>>(A, tau2m, x, prev, out, acc, acc_stride, F,
-                                                                 alpha, Lp1, step, flag);
-  else if (first)
-    k_step_f64<true, false, BATCH, MINB><<<grid, block, 0, st>>>(A, tau2m, x, prev, out, acc, acc_stride, F,
-                                                                  alpha, Lp1, step, flag);
-  else if (last)
-    k_step_f64<false, true, BATCH, MINB><<<grid, block, 0, st>>>(A, tau2m, x, prev, out, acc, acc_stride, F,
-                                                                  alpha, Lp1, step, flag);
-  else
-    k_step_f64<false, false, BATCH, MINB><<<grid, block, 0, st>>>(A, tau2m, x, prev, out, acc, acc_stride, F,
-                                                                   alpha, Lp1, step, flag);
+void step_f64_impl(int grid, int block, cudaStream_t st, bool first, bool last, const SellDev& A, const double* x,
+                   const double* prev, double* out, double* acc, int64_t acc_stride, int F, const double* alpha,
+                   int Lp1, int step, int* flag) {
+#define KES_F64_ARGS A, x, prev, out, acc, acc_stride, F, alpha, Lp1, step, flag
+  if (first && last) k_step_f64<true, true, BATCH, MINB><<<grid, block, 0, st>>>(KES_F64_ARGS);
+  else if (first) k_step_f64<true, false, BATCH, MINB><<<grid, block, 0, st>>>(KES_F64_ARGS);
+  else if (last) k_step_f64<false, true, BATCH, MINB><<<grid, block, 0, st>>>(KES_F64_ARGS);
+  else k_step_f64<false, false, BATCH, MINB><<<grid, block, 0, st>>>(KES_F64_ARGS);
+#undef KES_F64_ARGS
 }
 
 template <int BATCH, int MINB>
-void step_f32_impl(int grid, int block, cudaStream_t st, bool first, bool last, const SellDev& A,
-                   const float* tau2m, const float* x, const float* prev, float* out, float* acc_s, float* acc_c,
-                   double* acc64, int64_t acc_stride, int F, const float* ahi, const float* alo, int Lp1,
-                   int step, int* flag) {
-#define KES_F32_ARGS A, tau2m, x, prev, out, acc_s, acc_c, acc64, acc_stride, F, ahi, alo, Lp1, step, flag
+void step_f32_impl(int grid, int block, cudaStream_t st, bool first, bool last, const SellDev& A, const float* x,
+                   const float* prev, float* out, float* acc_s, float* acc_c, double* acc64, int64_t acc_stride,
+                   int F, const float* ahi, const float* alo, int Lp1, int step, int* flag) {
+#define KES_F32_ARGS A, x, prev, out, acc_s, acc_c, acc64, acc_stride, F, ahi, alo, Lp1, step, flag
   if (first && last) k_step_f32<true, true, BATCH, MINB><<<grid, block, 0, st>>>(KES_F32_ARGS);
   else if (first) k_step_f32<true, false, BATCH, MINB><<<grid, block, 0, st>>>(KES_F32_ARGS);
   else if (last) k_step_f32<false, true, BATCH, MINB><<<grid, block, 0, st>>>(KES_F32_ARGS);
@@ -288,19 +289,19 @@ int step_blocks_per_sm(bool fp32, int variant, int block) {
   return (e == cudaSuccess && nb > 0) ? nb : 2;
 }
 
-void launch_step_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bool first, const double* tau2m,
-                     const double* x, const double* prev, double* out, double* acc, int64_t acc_stride, int F,
-                     const double* alpha, int L, int step, bool last, int* flag) {
+void launch_step_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bool first, const double* x,
+                     const double* prev, double* out, double* acc, int64_t acc_stride, int F, const double* alpha,
+                     int L, int step, bool last, int* flag) {
   if (cfg.variant >= kRegStepVariants) {
-    launch_step_tma_f64(A, cfg.tma, cfg.n_sm, st, first, last, tau2m, x, prev, out, acc, acc_stride, F, alpha, L,
-                        step, flag);
+    launch_step_tma_f64(A, cfg.tma, cfg.n_sm, st, first, last, x, prev, out, acc, acc_stride, F, alpha, L, step,
+                        flag);
     return;
   }
   const int grid = grid_for(cfg, A.n_slices);
   switch (cfg.variant) {
 #define X(ID, B, M)                                                                                        \
   case ID:                                                                                                 \
-    step_f64_impl<B, M>(grid, cfg.block_step, st, first, last, A, tau2m, x, prev, out, acc, acc_stride, F, \
+    step_f64_impl<B, M>(grid, cfg.block_step, st, first, last, A, x, prev, out, acc, acc_stride, F,        \
                         alpha, L + 1, step, flag);                                                         \
     break;
     KES_STEP_VARIANTS(X)
@@ -310,12 +311,11 @@ void launch_step_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bo
   ++g_launches;
 }
 
-void launch_step_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bool first, bool last,
-                     const float* tau2m, const float* x, const float* prev, float* out, float* acc_s,
-                     float* acc_c, double* acc64, int64_t acc_stride, int F, const float* alpha_hi,
-                     const float* alpha_lo, int L, int step, int* flag) {
+void launch_step_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bool first, bool last, const float* x,
+                     const float* prev, float* out, float* acc_s, float* acc_c, double* acc64, int64_t acc_stride,
+                     int F, const float* alpha_hi, const float* alpha_lo, int L, int step, int* flag) {
   if (cfg.variant >= kRegStepVariants) {
-    launch_step_tma_f32(A, cfg.tma, cfg.n_sm, st, first, last, tau2m, x, prev, out, acc_s, acc_c, acc64, acc_stride, F,
+    launch_step_tma_f32(A, cfg.tma, cfg.n_sm, st, first, last, x, prev, out, acc_s, acc_c, acc64, acc_stride, F,
                         alpha_hi, alpha_lo, L, step, flag);
     return;
   }
@@ -323,7 +323,7 @@ void launch_step_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bo
   switch (cfg.variant) {
 #define X(ID, B, M)                                                                                        \
   case ID:                                                                                                 \
-    step_f32_impl<B, M>(grid, cfg.block_step, st, first, last, A, tau2m, x, prev, out, acc_s, acc_c, acc64, \
+    step_f32_impl<B, M>(grid, cfg.block_step, st, first, last, A, x, prev, out, acc_s, acc_c, acc64,        \
                         acc_stride, F, alpha_hi, alpha_lo, L + 1, step, flag);                             \
     break;
     KES_STEP_VARIANTS(X)
@@ -345,6 +345,12 @@ void launch_init_f32(cudaStream_t st, const SellDev& A, int nb, const double* r6
 void launch_spmv_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, const double* x,
                      const double* dscale, double* y) {
   k_spmv_f64<<<grid_for(cfg, A.n_slices), cfg.block_step, 0, st>>>(A, x, dscale, y);
+  ++g_launches;
+}
+
+void launch_scale_values(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, const double* tau2m,
+                         double* out64, float* out32) {
+  k_scale_values<<<grid_for(cfg, A.n_slices), cfg.block_step, 0, st>>>(A, tau2m, out64, out32);
   ++g_launches;
 }
 

@@ -83,8 +83,8 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
 }
 
 template <typename T, bool FIRST, bool LAST>
-__global__ void k_step_tma(SellDev A, int G, int S, int wmax, const T* __restrict__ tau2m,
-                           const T* __restrict__ x, const T* prev, T* out, T* acc_s, T* acc_c, double* acc64,
+__global__ void k_step_tma(SellDev A, int G, int S, int wmax, const T* __restrict__ x, const T* prev, T* out,
+                           T* acc_s, T* acc_c, double* acc64,
                            int64_t acc_stride, int F, const T* __restrict__ ahi, const T* __restrict__ alo,
                            int Lp1, int step, int* flag) {
   constexpr bool kF32 = std::is_same<T, float>::value;
@@ -154,23 +154,21 @@ __global__ void k_step_tma(SellDev A, int G, int S, int wmax, const T* __restric
         const int w = static_cast<int>((A.slice_ptr[s + 1] - beg) >> 5);
         const T* v = sval + st * stage_entries + (beg - base) + lane;
         const int32_t* cl = scol + st * stage_entries + (beg - base) + lane;
-        T sum0 = T(0), sum1 = T(0);
-        int k = 0;
-        for (; k + 2 <= w; k += 2) {
-          const int32_t c0 = cl[k * kSliceC], c1 = cl[(k + 1) * kSliceC];
-          const T x0 = __ldg(x + c0), x1 = __ldg(x + c1);
-          sum0 = fma(v[k * kSliceC], x0, sum0);
-          sum1 = fma(v[(k + 1) * kSliceC], x1, sum1);
-        }
-        if (k < w) sum0 = fma(v[k * kSliceC], __ldg(x + cl[k * kSliceC]), sum0);
-        const T sum = sum0 + sum1;
         const int64_t row = s * kSliceC + lane;
         const int64_t mesh = A.slice_mesh ? A.slice_mesh[s] : 0;
         const T xi = x[row];
         const T pi = FIRST ? xi : prev[row];
+        // u_{n+1} = (2 u_n - u_{n-1}) + A u_n, one FMA chain in entry order
         T un;
-        if constexpr (kF32) un = fmaf(-__ldcs(tau2m + row), sum, __fsub_rn(__fmul_rn(2.0f, xi), pi));
-        else un = fma(-__ldcs(tau2m + row), sum, 2.0 * xi - pi);
+        if constexpr (kF32) un = __fsub_rn(__fmul_rn(2.0f, xi), pi);
+        else un = 2.0 * xi - pi;
+        int k = 0;
+        for (; k + 2 <= w; k += 2) {
+          const int32_t c0 = cl[k * kSliceC], c1 = cl[(k + 1) * kSliceC];
+          const T x0 = __ldg(x + c0), x1 = __ldg(x + c1);
+          un = fma(v[(k + 1) * kSliceC], x1, fma(v[k * kSliceC], x0, un));
+        }
+        if (k < w) un = fma(v[k * kSliceC], __ldg(x + cl[k * kSliceC]), un);
         if (!LAST) out[row] = un;
         bool bad = false;
         for (int f = 0; f < F; ++f) {
@@ -211,19 +209,19 @@ size_t tma_smem(int G, int S, int wmax) {
 }
 
 template <typename T, bool FIRST, bool LAST>
-void tma_launch_one(const TmaShape& sh, int n_sm, cudaStream_t st, const SellDev& A, const T* tau2m, const T* x,
-                    const T* prev, T* out, T* acc_s, T* acc_c, double* acc64, int64_t acc_stride, int F,
-                    const T* ahi, const T* alo, int Lp1, int step, int* flag) {
+void tma_launch_one(const TmaShape& sh, int n_sm, cudaStream_t st, const SellDev& A, const T* x, const T* prev,
+                    T* out, T* acc_s, T* acc_c, double* acc64, int64_t acc_stride, int F, const T* ahi, const T* alo,
+                    int Lp1, int step, int* flag) {
   const size_t smem = tma_smem<T>(sh.G, sh.S, sh.wmax);
   k_step_tma<T, FIRST, LAST><<<n_sm * sh.ctas_per_sm, (sh.G + 1) * 32, smem, st>>>(
-      A, sh.G, sh.S, sh.wmax, tau2m, x, prev, out, acc_s, acc_c, acc64, acc_stride, F, ahi, alo, Lp1, step, flag);
+      A, sh.G, sh.S, sh.wmax, x, prev, out, acc_s, acc_c, acc64, acc_stride, F, ahi, alo, Lp1, step, flag);
 }
 
 template <typename T>
-void tma_dispatch(const TmaShape& sh, int n_sm, cudaStream_t st, bool first, bool last, const SellDev& A,
-                  const T* tau2m, const T* x, const T* prev, T* out, T* acc_s, T* acc_c, double* acc64,
-                  int64_t acc_stride, int F, const T* ahi, const T* alo, int Lp1, int step, int* flag) {
-#define KES_TMA_ARGS sh, n_sm, st, A, tau2m, x, prev, out, acc_s, acc_c, acc64, acc_stride, F, ahi, alo, Lp1, step, flag
+void tma_dispatch(const TmaShape& sh, int n_sm, cudaStream_t st, bool first, bool last, const SellDev& A, const T* x,
+                  const T* prev, T* out, T* acc_s, T* acc_c, double* acc64, int64_t acc_stride, int F, const T* ahi,
+                  const T* alo, int Lp1, int step, int* flag) {
+#define KES_TMA_ARGS sh, n_sm, st, A, x, prev, out, acc_s, acc_c, acc64, acc_stride, F, ahi, alo, Lp1, step, flag
   if (first && last) tma_launch_one<T, true, true>(KES_TMA_ARGS);
   else if (first) tma_launch_one<T, true, false>(KES_TMA_ARGS);
   else if (last) tma_launch_one<T, false, true>(KES_TMA_ARGS);
@@ -258,19 +256,19 @@ cudaError_t tma_prepare(bool fp32, const TmaShape& sh) {
 }
 
 void launch_step_tma_f64(const SellDev& A, const TmaShape& sh, int n_sm, cudaStream_t st, bool first, bool last,
-                         const double* tau2m, const double* x, const double* prev, double* out, double* acc,
-                         int64_t acc_stride, int F, const double* alpha, int L, int step, int* flag) {
-  tma_dispatch<double>(sh, n_sm, st, first, last, A, tau2m, x, prev, out, acc, nullptr, nullptr, acc_stride, F,
-                       alpha, nullptr, L + 1, step, flag);
+                         const double* x, const double* prev, double* out, double* acc, int64_t acc_stride, int F,
+                         const double* alpha, int L, int step, int* flag) {
+  tma_dispatch<double>(sh, n_sm, st, first, last, A, x, prev, out, acc, nullptr, nullptr, acc_stride, F, alpha,
+                       nullptr, L + 1, step, flag);
   ++g_launches;
 }
 
 void launch_step_tma_f32(const SellDev& A, const TmaShape& sh, int n_sm, cudaStream_t st, bool first, bool last,
-                         const float* tau2m, const float* x, const float* prev, float* out, float* acc_s,
-                         float* acc_c, double* acc64, int64_t acc_stride, int F, const float* alpha_hi,
-                         const float* alpha_lo, int L, int step, int* flag) {
-  tma_dispatch<float>(sh, n_sm, st, first, last, A, tau2m, x, prev, out, acc_s, acc_c, acc64, acc_stride, F,
-                      alpha_hi, alpha_lo, L + 1, step, flag);
+                         const float* x, const float* prev, float* out, float* acc_s, float* acc_c, double* acc64,
+                         int64_t acc_stride, int F, const float* alpha_hi, const float* alpha_lo, int L, int step,
+                         int* flag) {
+  tma_dispatch<float>(sh, n_sm, st, first, last, A, x, prev, out, acc_s, acc_c, acc64, acc_stride, F, alpha_hi,
+                      alpha_lo, L + 1, step, flag);
   ++g_launches;
 }
 

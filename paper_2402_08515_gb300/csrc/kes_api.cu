@@ -102,7 +102,18 @@ struct kes_ctx {
   double* m64 = nullptr;          // lumped mass (n_pad, zero padded)
   double* minv64 = nullptr;       // 1 / m
   double* tau2m64 = nullptr;      // tau^2 / m with the tau of the row's mesh
-  float* tau2m32 = nullptr;
+  double* step64 = nullptr;       // A = -tau^2 M^{-1} S, SELL layout (FP64 steps)
+  float* step32 = nullptr;        // the same in FP32 (FP32 steps)
+  SellDev step_A64() const {
+    SellDev a = A;
+    a.val64 = step64;
+    return a;
+  }
+  SellDev step_A32() const {
+    SellDev a = A;
+    a.val32 = step32;
+    return a;
+  }
   // filter
   bool filter_set = false;
   int F = 0, L = 0;
@@ -258,6 +269,7 @@ int64_t issue_filter_steps(kes_ctx* c, int NB, bool fp64) {
   if (fp64) {
     // in a context of the FP32 form the launch shape was tuned for the FP32 kernels:
     // the FP64 steps of the refinement take a fixed register-staged shape
+    const SellDev A64 = c->step_A64();
     LaunchCfg cfg = c->cfg;
     if (c->opts.precision != KES_PREC_FP64) {
       cfg.variant = 3;
@@ -269,13 +281,14 @@ int64_t issue_filter_steps(kes_ctx* c, int NB, bool fp64) {
       const double* prev = s <= 1 ? c->stage_in : c->U64[s & 1];
       double* out = c->U64[s & 1];
       if (NB == 1)
-        launch_step_f64(c->A, cfg, c->stream, first, c->tau2m64, x, prev, out, c->stage_out, stride, F, c->alpha64,
-                        L, s, last, c->d_flag);
+        launch_step_f64(A64, cfg, c->stream, first, x, prev, out, c->stage_out, stride, F, c->alpha64, L, s, last,
+                        c->d_flag);
       else
-        launch_step_blk_f64(c->A, cfg, c->stream, NB, first, last, c->tau2m64, x, prev, out, c->stage_out, stride,
-                            F, c->alpha64, L, s, c->d_flag);
+        launch_step_blk_f64(A64, cfg, c->stream, NB, first, last, x, prev, out, c->stage_out, stride, F, c->alpha64,
+                            L, s, c->d_flag);
     }
   } else {
+    const SellDev A32 = c->step_A32();
     launch_init_f32(c->stream, c->A, NB, c->stage_in, c->U32[2], c->acc_s, c->acc_c, stride, F, c->alpha64, L);
     for (int s = 0; s < L; ++s) {
       const bool first = s == 0, last = s == L - 1;
@@ -283,11 +296,11 @@ int64_t issue_filter_steps(kes_ctx* c, int NB, bool fp64) {
       const float* prev = s <= 1 ? c->U32[2] : c->U32[s & 1];
       float* out = c->U32[s & 1];
       if (NB == 1)
-        launch_step_f32(c->A, c->cfg, c->stream, first, last, c->tau2m32, x, prev, out, c->acc_s, c->acc_c,
-                        c->stage_out, stride, F, c->alpha_hi, c->alpha_lo, L, s, c->d_flag);
+        launch_step_f32(A32, c->cfg, c->stream, first, last, x, prev, out, c->acc_s, c->acc_c, c->stage_out, stride,
+                        F, c->alpha_hi, c->alpha_lo, L, s, c->d_flag);
       else
-        launch_step_blk_f32(c->A, c->cfg, c->stream, NB, first, last, c->tau2m32, x, prev, out, c->acc_s, c->acc_c,
-                            c->stage_out, stride, F, c->alpha_hi, c->alpha_lo, L, s, c->d_flag);
+        launch_step_blk_f32(A32, c->cfg, c->stream, NB, first, last, x, prev, out, c->acc_s, c->acc_c, c->stage_out,
+                            stride, F, c->alpha_hi, c->alpha_lo, L, s, c->d_flag);
     }
   }
   return g_launches - before;
@@ -295,8 +308,13 @@ int64_t issue_filter_steps(kes_ctx* c, int NB, bool fp64) {
 
 // The FP64 step kernels in a context of the FP32 form (used by the FP64 refinement).
 void ensure_fp64_state(kes_ctx* c) {
-  if (c->U64[0]) return;
-  for (int j = 0; j < 2; ++j) c->U64[j] = c->dzero_n<double>(c->n_pad * c->NBcap);
+  if (!c->U64[0])
+    for (int j = 0; j < 2; ++j) c->U64[j] = c->dzero_n<double>(c->n_pad * c->NBcap);
+  if (!c->step64) {
+    c->step64 = c->dzero_n<double>(c->nnz_pad);
+    launch_scale_values(c->A, c->cfg, c->stream, c->tau2m64, c->step64, nullptr);
+    KES_CHECK_LAUNCH();
+  }
 }
 
 void run_filter(kes_ctx* c, int NB, bool fp64) {
@@ -442,10 +460,10 @@ void tune_steps(kes_ctx* c) {
     const float ms = timed([&](int count) {
       for (int i = 0; i < count; ++i) {
         if (fp32)
-          launch_step_f32(c->A, c->cfg, c->stream, false, false, c->tau2m32, c->U32[0], c->U32[1], c->U32[1],
-                          c->acc_s, c->acc_c, c->stage_out, c->n_pad, 1, a32, a32, 7, 1, c->d_flag);
+          launch_step_f32(c->step_A32(), c->cfg, c->stream, false, false, c->U32[0], c->U32[1], c->U32[1], c->acc_s,
+                          c->acc_c, c->stage_out, c->n_pad, 1, a32, a32, 7, 1, c->d_flag);
         else
-          launch_step_f64(c->A, c->cfg, c->stream, false, c->tau2m64, c->U64[0], c->U64[1], c->U64[1], c->stage_out,
+          launch_step_f64(c->step_A64(), c->cfg, c->stream, false, c->U64[0], c->U64[1], c->U64[1], c->stage_out,
                           c->n_pad, 1, a64, 7, 1, false, c->d_flag);
       }
     });
@@ -466,12 +484,11 @@ void tune_steps(kes_ctx* c) {
       const float ms = timed([&](int count) {
         for (int i = 0; i < count; ++i) {
           if (fp32)
-            launch_step_blk_f32(c->A, c->cfg, c->stream, NB, false, false, c->tau2m32, c->U32[0], c->U32[1],
-                                c->U32[1], c->acc_s, c->acc_c, c->stage_out, c->n_pad * NB, 1, a32, a32, 7, 1,
-                                c->d_flag);
+            launch_step_blk_f32(c->step_A32(), c->cfg, c->stream, NB, false, false, c->U32[0], c->U32[1], c->U32[1],
+                                c->acc_s, c->acc_c, c->stage_out, c->n_pad * NB, 1, a32, a32, 7, 1, c->d_flag);
           else
-            launch_step_blk_f64(c->A, c->cfg, c->stream, NB, false, false, c->tau2m64, c->U64[0], c->U64[1],
-                                c->U64[1], c->stage_out, c->n_pad * NB, 1, a64, 7, 1, c->d_flag);
+            launch_step_blk_f64(c->step_A64(), c->cfg, c->stream, NB, false, false, c->U64[0], c->U64[1], c->U64[1],
+                                c->stage_out, c->n_pad * NB, 1, a64, 7, 1, c->d_flag);
         }
       });
       if (ms < best_ms) {
@@ -644,9 +661,10 @@ kes_status create_impl(kes_ctx** out, int32_t nm, const int64_t* n, const int64_
     const int64_t np = c->n_pad, nb = c->NBcap;
     c->tau2m64 = c->dzero_n<double>(np);
     if (c->opts.precision == KES_PREC_FP32) {
-      c->tau2m32 = c->dzero_n<float>(np);
+      c->step32 = c->dzero_n<float>(c->nnz_pad);
       for (int j = 0; j < 3; ++j) c->U32[j] = c->dzero_n<float>(np * nb);
     } else {
+      c->step64 = c->dzero_n<double>(c->nnz_pad);
       for (int j = 0; j < 2; ++j) c->U64[j] = c->dzero_n<double>(np * nb);
     }
     c->stage_in = c->dzero_n<double>(np * nb);
@@ -723,11 +741,9 @@ kes_status set_filters_impl(kes_ctx* c, int32_t F, const double* wmin, const dou
       for (int64_t i = 0; i < mi.n; ++i) t2m[mi.row_off + i] = tau[j] * tau[j] / m[mi.row_off + i];
     }
     KES_CUDA(cudaMemcpyAsync(c->tau2m64, t2m.data(), c->n_pad * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    if (c->tau2m32) {
-      std::vector<float> t32(t2m.begin(), t2m.end());
-      KES_CUDA(cudaMemcpyAsync(c->tau2m32, t32.data(), c->n_pad * sizeof(float), cudaMemcpyHostToDevice, c->stream));
-      c->sync();
-    }
+    // step values A = -tau^2 M^{-1} S (the FP32 ones rounded once from the FP64 product)
+    if (c->step64 || c->step32) launch_scale_values(c->A, c->cfg, c->stream, c->tau2m64, c->step64, c->step32);
+    KES_CHECK_LAUNCH();
     ensure_stage_out(c, F);
     c->sync();
     c->F = F;
@@ -1215,11 +1231,12 @@ kes_status kes_sync(kes_ctx* ctx) {
 
 int64_t kes_step_bytes(const kes_ctx* c, int32_t b, int32_t F) {
   if (!c || b < 1 || F < 1) return -1;
-  // matrix: value + int32 column per stored entry; per row: tau^2/m once; per row and
-  // vector: gather of u_n once, u_{n-1} read, u_{n+1} written, F accumulators read and written.
+  // matrix: value (of A = -tau^2 M^{-1} S) + int32 column per stored entry, plus a 4-byte
+  // row pointer per row as CSR would need; per row and vector: the gather of u_n once,
+  // u_{n-1} read, u_{n+1} written, F accumulators read and written (FP32 form: s and c).
   if (c->opts.precision == KES_PREC_FP64)
-    return 12 * c->nnz + 4 * (c->n + 1) + c->n * (8 + int64_t(b) * (8 + 8 + 8 + 16 * F));
-  return 8 * c->nnz + c->n * (4 + int64_t(b) * (4 + 4 + 4 + 16 * F));
+    return 12 * c->nnz + 4 * (c->n + 1) + c->n * int64_t(b) * (8 + 8 + 8 + 16 * F);
+  return 8 * c->nnz + 4 * (c->n + 1) + c->n * int64_t(b) * (4 + 4 + 4 + 16 * F);
 }
 
 kes_status kes_estimate_omega_max(kes_ctx* c, int32_t iters, const double* v0, double* omega_max,

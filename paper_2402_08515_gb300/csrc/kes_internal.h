@@ -64,20 +64,22 @@ struct LaunchCfg {
   int variant_blk = 0; // their launch shape (register cap), see blk_variant_count
 };
 
-// One fused leapfrog step, FP64 (Sec. 2.3, eq. 2stepmethod + eq. disc_filtercoeff):
-//   out = 2 x - prev - tau2m .* (S x);   acc_f += alpha_f[step+1] * out   (f < F)
+// One fused leapfrog step, FP64 (Sec. 2.3, eq. 2stepmethod + eq. disc_filtercoeff), on the
+// values of A = -tau^2 M^{-1} S (see launch_scale_values):
+//   out = (2 x - prev) + A x;   acc_f += alpha_f[step+1] * out   (f < F)
 // first: prev = x and acc_f = alpha_f[0] * x + alpha_f[1] * out.
-// x, prev, out, acc: length n_pad; acc_f at acc + f * acc_stride; alpha_f at alpha + f * (L+1).
-// last: the state of the final step is not stored; flag[0] |= 1 if any acc entry is not finite.
+// x, prev, out, acc: length n_pad; acc_f at acc + f * acc_stride; alpha of mesh m, table f at
+// alpha + (m * F + f) * (L+1). last: the state of the final step is not stored;
+// flag[0] |= 1 if any acc entry is not finite.
 void launch_step_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bool first,
-                     const double* tau2m, const double* x, const double* prev, double* out,
+                     const double* x, const double* prev, double* out,
                      double* acc, int64_t acc_stride, int F, const double* alpha, int L, int step,
                      bool last, int* flag);
 
 // FP32 form: values/state FP32, accumulator as an unevaluated FP32 sum (s + c) kept by
 // error-free transformations; alpha as FP32 pairs (hi + lo). last: writes acc64 = s + c in FP64.
 void launch_step_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bool first, bool last,
-                     const float* tau2m, const float* x, const float* prev, float* out, float* acc_s,
+                     const float* x, const float* prev, float* out, float* acc_s,
                      float* acc_c, double* acc64, int64_t acc_stride, int F, const float* alpha_hi,
                      const float* alpha_lo, int L, int step, int* flag);
 // FP32 start over n_pad x nb row-major values: x32 = (float) r64; s_f = fl(alpha_f[0] r),
@@ -89,12 +91,12 @@ void launch_init_f32(cudaStream_t st, const SellDev& A, int nb, const double* r6
 // (row i's NB values contiguous). Same arithmetic per column as the single-vector
 // kernels; acc_stride = n_pad * NB elements per weight table.
 void launch_step_blk_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, int NB, bool first, bool last,
-                         const double* tau2m, const double* x, const double* prev, double* out, double* acc,
-                         int64_t acc_stride, int F, const double* alpha, int L, int step, int* flag);
+                         const double* x, const double* prev, double* out, double* acc, int64_t acc_stride, int F,
+                         const double* alpha, int L, int step, int* flag);
 void launch_step_blk_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, int NB, bool first, bool last,
-                         const float* tau2m, const float* x, const float* prev, float* out, float* acc_s,
-                         float* acc_c, double* acc64, int64_t acc_stride, int F, const float* alpha_hi,
-                         const float* alpha_lo, int L, int step, int* flag);
+                         const float* x, const float* prev, float* out, float* acc_s, float* acc_c, double* acc64,
+                         int64_t acc_stride, int F, const float* alpha_hi, const float* alpha_lo, int L, int step,
+                         int* flag);
 int blk_variant_count();
 int blk_blocks_per_sm(bool fp32, int NB, int variant, int block);
 
@@ -125,12 +127,17 @@ TmaShape tma_variant_shape(int variant, int wmax);  // variant >= kRegStepVarian
 bool tma_shape_fits(bool fp32, const TmaShape& sh);
 cudaError_t tma_prepare(bool fp32, const TmaShape& sh);  // dynamic shared memory attribute
 void launch_step_tma_f64(const SellDev& A, const TmaShape& sh, int n_sm, cudaStream_t st, bool first, bool last,
-                         const double* tau2m, const double* x, const double* prev, double* out, double* acc,
-                         int64_t acc_stride, int F, const double* alpha, int L, int step, int* flag);
+                         const double* x, const double* prev, double* out, double* acc, int64_t acc_stride, int F,
+                         const double* alpha, int L, int step, int* flag);
 void launch_step_tma_f32(const SellDev& A, const TmaShape& sh, int n_sm, cudaStream_t st, bool first, bool last,
-                         const float* tau2m, const float* x, const float* prev, float* out, float* acc_s,
-                         float* acc_c, double* acc64, int64_t acc_stride, int F, const float* alpha_hi,
-                         const float* alpha_lo, int L, int step, int* flag);
+                         const float* x, const float* prev, float* out, float* acc_s, float* acc_c, double* acc64,
+                         int64_t acc_stride, int F, const float* alpha_hi, const float* alpha_lo, int L, int step,
+                         int* flag);
+
+// Step values A = -tau^2 M^{-1} S from the values of S (A.val64) and tau^2/m per row:
+// out64[e] = -tau2m[row(e)] * val64[e] and/or out32[e] = (float) of the same (either may be null).
+void launch_scale_values(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, const double* tau2m,
+                         double* out64, float* out32);
 
 // y = dscale .* (S x) (dscale may be null) in FP64.
 void launch_spmv_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, const double* x,
