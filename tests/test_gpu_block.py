@@ -167,3 +167,4 @@ def test_fp32_solve_with_fp64_refinement_reaches_fp64_residuals(b):
         assert np.min(np.abs(exact - th)) <= 1e-10 * th
         r = S @ x - th * p.m * x
         assert np.linalg.norm(r) <= 1.01e-8 * th * np.linalg.norm(p.m * x)
+
