@@ -91,7 +91,7 @@ typedef struct kes_solve_opts {
 typedef struct kes_result {
   int64_t n;             /* problem size */
   int32_t n_pairs;       /* accepted pairs: omega in [omega_min, omega_max] and rel_res <= tol */
-  int32_t k_used;        /* basis size reached */
+  int32_t k_used;        /* basis size reached (summed over the intervals of kes_block_krylov_solve) */
   int32_t breakdown;     /* 1 if the Krylov space became invariant (status KES_INFO_INVARIANT_SUBSPACE) */
   int32_t n_ritz;        /* Ritz values of the last projection */
   int64_t time_steps;    /* leapfrog steps taken (per start vector) */
@@ -100,10 +100,12 @@ typedef struct kes_result {
   double* rel_res;       /* [n_pairs] relative residual */
   double* abs_res;       /* [n_pairs] ||(S - theta M) x||_2 with ||x||_M = 1 (eq. res) */
   double* vectors;       /* n x n_pairs col-major, or NULL unless want_vectors */
-  double* ritz_omega2;   /* [n_ritz] every Ritz value of the last projection, ascending */
+  double* ritz_omega2;   /* [n_ritz] every Ritz value of the last projection, ascending (with several
+                            intervals: each interval's projection in turn) */
   double* ritz_rel_res;  /* [n_ritz] relative residual of the in-interval ones, NaN elsewhere */
   double solve_ms;       /* wall time of the call */
   int64_t refine_steps;  /* FP64 leapfrog steps of the refinement sweeps (per filtered block) */
+  int32_t* interval;     /* [n_pairs] the filter interval whose process found each pair (0 for one interval) */
 } kes_result;
 
 /* Counters accumulated by a context since creation or kes_reset_stats. */
@@ -190,6 +192,14 @@ kes_status kes_set_filters(kes_ctx* ctx, int32_t F, const double* omega_min, con
    give every mesh the same intervals and tau. */
 kes_status kes_set_filters_batch(kes_ctx* ctx, int32_t F, const double* omega_min, const double* omega_max,
                                  const double* tau, int32_t L);
+/* kes_set_weights -- any weight tables in place of eq. (weightf) (Sec. 4, "Weight
+   function": the method is not tied to the indicator; e.g. a Gaussian peak).
+   alpha[n_mesh][F][L+1] are the rectangle-rule weights tau * alpha(n tau) of eq.
+   (disc_filtercoeff); omega_min/omega_max[n_mesh * F] is the band in which the
+   solver accepts Ritz pairs; tau[n_mesh]. Same checks as kes_set_filters_batch;
+   non-finite weights return KES_ERR_ARG. */
+kes_status kes_set_weights(kes_ctx* ctx, int32_t F, const double* alpha, const double* omega_min,
+                           const double* omega_max, const double* tau, int32_t L);
 
 /* Host helpers, no context and no GPU needed. */
 /* kes_alpha_table: alpha[0..L] = tau * alpha(n tau) of eq. (weightf), T = L tau. */
@@ -198,6 +208,11 @@ kes_status kes_alpha_table(double omega_min, double omega_max, double tau, int32
    the filter applies to an eigenvector of frequency omega (Lemma 2.3). */
 kes_status kes_filter_response(double omega_min, double omega_max, double tau, int32_t L,
                                const double* omega, int64_t k, double* beta);
+/* kes_alpha_gaussian: alpha[0..L] = tau * alpha(n tau) for the Gaussian pass band
+   beta(omega) ~ exp(-(omega - center)^2 / (2 sigma^2)): by the inverse cosine transform
+   behind eq. (filterf), alpha(t) = 2 sigma sqrt(2/pi) exp(-sigma^2 t^2 / 2) cos(center t)
+   (Sec. 4, "Weight function"). Requires center >= 0, sigma > 0, tau > 0, L >= 1. */
+kes_status kes_alpha_gaussian(double center, double sigma, double tau, int32_t L, double* alpha);
 /* kes_sym_eig: eigenvalues (ascending, w[k]) and orthonormal eigenvectors (V, k x k col-major,
    may be NULL) of the symmetric k x k col-major matrix A (only its lower triangle is read).
    This is the small projected problem of eq. (projevp) with B^T M B = I. */
@@ -219,6 +234,18 @@ int64_t kes_step_bytes(const kes_ctx* ctx, int32_t b, int32_t F);
  * KES_ERR_UNSTABLE if a non-finite value appeared in the state.
  */
 kes_status kes_filter_apply(kes_ctx* ctx, const double* r_in, double* r_out, int32_t b, int32_t mem);
+
+/*
+ * kes_filter_apply_columns -- the b columns carry the trajectories of F different
+ * filters (the F weight tables of kes_set_filters): column j is filtered with table
+ * j / (b / F) only, so F intervals share one matrix stream. Each column's sum is the
+ * one kes_filter_apply forms with that table, rounded the same way.
+ *   r_in   n_total x b col-major float64 (host or device per `mem`)
+ *   r_out  n_total x b col-major float64: r_out_j = C_{j / (b / F)} r_in_j
+ *   b      2 <= b <= opts.block_b and a multiple of F (with F = 1, see kes_filter_apply)
+ * KES_ERR_ARG if b is not a multiple of F or b < 2; otherwise as kes_filter_apply.
+ */
+kes_status kes_filter_apply_columns(kes_ctx* ctx, const double* r_in, double* r_out, int32_t b, int32_t mem);
 
 /*
  * kes_krylov_solve -- Krylov space of C from r0 (Algorithm 2.5, with the
@@ -245,10 +272,20 @@ kes_status kes_krylov_solve(kes_ctx* ctx, const double* r0, int32_t mem, const k
  * multiplicity up to b.
  *   R0     n_total x b col-major start vectors (host or device per `mem`)
  *   b      1 <= b <= opts.block_b
- *   sopts  kmax counts basis vectors per mesh (kmax >= b)
+ *   sopts  kmax counts basis vectors per mesh and interval (kmax >= b / F)
  *   out    array of kes_mesh_count(ctx) result pointers, one per mesh (free each with
  *          kes_result_free); set on KES_OK and KES_INFO_INVARIANT_SUBSPACE
- * Requires a single filter interval per mesh.
+ * Several intervals (kes_set_filters with F > 1) run as F independent block solvers
+ * that share the matrix stream: b must be a multiple of F, and interval f owns the
+ * g = b / F columns f g .. f g + g - 1 of the start block and of every block step,
+ * filtered with its own weights (kes_filter_apply_columns). Each interval keeps its
+ * own basis (kmax vectors), projection and acceptance, exactly as a separate call with
+ * its g start vectors would; the accepted pairs of a mesh are merged in ascending
+ * omega and kes_result.interval names the interval of each (a pair that lies in two
+ * overlapping intervals can be reported by both). n_wanted counts a mesh's pairs over
+ * all its intervals. The refinement sweeps filter each interval's Ritz vectors with
+ * that interval's weights.
+ * KES_ERR_ARG if b is not a multiple of F or kmax < b / F.
  */
 kes_status kes_block_krylov_solve(kes_ctx* ctx, const double* R0, int32_t b, int32_t mem,
                                   const kes_solve_opts* sopts, kes_result** out);

@@ -39,7 +39,9 @@ __all__ = [
     "weight", "alpha_table", "q_values", "beta_tilde", "filter_apply",
     "filter_apply_multi", "power_iteration", "m_inner", "m_norm",
     "orthonormalize_cgs2", "rayleigh_ritz", "ritz_residuals", "krylov_solve",
-    "block_krylov_solve", "refine_subspace", "KrylovResult", "BREAKDOWN_RATIO",
+    "block_krylov_solve", "multi_interval_krylov_solve",
+    "refine_subspace", "gaussian_weight", "alpha_table_gaussian",
+    "KrylovResult", "BREAKDOWN_RATIO",
 ]
 
 BREAKDOWN_RATIO = 1e-10
@@ -73,6 +75,22 @@ def alpha_table(omega_min: float, omega_max: float, tau: float, L: int) -> np.nd
     T = L * tau
     n = np.arange(L + 1, dtype=np.float64)
     return tau * weight(n * tau, omega_min, omega_max, T)
+
+
+def gaussian_weight(t, center: float, sigma: float):
+    """Weight of a Gaussian pass band (Sec. 4, "Weight function": a Gaussian peak in
+    place of the indicator). With beta_alpha(s) = int_0^inf alpha(t) cos(ts) dt
+    (eq. filterfunc) and its inverse alpha(t) = (2/pi) int_0^inf beta(s) cos(ts) ds
+    (the transform eq. filterf applies to the indicator), the even band
+    beta(s) = exp(-(s-c)^2 / (2 sigma^2)) + exp(-(s+c)^2 / (2 sigma^2)) gives
+    alpha(t) = 2 sigma sqrt(2/pi) exp(-sigma^2 t^2 / 2) cos(c t)."""
+    t = np.asarray(t, dtype=np.float64)
+    return 2.0 * sigma * math.sqrt(2.0 / math.pi) * np.exp(-0.5 * sigma * sigma * t * t) * np.cos(center * t)
+
+
+def alpha_table_gaussian(center: float, sigma: float, tau: float, L: int) -> np.ndarray:
+    """Rectangle-rule weights tau * alpha(n tau), n = 0..L, of the Gaussian band."""
+    return tau * gaussian_weight(np.arange(L + 1, dtype=np.float64) * tau, center, sigma)
 
 
 # --------------------------------------------------------------------------
@@ -246,6 +264,7 @@ class KrylovResult:
     ritz_rel_res: np.ndarray      # rel. residual of the in-interval ones (nan elsewhere)
     basis: np.ndarray             # (k_used, n)
     history: list = field(default_factory=list)
+    interval: np.ndarray = None   # index of the interval each accepted pair lies in
 
 
 def krylov_solve(S, m: np.ndarray, r0: np.ndarray, omega_min: float,
@@ -368,6 +387,62 @@ def block_krylov_solve(S, m: np.ndarray, R0: np.ndarray, omega_min: float,
                         time_steps=steps, breakdown=breakdown, ritz_theta=theta,
                         ritz_rel_res=rel_all,
                         basis=B[:k] if keep_basis else None, history=history)
+
+
+def multi_interval_krylov_solve(S, m: np.ndarray, R0: np.ndarray, intervals, tau: float,
+                                L: int, kmax: int, tol: float, check_every: int = 5,
+                                refine_sweeps: int = 0) -> KrylovResult:
+    """F intervals searched at once by F independent block Krylov processes.
+
+    R0: (b, n) with b a multiple of F = len(intervals); g = b / F. Process f is the
+    block solver of Sec. 4 (block_krylov_solve) on interval f from the start vectors
+    R0[f g : (f + 1) g], with its own basis of up to kmax vectors; the processes only
+    share the time stepping (column j of the b-column trajectory belongs to process
+    j // g), which does not change what any of them computes. With refine_sweeps > 0,
+    each process's in-interval Ritz vectors then go through refine_subspace on its
+    interval. The accepted pairs of all processes are merged in ascending theta with
+    the index of the interval that found each (a pair in two overlapping intervals
+    is reported by both); k_used adds up over the processes, time_steps is the length
+    of the shared trajectory (the most steps any process took), and the Ritz values
+    of the last projections are listed process after process."""
+    R0 = np.atleast_2d(np.asarray(R0, dtype=np.float64))
+    b = R0.shape[0]
+    F = len(intervals)
+    if F < 1 or b % F:
+        raise ValueError("the block width must be a multiple of the number of intervals")
+    g = b // F
+    parts = []
+    for f, (lo, hi) in enumerate(intervals):
+        r = block_krylov_solve(S, m, R0[f * g:(f + 1) * g], lo, hi, tau, L, kmax, tol,
+                               check_every, keep_basis=refine_sweeps > 0)
+        if refine_sweeps > 0:
+            inside = ~np.isnan(r.ritz_rel_res)
+            theta_r, Y = rayleigh_ritz(S, r.basis)
+            X = (Y.T @ r.basis)[inside]
+            if len(X):
+                th, rel, Xa, thi, reli = refine_subspace(S, m, X, lo, hi, tau, L, tol,
+                                                         refine_sweeps)
+                X_acc, a_acc = Xa, np.array([np.linalg.norm(S @ x - t * (m * x))
+                                             for t, x in zip(th, Xa)])
+                r = KrylovResult(omega2=th, omega=np.sqrt(th), rel_res=rel, abs_res=a_acc,
+                                 vectors=X_acc, k_used=r.k_used, time_steps=r.time_steps,
+                                 breakdown=r.breakdown, ritz_theta=r.ritz_theta,
+                                 ritz_rel_res=r.ritz_rel_res, basis=None, history=r.history)
+        parts.append(r)
+    theta = np.concatenate([r.omega2 for r in parts])
+    label = np.concatenate([np.full(len(r.omega2), f, dtype=np.int64) for f, r in enumerate(parts)])
+    order = np.argsort(theta, kind="stable")
+    n = len(m)
+    return KrylovResult(
+        omega2=theta[order], omega=np.sqrt(theta[order]),
+        rel_res=np.concatenate([r.rel_res for r in parts])[order],
+        abs_res=np.concatenate([r.abs_res for r in parts])[order],
+        vectors=np.concatenate([np.reshape(r.vectors, (-1, n)) for r in parts])[order],
+        k_used=sum(r.k_used for r in parts), time_steps=max(r.time_steps for r in parts),
+        breakdown=any(r.breakdown for r in parts),
+        ritz_theta=np.concatenate([r.ritz_theta for r in parts]),
+        ritz_rel_res=np.concatenate([r.ritz_rel_res for r in parts]),
+        basis=None, history=[r.history for r in parts], interval=label[order])
 
 
 def refine_subspace(S, m: np.ndarray, X: np.ndarray, omega_min: float, omega_max: float,

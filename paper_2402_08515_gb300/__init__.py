@@ -25,7 +25,7 @@ __all__ = [
     "kes_filter_apply", "kes_krylov_solve", "kes_get_stats", "kes_reset_stats",
     "Context", "header_functions", "kes_filter_apply_noalloc", "KES_NOALLOC_MAX_N",
     "kes_create_batch", "kes_mesh_count", "kes_estimate_omega_max_batch", "kes_set_filters_batch",
-    "kes_block_krylov_solve",
+    "kes_block_krylov_solve", "kes_set_weights", "kes_alpha_gaussian", "kes_filter_apply_columns",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -70,7 +70,8 @@ class KesResult(C.Structure):
                 ("omega", C.POINTER(C.c_double)), ("rel_res", C.POINTER(C.c_double)),
                 ("abs_res", C.POINTER(C.c_double)), ("vectors", C.POINTER(C.c_double)),
                 ("ritz_omega2", C.POINTER(C.c_double)), ("ritz_rel_res", C.POINTER(C.c_double)),
-                ("solve_ms", C.c_double), ("refine_steps", C.c_int64)]
+                ("solve_ms", C.c_double), ("refine_steps", C.c_int64),
+                ("interval", C.POINTER(C.c_int32))]
 
 
 class KesStats(C.Structure):
@@ -97,6 +98,7 @@ _sig = {
     "kes_sym_eig": (C.c_int, [C.c_int32, _P, _P, _P]),
     "kes_step_bytes": (C.c_int64, [_P, C.c_int32, C.c_int32]),
     "kes_filter_apply": (C.c_int, [_P, _P, _P, C.c_int32, C.c_int32]),
+    "kes_filter_apply_columns": (C.c_int, [_P, _P, _P, C.c_int32, C.c_int32]),
     "kes_krylov_solve": (C.c_int, [_P, _P, C.c_int32, C.POINTER(KesSolveOpts), C.POINTER(C.POINTER(KesResult))]),
     "kes_result_free": (None, [C.POINTER(KesResult)]),
     "kes_get_stats": (C.c_int, [_P, C.POINTER(KesStats)]),
@@ -108,6 +110,8 @@ _sig = {
     "kes_set_filters_batch": (C.c_int, [_P, C.c_int32, _P, _P, _P, C.c_int32]),
     "kes_block_krylov_solve": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.POINTER(KesSolveOpts),
                                          C.POINTER(C.POINTER(KesResult))]),
+    "kes_set_weights": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, C.c_int32]),
+    "kes_alpha_gaussian": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_int32, _P]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(lib, _name)
@@ -215,6 +219,25 @@ def kes_filter_response(omega_min: float, omega_max: float, tau: float, L: int, 
     return out
 
 
+def kes_alpha_gaussian(center: float, sigma: float, tau: float, L: int) -> np.ndarray:
+    out = np.empty(L + 1)
+    _check(lib.kes_alpha_gaussian(float(center), float(sigma), float(tau), int(L), _ptr(out)), "kes_alpha_gaussian")
+    return out
+
+
+def kes_set_weights(ctx: int, alpha, omega_min, omega_max, tau, L: int) -> None:
+    """alpha: (n_mesh, F, L+1) weight tables; omega_min/omega_max: (n_mesh, F); tau: (n_mesh,)."""
+    a = np.ascontiguousarray(np.asarray(alpha, dtype=np.float64).reshape(-1))
+    wmin = np.ascontiguousarray(np.atleast_2d(omega_min), dtype=np.float64)
+    wmax = np.ascontiguousarray(np.atleast_2d(omega_max), dtype=np.float64)
+    t = _f64_host(np.atleast_1d(tau))
+    F = wmin.shape[1]
+    if a.size != wmin.shape[0] * F * (L + 1):
+        raise ValueError("alpha must hold n_mesh * F * (L + 1) weights")
+    _check(lib.kes_set_weights(ctx, F, a.ctypes.data, wmin.ctypes.data, wmax.ctypes.data, t.ctypes.data, int(L)),
+           "kes_set_weights")
+
+
 def kes_sym_eig(A) -> tuple[np.ndarray, np.ndarray]:
     A = np.asfortranarray(A, dtype=np.float64)
     k = A.shape[0]
@@ -241,6 +264,20 @@ def kes_filter_apply(ctx: int, r_in, r_out, b: int = 1) -> None:
            "kes_filter_apply")
 
 
+def kes_filter_apply_columns(ctx: int, r_in, r_out, b: int) -> None:
+    """r_in, r_out: (b, n) float64, both numpy (host) or both CUDA tensors; column j is
+    filtered with weight table j // (b // F)."""
+    dev = _is_device(r_in)
+    if dev != _is_device(r_out):
+        raise ValueError("r_in and r_out must both be host arrays or both device tensors")
+    if not dev:
+        if not (isinstance(r_out, np.ndarray) and r_out.dtype == np.float64 and r_out.flags.c_contiguous):
+            raise ValueError("r_out must be a C-contiguous float64 numpy array")
+        r_in = _f64_host(r_in)
+    _check(lib.kes_filter_apply_columns(ctx, _ptr(r_in), _ptr(r_out), int(b),
+                                        KES_MEM_DEVICE if dev else KES_MEM_HOST), "kes_filter_apply_columns")
+
+
 def _arr(p, k):
     return np.ctypeslib.as_array(p, shape=(k,)).copy() if k > 0 else np.zeros(0)
 
@@ -253,7 +290,9 @@ def _result_dict(rp, st) -> dict:
                    time_steps=r.time_steps, omega2=_arr(r.omega2, p), omega=_arr(r.omega, p),
                    rel_res=_arr(r.rel_res, p), abs_res=_arr(r.abs_res, p),
                    ritz_omega2=_arr(r.ritz_omega2, r.n_ritz), ritz_rel_res=_arr(r.ritz_rel_res, r.n_ritz),
-                   solve_ms=r.solve_ms, refine_steps=r.refine_steps, vectors=None)
+                   solve_ms=r.solve_ms, refine_steps=r.refine_steps, vectors=None,
+                   interval=(np.ctypeslib.as_array(r.interval, shape=(p,)).astype(np.int64) if p > 0
+                             else np.zeros(0, dtype=np.int64)))
         if r.vectors and p > 0:
             out["vectors"] = np.ctypeslib.as_array(r.vectors, shape=(p * r.n,)).copy().reshape(p, r.n)
     finally:

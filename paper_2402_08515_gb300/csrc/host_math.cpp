@@ -25,6 +25,19 @@ void alpha_table(double wmin, double wmax, double tau, int L, double* alpha) {
   }
 }
 
+// Gaussian pass band (Sec. 4, "Weight function"): the inverse cosine transform
+// alpha(t) = (2/pi) int_0^inf beta(s) cos(ts) ds of the even band
+// beta(s) = exp(-(s-c)^2/(2 sigma^2)) + exp(-(s+c)^2/(2 sigma^2)) is
+// 2 sigma sqrt(2/pi) exp(-sigma^2 t^2 / 2) cos(c t); alpha_n = tau alpha(n tau).
+void alpha_gaussian(double center, double sigma, double tau, int L, double* alpha) {
+  const double pi = 3.14159265358979323846;
+  const double amp = 2.0 * sigma * std::sqrt(2.0 / pi);
+  for (int n = 0; n <= L; ++n) {
+    const double t = n * tau;
+    alpha[n] = tau * amp * std::exp(-0.5 * sigma * sigma * t * t) * std::cos(center * t);
+  }
+}
+
 // beta~(omega) = sum_n alpha_n q_n(omega); q_{-1} = q_0 = 1,
 // q_{n+1} = (2 - tau^2 omega^2) q_n - q_{n-1}.
 void filter_response(double wmin, double wmax, double tau, int L, const double* omega, int64_t k,

@@ -93,7 +93,9 @@ template <typename T, int NB, bool FIRST, bool LAST, int MINB>
 __global__ void __launch_bounds__(256, MINB)
     k_step_blk(SellDev A, const T* __restrict__ x, const T* prev, T* out, T* acc_s,
                T* acc_c, double* acc64, int64_t acc_stride, int F, const T* __restrict__ ahi,
-               const T* __restrict__ alo, int Lp1, int step, int* flag) {
+               const T* __restrict__ alo, int Lp1, int step, int cpt, int* flag) {
+  // cpt == 0: every column accumulates with all F weight tables (F accumulators);
+  // cpt > 0: column j accumulates only with table min(j / cpt, F - 1) (one accumulator)
   constexpr bool kF32 = std::is_same<T, float>::value;
   const T* val;
   if constexpr (kF32) val = A.val32;
@@ -143,19 +145,41 @@ __global__ void __launch_bounds__(256, MINB)
     }
     if (!LAST) store_row<NB>(out + row * NB, un);
     bool bad = false;
-    for (int f = 0; f < F; ++f) {
-      const int64_t ai = (mesh * F + f) * Lp1;
+    const int nacc = cpt ? 1 : F;
+    for (int f = 0; f < nacc; ++f) {
       const int64_t at = f * acc_stride + row * NB;
+      // this step's weights per column (the start weight alpha_0 too on the first step)
+      T ah[NB], al[NB], a0[NB];
+      if (cpt) {
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+          const int64_t ai = (mesh * F + min(j / cpt, F - 1)) * Lp1;  // padding columns: last table
+          ah[j] = ahi[ai + step + 1];
+          if constexpr (kF32) al[j] = alo[ai + step + 1];
+          if constexpr (FIRST && !kF32) a0[j] = ahi[ai];
+        }
+      } else {
+        const int64_t ai = (mesh * F + f) * Lp1;
+        const T h = ahi[ai + step + 1];
+        T l = T(0), z = T(0);
+        if constexpr (kF32) l = alo[ai + step + 1];
+        if constexpr (FIRST && !kF32) z = ahi[ai];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+          ah[j] = h;
+          al[j] = l;
+          a0[j] = z;
+        }
+      }
       if constexpr (kF32) {
-        const float a_hi = ahi[ai + step + 1], a_lo = alo[ai + step + 1];
         float as[NB], ac[NB];
         load_plain<NB>(acc_s + at, as);
         load_plain<NB>(acc_c + at, ac);
         double v64[NB];
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
-          const float p = __fmul_rn(a_hi, un[j]);
-          const float pe = fmaf(a_lo, un[j], fmaf(a_hi, un[j], -p));
+          const float p = __fmul_rn(ah[j], un[j]);
+          const float pe = fmaf(al[j], un[j], fmaf(ah[j], un[j], -p));
           float sn, e;
           two_sum(as[j], p, sn, e);
           const float cn = __fadd_rn(ac[j], __fadd_rn(e, pe));
@@ -171,18 +195,16 @@ __global__ void __launch_bounds__(256, MINB)
           store_row<NB>(acc_c + at, ac);
         }
       } else {
-        const double a1 = ahi[ai + step + 1];
-        const double a0 = FIRST ? ahi[ai] : 0.0;
         double na[NB];
         if constexpr (FIRST) {
 #pragma unroll
-          for (int j = 0; j < NB; ++j) na[j] = a0 * xi[j];
+          for (int j = 0; j < NB; ++j) na[j] = a0[j] * xi[j];
         } else {
           load_plain<NB>(acc_s + at, na);
         }
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
-          na[j] = fma(a1, un[j], na[j]);
+          na[j] = fma(ah[j], un[j], na[j]);
           if (LAST) bad |= !isfinite(na[j]);
         }
         store_row<NB>(acc_s + at, na);
@@ -198,8 +220,8 @@ __global__ void __launch_bounds__(256, MINB)
 template <typename T, int NB, int MINB>
 void blk_impl(int grid, int block, cudaStream_t st, bool first, bool last, const SellDev& A, const T* x,
               const T* prev, T* out, T* acc_s, T* acc_c, double* acc64, int64_t acc_stride, int F, const T* ahi,
-              const T* alo, int Lp1, int step, int* flag) {
-#define KES_BLK_ARGS A, x, prev, out, acc_s, acc_c, acc64, acc_stride, F, ahi, alo, Lp1, step, flag
+              const T* alo, int Lp1, int step, int cpt, int* flag) {
+#define KES_BLK_ARGS A, x, prev, out, acc_s, acc_c, acc64, acc_stride, F, ahi, alo, Lp1, step, cpt, flag
   if (first && last) k_step_blk<T, NB, true, true, MINB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
   else if (first) k_step_blk<T, NB, true, false, MINB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
   else if (last) k_step_blk<T, NB, false, true, MINB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
@@ -210,12 +232,12 @@ void blk_impl(int grid, int block, cudaStream_t st, bool first, bool last, const
 template <typename T>
 void blk_dispatch(const LaunchCfg& cfg, int NB, cudaStream_t st, bool first, bool last, const SellDev& A,
                   const T* x, const T* prev, T* out, T* acc_s, T* acc_c, double* acc64, int64_t acc_stride, int F,
-                  const T* ahi, const T* alo, int Lp1, int step, int* flag) {
+                  const T* ahi, const T* alo, int Lp1, int step, int cpt, int* flag) {
   const int64_t need = (A.n_slices + 7) / 8;
   const int grid = static_cast<int>(need < cfg.grid_blk ? need : cfg.grid_blk);
 #define KES_CALL(NBV, M)                                                                                   \
   blk_impl<T, NBV, M>(grid, 256, st, first, last, A, x, prev, out, acc_s, acc_c, acc64, acc_stride, F,        \
-                      ahi, alo, Lp1, step, flag)
+                      ahi, alo, Lp1, step, cpt, flag)
 #define X(ID, M)                         \
   case ID:                               \
     if (NB == 2) KES_CALL(2, M);         \
@@ -319,18 +341,18 @@ int blk_blocks_per_sm(bool fp32, int NB, int variant, int block) {
 
 void launch_step_blk_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, int NB, bool first, bool last,
                          const double* x, const double* prev, double* out, double* acc, int64_t acc_stride, int F,
-                         const double* alpha, int L, int step, int* flag) {
+                         const double* alpha, int L, int step, int cpt, int* flag) {
   blk_dispatch<double>(cfg, NB, st, first, last, A, x, prev, out, acc, nullptr, nullptr, acc_stride, F, alpha,
-                       nullptr, L + 1, step, flag);
+                       nullptr, L + 1, step, cpt, flag);
   ++g_launches;
 }
 
 void launch_step_blk_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, int NB, bool first, bool last,
                          const float* x, const float* prev, float* out, float* acc_s, float* acc_c, double* acc64,
                          int64_t acc_stride, int F, const float* alpha_hi, const float* alpha_lo, int L, int step,
-                         int* flag) {
+                         int cpt, int* flag) {
   blk_dispatch<float>(cfg, NB, st, first, last, A, x, prev, out, acc_s, acc_c, acc64, acc_stride, F, alpha_hi,
-                      alpha_lo, L + 1, step, flag);
+                      alpha_lo, L + 1, step, cpt, flag);
   ++g_launches;
 }
 

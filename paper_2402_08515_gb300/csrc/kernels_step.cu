@@ -146,17 +146,21 @@ __global__ void __launch_bounds__(256, MINB) k_step_f32(SellDev A, const float* 
 }
 
 // FP32 start for nb columns (row-major, nb values per row): x32 = (float) r64 and the
-// compensated accumulator of weight table f set to alpha_f[0] r, split as s + c.
+// compensated accumulator of weight table f set to alpha_f[0] r, split as s + c (cpt > 0:
+// one accumulator per column, with table min(column / cpt, F - 1)).
 __global__ void k_init_f32(int64_t count, int nb, const double* __restrict__ r, float* __restrict__ x32,
                            float* __restrict__ acc_s, float* __restrict__ acc_c, int64_t acc_stride, int F,
-                           const double* __restrict__ alpha, int Lp1, const int32_t* __restrict__ slice_mesh) {
+                           const double* __restrict__ alpha, int Lp1, const int32_t* __restrict__ slice_mesh,
+                           int cpt) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < count;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const double ri = r[i];
     const int64_t mesh = slice_mesh ? slice_mesh[(i / nb) / kSliceC] : 0;
     x32[i] = static_cast<float>(ri);
-    for (int f = 0; f < F; ++f) {
-      const double t = alpha[(mesh * F + f) * Lp1] * ri;
+    const int nacc = cpt ? 1 : F;
+    for (int f = 0; f < nacc; ++f) {
+      const int table = cpt ? min(static_cast<int>(i % nb) / cpt, F - 1) : f;
+      const double t = alpha[(mesh * F + table) * Lp1] * ri;
       const float s = static_cast<float>(t);
       acc_s[f * acc_stride + i] = s;
       acc_c[f * acc_stride + i] = static_cast<float>(t - static_cast<double>(s));
@@ -334,11 +338,11 @@ void launch_step_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bo
 }
 
 void launch_init_f32(cudaStream_t st, const SellDev& A, int nb, const double* r64, float* x32, float* acc_s,
-                     float* acc_c, int64_t acc_stride, int F, const double* alpha64, int L) {
+                     float* acc_c, int64_t acc_stride, int F, const double* alpha64, int L, int cpt) {
   const int64_t count = A.n_pad * nb;
   const int64_t blocks = (count + 255) / 256;
   k_init_f32<<<static_cast<int>(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(
-      count, nb, r64, x32, acc_s, acc_c, acc_stride, F, alpha64, L + 1, A.slice_mesh);
+      count, nb, r64, x32, acc_s, acc_c, acc_stride, F, alpha64, L + 1, A.slice_mesh, cpt);
   ++g_launches;
 }
 

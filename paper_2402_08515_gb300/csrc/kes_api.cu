@@ -78,6 +78,7 @@ struct LaunchCount {
 struct GraphEntry {
   int NB = 0;
   bool fp64 = true;
+  int cpt = 0;
   cudaGraphExec_t exec = nullptr;
   int64_t nodes = 0;
 };
@@ -134,12 +135,13 @@ struct kes_ctx {
   std::vector<GraphEntry> graphs;
   int g_F = -1, g_L = -1;
   // Krylov workspace
-  int kcap = 0;
-  double* B = nullptr;   // n_pad x kcap, column-major; mesh j uses rows row_off_j ..
+  int kcap = 0, kF = 0;  // basis vectors per process, intervals (processes per mesh)
+  double* B = nullptr;   // n_pad x (kF * kcap), column-major: interval f owns columns f * kcap ..,
+                         // mesh j its rows row_off_j ..
   double* SB = nullptr;
-  double* Hd = nullptr;  // n_mesh x kcap x kcap; column k of mesh j holds b_i^T S b_k, i <= k
+  double* Hd = nullptr;  // (n_mesh * kF) x kcap x kcap; column k of process p holds b_i^T S b_k, i <= k
   double* partial = nullptr;
-  double* scal = nullptr;  // per mesh: 2 * kcap + kScal device scalars
+  double* scal = nullptr;  // per process: 2 * kcap + kScal device scalars
   double* Yd = nullptr;
   double* thd = nullptr;
   double* Xd = nullptr;
@@ -261,8 +263,9 @@ void block_out(kes_ctx* c, const double* src, int NB, int nb, double* dst, int32
 
 // --------------------------------------------------------------- filter
 // Issues the L fused steps of one filter application of an NB-column block on the
-// context stream: stage_in -> stage_out (F filtered blocks).
-int64_t issue_filter_steps(kes_ctx* c, int NB, bool fp64) {
+// context stream: stage_in -> stage_out (cpt = 0: F filtered blocks, every column with
+// every weight table; cpt > 0: one block, column j with table min(j / cpt, F - 1)).
+int64_t issue_filter_steps(kes_ctx* c, int NB, bool fp64, int cpt) {
   const int64_t before = g_launches;
   const int L = c->L, F = c->F;
   const int64_t stride = c->n_pad * NB;
@@ -285,11 +288,11 @@ int64_t issue_filter_steps(kes_ctx* c, int NB, bool fp64) {
                         c->d_flag);
       else
         launch_step_blk_f64(A64, cfg, c->stream, NB, first, last, x, prev, out, c->stage_out, stride, F, c->alpha64,
-                            L, s, c->d_flag);
+                            L, s, cpt, c->d_flag);
     }
   } else {
     const SellDev A32 = c->step_A32();
-    launch_init_f32(c->stream, c->A, NB, c->stage_in, c->U32[2], c->acc_s, c->acc_c, stride, F, c->alpha64, L);
+    launch_init_f32(c->stream, c->A, NB, c->stage_in, c->U32[2], c->acc_s, c->acc_c, stride, F, c->alpha64, L, cpt);
     for (int s = 0; s < L; ++s) {
       const bool first = s == 0, last = s == L - 1;
       const float* x = s == 0 ? c->U32[2] : c->U32[(s - 1) & 1];
@@ -300,7 +303,7 @@ int64_t issue_filter_steps(kes_ctx* c, int NB, bool fp64) {
                         F, c->alpha_hi, c->alpha_lo, L, s, c->d_flag);
       else
         launch_step_blk_f32(A32, c->cfg, c->stream, NB, first, last, x, prev, out, c->acc_s, c->acc_c, c->stage_out,
-                            stride, F, c->alpha_hi, c->alpha_lo, L, s, c->d_flag);
+                            stride, F, c->alpha_hi, c->alpha_lo, L, s, cpt, c->d_flag);
     }
   }
   return g_launches - before;
@@ -317,7 +320,8 @@ void ensure_fp64_state(kes_ctx* c) {
   }
 }
 
-void run_filter(kes_ctx* c, int NB, bool fp64) {
+void run_filter(kes_ctx* c, int NB, bool fp64, int cpt = 0) {
+  if (cpt > 0 && NB < 2) throw KesError{KES_ERR_ARG};  // per-column tables live in the block kernels
   if (fp64) ensure_fp64_state(c);
   cudaEvent_t e0 = c->get_event(), e1 = c->get_event();
   KES_CUDA(cudaEventRecord(e0, c->stream));
@@ -329,17 +333,18 @@ void run_filter(kes_ctx* c, int NB, bool fp64) {
     }
     GraphEntry* ge = nullptr;
     for (auto& g : c->graphs)
-      if (g.NB == NB && g.fp64 == fp64) ge = &g;
+      if (g.NB == NB && g.fp64 == fp64 && g.cpt == cpt) ge = &g;
     if (!ge) {
       cudaGraph_t graph;
       KES_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-      const int64_t nodes = issue_filter_steps(c, NB, fp64);
+      const int64_t nodes = issue_filter_steps(c, NB, fp64, cpt);
       cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
       g_launches -= nodes;  // captured, not launched
       KES_CUDA(ce);
       GraphEntry g;
       g.NB = NB;
       g.fp64 = fp64;
+      g.cpt = cpt;
       g.nodes = nodes;
       ce = cudaGraphInstantiate(&g.exec, graph, 0);
       cudaGraphDestroy(graph);
@@ -350,7 +355,7 @@ void run_filter(kes_ctx* c, int NB, bool fp64) {
     KES_CUDA(cudaGraphLaunch(ge->exec, c->stream));
     g_launches += ge->nodes;  // every node of the replayed graph is a kernel launch
   } else {
-    issue_filter_steps(c, NB, fp64);
+    issue_filter_steps(c, NB, fp64, cpt);
     KES_CHECK_LAUNCH();
   }
   KES_CUDA(cudaEventRecord(e1, c->stream));
@@ -386,21 +391,26 @@ kes_status check_flag(kes_ctx* c) {
 }
 
 // --------------------------------------------------------------- Krylov workspace
-void ensure_krylov(kes_ctx* c, int kmax) {
-  if (c->kcap >= kmax) return;
+// A process is the Krylov iteration of one mesh on one interval (p = mesh * F + f).
+void ensure_krylov(kes_ctx* c, int kmax, int F) {
+  if (c->kcap >= kmax && c->kF >= F) return;
   for (double* p : {c->B, c->SB, c->Hd, c->partial, c->scal, c->Yd, c->thd}) c->dfree(p);
-  const int nm = c->n_mesh();
+  kmax = std::max(kmax, c->kcap);
+  F = std::max(F, c->kF);
+  const int64_t nproc = static_cast<int64_t>(c->n_mesh()) * F;
   c->kcap = kmax;
-  c->B = c->dzero_n<double>(static_cast<int64_t>(kmax) * c->n_pad);
-  c->SB = c->dzero_n<double>(static_cast<int64_t>(kmax) * c->n_pad);
-  c->Hd = c->dzero_n<double>(static_cast<int64_t>(nm) * kmax * kmax);
+  c->kF = F;
+  c->B = c->dzero_n<double>(static_cast<int64_t>(F) * kmax * c->n_pad);
+  c->SB = c->dzero_n<double>(static_cast<int64_t>(F) * kmax * c->n_pad);
+  c->Hd = c->dzero_n<double>(nproc * kmax * kmax);
   c->partial = c->dalloc_n<double>(static_cast<int64_t>(kDotBlocks) * (2 * kmax + 8));
-  c->scal = c->dzero_n<double>(static_cast<int64_t>(nm) * (2 * kmax + kScal));
+  c->scal = c->dzero_n<double>(nproc * (2 * kmax + kScal));
   c->Yd = c->dalloc_n<double>(static_cast<int64_t>(kmax) * kmax);
   c->thd = c->dalloc_n<double>(kmax);
 }
 
-double* mesh_scal(kes_ctx* c, int j) { return c->scal + static_cast<int64_t>(j) * (2 * c->kcap + kScal); }
+// Device scalars of process p (of mesh p outside the solver).
+double* proc_scal(kes_ctx* c, int p) { return c->scal + static_cast<int64_t>(p) * (2 * c->kcap + kScal); }
 
 // The slices of one mesh as a matrix of its own (columns stay global row indices).
 SellDev mesh_sell(const kes_ctx* c, const MeshInfo& m) {
@@ -485,10 +495,10 @@ void tune_steps(kes_ctx* c) {
         for (int i = 0; i < count; ++i) {
           if (fp32)
             launch_step_blk_f32(c->step_A32(), c->cfg, c->stream, NB, false, false, c->U32[0], c->U32[1], c->U32[1],
-                                c->acc_s, c->acc_c, c->stage_out, c->n_pad * NB, 1, a32, a32, 7, 1, c->d_flag);
+                                c->acc_s, c->acc_c, c->stage_out, c->n_pad * NB, 1, a32, a32, 7, 1, 0, c->d_flag);
           else
             launch_step_blk_f64(c->step_A64(), c->cfg, c->stream, NB, false, false, c->U64[0], c->U64[1], c->U64[1],
-                                c->stage_out, c->n_pad * NB, 1, a64, 7, 1, c->d_flag);
+                                c->stage_out, c->n_pad * NB, 1, a64, 7, 1, 0, c->d_flag);
         }
       });
       if (ms < best_ms) {
@@ -694,8 +704,11 @@ kes_status create_impl(kes_ctx** out, int32_t nm, const int64_t* n, const int64_
   return KES_OK;
 }
 
-kes_status set_filters_impl(kes_ctx* c, int32_t F, const double* wmin, const double* wmax, const double* tau,
-                            int32_t L) {
+// Installs F weight tables per mesh (alpha: [n_mesh][F][L+1], or null: the indicator
+// weights of eq. (weightf) for [wmin, wmax]); [wmin, wmax] is also the interval in which
+// the solver accepts Ritz pairs.
+kes_status set_weights_impl(kes_ctx* c, int32_t F, const double* alpha, const double* wmin, const double* wmax,
+                            const double* tau, int32_t L) {
   const int nm = c->n_mesh();
   for (int j = 0; j < nm; ++j) {
     if (!(tau[j] > 0.0) || !std::isfinite(tau[j])) return KES_ERR_ARG;
@@ -705,13 +718,20 @@ kes_status set_filters_impl(kes_ctx* c, int32_t F, const double* wmin, const dou
     }
     if (c->meshes[j].omega_est > 0.0 && tau[j] * c->meshes[j].omega_est >= 2.0) return KES_ERR_UNSTABLE;
   }
+  const size_t need = static_cast<size_t>(nm) * F * (L + 1);
+  if (alpha)
+    for (size_t i = 0; i < need; ++i)
+      if (!std::isfinite(alpha[i])) return KES_ERR_ARG;
   return guarded([&]() -> kes_status {
-    const size_t need = static_cast<size_t>(nm) * F * (L + 1);
     std::vector<double> a64(need, 0.0);
-    for (int j = 0; j < nm; ++j)
-      for (int f = 0; f < F; ++f)
-        alpha_table(wmin[j * F + f], wmax[j * F + f], tau[j], L,
-                    a64.data() + (static_cast<size_t>(j) * F + f) * (L + 1));
+    if (alpha) {
+      std::memcpy(a64.data(), alpha, need * sizeof(double));
+    } else {
+      for (int j = 0; j < nm; ++j)
+        for (int f = 0; f < F; ++f)
+          alpha_table(wmin[j * F + f], wmax[j * F + f], tau[j], L,
+                      a64.data() + (static_cast<size_t>(j) * F + f) * (L + 1));
+    }
     c->sync();
     if (need > c->alpha_cap) {
       c->dfree(c->alpha64);
@@ -762,14 +782,14 @@ kes_status omega_impl(kes_ctx* c, int32_t iters, const double* v0, double* omega
   LaunchCount lc(&c->stats);
   return guarded([&]() -> kes_status {
     const int nm = c->n_mesh();
-    ensure_krylov(c, 2);
+    ensure_krylov(c, 2, 1);
     double* v = c->B;  // scratch n_pad vectors
     double* w = c->SB;
     cudaStream_t s = c->stream;
     block_in(c, v0, 1, KES_MEM_HOST, 1, w);
     for (int j = 0; j < nm; ++j) {
       const MeshInfo& mi = c->meshes[j];
-      double* sc = mesh_scal(c, j);
+      double* sc = proc_scal(c, j);
       launch_mdot(s, w + mi.row_off, 0, 1, w + mi.row_off, nullptr, mi.n_pad, c->partial, sc);
       launch_scale_rsqrt(s, w + mi.row_off, sc, v + mi.row_off, nullptr, mi.n_pad);
     }
@@ -777,7 +797,7 @@ kes_status omega_impl(kes_ctx* c, int32_t iters, const double* v0, double* omega
       launch_spmv_f64(c->A, c->cfg, s, v, c->minv64, w);
       for (int j = 0; j < nm; ++j) {
         const MeshInfo& mi = c->meshes[j];
-        double* sc = mesh_scal(c, j);
+        double* sc = proc_scal(c, j);
         launch_mdot(s, w + mi.row_off, 0, 1, w + mi.row_off, nullptr, mi.n_pad, c->partial, sc);
         launch_scale_rsqrt(s, w + mi.row_off, sc, v + mi.row_off, nullptr, mi.n_pad);
       }
@@ -786,7 +806,7 @@ kes_status omega_impl(kes_ctx* c, int32_t iters, const double* v0, double* omega
     std::vector<double> h(2 * nm);
     for (int j = 0; j < nm; ++j) {
       const MeshInfo& mi = c->meshes[j];
-      double* sc = mesh_scal(c, j);
+      double* sc = proc_scal(c, j);
       launch_mdot(s, v + mi.row_off, 0, 1, w + mi.row_off, nullptr, mi.n_pad, c->partial, sc);  // v^T S v
       launch_mdot(s, v + mi.row_off, 0, 1, v + mi.row_off, c->m64 + mi.row_off, mi.n_pad, c->partial,
                   sc + 1);  // v^T M v
@@ -806,26 +826,36 @@ kes_status omega_impl(kes_ctx* c, int32_t iters, const double* v0, double* omega
 // ------------------------------------------------------------------ block Krylov solver
 struct MeshSolve {
   int k = 0;            // basis vectors
-  bool done = false;    // no further blocks for this mesh
+  bool done = false;    // no further blocks for this process
   bool breakdown = false;
   int kproj = -1;       // basis size at the last projection
   std::vector<double> last_theta, last_rel;
   std::vector<double> acc_theta, acc_rel, acc_abs, acc_Y;
 };
 
-double* hdup(const std::vector<double>& v) {
-  double* d = static_cast<double*>(std::malloc(std::max<size_t>(1, v.size()) * sizeof(double)));
+template <typename T>
+T* hdup(const std::vector<T>& v) {
+  T* d = static_cast<T*>(std::malloc(std::max<size_t>(1, v.size()) * sizeof(T)));
   if (!d) throw std::bad_alloc();
-  if (!v.empty()) std::memcpy(d, v.data(), v.size() * sizeof(double));
+  if (!v.empty()) std::memcpy(d, v.data(), v.size() * sizeof(T));
   return d;
 }
 
+
+// The block solver over every mesh and interval of the context. Process p = mesh * F + f
+// is the block Krylov iteration of mesh p / F on interval f from start columns
+// f * g .. f * g + g - 1 (g = b / F), with its own basis, Gram-Schmidt scalars and
+// projected matrix; the processes share only the b-column trajectory of each block step.
 kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, const kes_solve_opts& so,
                             kes_result** out) {
   const int nm = c->n_mesh();
+  const int F = c->F;
+  const int P = nm * F;
+  const int g = b / F;                // columns per process
+  const int cpt = F > 1 ? g : 0;      // column j of a block takes weight table j / g
   const int kmax = so.kmax;
   const int NB = nb_for(b);
-  std::vector<MeshSolve> ms(nm);
+  std::vector<MeshSolve> ms(P);
   std::vector<kes_result*> res(nm, nullptr);
   for (int j = 0; j < nm; ++j) {
     res[j] = static_cast<kes_result*>(std::calloc(1, sizeof(kes_result)));
@@ -837,11 +867,10 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
   const auto t_start = std::chrono::steady_clock::now();
   LaunchCount lc(&c->stats);
   kes_status st = guarded([&]() -> kes_status {
-    ensure_krylov(c, kmax);
+    ensure_krylov(c, kmax, F);
     const int64_t np = c->n_pad;
+    const int64_t kc = c->kcap;
     cudaStream_t s = c->stream;
-    double* B = c->B;
-    double* SB = c->SB;
     auto other_begin = [&]() {
       cudaEvent_t e0 = c->get_event();
       KES_CUDA(cudaEventRecord(e0, s));
@@ -852,34 +881,45 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
       KES_CUDA(cudaEventRecord(e1, s));
       c->ev_other.emplace_back(e0, e1);
     };
-    auto Hcol = [&](int j, int k) { return c->Hd + (static_cast<int64_t>(j) * c->kcap + k) * c->kcap; };
+    auto mesh_of = [&](int p) -> const MeshInfo& { return c->meshes[p / F]; };
+    // column 0 of process p's basis over all rows (SpMV input) and on its mesh's rows
+    auto Bfull = [&](int p) { return c->B + (p % F) * kc * np; };
+    auto Bp = [&](int p) { return Bfull(p) + mesh_of(p).row_off; };
+    auto SBp = [&](int p) { return c->SB + (p % F) * kc * np + mesh_of(p).row_off; };
+    auto Hcol = [&](int p, int k) { return c->Hd + (static_cast<int64_t>(p) * kc + k) * kc; };
+    // process that owns column jj of a block of mesh j (-1: a padding column)
+    auto owner = [&](int j, int jj) {
+      const int f = F > 1 ? jj / g : 0;
+      return f < F ? j * F + f : -1;
+    };
 
-    // Orthogonalise column jj of Wc against each mesh's basis (two classical passes in
-    // the M-inner product) and append the vectors that are not dependent (Algorithm 2.5).
-    std::vector<char> want(nm, 1);  // meshes taking part in the current block step
+    // Orthogonalise column jj of Wc against the basis of the process that owns it on
+    // each mesh (two classical passes in the M-inner product) and append the vectors
+    // that are not dependent (Algorithm 2.5).
+    std::vector<char> want(P, 1);  // processes taking part in the current block step
     auto append_column = [&](int jj) {
+      std::vector<char> active(P, 0), added(P, 0);
       cudaEvent_t ev = other_begin();
-      std::vector<char> active(nm, 0);
       for (int j = 0; j < nm; ++j) {
-        if (!want[j] || ms[j].done || ms[j].k >= kmax) continue;
-        active[j] = 1;
+        const int p = owner(j, jj);
+        if (p < 0 || !want[p] || ms[p].done || ms[p].k >= kmax) continue;
+        active[p] = 1;
         const MeshInfo& mi = c->meshes[j];
         double* w = c->Wc + static_cast<int64_t>(jj) * np + mi.row_off;
-        const double* Bj = B + mi.row_off;
         const double* mj = c->m64 + mi.row_off;
-        double* sc = mesh_scal(c, j);
+        double* sc = proc_scal(c, p);
         launch_mdot(s, w, 0, 1, w, mj, mi.n_pad, c->partial, sc);  // ||w||_M^2 before
-        for (int pass = 0; pass < 2 && ms[j].k > 0; ++pass) {
-          launch_mdot(s, Bj, np, ms[j].k, w, mj, mi.n_pad, c->partial, sc + kScal);  // h = B^T M w
-          launch_gemv_sub(s, w, Bj, np, ms[j].k, sc + kScal, mi.n_pad);             // w -= B h
+        for (int pass = 0; pass < 2 && ms[p].k > 0; ++pass) {
+          launch_mdot(s, Bp(p), np, ms[p].k, w, mj, mi.n_pad, c->partial, sc + kScal);  // h = B^T M w
+          launch_gemv_sub(s, w, Bp(p), np, ms[p].k, sc + kScal, mi.n_pad);             // w -= B h
         }
         launch_mdot(s, w, 0, 1, w, mj, mi.n_pad, c->partial, sc + 1);  // ||w||_M^2 after
       }
       KES_CHECK_LAUNCH();
-      std::vector<double> nrm(2 * nm, 0.0);
-      for (int j = 0; j < nm; ++j)
-        if (active[j])
-          KES_CUDA(cudaMemcpyAsync(&nrm[2 * j], mesh_scal(c, j), 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      std::vector<double> nrm(2 * P, 0.0);
+      for (int p = 0; p < P; ++p)
+        if (active[p])
+          KES_CUDA(cudaMemcpyAsync(&nrm[2 * p], proc_scal(c, p), 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
       int flag = 0;
       KES_CUDA(cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
       other_end(ev);
@@ -889,74 +929,81 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
         throw KesError{(flag & 2) ? KES_ERR_TIMEOUT : KES_ERR_UNSTABLE};
       }
       ev = other_begin();
-      std::vector<char> added(nm, 0);
-      for (int j = 0; j < nm; ++j) {
-        if (!active[j]) continue;
-        if (!(std::sqrt(nrm[2 * j + 1]) > 1e-10 * std::sqrt(nrm[2 * j]))) continue;  // dependent vector
-        const MeshInfo& mi = c->meshes[j];
-        const int k = ms[j].k;
+      for (int p = 0; p < P; ++p) {
+        if (!active[p]) continue;
+        if (!(std::sqrt(nrm[2 * p + 1]) > 1e-10 * std::sqrt(nrm[2 * p]))) continue;  // dependent vector
+        const MeshInfo& mi = mesh_of(p);
+        const int k = ms[p].k;
         double* w = c->Wc + static_cast<int64_t>(jj) * np + mi.row_off;
-        double* bk = B + static_cast<int64_t>(k) * np + mi.row_off;
-        double* sbk = SB + static_cast<int64_t>(k) * np + mi.row_off;
-        launch_scale_rsqrt(s, w, mesh_scal(c, j) + 1, bk, nullptr, mi.n_pad);  // b_k
-        launch_spmv_f64(mesh_sell(c, mi), c->cfg, s, B + static_cast<int64_t>(k) * np, nullptr, sbk);  // S b_k
-        launch_mdot(s, B + mi.row_off, np, k + 1, sbk, nullptr, mi.n_pad, c->partial, Hcol(j, k));
-        ms[j].k = k + 1;
-        added[j] = 1;
+        double* sbk = SBp(p) + k * np;
+        launch_scale_rsqrt(s, w, proc_scal(c, p) + 1, Bp(p) + k * np, nullptr, mi.n_pad);  // b_k
+        launch_spmv_f64(mesh_sell(c, mi), c->cfg, s, Bfull(p) + k * np, nullptr, sbk);    // S b_k
+        launch_mdot(s, Bp(p), np, k + 1, sbk, nullptr, mi.n_pad, c->partial, Hcol(p, k));
+        ms[p].k = k + 1;
+        added[p] = 1;
       }
       KES_CHECK_LAUNCH();
       other_end(ev);
       return added;
     };
 
-    auto project = [&](int j) {
-      MeshSolve& m = ms[j];
-      const MeshInfo& mi = c->meshes[j];
-      const int kk = m.k;
-      m.kproj = kk;
+    // The projected matrix of process p mirrored into a full kk x kk array and its
+    // eigenpairs (theta ascending, clamped at 0).
+    auto projected_eig = [&](int p, std::vector<double>& theta, std::vector<double>& Y) {
+      const int kk = ms[p].k;
       std::vector<double> Hh(static_cast<size_t>(kk) * kk, 0.0);
-      KES_CUDA(cudaMemcpy2DAsync(Hh.data(), kk * sizeof(double), Hcol(j, 0), c->kcap * sizeof(double),
+      KES_CUDA(cudaMemcpy2DAsync(Hh.data(), kk * sizeof(double), Hcol(p, 0), kc * sizeof(double),
                                  kk * sizeof(double), kk, cudaMemcpyDeviceToHost, s));
       c->sync();
       // column i holds rows 0..i (upper triangle); mirror it into the lower triangle
       for (int i = 0; i < kk; ++i)
         for (int r = i + 1; r < kk; ++r) Hh[static_cast<size_t>(i) * kk + r] = Hh[static_cast<size_t>(r) * kk + i];
-      std::vector<double> theta(kk), Y(static_cast<size_t>(kk) * kk);
+      theta.assign(kk, 0.0);
+      Y.assign(static_cast<size_t>(kk) * kk, 0.0);
       if (!sym_eig(kk, Hh.data(), theta.data(), Y.data())) throw KesError{KES_ERR_CUDA};
       for (double& t : theta) t = std::max(t, 0.0);
-      const double wmin = mi.wmin[0], wmax = mi.wmax[0];
+    };
+
+    auto project = [&](int p) {
+      MeshSolve& m = ms[p];
+      const MeshInfo& mi = mesh_of(p);
+      const int kk = m.k;
+      m.kproj = kk;
+      std::vector<double> theta, Y;
+      projected_eig(p, theta, Y);
+      const double wmin = mi.wmin[p % F], wmax = mi.wmax[p % F];
       std::vector<int> inside;
       for (int q = 0; q < kk; ++q) {
         const double om = std::sqrt(theta[q]);
         if (om >= wmin && om <= wmax) inside.push_back(q);
       }
-      const int p = static_cast<int>(inside.size());
+      const int np_in = static_cast<int>(inside.size());
       m.last_theta = theta;
       m.last_rel.assign(kk, std::numeric_limits<double>::quiet_NaN());
       m.acc_theta.clear();
       m.acc_rel.clear();
       m.acc_abs.clear();
       m.acc_Y.clear();
-      if (p == 0) return;
-      std::vector<double> Ysel(static_cast<size_t>(kk) * p), thsel(p);
-      for (int q = 0; q < p; ++q) {
+      if (np_in == 0) return;
+      std::vector<double> Ysel(static_cast<size_t>(kk) * np_in), thsel(np_in);
+      for (int q = 0; q < np_in; ++q) {
         thsel[q] = theta[inside[q]];
         std::memcpy(&Ysel[static_cast<size_t>(q) * kk], &Y[static_cast<size_t>(inside[q]) * kk], kk * sizeof(double));
       }
       cudaEvent_t ev = other_begin();
-      double* sc = mesh_scal(c, j);
+      double* sc = proc_scal(c, p);
       KES_CUDA(cudaMemcpyAsync(c->Yd, Ysel.data(), Ysel.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-      KES_CUDA(cudaMemcpyAsync(c->thd, thsel.data(), p * sizeof(double), cudaMemcpyHostToDevice, s));
-      launch_ritz_residual(s, B + mi.row_off, SB + mi.row_off, np, kk, c->Yd, c->thd, p, c->m64 + mi.row_off,
-                           mi.n_pad, c->partial, sc + kScal);
+      KES_CUDA(cudaMemcpyAsync(c->thd, thsel.data(), np_in * sizeof(double), cudaMemcpyHostToDevice, s));
+      launch_ritz_residual(s, Bp(p), SBp(p), np, kk, c->Yd, c->thd, np_in, c->m64 + mi.row_off, mi.n_pad,
+                           c->partial, sc + kScal);
       KES_CHECK_LAUNCH();
-      std::vector<double> rr(2 * p);
-      KES_CUDA(cudaMemcpyAsync(rr.data(), sc + kScal, 2 * p * sizeof(double), cudaMemcpyDeviceToHost, s));
+      std::vector<double> rr(2 * np_in);
+      KES_CUDA(cudaMemcpyAsync(rr.data(), sc + kScal, 2 * np_in * sizeof(double), cudaMemcpyDeviceToHost, s));
       other_end(ev);
       c->sync();
-      for (int q = 0; q < p; ++q) {
+      for (int q = 0; q < np_in; ++q) {
         const double a = std::sqrt(std::max(rr[q], 0.0));
-        const double den = thsel[q] * std::sqrt(std::max(rr[p + q], 0.0));
+        const double den = thsel[q] * std::sqrt(std::max(rr[np_in + q], 0.0));
         const double rel = den > 0.0 ? a / den : std::numeric_limits<double>::infinity();
         m.last_rel[inside[q]] = rel;
         if (rel <= so.tol) {
@@ -969,7 +1016,18 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
       }
     };
 
-    // start block: the b start vectors, M-orthonormalised in order
+    // a mesh that asked for n_wanted pairs stops once its intervals hold that many
+    auto check_wanted = [&]() {
+      if (so.n_wanted <= 0) return;
+      for (int j = 0; j < nm; ++j) {
+        int got = 0;
+        for (int f = 0; f < F; ++f) got += static_cast<int>(ms[j * F + f].acc_theta.size());
+        if (got >= so.n_wanted)
+          for (int f = 0; f < F; ++f) ms[j * F + f].done = true;
+      }
+    };
+
+    // start block: the g start vectors of each process, M-orthonormalised in order
     {
       cudaEvent_t ev = other_begin();
       block_in(c, R0, b, mem, NB, c->stage_in);
@@ -977,173 +1035,220 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
       KES_CHECK_LAUNCH();
       other_end(ev);
       for (int jj = 0; jj < b; ++jj) append_column(jj);
-      for (int j = 0; j < nm; ++j)
-        if (ms[j].k == 0) ms[j].done = ms[j].breakdown = true;
+      for (int p = 0; p < P; ++p)
+        if (ms[p].k == 0) ms[p].done = ms[p].breakdown = true;
     }
     int64_t steps = 0;
-    std::vector<int> next_check(nm, so.check_every);
+    std::vector<int> next_check(P, so.check_every);
     std::vector<int32_t> colsel(static_cast<size_t>(nm) * NB, -1);
     for (;;) {
       bool any = false;
       std::fill(colsel.begin(), colsel.end(), -1);
-      for (int j = 0; j < nm; ++j) {
-        MeshSolve& m = ms[j];
+      for (int p = 0; p < P; ++p) {
+        MeshSolve& m = ms[p];
         if (m.done || m.k >= kmax) continue;
         any = true;
-        // filter the b newest basis vectors (Algorithm 2.5 filters the newest one)
-        for (int jj = 0; jj < b; ++jj) {
-          const int col = m.k - b + jj;
-          colsel[j * NB + jj] = col >= 0 ? col : -1;
+        // filter the g newest basis vectors of each process (Algorithm 2.5 filters the newest one)
+        const int j = p / F, f = p % F;
+        for (int i = 0; i < g; ++i) {
+          const int col = m.k - g + i;
+          colsel[j * NB + f * g + i] = col >= 0 ? static_cast<int32_t>(f * kc + col) : -1;
         }
       }
       if (!any) break;
       KES_CUDA(cudaMemcpyAsync(c->colsel, colsel.data(), colsel.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-      launch_pack_basis(s, B, np, c->colsel, c->slice_mesh, c->stage_in, NB, np);
+      launch_pack_basis(s, c->B, np, c->colsel, c->slice_mesh, c->stage_in, NB, np);
       KES_CHECK_LAUNCH();
-      run_filter(c, NB, c->opts.precision == KES_PREC_FP64);  // stage_in -> stage_out
+      run_filter(c, NB, c->opts.precision == KES_PREC_FP64, cpt);  // stage_in -> stage_out
       steps += c->L;
       launch_unpack_block(s, c->stage_out, NB, c->Wc, np);
       KES_CHECK_LAUNCH();
-      std::vector<int> added(nm, 0);
+      std::vector<int> added(P, 0);
       for (int jj = 0; jj < b; ++jj) {
         std::vector<char> a = append_column(jj);
-        for (int j = 0; j < nm; ++j) added[j] += a[j];
+        for (int p = 0; p < P; ++p) added[p] += a[p];
       }
-      for (int j = 0; j < nm; ++j) {
-        MeshSolve& m = ms[j];
+      for (int p = 0; p < P; ++p) {
+        MeshSolve& m = ms[p];
         if (m.done) continue;
-        if (added[j] == 0 && m.k < kmax) {  // the whole block was dependent: invariant subspace
+        if (added[p] == 0 && m.k < kmax) {  // the whole block was dependent: invariant subspace
           m.done = m.breakdown = true;
           continue;
         }
-        if (m.k >= next_check[j] && m.k < kmax) {
-          while (next_check[j] <= m.k) next_check[j] += so.check_every;
-          project(j);
-          if (so.n_wanted > 0 && static_cast<int>(m.acc_theta.size()) >= so.n_wanted) m.done = true;
+        if (m.k >= next_check[p] && m.k < kmax) {
+          while (next_check[p] <= m.k) next_check[p] += so.check_every;
+          project(p);
         }
       }
+      check_wanted();
     }
-    for (int j = 0; j < nm; ++j)
-      if (ms[j].kproj != ms[j].k) project(j);
+    for (int p = 0; p < P; ++p)
+      if (ms[p].kproj != ms[p].k) project(p);
 
     // FP64 refinement: sweeps of filtered subspace iteration on the in-interval Ritz
-    // vectors (Sec. 4 mentions fixed-dimension, FEAST-like use of the filter): X <- C X
-    // with the FP64 step kernels, M-orthonormalise, Rayleigh-Ritz, residuals.
+    // vectors of each process (Sec. 4 mentions fixed-dimension, FEAST-like use of the
+    // filter): X <- C X with the FP64 step kernels, M-orthonormalise, Rayleigh-Ritz,
+    // residuals. With F intervals the columns of a refinement block are grouped per
+    // interval like those of the Krylov blocks.
     int64_t refine_steps = 0;
+    const int NBr = F > 1 ? NB : c->NBcap;  // columns of one refinement filter call
+    const int gr = F > 1 ? g : NBr;         // of them per interval
     for (int sweep = 0; sweep < so.refine_sweeps; ++sweep) {
-      std::vector<int> pcount(nm, 0);
-      int pmax = 0;
-      for (int j = 0; j < nm; ++j) {
-        MeshSolve& m = ms[j];
-        int p = 0;
-        for (size_t q = 0; q < m.last_rel.size(); ++q) p += std::isnan(m.last_rel[q]) ? 0 : 1;
-        pcount[j] = p;
-        pmax = std::max(pmax, p);
+      std::vector<int> pcount(P, 0);
+      std::vector<int64_t> xoff(F + 1, 0);  // interval f uses columns xoff[f] .. of Xd (meshes share them)
+      int rounds = 0;
+      for (int p = 0; p < P; ++p) {
+        for (double r : ms[p].last_rel) pcount[p] += std::isnan(r) ? 0 : 1;
+        rounds = std::max(rounds, (pcount[p] + gr - 1) / gr);
       }
-      if (pmax == 0) break;
-      const size_t need = static_cast<size_t>(pmax) * np;
+      for (int f = 0; f < F; ++f) {
+        int mx = 0;
+        for (int j = 0; j < nm; ++j) mx = std::max(mx, pcount[j * F + f]);
+        xoff[f + 1] = xoff[f] + mx;
+      }
+      if (xoff[F] == 0) break;
+      const size_t need = static_cast<size_t>(xoff[F]) * np;
       if (need > c->Xd_cap) {
         c->dfree(c->Xd);
         c->Xd = c->dalloc_n<double>(need);
         c->Xd_cap = need;
       }
       KES_CUDA(cudaMemsetAsync(c->Xd, 0, need * sizeof(double), s));
-      // Ritz vectors of every in-interval Ritz value: Xd[:, q] = B y_q on the mesh's rows
-      for (int j = 0; j < nm; ++j) {
-        if (pcount[j] == 0) continue;
-        MeshSolve& m = ms[j];
-        const MeshInfo& mi = c->meshes[j];
+      // Ritz vectors of every in-interval Ritz value: X = B y_q on the mesh's rows
+      for (int p = 0; p < P; ++p) {
+        if (pcount[p] == 0) continue;
+        MeshSolve& m = ms[p];
+        const MeshInfo& mi = mesh_of(p);
         const int kk = m.k;
-        std::vector<double> Hh(static_cast<size_t>(kk) * kk, 0.0);
-        KES_CUDA(cudaMemcpy2DAsync(Hh.data(), kk * sizeof(double), Hcol(j, 0), c->kcap * sizeof(double),
-                                   kk * sizeof(double), kk, cudaMemcpyDeviceToHost, s));
-        c->sync();
-        for (int i = 0; i < kk; ++i)
-          for (int r = i + 1; r < kk; ++r)
-            Hh[static_cast<size_t>(i) * kk + r] = Hh[static_cast<size_t>(r) * kk + i];
-        std::vector<double> theta(kk), Y(static_cast<size_t>(kk) * kk), Ysel;
-        if (!sym_eig(kk, Hh.data(), theta.data(), Y.data())) throw KesError{KES_ERR_CUDA};
+        std::vector<double> theta, Y, Ysel;
+        projected_eig(p, theta, Y);
         for (int q = 0; q < kk; ++q)
           if (!std::isnan(m.last_rel[q]))
             Ysel.insert(Ysel.end(), Y.begin() + static_cast<size_t>(q) * kk, Y.begin() + static_cast<size_t>(q + 1) * kk);
         KES_CUDA(cudaMemcpyAsync(c->Yd, Ysel.data(), Ysel.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-        launch_gemm_bx(s, B + mi.row_off, np, kk, c->Yd, pcount[j], c->Xd + mi.row_off, np, mi.n_pad);
+        launch_gemm_bx(s, Bp(p), np, kk, c->Yd, pcount[p], c->Xd + xoff[p % F] * np + mi.row_off, np, mi.n_pad);
         KES_CHECK_LAUNCH();
-        c->sync();  // Yd is reused by the next mesh
+        c->sync();  // Yd is reused by the next process
       }
-      // filter them with the FP64 kernels, NB at a time, into fresh bases
-      const int NBr = c->NBcap;
-      for (int j = 0; j < nm; ++j) {
-        want[j] = pcount[j] > 0;
-        if (want[j]) {
-          ms[j].k = 0;
-          ms[j].done = false;
+      // filter them with the FP64 kernels, a block of NBr columns at a time, into fresh bases
+      for (int p = 0; p < P; ++p) {
+        want[p] = pcount[p] > 0;
+        if (want[p]) {
+          ms[p].k = 0;
+          ms[p].done = false;
         }
       }
       std::vector<int32_t> csel(static_cast<size_t>(nm) * NBr, -1);
-      for (int q0 = 0; q0 < pmax; q0 += NBr) {
-        for (int j = 0; j < nm; ++j)
-          for (int jj = 0; jj < NBr; ++jj) csel[j * NBr + jj] = (q0 + jj < pcount[j]) ? q0 + jj : -1;
+      for (int r = 0; r < rounds; ++r) {
+        std::fill(csel.begin(), csel.end(), -1);
+        for (int p = 0; p < P; ++p) {
+          const int j = p / F, f = p % F;
+          for (int i = 0; i < gr; ++i) {
+            const int q = r * gr + i;
+            if (q < pcount[p]) csel[j * NBr + f * gr + i] = static_cast<int32_t>(xoff[f] + q);
+          }
+        }
         KES_CUDA(cudaMemcpyAsync(c->colsel, csel.data(), csel.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
         launch_pack_basis(s, c->Xd, np, c->colsel, c->slice_mesh, c->stage_in, NBr, np);
         KES_CHECK_LAUNCH();
-        run_filter(c, NBr, true);
+        run_filter(c, NBr, true, cpt);
         refine_steps += c->L;
         launch_unpack_block(s, c->stage_out, NBr, c->Wc, np);
         KES_CHECK_LAUNCH();
-        for (int jj = 0; jj < NBr && q0 + jj < pmax; ++jj) {
-          for (int j = 0; j < nm; ++j) want[j] = q0 + jj < pcount[j];
-          append_column(jj);
+        for (int jj = 0; jj < NBr; ++jj) {
+          bool any = false;
+          for (int j = 0; j < nm; ++j) {
+            const int p = owner(j, jj);
+            if (p < 0) continue;
+            want[p] = csel[j * NBr + jj] >= 0;
+            any |= want[p] != 0;
+          }
+          if (any) append_column(jj);
         }
       }
-      for (int j = 0; j < nm; ++j) {
-        if (pcount[j] > 0) project(j);
-        want[j] = 1;
+      for (int p = 0; p < P; ++p) {
+        if (pcount[p] > 0) project(p);
+        want[p] = 1;
       }
     }
 
-    // results
+    // results: the pairs of a mesh's processes merged in ascending theta
     bool any_breakdown = false;
     for (int j = 0; j < nm; ++j) {
-      MeshSolve& m = ms[j];
       const MeshInfo& mi = c->meshes[j];
-      any_breakdown |= m.breakdown;
       kes_result* r = res[j];
-      const int p = static_cast<int>(m.acc_theta.size());
+      struct Pair {
+        double theta;
+        int f, q;
+      };
+      std::vector<Pair> pairs;
+      std::vector<double> ritz_th, ritz_rel;
+      int k_used = 0;
+      bool brk = false;
+      for (int f = 0; f < F; ++f) {
+        const MeshSolve& m = ms[j * F + f];
+        for (size_t q = 0; q < m.acc_theta.size(); ++q) pairs.push_back({m.acc_theta[q], f, static_cast<int>(q)});
+        ritz_th.insert(ritz_th.end(), m.last_theta.begin(), m.last_theta.end());
+        ritz_rel.insert(ritz_rel.end(), m.last_rel.begin(), m.last_rel.end());
+        k_used += m.k;
+        brk |= m.breakdown;
+      }
+      std::stable_sort(pairs.begin(), pairs.end(), [](const Pair& x, const Pair& y) { return x.theta < y.theta; });
+      const int np_acc = static_cast<int>(pairs.size());
+      std::vector<double> th(np_acc), om(np_acc), rel(np_acc), ab(np_acc);
+      std::vector<int32_t> iv(np_acc);
+      for (int t = 0; t < np_acc; ++t) {
+        const MeshSolve& m = ms[j * F + pairs[t].f];
+        th[t] = pairs[t].theta;
+        om[t] = std::sqrt(th[t]);
+        rel[t] = m.acc_rel[pairs[t].q];
+        ab[t] = m.acc_abs[pairs[t].q];
+        iv[t] = pairs[t].f;
+      }
+      any_breakdown |= brk;
       r->n = mi.n;
-      r->n_pairs = p;
-      r->k_used = m.k;
-      r->breakdown = m.breakdown ? 1 : 0;
-      r->n_ritz = static_cast<int32_t>(m.last_theta.size());
+      r->n_pairs = np_acc;
+      r->k_used = k_used;
+      r->breakdown = brk ? 1 : 0;
+      r->n_ritz = static_cast<int32_t>(ritz_th.size());
       r->time_steps = steps;
       r->refine_steps = refine_steps;
-      r->omega2 = hdup(m.acc_theta);
-      std::vector<double> om(p);
-      for (int q = 0; q < p; ++q) om[q] = std::sqrt(m.acc_theta[q]);
+      r->omega2 = hdup(th);
       r->omega = hdup(om);
-      r->rel_res = hdup(m.acc_rel);
-      r->abs_res = hdup(m.acc_abs);
-      r->ritz_omega2 = hdup(m.last_theta);
-      r->ritz_rel_res = hdup(m.last_rel);
-      if (so.want_vectors && p > 0) {
-        const size_t need = static_cast<size_t>(p) * np;
+      r->rel_res = hdup(rel);
+      r->abs_res = hdup(ab);
+      r->interval = hdup(iv);
+      r->ritz_omega2 = hdup(ritz_th);
+      r->ritz_rel_res = hdup(ritz_rel);
+      if (so.want_vectors && np_acc > 0) {
+        const size_t need = static_cast<size_t>(np_acc) * np;
         if (need > c->Xd_cap) {
           c->dfree(c->Xd);
           c->Xd = c->dalloc_n<double>(need);
           c->Xd_cap = need;
         }
         KES_CUDA(cudaMemsetAsync(c->Xd, 0, need * sizeof(double), s));
-        KES_CUDA(cudaMemcpyAsync(c->Yd, m.acc_Y.data(), m.acc_Y.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-        launch_gemm_bx(s, B + mi.row_off, np, m.k, c->Yd, p, c->Xd + mi.row_off, np, mi.n_pad);
-        KES_CHECK_LAUNCH();
-        r->vectors = static_cast<double*>(std::malloc(static_cast<size_t>(p) * mi.n * sizeof(double)));
+        // interval f's accepted vectors go to columns xo[f] .. of Xd
+        std::vector<int> xo(F + 1, 0);
+        for (int f = 0; f < F; ++f) {
+          const MeshSolve& m = ms[j * F + f];
+          const int cnt = static_cast<int>(m.acc_theta.size());
+          xo[f + 1] = xo[f] + cnt;
+          if (cnt == 0) continue;
+          KES_CUDA(cudaMemcpyAsync(c->Yd, m.acc_Y.data(), m.acc_Y.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+          launch_gemm_bx(s, Bp(j * F + f), np, m.k, c->Yd, cnt, c->Xd + static_cast<int64_t>(xo[f]) * np + mi.row_off,
+                         np, mi.n_pad);
+          KES_CHECK_LAUNCH();
+          c->sync();  // Yd is reused by the next interval
+        }
+        r->vectors = static_cast<double*>(std::malloc(static_cast<size_t>(np_acc) * mi.n * sizeof(double)));
         if (!r->vectors) throw std::bad_alloc();
         // scatter each Ritz vector to the caller's order and keep this mesh's rows
-        for (int q = 0; q < p; ++q) {
-          launch_scatter_rows(s, c->Xd + static_cast<int64_t>(q) * np, 1, 1, c->row_src, c->n, c->tmp_user, c->n,
-                              np);
+        for (int t = 0; t < np_acc; ++t) {
+          const int64_t col = xo[pairs[t].f] + pairs[t].q;
+          launch_scatter_rows(s, c->Xd + col * np, 1, 1, c->row_src, c->n, c->tmp_user, c->n, np);
           KES_CHECK_LAUNCH();
-          KES_CUDA(cudaMemcpyAsync(r->vectors + static_cast<size_t>(q) * mi.n, c->tmp_user + mi.src_off,
+          KES_CUDA(cudaMemcpyAsync(r->vectors + static_cast<size_t>(t) * mi.n, c->tmp_user + mi.src_off,
                                    mi.n * sizeof(double), cudaMemcpyDeviceToHost, s));
         }
         c->sync();
@@ -1261,7 +1366,7 @@ kes_status kes_set_filters(kes_ctx* c, int32_t F, const double* wmin, const doub
       a[j * F + f] = wmin[f];
       b[j * F + f] = wmax[f];
     }
-  return set_filters_impl(c, F, a.data(), b.data(), t.data(), L);
+  return set_weights_impl(c, F, nullptr, a.data(), b.data(), t.data(), L);
 }
 
 kes_status kes_set_filter(kes_ctx* c, double wmin, double wmax, double tau, int32_t L) {
@@ -1271,7 +1376,20 @@ kes_status kes_set_filter(kes_ctx* c, double wmin, double wmax, double tau, int3
 kes_status kes_set_filters_batch(kes_ctx* c, int32_t F, const double* wmin, const double* wmax, const double* tau,
                                  int32_t L) {
   if (!c || F < 1 || !wmin || !wmax || !tau || L < 1) return KES_ERR_ARG;
-  return set_filters_impl(c, F, wmin, wmax, tau, L);
+  return set_weights_impl(c, F, nullptr, wmin, wmax, tau, L);
+}
+
+kes_status kes_set_weights(kes_ctx* c, int32_t F, const double* alpha, const double* wmin, const double* wmax,
+                           const double* tau, int32_t L) {
+  if (!c || F < 1 || !alpha || !wmin || !wmax || !tau || L < 1) return KES_ERR_ARG;
+  return set_weights_impl(c, F, alpha, wmin, wmax, tau, L);
+}
+
+kes_status kes_alpha_gaussian(double center, double sigma, double tau, int32_t L, double* alpha) {
+  if (!alpha || L < 1 || !(tau > 0.0) || !(sigma > 0.0) || !(center >= 0.0) || !std::isfinite(center))
+    return KES_ERR_ARG;
+  kes::alpha_gaussian(center, sigma, tau, L, alpha);
+  return KES_OK;
 }
 
 kes_status kes_alpha_table(double wmin, double wmax, double tau, int32_t L, double* alpha) {
@@ -1310,6 +1428,23 @@ kes_status kes_filter_apply(kes_ctx* c, const double* r_in, double* r_out, int32
   });
 }
 
+kes_status kes_filter_apply_columns(kes_ctx* c, const double* r_in, double* r_out, int32_t b, int32_t mem) {
+  if (!c || !r_in || !r_out || b < 2 || b > c->opts.block_b || (mem != KES_MEM_HOST && mem != KES_MEM_DEVICE))
+    return KES_ERR_ARG;
+  if (!c->filter_set) return KES_ERR_STATE;
+  if (b % c->F != 0) return KES_ERR_ARG;
+  LaunchCount lc(&c->stats);
+  return guarded([&]() -> kes_status {
+    const int NB = nb_for(b);
+    block_in(c, r_in, b, mem, NB, c->stage_in);
+    run_filter(c, NB, c->opts.precision == KES_PREC_FP64, b / c->F);
+    block_out(c, c->stage_out, NB, b, r_out, mem);
+    KES_CHECK_LAUNCH();
+    if (mem == KES_MEM_HOST) return check_flag(c);
+    return KES_OK;
+  });
+}
+
 void kes_result_free(kes_result* r) {
   if (!r) return;
   std::free(r->omega2);
@@ -1319,6 +1454,7 @@ void kes_result_free(kes_result* r) {
   std::free(r->vectors);
   std::free(r->ritz_omega2);
   std::free(r->ritz_rel_res);
+  std::free(r->interval);
   std::free(r);
 }
 
@@ -1341,11 +1477,11 @@ kes_status kes_block_krylov_solve(kes_ctx* c, const double* R0, int32_t b, int32
     return KES_ERR_ARG;
   for (int j = 0; j < c->n_mesh(); ++j) out[j] = nullptr;
   if (!c->filter_set) return KES_ERR_STATE;
-  if (c->F != 1) return KES_ERR_UNSUPPORTED;
+  if (b % c->F != 0) return KES_ERR_ARG;
   kes_solve_opts so;
   if (so_in) so = *so_in;
   else kes_solve_opts_default(&so);
-  if (so.kmax < b || so.check_every < 1 || !(so.tol > 0.0) || so.refine_sweeps < 0) return KES_ERR_ARG;
+  if (so.kmax < b / c->F || so.check_every < 1 || !(so.tol > 0.0) || so.refine_sweeps < 0) return KES_ERR_ARG;
   return block_solve_impl(c, R0, b, mem, so, out);
 }
 

@@ -17,6 +17,7 @@ constexpr int kSliceC = 32;  // SELL slice height = warp width
 void alpha_table(double wmin, double wmax, double tau, int L, double* alpha);
 void filter_response(double wmin, double wmax, double tau, int L, const double* omega, int64_t k,
                      double* beta);
+void alpha_gaussian(double center, double sigma, double tau, int L, double* alpha);
 // Symmetric eigensolver for the projected problem: Householder tridiagonalisation
 // followed by implicit QR steps with Wilkinson shifts. A is k x k col-major (lower
 // triangle read), w ascending, V (optional) orthonormal eigenvectors col-major.
@@ -83,20 +84,23 @@ void launch_step_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bo
                      float* acc_c, double* acc64, int64_t acc_stride, int F, const float* alpha_hi,
                      const float* alpha_lo, int L, int step, int* flag);
 // FP32 start over n_pad x nb row-major values: x32 = (float) r64; s_f = fl(alpha_f[0] r),
-// c_f = alpha_f[0] r - s_f (rounded), with the weight table of each row's mesh.
+// c_f = alpha_f[0] r - s_f (rounded), with the weight table of each row's mesh (cpt > 0:
+// column j has one accumulator, with table j / cpt).
 void launch_init_f32(cudaStream_t st, const SellDev& A, int nb, const double* r64, float* x32, float* acc_s,
-                     float* acc_c, int64_t acc_stride, int F, const double* alpha64, int L);
+                     float* acc_c, int64_t acc_stride, int F, const double* alpha64, int L, int cpt);
 
 // Block step (SpMM form) for NB in {2, 4, 8} columns, row-major n_pad x NB state
 // (row i's NB values contiguous). Same arithmetic per column as the single-vector
-// kernels; acc_stride = n_pad * NB elements per weight table.
+// kernels; acc_stride = n_pad * NB elements per accumulator set. cpt = 0: every column
+// accumulates with all F weight tables; cpt > 0: column j only with table j / cpt (the
+// columns of several intervals share the matrix stream).
 void launch_step_blk_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, int NB, bool first, bool last,
                          const double* x, const double* prev, double* out, double* acc, int64_t acc_stride, int F,
-                         const double* alpha, int L, int step, int* flag);
+                         const double* alpha, int L, int step, int cpt, int* flag);
 void launch_step_blk_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, int NB, bool first, bool last,
                          const float* x, const float* prev, float* out, float* acc_s, float* acc_c, double* acc64,
                          int64_t acc_stride, int F, const float* alpha_hi, const float* alpha_lo, int L, int step,
-                         int* flag);
+                         int cpt, int* flag);
 int blk_variant_count();
 int blk_blocks_per_sm(bool fp32, int NB, int variant, int block);
 

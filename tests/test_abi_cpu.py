@@ -97,3 +97,11 @@ def test_host_helpers_reject_bad_arguments():
         K.kes_alpha_table(2.0, 3.0, -0.1, 10)
     with pytest.raises(K.KesError):
         K.kes_filter_response(2.0, 3.0, 0.1, 0, [1.0])
+
+
+def test_gaussian_weights_match_oracle():
+    for c, sigma, tau, L in [(25.0, 3.0, 0.0099, 300), (42.5, 1.5, 0.004, 600), (0.0, 2.0, 0.01, 50)]:
+        np.testing.assert_allclose(K.kes_alpha_gaussian(c, sigma, tau, L), O.alpha_table_gaussian(c, sigma, tau, L),
+                                   rtol=1e-13, atol=1e-16)
+    with pytest.raises(K.KesError):
+        K.kes_alpha_gaussian(1.0, -1.0, 0.1, 10)

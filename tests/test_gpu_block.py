@@ -168,3 +168,144 @@ def test_fp32_solve_with_fp64_refinement_reaches_fp64_residuals(b):
         r = S @ x - th * p.m * x
         assert np.linalg.norm(r) <= 1.01e-8 * th * np.linalg.norm(p.m * x)
 
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_gaussian_weights_filter_and_solve(precision):
+    p = square_grid(32)
+    S = p.to_scipy()
+    tau = _tau(p)
+    L = 300
+    c, sigma = 25.0, 2.5
+    alpha = O.alpha_table_gaussian(c, sigma, tau, L)
+    r = start_vectors(p.n, 1, 9)
+    ref = O.filter_apply(S, p.m, r[0], tau, alpha)
+    tol = 1e-8 if precision == "fp64" else 1e-5
+    with K.Context(p, precision=precision) as ctx:
+        K.kes_set_weights(ctx.handle, alpha[None, None, :], [[20.0]], [[30.0]], [tau], L)
+        out = np.zeros((1, 1, p.n))
+        K.kes_filter_apply(ctx.handle, r, out, 1)
+        assert filter_error(out[0], ref, r, p.m, alpha) <= filter_tol(L, precision)
+        so = K.kes_solve_opts_default()
+        so.kmax, so.tol = 80, tol
+        res = K.kes_krylov_solve(ctx.handle, start_vectors(p.n, 1, 0)[0], so)
+    exact = spectra.eigenvalues_in(p.cells, p.h, 20.0, 30.0)
+    print(f"{precision} Gaussian band: accepted {res['n_pairs']}")
+    assert res["n_pairs"] >= 5
+    for th in res["omega2"]:
+        assert np.min(np.abs(exact - th)) <= EIG_REL[precision] * th
+
+
+# ---------------------------------------------------------------- several intervals
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("F,b", [(2, 2), (2, 4), (3, 6), (4, 8)])
+def test_filter_apply_columns_matches_oracle(meshes, precision, F, b):
+    # column j is filtered with table j // (b // F) only; it rounds exactly like that
+    # table's sum for that column in kes_filter_apply (b = 6 pads to 8 columns)
+    p = meshes[1]
+    tau = _tau(p)
+    L = 80
+    bands = [(4.0 + 3 * f, 6.5 + 3 * f) for f in range(F)]
+    alphas = np.stack([O.alpha_table(a, c, tau, L) for a, c in bands])
+    R = start_vectors(p.n, b, 40 + b)
+    g = b // F
+    with K.Context(p, precision=precision, block_b=b) as c:
+        K.kes_set_filters(c.handle, [a for a, _ in bands], [x for _, x in bands], tau, L)
+        cols = np.zeros((b, p.n))
+        K.kes_filter_apply_columns(c.handle, R, cols, b)
+        full = np.zeros((F, b, p.n))
+        K.kes_filter_apply(c.handle, R, full, b)
+    for j in range(b):
+        ref = O.filter_apply(p.to_scipy(), p.m, R[j], tau, alphas[j // g])
+        err = filter_error(cols[j:j + 1], ref[None, :], R[j:j + 1], p.m, alphas[j // g])
+        assert err <= filter_tol(L, precision), (j, err)
+        np.testing.assert_array_equal(cols[j], full[j // g, j])
+
+
+def test_filter_apply_columns_rejects_bad_widths(meshes):
+    p = meshes[0]
+    with K.Context(p, block_b=4) as c:
+        K.kes_set_filters(c.handle, [5.0, 9.0], [7.0, 11.0], _tau(p), 20)
+        out = np.zeros((3, p.n))
+        with pytest.raises(K.KesError):
+            K.kes_filter_apply_columns(c.handle, start_vectors(p.n, 3, 0), out, 3)
+
+
+# listed high band first, so that the merge into ascending order permutes the labels
+MULTI_BANDS = [(36.0, 39.0), (20.0, 25.0)]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_multi_interval_solve_matches_oracle(precision):
+    p = square_grid(32)
+    S = p.to_scipy()
+    tau = _tau(p)
+    R = start_vectors(p.n, 4, 3)
+    tol = 1e-8 if precision == "fp64" else 1e-5
+    so = K.kes_solve_opts_default()
+    so.kmax, so.tol, so.want_vectors = 120, tol, 1
+    with K.Context(p, precision=precision, block_b=4) as c:
+        K.kes_set_filters(c.handle, [a for a, _ in MULTI_BANDS], [x for _, x in MULTI_BANDS], tau, 300)
+        res = K.kes_block_krylov_solve(c.handle, R, 4, so)[0]
+    ores = O.multi_interval_krylov_solve(S, p.m, R, MULTI_BANDS, tau, 300, 120, tol)
+    counts = [int(np.sum(res["interval"] == f)) for f in range(2)]
+    print(f"{precision}: GPU accepted {counts} per interval, oracle "
+          f"{[int(np.sum(ores.interval == f)) for f in range(2)]}")
+    assert np.all(np.diff(res["omega2"]) >= 0)
+    for f, (lo, hi) in enumerate(MULTI_BANDS):
+        exact = spectra.eigenvalues_in(p.cells, p.h, lo, hi)
+        got = res["omega2"][res["interval"] == f]
+        assert np.all((np.sqrt(got) >= lo) & (np.sqrt(got) <= hi))
+        for th in got:
+            assert np.min(np.abs(exact - th)) <= EIG_REL[precision] * th
+        if precision == "fp64":
+            assert len(got) == len(exact) == int(np.sum(ores.interval == f))
+            np.testing.assert_allclose(got, ores.omega2[ores.interval == f], rtol=1e-10)
+        else:
+            assert len(got) >= len(exact) - 4
+    for th, x in zip(res["omega2"], res["vectors"]):
+        assert np.linalg.norm(S @ x - th * p.m * x) <= tol * 1.01 * th * np.linalg.norm(p.m * x)
+
+
+def test_multi_interval_solve_equals_separate_solves():
+    # the intervals share the trajectory but nothing they compute: each interval's pairs
+    # are bit for bit those of a separate block solve from its own start vectors
+    p = square_grid(28)
+    tau = _tau(p)
+    R = start_vectors(p.n, 4, 11)
+    so = K.kes_solve_opts_default()
+    so.kmax, so.tol = 60, 1e-8
+    with K.Context(p, block_b=4) as c:
+        K.kes_set_filters(c.handle, [a for a, _ in MULTI_BANDS], [x for _, x in MULTI_BANDS], tau, 250)
+        both = K.kes_block_krylov_solve(c.handle, R, 4, so)[0]
+    for f, (lo, hi) in enumerate(MULTI_BANDS):
+        with K.Context(p, block_b=2) as c:
+            K.kes_set_filter(c.handle, lo, hi, tau, 250)
+            one = K.kes_block_krylov_solve(c.handle, R[2 * f:2 * f + 2], 2, so)[0]
+        np.testing.assert_array_equal(both["omega2"][both["interval"] == f], one["omega2"])
+        np.testing.assert_array_equal(both["rel_res"][both["interval"] == f], one["rel_res"])
+
+
+def test_multi_interval_fp32_with_refinement():
+    p = square_grid(32)
+    S = p.to_scipy()
+    tau = _tau(p)
+    R = start_vectors(p.n, 4, 3)
+    so = K.kes_solve_opts_default()
+    so.kmax, so.tol, so.want_vectors, so.refine_sweeps = 100, 1e-8, 1, 2
+    with K.Context(p, precision="fp32", block_b=4) as c:
+        K.kes_set_filters(c.handle, [a for a, _ in MULTI_BANDS], [x for _, x in MULTI_BANDS], tau, 300)
+        res = K.kes_block_krylov_solve(c.handle, R, 4, so)[0]
+    assert res["refine_steps"] > 0
+    for f, (lo, hi) in enumerate(MULTI_BANDS):
+        exact = spectra.eigenvalues_in(p.cells, p.h, lo, hi)
+        got = res["omega2"][res["interval"] == f]
+        d_exact, _ = spectra.distinct(exact)
+        d_got, _ = spectra.distinct(got)
+        print(f"interval {f}: refined FP32 accepted {len(got)} ({len(d_got)} of {len(d_exact)} distinct)")
+        assert len(d_got) >= len(d_exact) - 1
+        for th in got:
+            assert np.min(np.abs(exact - th)) <= 1e-10 * th
+    for th, x in zip(res["omega2"], res["vectors"]):
+        assert np.linalg.norm(S @ x - th * p.m * x) <= 1.01e-8 * th * np.linalg.norm(p.m * x)

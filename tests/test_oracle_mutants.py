@@ -127,3 +127,37 @@ def test_residual_without_mass_is_caught(monkeypatch):
     _patch(monkeypatch, "ritz_residuals", res_bad)
     with pytest.raises(AssertionError):
         pins.test_krylov_finds_every_distinct_eigenvalue_in_interval()
+
+
+def test_gaussian_normalisation_mutant_is_caught(monkeypatch):
+    orig = K.gaussian_weight
+
+    def half(t, c, sigma):
+        return 0.5 * orig(t, c, sigma)
+    monkeypatch.setattr(K, "gaussian_weight", half)
+    monkeypatch.setattr(oracle, "gaussian_weight", half)
+    with pytest.raises(AssertionError):
+        pins.test_gaussian_weight_matches_numerical_inverse_transform()
+
+
+def test_every_interval_searching_the_first_is_caught(monkeypatch):
+    orig = K.block_krylov_solve
+    lo0, hi0 = pins.MULTI_BANDS[0]
+
+    def first_only(S, m, R0, omega_min, omega_max, *a, **kw):
+        return orig(S, m, R0, lo0, hi0, *a, **kw)
+    _patch(monkeypatch, "block_krylov_solve", first_only)
+    with pytest.raises(AssertionError):
+        pins.test_multi_interval_solver_finds_every_eigenvalue_of_each_interval()
+
+
+def test_labels_not_following_the_merge_order_are_caught(monkeypatch):
+    orig = K.multi_interval_krylov_solve
+
+    def stale_labels(*a, **kw):
+        r = orig(*a, **kw)
+        r.interval = np.sort(r.interval)        # labels in interval order, not the merged order
+        return r
+    _patch(monkeypatch, "multi_interval_krylov_solve", stale_labels)
+    with pytest.raises(AssertionError):
+        pins.test_multi_interval_solver_finds_every_eigenvalue_of_each_interval()

@@ -324,6 +324,41 @@ def test_block_solver_resolves_multiple_eigenvalues():
     np.testing.assert_allclose(G, np.eye(len(exact)), atol=1e-8)
 
 
+# ---------------------------------------------------------------- several intervals (Sec. 4)
+
+# listed high band first, so that the merge into ascending order permutes the labels
+MULTI_BANDS = [(36.0, 39.0), (20.0, 25.0)]
+
+
+def test_multi_interval_solver_finds_every_eigenvalue_of_each_interval():
+    # two intervals, two start vectors each (double eigenvalues of the square need a
+    # block of two): every eigenvalue of each interval, found by that interval
+    p = square_grid(32)
+    S = p.to_scipy()
+    tau = 0.9 * 2 / math.sqrt(spectra.box_spectrum(p.cells, p.h).max())
+    res = O.multi_interval_krylov_solve(S, p.m, start_vectors(p.n, 4, 3), MULTI_BANDS, tau, 300, 120, 1e-8)
+    for f, (lo, hi) in enumerate(MULTI_BANDS):
+        exact = spectra.eigenvalues_in(p.cells, p.h, lo, hi)
+        got = res.omega2[res.interval == f]
+        assert len(got) == len(exact)
+        np.testing.assert_allclose(got, exact, rtol=1e-10)
+        assert np.all((np.sqrt(got) >= lo) & (np.sqrt(got) <= hi))
+    assert np.all(np.diff(res.omega2) >= 0)
+    for th, x in zip(res.omega2, res.vectors):
+        assert np.linalg.norm(S @ x - th * p.m * x) <= 1e-8 * th * np.linalg.norm(p.m * x)
+
+
+def test_multi_interval_with_one_interval_is_the_block_solver():
+    p = square_grid(20)
+    S = p.to_scipy()
+    tau = 0.9 * 2 / math.sqrt(spectra.box_spectrum(p.cells, p.h).max())
+    R = start_vectors(p.n, 2, 1)
+    a = O.block_krylov_solve(S, p.m, R, 15.0, 25.0, tau, 150, 40, 1e-8)
+    b = O.multi_interval_krylov_solve(S, p.m, R, [(15.0, 25.0)], tau, 150, 40, 1e-8)
+    np.testing.assert_array_equal(a.omega2, b.omega2)
+    assert np.all(b.interval == 0) and b.k_used == a.k_used
+
+
 # ---------------------------------------------------------------- FP64 refinement
 
 def test_refinement_keeps_exact_eigenvectors():
@@ -355,3 +390,27 @@ def test_refinement_damps_noise_by_the_filter_contrast():
     # the largest |beta~| outside the interval is ~0.08 against ~0.95 inside
     assert len(thi) == 1 and thi[0] == pytest.approx(lam, rel=1e-12)
     assert reli[0] < 1e-3 * rel0
+
+
+# ---------------------------------------------------------------- other weights (Sec. 4)
+
+def test_gaussian_weight_gives_gaussian_band():
+    # the inverse cosine transform of a Gaussian band, sampled by the rectangle rule,
+    # reproduces the band (Lemma 2.2 with a Gaussian peak instead of the indicator)
+    c, sigma = 3.0, 0.5
+    tau, L = 0.001, 20000                      # sigma * T = 10: truncation negligible
+    a = O.alpha_table_gaussian(c, sigma, tau, L)
+    w = np.array([1.0, 2.0, 2.5, 3.0, 3.4, 4.0, 5.0])
+    ref = np.exp(-(w - c) ** 2 / (2 * sigma ** 2)) + np.exp(-(w + c) ** 2 / (2 * sigma ** 2))
+    # the rectangle rule (full weight at t = 0) and the leapfrog phase error are O(tau):
+    # about 1e-3 at this tau, halving with tau
+    np.testing.assert_allclose(O.beta_tilde(w, a, tau), ref, atol=1.5e-3)
+
+
+def test_gaussian_weight_matches_numerical_inverse_transform():
+    c, sigma = 2.0, 0.7
+    s = np.linspace(0, 12, 120001)
+    band = np.exp(-(s - c) ** 2 / (2 * sigma ** 2)) + np.exp(-(s + c) ** 2 / (2 * sigma ** 2))
+    for t in [0.0, 0.3, 1.1, 2.5]:
+        num = 2 / math.pi * np.trapezoid(band * np.cos(t * s), s)
+        assert O.gaussian_weight(np.array([t]), c, sigma)[0] == pytest.approx(num, abs=1e-8)

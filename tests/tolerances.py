@@ -33,8 +33,8 @@ FILTER_TOL_C = 32 = 2 * c_loc * (safety factor 4). The FP32 form has
 eps = 2^-24 for values and state; its accumulator is compensated (two-sum and
 two-product), so the sum adds no error of its own.
 
-Eigenvalues: BASELINE targets are a relative 1e-10 (FP64 form) and 1e-6 (FP32
-form) against the exact (closed-form) spectrum.
+Eigenvalues: the targets are a relative 1e-10 (FP64 form) and 1e-6 (FP32 form)
+against the exact (closed-form) spectrum.
 """
 import numpy as np
 
