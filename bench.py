@@ -40,6 +40,7 @@ if ROOT not in sys.path:
 METRIC = "GDOF*steps/s"
 FALLBACK_HBM_GBS = 6800.0
 STEP_KERNEL_SRC = os.path.join(ROOT, "paper_2402_08515_gb300", "csrc", "kernels_step.cu")
+BLOCK_KERNEL_SRC = os.path.join(ROOT, "paper_2402_08515_gb300", "csrc", "kernels_block.cu")
 
 
 def parse_args(argv=None):
@@ -52,11 +53,12 @@ def parse_args(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="solve", choices=["solve", "filter", "tts"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "filter", "tts", "weights"],
                     help="filter: one filter application only (small profiling runs); tts: time to "
                          "converged eigenpairs at residual 1e-8, FP64 form against the FP32 forms with FP64 "
                          "refinement")
-    ap.add_argument("--kmax", type=int, default=200, help="Krylov dimension of --mode tts")
+    ap.add_argument("--tts-forms", default="", help="comma-separated subset of the --mode tts forms")
+    ap.add_argument("--tts-workloads", default="cube128_fp64,box2m_fp64", help="workloads of --mode tts")
     ap.add_argument("--L", type=int, default=0, help="override the workload's time steps (--mode filter)")
     ap.add_argument("--variant", type=int, default=None,
                     help="fixed step-kernel launch shape instead of the autotuner's choice")
@@ -171,20 +173,20 @@ def load_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash() -> str:
-    return hashlib.sha256(open(STEP_KERNEL_SRC, "rb").read()).hexdigest()[:16]
+def kernel_source_hash(src: str = STEP_KERNEL_SRC) -> str:
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
 
 
-def profiled_traffic(workload: str):
+def profiled_traffic(workload: str, src: str = STEP_KERNEL_SRC):
     """DRAM bytes per step-kernel launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
+    on the current source of that kernel, the file src (else None)."""
     path = os.path.join(ROOT, "profiles", f"step_kernel_{workload}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
     t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not h or not t or h.group(1) != kernel_source_hash():
+    if not h or not t or h.group(1) != kernel_source_hash(src):
         return None
     return float(t.group(1))
 
@@ -239,7 +241,7 @@ def run_kes(args):
 
     import paper_2402_08515_gb300 as K
     from fe_inputs import WORKLOADS
-    from oracle import spectra
+    from fe_inputs import spectra
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -259,8 +261,12 @@ def run_kes(args):
     taus = wl.cfl * 2.0 / omega_pow
     ivs = [wl.mesh_intervals(p) for p in problems]
     F = len(ivs[0])
-    wmin1 = np.array([[iv[0][0]] for iv in ivs])
-    wmax1 = np.array([[iv[0][1]] for iv in ivs])
+    wmin_all = np.array([[a for a, _ in iv] for iv in ivs])
+    wmax_all = np.array([[c for _, c in iv] for iv in ivs])
+    # the solve searches every interval of a mesh at once when the block splits evenly
+    # over them (interval f owns b / F columns); otherwise the first interval only
+    F_solve = F if F > 1 and b % F == 0 else 1
+    wmin1, wmax1 = wmin_all[:, :F_solve], wmax_all[:, :F_solve]
     K.kes_set_filters_batch(h, wmin1, wmax1, taus, wl.L)
     so = K.kes_solve_opts_default()
     so.kmax, so.tol, so.check_every = wl.kmax, wl.acceptance(), wl.check_every
@@ -269,7 +275,7 @@ def run_kes(args):
     torch.cuda.synchronize()
     if args.mode == "filter":
         L = args.L or wl.L
-        K.kes_set_filters_batch(h, wmin1, wmax1, taus, L)
+        K.kes_set_filters_batch(h, wmin1[:, :1], wmax1[:, :1], taus, L)
         out = torch.zeros((1, b, n), dtype=torch.float64, device=dev)
         K.kes_filter_apply(h, R0_dev, out, b)
         K.kes_sync(h)
@@ -313,13 +319,12 @@ def run_kes(args):
     bytes_step = K.kes_step_bytes(h, b, 1)
     achieved = bytes_step / (step_ms / 1e3) / 1e9
     peak, peak_src = load_peak()
-    traffic = profiled_traffic(args.workload) if b == 1 and not batch else None
+    traffic = profiled_traffic(args.workload, STEP_KERNEL_SRC if b == 1 else BLOCK_KERNEL_SRC)
 
     # several intervals from one trajectory: the same block filtered with F weight tables
     multi = None
     if F > 1:
-        K.kes_set_filters_batch(h, np.array([[a for a, _ in iv] for iv in ivs]),
-                                np.array([[c for _, c in iv] for iv in ivs]), taus, wl.L)
+        K.kes_set_filters_batch(h, wmin_all, wmax_all, taus, wl.L)
         out = torch.zeros((F, b, n), dtype=torch.float64, device=dev)
         K.kes_filter_apply(h, R0_dev, out, b)
         K.kes_sync(h)
@@ -364,9 +369,10 @@ def run_kes(args):
     eig_err = None
     for p, rr, iv in zip(problems, res, ivs):
         if p.cells and not p.meta.get("length") and rr["n_pairs"]:
-            exact = spectra.eigenvalues_in(p.cells, p.h, iv[0][0], iv[0][1])
-            e = float(max(np.min(np.abs(exact - t)) / t for t in rr["omega2"]))
-            eig_err = e if eig_err is None else max(eig_err, e)
+            for t, f in zip(rr["omega2"], rr["interval"]):
+                exact = spectra.omega2_in(p.cells, p.h, iv[f][0], iv[f][1])
+                e = float(np.min(np.abs(exact - t)) / t)
+                eig_err = e if eig_err is None else max(eig_err, e)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -382,7 +388,8 @@ def run_kes(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wl.precision == "fp64" else "f32",
         "data": "synthetic",
         "config": {"workload": args.workload, "meshes": len(problems), "dofs": n, "nnz": nnz, "b": b,
-                   "interval": [float(wmin1[0, 0]), float(wmax1[0, 0])] if not batch else "per mesh",
+                   "interval": ([float(wmin1[0, 0]), float(wmax1[0, 0])] if not batch
+                                else f"per mesh, {F_solve} interval(s) with {b // F_solve} column(s) each"),
                    "L": wl.L, "kmax": wl.kmax, "tau": float(taus[0]) if not batch else "per mesh",
                    "omega_max_power": float(omega_pow[0]) if not batch else "per mesh",
                    "format": "SELL-32 (sigma=1)", "parallelism": f"replicas x{world}",
@@ -391,7 +398,8 @@ def run_kes(args):
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
                      "kernel": ("k_step_f64" if wl.precision == "fp64" else "k_step_f32") if b == 1
                      else ("k_step_blk<double>" if wl.precision == "fp64" else "k_step_blk<float>"),
-                     "step_variant": stats["step_variant"], "step_grid": stats["step_grid"],
+                     "step_variant": stats["step_variant"] if b == 1 else stats["blk_variant"],
+                     "step_grid": stats["step_grid"] if b == 1 else stats["blk_grid"],
                      "step_us": step_ms * 1e3, "algorithmic_bytes_per_step": bytes_step},
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -450,56 +458,130 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+TTS_FORMS = (
+    # name, precision, block width, FP64 refinement sweeps
+    ("fp64", "fp64", 1, 0),
+    ("fp32+refine1", "fp32", 1, 1),
+    ("fp32+refine2", "fp32", 1, 2),
+)
+TTS_KMAX = (160, 200, 240, 280, 320, 360, 400)
+
+
 def run_tts(args):
-    """Time to converged eigenpairs on the cube: the plain FP64 form at rel_res <= 1e-8,
-    the FP32 form with an FP64 refinement sweep at 1e-8, and the FP32 forms (single
-    vector, blocks of 8) at the tolerances their rounding floor allows."""
+    """Time to all eigenpairs in the interval at rel_res <= 1e-8, on the 128^3 cube
+    (eigenvalues of multiplicity up to 6) and on a box of the same size with simple
+    eigenvalues: for each form a sweep over the Krylov dimension kmax (one projection at
+    the end, so that every run costs what a solve of that size costs), reporting each
+    run's time and the distinct eigenvalues it accepted; a form's time to solution is
+    that of the smallest kmax that accepts every distinct eigenvalue of the interval.
+    The FP32 forms reach 1e-8 through FP64 refinement sweeps on their in-interval Ritz
+    vectors, filtered 8 at a time."""
     import numpy as np
     import torch
 
     import paper_2402_08515_gb300 as K
     from fe_inputs import WORKLOADS, start_vectors
-    from oracle import spectra
+    from fe_inputs import spectra
 
-    wl = WORKLOADS["cube128_fp64"]
+    tol = 1e-8
+    forms = [f for f in TTS_FORMS if not args.tts_forms or f[0] in args.tts_forms.split(",")]
+    out = []
+    for wname in args.tts_workloads.split(","):
+        wl = WORKLOADS[wname]
+        p = wl.build()
+        exact = spectra.omega2_in(p.cells, p.h, wl.omega_min, wl.omega_max)
+        distinct, _ = spectra.cluster(exact)
+        v0 = start_vectors(p.n, 1, wl.seed)[0]
+        runs, summary = [], {}
+        for name, prec, b, refine in forms:
+            summary[name] = None
+            with K.Context(p, precision=prec, block_b=8) as c:
+                w, _ = K.kes_estimate_omega_max(c.handle, wl.power_iters, v0)
+                K.kes_set_filter(c.handle, wl.omega_min, wl.omega_max, wl.cfl * 2 / w, wl.L)
+                R = start_vectors(p.n, b, wl.seed + 1)
+                for kmax in TTS_KMAX:
+                    so = K.kes_solve_opts_default()
+                    so.kmax, so.tol, so.check_every, so.refine_sweeps = kmax, tol, kmax, refine
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    res = K.kes_block_krylov_solve(c.handle, R, b, so)[0]
+                    dt = time.perf_counter() - t0
+                    found, _ = spectra.cluster(res["omega2"])
+                    err = max((float(np.min(np.abs(exact - t)) / t) for t in res["omega2"]), default=None)
+                    runs.append({"form": name, "b": b, "kmax": kmax, "refine_sweeps": refine, "seconds": dt,
+                                 "accepted_pairs": res["n_pairs"], "accepted_distinct": len(found),
+                                 "max_rel_res": float(res["rel_res"].max()) if res["n_pairs"] else None,
+                                 "max_eig_rel_err_vs_exact": err, "leapfrog_steps": res["time_steps"],
+                                 "fp64_refine_steps": res["refine_steps"]})
+                    print(json.dumps({"workload": wname, **runs[-1]}), file=sys.stderr, flush=True)
+                    if len(found) >= len(distinct):
+                        summary[name] = {"seconds": dt, "kmax": kmax, "accepted_pairs": res["n_pairs"]}
+                        break
+        out.append({"workload": wname, "dofs": p.n, "interval": [wl.omega_min, wl.omega_max], "L": wl.L,
+                    "distinct_in_interval": len(distinct), "eigenvalues_in_interval": len(exact),
+                    "time_to_all_distinct": summary, "runs": runs})
+    print(json.dumps({"mode": "tts", "tol": tol, "workloads": out}), flush=True)
+
+
+def run_weights(args):
+    """Weight functions compared on the 64^2 square (Sec. 4, "Weight function"): the
+    indicator of [20, 30] against a Gaussian and a triangular band centred at 25 with
+    half of their peak at the interval's ends. For each: the filter factor beta~ over
+    the exact spectrum (smallest inside the interval, largest outside) and the FP64
+    Krylov solve until every distinct eigenvalue of [20, 30] is accepted at 1e-8."""
+    import math
+
+    import numpy as np
+    import torch
+
+    import paper_2402_08515_gb300 as K
+    from fe_inputs import WORKLOADS, start_vectors
+    from fe_inputs import spectra
+
+    wl = WORKLOADS["square64_fp64"]
     p = wl.build()
-    exact = spectra.eigenvalues_in(p.cells, p.h, wl.omega_min, wl.omega_max)
-    distinct, _ = spectra.distinct(exact)
+    lo, hi = wl.omega_min, wl.omega_max
+    c0, half = 0.5 * (lo + hi), 0.5 * (hi - lo)
+    w_all = np.sqrt(spectra.grid_omega2(p.cells, p.h))
+    inside = (w_all >= lo) & (w_all <= hi)
+    distinct, _ = spectra.cluster(spectra.omega2_in(p.cells, p.h, lo, hi))
     v0 = start_vectors(p.n, 1, wl.seed)[0]
-    runs = []
-    # the FP64 form at 1e-8; the FP32 forms at 1e-8 after FP64 refinement and at the
-    # tolerances their rounding floor allows
-    forms = (("fp64", "fp64", 1, 0, 1e-8), ("fp32+refine", "fp32", 1, 1, 1e-8),
-             ("fp32", "fp32", 1, 0, 1e-6), ("fp32_block8", "fp32", 8, 0, 1e-6),
-             ("fp32_block8", "fp32", 8, 0, 1e-5))
-    for name, prec, b, refine, tol in forms:
-        with K.Context(p, precision=prec, block_b=b) as c:
-            w, _ = K.kes_estimate_omega_max(c.handle, wl.power_iters, v0)
-            K.kes_set_filter(c.handle, wl.omega_min, wl.omega_max, wl.cfl * 2 / w, wl.L)
+    rows = []
+    with K.Context(p, precision="fp64") as c:
+        w, _ = K.kes_estimate_omega_max(c.handle, wl.power_iters, v0)
+        tau = wl.cfl * 2 / w
+        L = wl.L
+        tables = {
+            "indicator": K.kes_alpha_table(lo, hi, tau, L),
+            "gaussian": K.kes_alpha_gaussian(c0, half / math.sqrt(2 * math.log(2)), tau, L),
+            "triangle": K.kes_alpha_triangle(c0, 2 * half, tau, L),
+        }
+        for name, alpha in tables.items():
+            beta = K.kes_weights_response(alpha, tau, w_all)
+            K.kes_set_weights(c.handle, alpha[None, None, :], [[lo]], [[hi]], [tau], L)
             so = K.kes_solve_opts_default()
-            so.kmax, so.tol, so.check_every, so.refine_sweeps, so.want_vectors = args.kmax, tol, 20, refine, 0
-            R = start_vectors(p.n, b, wl.seed + 1)
+            so.kmax, so.tol, so.check_every, so.n_wanted = 300, 1e-8, 5, len(distinct)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            res = K.kes_block_krylov_solve(c.handle, R, b, so)[0]
+            res = K.kes_krylov_solve(c.handle, start_vectors(p.n, 1, wl.seed + 1)[0], so)
             dt = time.perf_counter() - t0
-            found, _ = spectra.distinct(res["omega2"])
-            err = max((float(np.min(np.abs(exact - t)) / t) for t in res["omega2"]), default=None)
-            runs.append({"form": name, "b": b, "kmax": args.kmax, "tol": tol, "refine_sweeps": refine,
-                         "seconds": dt, "accepted_pairs": res["n_pairs"],
+            found, _ = spectra.cluster(res["omega2"])
+            rows.append({"weight": name, "beta_min_inside": float(np.abs(beta[inside]).min()),
+                         "beta_max_outside": float(np.abs(beta[~inside]).max()),
                          "accepted_distinct": len(found), "distinct_in_interval": len(distinct),
-                         "max_rel_res": float(res["rel_res"].max()) if res["n_pairs"] else None,
-                         "max_eig_rel_err_vs_exact": err, "leapfrog_steps": res["time_steps"],
-                         "fp64_refine_steps": res["refine_steps"]})
-            print(json.dumps(runs[-1]), file=sys.stderr, flush=True)
-    print(json.dumps({"mode": "tts", "workload": "cube128", "interval": [wl.omega_min, wl.omega_max], "L": wl.L,
-                      "runs": runs}), flush=True)
+                         "krylov_vectors": res["k_used"], "leapfrog_steps": res["time_steps"], "seconds": dt})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    print(json.dumps({"mode": "weights", "workload": "square64", "interval": [lo, hi], "L": L, "tau": tau,
+                      "tol": 1e-8, "runs": rows}), flush=True)
 
 
 def main(argv=None):
     args = parse_args(argv)
     if args.mode == "tts":
         run_tts(args)
+        return
+    if args.mode == "weights":
+        run_weights(args)
         return
     if args.impl == "reference":
         run_reference(args)

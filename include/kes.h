@@ -40,13 +40,24 @@ typedef enum kes_status {
   KES_INFO_INVARIANT_SUBSPACE = 1, /* Krylov breakdown: an invariant subspace was found (Algorithm 2.5, "exact eigenspace found") */
   KES_ERR_ARG = -1,                /* invalid argument (null pointer, size, range, ordering) */
   KES_ERR_MASS = -2,               /* a lumped mass entry is <= 0 or not finite */
-  KES_ERR_UNSTABLE = -3,           /* CFL violated (tau * omega_max >= 2) or the time stepping produced Inf/NaN */
+  KES_ERR_UNSTABLE = -3,           /* CFL violated (tau * omega_max >= 2, or 2 sqrt(3) for the fourth-order
+                                      stepper) or the time stepping produced Inf/NaN */
   KES_ERR_CUDA = -4,               /* a CUDA runtime call failed */
   KES_ERR_OOM = -5,                /* device or host allocation failed */
   KES_ERR_TIMEOUT = -6,            /* a bounded device-side wait gave up */
   KES_ERR_STATE = -7,              /* call out of order (e.g. filter not set) */
   KES_ERR_UNSUPPORTED = -8         /* option combination not implemented */
 } kes_status;
+
+/* Time stepper of the filter (Remark 2.4: any explicit scheme diagonalised by the
+   eigenvectors keeps Lemma 2.3, with its own scalar recurrence q_l). */
+enum kes_stepper {
+  KES_STEPPER_LEAPFROG = 0,  /* eq. (2stepmethod): y_{l+1} = 2 y_l - y_{l-1} - tau^2 K y_l, K = M^{-1} S;
+                                q_{l+1} = (2 - x) q_l - q_{l-1}, x = tau^2 omega^2; stable for tau omega < 2 */
+  KES_STEPPER_LEAPFROG4 = 1  /* fourth-order modified equation: ... + (tau^4 / 12) K^2 y_l (two sparse products
+                                per step); q_{l+1} = (2 - x + x^2 / 12) q_l - q_{l-1}; stable for
+                                tau omega <= 2 sqrt(3), phase error O((omega tau)^5) */
+};
 
 enum kes_precision {
   KES_PREC_FP64 = 0, /* FP64 matrix values, state and accumulation */
@@ -72,6 +83,7 @@ typedef struct kes_opts {
   void* (*dev_alloc)(size_t bytes, void* user);
   void (*dev_free)(void* ptr, size_t bytes, void* user);
   void* alloc_user;
+  int32_t stepper;     /* enum kes_stepper (default KES_STEPPER_LEAPFROG) */
 } kes_opts;
 
 /* Options of kes_krylov_solve. Initialise with kes_solve_opts_default(). */
@@ -118,6 +130,8 @@ typedef struct kes_stats {
   int64_t bytes_per_step;   /* algorithmic HBM bytes of one fused step (see kes_step_bytes) */
   int32_t step_variant;     /* launch shape of the step kernel in use */
   int32_t step_grid;        /* its grid size (blocks of 256 threads) */
+  int32_t blk_variant;      /* launch shape of the block (SpMM) step kernel, -1 for single-vector contexts */
+  int32_t blk_grid;         /* its grid size */
 } kes_stats;
 
 void kes_opts_default(kes_opts* opts);
@@ -179,8 +193,11 @@ kes_status kes_estimate_omega_max_batch(kes_ctx* ctx, int32_t iters, const doubl
  * eq. (weightf) sampled by the rectangle rule of eq. (disc_filtercoeff),
  * with T = L tau. L is the number of leapfrog steps (L+1 weighted samples,
  * the last at t = T). Requires 0 <= omega_min < omega_max, tau > 0, L >= 1.
- * Returns KES_ERR_UNSTABLE if tau * gershgorin >= 2 (the CFL bound is then
- * violated for certain).
+ * Returns KES_ERR_UNSTABLE if tau times the last power-iteration estimate of
+ * omega_max (a lower bound of it) reaches the stepper's bound, 2 (leapfrog) or
+ * 2 sqrt(3) (fourth order): the CFL condition is then violated for certain.
+ * With the fourth-order stepper the filter factor is sum_n alpha_n q_n(omega) with
+ * that stepper's q_n (see kes_weights_response for the leapfrog's).
  * kes_set_filters sets F weight tables (intervals) that share tau and L;
  * kes_filter_apply then returns F filtered blocks from one trajectory.
  */
@@ -208,17 +225,26 @@ kes_status kes_alpha_table(double omega_min, double omega_max, double tau, int32
    the filter applies to an eigenvector of frequency omega (Lemma 2.3). */
 kes_status kes_filter_response(double omega_min, double omega_max, double tau, int32_t L,
                                const double* omega, int64_t k, double* beta);
+/* kes_weights_response: the same factor for any weight table alpha[0..L] (e.g. from
+   kes_alpha_gaussian): beta~(omega_i) = sum_n alpha_n q_n(omega_i), eq. (fullydiscfilter). */
+kes_status kes_weights_response(const double* alpha, double tau, int32_t L, const double* omega, int64_t k,
+                                double* beta);
 /* kes_alpha_gaussian: alpha[0..L] = tau * alpha(n tau) for the Gaussian pass band
    beta(omega) ~ exp(-(omega - center)^2 / (2 sigma^2)): by the inverse cosine transform
    behind eq. (filterf), alpha(t) = 2 sigma sqrt(2/pi) exp(-sigma^2 t^2 / 2) cos(center t)
    (Sec. 4, "Weight function"). Requires center >= 0, sigma > 0, tau > 0, L >= 1. */
 kes_status kes_alpha_gaussian(double center, double sigma, double tau, int32_t L, double* alpha);
+/* kes_alpha_triangle: the same for the triangular band beta(omega) = max(0, 1 - |omega - center| / half_width):
+   alpha(t) = (2 half_width / pi) cos(center t) (sin(t half_width / 2) / (t half_width / 2))^2.
+   Requires center >= 0, half_width > 0, tau > 0, L >= 1. */
+kes_status kes_alpha_triangle(double center, double half_width, double tau, int32_t L, double* alpha);
 /* kes_sym_eig: eigenvalues (ascending, w[k]) and orthonormal eigenvectors (V, k x k col-major,
    may be NULL) of the symmetric k x k col-major matrix A (only its lower triangle is read).
    This is the small projected problem of eq. (projevp) with B^T M B = I. */
 kes_status kes_sym_eig(int32_t k, const double* A, double* w, double* V);
 /* kes_step_bytes: algorithmic HBM bytes of one fused leapfrog step of this context for b vectors
-   and F intervals (every matrix entry, row pointer and per-row vector read or written once). */
+   and F intervals (every matrix entry, row pointer and per-row vector read or written once; the
+   fourth-order stepper adds its stage pass and the read of the stage). */
 int64_t kes_step_bytes(const kes_ctx* ctx, int32_t b, int32_t F);
 
 /*

@@ -40,7 +40,9 @@ __all__ = [
     "filter_apply_multi", "power_iteration", "m_inner", "m_norm",
     "orthonormalize_cgs2", "rayleigh_ritz", "ritz_residuals", "krylov_solve",
     "block_krylov_solve", "multi_interval_krylov_solve",
-    "refine_subspace", "gaussian_weight", "alpha_table_gaussian",
+    "refine_subspace", "gaussian_weight", "alpha_table_gaussian", "triangle_weight",
+    "alpha_table_triangle", "q_values_leapfrog4", "beta_tilde_leapfrog4",
+    "filter_apply_leapfrog4",
     "KrylovResult", "BREAKDOWN_RATIO",
 ]
 
@@ -93,6 +95,23 @@ def alpha_table_gaussian(center: float, sigma: float, tau: float, L: int) -> np.
     return tau * gaussian_weight(np.arange(L + 1, dtype=np.float64) * tau, center, sigma)
 
 
+def triangle_weight(t, center: float, half_width: float):
+    """Weight of a triangular (hat) pass band (Sec. 4, "Weight function"). For the even
+    band beta(s) = hat(s - c) + hat(s + c), hat(u) = max(0, 1 - |u| / h), the inverse
+    transform alpha(t) = (2/pi) int_0^inf beta(s) cos(ts) ds is (1/pi) times the integral
+    over the whole line, i.e. (2/pi) cos(c t) int hat(u) cos(t u) du, and the integral of
+    the hat against cos(t u) is h (sin(t h / 2) / (t h / 2))^2."""
+    t = np.asarray(t, dtype=np.float64)
+    x = 0.5 * t * half_width
+    sinc = np.where(x == 0, 1.0, np.sin(x) / np.where(x == 0, 1.0, x))
+    return 2.0 * half_width / math.pi * np.cos(center * t) * sinc * sinc
+
+
+def alpha_table_triangle(center: float, half_width: float, tau: float, L: int) -> np.ndarray:
+    """Rectangle-rule weights tau * alpha(n tau), n = 0..L, of the triangular band."""
+    return tau * triangle_weight(np.arange(L + 1, dtype=np.float64) * tau, center, half_width)
+
+
 # --------------------------------------------------------------------------
 # discrete filter: eq. (scalartimestep), eq. (fullydiscfilter)
 # --------------------------------------------------------------------------
@@ -136,6 +155,55 @@ def filter_apply(S, m: np.ndarray, r: np.ndarray, tau: float,
     acc = alpha[0] * y
     for l in range(L):
         y_next = -tau * tau * (S @ y) / m + 2.0 * y - y_prev
+        acc = acc + alpha[l + 1] * y_next
+        y_prev, y = y, y_next
+    return acc
+
+
+# --------------------------------------------------------------------------
+# another time stepper (Remark 2.4, Sec. 4 "Time-stepping"): the fourth-order
+# modified-equation leapfrog. Like eq. (2stepmethod) it is diagonalised by the
+# eigenvectors, so Lemma 2.3 holds with its own scalar recurrence.
+# --------------------------------------------------------------------------
+
+def q_values_leapfrog4(omega, tau: float, L: int) -> np.ndarray:
+    """q_l(omega), l = 0..L, of the fourth-order scheme on one eigenvector:
+    q_{-1} = q_0 = 1, q_{l+1} = (2 - x + x^2 / 12) q_l - q_{l-1}, x = tau^2 omega^2.
+    Returns shape (L+1, len(omega))."""
+    omega = np.atleast_1d(np.asarray(omega, dtype=np.float64))
+    x = tau * tau * omega * omega
+    a = 2.0 - x + x * x / 12.0
+    q = np.empty((L + 1, omega.size))
+    q_prev = np.ones_like(omega)
+    q_cur = np.ones_like(omega)
+    q[0] = q_cur
+    for l in range(L):
+        q_next = a * q_cur - q_prev
+        q[l + 1] = q_next
+        q_prev, q_cur = q_cur, q_next
+    return q
+
+
+def beta_tilde_leapfrog4(omega, alpha: np.ndarray, tau: float) -> np.ndarray:
+    """The factor the fourth-order filter applies to an eigenvector of frequency
+    omega: sum_{n=0..L} alpha_n q_n(omega) with q_values_leapfrog4."""
+    L = len(alpha) - 1
+    return alpha @ q_values_leapfrog4(omega, tau, L)
+
+
+def filter_apply_leapfrog4(S, m: np.ndarray, r: np.ndarray, tau: float,
+                           alpha: np.ndarray) -> np.ndarray:
+    """sum_{n=0..L} alpha_n y_n(r) for the fourth-order modified-equation leapfrog
+    y_{l+1} = 2 y_l - y_{l-1} - tau^2 K y_l + (tau^4 / 12) K^2 y_l, K = M^{-1} S,
+    from y_{-1} = y_0 = r (the start of eq. 12). Stable for tau omega_max <= 2 sqrt(3)."""
+    L = len(alpha) - 1
+    y_prev = np.array(r, dtype=np.float64)
+    y = np.array(r, dtype=np.float64)
+    acc = alpha[0] * y
+    for l in range(L):
+        Ky = (S @ y) / m
+        KKy = (S @ Ky) / m
+        y_next = 2.0 * y - y_prev - tau * tau * Ky + tau ** 4 / 12.0 * KKy
         acc = acc + alpha[l + 1] * y_next
         y_prev, y = y, y_next
     return acc

@@ -18,7 +18,8 @@ import numpy as np
 
 __all__ = [
     "KesError", "KesOpts", "KesSolveOpts", "KesResult", "KesStats", "lib", "LIB_PATH",
-    "KES_PREC_FP64", "KES_PREC_FP32", "KES_MEM_DEVICE", "KES_MEM_HOST",
+    "KES_PREC_FP64", "KES_PREC_FP32", "KES_MEM_DEVICE", "KES_MEM_HOST", "KES_STEPPER_LEAPFROG",
+    "KES_STEPPER_LEAPFROG4",
     "kes_opts_default", "kes_solve_opts_default", "kes_strerror", "kes_create", "kes_destroy",
     "kes_size", "kes_sync", "kes_estimate_omega_max", "kes_set_filter", "kes_set_filters",
     "kes_alpha_table", "kes_filter_response", "kes_sym_eig", "kes_step_bytes",
@@ -26,6 +27,7 @@ __all__ = [
     "Context", "header_functions", "kes_filter_apply_noalloc", "KES_NOALLOC_MAX_N",
     "kes_create_batch", "kes_mesh_count", "kes_estimate_omega_max_batch", "kes_set_filters_batch",
     "kes_block_krylov_solve", "kes_set_weights", "kes_alpha_gaussian", "kes_filter_apply_columns",
+    "kes_alpha_triangle", "kes_weights_response",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -40,6 +42,7 @@ lib = C.CDLL(LIB_PATH)
 KES_OK, KES_INFO_INVARIANT_SUBSPACE = 0, 1
 KES_PREC_FP64, KES_PREC_FP32 = 0, 1
 KES_MEM_DEVICE, KES_MEM_HOST = 0, 1
+KES_STEPPER_LEAPFROG, KES_STEPPER_LEAPFROG4 = 0, 1
 
 
 class KesError(RuntimeError):
@@ -54,8 +57,9 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
 
 class KesOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("sell_sigma", C.c_int32), ("use_graph", C.c_int32),
-                ("block_b", C.c_int32), ("autotune", C.c_int32), ("step_variant", C.c_int32), ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN),
-                ("dev_free", FREE_FN), ("alloc_user", C.c_void_p)]
+                ("block_b", C.c_int32), ("autotune", C.c_int32), ("step_variant", C.c_int32),
+                ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
+                ("alloc_user", C.c_void_p), ("stepper", C.c_int32)]
 
 
 class KesSolveOpts(C.Structure):
@@ -77,7 +81,8 @@ class KesResult(C.Structure):
 class KesStats(C.Structure):
     _fields_ = [("filter_calls", C.c_int64), ("filter_steps", C.c_int64), ("kernel_launches", C.c_int64),
                 ("filter_ms", C.c_double), ("solve_other_ms", C.c_double), ("bytes_per_step", C.c_int64),
-                ("step_variant", C.c_int32), ("step_grid", C.c_int32)]
+                ("step_variant", C.c_int32), ("step_grid", C.c_int32), ("blk_variant", C.c_int32),
+                ("blk_grid", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -112,6 +117,8 @@ _sig = {
                                          C.POINTER(C.POINTER(KesResult))]),
     "kes_set_weights": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, C.c_int32]),
     "kes_alpha_gaussian": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_int32, _P]),
+    "kes_alpha_triangle": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_int32, _P]),
+    "kes_weights_response": (C.c_int, [_P, C.c_double, C.c_int32, _P, C.c_int64, _P]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(lib, _name)
@@ -219,9 +226,26 @@ def kes_filter_response(omega_min: float, omega_max: float, tau: float, L: int, 
     return out
 
 
+def kes_weights_response(alpha, tau: float, omega) -> np.ndarray:
+    """beta~(omega) of the weight table alpha[0..L]."""
+    alpha = _f64_host(alpha)
+    omega = _f64_host(np.atleast_1d(omega))
+    out = np.empty_like(omega)
+    _check(lib.kes_weights_response(_ptr(alpha), float(tau), alpha.size - 1, _ptr(omega), omega.size, _ptr(out)),
+           "kes_weights_response")
+    return out
+
+
 def kes_alpha_gaussian(center: float, sigma: float, tau: float, L: int) -> np.ndarray:
     out = np.empty(L + 1)
     _check(lib.kes_alpha_gaussian(float(center), float(sigma), float(tau), int(L), _ptr(out)), "kes_alpha_gaussian")
+    return out
+
+
+def kes_alpha_triangle(center: float, half_width: float, tau: float, L: int) -> np.ndarray:
+    out = np.empty(L + 1)
+    _check(lib.kes_alpha_triangle(float(center), float(half_width), float(tau), int(L), _ptr(out)),
+           "kes_alpha_triangle")
     return out
 
 
@@ -395,8 +419,9 @@ class Context:
 
     def __init__(self, problem, precision: str = "fp64", sell_sigma: int = 1, use_graph: bool = True,
                  block_b: int = 1, stream=None, torch_alloc: bool = False, autotune: bool = True,
-                 step_variant: int | None = None):
+                 step_variant: int | None = None, stepper: str = "leapfrog"):
         o = kes_opts_default()
+        o.stepper = {"leapfrog": KES_STEPPER_LEAPFROG, "leapfrog4": KES_STEPPER_LEAPFROG4}[stepper]
         o.autotune = 1 if (autotune and step_variant is None) else 0
         o.step_variant = step_variant or 0
         o.precision = KES_PREC_FP32 if precision == "fp32" else KES_PREC_FP64

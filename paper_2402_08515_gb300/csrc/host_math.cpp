@@ -38,12 +38,29 @@ void alpha_gaussian(double center, double sigma, double tau, int L, double* alph
   }
 }
 
+// Triangular pass band: for the even band hat(s - c) + hat(s + c) with
+// hat(u) = max(0, 1 - |u|/h), the same transform gives alpha(t) = (2h/pi) cos(c t)
+// (sin(t h/2) / (t h/2))^2 (the hat's cosine integral is h times the squared sinc).
+void alpha_triangle(double center, double half_width, double tau, int L, double* alpha) {
+  const double pi = 3.14159265358979323846;
+  for (int n = 0; n <= L; ++n) {
+    const double t = n * tau;
+    const double x = 0.5 * t * half_width;
+    const double sinc = x == 0.0 ? 1.0 : std::sin(x) / x;
+    alpha[n] = tau * 2.0 * half_width / pi * std::cos(center * t) * sinc * sinc;
+  }
+}
+
 // beta~(omega) = sum_n alpha_n q_n(omega); q_{-1} = q_0 = 1,
 // q_{n+1} = (2 - tau^2 omega^2) q_n - q_{n-1}.
 void filter_response(double wmin, double wmax, double tau, int L, const double* omega, int64_t k,
                      double* beta) {
   std::vector<double> alpha(L + 1);
   alpha_table(wmin, wmax, tau, L, alpha.data());
+  weights_response(alpha.data(), tau, L, omega, k, beta);
+}
+
+void weights_response(const double* alpha, double tau, int L, const double* omega, int64_t k, double* beta) {
   for (int64_t i = 0; i < k; ++i) {
     const double two_minus = 2.0 - tau * tau * omega[i] * omega[i];
     double q_prev = 1.0, q = 1.0, sum = alpha[0];

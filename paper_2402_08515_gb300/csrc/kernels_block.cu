@@ -20,6 +20,10 @@ namespace {
 template <typename T>
 __device__ __forceinline__ T ld_cs(const T* p) { return __ldcs(p); }
 
+// Asks the memory system to bring the line holding p into L2; moves nothing into
+// registers, so a kernel computes the same with or without it.
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // NB contiguous values at p (16-byte aligned for NB * sizeof(T) >= 16) through the read-only path.
 template <int NB>
 __device__ __forceinline__ void load_row(const float* __restrict__ p, float (&v)[NB]) {
@@ -89,9 +93,11 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
   t = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
 }
 
-template <typename T, int NB, bool FIRST, bool LAST, int MINB>
+// g: the rows the sums gather from (x itself for the leapfrog, the fourth-order stage
+// otherwise); x seeds each row with 2 u_n - u_{n-1}.
+template <typename T, int NB, bool FIRST, bool LAST, int MINB, bool PF>
 __global__ void __launch_bounds__(256, MINB)
-    k_step_blk(SellDev A, const T* __restrict__ x, const T* prev, T* out, T* acc_s,
+    k_step_blk(SellDev A, const T* __restrict__ x, const T* __restrict__ g, const T* prev, T* out, T* acc_s,
                T* acc_c, double* acc64, int64_t acc_stride, int F, const T* __restrict__ ahi,
                const T* __restrict__ alo, int Lp1, int step, int cpt, int* flag) {
   // cpt == 0: every column accumulates with all F weight tables (F accumulators);
@@ -102,8 +108,34 @@ __global__ void __launch_bounds__(256, MINB)
   else val = A.val64;
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t s = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; s < A.n_slices;
-       s += nwarps) {
+  // PF: L2 prefetch of a slice's streamed lines (column indices, values, u_{n-1} and
+  // accumulator rows), the warp's first slice up front and each next slice while the
+  // current one is gathered, so that the dependent index -> gather -> FMA chain meets
+  // L2 instead of HBM latency. Every address lies inside the slice's own entries/rows.
+  const int nacc = cpt ? 1 : F;
+  auto prefetch_slice = [&](int64_t sn) {
+    if (sn >= A.n_slices) return;
+    const int64_t bn = A.slice_ptr[sn];
+    const int wn = static_cast<int>((A.slice_ptr[sn + 1] - bn) >> 5);
+    constexpr int kValLines = static_cast<int>(sizeof(T)) / 4;  // 128-byte lines per 32 values
+    for (int l = lane; l < wn; l += 32) prefetch_l2(A.col + bn + static_cast<int64_t>(l) * kSliceC);
+    for (int l = lane; l < wn * kValLines; l += 32)
+      prefetch_l2(val + bn + static_cast<int64_t>(l) * (128 / static_cast<int>(sizeof(T))));
+    constexpr int kRowLines = kSliceC * NB * static_cast<int>(sizeof(T)) / 128;  // lines of 32 rows x NB
+    if (lane < kRowLines) {
+      const int64_t off = sn * kSliceC * NB + lane * (128 / static_cast<int>(sizeof(T)));
+      if (!FIRST) prefetch_l2(prev + off);
+      if (kF32 || !FIRST)
+        for (int f = 0; f < nacc; ++f) {
+          prefetch_l2(acc_s + f * acc_stride + off);
+          if (kF32) prefetch_l2(acc_c + f * acc_stride + off);
+        }
+    }
+  };
+  const int64_t s0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  if constexpr (PF) prefetch_slice(s0);
+  for (int64_t s = s0; s < A.n_slices; s += nwarps) {
+    if constexpr (PF) prefetch_slice(s + nwarps);
     const int64_t beg = A.slice_ptr[s];
     const int w = static_cast<int>((A.slice_ptr[s + 1] - beg) >> 5);
     const int64_t mesh = A.slice_mesh ? A.slice_mesh[s] : 0;
@@ -130,8 +162,8 @@ __global__ void __launch_bounds__(256, MINB)
       const int32_t c0 = ld_cs(cp + k * kSliceC), c1 = ld_cs(cp + (k + 1) * kSliceC);
       const T v0 = ld_cs(vp + k * kSliceC), v1 = ld_cs(vp + (k + 1) * kSliceC);
       T x0[NB], x1[NB];
-      load_row<NB>(x + static_cast<int64_t>(c0) * NB, x0);
-      load_row<NB>(x + static_cast<int64_t>(c1) * NB, x1);
+      load_row<NB>(g + static_cast<int64_t>(c0) * NB, x0);
+      load_row<NB>(g + static_cast<int64_t>(c1) * NB, x1);
 #pragma unroll
       for (int j = 0; j < NB; ++j) un[j] = fma(v1, x1[j], fma(v0, x0[j], un[j]));
     }
@@ -139,13 +171,12 @@ __global__ void __launch_bounds__(256, MINB)
       const int32_t c0 = ld_cs(cp + k * kSliceC);
       const T v0 = ld_cs(vp + k * kSliceC);
       T x0[NB];
-      load_row<NB>(x + static_cast<int64_t>(c0) * NB, x0);
+      load_row<NB>(g + static_cast<int64_t>(c0) * NB, x0);
 #pragma unroll
       for (int j = 0; j < NB; ++j) un[j] = fma(v0, x0[j], un[j]);
     }
     if (!LAST) store_row<NB>(out + row * NB, un);
     bool bad = false;
-    const int nacc = cpt ? 1 : F;
     for (int f = 0; f < nacc; ++f) {
       const int64_t at = f * acc_stride + row * NB;
       // this step's weights per column (the start weight alpha_0 too on the first step)
@@ -214,35 +245,37 @@ __global__ void __launch_bounds__(256, MINB)
   }
 }
 
-// Launch shapes of the block kernels: minimum resident 256-thread blocks per SM.
-#define KES_BLK_VARIANTS(X) X(0, 1) X(1, 2) X(2, 3) X(3, 4)
+// Launch shapes of the block kernels: minimum resident 256-thread blocks per SM, and
+// whether the slices are prefetched into L2.
+#define KES_BLK_VARIANTS(X) X(0, 1, false) X(1, 2, false) X(2, 3, false) X(3, 4, false) \
+  X(4, 1, true) X(5, 2, true) X(6, 3, true) X(7, 4, true)
 
-template <typename T, int NB, int MINB>
+template <typename T, int NB, int MINB, bool PF>
 void blk_impl(int grid, int block, cudaStream_t st, bool first, bool last, const SellDev& A, const T* x,
-              const T* prev, T* out, T* acc_s, T* acc_c, double* acc64, int64_t acc_stride, int F, const T* ahi,
+              const T* g, const T* prev, T* out, T* acc_s, T* acc_c, double* acc64, int64_t acc_stride, int F, const T* ahi,
               const T* alo, int Lp1, int step, int cpt, int* flag) {
-#define KES_BLK_ARGS A, x, prev, out, acc_s, acc_c, acc64, acc_stride, F, ahi, alo, Lp1, step, cpt, flag
-  if (first && last) k_step_blk<T, NB, true, true, MINB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
-  else if (first) k_step_blk<T, NB, true, false, MINB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
-  else if (last) k_step_blk<T, NB, false, true, MINB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
-  else k_step_blk<T, NB, false, false, MINB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
+#define KES_BLK_ARGS A, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, F, ahi, alo, Lp1, step, cpt, flag
+  if (first && last) k_step_blk<T, NB, true, true, MINB, PF><<<grid, block, 0, st>>>(KES_BLK_ARGS);
+  else if (first) k_step_blk<T, NB, true, false, MINB, PF><<<grid, block, 0, st>>>(KES_BLK_ARGS);
+  else if (last) k_step_blk<T, NB, false, true, MINB, PF><<<grid, block, 0, st>>>(KES_BLK_ARGS);
+  else k_step_blk<T, NB, false, false, MINB, PF><<<grid, block, 0, st>>>(KES_BLK_ARGS);
 #undef KES_BLK_ARGS
 }
 
 template <typename T>
 void blk_dispatch(const LaunchCfg& cfg, int NB, cudaStream_t st, bool first, bool last, const SellDev& A,
-                  const T* x, const T* prev, T* out, T* acc_s, T* acc_c, double* acc64, int64_t acc_stride, int F,
+                  const T* x, const T* g, const T* prev, T* out, T* acc_s, T* acc_c, double* acc64, int64_t acc_stride, int F,
                   const T* ahi, const T* alo, int Lp1, int step, int cpt, int* flag) {
   const int64_t need = (A.n_slices + 7) / 8;
   const int grid = static_cast<int>(need < cfg.grid_blk ? need : cfg.grid_blk);
-#define KES_CALL(NBV, M)                                                                                   \
-  blk_impl<T, NBV, M>(grid, 256, st, first, last, A, x, prev, out, acc_s, acc_c, acc64, acc_stride, F,        \
-                      ahi, alo, Lp1, step, cpt, flag)
-#define X(ID, M)                         \
-  case ID:                               \
-    if (NB == 2) KES_CALL(2, M);         \
-    else if (NB == 4) KES_CALL(4, M);    \
-    else KES_CALL(8, M);                 \
+#define KES_CALL(NBV, M, P)                                                                                \
+  blk_impl<T, NBV, M, P>(grid, 256, st, first, last, A, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, F,     \
+                         ahi, alo, Lp1, step, cpt, flag)
+#define X(ID, M, P)                         \
+  case ID:                                  \
+    if (NB == 2) KES_CALL(2, M, P);         \
+    else if (NB == 4) KES_CALL(4, M, P);    \
+    else KES_CALL(8, M, P);                 \
     break;
   switch (cfg.variant_blk) {
     KES_BLK_VARIANTS(X)
@@ -252,10 +285,63 @@ void blk_dispatch(const LaunchCfg& cfg, int NB, cudaStream_t st, bool first, boo
 #undef KES_CALL
 }
 
-template <typename T, int NB, int M>
+// Stage of the fourth-order modified-equation leapfrog (Remark 2.4): v = u + A u / 12
+// for NB row-major columns (NB = 1: a plain vector), A = -tau^2 M^{-1} S in the SELL
+// layout, one warp per 32-row slice as in the step kernels. The step kernel then
+// gathers A v = -tau^2 K u + (tau^4 / 12) K^2 u (K = M^{-1} S).
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) k_stage4(SellDev A, const T* __restrict__ x, T* __restrict__ v) {
+  constexpr bool kF32 = std::is_same<T, float>::value;
+  const T* val;
+  if constexpr (kF32) val = A.val32;
+  else val = A.val64;
+  const T twelfth = T(1) / T(12);
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t s = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; s < A.n_slices;
+       s += nwarps) {
+    const int64_t beg = A.slice_ptr[s];
+    const int w = static_cast<int>((A.slice_ptr[s + 1] - beg) >> 5);
+    const T* vp = val + beg + lane;
+    const int32_t* cp = A.col + beg + lane;
+    const int64_t row = s * kSliceC + lane;
+    T acc[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) acc[j] = T(0);
+    for (int k = 0; k < w; ++k) {
+      const int32_t c0 = ld_cs(cp + k * kSliceC);
+      const T a0 = ld_cs(vp + k * kSliceC);
+      T xr[NB];
+      if constexpr (NB == 1) xr[0] = __ldg(x + c0);
+      else load_row<NB>(x + static_cast<int64_t>(c0) * NB, xr);
+#pragma unroll
+      for (int j = 0; j < NB; ++j) acc[j] = fma(a0, xr[j], acc[j]);
+    }
+    T xi[NB];
+    if constexpr (NB == 1) xi[0] = x[row];
+    else load_plain<NB>(x + row * NB, xi);
+#pragma unroll
+    for (int j = 0; j < NB; ++j) acc[j] = fma(acc[j], twelfth, xi[j]);
+    if constexpr (NB == 1) v[row] = acc[0];
+    else store_row<NB>(v + row * NB, acc);
+  }
+}
+
+template <typename T>
+void stage4_dispatch(const SellDev& A, int n_sm, cudaStream_t st, int NB, const T* x, T* v) {
+  const int64_t need = (A.n_slices + 7) / 8;  // 8 warps of 256 threads, one slice each
+  const int64_t cap = static_cast<int64_t>(n_sm) * 8;
+  const int grid = static_cast<int>(need < cap ? (need > 0 ? need : 1) : cap);
+  if (NB == 1) k_stage4<T, 1><<<grid, 256, 0, st>>>(A, x, v);
+  else if (NB == 2) k_stage4<T, 2><<<grid, 256, 0, st>>>(A, x, v);
+  else if (NB == 4) k_stage4<T, 4><<<grid, 256, 0, st>>>(A, x, v);
+  else k_stage4<T, 8><<<grid, 256, 0, st>>>(A, x, v);
+}
+
+template <typename T, int NB, int M, bool P>
 int occ_one(int block) {
   int nb = 0;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_blk<T, NB, false, false, M>, block, 0) ==
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_blk<T, NB, false, false, M, P>, block, 0) ==
                  cudaSuccess
              ? nb
              : 0;
@@ -316,7 +402,7 @@ int elem_grid(int64_t count) {
 
 int blk_variant_count() {
   int n = 0;
-#define X(ID, M) ++n;
+#define X(ID, M, P) ++n;
   KES_BLK_VARIANTS(X)
 #undef X
   return n;
@@ -324,12 +410,12 @@ int blk_variant_count() {
 
 int blk_blocks_per_sm(bool fp32, int NB, int variant, int block) {
   int nb = 0;
-#define X(ID, M)                                                                                  \
-  case ID:                                                                                        \
-    if (fp32) nb = NB == 2 ? occ_one<float, 2, M>(block) : NB == 4 ? occ_one<float, 4, M>(block)   \
-                                                                   : occ_one<float, 8, M>(block);  \
-    else nb = NB == 2 ? occ_one<double, 2, M>(block) : NB == 4 ? occ_one<double, 4, M>(block)      \
-                                                               : occ_one<double, 8, M>(block);     \
+#define X(ID, M, P)                                                                                     \
+  case ID:                                                                                              \
+    if (fp32) nb = NB == 2 ? occ_one<float, 2, M, P>(block) : NB == 4 ? occ_one<float, 4, M, P>(block)   \
+                                                                      : occ_one<float, 8, M, P>(block);  \
+    else nb = NB == 2 ? occ_one<double, 2, M, P>(block) : NB == 4 ? occ_one<double, 4, M, P>(block)      \
+                                                                  : occ_one<double, 8, M, P>(block);     \
     break;
   switch (variant) {
     KES_BLK_VARIANTS(X)
@@ -340,18 +426,18 @@ int blk_blocks_per_sm(bool fp32, int NB, int variant, int block) {
 }
 
 void launch_step_blk_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, int NB, bool first, bool last,
-                         const double* x, const double* prev, double* out, double* acc, int64_t acc_stride, int F,
-                         const double* alpha, int L, int step, int cpt, int* flag) {
-  blk_dispatch<double>(cfg, NB, st, first, last, A, x, prev, out, acc, nullptr, nullptr, acc_stride, F, alpha,
+                         const double* x, const double* g, const double* prev, double* out, double* acc,
+                         int64_t acc_stride, int F, const double* alpha, int L, int step, int cpt, int* flag) {
+  blk_dispatch<double>(cfg, NB, st, first, last, A, x, g, prev, out, acc, nullptr, nullptr, acc_stride, F, alpha,
                        nullptr, L + 1, step, cpt, flag);
   ++g_launches;
 }
 
 void launch_step_blk_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, int NB, bool first, bool last,
-                         const float* x, const float* prev, float* out, float* acc_s, float* acc_c, double* acc64,
-                         int64_t acc_stride, int F, const float* alpha_hi, const float* alpha_lo, int L, int step,
-                         int cpt, int* flag) {
-  blk_dispatch<float>(cfg, NB, st, first, last, A, x, prev, out, acc_s, acc_c, acc64, acc_stride, F, alpha_hi,
+                         const float* x, const float* g, const float* prev, float* out, float* acc_s, float* acc_c,
+                         double* acc64, int64_t acc_stride, int F, const float* alpha_hi, const float* alpha_lo,
+                         int L, int step, int cpt, int* flag) {
+  blk_dispatch<float>(cfg, NB, st, first, last, A, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, F, alpha_hi,
                       alpha_lo, L + 1, step, cpt, flag);
   ++g_launches;
 }
@@ -365,6 +451,16 @@ void launch_gather_rows(cudaStream_t st, const double* src, int64_t ld_src, int 
 void launch_scatter_rows(cudaStream_t st, const double* src, int NB, int ncols, const int32_t* row_src,
                          int64_t n_valid, double* dst, int64_t ld_dst, int64_t n_pad) {
   k_scatter_rows<<<elem_grid(n_pad * NB), 256, 0, st>>>(src, NB, ncols, row_src, n_valid, dst, ld_dst, n_pad);
+  ++g_launches;
+}
+
+void launch_stage4_f64(const SellDev& A, int n_sm, cudaStream_t st, int NB, const double* x, double* v) {
+  stage4_dispatch<double>(A, n_sm, st, NB, x, v);
+  ++g_launches;
+}
+
+void launch_stage4_f32(const SellDev& A, int n_sm, cudaStream_t st, int NB, const float* x, float* v) {
+  stage4_dispatch<float>(A, n_sm, st, NB, x, v);
   ++g_launches;
 }
 

@@ -64,8 +64,11 @@ __device__ __forceinline__ T row_dot(T acc, const T* __restrict__ v, const int32
   return acc;
 }
 
+// g is the vector the row sums gather from: u_n itself for the leapfrog, the stage
+// v = u_n + A u_n / 12 for the fourth-order scheme; x = u_n seeds the row (2 u_n - u_{n-1}).
 template <bool FIRST, bool LAST, int BATCH, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_step_f64(SellDev A, const double* __restrict__ x, const double* prev,
+__global__ void __launch_bounds__(256, MINB) k_step_f64(SellDev A, const double* __restrict__ x,
+                                                  const double* __restrict__ g, const double* prev,
                                                   double* out, double* acc, int64_t acc_stride, int F,
                                                   const double* __restrict__ alpha, int Lp1, int step,
                                                   int* flag) {
@@ -79,7 +82,7 @@ __global__ void __launch_bounds__(256, MINB) k_step_f64(SellDev A, const double*
     const int64_t mesh = A.slice_mesh ? A.slice_mesh[s] : 0;
     const double xi = x[row];
     const double pi = FIRST ? xi : prev[row];
-    const double un = row_dot<double, BATCH>(2.0 * xi - pi, A.val64 + beg + lane, A.col + beg + lane, w, x);
+    const double un = row_dot<double, BATCH>(2.0 * xi - pi, A.val64 + beg + lane, A.col + beg + lane, w, g);
     if (!LAST) out[row] = un;
     bool bad = false;
     for (int f = 0; f < F; ++f) {
@@ -103,7 +106,8 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
 }
 
 template <bool FIRST, bool LAST, int BATCH, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_step_f32(SellDev A, const float* __restrict__ x, const float* prev,
+__global__ void __launch_bounds__(256, MINB) k_step_f32(SellDev A, const float* __restrict__ x,
+                                                  const float* __restrict__ g, const float* prev,
                                                   float* out, float* acc_s, float* acc_c, double* acc64,
                                                   int64_t acc_stride, int F, const float* __restrict__ ahi,
                                                   const float* __restrict__ alo, int Lp1, int step,
@@ -119,7 +123,7 @@ __global__ void __launch_bounds__(256, MINB) k_step_f32(SellDev A, const float* 
     const float xi = x[row];
     const float pi = FIRST ? xi : prev[row];
     const float un = row_dot<float, BATCH>(__fsub_rn(__fmul_rn(2.0f, xi), pi), A.val32 + beg + lane,
-                                           A.col + beg + lane, w, x);
+                                           A.col + beg + lane, w, g);
     if (!LAST) out[row] = un;
     bool bad = false;
     for (int f = 0; f < F; ++f) {
@@ -214,14 +218,16 @@ int grid_for(const LaunchCfg& cfg, int64_t n_slices) {
 
 // Launch shapes of the step kernels: (load batch, minimum resident blocks of 256
 // threads per SM, which caps the registers). Every variant computes the same sums.
+// (An L2 prefetch of each warp's next slice was measured as well: 8-50% slower on the
+// 128^3 cube in every shape, so it is not offered.)
 #define KES_STEP_VARIANTS(X) \
   X(0, 8, 1) X(1, 8, 3) X(2, 8, 4) X(3, 4, 4) X(4, 4, 5) X(5, 4, 6) X(6, 2, 6) X(7, 2, 8)
 
 template <int BATCH, int MINB>
 void step_f64_impl(int grid, int block, cudaStream_t st, bool first, bool last, const SellDev& A, const double* x,
-                   const double* prev, double* out, double* acc, int64_t acc_stride, int F, const double* alpha,
+                   const double* g, const double* prev, double* out, double* acc, int64_t acc_stride, int F, const double* alpha,
                    int Lp1, int step, int* flag) {
-#define KES_F64_ARGS A, x, prev, out, acc, acc_stride, F, alpha, Lp1, step, flag
+#define KES_F64_ARGS A, x, g, prev, out, acc, acc_stride, F, alpha, Lp1, step, flag
   if (first && last) k_step_f64<true, true, BATCH, MINB><<<grid, block, 0, st>>>(KES_F64_ARGS);
   else if (first) k_step_f64<true, false, BATCH, MINB><<<grid, block, 0, st>>>(KES_F64_ARGS);
   else if (last) k_step_f64<false, true, BATCH, MINB><<<grid, block, 0, st>>>(KES_F64_ARGS);
@@ -231,9 +237,9 @@ void step_f64_impl(int grid, int block, cudaStream_t st, bool first, bool last, 
 
 template <int BATCH, int MINB>
 void step_f32_impl(int grid, int block, cudaStream_t st, bool first, bool last, const SellDev& A, const float* x,
-                   const float* prev, float* out, float* acc_s, float* acc_c, double* acc64, int64_t acc_stride,
+                   const float* g, const float* prev, float* out, float* acc_s, float* acc_c, double* acc64, int64_t acc_stride,
                    int F, const float* ahi, const float* alo, int Lp1, int step, int* flag) {
-#define KES_F32_ARGS A, x, prev, out, acc_s, acc_c, acc64, acc_stride, F, ahi, alo, Lp1, step, flag
+#define KES_F32_ARGS A, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, F, ahi, alo, Lp1, step, flag
   if (first && last) k_step_f32<true, true, BATCH, MINB><<<grid, block, 0, st>>>(KES_F32_ARGS);
   else if (first) k_step_f32<true, false, BATCH, MINB><<<grid, block, 0, st>>>(KES_F32_ARGS);
   else if (last) k_step_f32<false, true, BATCH, MINB><<<grid, block, 0, st>>>(KES_F32_ARGS);
@@ -294,8 +300,15 @@ int step_blocks_per_sm(bool fp32, int variant, int block) {
 }
 
 void launch_step_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bool first, const double* x,
-                     const double* prev, double* out, double* acc, int64_t acc_stride, int F, const double* alpha,
-                     int L, int step, bool last, int* flag) {
+                     const double* g, const double* prev, double* out, double* acc, int64_t acc_stride, int F,
+                     const double* alpha, int L, int step, bool last, int* flag) {
+  if (cfg.variant >= kRegStepVariants && g != x) {  // the bulk-copy shapes gather from u_n only
+    LaunchCfg reg = cfg;
+    reg.variant = 3;
+    reg.grid_step = cfg.n_sm * step_blocks_per_sm(false, 3, cfg.block_step);
+    launch_step_f64(A, reg, st, first, x, g, prev, out, acc, acc_stride, F, alpha, L, step, last, flag);
+    return;
+  }
   if (cfg.variant >= kRegStepVariants) {
     launch_step_tma_f64(A, cfg.tma, cfg.n_sm, st, first, last, x, prev, out, acc, acc_stride, F, alpha, L, step,
                         flag);
@@ -305,7 +318,7 @@ void launch_step_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bo
   switch (cfg.variant) {
 #define X(ID, B, M)                                                                                        \
   case ID:                                                                                                 \
-    step_f64_impl<B, M>(grid, cfg.block_step, st, first, last, A, x, prev, out, acc, acc_stride, F,        \
+    step_f64_impl<B, M>(grid, cfg.block_step, st, first, last, A, x, g, prev, out, acc, acc_stride, F,     \
                         alpha, L + 1, step, flag);                                                         \
     break;
     KES_STEP_VARIANTS(X)
@@ -316,8 +329,17 @@ void launch_step_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bo
 }
 
 void launch_step_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bool first, bool last, const float* x,
-                     const float* prev, float* out, float* acc_s, float* acc_c, double* acc64, int64_t acc_stride,
-                     int F, const float* alpha_hi, const float* alpha_lo, int L, int step, int* flag) {
+                     const float* g, const float* prev, float* out, float* acc_s, float* acc_c, double* acc64,
+                     int64_t acc_stride, int F, const float* alpha_hi, const float* alpha_lo, int L, int step,
+                     int* flag) {
+  if (cfg.variant >= kRegStepVariants && g != x) {  // the bulk-copy shapes gather from u_n only
+    LaunchCfg reg = cfg;
+    reg.variant = 3;
+    reg.grid_step = cfg.n_sm * step_blocks_per_sm(true, 3, cfg.block_step);
+    launch_step_f32(A, reg, st, first, last, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, F, alpha_hi, alpha_lo,
+                    L, step, flag);
+    return;
+  }
   if (cfg.variant >= kRegStepVariants) {
     launch_step_tma_f32(A, cfg.tma, cfg.n_sm, st, first, last, x, prev, out, acc_s, acc_c, acc64, acc_stride, F,
                         alpha_hi, alpha_lo, L, step, flag);
@@ -327,7 +349,7 @@ void launch_step_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bo
   switch (cfg.variant) {
 #define X(ID, B, M)                                                                                        \
   case ID:                                                                                                 \
-    step_f32_impl<B, M>(grid, cfg.block_step, st, first, last, A, x, prev, out, acc_s, acc_c, acc64,        \
+    step_f32_impl<B, M>(grid, cfg.block_step, st, first, last, A, x, g, prev, out, acc_s, acc_c, acc64,     \
                         acc_stride, F, alpha_hi, alpha_lo, L + 1, step, flag);                             \
     break;
     KES_STEP_VARIANTS(X)

@@ -128,6 +128,8 @@ struct kes_ctx {
   int stage_out_F = 0;
   double* U64[2] = {nullptr, nullptr};
   float* U32[3] = {nullptr, nullptr, nullptr};
+  double* V64 = nullptr;  // fourth-order stage v = u + A u / 12 (n_pad x NBcap), allocated on first use
+  float* V32 = nullptr;
   float* acc_s = nullptr;
   float* acc_c = nullptr;
   double* tmp_user = nullptr;  // n x NBcap, caller layout
@@ -262,11 +264,15 @@ void block_out(kes_ctx* c, const double* src, int NB, int nb, double* dst, int32
 }
 
 // --------------------------------------------------------------- filter
+// Largest stable tau * omega of the context's stepper.
+double cfl_bound(const kes_ctx* c) { return c->opts.stepper == KES_STEPPER_LEAPFROG4 ? 2.0 * std::sqrt(3.0) : 2.0; }
+
 // Issues the L fused steps of one filter application of an NB-column block on the
 // context stream: stage_in -> stage_out (cpt = 0: F filtered blocks, every column with
 // every weight table; cpt > 0: one block, column j with table min(j / cpt, F - 1)).
 int64_t issue_filter_steps(kes_ctx* c, int NB, bool fp64, int cpt) {
   const int64_t before = g_launches;
+  const bool ho = c->opts.stepper == KES_STEPPER_LEAPFROG4;
   const int L = c->L, F = c->F;
   const int64_t stride = c->n_pad * NB;
   if (fp64) {
@@ -283,12 +289,17 @@ int64_t issue_filter_steps(kes_ctx* c, int NB, bool fp64, int cpt) {
       const double* x = s == 0 ? c->stage_in : c->U64[(s - 1) & 1];
       const double* prev = s <= 1 ? c->stage_in : c->U64[s & 1];
       double* out = c->U64[s & 1];
+      const double* g = x;
+      if (ho) {  // fourth order: the step gathers from v = u_n + A u_n / 12
+        launch_stage4_f64(A64, cfg.n_sm, c->stream, NB, x, c->V64);
+        g = c->V64;
+      }
       if (NB == 1)
-        launch_step_f64(A64, cfg, c->stream, first, x, prev, out, c->stage_out, stride, F, c->alpha64, L, s, last,
-                        c->d_flag);
+        launch_step_f64(A64, cfg, c->stream, first, x, g, prev, out, c->stage_out, stride, F, c->alpha64, L, s,
+                        last, c->d_flag);
       else
-        launch_step_blk_f64(A64, cfg, c->stream, NB, first, last, x, prev, out, c->stage_out, stride, F, c->alpha64,
-                            L, s, cpt, c->d_flag);
+        launch_step_blk_f64(A64, cfg, c->stream, NB, first, last, x, g, prev, out, c->stage_out, stride, F,
+                            c->alpha64, L, s, cpt, c->d_flag);
     }
   } else {
     const SellDev A32 = c->step_A32();
@@ -298,12 +309,17 @@ int64_t issue_filter_steps(kes_ctx* c, int NB, bool fp64, int cpt) {
       const float* x = s == 0 ? c->U32[2] : c->U32[(s - 1) & 1];
       const float* prev = s <= 1 ? c->U32[2] : c->U32[s & 1];
       float* out = c->U32[s & 1];
+      const float* g = x;
+      if (ho) {
+        launch_stage4_f32(A32, c->cfg.n_sm, c->stream, NB, x, c->V32);
+        g = c->V32;
+      }
       if (NB == 1)
-        launch_step_f32(A32, c->cfg, c->stream, first, last, x, prev, out, c->acc_s, c->acc_c, c->stage_out, stride,
-                        F, c->alpha_hi, c->alpha_lo, L, s, c->d_flag);
+        launch_step_f32(A32, c->cfg, c->stream, first, last, x, g, prev, out, c->acc_s, c->acc_c, c->stage_out,
+                        stride, F, c->alpha_hi, c->alpha_lo, L, s, c->d_flag);
       else
-        launch_step_blk_f32(A32, c->cfg, c->stream, NB, first, last, x, prev, out, c->acc_s, c->acc_c, c->stage_out,
-                            stride, F, c->alpha_hi, c->alpha_lo, L, s, cpt, c->d_flag);
+        launch_step_blk_f32(A32, c->cfg, c->stream, NB, first, last, x, g, prev, out, c->acc_s, c->acc_c,
+                            c->stage_out, stride, F, c->alpha_hi, c->alpha_lo, L, s, cpt, c->d_flag);
     }
   }
   return g_launches - before;
@@ -323,6 +339,10 @@ void ensure_fp64_state(kes_ctx* c) {
 void run_filter(kes_ctx* c, int NB, bool fp64, int cpt = 0) {
   if (cpt > 0 && NB < 2) throw KesError{KES_ERR_ARG};  // per-column tables live in the block kernels
   if (fp64) ensure_fp64_state(c);
+  if (c->opts.stepper == KES_STEPPER_LEAPFROG4) {  // stage buffers before any graph captures them
+    if (fp64 && !c->V64) c->V64 = c->dzero_n<double>(c->n_pad * c->NBcap);
+    if (!fp64 && !c->V32) c->V32 = c->dzero_n<float>(c->n_pad * c->NBcap);
+  }
   cudaEvent_t e0 = c->get_event(), e1 = c->get_event();
   KES_CUDA(cudaEventRecord(e0, c->stream));
   if (c->opts.use_graph) {
@@ -466,15 +486,17 @@ void tune_steps(kes_ctx* c) {
   int best = 0;
   float best_ms = 3.0e38f;
   for (int v = 0; v < step_variant_count(); ++v) {
+    // the fourth-order step gathers from its stage, which the bulk-copy shapes do not
+    if (c->opts.stepper == KES_STEPPER_LEAPFROG4 && v >= kRegStepVariants) continue;
     if (!select_variant(c, v)) continue;
     const float ms = timed([&](int count) {
       for (int i = 0; i < count; ++i) {
         if (fp32)
-          launch_step_f32(c->step_A32(), c->cfg, c->stream, false, false, c->U32[0], c->U32[1], c->U32[1], c->acc_s,
-                          c->acc_c, c->stage_out, c->n_pad, 1, a32, a32, 7, 1, c->d_flag);
+          launch_step_f32(c->step_A32(), c->cfg, c->stream, false, false, c->U32[0], c->U32[0], c->U32[1], c->U32[1],
+                          c->acc_s, c->acc_c, c->stage_out, c->n_pad, 1, a32, a32, 7, 1, c->d_flag);
         else
-          launch_step_f64(c->step_A64(), c->cfg, c->stream, false, c->U64[0], c->U64[1], c->U64[1], c->stage_out,
-                          c->n_pad, 1, a64, 7, 1, false, c->d_flag);
+          launch_step_f64(c->step_A64(), c->cfg, c->stream, false, c->U64[0], c->U64[0], c->U64[1], c->U64[1],
+                          c->stage_out, c->n_pad, 1, a64, 7, 1, false, c->d_flag);
       }
     });
     if (ms < best_ms) {
@@ -494,10 +516,12 @@ void tune_steps(kes_ctx* c) {
       const float ms = timed([&](int count) {
         for (int i = 0; i < count; ++i) {
           if (fp32)
-            launch_step_blk_f32(c->step_A32(), c->cfg, c->stream, NB, false, false, c->U32[0], c->U32[1], c->U32[1],
+            launch_step_blk_f32(c->step_A32(), c->cfg, c->stream, NB, false, false, c->U32[0], c->U32[0], c->U32[1],
+                                c->U32[1],
                                 c->acc_s, c->acc_c, c->stage_out, c->n_pad * NB, 1, a32, a32, 7, 1, 0, c->d_flag);
           else
-            launch_step_blk_f64(c->step_A64(), c->cfg, c->stream, NB, false, false, c->U64[0], c->U64[1], c->U64[1],
+            launch_step_blk_f64(c->step_A64(), c->cfg, c->stream, NB, false, false, c->U64[0], c->U64[0], c->U64[1],
+                                c->U64[1],
                                 c->stage_out, c->n_pad * NB, 1, a64, 7, 1, 0, c->d_flag);
         }
       });
@@ -652,6 +676,8 @@ kes_status create_impl(kes_ctx** out, int32_t nm, const int64_t* n, const int64_
     if (c->opts.block_b > 8) throw KesError{KES_ERR_UNSUPPORTED};
     if ((c->opts.dev_alloc == nullptr) != (c->opts.dev_free == nullptr)) throw KesError{KES_ERR_ARG};
     if (c->opts.step_variant < 0 || c->opts.step_variant >= step_variant_count()) throw KesError{KES_ERR_ARG};
+    if (c->opts.stepper != KES_STEPPER_LEAPFROG && c->opts.stepper != KES_STEPPER_LEAPFROG4)
+      throw KesError{KES_ERR_ARG};
     // host-side validation first: a bad input never reaches the GPU
     for (int j = 0; j < nm; ++j) {
       if (!row_ptr[j] || !col[j] || !val[j] || !m_diag[j]) throw KesError{KES_ERR_ARG};
@@ -694,6 +720,8 @@ kes_status create_impl(kes_ctx** out, int32_t nm, const int64_t* n, const int64_
     c->stats.bytes_per_step = kes_step_bytes(c, 1, 1);
     c->stats.step_variant = c->cfg.variant;
     c->stats.step_grid = c->cfg.grid_step;
+    c->stats.blk_variant = c->NBcap > 1 ? c->cfg.variant_blk : -1;
+    c->stats.blk_grid = c->NBcap > 1 ? c->cfg.grid_blk : 0;
     return KES_OK;
   });
   if (st != KES_OK) {
@@ -716,7 +744,7 @@ kes_status set_weights_impl(kes_ctx* c, int32_t F, const double* alpha, const do
       const double a = wmin[j * F + f], b = wmax[j * F + f];
       if (!(a >= 0.0) || !(b > a) || !std::isfinite(b)) return KES_ERR_ARG;
     }
-    if (c->meshes[j].omega_est > 0.0 && tau[j] * c->meshes[j].omega_est >= 2.0) return KES_ERR_UNSTABLE;
+    if (c->meshes[j].omega_est > 0.0 && tau[j] * c->meshes[j].omega_est >= cfl_bound(c)) return KES_ERR_UNSTABLE;
   }
   const size_t need = static_cast<size_t>(nm) * F * (L + 1);
   if (alpha)
@@ -1339,9 +1367,13 @@ int64_t kes_step_bytes(const kes_ctx* c, int32_t b, int32_t F) {
   // matrix: value (of A = -tau^2 M^{-1} S) + int32 column per stored entry, plus a 4-byte
   // row pointer per row as CSR would need; per row and vector: the gather of u_n once,
   // u_{n-1} read, u_{n+1} written, F accumulators read and written (FP32 form: s and c).
-  if (c->opts.precision == KES_PREC_FP64)
-    return 12 * c->nnz + 4 * (c->n + 1) + c->n * int64_t(b) * (8 + 8 + 8 + 16 * F);
-  return 8 * c->nnz + 4 * (c->n + 1) + c->n * int64_t(b) * (4 + 4 + 4 + 16 * F);
+  // The fourth-order stepper adds a stage pass (matrix and row pointers again, u_n gathered,
+  // the stage written) and the step reads the stage (gathered) besides u_n.
+  const int64_t vs = c->opts.precision == KES_PREC_FP64 ? 8 : 4;
+  const int64_t mat = (vs + 4) * c->nnz + 4 * (c->n + 1);
+  const int64_t step = mat + c->n * int64_t(b) * (3 * vs + 16 * F);
+  if (c->opts.stepper == KES_STEPPER_LEAPFROG4) return step + mat + c->n * int64_t(b) * (3 * vs);
+  return step;
 }
 
 kes_status kes_estimate_omega_max(kes_ctx* c, int32_t iters, const double* v0, double* omega_max,
@@ -1392,6 +1424,14 @@ kes_status kes_alpha_gaussian(double center, double sigma, double tau, int32_t L
   return KES_OK;
 }
 
+kes_status kes_alpha_triangle(double center, double half_width, double tau, int32_t L, double* alpha) {
+  if (!alpha || L < 1 || !(tau > 0.0) || !(half_width > 0.0) || !(center >= 0.0) || !std::isfinite(center) ||
+      !std::isfinite(half_width))
+    return KES_ERR_ARG;
+  kes::alpha_triangle(center, half_width, tau, L, alpha);
+  return KES_OK;
+}
+
 kes_status kes_alpha_table(double wmin, double wmax, double tau, int32_t L, double* alpha) {
   if (!alpha || L < 1 || !(tau > 0.0) || !(wmax > wmin) || !(wmin >= 0.0)) return KES_ERR_ARG;
   kes::alpha_table(wmin, wmax, tau, L, alpha);
@@ -1402,6 +1442,13 @@ kes_status kes_filter_response(double wmin, double wmax, double tau, int32_t L, 
                                double* beta) {
   if (!omega || !beta || k < 0 || L < 1 || !(tau > 0.0) || !(wmax > wmin) || !(wmin >= 0.0)) return KES_ERR_ARG;
   kes::filter_response(wmin, wmax, tau, L, omega, k, beta);
+  return KES_OK;
+}
+
+kes_status kes_weights_response(const double* alpha, double tau, int32_t L, const double* omega, int64_t k,
+                                double* beta) {
+  if (!alpha || !omega || !beta || k < 0 || L < 1 || !(tau > 0.0)) return KES_ERR_ARG;
+  kes::weights_response(alpha, tau, L, omega, k, beta);
   return KES_OK;
 }
 
@@ -1503,6 +1550,8 @@ kes_status kes_reset_stats(kes_ctx* c) {
     c->stats.bytes_per_step = bps;
     c->stats.step_variant = c->cfg.variant;
     c->stats.step_grid = c->cfg.grid_step;
+    c->stats.blk_variant = c->NBcap > 1 ? c->cfg.variant_blk : -1;
+    c->stats.blk_grid = c->NBcap > 1 ? c->cfg.grid_blk : 0;
     return KES_OK;
   });
 }

@@ -18,6 +18,8 @@ void alpha_table(double wmin, double wmax, double tau, int L, double* alpha);
 void filter_response(double wmin, double wmax, double tau, int L, const double* omega, int64_t k,
                      double* beta);
 void alpha_gaussian(double center, double sigma, double tau, int L, double* alpha);
+void alpha_triangle(double center, double half_width, double tau, int L, double* alpha);
+void weights_response(const double* alpha, double tau, int L, const double* omega, int64_t k, double* beta);
 // Symmetric eigensolver for the projected problem: Householder tridiagonalisation
 // followed by implicit QR steps with Wilkinson shifts. A is k x k col-major (lower
 // triangle read), w ascending, V (optional) orthonormal eigenvectors col-major.
@@ -67,20 +69,22 @@ struct LaunchCfg {
 
 // One fused leapfrog step, FP64 (Sec. 2.3, eq. 2stepmethod + eq. disc_filtercoeff), on the
 // values of A = -tau^2 M^{-1} S (see launch_scale_values):
-//   out = (2 x - prev) + A x;   acc_f += alpha_f[step+1] * out   (f < F)
+//   out = (2 x - prev) + A g;   acc_f += alpha_f[step+1] * out   (f < F)
+// g = x for the leapfrog; g = the stage v = x + A x / 12 (launch_stage4_*) for the
+// fourth-order scheme (bulk-copy shapes need g = x and fall back to a register shape).
 // first: prev = x and acc_f = alpha_f[0] * x + alpha_f[1] * out.
 // x, prev, out, acc: length n_pad; acc_f at acc + f * acc_stride; alpha of mesh m, table f at
 // alpha + (m * F + f) * (L+1). last: the state of the final step is not stored;
 // flag[0] |= 1 if any acc entry is not finite.
 void launch_step_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bool first,
-                     const double* x, const double* prev, double* out,
+                     const double* x, const double* g, const double* prev, double* out,
                      double* acc, int64_t acc_stride, int F, const double* alpha, int L, int step,
                      bool last, int* flag);
 
 // FP32 form: values/state FP32, accumulator as an unevaluated FP32 sum (s + c) kept by
 // error-free transformations; alpha as FP32 pairs (hi + lo). last: writes acc64 = s + c in FP64.
 void launch_step_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bool first, bool last,
-                     const float* x, const float* prev, float* out, float* acc_s,
+                     const float* x, const float* g, const float* prev, float* out, float* acc_s,
                      float* acc_c, double* acc64, int64_t acc_stride, int F, const float* alpha_hi,
                      const float* alpha_lo, int L, int step, int* flag);
 // FP32 start over n_pad x nb row-major values: x32 = (float) r64; s_f = fl(alpha_f[0] r),
@@ -95,12 +99,16 @@ void launch_init_f32(cudaStream_t st, const SellDev& A, int nb, const double* r6
 // accumulates with all F weight tables; cpt > 0: column j only with table j / cpt (the
 // columns of several intervals share the matrix stream).
 void launch_step_blk_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, int NB, bool first, bool last,
-                         const double* x, const double* prev, double* out, double* acc, int64_t acc_stride, int F,
-                         const double* alpha, int L, int step, int cpt, int* flag);
+                         const double* x, const double* g, const double* prev, double* out, double* acc,
+                         int64_t acc_stride, int F, const double* alpha, int L, int step, int cpt, int* flag);
 void launch_step_blk_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, int NB, bool first, bool last,
-                         const float* x, const float* prev, float* out, float* acc_s, float* acc_c, double* acc64,
-                         int64_t acc_stride, int F, const float* alpha_hi, const float* alpha_lo, int L, int step,
-                         int cpt, int* flag);
+                         const float* x, const float* g, const float* prev, float* out, float* acc_s, float* acc_c,
+                         double* acc64, int64_t acc_stride, int F, const float* alpha_hi, const float* alpha_lo,
+                         int L, int step, int cpt, int* flag);
+// Stage of the fourth-order modified-equation leapfrog: v = x + A x / 12 over NB row-major
+// columns (NB in {1, 2, 4, 8}; n_pad x NB).
+void launch_stage4_f64(const SellDev& A, int n_sm, cudaStream_t st, int NB, const double* x, double* v);
+void launch_stage4_f32(const SellDev& A, int n_sm, cudaStream_t st, int NB, const float* x, float* v);
 int blk_variant_count();
 int blk_blocks_per_sm(bool fp32, int NB, int variant, int block);
 

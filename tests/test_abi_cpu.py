@@ -2,6 +2,7 @@
 include/kes.h declares, and its host-side logic (weights, filter response,
 small symmetric eigensolver, input validation) is right."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -105,3 +106,49 @@ def test_gaussian_weights_match_oracle():
                                    rtol=1e-13, atol=1e-16)
     with pytest.raises(K.KesError):
         K.kes_alpha_gaussian(1.0, -1.0, 0.1, 10)
+
+
+def test_weights_response_matches_oracle():
+    tau, L = 0.0099, 300
+    w = np.linspace(0.0, 60.0, 97)
+    for a in [O.alpha_table(20.0, 30.0, tau, L), O.alpha_table_gaussian(25.0, 3.0, tau, L),
+              O.alpha_table_triangle(25.0, 5.0, tau, L)]:
+        np.testing.assert_allclose(K.kes_weights_response(a, tau, w), O.beta_tilde(w, a, tau), rtol=1e-11, atol=1e-12)
+
+
+def test_triangle_weights_match_oracle():
+    for c, h, tau, L in [(25.0, 5.0, 0.0099, 300), (42.5, 2.5, 0.004, 600), (0.0, 2.0, 0.01, 50)]:
+        np.testing.assert_allclose(K.kes_alpha_triangle(c, h, tau, L), O.alpha_table_triangle(c, h, tau, L),
+                                   rtol=1e-13, atol=1e-16)
+    with pytest.raises(K.KesError):
+        K.kes_alpha_triangle(1.0, 0.0, 0.1, 10)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    # the ctypes mirrors of kes_opts, kes_solve_opts, kes_result and kes_stats must have
+    # the C sizes and field offsets: compile a probe against include/kes.h
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"kes_opts": K.KesOpts, "kes_solve_opts": K.KesSolveOpts, "kes_result": K.KesResult,
+               "kes_stats": K.KesStats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "kes.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "probe"
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    subprocess.run([cc, "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    for line in filter(None, out):
+        cname, what, val = line.split()
+        py = structs[cname]
+        got = ctypes.sizeof(py) if what == "size" else getattr(py, what).offset
+        assert got == int(val), (cname, what, got, val)

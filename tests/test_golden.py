@@ -27,3 +27,18 @@ def test_workload_interval_counts():
     data = json.load(open(GOLDEN))
     assert (data["square64"]["count"], len(data["square64"]["distinct"])) == (38, 20)
     assert (data["cube128"]["count"], len(data["cube128"]["distinct"])) == (424, 83)
+
+
+def test_workload_spectra_agree_with_the_oracle():
+    # bench.py counts and checks eigenvalues with fe_inputs.spectra, the tests with the
+    # oracle's closed form: the two copies must agree
+    from fe_inputs import spectra as wl_spectra
+    for cells, h, iv in [((64, 64), (1 / 64, 1 / 64), (20.0, 30.0)), ((23, 19, 17), (1 / 23, 0.9 / 19, 0.8 / 17), (6.0, 10.0)),
+                         ((128, 128, 128), (1 / 128,) * 3, (40.0, 45.0))]:
+        a = spectra.eigenvalues_in(cells, h, *iv)
+        b = wl_spectra.omega2_in(cells, h, *iv)
+        np.testing.assert_allclose(b, a, rtol=1e-14)
+        va, ma = spectra.distinct(a)
+        vb, mb = wl_spectra.cluster(b)
+        np.testing.assert_allclose(vb, va, rtol=1e-14)
+        np.testing.assert_array_equal(mb, ma)

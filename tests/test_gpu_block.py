@@ -9,7 +9,7 @@ import oracle as O
 import paper_2402_08515_gb300 as K
 from fe_inputs import box_grid, flared_tube, square_grid, start_vectors
 from oracle import spectra
-from tests.tolerances import EIG_REL, filter_error, filter_tol
+from tests.tolerances import EIG_REL, filter_error, filter_tol, filter_tol_leapfrog4
 
 pytestmark = pytest.mark.gpu
 
@@ -171,13 +171,16 @@ def test_fp32_solve_with_fp64_refinement_reaches_fp64_residuals(b):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_gaussian_weights_filter_and_solve(precision):
+@pytest.mark.parametrize("band", ["gaussian", "triangle"])
+def test_band_weights_filter_and_solve(precision, band):
     p = square_grid(32)
     S = p.to_scipy()
     tau = _tau(p)
     L = 300
-    c, sigma = 25.0, 2.5
-    alpha = O.alpha_table_gaussian(c, sigma, tau, L)
+    if band == "gaussian":
+        alpha = O.alpha_table_gaussian(25.0, 2.5, tau, L)
+    else:
+        alpha = O.alpha_table_triangle(25.0, 5.0, tau, L)
     r = start_vectors(p.n, 1, 9)
     ref = O.filter_apply(S, p.m, r[0], tau, alpha)
     tol = 1e-8 if precision == "fp64" else 1e-5
@@ -190,7 +193,7 @@ def test_gaussian_weights_filter_and_solve(precision):
         so.kmax, so.tol = 80, tol
         res = K.kes_krylov_solve(ctx.handle, start_vectors(p.n, 1, 0)[0], so)
     exact = spectra.eigenvalues_in(p.cells, p.h, 20.0, 30.0)
-    print(f"{precision} Gaussian band: accepted {res['n_pairs']}")
+    print(f"{precision} {band} band: accepted {res['n_pairs']}")
     assert res["n_pairs"] >= 5
     for th in res["omega2"]:
         assert np.min(np.abs(exact - th)) <= EIG_REL[precision] * th
@@ -309,3 +312,64 @@ def test_multi_interval_fp32_with_refinement():
             assert np.min(np.abs(exact - th)) <= 1e-10 * th
     for th, x in zip(res["omega2"], res["vectors"]):
         assert np.linalg.norm(S @ x - th * p.m * x) <= 1.01e-8 * th * np.linalg.norm(p.m * x)
+
+
+# ---------------------------------------------------------------- fourth-order stepper (Remark 2.4)
+
+def _tau4(p):
+    return 0.9 * 2 * math.sqrt(3) / O.power_iteration(p.to_scipy(), p.m, start_vectors(p.n, 1, 0)[0], 300)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("b", [1, 4])
+def test_leapfrog4_filter_matches_oracle(meshes, precision, b):
+    p = meshes[1]
+    tau = _tau4(p)
+    L = 80
+    alpha = O.alpha_table(6.0, 10.0, tau, L)
+    R = start_vectors(p.n, b, 23)
+    with K.Context(p, precision=precision, block_b=b, stepper="leapfrog4") as c:
+        K.kes_set_filter(c.handle, 6.0, 10.0, tau, L)
+        out = np.zeros((1, b, p.n))
+        K.kes_filter_apply(c.handle, R, out, b)
+        st = K.kes_get_stats(c.handle)
+    assert st["kernel_launches"] >= 2 * L      # a stage and a step per time step
+    for j in range(b):
+        ref = O.filter_apply_leapfrog4(p.to_scipy(), p.m, R[j], tau, alpha)
+        err = filter_error(out[0, j], ref, R[j], p.m, alpha)
+        print(f"{precision} b={b} column {j}: error {err:.2e} (tolerance {filter_tol_leapfrog4(L, precision):.2e})")
+        assert err <= filter_tol_leapfrog4(L, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_leapfrog4_solve_finds_closed_form_eigenvalues(precision):
+    p = square_grid(32)
+    S = p.to_scipy()
+    tau = _tau4(p)
+    L = 175                                     # T close to the leapfrog tests' 300 steps of 0.9 * 2 / omega
+    tol = 1e-8 if precision == "fp64" else 1e-5
+    so = K.kes_solve_opts_default()
+    so.kmax, so.tol, so.want_vectors = 80, tol, 1
+    with K.Context(p, precision=precision, stepper="leapfrog4") as c:
+        K.kes_set_filter(c.handle, 20.0, 30.0, tau, L)
+        res = K.kes_krylov_solve(c.handle, start_vectors(p.n, 1, 0)[0], so)
+    exact = spectra.eigenvalues_in(p.cells, p.h, 20.0, 30.0)
+    d_exact, _ = spectra.distinct(exact)
+    d_got, _ = spectra.distinct(res["omega2"])
+    print(f"{precision}: accepted {len(d_got)} of {len(d_exact)} distinct")
+    assert len(d_got) >= len(d_exact) - (0 if precision == "fp64" else 4)
+    for th, x in zip(res["omega2"], res["vectors"]):
+        assert np.min(np.abs(exact - th)) <= EIG_REL[precision] * th
+        assert np.linalg.norm(S @ x - th * p.m * x) <= tol * 1.01 * th * np.linalg.norm(p.m * x)
+
+
+def test_leapfrog4_cfl_bound():
+    p = square_grid(24)
+    for stepper, ratio, ok in [("leapfrog", 2.5, False), ("leapfrog4", 2.5, True), ("leapfrog4", 3.5, False)]:
+        with K.Context(p, stepper=stepper) as c:
+            w, _ = K.kes_estimate_omega_max(c.handle, 300, start_vectors(p.n, 1, 0)[0])
+            if ok:
+                K.kes_set_filter(c.handle, 10.0, 20.0, ratio / w, 20)
+            else:
+                with pytest.raises(K.KesError):
+                    K.kes_set_filter(c.handle, 10.0, 20.0, ratio / w, 20)

@@ -161,3 +161,48 @@ def test_labels_not_following_the_merge_order_are_caught(monkeypatch):
     _patch(monkeypatch, "multi_interval_krylov_solve", stale_labels)
     with pytest.raises(AssertionError):
         pins.test_multi_interval_solver_finds_every_eigenvalue_of_each_interval()
+
+
+def test_triangle_sinc_not_squared_is_caught(monkeypatch):
+    def unsquared(t, c, h):
+        t = np.asarray(t, dtype=np.float64)
+        x = 0.5 * t * h
+        sinc = np.where(x == 0, 1.0, np.sin(x) / np.where(x == 0, 1.0, x))
+        return 2.0 * h / math.pi * np.cos(c * t) * sinc
+    monkeypatch.setattr(K, "triangle_weight", unsquared)
+    monkeypatch.setattr(oracle, "triangle_weight", unsquared)
+    with pytest.raises(AssertionError):
+        pins.test_triangle_weight_matches_numerical_inverse_transform()
+
+
+def test_leapfrog4_wrong_correction_in_filter_is_caught(monkeypatch):
+    def halved_correction(S, m, r, tau, alpha):    # tau^4 / 24 instead of tau^4 / 12
+        L = len(alpha) - 1
+        y_prev, y = np.array(r, dtype=np.float64), np.array(r, dtype=np.float64)
+        acc = alpha[0] * y
+        for l in range(L):
+            Ky = (S @ y) / m
+            y_next = 2.0 * y - y_prev - tau * tau * Ky + tau ** 4 / 24.0 * ((S @ Ky) / m)
+            acc = acc + alpha[l + 1] * y_next
+            y_prev, y = y, y_next
+        return acc
+    _patch(monkeypatch, "filter_apply_leapfrog4", halved_correction)
+    with pytest.raises(AssertionError):
+        pins.test_leapfrog4_filter_maps_eigenvectors_by_its_beta_tilde("box")
+
+
+def test_leapfrog4_wrong_recurrence_is_caught(monkeypatch):
+    def q_bad(omega, tau, L):                       # x^2 / 6 instead of x^2 / 12
+        omega = np.atleast_1d(np.asarray(omega, dtype=np.float64))
+        x = tau * tau * omega * omega
+        q = np.empty((L + 1, omega.size))
+        qp, qc = np.ones_like(omega), np.ones_like(omega)
+        q[0] = qc
+        for l in range(L):
+            qn = (2 - x + x * x / 6) * qc - qp
+            q[l + 1] = qn
+            qp, qc = qc, qn
+        return q
+    _patch(monkeypatch, "q_values_leapfrog4", q_bad)
+    with pytest.raises(AssertionError):
+        pins.test_leapfrog4_recurrence_is_third_kind_chebyshev_of_its_phase()

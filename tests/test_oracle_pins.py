@@ -414,3 +414,86 @@ def test_gaussian_weight_matches_numerical_inverse_transform():
     for t in [0.0, 0.3, 1.1, 2.5]:
         num = 2 / math.pi * np.trapezoid(band * np.cos(t * s), s)
         assert O.gaussian_weight(np.array([t]), c, sigma)[0] == pytest.approx(num, abs=1e-8)
+
+
+def test_triangle_weight_matches_numerical_inverse_transform():
+    c, h = 3.0, 1.2
+    s = np.linspace(0, 12, 240001)
+    band = np.maximum(0, 1 - np.abs(s - c) / h) + np.maximum(0, 1 - np.abs(s + c) / h)
+    for t in [0.0, 0.4, 1.7, 3.3, 9.0]:
+        num = 2 / math.pi * np.trapezoid(band * np.cos(t * s), s)
+        assert O.triangle_weight(np.array([t]), c, h)[0] == pytest.approx(num, abs=1e-8)
+
+
+def test_triangle_weight_gives_triangle_band():
+    c, h = 3.0, 1.0
+    tau, L = 0.001, 40000
+    a = O.alpha_table_triangle(c, h, tau, L)
+    # smooth points of the hat: rectangle rule and leapfrog phase error, O(tau)
+    w = np.array([1.0, 2.2, 2.5, 3.5, 3.9, 5.0])
+    ref = np.maximum(0, 1 - np.abs(w - c) / h)
+    np.testing.assert_allclose(O.beta_tilde(w, a, tau), ref, atol=2e-3)
+    # the peak is a kink: the transform decays like 1/t^2, and the tail cut at T = L tau
+    # is bounded there by int_T^inf |alpha| dt <= 8 / (pi h T)
+    T = L * tau
+    assert abs(O.beta_tilde(np.array([c]), a, tau)[0] - 1.0) <= 8 / (math.pi * h * T) + 2e-3
+
+
+# ---------------------------------------------------------------- fourth-order stepper (Remark 2.4)
+
+def test_leapfrog4_recurrence_is_third_kind_chebyshev_of_its_phase():
+    # with 2 cos(theta) = 2 - x + x^2/12 the recurrence is the leapfrog's with that
+    # theta: q_l = cos((l + 1/2) theta) / cos(theta / 2)
+    tau, L = 0.05, 60
+    omega = np.array([0.5, 3.0, 20.0, 40.0, 60.0, 69.0])
+    x = (tau * omega) ** 2
+    theta = np.arccos(1 - x / 2 + x * x / 24)
+    l = np.arange(L + 1)[:, None]
+    ref = np.cos((l + 0.5) * theta) / np.cos(theta / 2)
+    np.testing.assert_allclose(O.q_values_leapfrog4(omega, tau, L), ref, atol=1e-9)
+
+
+def test_leapfrog4_phase_error_is_fourth_order():
+    # theta - omega tau = O((omega tau)^5) for the modified-equation scheme, O(^3) for
+    # the plain leapfrog: halving omega tau divides the errors by ~32 and ~8
+    def theta4(z):
+        return np.arccos(1 - z * z / 2 + z ** 4 / 24)
+
+    def theta2(z):
+        return np.arccos(1 - z * z / 2)
+    z = np.array([0.4, 0.2, 0.1])
+    e4 = np.abs(theta4(z) - z)
+    e2 = np.abs(theta2(z) - z)
+    np.testing.assert_allclose(e4[:-1] / e4[1:], 32.0, rtol=0.05)
+    np.testing.assert_allclose(e2[:-1] / e2[1:], 8.0, rtol=0.05)
+    # and the oracle's q follows its phase: q_l(omega) for a tiny tau tracks cos(l omega tau)
+    tau, L, om = 1e-3, 2000, np.array([7.0])
+    q = O.q_values_leapfrog4(om, tau, L)[:, 0]
+    assert np.max(np.abs(q - np.cos((np.arange(L + 1) + 0.5) * om * tau) / np.cos(om * tau / 2))) < 1e-9
+
+
+def test_leapfrog4_stable_to_2_sqrt3():
+    tau, L = 0.01, 200                         # just past the bound q grows ~1.6x a step
+    w_ok = np.array([0.99 * 2 * math.sqrt(3) / tau])
+    w_bad = np.array([1.01 * 2 * math.sqrt(3) / tau])
+    assert np.max(np.abs(O.q_values_leapfrog4(w_ok, tau, L))) < 50
+    assert np.max(np.abs(O.q_values_leapfrog4(w_bad, tau, L))) > 1e6
+
+
+@pytest.mark.parametrize("kind", ["random", "box"])
+def test_leapfrog4_filter_maps_eigenvectors_by_its_beta_tilde(kind):
+    if kind == "random":
+        S, m = random_pencil(40, 5)
+        w2, V = dense_pencil(S, m)
+        vecs, omegas = V.T[::7], np.sqrt(w2[::7])
+    else:
+        p = box_grid((6, 5, 4))
+        S, m = p.to_scipy(), p.m
+        w2, V = dense_pencil(S, m)
+        vecs, omegas = V.T[::11], np.sqrt(w2[::11])
+    tau = 0.9 * 2 * math.sqrt(3) / math.sqrt(w2.max())
+    alpha = O.alpha_table(0.3 * omegas.max(), 0.6 * omegas.max(), tau, 40)
+    beta = O.beta_tilde_leapfrog4(omegas, alpha, tau)
+    for v, b in zip(vecs, beta):
+        out = O.filter_apply_leapfrog4(S, m, v, tau, alpha)
+        np.testing.assert_allclose(out, b * v, atol=1e-10 * np.abs(v).max() * np.abs(alpha).sum())

@@ -46,6 +46,19 @@ FILTER_TOL_C = 32.0
 EIG_REL = {"fp64": 1e-10, "fp32": 1e-6}
 
 
+# Fourth-order stepper (stage v = u + A u / 12, then the step gathers A v): the stage's
+# rounding, about 2 eps |u| (its row sum of terms adding up to ||A|| / 12 |u| <= |u|, and
+# the final add), reaches u_{n+1} through A, ||A|| = tau^2 ||M^-1 S|| <= 0.81 * 12 ~ 10 at
+# 0.9 of its CFL bound: c_loc grows from ~4 to ~4 + 10 * 2 = 24, six times the leapfrog's.
+FILTER4_TOL_C = 6 * FILTER_TOL_C
+
+
+def filter_tol_leapfrog4(L: int, precision: str) -> float:
+    """filter_tol for the fourth-order modified-equation leapfrog."""
+    eps = EPS64 if precision == "fp64" else EPS32
+    return FILTER4_TOL_C * eps * (L + 1) ** 0.5
+
+
 def filter_tol(L: int, precision: str) -> float:
     """Tolerance on ||C_gpu r - C_oracle r||_M / (sum_n |alpha_n| * ||r||_M)."""
     eps = EPS64 if precision == "fp64" else EPS32
