@@ -60,6 +60,8 @@ def parse_args(argv=None):
     ap.add_argument("--tts-forms", default="", help="comma-separated subset of the --mode tts forms")
     ap.add_argument("--tts-workloads", default="cube128_fp64,box2m_fp64", help="workloads of --mode tts")
     ap.add_argument("--L", type=int, default=0, help="override the workload's time steps (--mode filter)")
+    ap.add_argument("--blk-variant", type=int, default=None,
+                    help="fixed block step-kernel launch shape instead of the autotuner's choice")
     ap.add_argument("--variant", type=int, default=None,
                     help="fixed step-kernel launch shape instead of the autotuner's choice")
     return ap.parse_args(argv)
@@ -254,7 +256,7 @@ def run_kes(args):
     b = wl.b
     stream = torch.cuda.Stream(device=dev)
     ctx = K.Context(problems if batch else problems[0], precision=wl.precision, stream=stream,
-                    step_variant=args.variant, block_b=b)
+                    step_variant=args.variant, blk_variant=args.blk_variant, block_b=b)
     h = ctx.handle
     v0 = start_block(problems, 1, wl.seed)[0]
     omega_pow, gersh = K.kes_estimate_omega_max_batch(h, wl.power_iters, v0)
@@ -464,7 +466,7 @@ TTS_FORMS = (
     ("fp32+refine1", "fp32", 1, 1),
     ("fp32+refine2", "fp32", 1, 2),
 )
-TTS_KMAX = (160, 200, 240, 280, 320, 360, 400)
+TTS_KMAX = (160, 200, 240, 280, 320, 360, 400)   # coarse sweep; then steps of 10 below the first success
 
 
 def run_tts(args):
@@ -473,7 +475,7 @@ def run_tts(args):
     eigenvalues: for each form a sweep over the Krylov dimension kmax (one projection at
     the end, so that every run costs what a solve of that size costs), reporting each
     run's time and the distinct eigenvalues it accepted; a form's time to solution is
-    that of the smallest kmax that accepts every distinct eigenvalue of the interval.
+    that of the smallest kmax (to within 10) that accepts every distinct eigenvalue.
     The FP32 forms reach 1e-8 through FP64 refinement sweeps on their in-interval Ritz
     vectors, filtered 8 at a time."""
     import numpy as np
@@ -499,7 +501,8 @@ def run_tts(args):
                 w, _ = K.kes_estimate_omega_max(c.handle, wl.power_iters, v0)
                 K.kes_set_filter(c.handle, wl.omega_min, wl.omega_max, wl.cfl * 2 / w, wl.L)
                 R = start_vectors(p.n, b, wl.seed + 1)
-                for kmax in TTS_KMAX:
+
+                def run(kmax):
                     so = K.kes_solve_opts_default()
                     so.kmax, so.tol, so.check_every, so.refine_sweeps = kmax, tol, kmax, refine
                     torch.cuda.synchronize()
@@ -516,7 +519,18 @@ def run_tts(args):
                     print(json.dumps({"workload": wname, **runs[-1]}), file=sys.stderr, flush=True)
                     if len(found) >= len(distinct):
                         summary[name] = {"seconds": dt, "kmax": kmax, "accepted_pairs": res["n_pairs"]}
+                        return True
+                    return False
+
+                last_fail = None
+                for kmax in TTS_KMAX:
+                    if run(kmax):
+                        lo = (last_fail or kmax - 40) + 10
+                        for k in range(lo, kmax, 10):   # the coarse step overshoots by up to 30
+                            if run(k):
+                                break
                         break
+                    last_fail = kmax
         out.append({"workload": wname, "dofs": p.n, "interval": [wl.omega_min, wl.omega_max], "L": wl.L,
                     "distinct_in_interval": len(distinct), "eigenvalues_in_interval": len(exact),
                     "time_to_all_distinct": summary, "runs": runs})
@@ -559,13 +573,17 @@ def run_weights(args):
         for name, alpha in tables.items():
             beta = K.kes_weights_response(alpha, tau, w_all)
             K.kes_set_weights(c.handle, alpha[None, None, :], [[lo]], [[hi]], [tau], L)
-            so = K.kes_solve_opts_default()
-            so.kmax, so.tol, so.check_every, so.n_wanted = 300, 1e-8, 5, len(distinct)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            res = K.kes_krylov_solve(c.handle, start_vectors(p.n, 1, wl.seed + 1)[0], so)
-            dt = time.perf_counter() - t0
-            found, _ = spectra.cluster(res["omega2"])
+            # the smallest Krylov dimension (steps of 5) that accepts every distinct eigenvalue
+            for kmax in range(20, 305, 5):
+                so = K.kes_solve_opts_default()
+                so.kmax, so.tol, so.check_every = kmax, 1e-8, kmax
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                res = K.kes_krylov_solve(c.handle, start_vectors(p.n, 1, wl.seed + 1)[0], so)
+                dt = time.perf_counter() - t0
+                found, _ = spectra.cluster(res["omega2"])
+                if len(found) >= len(distinct):
+                    break
             rows.append({"weight": name, "beta_min_inside": float(np.abs(beta[inside]).min()),
                          "beta_max_outside": float(np.abs(beta[~inside]).max()),
                          "accepted_distinct": len(found), "distinct_in_interval": len(distinct),

@@ -84,6 +84,7 @@ typedef struct kes_opts {
   void (*dev_free)(void* ptr, size_t bytes, void* user);
   void* alloc_user;
   int32_t stepper;     /* enum kes_stepper (default KES_STEPPER_LEAPFROG) */
+  int32_t blk_variant; /* launch shape of the block (SpMM) step kernel when autotune is 0 */
 } kes_opts;
 
 /* Options of kes_krylov_solve. Initialise with kes_solve_opts_default(). */
@@ -242,6 +243,9 @@ kes_status kes_alpha_triangle(double center, double half_width, double tau, int3
    may be NULL) of the symmetric k x k col-major matrix A (only its lower triangle is read).
    This is the small projected problem of eq. (projevp) with B^T M B = I. */
 kes_status kes_sym_eig(int32_t k, const double* A, double* w, double* V);
+/* kes_launch_shapes: the number of launch shapes of the single-vector step kernel
+   (kes_opts.step_variant) and of the block step kernel (kes_opts.blk_variant). */
+void kes_launch_shapes(int32_t* n_step, int32_t* n_block);
 /* kes_step_bytes: algorithmic HBM bytes of one fused leapfrog step of this context for b vectors
    and F intervals (every matrix entry, row pointer and per-row vector read or written once; the
    fourth-order stepper adds its stage pass and the read of the stage). */

@@ -27,7 +27,7 @@ __all__ = [
     "Context", "header_functions", "kes_filter_apply_noalloc", "KES_NOALLOC_MAX_N",
     "kes_create_batch", "kes_mesh_count", "kes_estimate_omega_max_batch", "kes_set_filters_batch",
     "kes_block_krylov_solve", "kes_set_weights", "kes_alpha_gaussian", "kes_filter_apply_columns",
-    "kes_alpha_triangle", "kes_weights_response",
+    "kes_alpha_triangle", "kes_weights_response", "kes_launch_shapes",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -59,7 +59,7 @@ class KesOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("sell_sigma", C.c_int32), ("use_graph", C.c_int32),
                 ("block_b", C.c_int32), ("autotune", C.c_int32), ("step_variant", C.c_int32),
                 ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
-                ("alloc_user", C.c_void_p), ("stepper", C.c_int32)]
+                ("alloc_user", C.c_void_p), ("stepper", C.c_int32), ("blk_variant", C.c_int32)]
 
 
 class KesSolveOpts(C.Structure):
@@ -119,6 +119,7 @@ _sig = {
     "kes_alpha_gaussian": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_int32, _P]),
     "kes_alpha_triangle": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_int32, _P]),
     "kes_weights_response": (C.c_int, [_P, C.c_double, C.c_int32, _P, C.c_int64, _P]),
+    "kes_launch_shapes": (None, [C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(lib, _name)
@@ -224,6 +225,13 @@ def kes_filter_response(omega_min: float, omega_max: float, tau: float, L: int, 
     _check(lib.kes_filter_response(float(omega_min), float(omega_max), float(tau), int(L), _ptr(omega),
                                    omega.size, _ptr(out)), "kes_filter_response")
     return out
+
+
+def kes_launch_shapes() -> tuple:
+    """(launch shapes of the single-vector step kernel, of the block step kernel)."""
+    a, b = C.c_int32(), C.c_int32()
+    lib.kes_launch_shapes(C.byref(a), C.byref(b))
+    return a.value, b.value
 
 
 def kes_weights_response(alpha, tau: float, omega) -> np.ndarray:
@@ -419,11 +427,12 @@ class Context:
 
     def __init__(self, problem, precision: str = "fp64", sell_sigma: int = 1, use_graph: bool = True,
                  block_b: int = 1, stream=None, torch_alloc: bool = False, autotune: bool = True,
-                 step_variant: int | None = None, stepper: str = "leapfrog"):
+                 step_variant: int | None = None, stepper: str = "leapfrog", blk_variant: int | None = None):
         o = kes_opts_default()
         o.stepper = {"leapfrog": KES_STEPPER_LEAPFROG, "leapfrog4": KES_STEPPER_LEAPFROG4}[stepper]
-        o.autotune = 1 if (autotune and step_variant is None) else 0
+        o.autotune = 1 if (autotune and step_variant is None and blk_variant is None) else 0
         o.step_variant = step_variant or 0
+        o.blk_variant = blk_variant or 0
         o.precision = KES_PREC_FP32 if precision == "fp32" else KES_PREC_FP64
         o.sell_sigma = sell_sigma
         o.use_graph = 1 if use_graph else 0

@@ -27,7 +27,9 @@ __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefe
 // NB contiguous values at p (16-byte aligned for NB * sizeof(T) >= 16) through the read-only path.
 template <int NB>
 __device__ __forceinline__ void load_row(const float* __restrict__ p, float (&v)[NB]) {
-  if constexpr (NB >= 4) {
+  if constexpr (NB == 1) {
+    v[0] = __ldg(p);
+  } else if constexpr (NB >= 4) {
 #pragma unroll
     for (int q = 0; q < NB / 4; ++q) {
       const float4 t = __ldg(reinterpret_cast<const float4*>(p) + q);
@@ -40,6 +42,10 @@ __device__ __forceinline__ void load_row(const float* __restrict__ p, float (&v)
 }
 template <int NB>
 __device__ __forceinline__ void load_row(const double* __restrict__ p, double (&v)[NB]) {
+  if constexpr (NB == 1) {
+    v[0] = __ldg(p);
+    return;
+  }
 #pragma unroll
   for (int q = 0; q < NB / 2; ++q) {
     const double2 t = __ldg(reinterpret_cast<const double2*>(p) + q);
@@ -51,7 +57,9 @@ __device__ __forceinline__ void load_row(const double* __restrict__ p, double (&
 // 1-4 instructions instead of NB scalar ones that each touch a separate sector.
 template <int NB>
 __device__ __forceinline__ void load_plain(const float* p, float (&v)[NB]) {
-  if constexpr (NB >= 4) {
+  if constexpr (NB == 1) {
+    v[0] = *p;
+  } else if constexpr (NB >= 4) {
 #pragma unroll
     for (int q = 0; q < NB / 4; ++q) {
       const float4 t = reinterpret_cast<const float4*>(p)[q];
@@ -64,6 +72,10 @@ __device__ __forceinline__ void load_plain(const float* p, float (&v)[NB]) {
 }
 template <int NB>
 __device__ __forceinline__ void load_plain(const double* p, double (&v)[NB]) {
+  if constexpr (NB == 1) {
+    v[0] = *p;
+    return;
+  }
 #pragma unroll
   for (int q = 0; q < NB / 2; ++q) {
     const double2 t = reinterpret_cast<const double2*>(p)[q];
@@ -72,7 +84,9 @@ __device__ __forceinline__ void load_plain(const double* p, double (&v)[NB]) {
 }
 template <int NB>
 __device__ __forceinline__ void store_row(float* p, const float (&v)[NB]) {
-  if constexpr (NB >= 4) {
+  if constexpr (NB == 1) {
+    *p = v[0];
+  } else if constexpr (NB >= 4) {
 #pragma unroll
     for (int q = 0; q < NB / 4; ++q)
       reinterpret_cast<float4*>(p)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
@@ -82,6 +96,10 @@ __device__ __forceinline__ void store_row(float* p, const float (&v)[NB]) {
 }
 template <int NB>
 __device__ __forceinline__ void store_row(double* p, const double (&v)[NB]) {
+  if constexpr (NB == 1) {
+    *p = v[0];
+    return;
+  }
 #pragma unroll
   for (int q = 0; q < NB / 2; ++q) reinterpret_cast<double2*>(p)[q] = make_double2(v[2 * q], v[2 * q + 1]);
 }
@@ -95,7 +113,11 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
 
 // g: the rows the sums gather from (x itself for the leapfrog, the fourth-order stage
 // otherwise); x seeds each row with 2 u_n - u_{n-1}.
-template <typename T, int NB, bool FIRST, bool LAST, int MINB, bool PF>
+// LPR lanes share a row: LPR = 1 gives a lane a whole row of NB columns and a warp a
+// 32-row slice; LPR = 2 gives a lane NB / 2 columns and a warp half a slice (16 rows),
+// which halves the registers a thread needs for its columns. Either way every column is
+// the same FMA chain in entry order, so the shapes round identically.
+template <typename T, int NB, bool FIRST, bool LAST, int MINB, bool PF, int LPR>
 __global__ void __launch_bounds__(256, MINB)
     k_step_blk(SellDev A, const T* __restrict__ x, const T* __restrict__ g, const T* prev, T* out, T* acc_s,
                T* acc_c, double* acc64, int64_t acc_stride, int F, const T* __restrict__ ahi,
@@ -103,11 +125,17 @@ __global__ void __launch_bounds__(256, MINB)
   // cpt == 0: every column accumulates with all F weight tables (F accumulators);
   // cpt > 0: column j accumulates only with table min(j / cpt, F - 1) (one accumulator)
   constexpr bool kF32 = std::is_same<T, float>::value;
+  constexpr int NH = NB / LPR;            // columns of this lane
+  constexpr int kRows = kSliceC / LPR;    // rows of a warp's unit
+  static_assert(LPR == 1 || !PF, "the L2 prefetch shapes take whole slices");
   const T* val;
   if constexpr (kF32) val = A.val32;
   else val = A.val64;
   const int lane = threadIdx.x & 31;
+  const int sub = lane / LPR;             // row within the unit
+  const int co = (lane % LPR) * NH;       // first column of this lane
   const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  const int64_t n_units = A.n_slices * LPR;
   // PF: L2 prefetch of a slice's streamed lines (column indices, values, u_{n-1} and
   // accumulator rows), the warp's first slice up front and each next slice while the
   // current one is gathered, so that the dependent index -> gather -> FMA chain meets
@@ -132,28 +160,31 @@ __global__ void __launch_bounds__(256, MINB)
         }
     }
   };
-  const int64_t s0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  if constexpr (PF) prefetch_slice(s0);
-  for (int64_t s = s0; s < A.n_slices; s += nwarps) {
-    if constexpr (PF) prefetch_slice(s + nwarps);
+  const int64_t u0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  if constexpr (PF) prefetch_slice(u0);
+  for (int64_t u = u0; u < n_units; u += nwarps) {
+    if constexpr (PF) prefetch_slice(u + nwarps);
+    const int64_t s = u / LPR;
+    const int rs = static_cast<int>(u % LPR) * kRows + sub;  // row within the slice
     const int64_t beg = A.slice_ptr[s];
     const int w = static_cast<int>((A.slice_ptr[s + 1] - beg) >> 5);
     const int64_t mesh = A.slice_mesh ? A.slice_mesh[s] : 0;
-    const T* vp = val + beg + lane;
-    const int32_t* cp = A.col + beg + lane;
-    const int64_t row = s * kSliceC + lane;
-    T xi[NB], pi[NB], un[NB];
-    load_plain<NB>(x + row * NB, xi);
+    const T* vp = val + beg + rs;
+    const int32_t* cp = A.col + beg + rs;
+    const int64_t row = s * kSliceC + rs;
+    const int64_t ro = row * NB + co;  // this lane's values in a row-major block
+    T xi[NH], pi[NH], un[NH];
+    load_plain<NH>(x + ro, xi);
     if constexpr (FIRST) {
 #pragma unroll
-      for (int j = 0; j < NB; ++j) pi[j] = xi[j];
+      for (int j = 0; j < NH; ++j) pi[j] = xi[j];
     } else {
-      load_plain<NB>(prev + row * NB, pi);
+      load_plain<NH>(prev + ro, pi);
     }
     // u_{n+1} = (2 u_n - u_{n-1}) + A u_n: one FMA chain per column in entry order,
     // seeded like the single-vector kernels, so every column rounds like them
 #pragma unroll
-    for (int j = 0; j < NB; ++j) {
+    for (int j = 0; j < NH; ++j) {
       if constexpr (kF32) un[j] = __fsub_rn(__fmul_rn(2.0f, xi[j]), pi[j]);
       else un[j] = 2.0 * xi[j] - pi[j];
     }
@@ -161,30 +192,30 @@ __global__ void __launch_bounds__(256, MINB)
     for (; k + 2 <= w; k += 2) {
       const int32_t c0 = ld_cs(cp + k * kSliceC), c1 = ld_cs(cp + (k + 1) * kSliceC);
       const T v0 = ld_cs(vp + k * kSliceC), v1 = ld_cs(vp + (k + 1) * kSliceC);
-      T x0[NB], x1[NB];
-      load_row<NB>(g + static_cast<int64_t>(c0) * NB, x0);
-      load_row<NB>(g + static_cast<int64_t>(c1) * NB, x1);
+      T x0[NH], x1[NH];
+      load_row<NH>(g + static_cast<int64_t>(c0) * NB + co, x0);
+      load_row<NH>(g + static_cast<int64_t>(c1) * NB + co, x1);
 #pragma unroll
-      for (int j = 0; j < NB; ++j) un[j] = fma(v1, x1[j], fma(v0, x0[j], un[j]));
+      for (int j = 0; j < NH; ++j) un[j] = fma(v1, x1[j], fma(v0, x0[j], un[j]));
     }
     if (k < w) {
       const int32_t c0 = ld_cs(cp + k * kSliceC);
       const T v0 = ld_cs(vp + k * kSliceC);
-      T x0[NB];
-      load_row<NB>(g + static_cast<int64_t>(c0) * NB, x0);
+      T x0[NH];
+      load_row<NH>(g + static_cast<int64_t>(c0) * NB + co, x0);
 #pragma unroll
-      for (int j = 0; j < NB; ++j) un[j] = fma(v0, x0[j], un[j]);
+      for (int j = 0; j < NH; ++j) un[j] = fma(v0, x0[j], un[j]);
     }
-    if (!LAST) store_row<NB>(out + row * NB, un);
+    if (!LAST) store_row<NH>(out + ro, un);
     bool bad = false;
     for (int f = 0; f < nacc; ++f) {
-      const int64_t at = f * acc_stride + row * NB;
+      const int64_t at = f * acc_stride + ro;
       // this step's weights per column (the start weight alpha_0 too on the first step)
-      T ah[NB], al[NB], a0[NB];
+      T ah[NH], al[NH], a0[NH];
       if (cpt) {
 #pragma unroll
-        for (int j = 0; j < NB; ++j) {
-          const int64_t ai = (mesh * F + min(j / cpt, F - 1)) * Lp1;  // padding columns: last table
+        for (int j = 0; j < NH; ++j) {
+          const int64_t ai = (mesh * F + min((co + j) / cpt, F - 1)) * Lp1;  // padding columns: last table
           ah[j] = ahi[ai + step + 1];
           if constexpr (kF32) al[j] = alo[ai + step + 1];
           if constexpr (FIRST && !kF32) a0[j] = ahi[ai];
@@ -196,19 +227,19 @@ __global__ void __launch_bounds__(256, MINB)
         if constexpr (kF32) l = alo[ai + step + 1];
         if constexpr (FIRST && !kF32) z = ahi[ai];
 #pragma unroll
-        for (int j = 0; j < NB; ++j) {
+        for (int j = 0; j < NH; ++j) {
           ah[j] = h;
           al[j] = l;
           a0[j] = z;
         }
       }
       if constexpr (kF32) {
-        float as[NB], ac[NB];
-        load_plain<NB>(acc_s + at, as);
-        load_plain<NB>(acc_c + at, ac);
-        double v64[NB];
+        float as[NH], ac[NH];
+        load_plain<NH>(acc_s + at, as);
+        load_plain<NH>(acc_c + at, ac);
+        double v64[NH];
 #pragma unroll
-        for (int j = 0; j < NB; ++j) {
+        for (int j = 0; j < NH; ++j) {
           const float p = __fmul_rn(ah[j], un[j]);
           const float pe = fmaf(al[j], un[j], fmaf(ah[j], un[j], -p));
           float sn, e;
@@ -220,45 +251,46 @@ __global__ void __launch_bounds__(256, MINB)
           if (LAST) bad |= !isfinite(v64[j]);
         }
         if (LAST) {
-          store_row<NB>(acc64 + at, v64);
+          store_row<NH>(acc64 + at, v64);
         } else {
-          store_row<NB>(acc_s + at, as);
-          store_row<NB>(acc_c + at, ac);
+          store_row<NH>(acc_s + at, as);
+          store_row<NH>(acc_c + at, ac);
         }
       } else {
-        double na[NB];
+        double na[NH];
         if constexpr (FIRST) {
 #pragma unroll
-          for (int j = 0; j < NB; ++j) na[j] = a0[j] * xi[j];
+          for (int j = 0; j < NH; ++j) na[j] = a0[j] * xi[j];
         } else {
-          load_plain<NB>(acc_s + at, na);
+          load_plain<NH>(acc_s + at, na);
         }
 #pragma unroll
-        for (int j = 0; j < NB; ++j) {
+        for (int j = 0; j < NH; ++j) {
           na[j] = fma(ah[j], un[j], na[j]);
           if (LAST) bad |= !isfinite(na[j]);
         }
-        store_row<NB>(acc_s + at, na);
+        store_row<NH>(acc_s + at, na);
       }
     }
     if (LAST && bad) atomicOr(flag, 1);
   }
 }
 
-// Launch shapes of the block kernels: minimum resident 256-thread blocks per SM, and
-// whether the slices are prefetched into L2.
-#define KES_BLK_VARIANTS(X) X(0, 1, false) X(1, 2, false) X(2, 3, false) X(3, 4, false) \
-  X(4, 1, true) X(5, 2, true) X(6, 3, true) X(7, 4, true)
+// Launch shapes of the block kernels: minimum resident 256-thread blocks per SM, whether
+// the slices are prefetched into L2, lanes per row.
+#define KES_BLK_VARIANTS(X)                                                                                   \
+  X(0, 1, false, 1) X(1, 2, false, 1) X(2, 3, false, 1) X(3, 4, false, 1) X(4, 1, true, 1) X(5, 2, true, 1) \
+  X(6, 3, true, 1) X(7, 4, true, 1) X(8, 4, false, 2) X(9, 5, false, 2) X(10, 6, false, 2)
 
-template <typename T, int NB, int MINB, bool PF>
+template <typename T, int NB, int MINB, bool PF, int LPR>
 void blk_impl(int grid, int block, cudaStream_t st, bool first, bool last, const SellDev& A, const T* x,
               const T* g, const T* prev, T* out, T* acc_s, T* acc_c, double* acc64, int64_t acc_stride, int F, const T* ahi,
               const T* alo, int Lp1, int step, int cpt, int* flag) {
 #define KES_BLK_ARGS A, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, F, ahi, alo, Lp1, step, cpt, flag
-  if (first && last) k_step_blk<T, NB, true, true, MINB, PF><<<grid, block, 0, st>>>(KES_BLK_ARGS);
-  else if (first) k_step_blk<T, NB, true, false, MINB, PF><<<grid, block, 0, st>>>(KES_BLK_ARGS);
-  else if (last) k_step_blk<T, NB, false, true, MINB, PF><<<grid, block, 0, st>>>(KES_BLK_ARGS);
-  else k_step_blk<T, NB, false, false, MINB, PF><<<grid, block, 0, st>>>(KES_BLK_ARGS);
+  if (first && last) k_step_blk<T, NB, true, true, MINB, PF, LPR><<<grid, block, 0, st>>>(KES_BLK_ARGS);
+  else if (first) k_step_blk<T, NB, true, false, MINB, PF, LPR><<<grid, block, 0, st>>>(KES_BLK_ARGS);
+  else if (last) k_step_blk<T, NB, false, true, MINB, PF, LPR><<<grid, block, 0, st>>>(KES_BLK_ARGS);
+  else k_step_blk<T, NB, false, false, MINB, PF, LPR><<<grid, block, 0, st>>>(KES_BLK_ARGS);
 #undef KES_BLK_ARGS
 }
 
@@ -266,16 +298,22 @@ template <typename T>
 void blk_dispatch(const LaunchCfg& cfg, int NB, cudaStream_t st, bool first, bool last, const SellDev& A,
                   const T* x, const T* g, const T* prev, T* out, T* acc_s, T* acc_c, double* acc64, int64_t acc_stride, int F,
                   const T* ahi, const T* alo, int Lp1, int step, int cpt, int* flag) {
-  const int64_t need = (A.n_slices + 7) / 8;
+  // a block of 256 threads is 8 warps; a warp takes a slice (or half a slice, LPR = 2)
+  int lpr = 1;
+#define X(ID, M, P, R) \
+  if (cfg.variant_blk == ID) lpr = R;
+  KES_BLK_VARIANTS(X)
+#undef X
+  const int64_t need = (A.n_slices * lpr + 7) / 8;
   const int grid = static_cast<int>(need < cfg.grid_blk ? need : cfg.grid_blk);
-#define KES_CALL(NBV, M, P)                                                                                \
-  blk_impl<T, NBV, M, P>(grid, 256, st, first, last, A, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, F,     \
+#define KES_CALL(NBV, M, P, R)                                                                             \
+  blk_impl<T, NBV, M, P, R>(grid, 256, st, first, last, A, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, F,  \
                          ahi, alo, Lp1, step, cpt, flag)
-#define X(ID, M, P)                         \
-  case ID:                                  \
-    if (NB == 2) KES_CALL(2, M, P);         \
-    else if (NB == 4) KES_CALL(4, M, P);    \
-    else KES_CALL(8, M, P);                 \
+#define X(ID, M, P, R)                         \
+  case ID:                                     \
+    if (NB == 2) KES_CALL(2, M, P, R);         \
+    else if (NB == 4) KES_CALL(4, M, P, R);    \
+    else KES_CALL(8, M, P, R);                 \
     break;
   switch (cfg.variant_blk) {
     KES_BLK_VARIANTS(X)
@@ -338,10 +376,10 @@ void stage4_dispatch(const SellDev& A, int n_sm, cudaStream_t st, int NB, const 
   else k_stage4<T, 8><<<grid, 256, 0, st>>>(A, x, v);
 }
 
-template <typename T, int NB, int M, bool P>
+template <typename T, int NB, int M, bool P, int R>
 int occ_one(int block) {
   int nb = 0;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_blk<T, NB, false, false, M, P>, block, 0) ==
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_blk<T, NB, false, false, M, P, R>, block, 0) ==
                  cudaSuccess
              ? nb
              : 0;
@@ -402,7 +440,7 @@ int elem_grid(int64_t count) {
 
 int blk_variant_count() {
   int n = 0;
-#define X(ID, M, P) ++n;
+#define X(ID, M, P, R) ++n;
   KES_BLK_VARIANTS(X)
 #undef X
   return n;
@@ -410,12 +448,12 @@ int blk_variant_count() {
 
 int blk_blocks_per_sm(bool fp32, int NB, int variant, int block) {
   int nb = 0;
-#define X(ID, M, P)                                                                                     \
-  case ID:                                                                                              \
-    if (fp32) nb = NB == 2 ? occ_one<float, 2, M, P>(block) : NB == 4 ? occ_one<float, 4, M, P>(block)   \
-                                                                      : occ_one<float, 8, M, P>(block);  \
-    else nb = NB == 2 ? occ_one<double, 2, M, P>(block) : NB == 4 ? occ_one<double, 4, M, P>(block)      \
-                                                                  : occ_one<double, 8, M, P>(block);     \
+#define X(ID, M, P, R)                                                                                        \
+  case ID:                                                                                                    \
+    if (fp32) nb = NB == 2 ? occ_one<float, 2, M, P, R>(block) : NB == 4 ? occ_one<float, 4, M, P, R>(block)   \
+                                                                         : occ_one<float, 8, M, P, R>(block);  \
+    else nb = NB == 2 ? occ_one<double, 2, M, P, R>(block) : NB == 4 ? occ_one<double, 4, M, P, R>(block)      \
+                                                                     : occ_one<double, 8, M, P, R>(block);     \
     break;
   switch (variant) {
     KES_BLK_VARIANTS(X)

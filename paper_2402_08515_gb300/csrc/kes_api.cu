@@ -676,6 +676,7 @@ kes_status create_impl(kes_ctx** out, int32_t nm, const int64_t* n, const int64_
     if (c->opts.block_b > 8) throw KesError{KES_ERR_UNSUPPORTED};
     if ((c->opts.dev_alloc == nullptr) != (c->opts.dev_free == nullptr)) throw KesError{KES_ERR_ARG};
     if (c->opts.step_variant < 0 || c->opts.step_variant >= step_variant_count()) throw KesError{KES_ERR_ARG};
+    if (c->opts.blk_variant < 0 || c->opts.blk_variant >= blk_variant_count()) throw KesError{KES_ERR_ARG};
     if (c->opts.stepper != KES_STEPPER_LEAPFROG && c->opts.stepper != KES_STEPPER_LEAPFROG4)
       throw KesError{KES_ERR_ARG};
     // host-side validation first: a bad input never reaches the GPU
@@ -713,8 +714,9 @@ kes_status create_impl(kes_ctx** out, int32_t nm, const int64_t* n, const int64_
     c->cfg.n_sm = n_sm;
     c->cfg.block_step = 256;
     if (!select_variant(c, c->opts.step_variant)) throw KesError{KES_ERR_UNSUPPORTED};
-    c->cfg.variant_blk = 0;
-    c->cfg.grid_blk = n_sm * blk_blocks_per_sm(fp32, c->NBcap > 1 ? c->NBcap : 2, 0, c->cfg.block_step);
+    c->cfg.variant_blk = c->opts.blk_variant;
+    c->cfg.grid_blk =
+        n_sm * blk_blocks_per_sm(fp32, c->NBcap > 1 ? c->NBcap : 2, c->opts.blk_variant, c->cfg.block_step);
     if (c->opts.autotune) tune_steps(c);
     c->sync();
     c->stats.bytes_per_step = kes_step_bytes(c, 1, 1);
@@ -1360,6 +1362,11 @@ int32_t kes_mesh_count(const kes_ctx* ctx) { return ctx ? ctx->n_mesh() : -1; }
 kes_status kes_sync(kes_ctx* ctx) {
   if (!ctx) return KES_ERR_ARG;
   return guarded([&]() -> kes_status { return check_flag(ctx); });
+}
+
+void kes_launch_shapes(int32_t* n_step, int32_t* n_block) {
+  if (n_step) *n_step = step_variant_count();
+  if (n_block) *n_block = blk_variant_count();
 }
 
 int64_t kes_step_bytes(const kes_ctx* c, int32_t b, int32_t F) {

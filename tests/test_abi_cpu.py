@@ -152,3 +152,8 @@ def test_struct_layouts_match_the_header(tmp_path):
         py = structs[cname]
         got = ctypes.sizeof(py) if what == "size" else getattr(py, what).offset
         assert got == int(val), (cname, what, got, val)
+
+
+def test_launch_shape_counts():
+    n_step, n_block = K.kes_launch_shapes()
+    assert n_step >= 8 and n_block >= 4

@@ -59,6 +59,28 @@ def test_block_columns_equal_single_vector_runs(meshes):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("b", [2, 4, 8])
+def test_every_block_launch_shape_rounds_identically(meshes, precision, b):
+    # lane-per-row and two-lanes-per-row shapes, with and without L2 prefetch: every
+    # column is the same FMA chain, so the filtered blocks agree bit for bit
+    p = meshes[2]
+    tau = _tau(p)
+    R = start_vectors(p.n, b, 31)
+    outs = []
+    for v in range(K.kes_launch_shapes()[1]):
+        with K.Context(p, precision=precision, block_b=b, blk_variant=v) as c:
+            K.kes_set_filters(c.handle, [8.0, 14.0], [12.0, 18.0], tau, 30)
+            o = np.zeros((2, b, p.n))
+            K.kes_filter_apply(c.handle, R, o, b)
+            cols = np.zeros((b, p.n))
+            K.kes_filter_apply_columns(c.handle, R, cols, b)
+            outs.append((o, cols))
+    for o, cols in outs[1:]:
+        np.testing.assert_array_equal(o, outs[0][0])
+        np.testing.assert_array_equal(cols, outs[0][1])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_batched_meshes_filter_matches_oracle(meshes, precision):
     taus = np.array([_tau(p) for p in meshes])
     L = 70
