@@ -410,7 +410,8 @@ def run_kes(args):
         "solve": {"accepted_pairs": [x["n_pairs"] for x in res] if batch else res[0]["n_pairs"],
                   "k_used": res[0]["k_used"], "time_steps": steps_per_solve,
                   "max_rel_res": max((float(x["rel_res"].max()) for x in res if x["n_pairs"]), default=None),
-                  "max_eig_rel_err_vs_exact": eig_err, "filter_ms_share": stats["filter_ms"] / ms_local},
+                  "max_eig_rel_err_vs_exact": eig_err, "filter_ms_share": stats["filter_ms"] / ms_local,
+                  "other_kernels_ms_share": stats["solve_other_ms"] / ms_local},
     }
     if multi:
         line["filter_multi_interval"] = multi
@@ -461,10 +462,11 @@ def run_reference(args):
 
 
 TTS_FORMS = (
-    # name, precision, block width, FP64 refinement sweeps
-    ("fp64", "fp64", 1, 0),
-    ("fp32+refine1", "fp32", 1, 1),
-    ("fp32+refine2", "fp32", 1, 2),
+    # name, precision, block width, FP64 refinement sweeps, refinement filter length / L
+    ("fp64", "fp64", 1, 0, 1.0),
+    ("fp32+refine1", "fp32", 1, 1, 1.0),
+    ("fp32+refine1_L/4", "fp32", 1, 1, 0.25),
+    ("fp32+refine1_L/8", "fp32", 1, 1, 0.125),
 )
 TTS_KMAX = (160, 200, 240, 280, 320, 360, 400)   # coarse sweep; then steps of 10 below the first success
 
@@ -477,7 +479,7 @@ def run_tts(args):
     run's time and the distinct eigenvalues it accepted; a form's time to solution is
     that of the smallest kmax (to within 10) that accepts every distinct eigenvalue.
     The FP32 forms reach 1e-8 through FP64 refinement sweeps on their in-interval Ritz
-    vectors, filtered 8 at a time."""
+    vectors, filtered 8 at a time, with the full filter or its first L/4 or L/8 steps."""
     import numpy as np
     import torch
 
@@ -495,7 +497,7 @@ def run_tts(args):
         distinct, _ = spectra.cluster(exact)
         v0 = start_vectors(p.n, 1, wl.seed)[0]
         runs, summary = [], {}
-        for name, prec, b, refine in forms:
+        for name, prec, b, refine, frac in forms:
             summary[name] = None
             with K.Context(p, precision=prec, block_b=8) as c:
                 w, _ = K.kes_estimate_omega_max(c.handle, wl.power_iters, v0)
@@ -505,13 +507,15 @@ def run_tts(args):
                 def run(kmax):
                     so = K.kes_solve_opts_default()
                     so.kmax, so.tol, so.check_every, so.refine_sweeps = kmax, tol, kmax, refine
+                    so.refine_L = int(round(frac * wl.L)) if frac < 1.0 else 0
                     torch.cuda.synchronize()
                     t0 = time.perf_counter()
                     res = K.kes_block_krylov_solve(c.handle, R, b, so)[0]
                     dt = time.perf_counter() - t0
                     found, _ = spectra.cluster(res["omega2"])
                     err = max((float(np.min(np.abs(exact - t)) / t) for t in res["omega2"]), default=None)
-                    runs.append({"form": name, "b": b, "kmax": kmax, "refine_sweeps": refine, "seconds": dt,
+                    runs.append({"form": name, "b": b, "kmax": kmax, "refine_sweeps": refine,
+                                 "refine_L": so.refine_L or wl.L, "seconds": dt,
                                  "accepted_pairs": res["n_pairs"], "accepted_distinct": len(found),
                                  "max_rel_res": float(res["rel_res"].max()) if res["n_pairs"] else None,
                                  "max_eig_rel_err_vs_exact": err, "leapfrog_steps": res["time_steps"],

@@ -97,7 +97,9 @@ typedef struct kes_solve_opts {
   int32_t refine_sweeps; /* after the Krylov phase: sweeps of FP64 filtered subspace iteration on the
                             in-interval Ritz vectors (X <- C X with the FP64 step kernels, then
                             Rayleigh-Ritz); lifts FP32-form pairs to FP64 residuals. 0: none */
-  int32_t reserved;      /* set to 0 */
+  int32_t refine_L;      /* leapfrog steps of the refinement filter: the first refine_L + 1 weights of the
+                            installed tables, i.e. the same interval with end time refine_L * tau
+                            (eq. weightf does not depend on T); 0 or >= L: L */
 } kes_solve_opts;
 
 /* Result of kes_krylov_solve; host memory owned by the library. */

@@ -65,7 +65,7 @@ class KesOpts(C.Structure):
 class KesSolveOpts(C.Structure):
     _fields_ = [("kmax", C.c_int32), ("check_every", C.c_int32), ("n_wanted", C.c_int32),
                 ("want_vectors", C.c_int32), ("tol", C.c_double), ("refine_sweeps", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("refine_L", C.c_int32)]
 
 
 class KesResult(C.Structure):

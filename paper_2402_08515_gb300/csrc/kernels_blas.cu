@@ -204,7 +204,124 @@ int rows_grid(int64_t n, int cap) {
   return static_cast<int>(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
+// The batched kernels: blockIdx.z (or .y) picks the job; a job with fewer row blocks or
+// columns than the grid leaves the extra blocks idle (a block-uniform early return,
+// before any barrier). Each job strides its rows by its own nblk, as its single launch does.
+__global__ void __launch_bounds__(kThreads) k_mdot_jobs(const DotJob* __restrict__ jobs,
+                                                        double* __restrict__ partial) {
+  const DotJob jb = jobs[blockIdx.z];
+  const int j0 = blockIdx.y * kGroup;
+  if (static_cast<int>(blockIdx.x) >= jb.nblk || j0 >= jb.k) return;
+  double acc[kGroup];
+#pragma unroll
+  for (int g = 0; g < kGroup; ++g) acc[g] = 0.0;
+  const int ng = min(kGroup, jb.k - j0);
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; i < jb.n;
+       i += static_cast<int64_t>(jb.nblk) * kThreads) {
+    const double wv = jb.w ? jb.w[i] * jb.v[i] : jb.v[i];
+#pragma unroll
+    for (int g = 0; g < kGroup; ++g)
+      if (g < ng) acc[g] = fma(jb.B[(j0 + g) * jb.ldb + i], wv, acc[g]);
+  }
+  double tot[kGroup];
+  block_sum<kGroup>(acc, tot);
+  if (threadIdx.x == 0)
+    for (int g = 0; g < ng; ++g) partial[jb.poff + static_cast<int64_t>(j0 + g) * jb.nblk + blockIdx.x] = tot[g];
+}
+
+__global__ void __launch_bounds__(kThreads) k_reduce_jobs(const DotJob* __restrict__ jobs,
+                                                          const double* __restrict__ partial) {
+  const DotJob jb = jobs[blockIdx.y];
+  const int j = blockIdx.x;
+  if (j >= jb.k) return;
+  double v[1] = {0.0};
+  for (int b = threadIdx.x; b < jb.nblk; b += kThreads) v[0] += partial[jb.poff + static_cast<int64_t>(j) * jb.nblk + b];
+  double tot[1];
+  block_sum<1>(v, tot);
+  if (threadIdx.x == 0) jb.out[j] = tot[0];
+}
+
+__global__ void __launch_bounds__(kThreads) k_gemv_sub_jobs(const GemvJob* __restrict__ jobs) {
+  extern __shared__ double sh_h[];
+  const GemvJob jb = jobs[blockIdx.y];
+  if (static_cast<int>(blockIdx.x) >= jb.nblk) return;
+  for (int j = threadIdx.x; j < jb.k; j += kThreads) sh_h[j] = jb.h[j];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; i < jb.n;
+       i += static_cast<int64_t>(jb.nblk) * kThreads) {
+    double s0 = 0.0, s1 = 0.0;
+    int j = 0;
+    for (; j + 2 <= jb.k; j += 2) {
+      s0 = fma(jb.B[j * jb.ldb + i], sh_h[j], s0);
+      s1 = fma(jb.B[(j + 1) * jb.ldb + i], sh_h[j + 1], s1);
+    }
+    if (j < jb.k) s0 = fma(jb.B[j * jb.ldb + i], sh_h[j], s0);
+    jb.v[i] -= s0 + s1;
+  }
+}
+
+// S x over every SELL slice, each mesh with its own vectors x_of[mesh] / y_of[mesh] (global
+// row indexing; a null x_of skips the mesh's rows). Each row sum is one FMA chain from 0 in
+// entry order, the sum the step kernels' SpMV forms, so it equals the per-mesh product.
+__global__ void __launch_bounds__(kThreads) k_spmv_f64_meshes(SellDev A, const double* const* __restrict__ x_of,
+                                                              double* const* __restrict__ y_of) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t s = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; s < A.n_slices;
+       s += nwarps) {
+    const int mesh = A.slice_mesh ? A.slice_mesh[s] : 0;
+    const double* x = x_of[mesh];
+    if (!x) continue;  // warp-uniform: a slice belongs to one mesh
+    const int64_t beg = A.slice_ptr[s];
+    const int w = static_cast<int>((A.slice_ptr[s + 1] - beg) >> 5);
+    const double* v = A.val64 + beg + lane;
+    const int32_t* c = A.col + beg + lane;
+    double acc = 0.0;
+    for (int k = 0; k < w; ++k) acc = fma(__ldcs(v + k * kSliceC), __ldg(x + __ldcs(c + k * kSliceC)), acc);
+    y_of[mesh][s * kSliceC + lane] = acc;
+  }
+}
+
+__global__ void k_scale_jobs(const ScaleJob* __restrict__ jobs) {
+  const ScaleJob jb = jobs[blockIdx.y];
+  const double nrm = sqrt(jb.nrm2[0]);
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < jb.n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    jb.dst[i] = jb.v[i] / nrm;
+}
+
 }  // namespace
+
+int dot_blocks(int64_t n) { return rows_grid(n, kDotBlocks); }
+int gemv_blocks(int64_t n) { return rows_grid(n, 2048); }
+
+void launch_mdot_jobs(cudaStream_t st, const DotJob* jobs, int njobs, int max_k, int max_nblk, double* partial) {
+  if (njobs <= 0 || max_k <= 0) return;
+  dim3 grid(max_nblk, (max_k + kGroup - 1) / kGroup, njobs);
+  k_mdot_jobs<<<grid, kThreads, 0, st>>>(jobs, partial);
+  k_reduce_jobs<<<dim3(max_k, njobs), kThreads, 0, st>>>(jobs, partial);
+  g_launches += 2;
+}
+
+void launch_gemv_sub_jobs(cudaStream_t st, const GemvJob* jobs, int njobs, int max_k, int max_nblk) {
+  if (njobs <= 0 || max_k <= 0) return;
+  k_gemv_sub_jobs<<<dim3(max_nblk, njobs), kThreads, max_k * sizeof(double), st>>>(jobs);
+  ++g_launches;
+}
+
+void launch_spmv_f64_meshes(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, const double* const* x_of,
+                            double* const* y_of) {
+  const int64_t need = (A.n_slices + 7) / 8;  // 8 warps per block, a slice per warp
+  const int64_t cap = static_cast<int64_t>(cfg.n_sm) * 8;
+  k_spmv_f64_meshes<<<static_cast<int>(need < cap ? (need > 0 ? need : 1) : cap), kThreads, 0, st>>>(A, x_of, y_of);
+  ++g_launches;
+}
+
+void launch_scale_jobs(cudaStream_t st, const ScaleJob* jobs, int njobs, int max_nblk) {
+  if (njobs <= 0) return;
+  k_scale_jobs<<<dim3(max_nblk, njobs), kThreads, 0, st>>>(jobs);
+  ++g_launches;
+}
 
 void launch_mdot(cudaStream_t st, const double* B, int64_t ldb, int k, const double* v, const double* w,
                  int64_t n, double* partial, double* h) {

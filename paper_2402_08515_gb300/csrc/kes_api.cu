@@ -10,12 +10,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <limits>
 #include <new>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -79,6 +81,7 @@ struct GraphEntry {
   int NB = 0;
   bool fp64 = true;
   int cpt = 0;
+  int steps = 0;
   cudaGraphExec_t exec = nullptr;
   int64_t nodes = 0;
 };
@@ -144,6 +147,9 @@ struct kes_ctx {
   double* Hd = nullptr;  // (n_mesh * kF) x kcap x kcap; column k of process p holds b_i^T S b_k, i <= k
   double* partial = nullptr;
   double* scal = nullptr;  // per process: 2 * kcap + kScal device scalars
+  double* normd = nullptr; // per process: ||w||_M^2 before and after orthogonalisation
+  char* jobs = nullptr;    // job descriptors of the batched Gram-Schmidt stages
+  size_t jobs_bytes = 0;
   double* Yd = nullptr;
   double* thd = nullptr;
   double* Xd = nullptr;
@@ -267,13 +273,15 @@ void block_out(kes_ctx* c, const double* src, int NB, int nb, double* dst, int32
 // Largest stable tau * omega of the context's stepper.
 double cfl_bound(const kes_ctx* c) { return c->opts.stepper == KES_STEPPER_LEAPFROG4 ? 2.0 * std::sqrt(3.0) : 2.0; }
 
-// Issues the L fused steps of one filter application of an NB-column block on the
-// context stream: stage_in -> stage_out (cpt = 0: F filtered blocks, every column with
-// every weight table; cpt > 0: one block, column j with table min(j / cpt, F - 1)).
-int64_t issue_filter_steps(kes_ctx* c, int NB, bool fp64, int cpt) {
+// Issues the fused steps of one filter application of an NB-column block on the context
+// stream: stage_in -> stage_out (cpt = 0: F filtered blocks, every column with every
+// weight table; cpt > 0: one block, column j with table min(j / cpt, F - 1)). steps <= L
+// runs the first steps + 1 weights of the tables: alpha(t) of eq. (weightf) does not
+// depend on T, so that is the filter of end time steps * tau.
+int64_t issue_filter_steps(kes_ctx* c, int NB, bool fp64, int cpt, int steps) {
   const int64_t before = g_launches;
   const bool ho = c->opts.stepper == KES_STEPPER_LEAPFROG4;
-  const int L = c->L, F = c->F;
+  const int L = c->L, F = c->F;  // L: the tables' length (their stride is L + 1)
   const int64_t stride = c->n_pad * NB;
   if (fp64) {
     // in a context of the FP32 form the launch shape was tuned for the FP32 kernels:
@@ -284,8 +292,8 @@ int64_t issue_filter_steps(kes_ctx* c, int NB, bool fp64, int cpt) {
       cfg.variant = 3;
       cfg.grid_step = cfg.n_sm * step_blocks_per_sm(false, 3, cfg.block_step);
     }
-    for (int s = 0; s < L; ++s) {
-      const bool first = s == 0, last = s == L - 1;
+    for (int s = 0; s < steps; ++s) {
+      const bool first = s == 0, last = s == steps - 1;
       const double* x = s == 0 ? c->stage_in : c->U64[(s - 1) & 1];
       const double* prev = s <= 1 ? c->stage_in : c->U64[s & 1];
       double* out = c->U64[s & 1];
@@ -304,8 +312,8 @@ int64_t issue_filter_steps(kes_ctx* c, int NB, bool fp64, int cpt) {
   } else {
     const SellDev A32 = c->step_A32();
     launch_init_f32(c->stream, c->A, NB, c->stage_in, c->U32[2], c->acc_s, c->acc_c, stride, F, c->alpha64, L, cpt);
-    for (int s = 0; s < L; ++s) {
-      const bool first = s == 0, last = s == L - 1;
+    for (int s = 0; s < steps; ++s) {
+      const bool first = s == 0, last = s == steps - 1;
       const float* x = s == 0 ? c->U32[2] : c->U32[(s - 1) & 1];
       const float* prev = s <= 1 ? c->U32[2] : c->U32[s & 1];
       float* out = c->U32[s & 1];
@@ -336,8 +344,9 @@ void ensure_fp64_state(kes_ctx* c) {
   }
 }
 
-void run_filter(kes_ctx* c, int NB, bool fp64, int cpt = 0) {
+void run_filter(kes_ctx* c, int NB, bool fp64, int cpt = 0, int steps = 0) {
   if (cpt > 0 && NB < 2) throw KesError{KES_ERR_ARG};  // per-column tables live in the block kernels
+  if (steps <= 0 || steps > c->L) steps = c->L;
   if (fp64) ensure_fp64_state(c);
   if (c->opts.stepper == KES_STEPPER_LEAPFROG4) {  // stage buffers before any graph captures them
     if (fp64 && !c->V64) c->V64 = c->dzero_n<double>(c->n_pad * c->NBcap);
@@ -353,11 +362,11 @@ void run_filter(kes_ctx* c, int NB, bool fp64, int cpt = 0) {
     }
     GraphEntry* ge = nullptr;
     for (auto& g : c->graphs)
-      if (g.NB == NB && g.fp64 == fp64 && g.cpt == cpt) ge = &g;
+      if (g.NB == NB && g.fp64 == fp64 && g.cpt == cpt && g.steps == steps) ge = &g;
     if (!ge) {
       cudaGraph_t graph;
       KES_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-      const int64_t nodes = issue_filter_steps(c, NB, fp64, cpt);
+      const int64_t nodes = issue_filter_steps(c, NB, fp64, cpt, steps);
       cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
       g_launches -= nodes;  // captured, not launched
       KES_CUDA(ce);
@@ -365,6 +374,7 @@ void run_filter(kes_ctx* c, int NB, bool fp64, int cpt = 0) {
       g.NB = NB;
       g.fp64 = fp64;
       g.cpt = cpt;
+      g.steps = steps;
       g.nodes = nodes;
       ce = cudaGraphInstantiate(&g.exec, graph, 0);
       cudaGraphDestroy(graph);
@@ -375,13 +385,13 @@ void run_filter(kes_ctx* c, int NB, bool fp64, int cpt = 0) {
     KES_CUDA(cudaGraphLaunch(ge->exec, c->stream));
     g_launches += ge->nodes;  // every node of the replayed graph is a kernel launch
   } else {
-    issue_filter_steps(c, NB, fp64, cpt);
+    issue_filter_steps(c, NB, fp64, cpt, steps);
     KES_CHECK_LAUNCH();
   }
   KES_CUDA(cudaEventRecord(e1, c->stream));
   c->ev_filter.emplace_back(e0, e1);
   c->stats.filter_calls += 1;
-  c->stats.filter_steps += c->L;
+  c->stats.filter_steps += steps;
 }
 
 void ensure_stage_out(kes_ctx* c, int F) {
@@ -414,7 +424,8 @@ kes_status check_flag(kes_ctx* c) {
 // A process is the Krylov iteration of one mesh on one interval (p = mesh * F + f).
 void ensure_krylov(kes_ctx* c, int kmax, int F) {
   if (c->kcap >= kmax && c->kF >= F) return;
-  for (double* p : {c->B, c->SB, c->Hd, c->partial, c->scal, c->Yd, c->thd}) c->dfree(p);
+  for (double* p : {c->B, c->SB, c->Hd, c->partial, c->scal, c->Yd, c->thd, c->normd}) c->dfree(p);
+  c->dfree(c->jobs);
   kmax = std::max(kmax, c->kcap);
   F = std::max(F, c->kF);
   const int64_t nproc = static_cast<int64_t>(c->n_mesh()) * F;
@@ -423,10 +434,16 @@ void ensure_krylov(kes_ctx* c, int kmax, int F) {
   c->B = c->dzero_n<double>(static_cast<int64_t>(F) * kmax * c->n_pad);
   c->SB = c->dzero_n<double>(static_cast<int64_t>(F) * kmax * c->n_pad);
   c->Hd = c->dzero_n<double>(nproc * kmax * kmax);
-  c->partial = c->dalloc_n<double>(static_cast<int64_t>(kDotBlocks) * (2 * kmax + 8));
+  // partial sums: every process's inner products of one batched stage at once
+  c->partial = c->dalloc_n<double>(nproc * kDotBlocks * (2 * kmax + 8));
+  c->normd = c->dzero_n<double>(2 * nproc);
+  // job descriptors of the batched Gram-Schmidt stages (see append_column)
+  c->jobs_bytes = static_cast<size_t>(nproc) * (4 * sizeof(DotJob) + sizeof(GemvJob) + sizeof(ScaleJob)) +
+                  static_cast<size_t>(2 * F * c->n_mesh()) * sizeof(double*) + 256;
+  c->jobs = static_cast<char*>(c->dalloc(c->jobs_bytes));
   c->scal = c->dzero_n<double>(nproc * (2 * kmax + kScal));
-  c->Yd = c->dalloc_n<double>(static_cast<int64_t>(kmax) * kmax);
-  c->thd = c->dalloc_n<double>(kmax);
+  c->Yd = c->dalloc_n<double>(nproc * kmax * kmax);  // every process's selected Ritz vectors at once
+  c->thd = c->dalloc_n<double>(nproc * kmax);
 }
 
 // Device scalars of process p (of mesh p outside the solver).
@@ -928,28 +945,62 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
     // that are not dependent (Algorithm 2.5).
     std::vector<char> want(P, 1);  // processes taking part in the current block step
     auto append_column = [&](int jj) {
-      std::vector<char> active(P, 0), added(P, 0);
-      cudaEvent_t ev = other_begin();
+      std::vector<char> added(P, 0);
+      std::vector<int> act;  // processes that take column jj
       for (int j = 0; j < nm; ++j) {
         const int p = owner(j, jj);
         if (p < 0 || !want[p] || ms[p].done || ms[p].k >= kmax) continue;
-        active[p] = 1;
-        const MeshInfo& mi = c->meshes[j];
+        act.push_back(p);
+      }
+      if (act.empty()) return added;
+      const int na = static_cast<int>(act.size());
+      // phase 1, one launch per stage for all of them: ||w||_M^2, two passes of
+      // h = B^T M w and w -= B h, ||w||_M^2 again
+      std::vector<DotJob> nb_jobs(na), na_jobs(na), h_jobs;
+      std::vector<GemvJob> g_jobs;
+      int max_k = 0, max_nblk = 1, max_gblk = 1;
+      int64_t poff = 0, poff_h = 0;
+      for (int i = 0; i < na; ++i) {
+        const int p = act[i];
+        const MeshInfo& mi = mesh_of(p);
         double* w = c->Wc + static_cast<int64_t>(jj) * np + mi.row_off;
         const double* mj = c->m64 + mi.row_off;
-        double* sc = proc_scal(c, p);
-        launch_mdot(s, w, 0, 1, w, mj, mi.n_pad, c->partial, sc);  // ||w||_M^2 before
-        for (int pass = 0; pass < 2 && ms[p].k > 0; ++pass) {
-          launch_mdot(s, Bp(p), np, ms[p].k, w, mj, mi.n_pad, c->partial, sc + kScal);  // h = B^T M w
-          launch_gemv_sub(s, w, Bp(p), np, ms[p].k, sc + kScal, mi.n_pad);             // w -= B h
+        const int nblk = dot_blocks(mi.n_pad), gblk = gemv_blocks(mi.n_pad);
+        max_nblk = std::max(max_nblk, nblk);
+        max_gblk = std::max(max_gblk, gblk);
+        nb_jobs[i] = DotJob{w, w, mj, c->normd + 2 * p, mi.n_pad, 0, poff, 1, nblk};
+        na_jobs[i] = DotJob{w, w, mj, c->normd + 2 * p + 1, mi.n_pad, 0, poff, 1, nblk};
+        poff += nblk;
+        const int k = ms[p].k;
+        if (k > 0) {
+          h_jobs.push_back(DotJob{Bp(p), w, mj, proc_scal(c, p) + kScal, mi.n_pad, np, poff_h, k, nblk});
+          g_jobs.push_back(GemvJob{w, Bp(p), proc_scal(c, p) + kScal, mi.n_pad, np, k, gblk});
+          poff_h += static_cast<int64_t>(k) * nblk;
+          max_k = std::max(max_k, k);
         }
-        launch_mdot(s, w, 0, 1, w, mj, mi.n_pad, c->partial, sc + 1);  // ||w||_M^2 after
       }
+      const int nh = static_cast<int>(h_jobs.size());
+      char* jb = c->jobs;
+      DotJob* d_nb = reinterpret_cast<DotJob*>(jb);
+      DotJob* d_na = d_nb + P;
+      DotJob* d_h = d_na + P;
+      GemvJob* d_g = reinterpret_cast<GemvJob*>(d_h + P);
+      cudaEvent_t ev = other_begin();
+      KES_CUDA(cudaMemcpyAsync(d_nb, nb_jobs.data(), na * sizeof(DotJob), cudaMemcpyHostToDevice, s));
+      KES_CUDA(cudaMemcpyAsync(d_na, na_jobs.data(), na * sizeof(DotJob), cudaMemcpyHostToDevice, s));
+      if (nh > 0) {
+        KES_CUDA(cudaMemcpyAsync(d_h, h_jobs.data(), nh * sizeof(DotJob), cudaMemcpyHostToDevice, s));
+        KES_CUDA(cudaMemcpyAsync(d_g, g_jobs.data(), nh * sizeof(GemvJob), cudaMemcpyHostToDevice, s));
+      }
+      launch_mdot_jobs(s, d_nb, na, 1, max_nblk, c->partial);  // ||w||_M^2 before
+      for (int pass = 0; pass < 2 && nh > 0; ++pass) {
+        launch_mdot_jobs(s, d_h, nh, max_k, max_nblk, c->partial);  // h = B^T M w
+        launch_gemv_sub_jobs(s, d_g, nh, max_k, max_gblk);          // w -= B h
+      }
+      launch_mdot_jobs(s, d_na, na, 1, max_nblk, c->partial);  // ||w||_M^2 after
       KES_CHECK_LAUNCH();
       std::vector<double> nrm(2 * P, 0.0);
-      for (int p = 0; p < P; ++p)
-        if (active[p])
-          KES_CUDA(cudaMemcpyAsync(&nrm[2 * p], proc_scal(c, p), 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      KES_CUDA(cudaMemcpyAsync(nrm.data(), c->normd, 2 * P * sizeof(double), cudaMemcpyDeviceToHost, s));
       int flag = 0;
       KES_CUDA(cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
       other_end(ev);
@@ -958,22 +1009,55 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
         KES_CUDA(cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
         throw KesError{(flag & 2) ? KES_ERR_TIMEOUT : KES_ERR_UNSTABLE};
       }
-      ev = other_begin();
-      for (int p = 0; p < P; ++p) {
-        if (!active[p]) continue;
+      // phase 2 for the vectors that are not dependent: b_k = w / ||w||_M, S b_k (one
+      // launch per interval over all meshes), the new column b_i^T S b_k of H
+      std::vector<ScaleJob> s_jobs;
+      std::vector<DotJob> c_jobs;
+      std::vector<const double*> x_of(static_cast<size_t>(F) * nm, nullptr);
+      std::vector<double*> y_of(static_cast<size_t>(F) * nm, nullptr);
+      int max_k1 = 0, max_sblk = 1;
+      poff = 0;
+      for (int i = 0; i < na; ++i) {
+        const int p = act[i];
         if (!(std::sqrt(nrm[2 * p + 1]) > 1e-10 * std::sqrt(nrm[2 * p]))) continue;  // dependent vector
         const MeshInfo& mi = mesh_of(p);
         const int k = ms[p].k;
         double* w = c->Wc + static_cast<int64_t>(jj) * np + mi.row_off;
         double* sbk = SBp(p) + k * np;
-        launch_scale_rsqrt(s, w, proc_scal(c, p) + 1, Bp(p) + k * np, nullptr, mi.n_pad);  // b_k
-        launch_spmv_f64(mesh_sell(c, mi), c->cfg, s, Bfull(p) + k * np, nullptr, sbk);    // S b_k
-        launch_mdot(s, Bp(p), np, k + 1, sbk, nullptr, mi.n_pad, c->partial, Hcol(p, k));
+        const int nblk = dot_blocks(mi.n_pad);
+        s_jobs.push_back(ScaleJob{w, c->normd + 2 * p + 1, Bp(p) + k * np, mi.n_pad});
+        max_sblk = std::max(max_sblk, gemv_blocks(mi.n_pad));
+        x_of[static_cast<size_t>(p % F) * nm + p / F] = Bfull(p) + k * np;
+        y_of[static_cast<size_t>(p % F) * nm + p / F] = c->SB + (p % F) * kc * np + k * np;
+        c_jobs.push_back(DotJob{Bp(p), sbk, nullptr, Hcol(p, k), mi.n_pad, np, poff, k + 1, nblk});
+        poff += static_cast<int64_t>(k + 1) * nblk;
+        max_k1 = std::max(max_k1, k + 1);
         ms[p].k = k + 1;
         added[p] = 1;
       }
-      KES_CHECK_LAUNCH();
-      other_end(ev);
+      const int ns = static_cast<int>(s_jobs.size());
+      if (ns > 0) {
+        ev = other_begin();
+        ScaleJob* d_s = reinterpret_cast<ScaleJob*>(d_g + P);
+        DotJob* d_c = reinterpret_cast<DotJob*>(d_s + P);
+        char* ptrs = reinterpret_cast<char*>(d_c + P);  // x_of, then y_of, F * nm pointers each
+        const double** d_x = reinterpret_cast<const double**>(ptrs);
+        double** d_y = reinterpret_cast<double**>(ptrs + static_cast<size_t>(F) * nm * sizeof(double*));
+        KES_CUDA(cudaMemcpyAsync(d_s, s_jobs.data(), ns * sizeof(ScaleJob), cudaMemcpyHostToDevice, s));
+        KES_CUDA(cudaMemcpyAsync(d_c, c_jobs.data(), ns * sizeof(DotJob), cudaMemcpyHostToDevice, s));
+        KES_CUDA(cudaMemcpyAsync(d_x, x_of.data(), x_of.size() * sizeof(double*), cudaMemcpyHostToDevice, s));
+        KES_CUDA(cudaMemcpyAsync(d_y, y_of.data(), y_of.size() * sizeof(double*), cudaMemcpyHostToDevice, s));
+        launch_scale_jobs(s, d_s, ns, max_sblk);
+        for (int f = 0; f < F; ++f) {
+          bool any = false;
+          for (int j = 0; j < nm; ++j) any |= x_of[static_cast<size_t>(f) * nm + j] != nullptr;
+          if (any) launch_spmv_f64_meshes(c->A, c->cfg, s, d_x + static_cast<size_t>(f) * nm,
+                                          d_y + static_cast<size_t>(f) * nm);
+        }
+        launch_mdot_jobs(s, d_c, ns, max_k1, max_nblk, c->partial);
+        KES_CHECK_LAUNCH();
+        other_end(ev);
+      }
       return added;
     };
 
@@ -994,54 +1078,104 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
       for (double& t : theta) t = std::max(t, 0.0);
     };
 
-    auto project = [&](int p) {
-      MeshSolve& m = ms[p];
-      const MeshInfo& mi = mesh_of(p);
-      const int kk = m.k;
-      m.kproj = kk;
-      std::vector<double> theta, Y;
-      projected_eig(p, theta, Y);
-      const double wmin = mi.wmin[p % F], wmax = mi.wmax[p % F];
-      std::vector<int> inside;
-      for (int q = 0; q < kk; ++q) {
-        const double om = std::sqrt(theta[q]);
-        if (om >= wmin && om <= wmax) inside.push_back(q);
+    // Rayleigh-Ritz (eq. projevp) and the residual acceptance (eq. res) of several
+    // processes at once: their projected matrices come back with one synchronisation,
+    // the small eigenproblems are solved on host threads, and the residual kernels run
+    // back to back before one more synchronisation.
+    auto project_many = [&](const std::vector<int>& ps) {
+      const int np_ = static_cast<int>(ps.size());
+      if (np_ == 0) return;
+      std::vector<std::vector<double>> Hs(np_), th(np_), Ys(np_);
+      for (int i = 0; i < np_; ++i) {
+        const int kk = ms[ps[i]].k;
+        Hs[i].assign(static_cast<size_t>(kk) * kk, 0.0);
+        if (kk > 0)
+          KES_CUDA(cudaMemcpy2DAsync(Hs[i].data(), kk * sizeof(double), Hcol(ps[i], 0), kc * sizeof(double),
+                                     kk * sizeof(double), kk, cudaMemcpyDeviceToHost, s));
       }
-      const int np_in = static_cast<int>(inside.size());
-      m.last_theta = theta;
-      m.last_rel.assign(kk, std::numeric_limits<double>::quiet_NaN());
-      m.acc_theta.clear();
-      m.acc_rel.clear();
-      m.acc_abs.clear();
-      m.acc_Y.clear();
-      if (np_in == 0) return;
-      std::vector<double> Ysel(static_cast<size_t>(kk) * np_in), thsel(np_in);
-      for (int q = 0; q < np_in; ++q) {
-        thsel[q] = theta[inside[q]];
-        std::memcpy(&Ysel[static_cast<size_t>(q) * kk], &Y[static_cast<size_t>(inside[q]) * kk], kk * sizeof(double));
-      }
+      c->sync();
+      std::atomic<int> next{0};
+      std::atomic<bool> failed{false};
+      auto worker = [&]() {
+        for (int i = next++; i < np_; i = next++) {
+          const int kk = ms[ps[i]].k;
+          std::vector<double>& H = Hs[i];
+          // column i holds rows 0..i (upper triangle); mirror it into the lower triangle
+          for (int a = 0; a < kk; ++a)
+            for (int r = a + 1; r < kk; ++r) H[static_cast<size_t>(a) * kk + r] = H[static_cast<size_t>(r) * kk + a];
+          th[i].assign(kk, 0.0);
+          Ys[i].assign(static_cast<size_t>(kk) * kk, 0.0);
+          if (!sym_eig(kk, H.data(), th[i].data(), Ys[i].data())) failed = true;
+          for (double& t : th[i]) t = std::max(t, 0.0);
+        }
+      };
+      const int hw = static_cast<int>(std::thread::hardware_concurrency());
+      const int nt = std::min(np_, std::max(1, std::min(hw, 16)));
+      std::vector<std::thread> pool;
+      for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+      worker();
+      for (auto& t : pool) t.join();
+      if (failed) throw KesError{KES_ERR_CUDA};
+      std::vector<std::vector<int>> inside(np_);
+      std::vector<std::vector<double>> Ysel(np_), thsel(np_), rr(np_);
       cudaEvent_t ev = other_begin();
-      double* sc = proc_scal(c, p);
-      KES_CUDA(cudaMemcpyAsync(c->Yd, Ysel.data(), Ysel.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-      KES_CUDA(cudaMemcpyAsync(c->thd, thsel.data(), np_in * sizeof(double), cudaMemcpyHostToDevice, s));
-      launch_ritz_residual(s, Bp(p), SBp(p), np, kk, c->Yd, c->thd, np_in, c->m64 + mi.row_off, mi.n_pad,
-                           c->partial, sc + kScal);
-      KES_CHECK_LAUNCH();
-      std::vector<double> rr(2 * np_in);
-      KES_CUDA(cudaMemcpyAsync(rr.data(), sc + kScal, 2 * np_in * sizeof(double), cudaMemcpyDeviceToHost, s));
+      int64_t yo = 0, to = 0;
+      for (int i = 0; i < np_; ++i) {
+        const int p = ps[i];
+        MeshSolve& m = ms[p];
+        const MeshInfo& mi = mesh_of(p);
+        const int kk = m.k;
+        m.kproj = kk;
+        const double wmin = mi.wmin[p % F], wmax = mi.wmax[p % F];
+        for (int q = 0; q < kk; ++q) {
+          const double om = std::sqrt(th[i][q]);
+          if (om >= wmin && om <= wmax) inside[i].push_back(q);
+        }
+        const int np_in = static_cast<int>(inside[i].size());
+        m.last_theta = th[i];
+        m.last_rel.assign(kk, std::numeric_limits<double>::quiet_NaN());
+        m.acc_theta.clear();
+        m.acc_rel.clear();
+        m.acc_abs.clear();
+        m.acc_Y.clear();
+        if (np_in == 0) continue;
+        Ysel[i].resize(static_cast<size_t>(kk) * np_in);
+        thsel[i].resize(np_in);
+        for (int q = 0; q < np_in; ++q) {
+          thsel[i][q] = th[i][inside[i][q]];
+          std::memcpy(&Ysel[i][static_cast<size_t>(q) * kk], &Ys[i][static_cast<size_t>(inside[i][q]) * kk],
+                      kk * sizeof(double));
+        }
+        KES_CUDA(cudaMemcpyAsync(c->Yd + yo, Ysel[i].data(), Ysel[i].size() * sizeof(double), cudaMemcpyHostToDevice,
+                                 s));
+        KES_CUDA(cudaMemcpyAsync(c->thd + to, thsel[i].data(), np_in * sizeof(double), cudaMemcpyHostToDevice, s));
+        double* sc = proc_scal(c, p);
+        launch_ritz_residual(s, Bp(p), SBp(p), np, kk, c->Yd + yo, c->thd + to, np_in, c->m64 + mi.row_off,
+                             mi.n_pad, c->partial, sc + kScal);
+        KES_CHECK_LAUNCH();
+        rr[i].resize(2 * np_in);
+        KES_CUDA(cudaMemcpyAsync(rr[i].data(), sc + kScal, 2 * np_in * sizeof(double), cudaMemcpyDeviceToHost, s));
+        yo += static_cast<int64_t>(kk) * np_in;
+        to += np_in;
+      }
       other_end(ev);
       c->sync();
-      for (int q = 0; q < np_in; ++q) {
-        const double a = std::sqrt(std::max(rr[q], 0.0));
-        const double den = thsel[q] * std::sqrt(std::max(rr[np_in + q], 0.0));
-        const double rel = den > 0.0 ? a / den : std::numeric_limits<double>::infinity();
-        m.last_rel[inside[q]] = rel;
-        if (rel <= so.tol) {
-          m.acc_theta.push_back(thsel[q]);
-          m.acc_rel.push_back(rel);
-          m.acc_abs.push_back(a);
-          m.acc_Y.insert(m.acc_Y.end(), Ysel.begin() + static_cast<size_t>(q) * kk,
-                         Ysel.begin() + static_cast<size_t>(q + 1) * kk);
+      for (int i = 0; i < np_; ++i) {
+        MeshSolve& m = ms[ps[i]];
+        const int kk = m.k;
+        const int np_in = static_cast<int>(inside[i].size());
+        for (int q = 0; q < np_in; ++q) {
+          const double a = std::sqrt(std::max(rr[i][q], 0.0));
+          const double den = thsel[i][q] * std::sqrt(std::max(rr[i][np_in + q], 0.0));
+          const double rel = den > 0.0 ? a / den : std::numeric_limits<double>::infinity();
+          m.last_rel[inside[i][q]] = rel;
+          if (rel <= so.tol) {
+            m.acc_theta.push_back(thsel[i][q]);
+            m.acc_rel.push_back(rel);
+            m.acc_abs.push_back(a);
+            m.acc_Y.insert(m.acc_Y.end(), Ysel[i].begin() + static_cast<size_t>(q) * kk,
+                           Ysel[i].begin() + static_cast<size_t>(q + 1) * kk);
+          }
         }
       }
     };
@@ -1098,6 +1232,7 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
         std::vector<char> a = append_column(jj);
         for (int p = 0; p < P; ++p) added[p] += a[p];
       }
+      std::vector<int> due;
       for (int p = 0; p < P; ++p) {
         MeshSolve& m = ms[p];
         if (m.done) continue;
@@ -1107,13 +1242,18 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
         }
         if (m.k >= next_check[p] && m.k < kmax) {
           while (next_check[p] <= m.k) next_check[p] += so.check_every;
-          project(p);
+          due.push_back(p);
         }
       }
+      project_many(due);
       check_wanted();
     }
-    for (int p = 0; p < P; ++p)
-      if (ms[p].kproj != ms[p].k) project(p);
+    {
+      std::vector<int> due;
+      for (int p = 0; p < P; ++p)
+        if (ms[p].kproj != ms[p].k) due.push_back(p);
+      project_many(due);
+    }
 
     // FP64 refinement: sweeps of filtered subspace iteration on the in-interval Ritz
     // vectors of each process (Sec. 4 mentions fixed-dimension, FEAST-like use of the
@@ -1181,8 +1321,9 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
         KES_CUDA(cudaMemcpyAsync(c->colsel, csel.data(), csel.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
         launch_pack_basis(s, c->Xd, np, c->colsel, c->slice_mesh, c->stage_in, NBr, np);
         KES_CHECK_LAUNCH();
-        run_filter(c, NBr, true, cpt);
-        refine_steps += c->L;
+        const int Lr = so.refine_L > 0 && so.refine_L < c->L ? so.refine_L : c->L;
+        run_filter(c, NBr, true, cpt, Lr);
+        refine_steps += Lr;
         launch_unpack_block(s, c->stage_out, NBr, c->Wc, np);
         KES_CHECK_LAUNCH();
         for (int jj = 0; jj < NBr; ++jj) {
@@ -1196,10 +1337,12 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
           if (any) append_column(jj);
         }
       }
+      std::vector<int> due;
       for (int p = 0; p < P; ++p) {
-        if (pcount[p] > 0) project(p);
+        if (pcount[p] > 0) due.push_back(p);
         want[p] = 1;
       }
+      project_many(due);
     }
 
     // results: the pairs of a mesh's processes merged in ascending theta
@@ -1521,7 +1664,8 @@ kes_status kes_krylov_solve(kes_ctx* c, const double* r0, int32_t mem, const kes
   kes_solve_opts so;
   if (so_in) so = *so_in;
   else kes_solve_opts_default(&so);
-  if (so.kmax < 1 || so.check_every < 1 || !(so.tol > 0.0) || so.refine_sweeps < 0) return KES_ERR_ARG;
+  if (so.kmax < 1 || so.check_every < 1 || !(so.tol > 0.0) || so.refine_sweeps < 0 || so.refine_L < 0)
+    return KES_ERR_ARG;
   return block_solve_impl(c, r0, 1, mem, so, out);
 }
 
@@ -1535,7 +1679,8 @@ kes_status kes_block_krylov_solve(kes_ctx* c, const double* R0, int32_t b, int32
   kes_solve_opts so;
   if (so_in) so = *so_in;
   else kes_solve_opts_default(&so);
-  if (so.kmax < b / c->F || so.check_every < 1 || !(so.tol > 0.0) || so.refine_sweeps < 0) return KES_ERR_ARG;
+  if (so.kmax < b / c->F || so.check_every < 1 || !(so.tol > 0.0) || so.refine_sweeps < 0 || so.refine_L < 0)
+    return KES_ERR_ARG;
   return block_solve_impl(c, R0, b, mem, so, out);
 }
 

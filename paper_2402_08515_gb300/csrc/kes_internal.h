@@ -158,6 +158,46 @@ void launch_spmv_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, co
 // Sets flag[0] = 1 if any of v[0..n) is not finite.
 void launch_check_finite(cudaStream_t st, const double* v, int64_t n, int* flag);
 
+// Batched forms of the Gram-Schmidt kernels: one launch serves every process (mesh and
+// interval) of a block step. A job is one process's part; it is reduced through the same
+// number of row blocks as the single launch for its rows would use (rows_for_dot), so the
+// results are bit for bit those of the separate launches.
+struct DotJob {        // out[j] = sum_i B[j * ldb + i] * (w ? w[i] : 1) * v[i], j < k
+  const double* B;
+  const double* v;
+  const double* w;
+  double* out;
+  int64_t n;
+  int64_t ldb;
+  int64_t poff;        // offset of this job's k * nblk partial sums in `partial`
+  int k;
+  int nblk;
+};
+struct GemvJob {       // v -= B h (k columns)
+  double* v;
+  const double* B;
+  const double* h;
+  int64_t n;
+  int64_t ldb;
+  int k;
+  int nblk;
+};
+struct ScaleJob {      // dst = v / sqrt(nrm2[0])
+  const double* v;
+  const double* nrm2;
+  double* dst;
+  int64_t n;
+};
+int dot_blocks(int64_t n);   // row blocks of launch_mdot for n rows
+int gemv_blocks(int64_t n);  // row blocks of launch_gemv_sub for n rows
+void launch_mdot_jobs(cudaStream_t st, const DotJob* jobs, int njobs, int max_k, int max_nblk, double* partial);
+void launch_gemv_sub_jobs(cudaStream_t st, const GemvJob* jobs, int njobs, int max_k, int max_nblk);
+void launch_scale_jobs(cudaStream_t st, const ScaleJob* jobs, int njobs, int max_nblk);
+// S x for the slices of every mesh at once, each with its own vectors: x_of[mesh] (global
+// row indexing) and y_of[mesh]; a mesh with a null x_of is skipped.
+void launch_spmv_f64_meshes(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, const double* const* x_of,
+                            double* const* y_of);
+
 // h_j = sum_i B[j*ldb + i] * w[i] * v[i] for j < k (w may be null); deterministic two-pass
 // reduction through `partial` (size >= k * kDotBlocks); result written to h (device).
 constexpr int kDotBlocks = 608;

@@ -167,18 +167,19 @@ def test_batched_block_solver_per_mesh(meshes):
         assert abs(r["n_pairs"] - len(oref.omega2)) <= 2
 
 
-@pytest.mark.parametrize("b", [1, 2])
-def test_fp32_solve_with_fp64_refinement_reaches_fp64_residuals(b):
+@pytest.mark.parametrize("b,refine_L", [(1, 0), (2, 0), (1, 100)])
+def test_fp32_solve_with_fp64_refinement_reaches_fp64_residuals(b, refine_L):
     p = square_grid(32)
     S = p.to_scipy()
     tau = _tau(p)
     exact = spectra.eigenvalues_in(p.cells, p.h, 20.0, 30.0)
     R = start_vectors(p.n, b, 3)
     so = K.kes_solve_opts_default()
-    so.kmax, so.tol, so.want_vectors, so.refine_sweeps = 100, 1e-8, 1, 2
+    so.kmax, so.tol, so.want_vectors, so.refine_sweeps, so.refine_L = 100, 1e-8, 1, 2, refine_L
     with K.Context(p, precision="fp32", block_b=b) as c:
         K.kes_set_filter(c.handle, 20.0, 30.0, tau, 300)
         res = K.kes_block_krylov_solve(c.handle, R, b, so)[0]
+    assert res["refine_steps"] > 0 and res["refine_steps"] % (refine_L or 300) == 0
     distinct, _ = spectra.distinct(exact)
     found, _ = spectra.distinct(res["omega2"])
     print(f"b={b}: refined FP32 accepted {res['n_pairs']} pairs ({len(found)} of {len(distinct)} distinct) "
@@ -395,3 +396,28 @@ def test_leapfrog4_cfl_bound():
             else:
                 with pytest.raises(K.KesError):
                     K.kes_set_filter(c.handle, 10.0, 20.0, ratio / w, 20)
+
+
+def test_meshes_times_intervals_equal_separate_solves(meshes):
+    # two meshes of different sizes, two intervals each, in one solve: the batched
+    # Gram-Schmidt stages serve all four processes with one launch per stage, and each
+    # process's pairs must still be bit for bit those of its own separate solve
+    sq, box = meshes[0], meshes[1]
+    taus = np.array([_tau(sq), _tau(box)])
+    wmin = np.array([[14.0, 22.0], [6.0, 11.0]])
+    wmax = np.array([[19.0, 27.0], [9.0, 14.0]])
+    Rs = [start_vectors(sq.n, 4, 41), start_vectors(box.n, 4, 42)]
+    so = K.kes_solve_opts_default()
+    so.kmax, so.tol, so.check_every = 40, 1e-8, 8
+    with K.Context([sq, box], block_b=4) as c:
+        K.kes_set_filters_batch(c.handle, wmin, wmax, taus, 200)
+        both = K.kes_block_krylov_solve(c.handle, np.concatenate(Rs, axis=1), 4, so)
+    for j, p in enumerate([sq, box]):
+        for f in range(2):
+            with K.Context(p, block_b=2) as c:
+                K.kes_set_filter(c.handle, wmin[j, f], wmax[j, f], taus[j], 200)
+                one = K.kes_block_krylov_solve(c.handle, Rs[j][2 * f:2 * f + 2], 2, so)[0]
+            sel = both[j]["interval"] == f
+            print(f"mesh {j} interval {f}: {int(sel.sum())} pairs")
+            np.testing.assert_array_equal(both[j]["omega2"][sel], one["omega2"])
+            np.testing.assert_array_equal(both[j]["rel_res"][sel], one["rel_res"])

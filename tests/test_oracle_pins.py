@@ -64,6 +64,13 @@ def test_weight_support_is_closed_interval():
     assert vals[1] == 0.0 and vals[2] == 0.0
 
 
+def test_shorter_filter_is_a_truncated_table():
+    # alpha(t) of eq. (weightf) does not depend on T: the weights of L' < L steps are the
+    # first L' + 1 of the L-step table (what a shorter refinement filter runs)
+    full = O.alpha_table(20.0, 30.0, 0.01, 600)
+    np.testing.assert_array_equal(O.alpha_table(20.0, 30.0, 0.01, 150), full[:151])
+
+
 def test_alpha_table_indexing():
     wmin, wmax, tau, L = 20.0, 30.0, 0.0099, 300
     a = O.alpha_table(wmin, wmax, tau, L)
