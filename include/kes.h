@@ -321,6 +321,25 @@ kes_status kes_krylov_solve(kes_ctx* ctx, const double* r0, int32_t mem, const k
  */
 kes_status kes_block_krylov_solve(kes_ctx* ctx, const double* R0, int32_t b, int32_t mem,
                                   const kes_solve_opts* sopts, kes_result** out);
+
+/*
+ * kes_subspace_solve -- the fixed-dimension alternative of Sec. 4 (a FEAST-like
+ * iteration with the time-domain filter): from the p columns of X0, each of
+ * sopts->refine_sweeps sweeps filters every vector (X <- C X, in the context's
+ * precision, sopts->refine_L steps if set), M-orthonormalises the results (dependent
+ * ones dropped), solves the projected problem (eq. projevp) and feeds all of its Ritz
+ * vectors to the next sweep, so memory stays at p basis vectors per mesh. The pairs of
+ * the last sweep in the interval with rel_res <= tol are returned. The iteration
+ * converges to the p eigenvectors with the largest |beta~|: choose p above the number
+ * of eigenvalues in the interval.
+ *   X0     n_total x p col-major (host or device per `mem`); every mesh starts from its rows
+ *   sopts  refine_sweeps >= 1 (the sweeps), kmax >= p, tol; check_every and n_wanted unused
+ *   out    array of kes_mesh_count(ctx) result pointers (time_steps = 0, refine_steps = the
+ *          leapfrog steps of the sweeps per filtered block)
+ * Requires a single interval per mesh (KES_ERR_UNSUPPORTED otherwise).
+ */
+kes_status kes_subspace_solve(kes_ctx* ctx, const double* X0, int32_t p, int32_t mem, const kes_solve_opts* sopts,
+                              kes_result** out);
 void kes_result_free(kes_result* res);
 
 kes_status kes_get_stats(kes_ctx* ctx, kes_stats* stats); /* synchronises the stream */

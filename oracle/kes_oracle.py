@@ -39,7 +39,7 @@ __all__ = [
     "weight", "alpha_table", "q_values", "beta_tilde", "filter_apply",
     "filter_apply_multi", "power_iteration", "m_inner", "m_norm",
     "orthonormalize_cgs2", "rayleigh_ritz", "ritz_residuals", "krylov_solve",
-    "block_krylov_solve", "multi_interval_krylov_solve",
+    "block_krylov_solve", "multi_interval_krylov_solve", "subspace_iteration",
     "refine_subspace", "gaussian_weight", "alpha_table_gaussian", "triangle_weight",
     "alpha_table_triangle", "q_values_leapfrog4", "beta_tilde_leapfrog4",
     "filter_apply_leapfrog4",
@@ -541,3 +541,36 @@ def refine_subspace(S, m: np.ndarray, X: np.ndarray, omega_min: float, omega_max
         th_acc, rel_acc, X_acc = th_in[acc], r[acc], Xi[acc]
         X = Xi
     return th_acc, rel_acc, X_acc, th_in, rel_in
+
+
+def subspace_iteration(S, m: np.ndarray, X0: np.ndarray, omega_min: float, omega_max: float,
+                       tau: float, L: int, tol: float, sweeps: int):
+    """The fixed-dimension alternative of Sec. 4 (FEAST-like filtered subspace
+    iteration): from the p rows of X0, each sweep filters every vector (X <- C X),
+    M-orthonormalises them in order (CGS2, dependent vectors dropped), solves the
+    projected problem (eq. projevp) and takes all of its Ritz vectors, ascending, as the
+    next X, so the subspace keeps its dimension. The pairs of the last sweep with omega
+    in the interval and rel_res <= tol are accepted. Returns (theta_acc, rel_acc, X_acc,
+    theta_all, rel_inside) where rel_inside is nan outside the interval."""
+    alpha = alpha_table(omega_min, omega_max, tau, L)
+    X = np.atleast_2d(np.asarray(X0, dtype=np.float64))
+    theta = np.zeros(0)
+    rel_all = np.zeros(0)
+    th_acc = rel_acc = np.zeros(0)
+    X_acc = np.zeros((0, X.shape[1]))
+    for _ in range(sweeps):
+        B = np.zeros((0, X.shape[1]))
+        for x in X:
+            v, nb, na = orthonormalize_cgs2(B, filter_apply(S, m, x, tau, alpha), m)
+            if v is not None:
+                B = np.vstack([B, v])
+        theta, Y = rayleigh_ritz(S, B)
+        omega = np.sqrt(theta)
+        inside = (omega >= omega_min) & (omega <= omega_max)
+        Xi, a, r = ritz_residuals(S, m, B, theta[inside], Y[:, inside])
+        rel_all = np.full(len(theta), np.nan)
+        rel_all[inside] = r
+        acc = r <= tol
+        th_acc, rel_acc, X_acc = theta[inside][acc], r[acc], Xi[acc]
+        X = Y.T @ B
+    return th_acc, rel_acc, X_acc, theta, rel_all

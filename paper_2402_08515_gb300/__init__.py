@@ -27,7 +27,7 @@ __all__ = [
     "Context", "header_functions", "kes_filter_apply_noalloc", "KES_NOALLOC_MAX_N",
     "kes_create_batch", "kes_mesh_count", "kes_estimate_omega_max_batch", "kes_set_filters_batch",
     "kes_block_krylov_solve", "kes_set_weights", "kes_alpha_gaussian", "kes_filter_apply_columns",
-    "kes_alpha_triangle", "kes_weights_response", "kes_launch_shapes",
+    "kes_alpha_triangle", "kes_weights_response", "kes_launch_shapes", "kes_subspace_solve",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -114,6 +114,8 @@ _sig = {
     "kes_estimate_omega_max_batch": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "kes_set_filters_batch": (C.c_int, [_P, C.c_int32, _P, _P, _P, C.c_int32]),
     "kes_block_krylov_solve": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.POINTER(KesSolveOpts),
+                                         C.POINTER(C.POINTER(KesResult))]),
+    "kes_subspace_solve": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.POINTER(KesSolveOpts),
                                          C.POINTER(C.POINTER(KesResult))]),
     "kes_set_weights": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, C.c_int32]),
     "kes_alpha_gaussian": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_int32, _P]),
@@ -354,6 +356,19 @@ def kes_block_krylov_solve(ctx: int, R0, b: int, sopts: KesSolveOpts | None = No
                                     C.byref(sopts) if sopts is not None else None,
                                     C.cast(arr, C.POINTER(C.POINTER(KesResult))))
     _check(st, "kes_block_krylov_solve", allow_info=True)
+    return [_result_dict(arr[j], st) for j in range(nm)]
+
+
+def kes_subspace_solve(ctx: int, X0, sopts: KesSolveOpts) -> list[dict]:
+    """X0: (p, n_total) start vectors (numpy or CUDA tensor); one result dict per mesh."""
+    dev = _is_device(X0)
+    if not dev:
+        X0 = _f64_host(X0)
+    nm = lib.kes_mesh_count(ctx)
+    arr = (C.POINTER(KesResult) * nm)()
+    st = lib.kes_subspace_solve(ctx, _ptr(X0), int(X0.shape[0]), KES_MEM_DEVICE if dev else KES_MEM_HOST,
+                                C.byref(sopts), C.cast(arr, C.POINTER(C.POINTER(KesResult))))
+    _check(st, "kes_subspace_solve", allow_info=True)
     return [_result_dict(arr[j], st) for j in range(nm)]
 
 

@@ -204,19 +204,31 @@ int rows_grid(int64_t n, int cap) {
   return static_cast<int>(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
-// The batched kernels: blockIdx.z (or .y) picks the job; a job with fewer row blocks or
-// columns than the grid leaves the extra blocks idle (a block-uniform early return,
-// before any barrier). Each job strides its rows by its own nblk, as its single launch does.
-__global__ void __launch_bounds__(kThreads) k_mdot_jobs(const DotJob* __restrict__ jobs,
+// The batched kernels: the 1D grid is the concatenation of the jobs' blocks; a block finds
+// its job by binary search over the jobs' first blocks, then works as a block of that
+// job's own launch would (rows strided by the job's nblk), so the sums are the same.
+template <typename J>
+__device__ __forceinline__ int job_of(const J* __restrict__ jobs, int njobs, int64_t bid) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].first <= bid) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kThreads) k_mdot_jobs(const DotJob* __restrict__ jobs, int njobs,
                                                         double* __restrict__ partial) {
-  const DotJob jb = jobs[blockIdx.z];
-  const int j0 = blockIdx.y * kGroup;
-  if (static_cast<int>(blockIdx.x) >= jb.nblk || j0 >= jb.k) return;
+  const DotJob jb = jobs[job_of(jobs, njobs, blockIdx.x)];
+  const int64_t local = blockIdx.x - jb.first;
+  const int blk = static_cast<int>(local % jb.nblk);
+  const int j0 = static_cast<int>(local / jb.nblk) * kGroup;
   double acc[kGroup];
 #pragma unroll
   for (int g = 0; g < kGroup; ++g) acc[g] = 0.0;
   const int ng = min(kGroup, jb.k - j0);
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; i < jb.n;
+  for (int64_t i = blk * static_cast<int64_t>(kThreads) + threadIdx.x; i < jb.n;
        i += static_cast<int64_t>(jb.nblk) * kThreads) {
     const double wv = jb.w ? jb.w[i] * jb.v[i] : jb.v[i];
 #pragma unroll
@@ -226,7 +238,7 @@ __global__ void __launch_bounds__(kThreads) k_mdot_jobs(const DotJob* __restrict
   double tot[kGroup];
   block_sum<kGroup>(acc, tot);
   if (threadIdx.x == 0)
-    for (int g = 0; g < ng; ++g) partial[jb.poff + static_cast<int64_t>(j0 + g) * jb.nblk + blockIdx.x] = tot[g];
+    for (int g = 0; g < ng; ++g) partial[jb.poff + static_cast<int64_t>(j0 + g) * jb.nblk + blk] = tot[g];
 }
 
 __global__ void __launch_bounds__(kThreads) k_reduce_jobs(const DotJob* __restrict__ jobs,
@@ -241,13 +253,13 @@ __global__ void __launch_bounds__(kThreads) k_reduce_jobs(const DotJob* __restri
   if (threadIdx.x == 0) jb.out[j] = tot[0];
 }
 
-__global__ void __launch_bounds__(kThreads) k_gemv_sub_jobs(const GemvJob* __restrict__ jobs) {
+__global__ void __launch_bounds__(kThreads) k_gemv_sub_jobs(const GemvJob* __restrict__ jobs, int njobs) {
   extern __shared__ double sh_h[];
-  const GemvJob jb = jobs[blockIdx.y];
-  if (static_cast<int>(blockIdx.x) >= jb.nblk) return;
+  const GemvJob jb = jobs[job_of(jobs, njobs, blockIdx.x)];
+  const int64_t blk = blockIdx.x - jb.first;
   for (int j = threadIdx.x; j < jb.k; j += kThreads) sh_h[j] = jb.h[j];
   __syncthreads();
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; i < jb.n;
+  for (int64_t i = blk * static_cast<int64_t>(kThreads) + threadIdx.x; i < jb.n;
        i += static_cast<int64_t>(jb.nblk) * kThreads) {
     double s0 = 0.0, s1 = 0.0;
     int j = 0;
@@ -295,17 +307,17 @@ __global__ void k_scale_jobs(const ScaleJob* __restrict__ jobs) {
 int dot_blocks(int64_t n) { return rows_grid(n, kDotBlocks); }
 int gemv_blocks(int64_t n) { return rows_grid(n, 2048); }
 
-void launch_mdot_jobs(cudaStream_t st, const DotJob* jobs, int njobs, int max_k, int max_nblk, double* partial) {
-  if (njobs <= 0 || max_k <= 0) return;
-  dim3 grid(max_nblk, (max_k + kGroup - 1) / kGroup, njobs);
-  k_mdot_jobs<<<grid, kThreads, 0, st>>>(jobs, partial);
+void launch_mdot_jobs(cudaStream_t st, const DotJob* jobs, int njobs, int max_k, int64_t total_blocks,
+                      double* partial) {
+  if (njobs <= 0 || max_k <= 0 || total_blocks <= 0) return;
+  k_mdot_jobs<<<static_cast<unsigned>(total_blocks), kThreads, 0, st>>>(jobs, njobs, partial);
   k_reduce_jobs<<<dim3(max_k, njobs), kThreads, 0, st>>>(jobs, partial);
   g_launches += 2;
 }
 
-void launch_gemv_sub_jobs(cudaStream_t st, const GemvJob* jobs, int njobs, int max_k, int max_nblk) {
-  if (njobs <= 0 || max_k <= 0) return;
-  k_gemv_sub_jobs<<<dim3(max_nblk, njobs), kThreads, max_k * sizeof(double), st>>>(jobs);
+void launch_gemv_sub_jobs(cudaStream_t st, const GemvJob* jobs, int njobs, int max_k, int64_t total_blocks) {
+  if (njobs <= 0 || max_k <= 0 || total_blocks <= 0) return;
+  k_gemv_sub_jobs<<<static_cast<unsigned>(total_blocks), kThreads, max_k * sizeof(double), st>>>(jobs, njobs);
   ++g_launches;
 }
 

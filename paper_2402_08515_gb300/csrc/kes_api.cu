@@ -880,6 +880,20 @@ struct MeshSolve {
   std::vector<double> acc_theta, acc_rel, acc_abs, acc_Y;
 };
 
+// Sets each job's first block of a batched launch (prefix sums in job order) and returns
+// the launch's total blocks.
+inline int64_t job_blocks(const DotJob& j) { return dot_job_blocks(j); }
+inline int64_t job_blocks(const GemvJob& j) { return gemv_job_blocks(j); }
+template <typename J>
+int64_t first_blocks(std::vector<J>& jobs) {
+  int64_t total = 0;
+  for (J& j : jobs) {
+    j.first = total;
+    total += job_blocks(j);
+  }
+  return total;
+}
+
 template <typename T>
 T* hdup(const std::vector<T>& v) {
   T* d = static_cast<T*>(std::malloc(std::max<size_t>(1, v.size()) * sizeof(T)));
@@ -893,8 +907,11 @@ T* hdup(const std::vector<T>& v) {
 // is the block Krylov iteration of mesh p / F on interval f from start columns
 // f * g .. f * g + g - 1 (g = b / F), with its own basis, Gram-Schmidt scalars and
 // projected matrix; the processes share only the b-column trajectory of each block step.
+// X0 (p0 caller vectors, n_total x p0 column-major) selects the fixed-dimension mode: no
+// Krylov phase; refine_sweeps sweeps of X <- C X, M-orthonormalisation and Rayleigh-Ritz
+// from X0, every Ritz vector fed back (the FEAST-like use of the filter in Sec. 4).
 kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, const kes_solve_opts& so,
-                            kes_result** out) {
+                            kes_result** out, const double* X0 = nullptr, int p0 = 0) {
   const int nm = c->n_mesh();
   const int F = c->F;
   const int P = nm * F;
@@ -958,7 +975,7 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
       // h = B^T M w and w -= B h, ||w||_M^2 again
       std::vector<DotJob> nb_jobs(na), na_jobs(na), h_jobs;
       std::vector<GemvJob> g_jobs;
-      int max_k = 0, max_nblk = 1, max_gblk = 1;
+      int max_k = 0;
       int64_t poff = 0, poff_h = 0;
       for (int i = 0; i < na; ++i) {
         const int p = act[i];
@@ -966,20 +983,20 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
         double* w = c->Wc + static_cast<int64_t>(jj) * np + mi.row_off;
         const double* mj = c->m64 + mi.row_off;
         const int nblk = dot_blocks(mi.n_pad), gblk = gemv_blocks(mi.n_pad);
-        max_nblk = std::max(max_nblk, nblk);
-        max_gblk = std::max(max_gblk, gblk);
-        nb_jobs[i] = DotJob{w, w, mj, c->normd + 2 * p, mi.n_pad, 0, poff, 1, nblk};
-        na_jobs[i] = DotJob{w, w, mj, c->normd + 2 * p + 1, mi.n_pad, 0, poff, 1, nblk};
+        nb_jobs[i] = DotJob{w, w, mj, c->normd + 2 * p, mi.n_pad, 0, poff, 0, 1, nblk};
+        na_jobs[i] = DotJob{w, w, mj, c->normd + 2 * p + 1, mi.n_pad, 0, poff, 0, 1, nblk};
         poff += nblk;
         const int k = ms[p].k;
         if (k > 0) {
-          h_jobs.push_back(DotJob{Bp(p), w, mj, proc_scal(c, p) + kScal, mi.n_pad, np, poff_h, k, nblk});
-          g_jobs.push_back(GemvJob{w, Bp(p), proc_scal(c, p) + kScal, mi.n_pad, np, k, gblk});
+          h_jobs.push_back(DotJob{Bp(p), w, mj, proc_scal(c, p) + kScal, mi.n_pad, np, poff_h, 0, k, nblk});
+          g_jobs.push_back(GemvJob{w, Bp(p), proc_scal(c, p) + kScal, mi.n_pad, np, 0, k, gblk});
           poff_h += static_cast<int64_t>(k) * nblk;
           max_k = std::max(max_k, k);
         }
       }
       const int nh = static_cast<int>(h_jobs.size());
+      const int64_t nb_blocks = first_blocks(nb_jobs), na_blocks = first_blocks(na_jobs);
+      const int64_t h_blocks = first_blocks(h_jobs), g_blocks = first_blocks(g_jobs);
       char* jb = c->jobs;
       DotJob* d_nb = reinterpret_cast<DotJob*>(jb);
       DotJob* d_na = d_nb + P;
@@ -992,12 +1009,12 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
         KES_CUDA(cudaMemcpyAsync(d_h, h_jobs.data(), nh * sizeof(DotJob), cudaMemcpyHostToDevice, s));
         KES_CUDA(cudaMemcpyAsync(d_g, g_jobs.data(), nh * sizeof(GemvJob), cudaMemcpyHostToDevice, s));
       }
-      launch_mdot_jobs(s, d_nb, na, 1, max_nblk, c->partial);  // ||w||_M^2 before
+      launch_mdot_jobs(s, d_nb, na, 1, nb_blocks, c->partial);  // ||w||_M^2 before
       for (int pass = 0; pass < 2 && nh > 0; ++pass) {
-        launch_mdot_jobs(s, d_h, nh, max_k, max_nblk, c->partial);  // h = B^T M w
-        launch_gemv_sub_jobs(s, d_g, nh, max_k, max_gblk);          // w -= B h
+        launch_mdot_jobs(s, d_h, nh, max_k, h_blocks, c->partial);  // h = B^T M w
+        launch_gemv_sub_jobs(s, d_g, nh, max_k, g_blocks);          // w -= B h
       }
-      launch_mdot_jobs(s, d_na, na, 1, max_nblk, c->partial);  // ||w||_M^2 after
+      launch_mdot_jobs(s, d_na, na, 1, na_blocks, c->partial);  // ||w||_M^2 after
       KES_CHECK_LAUNCH();
       std::vector<double> nrm(2 * P, 0.0);
       KES_CUDA(cudaMemcpyAsync(nrm.data(), c->normd, 2 * P * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1029,13 +1046,14 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
         max_sblk = std::max(max_sblk, gemv_blocks(mi.n_pad));
         x_of[static_cast<size_t>(p % F) * nm + p / F] = Bfull(p) + k * np;
         y_of[static_cast<size_t>(p % F) * nm + p / F] = c->SB + (p % F) * kc * np + k * np;
-        c_jobs.push_back(DotJob{Bp(p), sbk, nullptr, Hcol(p, k), mi.n_pad, np, poff, k + 1, nblk});
+        c_jobs.push_back(DotJob{Bp(p), sbk, nullptr, Hcol(p, k), mi.n_pad, np, poff, 0, k + 1, nblk});
         poff += static_cast<int64_t>(k + 1) * nblk;
         max_k1 = std::max(max_k1, k + 1);
         ms[p].k = k + 1;
         added[p] = 1;
       }
       const int ns = static_cast<int>(s_jobs.size());
+      const int64_t c_blocks = first_blocks(c_jobs);
       if (ns > 0) {
         ev = other_begin();
         ScaleJob* d_s = reinterpret_cast<ScaleJob*>(d_g + P);
@@ -1054,7 +1072,7 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
           if (any) launch_spmv_f64_meshes(c->A, c->cfg, s, d_x + static_cast<size_t>(f) * nm,
                                           d_y + static_cast<size_t>(f) * nm);
         }
-        launch_mdot_jobs(s, d_c, ns, max_k1, max_nblk, c->partial);
+        launch_mdot_jobs(s, d_c, ns, max_k1, c_blocks, c->partial);
         KES_CHECK_LAUNCH();
         other_end(ev);
       }
@@ -1191,8 +1209,9 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
       }
     };
 
+    int64_t steps = 0;
     // start block: the g start vectors of each process, M-orthonormalised in order
-    {
+    if (!X0) {
       cudaEvent_t ev = other_begin();
       block_in(c, R0, b, mem, NB, c->stage_in);
       launch_unpack_block(s, c->stage_in, NB, c->Wc, np);
@@ -1202,10 +1221,9 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
       for (int p = 0; p < P; ++p)
         if (ms[p].k == 0) ms[p].done = ms[p].breakdown = true;
     }
-    int64_t steps = 0;
     std::vector<int> next_check(P, so.check_every);
     std::vector<int32_t> colsel(static_cast<size_t>(nm) * NB, -1);
-    for (;;) {
+    for (; !X0;) {
       bool any = false;
       std::fill(colsel.begin(), colsel.end(), -1);
       for (int p = 0; p < P; ++p) {
@@ -1248,7 +1266,7 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
       project_many(due);
       check_wanted();
     }
-    {
+    if (!X0) {
       std::vector<int> due;
       for (int p = 0; p < P; ++p)
         if (ms[p].kproj != ms[p].k) due.push_back(p);
@@ -1260,15 +1278,22 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
     // filter): X <- C X with the FP64 step kernels, M-orthonormalise, Rayleigh-Ritz,
     // residuals. With F intervals the columns of a refinement block are grouped per
     // interval like those of the Krylov blocks.
+    // In the fixed-dimension mode the sweeps filter in the context's precision and keep
+    // every Ritz vector; the refinement filters in FP64 and keeps the in-interval ones.
     int64_t refine_steps = 0;
     const int NBr = F > 1 ? NB : c->NBcap;  // columns of one refinement filter call
     const int gr = F > 1 ? g : NBr;         // of them per interval
+    const bool sweep_fp64 = X0 ? c->opts.precision == KES_PREC_FP64 : true;
+    auto keep = [&](const MeshSolve& m, int q) { return X0 != nullptr || !std::isnan(m.last_rel[q]); };
     for (int sweep = 0; sweep < so.refine_sweeps; ++sweep) {
+      const bool from_x0 = X0 && sweep == 0;
       std::vector<int> pcount(P, 0);
       std::vector<int64_t> xoff(F + 1, 0);  // interval f uses columns xoff[f] .. of Xd (meshes share them)
       int rounds = 0;
       for (int p = 0; p < P; ++p) {
-        for (double r : ms[p].last_rel) pcount[p] += std::isnan(r) ? 0 : 1;
+        if (from_x0) pcount[p] = p0;
+        else
+          for (size_t q = 0; q < ms[p].last_rel.size(); ++q) pcount[p] += keep(ms[p], static_cast<int>(q)) ? 1 : 0;
         rounds = std::max(rounds, (pcount[p] + gr - 1) / gr);
       }
       for (int f = 0; f < F; ++f) {
@@ -1284,8 +1309,20 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
         c->Xd_cap = need;
       }
       KES_CUDA(cudaMemsetAsync(c->Xd, 0, need * sizeof(double), s));
-      // Ritz vectors of every in-interval Ritz value: X = B y_q on the mesh's rows
-      for (int p = 0; p < P; ++p) {
+      if (from_x0) {  // the caller's vectors, one column at a time into the padded row order
+        for (int q = 0; q < p0; ++q) {
+          const double* src = X0 + static_cast<int64_t>(q) * c->n;
+          if (mem == KES_MEM_HOST) {
+            KES_CUDA(cudaMemcpyAsync(c->tmp_user, src, static_cast<size_t>(c->n) * sizeof(double),
+                                     cudaMemcpyHostToDevice, s));
+            src = c->tmp_user;
+          }
+          launch_gather_rows(s, src, c->n, 1, c->row_src, c->n, c->Xd + static_cast<int64_t>(q) * np, 1, np);
+        }
+        KES_CHECK_LAUNCH();
+      }
+      // Ritz vectors (all of them, or those of in-interval Ritz values): X = B y_q
+      for (int p = 0; p < P && !from_x0; ++p) {
         if (pcount[p] == 0) continue;
         MeshSolve& m = ms[p];
         const MeshInfo& mi = mesh_of(p);
@@ -1293,7 +1330,7 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
         std::vector<double> theta, Y, Ysel;
         projected_eig(p, theta, Y);
         for (int q = 0; q < kk; ++q)
-          if (!std::isnan(m.last_rel[q]))
+          if (keep(m, q))
             Ysel.insert(Ysel.end(), Y.begin() + static_cast<size_t>(q) * kk, Y.begin() + static_cast<size_t>(q + 1) * kk);
         KES_CUDA(cudaMemcpyAsync(c->Yd, Ysel.data(), Ysel.size() * sizeof(double), cudaMemcpyHostToDevice, s));
         launch_gemm_bx(s, Bp(p), np, kk, c->Yd, pcount[p], c->Xd + xoff[p % F] * np + mi.row_off, np, mi.n_pad);
@@ -1322,7 +1359,7 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
         launch_pack_basis(s, c->Xd, np, c->colsel, c->slice_mesh, c->stage_in, NBr, np);
         KES_CHECK_LAUNCH();
         const int Lr = so.refine_L > 0 && so.refine_L < c->L ? so.refine_L : c->L;
-        run_filter(c, NBr, true, cpt, Lr);
+        run_filter(c, NBr, sweep_fp64, cpt, Lr);
         refine_steps += Lr;
         launch_unpack_block(s, c->stage_out, NBr, c->Wc, np);
         KES_CHECK_LAUNCH();
@@ -1682,6 +1719,19 @@ kes_status kes_block_krylov_solve(kes_ctx* c, const double* R0, int32_t b, int32
   if (so.kmax < b / c->F || so.check_every < 1 || !(so.tol > 0.0) || so.refine_sweeps < 0 || so.refine_L < 0)
     return KES_ERR_ARG;
   return block_solve_impl(c, R0, b, mem, so, out);
+}
+
+kes_status kes_subspace_solve(kes_ctx* c, const double* X0, int32_t p, int32_t mem, const kes_solve_opts* so_in,
+                              kes_result** out) {
+  if (!c || !X0 || !out || p < 1 || (mem != KES_MEM_HOST && mem != KES_MEM_DEVICE)) return KES_ERR_ARG;
+  for (int j = 0; j < c->n_mesh(); ++j) out[j] = nullptr;
+  if (!c->filter_set) return KES_ERR_STATE;
+  if (c->F != 1) return KES_ERR_UNSUPPORTED;
+  kes_solve_opts so;
+  if (so_in) so = *so_in;
+  else kes_solve_opts_default(&so);
+  if (so.kmax < p || so.refine_sweeps < 1 || !(so.tol > 0.0) || so.refine_L < 0) return KES_ERR_ARG;
+  return block_solve_impl(c, nullptr, 1, mem, so, out, X0, p);
 }
 
 kes_status kes_get_stats(kes_ctx* c, kes_stats* s) {

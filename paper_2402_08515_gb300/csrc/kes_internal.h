@@ -170,6 +170,7 @@ struct DotJob {        // out[j] = sum_i B[j * ldb + i] * (w ? w[i] : 1) * v[i],
   int64_t n;
   int64_t ldb;
   int64_t poff;        // offset of this job's k * nblk partial sums in `partial`
+  int64_t first;       // its first block of the launch (set by launch_mdot_jobs' caller: prefix sums)
   int k;
   int nblk;
 };
@@ -179,9 +180,13 @@ struct GemvJob {       // v -= B h (k columns)
   const double* h;
   int64_t n;
   int64_t ldb;
+  int64_t first;       // its first block of the launch
   int k;
   int nblk;
 };
+// Blocks a job takes in a batched launch (the launch's grid is the sum over its jobs).
+inline int64_t dot_job_blocks(const DotJob& j) { return static_cast<int64_t>(j.nblk) * ((j.k + 7) / 8); }
+inline int64_t gemv_job_blocks(const GemvJob& j) { return j.nblk; }
 struct ScaleJob {      // dst = v / sqrt(nrm2[0])
   const double* v;
   const double* nrm2;
@@ -190,8 +195,11 @@ struct ScaleJob {      // dst = v / sqrt(nrm2[0])
 };
 int dot_blocks(int64_t n);   // row blocks of launch_mdot for n rows
 int gemv_blocks(int64_t n);  // row blocks of launch_gemv_sub for n rows
-void launch_mdot_jobs(cudaStream_t st, const DotJob* jobs, int njobs, int max_k, int max_nblk, double* partial);
-void launch_gemv_sub_jobs(cudaStream_t st, const GemvJob* jobs, int njobs, int max_k, int max_nblk);
+// total_blocks: sum of dot_job_blocks / gemv_job_blocks over the jobs, whose `first` fields
+// hold the prefix sums in job order.
+void launch_mdot_jobs(cudaStream_t st, const DotJob* jobs, int njobs, int max_k, int64_t total_blocks,
+                      double* partial);
+void launch_gemv_sub_jobs(cudaStream_t st, const GemvJob* jobs, int njobs, int max_k, int64_t total_blocks);
 void launch_scale_jobs(cudaStream_t st, const ScaleJob* jobs, int njobs, int max_nblk);
 // S x for the slices of every mesh at once, each with its own vectors: x_of[mesh] (global
 // row indexing) and y_of[mesh]; a mesh with a null x_of is skipped.

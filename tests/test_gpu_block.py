@@ -421,3 +421,37 @@ def test_meshes_times_intervals_equal_separate_solves(meshes):
             print(f"mesh {j} interval {f}: {int(sel.sum())} pairs")
             np.testing.assert_array_equal(both[j]["omega2"][sel], one["omega2"])
             np.testing.assert_array_equal(both[j]["rel_res"][sel], one["rel_res"])
+
+
+# ---------------------------------------------------------------- fixed-dimension iteration (Sec. 4)
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_subspace_solve_matches_oracle(precision):
+    p = square_grid(24)
+    S = p.to_scipy()
+    tau = _tau(p)
+    lo, hi, L, dim, sweeps = 15.0, 22.0, 200, 36, 14
+    X0 = start_vectors(p.n, dim, 5)
+    tol = 1e-8 if precision == "fp64" else 1e-5
+    so = K.kes_solve_opts_default()
+    so.kmax, so.tol, so.refine_sweeps, so.want_vectors = dim, tol, sweeps, 1
+    with K.Context(p, precision=precision, block_b=8) as c:
+        K.kes_set_filter(c.handle, lo, hi, tau, L)
+        res = K.kes_subspace_solve(c.handle, X0, so)[0]
+    th, rel, X, tha, rela = O.subspace_iteration(S, p.m, X0, lo, hi, tau, L, tol, sweeps)
+    exact = spectra.eigenvalues_in(p.cells, p.h, lo, hi)
+    print(f"{precision}: GPU accepted {res['n_pairs']}, oracle {len(th)} of {len(exact)}; "
+          f"{res['refine_steps']} steps")
+    assert res["time_steps"] == 0 and res["refine_steps"] > 0 and res["k_used"] <= dim
+    for t in res["omega2"]:
+        assert np.min(np.abs(exact - t)) <= EIG_REL[precision] * t
+    if precision == "fp64":
+        # every oracle pair well inside the tolerance is found (pairs near it may land
+        # on either side with a different rounding order)
+        for t in th[rel <= tol / 10]:
+            assert np.min(np.abs(res["omega2"] - t)) <= 1e-10 * t
+        assert abs(res["n_pairs"] - len(th)) <= 2
+    else:
+        assert res["n_pairs"] >= len(th) - 3
+    for t, x in zip(res["omega2"], res["vectors"]):
+        assert np.linalg.norm(S @ x - t * p.m * x) <= tol * 1.01 * t * np.linalg.norm(p.m * x)

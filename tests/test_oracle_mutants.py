@@ -206,3 +206,11 @@ def test_leapfrog4_wrong_recurrence_is_caught(monkeypatch):
     _patch(monkeypatch, "q_values_leapfrog4", q_bad)
     with pytest.raises(AssertionError):
         pins.test_leapfrog4_recurrence_is_third_kind_chebyshev_of_its_phase()
+
+
+def test_subspace_iteration_without_filter_is_caught(monkeypatch):
+    def no_filter(S, m, r, tau, alpha):
+        return np.array(r, dtype=np.float64)
+    _patch(monkeypatch, "filter_apply", no_filter)
+    with pytest.raises(AssertionError):
+        pins.test_subspace_iteration_finds_the_dominant_eigenvalues_of_the_filter()

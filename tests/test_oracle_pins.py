@@ -504,3 +504,40 @@ def test_leapfrog4_filter_maps_eigenvectors_by_its_beta_tilde(kind):
     for v, b in zip(vecs, beta):
         out = O.filter_apply_leapfrog4(S, m, v, tau, alpha)
         np.testing.assert_allclose(out, b * v, atol=1e-10 * np.abs(v).max() * np.abs(alpha).sum())
+
+
+# ---------------------------------------------------------------- fixed-dimension iteration (Sec. 4)
+
+def test_subspace_iteration_from_exact_eigenvectors_is_exact():
+    p = square_grid(20)
+    S = p.to_scipy()
+    tau = 0.9 * 2 / math.sqrt(spectra.box_spectrum(p.cells, p.h).max())
+    modes = [(2, 3), (3, 2), (4, 1), (1, 4), (6, 6)]       # (6, 6) lies outside the interval
+    X = np.stack([spectra.box_eigenvector(p.cells, k) for k in modes])
+    lam = [4 * 400 * (math.sin(a * math.pi / 40) ** 2 + math.sin(b * math.pi / 40) ** 2) for a, b in modes]
+    th, rel, Xa, tha, rela = O.subspace_iteration(S, p.m, X, 10.0, 15.0, tau, 150, 1e-10, 1)
+    np.testing.assert_allclose(np.sort(tha), np.sort(lam), rtol=1e-12)
+    inside = sorted(x for x in lam if 10.0 <= math.sqrt(x) <= 15.0)
+    np.testing.assert_allclose(np.sort(th), inside, rtol=1e-12)
+
+
+def test_subspace_iteration_finds_the_dominant_eigenvalues_of_the_filter():
+    # from p random vectors the iteration converges to the p eigenvectors with the largest
+    # |beta~|: every eigenvalue of the interval whose |beta~| is at least twice the
+    # (p+1)-th largest of the whole spectrum is found, and nothing else is accepted
+    p = square_grid(24)
+    S = p.to_scipy()
+    tau = 0.9 * 2 / math.sqrt(spectra.box_spectrum(p.cells, p.h).max())
+    lo, hi, L, dim = 15.0, 22.0, 200, 36
+    lam = spectra.box_spectrum(p.cells, p.h)
+    beta = np.abs(O.beta_tilde(np.sqrt(lam), O.alpha_table(lo, hi, tau, L), tau))
+    cut = np.sort(beta)[::-1][dim]
+    w = np.sqrt(lam)
+    must = np.sort(lam[(w >= lo) & (w <= hi) & (beta >= 2 * cut)])
+    th, rel, X, tha, rela = O.subspace_iteration(S, p.m, start_vectors(p.n, dim, 5), lo, hi, tau, L, 1e-8, 14)
+    exact = spectra.eigenvalues_in(p.cells, p.h, lo, hi)
+    assert len(must) >= 15 and len(th) >= len(must)
+    for t in th:
+        assert np.min(np.abs(exact - t)) <= 1e-10 * t
+    for t in must:
+        assert np.min(np.abs(th - t)) <= 1e-10 * t
