@@ -85,6 +85,10 @@ typedef struct kes_opts {
   void* alloc_user;
   int32_t stepper;     /* enum kes_stepper (default KES_STEPPER_LEAPFROG) */
   int32_t blk_variant; /* launch shape of the block (SpMM) step kernel when autotune is 0 */
+  int32_t compact_cols; /* 1 (default): the step kernels read each stored entry's column as the 16-bit
+                           difference column - row when every entry's fits (2 bytes instead of 4: tensor
+                           grids up to about 180 x 180 nodes per plane), else as int32; 0: always int32.
+                           Results are the same either way. The bulk-copy launch shapes read int32. */
 } kes_opts;
 
 /* Options of kes_krylov_solve. Initialise with kes_solve_opts_default(). */

@@ -59,7 +59,8 @@ class KesOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("sell_sigma", C.c_int32), ("use_graph", C.c_int32),
                 ("block_b", C.c_int32), ("autotune", C.c_int32), ("step_variant", C.c_int32),
                 ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
-                ("alloc_user", C.c_void_p), ("stepper", C.c_int32), ("blk_variant", C.c_int32)]
+                ("alloc_user", C.c_void_p), ("stepper", C.c_int32), ("blk_variant", C.c_int32),
+                ("compact_cols", C.c_int32)]
 
 
 class KesSolveOpts(C.Structure):
@@ -442,8 +443,10 @@ class Context:
 
     def __init__(self, problem, precision: str = "fp64", sell_sigma: int = 1, use_graph: bool = True,
                  block_b: int = 1, stream=None, torch_alloc: bool = False, autotune: bool = True,
-                 step_variant: int | None = None, stepper: str = "leapfrog", blk_variant: int | None = None):
+                 step_variant: int | None = None, stepper: str = "leapfrog", blk_variant: int | None = None,
+                 compact_cols: bool = True):
         o = kes_opts_default()
+        o.compact_cols = 1 if compact_cols else 0
         o.stepper = {"leapfrog": KES_STEPPER_LEAPFROG, "leapfrog4": KES_STEPPER_LEAPFROG4}[stepper]
         o.autotune = 1 if (autotune and step_variant is None and blk_variant is None) else 0
         o.step_variant = step_variant or 0

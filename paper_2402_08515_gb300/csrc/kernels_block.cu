@@ -111,6 +111,35 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
   t = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
 }
 
+__device__ __forceinline__ int32_t ld_idx(const int32_t* p) { return __ldcs(p); }
+__device__ __forceinline__ int32_t ld_idx(const int16_t* p) { return __ldcs(reinterpret_cast<const short*>(p)); }
+
+// un[j] += sum_k v[32k] * g[col_k * NB + co + j], j < NH, over the w entries of a row, in
+// entry order; col_k = base + c[32k] (absolute int32 columns with base 0, or the 16-bit
+// column - row differences with base = row). Two entries' loads are issued together.
+template <typename T, int NB, int NH, typename I>
+__device__ __forceinline__ void row_sums(T (&un)[NH], const T* __restrict__ vp, const I* __restrict__ cp, int base,
+                                         int w, const T* __restrict__ g, int co) {
+  int k = 0;
+  for (; k + 2 <= w; k += 2) {
+    const int32_t c0 = base + ld_idx(cp + k * kSliceC), c1 = base + ld_idx(cp + (k + 1) * kSliceC);
+    const T v0 = ld_cs(vp + k * kSliceC), v1 = ld_cs(vp + (k + 1) * kSliceC);
+    T x0[NH], x1[NH];
+    load_row<NH>(g + static_cast<int64_t>(c0) * NB + co, x0);
+    load_row<NH>(g + static_cast<int64_t>(c1) * NB + co, x1);
+#pragma unroll
+    for (int j = 0; j < NH; ++j) un[j] = fma(v1, x1[j], fma(v0, x0[j], un[j]));
+  }
+  if (k < w) {
+    const int32_t c0 = base + ld_idx(cp + k * kSliceC);
+    const T v0 = ld_cs(vp + k * kSliceC);
+    T x0[NH];
+    load_row<NH>(g + static_cast<int64_t>(c0) * NB + co, x0);
+#pragma unroll
+    for (int j = 0; j < NH; ++j) un[j] = fma(v0, x0[j], un[j]);
+  }
+}
+
 // g: the rows the sums gather from (x itself for the leapfrog, the fourth-order stage
 // otherwise); x seeds each row with 2 u_n - u_{n-1}.
 // LPR lanes share a row: LPR = 1 gives a lane a whole row of NB columns and a warp a
@@ -170,7 +199,6 @@ __global__ void __launch_bounds__(256, MINB)
     const int w = static_cast<int>((A.slice_ptr[s + 1] - beg) >> 5);
     const int64_t mesh = A.slice_mesh ? A.slice_mesh[s] : 0;
     const T* vp = val + beg + rs;
-    const int32_t* cp = A.col + beg + rs;
     const int64_t row = s * kSliceC + rs;
     const int64_t ro = row * NB + co;  // this lane's values in a row-major block
     T xi[NH], pi[NH], un[NH];
@@ -188,24 +216,8 @@ __global__ void __launch_bounds__(256, MINB)
       if constexpr (kF32) un[j] = __fsub_rn(__fmul_rn(2.0f, xi[j]), pi[j]);
       else un[j] = 2.0 * xi[j] - pi[j];
     }
-    int k = 0;
-    for (; k + 2 <= w; k += 2) {
-      const int32_t c0 = ld_cs(cp + k * kSliceC), c1 = ld_cs(cp + (k + 1) * kSliceC);
-      const T v0 = ld_cs(vp + k * kSliceC), v1 = ld_cs(vp + (k + 1) * kSliceC);
-      T x0[NH], x1[NH];
-      load_row<NH>(g + static_cast<int64_t>(c0) * NB + co, x0);
-      load_row<NH>(g + static_cast<int64_t>(c1) * NB + co, x1);
-#pragma unroll
-      for (int j = 0; j < NH; ++j) un[j] = fma(v1, x1[j], fma(v0, x0[j], un[j]));
-    }
-    if (k < w) {
-      const int32_t c0 = ld_cs(cp + k * kSliceC);
-      const T v0 = ld_cs(vp + k * kSliceC);
-      T x0[NH];
-      load_row<NH>(g + static_cast<int64_t>(c0) * NB + co, x0);
-#pragma unroll
-      for (int j = 0; j < NH; ++j) un[j] = fma(v0, x0[j], un[j]);
-    }
+    if (A.dcol) row_sums<T, NB, NH>(un, vp, A.dcol + beg + rs, static_cast<int>(row), w, g, co);
+    else row_sums<T, NB, NH>(un, vp, A.col + beg + rs, 0, w, g, co);
     if (!LAST) store_row<NH>(out + ro, un);
     bool bad = false;
     for (int f = 0; f < nacc; ++f) {
@@ -341,20 +353,12 @@ __global__ void __launch_bounds__(256) k_stage4(SellDev A, const T* __restrict__
     const int64_t beg = A.slice_ptr[s];
     const int w = static_cast<int>((A.slice_ptr[s + 1] - beg) >> 5);
     const T* vp = val + beg + lane;
-    const int32_t* cp = A.col + beg + lane;
     const int64_t row = s * kSliceC + lane;
     T acc[NB];
 #pragma unroll
     for (int j = 0; j < NB; ++j) acc[j] = T(0);
-    for (int k = 0; k < w; ++k) {
-      const int32_t c0 = ld_cs(cp + k * kSliceC);
-      const T a0 = ld_cs(vp + k * kSliceC);
-      T xr[NB];
-      if constexpr (NB == 1) xr[0] = __ldg(x + c0);
-      else load_row<NB>(x + static_cast<int64_t>(c0) * NB, xr);
-#pragma unroll
-      for (int j = 0; j < NB; ++j) acc[j] = fma(a0, xr[j], acc[j]);
-    }
+    if (A.dcol) row_sums<T, NB, NB>(acc, vp, A.dcol + beg + lane, static_cast<int>(row), w, x, 0);
+    else row_sums<T, NB, NB>(acc, vp, A.col + beg + lane, 0, w, x, 0);
     T xi[NB];
     if constexpr (NB == 1) xi[0] = x[row];
     else load_plain<NB>(x + row * NB, xi);

@@ -25,19 +25,22 @@ namespace {
 __device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
 __device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
 __device__ __forceinline__ int32_t ld_stream(const int32_t* p) { return __ldcs(p); }
+__device__ __forceinline__ int32_t ld_stream(const int16_t* p) { return __ldcs(reinterpret_cast<const short*>(p)); }
 
-// init + sum_k val[32k] * x[col[32k]] over the w entries of one lane's row, one FMA
+// init + sum_k val[32k] * x[col_k] over the w entries of one lane's row, one FMA
 // chain in entry order (every step kernel forms it the same way, so all launch
-// shapes round identically). Loads are issued BATCH entries at a time.
-template <typename T, int BATCH>
-__device__ __forceinline__ T row_dot(T acc, const T* __restrict__ v, const int32_t* __restrict__ c, int w,
+// shapes round identically). Loads are issued BATCH entries at a time. The column is
+// base + c[32k]: absolute int32 columns with base 0, or 16-bit column - row
+// differences with base = row (the compact index SellDev::dcol).
+template <typename T, int BATCH, typename I>
+__device__ __forceinline__ T row_dot(T acc, const T* __restrict__ v, const I* __restrict__ c, int base, int w,
                                      const T* __restrict__ x) {
   int k = 0;
   for (; k + BATCH <= w; k += BATCH) {
     int32_t cc[BATCH];
     T vv[BATCH], xx[BATCH];
 #pragma unroll
-    for (int j = 0; j < BATCH; ++j) cc[j] = ld_stream(c + (k + j) * kSliceC);
+    for (int j = 0; j < BATCH; ++j) cc[j] = base + ld_stream(c + (k + j) * kSliceC);
 #pragma unroll
     for (int j = 0; j < BATCH; ++j) vv[j] = ld_stream(v + (k + j) * kSliceC);
 #pragma unroll
@@ -50,7 +53,7 @@ __device__ __forceinline__ T row_dot(T acc, const T* __restrict__ v, const int32
     T vv[BATCH], xx[BATCH];
 #pragma unroll
     for (int j = 0; j < BATCH; ++j)
-      if (k + j < w) cc[j] = ld_stream(c + (k + j) * kSliceC);
+      if (k + j < w) cc[j] = base + ld_stream(c + (k + j) * kSliceC);
 #pragma unroll
     for (int j = 0; j < BATCH; ++j)
       if (k + j < w) vv[j] = ld_stream(v + (k + j) * kSliceC);
@@ -66,7 +69,9 @@ __device__ __forceinline__ T row_dot(T acc, const T* __restrict__ v, const int32
 
 // g is the vector the row sums gather from: u_n itself for the leapfrog, the stage
 // v = u_n + A u_n / 12 for the fourth-order scheme; x = u_n seeds the row (2 u_n - u_{n-1}).
-template <bool FIRST, bool LAST, int BATCH, int MINB>
+// IDX16: the row sums read the compact 16-bit column - row index (A.dcol) instead of the
+// int32 columns; one index form per instantiation keeps a single loop in the kernel.
+template <bool FIRST, bool LAST, int BATCH, int MINB, bool IDX16>
 __global__ void __launch_bounds__(256, MINB) k_step_f64(SellDev A, const double* __restrict__ x,
                                                   const double* __restrict__ g, const double* prev,
                                                   double* out, double* acc, int64_t acc_stride, int F,
@@ -82,7 +87,12 @@ __global__ void __launch_bounds__(256, MINB) k_step_f64(SellDev A, const double*
     const int64_t mesh = A.slice_mesh ? A.slice_mesh[s] : 0;
     const double xi = x[row];
     const double pi = FIRST ? xi : prev[row];
-    const double un = row_dot<double, BATCH>(2.0 * xi - pi, A.val64 + beg + lane, A.col + beg + lane, w, g);
+    const double seed = 2.0 * xi - pi;
+    double un;
+    if constexpr (IDX16)
+      un = row_dot<double, BATCH>(seed, A.val64 + beg + lane, A.dcol + beg + lane, static_cast<int>(row), w, g);
+    else
+      un = row_dot<double, BATCH>(seed, A.val64 + beg + lane, A.col + beg + lane, 0, w, g);
     if (!LAST) out[row] = un;
     bool bad = false;
     for (int f = 0; f < F; ++f) {
@@ -105,7 +115,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
   t = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
 }
 
-template <bool FIRST, bool LAST, int BATCH, int MINB>
+template <bool FIRST, bool LAST, int BATCH, int MINB, bool IDX16>
 __global__ void __launch_bounds__(256, MINB) k_step_f32(SellDev A, const float* __restrict__ x,
                                                   const float* __restrict__ g, const float* prev,
                                                   float* out, float* acc_s, float* acc_c, double* acc64,
@@ -122,8 +132,12 @@ __global__ void __launch_bounds__(256, MINB) k_step_f32(SellDev A, const float* 
     const int64_t mesh = A.slice_mesh ? A.slice_mesh[s] : 0;
     const float xi = x[row];
     const float pi = FIRST ? xi : prev[row];
-    const float un = row_dot<float, BATCH>(__fsub_rn(__fmul_rn(2.0f, xi), pi), A.val32 + beg + lane,
-                                           A.col + beg + lane, w, g);
+    const float seed = __fsub_rn(__fmul_rn(2.0f, xi), pi);
+    float un;
+    if constexpr (IDX16)
+      un = row_dot<float, BATCH>(seed, A.val32 + beg + lane, A.dcol + beg + lane, static_cast<int>(row), w, g);
+    else
+      un = row_dot<float, BATCH>(seed, A.val32 + beg + lane, A.col + beg + lane, 0, w, g);
     if (!LAST) out[row] = un;
     bool bad = false;
     for (int f = 0; f < F; ++f) {
@@ -180,7 +194,7 @@ __global__ void __launch_bounds__(256) k_spmv_f64(SellDev A, const double* __res
        s += nwarps) {
     const int64_t beg = A.slice_ptr[s];
     const int w = static_cast<int>((A.slice_ptr[s + 1] - beg) >> 5);
-    const double sum = row_dot<double, 8>(0.0, A.val64 + beg + lane, A.col + beg + lane, w, x);
+    const double sum = row_dot<double, 8>(0.0, A.val64 + beg + lane, A.col + beg + lane, 0, w, x);
     const int64_t row = s * kSliceC + lane;
     y[row] = dscale ? sum * dscale[row] : sum;
   }
@@ -228,10 +242,17 @@ void step_f64_impl(int grid, int block, cudaStream_t st, bool first, bool last, 
                    const double* g, const double* prev, double* out, double* acc, int64_t acc_stride, int F, const double* alpha,
                    int Lp1, int step, int* flag) {
 #define KES_F64_ARGS A, x, g, prev, out, acc, acc_stride, F, alpha, Lp1, step, flag
-  if (first && last) k_step_f64<true, true, BATCH, MINB><<<grid, block, 0, st>>>(KES_F64_ARGS);
-  else if (first) k_step_f64<true, false, BATCH, MINB><<<grid, block, 0, st>>>(KES_F64_ARGS);
-  else if (last) k_step_f64<false, true, BATCH, MINB><<<grid, block, 0, st>>>(KES_F64_ARGS);
-  else k_step_f64<false, false, BATCH, MINB><<<grid, block, 0, st>>>(KES_F64_ARGS);
+  if (A.dcol) {
+    if (first && last) k_step_f64<true, true, BATCH, MINB, true><<<grid, block, 0, st>>>(KES_F64_ARGS);
+    else if (first) k_step_f64<true, false, BATCH, MINB, true><<<grid, block, 0, st>>>(KES_F64_ARGS);
+    else if (last) k_step_f64<false, true, BATCH, MINB, true><<<grid, block, 0, st>>>(KES_F64_ARGS);
+    else k_step_f64<false, false, BATCH, MINB, true><<<grid, block, 0, st>>>(KES_F64_ARGS);
+  } else {
+    if (first && last) k_step_f64<true, true, BATCH, MINB, false><<<grid, block, 0, st>>>(KES_F64_ARGS);
+    else if (first) k_step_f64<true, false, BATCH, MINB, false><<<grid, block, 0, st>>>(KES_F64_ARGS);
+    else if (last) k_step_f64<false, true, BATCH, MINB, false><<<grid, block, 0, st>>>(KES_F64_ARGS);
+    else k_step_f64<false, false, BATCH, MINB, false><<<grid, block, 0, st>>>(KES_F64_ARGS);
+  }
 #undef KES_F64_ARGS
 }
 
@@ -240,10 +261,17 @@ void step_f32_impl(int grid, int block, cudaStream_t st, bool first, bool last, 
                    const float* g, const float* prev, float* out, float* acc_s, float* acc_c, double* acc64, int64_t acc_stride,
                    int F, const float* ahi, const float* alo, int Lp1, int step, int* flag) {
 #define KES_F32_ARGS A, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, F, ahi, alo, Lp1, step, flag
-  if (first && last) k_step_f32<true, true, BATCH, MINB><<<grid, block, 0, st>>>(KES_F32_ARGS);
-  else if (first) k_step_f32<true, false, BATCH, MINB><<<grid, block, 0, st>>>(KES_F32_ARGS);
-  else if (last) k_step_f32<false, true, BATCH, MINB><<<grid, block, 0, st>>>(KES_F32_ARGS);
-  else k_step_f32<false, false, BATCH, MINB><<<grid, block, 0, st>>>(KES_F32_ARGS);
+  if (A.dcol) {
+    if (first && last) k_step_f32<true, true, BATCH, MINB, true><<<grid, block, 0, st>>>(KES_F32_ARGS);
+    else if (first) k_step_f32<true, false, BATCH, MINB, true><<<grid, block, 0, st>>>(KES_F32_ARGS);
+    else if (last) k_step_f32<false, true, BATCH, MINB, true><<<grid, block, 0, st>>>(KES_F32_ARGS);
+    else k_step_f32<false, false, BATCH, MINB, true><<<grid, block, 0, st>>>(KES_F32_ARGS);
+  } else {
+    if (first && last) k_step_f32<true, true, BATCH, MINB, false><<<grid, block, 0, st>>>(KES_F32_ARGS);
+    else if (first) k_step_f32<true, false, BATCH, MINB, false><<<grid, block, 0, st>>>(KES_F32_ARGS);
+    else if (last) k_step_f32<false, true, BATCH, MINB, false><<<grid, block, 0, st>>>(KES_F32_ARGS);
+    else k_step_f32<false, false, BATCH, MINB, false><<<grid, block, 0, st>>>(KES_F32_ARGS);
+  }
 #undef KES_F32_ARGS
 }
 
@@ -289,8 +317,8 @@ int step_blocks_per_sm(bool fp32, int variant, int block) {
   switch (variant) {
 #define X(ID, B, M)                                                                                      \
   case ID:                                                                                               \
-    e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_f32<false, false, B, M>, block, 0) \
-             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_f64<false, false, B, M>, block, 0); \
+    e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_f32<false, false, B, M, true>, block, 0) \
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_f64<false, false, B, M, true>, block, 0); \
     break;
     KES_STEP_VARIANTS(X)
 #undef X

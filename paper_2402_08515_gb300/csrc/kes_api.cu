@@ -503,8 +503,9 @@ void tune_steps(kes_ctx* c) {
   int best = 0;
   float best_ms = 3.0e38f;
   for (int v = 0; v < step_variant_count(); ++v) {
-    // the fourth-order step gathers from its stage, which the bulk-copy shapes do not
-    if (c->opts.stepper == KES_STEPPER_LEAPFROG4 && v >= kRegStepVariants) continue;
+    // the fourth-order step gathers from its stage and the compact index is read only by
+    // the register-staged shapes: the bulk-copy shapes take part in neither
+    if ((c->opts.stepper == KES_STEPPER_LEAPFROG4 || c->A.dcol) && v >= kRegStepVariants) continue;
     if (!select_variant(c, v)) continue;
     const float ms = timed([&](int count) {
       for (int i = 0; i < count; ++i) {
@@ -639,6 +640,24 @@ void build_context(kes_ctx* c, int nm, const int64_t* n, const int64_t* const* r
   for (int64_t sl = 0; sl < n_slices; ++sl) wmax = std::max(wmax, (sp[sl + 1] - sp[sl]) / kSliceC);
   c->cfg.tma.wmax = static_cast<int>(wmax);
   sells.clear();
+  // compact index for the step kernels: column - row as 16 bits when every entry allows it
+  // (padding entries point at their own row: difference 0)
+  std::vector<int16_t> dcol;
+  if (c->opts.compact_cols) {
+    dcol.resize(nnz_pad);
+    bool fits = true;
+    for (int64_t sl = 0; sl < n_slices && fits; ++sl)
+      for (int64_t e = sp[sl]; e < sp[sl + 1]; ++e) {
+        const int64_t row = sl * kSliceC + (e - sp[sl]) % kSliceC;
+        const int64_t d = static_cast<int64_t>(cols[e]) - row;
+        if (d < -32767 || d > 32767) {
+          fits = false;
+          break;
+        }
+        dcol[e] = static_cast<int16_t>(d);
+      }
+    if (!fits) dcol.clear();
+  }
   int64_t* d_sp = c->dalloc_n<int64_t>(n_slices + 1);
   int32_t* d_col = c->dalloc_n<int32_t>(nnz_pad);
   double* d_val = c->dalloc_n<double>(nnz_pad);
@@ -650,6 +669,11 @@ void build_context(kes_ctx* c, int nm, const int64_t* n, const int64_t* const* r
   c->A.n_slices = n_slices;
   c->A.slice_ptr = d_sp;
   c->A.col = d_col;
+  if (!dcol.empty()) {
+    int16_t* d_dcol = c->dalloc_n<int16_t>(nnz_pad);
+    KES_CUDA(cudaMemcpyAsync(d_dcol, dcol.data(), nnz_pad * sizeof(int16_t), cudaMemcpyHostToDevice, c->stream));
+    c->A.dcol = d_dcol;
+  }
   c->A.val64 = d_val;  // FP64 values are always kept: the Krylov basis needs S b_k in FP64
   if (c->opts.precision == KES_PREC_FP32) {
     std::vector<float> v32(vals.begin(), vals.end());
@@ -1494,6 +1518,7 @@ void kes_opts_default(kes_opts* o) {
   o->use_graph = 1;
   o->block_b = 1;
   o->autotune = 1;
+  o->compact_cols = 1;
 }
 
 void kes_solve_opts_default(kes_solve_opts* o) {
@@ -1555,9 +1580,11 @@ int64_t kes_step_bytes(const kes_ctx* c, int32_t b, int32_t F) {
   // row pointer per row as CSR would need; per row and vector: the gather of u_n once,
   // u_{n-1} read, u_{n+1} written, F accumulators read and written (FP32 form: s and c).
   // The fourth-order stepper adds a stage pass (matrix and row pointers again, u_n gathered,
-  // the stage written) and the step reads the stage (gathered) besides u_n.
+  // the stage written) and the step reads the stage (gathered) besides u_n. With the
+  // compact index a stored entry's column takes 2 bytes instead of 4.
   const int64_t vs = c->opts.precision == KES_PREC_FP64 ? 8 : 4;
-  const int64_t mat = (vs + 4) * c->nnz + 4 * (c->n + 1);
+  const int64_t is = c->A.dcol ? 2 : 4;
+  const int64_t mat = (vs + is) * c->nnz + 4 * (c->n + 1);
   const int64_t step = mat + c->n * int64_t(b) * (3 * vs + 16 * F);
   if (c->opts.stepper == KES_STEPPER_LEAPFROG4) return step + mat + c->n * int64_t(b) * (3 * vs);
   return step;

@@ -44,6 +44,9 @@ struct SellDev {
   int64_t n = 0, n_pad = 0, n_slices = 0;
   const int64_t* slice_ptr = nullptr;
   const int32_t* col = nullptr;
+  // compact index of the step kernels: column - row of every stored entry as 16 bits,
+  // when all of them fit (null otherwise); the same columns as `col`
+  const int16_t* dcol = nullptr;
   const double* val64 = nullptr;
   const float* val32 = nullptr;
   // mesh of each slice when several meshes are stacked block-diagonally (null: one mesh).

@@ -455,3 +455,25 @@ def test_subspace_solve_matches_oracle(precision):
         assert res["n_pairs"] >= len(th) - 3
     for t, x in zip(res["omega2"], res["vectors"]):
         assert np.linalg.norm(S @ x - t * p.m * x) <= tol * 1.01 * t * np.linalg.norm(p.m * x)
+
+
+# ---------------------------------------------------------------- compact column index
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("b,stepper", [(1, "leapfrog"), (4, "leapfrog"), (1, "leapfrog4"), (4, "leapfrog4")])
+def test_compact_column_index_rounds_identically(meshes, precision, b, stepper):
+    # the 16-bit column - row index names the same columns as the int32 one: the filtered
+    # blocks agree bit for bit, and the step moves 2 bytes less per stored entry
+    p = meshes[1]
+    tau = _tau4(p) if stepper == "leapfrog4" else _tau(p)
+    R = start_vectors(p.n, b, 61)
+    outs, steps = [], []
+    for compact in (False, True):
+        with K.Context(p, precision=precision, block_b=b, stepper=stepper, compact_cols=compact) as c:
+            K.kes_set_filter(c.handle, 6.0, 10.0, tau, 40)
+            o = np.zeros((1, b, p.n))
+            K.kes_filter_apply(c.handle, R, o, b)
+            outs.append(o)
+            steps.append(K.kes_step_bytes(c.handle, 1, 1))
+    np.testing.assert_array_equal(outs[0], outs[1])
+    assert steps[1] == steps[0] - 2 * p.nnz * (2 if stepper == "leapfrog4" else 1)
