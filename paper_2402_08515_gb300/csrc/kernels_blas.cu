@@ -304,7 +304,10 @@ __global__ void k_scale_jobs(const ScaleJob* __restrict__ jobs) {
 
 }  // namespace
 
-int dot_blocks(int64_t n) { return rows_grid(n, kDotBlocks); }
+// Row blocks of the batched inner products: about 64 rows per thread, so that a block's
+// final reduction (8 sums over 256 threads) stays small next to its FMAs; at most
+// kDotBlocks per column group.
+int dot_blocks(int64_t n) { return rows_grid((n + 63) / 64, kDotBlocks); }
 int gemv_blocks(int64_t n) { return rows_grid(n, 2048); }
 
 void launch_mdot_jobs(cudaStream_t st, const DotJob* jobs, int njobs, int max_k, int64_t total_blocks,

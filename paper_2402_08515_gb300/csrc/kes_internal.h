@@ -196,7 +196,7 @@ struct ScaleJob {      // dst = v / sqrt(nrm2[0])
   double* dst;
   int64_t n;
 };
-int dot_blocks(int64_t n);   // row blocks of launch_mdot for n rows
+int dot_blocks(int64_t n);   // row blocks of a batched inner-product job over n rows
 int gemv_blocks(int64_t n);  // row blocks of launch_gemv_sub for n rows
 // total_blocks: sum of dot_job_blocks / gemv_job_blocks over the jobs, whose `first` fields
 // hold the prefix sums in job order.
