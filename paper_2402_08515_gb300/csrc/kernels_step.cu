@@ -235,7 +235,7 @@ int grid_for(const LaunchCfg& cfg, int64_t n_slices) {
 // (An L2 prefetch of each warp's next slice was measured as well: 8-50% slower on the
 // 128^3 cube in every shape, so it is not offered.)
 #define KES_STEP_VARIANTS(X) \
-  X(0, 8, 1) X(1, 8, 3) X(2, 8, 4) X(3, 4, 4) X(4, 4, 5) X(5, 4, 6) X(6, 2, 6) X(7, 2, 8) X(8, 16, 2) X(9, 16, 3)
+  X(0, 8, 1) X(1, 8, 3) X(2, 8, 4) X(3, 4, 4) X(4, 4, 5) X(5, 4, 6) X(6, 2, 6) X(7, 2, 8)
 
 template <int BATCH, int MINB>
 void step_f64_impl(int grid, int block, cudaStream_t st, bool first, bool last, const SellDev& A, const double* x,
@@ -286,7 +286,7 @@ int step_variant_count() {
 #define X(ID, B, M) ++n;
   KES_STEP_VARIANTS(X)
 #undef X
-  static_assert(kRegStepVariants == 10, "register-staged variant count");
+  static_assert(kRegStepVariants == 8, "register-staged variant count");
 #define X(ID, G, S, C) ++n;
   KES_TMA_SHAPES(X)
 #undef X

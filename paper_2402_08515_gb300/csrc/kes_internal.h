@@ -133,7 +133,7 @@ void launch_unpack_block(cudaStream_t st, const double* stage, int NB, double* W
 // register cap) and the resident blocks per SM of one variant (occupancy calculator);
 // the step grid is n_sm * that, so that the grid-stride loop runs in one wave.
 // Variants 0 .. kRegStepVariants-1 stage the matrix in registers; the TMA shapes follow.
-constexpr int kRegStepVariants = 10;
+constexpr int kRegStepVariants = 8;
 int step_variant_count();
 int step_blocks_per_sm(bool fp32, int variant, int block);
 TmaShape tma_variant_shape(int variant, int wmax);  // variant >= kRegStepVariants
