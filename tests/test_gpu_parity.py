@@ -242,3 +242,46 @@ def test_every_step_launch_shape_rounds_identically(problems, precision):
     assert len(outs) >= 10
     for o in outs[1:]:
         np.testing.assert_array_equal(o, outs[0])
+
+
+def _long_range_chain(n=70000, reach=40000, seed=3):
+    """A weighted path graph with extra couplings i <-> i + reach (|col - row| beyond 16
+    bits), as a graph Laplacian plus a diagonal shift: symmetric positive definite."""
+    import scipy.sparse as sp
+    from fe_inputs import Problem
+    rng = np.random.default_rng(seed)
+    i = np.arange(n - 1)
+    j = np.arange(n - reach)
+    rows = np.concatenate([i, j])
+    cols = np.concatenate([i + 1, j + reach])
+    w = rng.uniform(0.5, 1.5, rows.size)
+    A = sp.coo_matrix((w, (rows, cols)), shape=(n, n)).tocsr()
+    A = A + A.T
+    L = (sp.diags(np.asarray(A.sum(axis=1)).ravel() + 0.1) - A).tocsr()
+    L.sort_indices()
+    return Problem("long_range_chain", n, L.indptr.astype(np.int64), L.indices.astype(np.int32),
+                   L.data.astype(np.float64), rng.uniform(0.5, 2.0, n))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_wide_matrix_keeps_int32_columns_and_matches_oracle(precision):
+    # differences column - row beyond 16 bits: the context keeps int32 columns (the step
+    # bytes count 4 per entry with compact_cols on or off) and the filter matches the oracle
+    p = _long_range_chain()
+    S = p.to_scipy()
+    tau = 0.9 * 2 / O.power_iteration(S, p.m, start_vectors(p.n, 1, 0)[0], 200)
+    L = 30
+    alpha = O.alpha_table(0.2, 0.6, tau, L)
+    r = start_vectors(p.n, 1, 4)
+    ref = O.filter_apply(S, p.m, r[0], tau, alpha)
+    outs, steps = [], []
+    for compact in (True, False):
+        with K.Context(p, precision=precision, compact_cols=compact) as c:
+            K.kes_set_filter(c.handle, 0.2, 0.6, tau, L)
+            o = np.zeros((1, 1, p.n))
+            K.kes_filter_apply(c.handle, r, o, 1)
+            outs.append(o)
+            steps.append(K.kes_step_bytes(c.handle, 1, 1))
+    assert steps[0] == steps[1]
+    np.testing.assert_array_equal(outs[0], outs[1])
+    assert filter_error(outs[0][0], ref, r, p.m, alpha) <= filter_tol(L, precision)
