@@ -253,8 +253,9 @@ kes_status kes_sym_eig(int32_t k, const double* A, double* w, double* V);
    (kes_opts.step_variant) and of the block step kernel (kes_opts.blk_variant). */
 void kes_launch_shapes(int32_t* n_step, int32_t* n_block);
 /* kes_step_bytes: algorithmic HBM bytes of one fused leapfrog step of this context for b vectors
-   and F intervals (every matrix entry, row pointer and per-row vector read or written once; the
-   fourth-order stepper adds its stage pass and the read of the stage). */
+   and F intervals (every matrix entry, row pointer and per-row vector read or written once; an
+   entry is its value plus a 2-byte column difference when the compact index is in use, else a
+   4-byte column; the fourth-order stepper adds its stage pass and the read of the stage). */
 int64_t kes_step_bytes(const kes_ctx* ctx, int32_t b, int32_t F);
 
 /*
