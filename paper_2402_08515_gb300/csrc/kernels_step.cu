@@ -69,9 +69,48 @@ __device__ __forceinline__ T row_dot(T acc, const T* __restrict__ v, const I* __
 
 // g is the vector the row sums gather from: u_n itself for the leapfrog, the stage
 // v = u_n + A u_n / 12 for the fourth-order scheme; x = u_n seeds the row (2 u_n - u_{n-1}).
-// IDX16: the row sums read the compact 16-bit column - row index (A.dcol) instead of the
-// int32 columns; one index form per instantiation keeps a single loop in the kernel.
-template <bool FIRST, bool LAST, int BATCH, int MINB, bool IDX16>
+// The same sum over the pair layout: pair p of the lane holds entries 2p and 2p+1 (one
+// float2 / double2 of values, one 32-bit word of two 16-bit column differences, low half first),
+// NP pairs' loads issued together; the chain is still in entry order.
+template <typename T> struct Pair2;
+template <> struct Pair2<float> { using type = float2; };
+template <> struct Pair2<double> { using type = double2; };
+
+template <typename T, int NP>
+__device__ __forceinline__ T row_dot_pairs(T acc, const typename Pair2<T>::type* __restrict__ v,
+                                           const int32_t* __restrict__ c, int row, int wp, const T* __restrict__ x) {
+  using T2 = typename Pair2<T>::type;
+  int k = 0;
+  for (; k + NP <= wp; k += NP) {
+    int32_t cc[NP];
+    T2 vv[NP];
+    T xa[NP], xb[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) cc[j] = __ldcs(c + (k + j) * kSliceC);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) vv[j] = __ldcs(v + (k + j) * kSliceC);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      xa[j] = __ldg(x + row + static_cast<int16_t>(cc[j] & 0xffff));
+      xb[j] = __ldg(x + row + (cc[j] >> 16));
+    }
+#pragma unroll
+    for (int j = 0; j < NP; ++j) acc = fma(vv[j].y, xb[j], fma(vv[j].x, xa[j], acc));
+  }
+  for (; k < wp; ++k) {
+    const int32_t c0 = __ldcs(c + k * kSliceC);
+    const T2 v0 = __ldcs(v + k * kSliceC);
+    const T a = __ldg(x + row + static_cast<int16_t>(c0 & 0xffff));
+    const T b = __ldg(x + row + (c0 >> 16));
+    acc = fma(v0.y, b, fma(v0.x, a, acc));
+  }
+  return acc;
+}
+
+// IDX: how the row sums read columns: 0 the int32 columns, 1 the compact 16-bit column -
+// row differences (A.dcol), 2 the pair layout (A.val64p, A.dcolp); one form per
+// instantiation keeps a single loop in the kernel.
+template <bool FIRST, bool LAST, int BATCH, int MINB, int IDX>
 __global__ void __launch_bounds__(256, MINB) k_step_f64(SellDev A, const double* __restrict__ x,
                                                   const double* __restrict__ g, const double* prev,
                                                   double* out, double* acc, int64_t acc_stride, int F,
@@ -89,10 +128,17 @@ __global__ void __launch_bounds__(256, MINB) k_step_f64(SellDev A, const double*
     const double pi = FIRST ? xi : prev[row];
     const double seed = 2.0 * xi - pi;
     double un;
-    if constexpr (IDX16)
+    if constexpr (IDX == 2) {
+      const int64_t b2 = A.slice_ptr2[s];
+      const int wp = static_cast<int>((A.slice_ptr2[s + 1] - b2) >> 6);
+      un = row_dot_pairs<double, (BATCH >= 2 ? BATCH / 2 : 1)>(
+          seed, reinterpret_cast<const double2*>(A.val64p + b2) + lane,
+          reinterpret_cast<const int32_t*>(A.dcolp + b2) + lane, static_cast<int>(row), wp, g);
+    } else if constexpr (IDX == 1) {
       un = row_dot<double, BATCH>(seed, A.val64 + beg + lane, A.dcol + beg + lane, static_cast<int>(row), w, g);
-    else
+    } else {
       un = row_dot<double, BATCH>(seed, A.val64 + beg + lane, A.col + beg + lane, 0, w, g);
+    }
     if (!LAST) out[row] = un;
     bool bad = false;
     for (int f = 0; f < F; ++f) {
@@ -113,39 +159,6 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
   const float bp = __fsub_rn(s, a);
   const float ap = __fsub_rn(s, bp);
   t = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
-}
-
-// The same sum over the pair layout: pair p of the lane holds entries 2p and 2p+1 (one
-// float2 of values, one 32-bit word of two 16-bit column differences, low half first),
-// NP pairs' loads issued together; the chain is still in entry order.
-template <int NP>
-__device__ __forceinline__ float row_dot_pairs(float acc, const float2* __restrict__ v, const int32_t* __restrict__ c,
-                                               int row, int wp, const float* __restrict__ x) {
-  int k = 0;
-  for (; k + NP <= wp; k += NP) {
-    int32_t cc[NP];
-    float2 vv[NP];
-    float xa[NP], xb[NP];
-#pragma unroll
-    for (int j = 0; j < NP; ++j) cc[j] = __ldcs(c + (k + j) * kSliceC);
-#pragma unroll
-    for (int j = 0; j < NP; ++j) vv[j] = __ldcs(v + (k + j) * kSliceC);
-#pragma unroll
-    for (int j = 0; j < NP; ++j) {
-      xa[j] = __ldg(x + row + static_cast<int16_t>(cc[j] & 0xffff));
-      xb[j] = __ldg(x + row + (cc[j] >> 16));
-    }
-#pragma unroll
-    for (int j = 0; j < NP; ++j) acc = fmaf(vv[j].y, xb[j], fmaf(vv[j].x, xa[j], acc));
-  }
-  for (; k < wp; ++k) {
-    const int32_t c0 = __ldcs(c + k * kSliceC);
-    const float2 v0 = __ldcs(v + k * kSliceC);
-    const float a = __ldg(x + row + static_cast<int16_t>(c0 & 0xffff));
-    const float b = __ldg(x + row + (c0 >> 16));
-    acc = fmaf(v0.y, b, fmaf(v0.x, a, acc));
-  }
-  return acc;
 }
 
 // IDX: 0 int32 columns, 1 the compact 16-bit differences, 2 the pair layout.
@@ -171,7 +184,7 @@ __global__ void __launch_bounds__(256, MINB) k_step_f32(SellDev A, const float* 
     if constexpr (IDX == 2) {
       const int64_t b2 = A.slice_ptr2[s];
       const int wp = static_cast<int>((A.slice_ptr2[s + 1] - b2) >> 6);
-      un = row_dot_pairs<(BATCH >= 2 ? BATCH / 2 : 1)>(
+      un = row_dot_pairs<float, (BATCH >= 2 ? BATCH / 2 : 1)>(
           seed, reinterpret_cast<const float2*>(A.val32p + b2) + lane,
           reinterpret_cast<const int32_t*>(A.dcolp + b2) + lane, static_cast<int>(row), wp, g);
     } else if constexpr (IDX == 1) {
@@ -242,10 +255,11 @@ __global__ void __launch_bounds__(256) k_spmv_f64(SellDev A, const double* __res
 }
 
 // A = -tau^2 M^{-1} S in the SELL layout: out[e] = -tau2m[row(e)] * val64[e]
-// (out32p: the same FP32 values in the pair layout of A.slice_ptr2; its padding entries
-// keep the zeros they were allocated with.)
+// (out64p / out32p: the same values in the pair layout of A.slice_ptr2; their padding
+// entries keep the zeros they were allocated with.)
 __global__ void k_scale_values(SellDev A, const double* __restrict__ tau2m, double* __restrict__ out64,
-                               float* __restrict__ out32, float* __restrict__ out32p) {
+                               float* __restrict__ out32, double* __restrict__ out64p,
+                               float* __restrict__ out32p) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
   for (int64_t s = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; s < A.n_slices;
@@ -257,7 +271,9 @@ __global__ void k_scale_values(SellDev A, const double* __restrict__ tau2m, doub
       const double a = t * A.val64[e];
       if (out64) out64[e] = a;
       if (out32) out32[e] = static_cast<float>(a);
-      if (out32p) out32p[A.slice_ptr2[s] + 64 * (k >> 1) + 2 * lane + (k & 1)] = static_cast<float>(a);
+      const int64_t p2 = A.slice_ptr2 ? A.slice_ptr2[s] + 64 * (k >> 1) + 2 * lane + (k & 1) : 0;
+      if (out64p) out64p[p2] = a;
+      if (out32p) out32p[p2] = static_cast<float>(a);
     }
   }
 }
@@ -287,17 +303,19 @@ void step_f64_impl(int grid, int block, cudaStream_t st, bool first, bool last, 
                    const double* g, const double* prev, double* out, double* acc, int64_t acc_stride, int F, const double* alpha,
                    int Lp1, int step, int* flag) {
 #define KES_F64_ARGS A, x, g, prev, out, acc, acc_stride, F, alpha, Lp1, step, flag
-  if (A.dcol) {
-    if (first && last) k_step_f64<true, true, BATCH, MINB, true><<<grid, block, 0, st>>>(KES_F64_ARGS);
-    else if (first) k_step_f64<true, false, BATCH, MINB, true><<<grid, block, 0, st>>>(KES_F64_ARGS);
-    else if (last) k_step_f64<false, true, BATCH, MINB, true><<<grid, block, 0, st>>>(KES_F64_ARGS);
-    else k_step_f64<false, false, BATCH, MINB, true><<<grid, block, 0, st>>>(KES_F64_ARGS);
+#define KES_F64_LAUNCH(I)                                                                        \
+  if (first && last) k_step_f64<true, true, BATCH, MINB, I><<<grid, block, 0, st>>>(KES_F64_ARGS);    \
+  else if (first) k_step_f64<true, false, BATCH, MINB, I><<<grid, block, 0, st>>>(KES_F64_ARGS);      \
+  else if (last) k_step_f64<false, true, BATCH, MINB, I><<<grid, block, 0, st>>>(KES_F64_ARGS);       \
+  else k_step_f64<false, false, BATCH, MINB, I><<<grid, block, 0, st>>>(KES_F64_ARGS);
+  if (A.val64p) {
+    KES_F64_LAUNCH(2)
+  } else if (A.dcol) {
+    KES_F64_LAUNCH(1)
   } else {
-    if (first && last) k_step_f64<true, true, BATCH, MINB, false><<<grid, block, 0, st>>>(KES_F64_ARGS);
-    else if (first) k_step_f64<true, false, BATCH, MINB, false><<<grid, block, 0, st>>>(KES_F64_ARGS);
-    else if (last) k_step_f64<false, true, BATCH, MINB, false><<<grid, block, 0, st>>>(KES_F64_ARGS);
-    else k_step_f64<false, false, BATCH, MINB, false><<<grid, block, 0, st>>>(KES_F64_ARGS);
+    KES_F64_LAUNCH(0)
   }
+#undef KES_F64_LAUNCH
 #undef KES_F64_ARGS
 }
 
@@ -365,7 +383,7 @@ int step_blocks_per_sm(bool fp32, int variant, int block) {
 #define X(ID, B, M)                                                                                      \
   case ID:                                                                                               \
     e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_f32<false, false, B, M, 2>, block, 0) \
-             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_f64<false, false, B, M, true>, block, 0); \
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_f64<false, false, B, M, 2>, block, 0); \
     break;
     KES_STEP_VARIANTS(X)
 #undef X
@@ -450,8 +468,8 @@ void launch_spmv_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, co
 }
 
 void launch_scale_values(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, const double* tau2m,
-                         double* out64, float* out32, float* out32p) {
-  k_scale_values<<<grid_for(cfg, A.n_slices), cfg.block_step, 0, st>>>(A, tau2m, out64, out32, out32p);
+                         double* out64, float* out32, double* out64p, float* out32p) {
+  k_scale_values<<<grid_for(cfg, A.n_slices), cfg.block_step, 0, st>>>(A, tau2m, out64, out32, out64p, out32p);
   ++g_launches;
 }
 

@@ -107,12 +107,14 @@ struct kes_ctx {
   double* minv64 = nullptr;       // 1 / m
   double* tau2m64 = nullptr;      // tau^2 / m with the tau of the row's mesh
   double* step64 = nullptr;       // A = -tau^2 M^{-1} S, SELL layout (FP64 steps)
+  double* step64p = nullptr;      // the same in the pair layout (A.slice_ptr2), FP64 contexts
   float* step32 = nullptr;        // the same in FP32 (FP32 steps)
   float* step32p = nullptr;       // the FP32 ones in the pair layout (A.slice_ptr2), if built
   int64_t nnz_pair = 0;           // entries of the pair layout (with its padding)
   SellDev step_A64() const {
     SellDev a = A;
     a.val64 = step64;
+    a.val64p = step64p;
     return a;
   }
   SellDev step_A32() const {
@@ -342,7 +344,7 @@ void ensure_fp64_state(kes_ctx* c) {
     for (int j = 0; j < 2; ++j) c->U64[j] = c->dzero_n<double>(c->n_pad * c->NBcap);
   if (!c->step64) {
     c->step64 = c->dzero_n<double>(c->nnz_pad);
-    launch_scale_values(c->A, c->cfg, c->stream, c->tau2m64, c->step64, nullptr, nullptr);
+    launch_scale_values(c->A, c->cfg, c->stream, c->tau2m64, c->step64, nullptr, nullptr, nullptr);
     KES_CHECK_LAUNCH();
   }
 }
@@ -676,8 +678,8 @@ void build_context(kes_ctx* c, int nm, const int64_t* n, const int64_t* const* r
     int16_t* d_dcol = c->dalloc_n<int16_t>(nnz_pad);
     KES_CUDA(cudaMemcpyAsync(d_dcol, dcol.data(), nnz_pad * sizeof(int16_t), cudaMemcpyHostToDevice, c->stream));
     c->A.dcol = d_dcol;
-    if (c->opts.precision == KES_PREC_FP32) {
-      // pair layout for the FP32 single-vector step: entry k of lane l of slice s at
+    {
+      // pair layout for the single-vector steps: entry k of lane l of slice s at
       // sp2[s] + 64 (k / 2) + 2 l + k % 2, odd widths padded with a zero entry per lane
       std::vector<int64_t> sp2(n_slices + 1, 0);
       for (int64_t sl = 0; sl < n_slices; ++sl) {
@@ -772,6 +774,7 @@ kes_status create_impl(kes_ctx** out, int32_t nm, const int64_t* n, const int64_
       for (int j = 0; j < 3; ++j) c->U32[j] = c->dzero_n<float>(np * nb);
     } else {
       c->step64 = c->dzero_n<double>(c->nnz_pad);
+      if (c->A.slice_ptr2) c->step64p = c->dzero_n<double>(c->nnz_pair);  // padding stays zero
       for (int j = 0; j < 2; ++j) c->U64[j] = c->dzero_n<double>(np * nb);
     }
     c->stage_in = c->dzero_n<double>(np * nb);
@@ -863,7 +866,7 @@ kes_status set_weights_impl(kes_ctx* c, int32_t F, const double* alpha, const do
     KES_CUDA(cudaMemcpyAsync(c->tau2m64, t2m.data(), c->n_pad * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     // step values A = -tau^2 M^{-1} S (the FP32 ones rounded once from the FP64 product)
     if (c->step64 || c->step32)
-      launch_scale_values(c->A, c->cfg, c->stream, c->tau2m64, c->step64, c->step32, c->step32p);
+      launch_scale_values(c->A, c->cfg, c->stream, c->tau2m64, c->step64, c->step32, c->step64p, c->step32p);
     KES_CHECK_LAUNCH();
     ensure_stage_out(c, F);
     c->sync();

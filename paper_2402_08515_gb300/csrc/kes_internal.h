@@ -47,11 +47,12 @@ struct SellDev {
   // compact index of the step kernels: column - row of every stored entry as 16 bits,
   // when all of them fit (null otherwise); the same columns as `col`
   const int16_t* dcol = nullptr;
-  // pair layout of the FP32 single-vector step: a lane's entries 2k and 2k+1 adjacent, at
+  // pair layout of the single-vector steps: a lane's entries 2k and 2k+1 adjacent, at
   // slice_ptr2[s] + 64 (k / 2) + 2 lane + k % 2, odd slice widths padded with one zero entry
-  // per lane (difference 0); values val32p, differences dcolp. Null where not built.
+  // per lane (difference 0); values val32p / val64p, differences dcolp. Null where not built.
   const int64_t* slice_ptr2 = nullptr;
   const float* val32p = nullptr;
+  const double* val64p = nullptr;
   const int16_t* dcolp = nullptr;
   const double* val64 = nullptr;
   const float* val32 = nullptr;
@@ -158,7 +159,8 @@ void launch_step_tma_f32(const SellDev& A, const TmaShape& sh, int n_sm, cudaStr
 // Step values A = -tau^2 M^{-1} S from the values of S (A.val64) and tau^2/m per row:
 // out64[e] = -tau2m[row(e)] * val64[e] and/or out32[e] = (float) of the same (either may be null).
 void launch_scale_values(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, const double* tau2m,
-                         double* out64, float* out32, float* out32p);  // out32p: pair layout (A.slice_ptr2)
+                         double* out64, float* out32, double* out64p,
+                         float* out32p);  // out64p / out32p: pair layout (A.slice_ptr2)
 
 // y = dscale .* (S x) (dscale may be null) in FP64.
 void launch_spmv_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, const double* x,
