@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(256, MINB)
 #pragma unroll
     for (int j = 0; j < NH; ++j) {
       if constexpr (kF32) un[j] = __fsub_rn(__fmul_rn(2.0f, xi[j]), pi[j]);
-      else un[j] = 2.0 * xi[j] - pi[j];
+      else un[j] = A.fold2 ? -pi[j] : 2.0 * xi[j] - pi[j];  // A.fold2: 2 x_j is in the diagonal
     }
     if (A.dcol) row_sums<T, NB, NH>(un, vp, A.dcol + beg + rs, static_cast<int>(row), w, g, co);
     else row_sums<T, NB, NH>(un, vp, A.col + beg + rs, 0, w, g, co);

@@ -71,15 +71,17 @@ __device__ __forceinline__ T row_dot(T acc, const T* __restrict__ v, const I* __
 // v = u_n + A u_n / 12 for the fourth-order scheme; x = u_n seeds the row (2 u_n - u_{n-1}).
 // The same sum over the pair layout: pair p of the lane holds entries 2p and 2p+1 (one
 // float2 / double2 of values, one 32-bit word of two 16-bit column differences, low half first),
-// NP pairs' loads issued together; the chain is still in entry order.
+// NP pairs' loads issued together; the chain is still in entry order. w is the row's
+// number of entries: for odd w the last pair's second entry is padding and is skipped.
 template <typename T> struct Pair2;
 template <> struct Pair2<float> { using type = float2; };
 template <> struct Pair2<double> { using type = double2; };
 
 template <typename T, int NP>
 __device__ __forceinline__ T row_dot_pairs(T acc, const typename Pair2<T>::type* __restrict__ v,
-                                           const int32_t* __restrict__ c, int row, int wp, const T* __restrict__ x) {
+                                           const int32_t* __restrict__ c, int row, int w, const T* __restrict__ x) {
   using T2 = typename Pair2<T>::type;
+  const int wp = w >> 1;  // full pairs
   int k = 0;
   for (; k + NP <= wp; k += NP) {
     int32_t cc[NP];
@@ -104,12 +106,20 @@ __device__ __forceinline__ T row_dot_pairs(T acc, const typename Pair2<T>::type*
     const T b = __ldg(x + row + (c0 >> 16));
     acc = fma(v0.y, b, fma(v0.x, a, acc));
   }
+  if (w & 1) {
+    const int32_t c0 = __ldcs(c + wp * kSliceC);
+    const T2 v0 = __ldcs(v + wp * kSliceC);
+    acc = fma(v0.x, __ldg(x + row + static_cast<int16_t>(c0 & 0xffff)), acc);
+  }
   return acc;
 }
 
 // IDX: how the row sums read columns: 0 the int32 columns, 1 the compact 16-bit column -
 // row differences (A.dcol), 2 the pair layout (A.val64p, A.dcolp); one form per
-// instantiation keeps a single loop in the kernel.
+// instantiation keeps a single loop in the kernel. With A.fold2 the values hold A + 2I (the
+// 2 u_n of eq. 2stepmethod folded into the diagonal; only for the leapfrog, where g = x) and
+// the row seeds with -u_{n-1} alone: one FP64 operation less per row. The pair values are
+// built only in that form, so IDX 2 implies it.
 template <bool FIRST, bool LAST, int BATCH, int MINB, int IDX>
 __global__ void __launch_bounds__(256, MINB) k_step_f64(SellDev A, const double* __restrict__ x,
                                                   const double* __restrict__ g, const double* prev,
@@ -126,14 +136,13 @@ __global__ void __launch_bounds__(256, MINB) k_step_f64(SellDev A, const double*
     const int64_t mesh = A.slice_mesh ? A.slice_mesh[s] : 0;
     const double xi = x[row];
     const double pi = FIRST ? xi : prev[row];
-    const double seed = 2.0 * xi - pi;
+    const double seed = (IDX == 2 || A.fold2) ? -pi : 2.0 * xi - pi;
     double un;
     if constexpr (IDX == 2) {
       const int64_t b2 = A.slice_ptr2[s];
-      const int wp = static_cast<int>((A.slice_ptr2[s + 1] - b2) >> 6);
       un = row_dot_pairs<double, (BATCH >= 2 ? BATCH / 2 : 1)>(
           seed, reinterpret_cast<const double2*>(A.val64p + b2) + lane,
-          reinterpret_cast<const int32_t*>(A.dcolp + b2) + lane, static_cast<int>(row), wp, g);
+          reinterpret_cast<const int32_t*>(A.dcolp + b2) + lane, static_cast<int>(row), w, g);
     } else if constexpr (IDX == 1) {
       un = row_dot<double, BATCH>(seed, A.val64 + beg + lane, A.dcol + beg + lane, static_cast<int>(row), w, g);
     } else {
@@ -183,10 +192,9 @@ __global__ void __launch_bounds__(256, MINB) k_step_f32(SellDev A, const float* 
     float un;
     if constexpr (IDX == 2) {
       const int64_t b2 = A.slice_ptr2[s];
-      const int wp = static_cast<int>((A.slice_ptr2[s + 1] - b2) >> 6);
       un = row_dot_pairs<float, (BATCH >= 2 ? BATCH / 2 : 1)>(
           seed, reinterpret_cast<const float2*>(A.val32p + b2) + lane,
-          reinterpret_cast<const int32_t*>(A.dcolp + b2) + lane, static_cast<int>(row), wp, g);
+          reinterpret_cast<const int32_t*>(A.dcolp + b2) + lane, static_cast<int>(row), w, g);
     } else if constexpr (IDX == 1) {
       un = row_dot<float, BATCH>(seed, A.val32 + beg + lane, A.dcol + beg + lane, static_cast<int>(row), w, g);
     } else {
@@ -256,23 +264,29 @@ __global__ void __launch_bounds__(256) k_spmv_f64(SellDev A, const double* __res
 
 // A = -tau^2 M^{-1} S in the SELL layout: out[e] = -tau2m[row(e)] * val64[e]
 // (out64p / out32p: the same values in the pair layout of A.slice_ptr2; their padding
-// entries keep the zeros they were allocated with.)
+// entries keep the zeros they were allocated with. fold2: out64 and out64p hold A + 2I, 2
+// added to the first entry of each row at its own column, which the context has checked
+// exists: a stored diagonal, or SELL padding, which points at its own row.)
 __global__ void k_scale_values(SellDev A, const double* __restrict__ tau2m, double* __restrict__ out64,
                                float* __restrict__ out32, double* __restrict__ out64p,
-                               float* __restrict__ out32p) {
+                               float* __restrict__ out32p, int fold2) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
   for (int64_t s = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; s < A.n_slices;
        s += nwarps) {
     const int64_t beg = A.slice_ptr[s], end = A.slice_ptr[s + 1];
     const double t = -tau2m[s * kSliceC + lane];
+    const int64_t row = s * kSliceC + lane;
+    bool diag_done = false;
     int k = 0;
     for (int64_t e = beg + lane; e < end; e += kSliceC, ++k) {
       const double a = t * A.val64[e];
-      if (out64) out64[e] = a;
+      const bool fold = fold2 && !diag_done && A.col[e] == row;
+      diag_done |= fold;
+      if (out64) out64[e] = fold ? a + 2.0 : a;
       if (out32) out32[e] = static_cast<float>(a);
       const int64_t p2 = A.slice_ptr2 ? A.slice_ptr2[s] + 64 * (k >> 1) + 2 * lane + (k & 1) : 0;
-      if (out64p) out64p[p2] = a;
+      if (out64p) out64p[p2] = fold ? a + 2.0 : a;
       if (out32p) out32p[p2] = static_cast<float>(a);
     }
   }
@@ -308,7 +322,7 @@ void step_f64_impl(int grid, int block, cudaStream_t st, bool first, bool last, 
   else if (first) k_step_f64<true, false, BATCH, MINB, I><<<grid, block, 0, st>>>(KES_F64_ARGS);      \
   else if (last) k_step_f64<false, true, BATCH, MINB, I><<<grid, block, 0, st>>>(KES_F64_ARGS);       \
   else k_step_f64<false, false, BATCH, MINB, I><<<grid, block, 0, st>>>(KES_F64_ARGS);
-  if (A.val64p) {
+  if (A.val64p && A.fold2) {  // the pair form seeds with -u_{n-1}: the values must hold A + 2I
     KES_F64_LAUNCH(2)
   } else if (A.dcol) {
     KES_F64_LAUNCH(1)
@@ -468,8 +482,9 @@ void launch_spmv_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, co
 }
 
 void launch_scale_values(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, const double* tau2m,
-                         double* out64, float* out32, double* out64p, float* out32p) {
-  k_scale_values<<<grid_for(cfg, A.n_slices), cfg.block_step, 0, st>>>(A, tau2m, out64, out32, out64p, out32p);
+                         double* out64, float* out32, double* out64p, float* out32p, bool fold2) {
+  k_scale_values<<<grid_for(cfg, A.n_slices), cfg.block_step, 0, st>>>(A, tau2m, out64, out32, out64p, out32p,
+                                                                        fold2 ? 1 : 0);
   ++g_launches;
 }
 

@@ -161,7 +161,7 @@ __global__ void k_step_tma(SellDev A, int G, int S, int wmax, const T* __restric
         // u_{n+1} = (2 u_n - u_{n-1}) + A u_n, one FMA chain in entry order
         T un;
         if constexpr (kF32) un = __fsub_rn(__fmul_rn(2.0f, xi), pi);
-        else un = 2.0 * xi - pi;
+        else un = A.fold2 ? -pi : 2.0 * xi - pi;  // A.fold2: 2 x is in the diagonal
         int k = 0;
         for (; k + 2 <= w; k += 2) {
           const int32_t c0 = cl[k * kSliceC], c1 = cl[(k + 1) * kSliceC];

@@ -107,14 +107,18 @@ struct kes_ctx {
   double* minv64 = nullptr;       // 1 / m
   double* tau2m64 = nullptr;      // tau^2 / m with the tau of the row's mesh
   double* step64 = nullptr;       // A = -tau^2 M^{-1} S, SELL layout (FP64 steps)
-  double* step64p = nullptr;      // the same in the pair layout (A.slice_ptr2), FP64 contexts
+  double* step64p = nullptr;      // the same in the pair layout (A.slice_ptr2); FP64 contexts with fold64
   float* step32 = nullptr;        // the same in FP32 (FP32 steps)
   float* step32p = nullptr;       // the FP32 ones in the pair layout (A.slice_ptr2), if built
   int64_t nnz_pair = 0;           // entries of the pair layout (with its padding)
+  bool diag_in_rows = false;      // every row of the SELL layout stores its diagonal among its slice's
+                                  // width (a real entry or padding): the 2 u_n can fold into A
+  bool fold64 = false;            // the FP64 step values hold A + 2I (leapfrog and diag_in_rows)
   SellDev step_A64() const {
     SellDev a = A;
     a.val64 = step64;
     a.val64p = step64p;
+    a.fold2 = fold64 ? 1 : 0;
     return a;
   }
   SellDev step_A32() const {
@@ -344,7 +348,7 @@ void ensure_fp64_state(kes_ctx* c) {
     for (int j = 0; j < 2; ++j) c->U64[j] = c->dzero_n<double>(c->n_pad * c->NBcap);
   if (!c->step64) {
     c->step64 = c->dzero_n<double>(c->nnz_pad);
-    launch_scale_values(c->A, c->cfg, c->stream, c->tau2m64, c->step64, nullptr, nullptr, nullptr);
+    launch_scale_values(c->A, c->cfg, c->stream, c->tau2m64, c->step64, nullptr, nullptr, nullptr, c->fold64);
     KES_CHECK_LAUNCH();
   }
 }
@@ -645,8 +649,27 @@ void build_context(kes_ctx* c, int nm, const int64_t* n, const int64_t* const* r
   for (int64_t sl = 0; sl < n_slices; ++sl) wmax = std::max(wmax, (sp[sl + 1] - sp[sl]) / kSliceC);
   c->cfg.tma.wmax = static_cast<int>(wmax);
   sells.clear();
+  // the leapfrog's 2 u_n folds into the diagonal of the FP64 step values when each row of a
+  // mesh has an entry at its own column (a stored diagonal, or SELL padding of a short row,
+  // which points at its row) among the first w of its slice; a slice of empty rows (w = 0)
+  // has none. The padding rows past a mesh's last row need none: they gather only zeros,
+  // read from no real row, and stay bounded (-u_(n-1)) with or without the 2 u_n.
+  {
+    bool diag = true;
+    for (int64_t sl = 0; sl < n_slices && diag; ++sl) {
+      const int64_t w = (sp[sl + 1] - sp[sl]) / kSliceC;
+      for (int64_t l = 0; l < kSliceC && diag; ++l) {
+        if (rsrc[sl * kSliceC + l] < 0) continue;  // padding row
+        bool found = false;
+        for (int64_t k = 0; k < w && !found; ++k) found = cols[sp[sl] + k * kSliceC + l] == sl * kSliceC + l;
+        diag = found;
+      }
+    }
+    c->diag_in_rows = diag;
+  }
   // compact index for the step kernels: column - row as 16 bits when every entry allows it
-  // (padding entries point at their own row: difference 0)
+  // (padding of a short row points at its own row: difference 0; padding rows past a mesh's
+  // last row point at that row)
   std::vector<int16_t> dcol;
   if (c->opts.compact_cols) {
     dcol.resize(nnz_pad);
@@ -766,6 +789,7 @@ kes_status create_impl(kes_ctx** out, int32_t nm, const int64_t* n, const int64_
       c->own_stream = true;
     }
     build_context(c, nm, n, row_ptr, col, val, m_diag);
+    c->fold64 = c->diag_in_rows && c->opts.stepper == KES_STEPPER_LEAPFROG;
     const int64_t np = c->n_pad, nb = c->NBcap;
     c->tau2m64 = c->dzero_n<double>(np);
     if (c->opts.precision == KES_PREC_FP32) {
@@ -774,7 +798,7 @@ kes_status create_impl(kes_ctx** out, int32_t nm, const int64_t* n, const int64_
       for (int j = 0; j < 3; ++j) c->U32[j] = c->dzero_n<float>(np * nb);
     } else {
       c->step64 = c->dzero_n<double>(c->nnz_pad);
-      if (c->A.slice_ptr2) c->step64p = c->dzero_n<double>(c->nnz_pair);  // padding stays zero
+      if (c->A.slice_ptr2 && c->fold64) c->step64p = c->dzero_n<double>(c->nnz_pair);  // padding stays zero
       for (int j = 0; j < 2; ++j) c->U64[j] = c->dzero_n<double>(np * nb);
     }
     c->stage_in = c->dzero_n<double>(np * nb);
@@ -866,7 +890,8 @@ kes_status set_weights_impl(kes_ctx* c, int32_t F, const double* alpha, const do
     KES_CUDA(cudaMemcpyAsync(c->tau2m64, t2m.data(), c->n_pad * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     // step values A = -tau^2 M^{-1} S (the FP32 ones rounded once from the FP64 product)
     if (c->step64 || c->step32)
-      launch_scale_values(c->A, c->cfg, c->stream, c->tau2m64, c->step64, c->step32, c->step64p, c->step32p);
+      launch_scale_values(c->A, c->cfg, c->stream, c->tau2m64, c->step64, c->step32, c->step64p, c->step32p,
+                          c->fold64);
     KES_CHECK_LAUNCH();
     ensure_stage_out(c, F);
     c->sync();

@@ -49,13 +49,17 @@ struct SellDev {
   const int16_t* dcol = nullptr;
   // pair layout of the single-vector steps: a lane's entries 2k and 2k+1 adjacent, at
   // slice_ptr2[s] + 64 (k / 2) + 2 lane + k % 2, odd slice widths padded with one zero entry
-  // per lane (difference 0); values val32p / val64p, differences dcolp. Null where not built.
+  // per lane (difference 0, skipped by the row sums); values val32p / val64p, differences
+  // dcolp. Null where not built; val64p is built only where fold2 is set.
   const int64_t* slice_ptr2 = nullptr;
   const float* val32p = nullptr;
   const double* val64p = nullptr;
   const int16_t* dcolp = nullptr;
   const double* val64 = nullptr;
   const float* val32 = nullptr;
+  // the FP64 step values (val64, val64p) hold A + 2I: the leapfrog's 2 u_n folded into the
+  // diagonal, so a row sum seeds with -u_{n-1} alone (FP32 values never hold it)
+  int fold2 = 0;
   // mesh of each slice when several meshes are stacked block-diagonally (null: one mesh).
   // Weight tables are indexed (mesh * F + f) * (L + 1) + n.
   const int32_t* slice_mesh = nullptr;
@@ -80,6 +84,7 @@ struct LaunchCfg {
 // One fused leapfrog step, FP64 (Sec. 2.3, eq. 2stepmethod + eq. disc_filtercoeff), on the
 // values of A = -tau^2 M^{-1} S (see launch_scale_values):
 //   out = (2 x - prev) + A g;   acc_f += alpha_f[step+1] * out   (f < F)
+// (A.fold2: out = -prev + (A + 2I) x, the same sum with the 2 x in the diagonal values.)
 // g = x for the leapfrog; g = the stage v = x + A x / 12 (launch_stage4_*) for the
 // fourth-order scheme (bulk-copy shapes need g = x and fall back to a register shape).
 // first: prev = x and acc_f = alpha_f[0] * x + alpha_f[1] * out.
@@ -158,9 +163,12 @@ void launch_step_tma_f32(const SellDev& A, const TmaShape& sh, int n_sm, cudaStr
 
 // Step values A = -tau^2 M^{-1} S from the values of S (A.val64) and tau^2/m per row:
 // out64[e] = -tau2m[row(e)] * val64[e] and/or out32[e] = (float) of the same (either may be null).
+// fold2: out64 and out64p get 2 added at each row's first entry at its own column (A + 2I);
+// the caller has checked that every row has one.
 void launch_scale_values(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, const double* tau2m,
                          double* out64, float* out32, double* out64p,
-                         float* out32p);  // out64p / out32p: pair layout (A.slice_ptr2)
+                         float* out32p,  // out64p / out32p: pair layout (A.slice_ptr2)
+                         bool fold2);
 
 // y = dscale .* (S x) (dscale may be null) in FP64.
 void launch_spmv_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, const double* x,

@@ -263,6 +263,48 @@ def _long_range_chain(n=70000, reach=40000, seed=3):
                    L.data.astype(np.float64), rng.uniform(0.5, 2.0, n))
 
 
+def _chain_with_isolated_nodes(n=6000, n_iso=300, seed=5):
+    """A weighted path graph Laplacian plus a diagonal shift on the first n - n_iso nodes,
+    and n_iso nodes with no coupling at all: rows without a single stored entry."""
+    import scipy.sparse as sp
+    from fe_inputs import Problem
+    rng = np.random.default_rng(seed)
+    m = n - n_iso
+    i = np.arange(m - 1)
+    A = sp.coo_matrix((rng.uniform(0.5, 1.5, m - 1), (i, i + 1)), shape=(m, m)).tocsr()
+    A = A + A.T
+    Lm = sp.diags(np.asarray(A.sum(axis=1)).ravel() + 0.1) - A
+    L = sp.block_diag((Lm, sp.csr_matrix((n_iso, n_iso)))).tocsr()
+    L.eliminate_zeros()
+    L.sort_indices()
+    assert np.all(np.diff(L.indptr)[m:] == 0)
+    return Problem("chain_isolated", n, L.indptr.astype(np.int64), L.indices.astype(np.int32),
+                   L.data.astype(np.float64), rng.uniform(0.5, 2.0, n))
+
+
+@pytest.mark.parametrize("b", [1, 2])
+def test_rows_without_entries_keep_the_explicit_leapfrog_seed(b):
+    # the FP64 step values fold the leapfrog's 2 u_n into the diagonal only when every row
+    # of the SELL layout has an entry at its own column; a slice of empty rows has none,
+    # so the context keeps A and the seed 2 u_n - u_(n-1) (an isolated node then stays
+    # constant: u_(n+1) = 2 u_n - u_(n-1) = u_0) and the filter still matches the oracle
+    p = _chain_with_isolated_nodes()
+    S = p.to_scipy()
+    tau = 0.9 * 2 / O.power_iteration(S, p.m, start_vectors(p.n, 1, 0)[0], 200)
+    L = 40
+    alpha = O.alpha_table(0.3, 0.8, tau, L)
+    R = start_vectors(p.n, b, 6)
+    with K.Context(p, block_b=b) as c:
+        K.kes_set_filter(c.handle, 0.3, 0.8, tau, L)
+        o = np.zeros((1, b, p.n))
+        K.kes_filter_apply(c.handle, R, o, b)
+    for j in range(b):
+        ref = O.filter_apply(S, p.m, R[j], tau, alpha)
+        assert filter_error(o[0, j], ref, R[j:j + 1], p.m, alpha) <= filter_tol(L, "fp64")
+    iso = slice(p.n - 300, p.n)
+    np.testing.assert_allclose(o[0, :, iso], alpha.sum() * R[:, iso], rtol=1e-10, atol=0)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_wide_matrix_keeps_int32_columns_and_matches_oracle(precision):
     # differences column - row beyond 16 bits: the context keeps int32 columns (the step
