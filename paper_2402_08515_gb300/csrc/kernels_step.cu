@@ -72,7 +72,8 @@ __device__ __forceinline__ T row_dot(T acc, const T* __restrict__ v, const I* __
 // The same sum over the pair layout: pair p of the lane holds entries 2p and 2p+1 (one
 // float2 / double2 of values, one 32-bit word of two 16-bit column differences, low half first),
 // NP pairs' loads issued together; the chain is still in entry order. w is the row's
-// number of entries: for odd w the last pair's second entry is padding and is skipped.
+// number of entries: for odd w the last pair's second entry is padding. Its pair is loaded
+// with its batch (no extra round trip) but the padding is neither gathered nor summed.
 template <typename T> struct Pair2;
 template <> struct Pair2<float> { using type = float2; };
 template <> struct Pair2<double> { using type = double2; };
@@ -81,9 +82,10 @@ template <typename T, int NP>
 __device__ __forceinline__ T row_dot_pairs(T acc, const typename Pair2<T>::type* __restrict__ v,
                                            const int32_t* __restrict__ c, int row, int w, const T* __restrict__ x) {
   using T2 = typename Pair2<T>::type;
-  const int wp = w >> 1;  // full pairs
+  const int wp = w >> 1;          // full pairs
+  const int wpp = (w + 1) >> 1;   // stored pairs
   int k = 0;
-  for (; k + NP <= wp; k += NP) {
+  for (; k + NP <= wpp; k += NP) {
     int32_t cc[NP];
     T2 vv[NP];
     T xa[NP], xb[NP];
@@ -94,22 +96,21 @@ __device__ __forceinline__ T row_dot_pairs(T acc, const typename Pair2<T>::type*
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
       xa[j] = __ldg(x + row + static_cast<int16_t>(cc[j] & 0xffff));
-      xb[j] = __ldg(x + row + (cc[j] >> 16));
+      xb[j] = k + j < wp ? __ldg(x + row + (cc[j] >> 16)) : T(0);
     }
 #pragma unroll
-    for (int j = 0; j < NP; ++j) acc = fma(vv[j].y, xb[j], fma(vv[j].x, xa[j], acc));
+    for (int j = 0; j < NP; ++j) {
+      acc = fma(vv[j].x, xa[j], acc);
+      if (k + j < wp) acc = fma(vv[j].y, xb[j], acc);
+    }
   }
-  for (; k < wp; ++k) {
+  for (; k < wpp; ++k) {
     const int32_t c0 = __ldcs(c + k * kSliceC);
     const T2 v0 = __ldcs(v + k * kSliceC);
     const T a = __ldg(x + row + static_cast<int16_t>(c0 & 0xffff));
-    const T b = __ldg(x + row + (c0 >> 16));
-    acc = fma(v0.y, b, fma(v0.x, a, acc));
-  }
-  if (w & 1) {
-    const int32_t c0 = __ldcs(c + wp * kSliceC);
-    const T2 v0 = __ldcs(v + wp * kSliceC);
-    acc = fma(v0.x, __ldg(x + row + static_cast<int16_t>(c0 & 0xffff)), acc);
+    const T b = k < wp ? __ldg(x + row + (c0 >> 16)) : T(0);
+    acc = fma(v0.x, a, acc);
+    if (k < wp) acc = fma(v0.y, b, acc);
   }
   return acc;
 }
