@@ -96,37 +96,23 @@ __device__ __forceinline__ T row_dot_pairs(T acc, const typename Pair2<T>::type*
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
       xa[j] = __ldg(x + row + static_cast<int16_t>(cc[j] & 0xffff));
-      xb[j] = k + j < wp ? __ldg(x + row + (cc[j] >> 16)) : T(0);  // no gather for padding
+      xb[j] = k + j < wp ? __ldg(x + row + (cc[j] >> 16)) : T(0);
     }
-    // a branch (uniform over the warp: one slice, one width), not a select: the padding's
-    // FMA must not be issued at all
-    if (k + NP <= wp) {
 #pragma unroll
-      for (int j = 0; j < NP; ++j) acc = fma(vv[j].y, xb[j], fma(vv[j].x, xa[j], acc));
-    } else {  // the batch ends with the half-empty pair
-#pragma unroll
-      for (int j = 0; j < NP - 1; ++j) acc = fma(vv[j].y, xb[j], fma(vv[j].x, xa[j], acc));
-      acc = fma(vv[NP - 1].x, xa[NP - 1], acc);
+    for (int j = 0; j < NP; ++j) {
+      acc = fma(vv[j].x, xa[j], acc);
+      if (k + j < wp) acc = fma(vv[j].y, xb[j], acc);
     }
   }
   for (; k < wpp; ++k) {
     const int32_t c0 = __ldcs(c + k * kSliceC);
     const T2 v0 = __ldcs(v + k * kSliceC);
     const T a = __ldg(x + row + static_cast<int16_t>(c0 & 0xffff));
-    if (k < wp) {
-      const T b = __ldg(x + row + (c0 >> 16));
-      acc = fma(v0.y, b, fma(v0.x, a, acc));
-    } else {
-      acc = fma(v0.x, a, acc);
-    }
+    const T b = k < wp ? __ldg(x + row + (c0 >> 16)) : T(0);
+    acc = fma(v0.x, a, acc);
+    if (k < wp) acc = fma(v0.y, b, acc);
   }
   return acc;
-}
-
-// -x by flipping the sign bit on the integer pipe (exact, as IEEE negation is), so that the
-// FP64-pipe-bound step spends no DADD on its seed
-__device__ __forceinline__ double neg_bits(double x) {
-  return __longlong_as_double(__double_as_longlong(x) ^ static_cast<long long>(0x8000000000000000ull));
 }
 
 // IDX: how the row sums read columns: 0 the int32 columns, 1 the compact 16-bit column -
@@ -151,7 +137,7 @@ __global__ void __launch_bounds__(256, MINB) k_step_f64(SellDev A, const double*
     const int64_t mesh = A.slice_mesh ? A.slice_mesh[s] : 0;
     const double xi = x[row];
     const double pi = FIRST ? xi : prev[row];
-    const double seed = (IDX == 2 || A.fold2) ? neg_bits(pi) : 2.0 * xi - pi;
+    const double seed = (IDX == 2 || A.fold2) ? -pi : 2.0 * xi - pi;
     double un;
     if constexpr (IDX == 2) {
       const int64_t b2 = A.slice_ptr2[s];
