@@ -69,22 +69,26 @@ __device__ __forceinline__ T row_dot(T acc, const T* __restrict__ v, const I* __
 
 // g is the vector the row sums gather from: u_n itself for the leapfrog, the stage
 // v = u_n + A u_n / 12 for the fourth-order scheme; x = u_n seeds the row (2 u_n - u_{n-1}).
-// The same sum over the pair layout (pair_pos): one float2 / double2 of values and one 32-bit
-// word of two 16-bit column differences (low half first) per pair, NP pairs' loads issued
-// together. wp = the lane's pairs; v, c point at its first pair. For odd widths (ODD) entry 0
-// stands alone at v1, c1: its loads go out with the first batch's and its FMA starts the
-// chain, so the chain stays in entry order and no padding is loaded or summed.
+// The same sum over the pair layout: pair p of the lane holds entries 2p and 2p+1 (one
+// float2 / double2 of values, one 32-bit word of two 16-bit column differences, low half first),
+// NP pairs' loads issued together; the chain is still in entry order. w is the row's
+// number of entries: for odd w the last pair's second entry is padding. Its pair is loaded
+// with its batch (no extra round trip) but the padding is neither gathered nor summed.
 template <typename T> struct Pair2;
 template <> struct Pair2<float> { using type = float2; };
 template <> struct Pair2<double> { using type = double2; };
 
 template <typename T, int NP>
-struct PairBatch {
-  typename Pair2<T>::type vv[NP];
-  T xa[NP], xb[NP];
-  __device__ __forceinline__ void load(const typename Pair2<T>::type* __restrict__ v,
-                                       const int32_t* __restrict__ c, int k, int row, const T* __restrict__ x) {
+__device__ __forceinline__ T row_dot_pairs(T acc, const typename Pair2<T>::type* __restrict__ v,
+                                           const int32_t* __restrict__ c, int row, int w, const T* __restrict__ x) {
+  using T2 = typename Pair2<T>::type;
+  const int wp = w >> 1;          // full pairs
+  const int wpp = (w + 1) >> 1;   // stored pairs
+  int k = 0;
+  for (; k + NP <= wpp; k += NP) {
     int32_t cc[NP];
+    T2 vv[NP];
+    T xa[NP], xb[NP];
 #pragma unroll
     for (int j = 0; j < NP; ++j) cc[j] = __ldcs(c + (k + j) * kSliceC);
 #pragma unroll
@@ -92,47 +96,21 @@ struct PairBatch {
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
       xa[j] = __ldg(x + row + static_cast<int16_t>(cc[j] & 0xffff));
-      xb[j] = __ldg(x + row + (cc[j] >> 16));
+      xb[j] = k + j < wp ? __ldg(x + row + (cc[j] >> 16)) : T(0);
     }
-  }
-  __device__ __forceinline__ T sum(T acc) const {
 #pragma unroll
-    for (int j = 0; j < NP; ++j) acc = fma(vv[j].y, xb[j], fma(vv[j].x, xa[j], acc));
-    return acc;
-  }
-};
-
-template <typename T, int NP, bool ODD>
-__device__ __forceinline__ T row_dot_pairs(T acc, const typename Pair2<T>::type* __restrict__ v,
-                                           const int32_t* __restrict__ c, const T* __restrict__ v1,
-                                           const int16_t* __restrict__ c1, int row, int wp,
-                                           const T* __restrict__ x) {
-  using T2 = typename Pair2<T>::type;
-  int k = 0;
-  if constexpr (ODD) {
-    const int d1 = ld_stream(c1);
-    const T a1 = __ldcs(v1);
-    if (wp >= NP) {
-      PairBatch<T, NP> b;
-      b.load(v, c, 0, row, x);
-      const T x1 = __ldg(x + row + d1);
-      acc = b.sum(fma(a1, x1, acc));
-      k = NP;
-    } else {
-      acc = fma(a1, __ldg(x + row + d1), acc);
+    for (int j = 0; j < NP; ++j) {
+      acc = fma(vv[j].x, xa[j], acc);
+      if (k + j < wp) acc = fma(vv[j].y, xb[j], acc);
     }
   }
-  for (; k + NP <= wp; k += NP) {
-    PairBatch<T, NP> b;
-    b.load(v, c, k, row, x);
-    acc = b.sum(acc);
-  }
-  for (; k < wp; ++k) {
+  for (; k < wpp; ++k) {
     const int32_t c0 = __ldcs(c + k * kSliceC);
     const T2 v0 = __ldcs(v + k * kSliceC);
     const T a = __ldg(x + row + static_cast<int16_t>(c0 & 0xffff));
-    const T b = __ldg(x + row + (c0 >> 16));
-    acc = fma(v0.y, b, fma(v0.x, a, acc));
+    const T b = k < wp ? __ldg(x + row + (c0 >> 16)) : T(0);
+    acc = fma(v0.x, a, acc);
+    if (k < wp) acc = fma(v0.y, b, acc);
   }
   return acc;
 }
@@ -162,15 +140,10 @@ __global__ void __launch_bounds__(256, MINB) k_step_f64(SellDev A, const double*
     const double seed = (IDX == 2 || A.fold2) ? -pi : 2.0 * xi - pi;
     double un;
     if constexpr (IDX == 2) {
-      constexpr int NP = BATCH >= 2 ? BATCH / 2 : 1;
-      const int64_t b2 = beg + ((w & 1) ? kSliceC : 0);  // first pair
-      const double2* vp = reinterpret_cast<const double2*>(A.val64p + b2) + lane;
-      const int32_t* cp = reinterpret_cast<const int32_t*>(A.dcolp + b2) + lane;
-      if (w & 1)
-        un = row_dot_pairs<double, NP, true>(seed, vp, cp, A.val64p + beg + lane, A.dcolp + beg + lane,
-                                             static_cast<int>(row), w >> 1, g);
-      else
-        un = row_dot_pairs<double, NP, false>(seed, vp, cp, nullptr, nullptr, static_cast<int>(row), w >> 1, g);
+      const int64_t b2 = A.slice_ptr2[s];
+      un = row_dot_pairs<double, (BATCH >= 2 ? BATCH / 2 : 1)>(
+          seed, reinterpret_cast<const double2*>(A.val64p + b2) + lane,
+          reinterpret_cast<const int32_t*>(A.dcolp + b2) + lane, static_cast<int>(row), w, g);
     } else if constexpr (IDX == 1) {
       un = row_dot<double, BATCH>(seed, A.val64 + beg + lane, A.dcol + beg + lane, static_cast<int>(row), w, g);
     } else {
@@ -219,15 +192,10 @@ __global__ void __launch_bounds__(256, MINB) k_step_f32(SellDev A, const float* 
     const float seed = __fsub_rn(__fmul_rn(2.0f, xi), pi);
     float un;
     if constexpr (IDX == 2) {
-      constexpr int NP = BATCH >= 2 ? BATCH / 2 : 1;
-      const int64_t b2 = beg + ((w & 1) ? kSliceC : 0);  // first pair
-      const float2* vp = reinterpret_cast<const float2*>(A.val32p + b2) + lane;
-      const int32_t* cp = reinterpret_cast<const int32_t*>(A.dcolp + b2) + lane;
-      if (w & 1)
-        un = row_dot_pairs<float, NP, true>(seed, vp, cp, A.val32p + beg + lane, A.dcolp + beg + lane,
-                                            static_cast<int>(row), w >> 1, g);
-      else
-        un = row_dot_pairs<float, NP, false>(seed, vp, cp, nullptr, nullptr, static_cast<int>(row), w >> 1, g);
+      const int64_t b2 = A.slice_ptr2[s];
+      un = row_dot_pairs<float, (BATCH >= 2 ? BATCH / 2 : 1)>(
+          seed, reinterpret_cast<const float2*>(A.val32p + b2) + lane,
+          reinterpret_cast<const int32_t*>(A.dcolp + b2) + lane, static_cast<int>(row), w, g);
     } else if constexpr (IDX == 1) {
       un = row_dot<float, BATCH>(seed, A.val32 + beg + lane, A.dcol + beg + lane, static_cast<int>(row), w, g);
     } else {
@@ -296,9 +264,10 @@ __global__ void __launch_bounds__(256) k_spmv_f64(SellDev A, const double* __res
 }
 
 // A = -tau^2 M^{-1} S in the SELL layout: out[e] = -tau2m[row(e)] * val64[e]
-// (out64p / out32p: the same values in the pair layout, at pair_pos.) fold2: out64 and
-// out64p hold A + 2I, 2 added to the first entry of each row at its own column, which the
-// context has checked exists: a stored diagonal, or SELL padding, which points at its own row.
+// (out64p / out32p: the same values in the pair layout of A.slice_ptr2; their padding
+// entries keep the zeros they were allocated with. fold2: out64 and out64p hold A + 2I, 2
+// added to the first entry of each row at its own column, which the context has checked
+// exists: a stored diagonal, or SELL padding, which points at its own row.)
 __global__ void k_scale_values(SellDev A, const double* __restrict__ tau2m, double* __restrict__ out64,
                                float* __restrict__ out32, double* __restrict__ out64p,
                                float* __restrict__ out32p, int fold2) {
@@ -317,7 +286,7 @@ __global__ void k_scale_values(SellDev A, const double* __restrict__ tau2m, doub
       diag_done |= fold;
       if (out64) out64[e] = fold ? a + 2.0 : a;
       if (out32) out32[e] = static_cast<float>(a);
-      const int64_t p2 = A.dcolp ? pair_pos(beg, (end - beg) >> 5, k, lane) : 0;
+      const int64_t p2 = A.slice_ptr2 ? A.slice_ptr2[s] + 64 * (k >> 1) + 2 * lane + (k & 1) : 0;
       if (out64p) out64p[p2] = fold ? a + 2.0 : a;
       if (out32p) out32p[p2] = static_cast<float>(a);
     }

@@ -107,9 +107,10 @@ struct kes_ctx {
   double* minv64 = nullptr;       // 1 / m
   double* tau2m64 = nullptr;      // tau^2 / m with the tau of the row's mesh
   double* step64 = nullptr;       // A = -tau^2 M^{-1} S, SELL layout (FP64 steps)
-  double* step64p = nullptr;      // the same in the pair layout (pair_pos); FP64 contexts with fold64
+  double* step64p = nullptr;      // the same in the pair layout (A.slice_ptr2); FP64 contexts with fold64
   float* step32 = nullptr;        // the same in FP32 (FP32 steps)
-  float* step32p = nullptr;       // the FP32 ones in the pair layout (pair_pos), if built
+  float* step32p = nullptr;       // the FP32 ones in the pair layout (A.slice_ptr2), if built
+  int64_t nnz_pair = 0;           // entries of the pair layout (with its padding)
   bool diag_in_rows = false;      // every row of the SELL layout stores its diagonal among its slice's
                                   // width (a real entry or padding): the 2 u_n can fold into A
   bool fold64 = false;            // the FP64 step values hold A + 2I (leapfrog and diag_in_rows)
@@ -701,19 +702,27 @@ void build_context(kes_ctx* c, int nm, const int64_t* n, const int64_t* const* r
     KES_CUDA(cudaMemcpyAsync(d_dcol, dcol.data(), nnz_pad * sizeof(int16_t), cudaMemcpyHostToDevice, c->stream));
     c->A.dcol = d_dcol;
     {
-      // pair layout for the single-vector steps: the same slice ranges, entries moved to
-      // pair_pos (a permutation within each slice)
-      std::vector<int16_t> dcolp(nnz_pad, 0);
+      // pair layout for the single-vector steps: entry k of lane l of slice s at
+      // sp2[s] + 64 (k / 2) + 2 l + k % 2, odd widths padded with a zero entry per lane
+      std::vector<int64_t> sp2(n_slices + 1, 0);
       for (int64_t sl = 0; sl < n_slices; ++sl) {
         const int64_t w = (sp[sl + 1] - sp[sl]) / kSliceC;
+        sp2[sl + 1] = sp2[sl] + kSliceC * (w + (w & 1));
+      }
+      std::vector<int16_t> dcolp(sp2[n_slices], 0);
+      for (int64_t sl = 0; sl < n_slices; ++sl)
         for (int64_t e = sp[sl]; e < sp[sl + 1]; ++e) {
           const int64_t k = (e - sp[sl]) / kSliceC, l = (e - sp[sl]) % kSliceC;
-          dcolp[pair_pos(sp[sl], w, k, l)] = dcol[e];
+          dcolp[sp2[sl] + 64 * (k >> 1) + 2 * l + (k & 1)] = dcol[e];
         }
-      }
-      int16_t* d_dcolp = c->dalloc_n<int16_t>(nnz_pad);
-      KES_CUDA(cudaMemcpyAsync(d_dcolp, dcolp.data(), nnz_pad * sizeof(int16_t), cudaMemcpyHostToDevice,
+      c->nnz_pair = sp2[n_slices];
+      int64_t* d_sp2 = c->dalloc_n<int64_t>(n_slices + 1);
+      int16_t* d_dcolp = c->dalloc_n<int16_t>(c->nnz_pair);
+      KES_CUDA(cudaMemcpyAsync(d_sp2, sp2.data(), (n_slices + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
                                c->stream));
+      KES_CUDA(cudaMemcpyAsync(d_dcolp, dcolp.data(), c->nnz_pair * sizeof(int16_t), cudaMemcpyHostToDevice,
+                               c->stream));
+      c->A.slice_ptr2 = d_sp2;
       c->A.dcolp = d_dcolp;
       c->sync();  // the host vectors go out of scope
     }
@@ -785,11 +794,11 @@ kes_status create_impl(kes_ctx** out, int32_t nm, const int64_t* n, const int64_
     c->tau2m64 = c->dzero_n<double>(np);
     if (c->opts.precision == KES_PREC_FP32) {
       c->step32 = c->dzero_n<float>(c->nnz_pad);
-      if (c->A.dcolp) c->step32p = c->dzero_n<float>(c->nnz_pad);
+      if (c->A.slice_ptr2) c->step32p = c->dzero_n<float>(c->nnz_pair);  // padding stays zero
       for (int j = 0; j < 3; ++j) c->U32[j] = c->dzero_n<float>(np * nb);
     } else {
       c->step64 = c->dzero_n<double>(c->nnz_pad);
-      if (c->A.dcolp && c->fold64) c->step64p = c->dzero_n<double>(c->nnz_pad);
+      if (c->A.slice_ptr2 && c->fold64) c->step64p = c->dzero_n<double>(c->nnz_pair);  // padding stays zero
       for (int j = 0; j < 2; ++j) c->U64[j] = c->dzero_n<double>(np * nb);
     }
     c->stage_in = c->dzero_n<double>(np * nb);

@@ -13,26 +13,6 @@ namespace kes {
 
 constexpr int kSliceC = 32;  // SELL slice height = warp width
 
-#ifdef __CUDACC__
-#define KES_HD __host__ __device__
-#else
-#define KES_HD
-#endif
-
-// Position of entry k of lane l in the pair layout of a slice of width w that starts at base
-// (the same range as the slice's SELL entries): a lane's entries side by side in pairs, so that
-// one 2-wide load covers two of them. For even w, entries (2p, 2p+1) from base; for odd w,
-// entry 0 of every lane stands alone at base + l and the pairs (2p+1, 2p+2) follow from
-// base + 32. No padding, and a row sum over the layout keeps its entry order.
-KES_HD inline int64_t pair_pos(int64_t base, int64_t w, int64_t k, int64_t l) {
-  if (w & 1) {
-    if (k == 0) return base + l;
-    base += kSliceC;
-    k -= 1;
-  }
-  return base + 2 * kSliceC * (k >> 1) + 2 * l + (k & 1);
-}
-
 // ---------------------------------------------------------------- host math
 void alpha_table(double wmin, double wmax, double tau, int L, double* alpha);
 void filter_response(double wmin, double wmax, double tau, int L, const double* omega, int64_t k,
@@ -67,9 +47,11 @@ struct SellDev {
   // compact index of the step kernels: column - row of every stored entry as 16 bits,
   // when all of them fit (null otherwise); the same columns as `col`
   const int16_t* dcol = nullptr;
-  // pair layout of the single-vector steps (pair_pos, over the SELL slice ranges): values
-  // val32p / val64p, 16-bit column differences dcolp. Null where not built; val64p is built
-  // only where fold2 is set.
+  // pair layout of the single-vector steps: a lane's entries 2k and 2k+1 adjacent, at
+  // slice_ptr2[s] + 64 (k / 2) + 2 lane + k % 2, odd slice widths padded with one zero entry
+  // per lane (difference 0, skipped by the row sums); values val32p / val64p, differences
+  // dcolp. Null where not built; val64p is built only where fold2 is set.
+  const int64_t* slice_ptr2 = nullptr;
   const float* val32p = nullptr;
   const double* val64p = nullptr;
   const int16_t* dcolp = nullptr;
@@ -185,7 +167,7 @@ void launch_step_tma_f32(const SellDev& A, const TmaShape& sh, int n_sm, cudaStr
 // the caller has checked that every row has one.
 void launch_scale_values(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, const double* tau2m,
                          double* out64, float* out32, double* out64p,
-                         float* out32p,  // out64p / out32p: pair layout (pair_pos)
+                         float* out32p,  // out64p / out32p: pair layout (A.slice_ptr2)
                          bool fold2);
 
 // y = dscale .* (S x) (dscale may be null) in FP64.
