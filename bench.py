@@ -38,6 +38,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "GDOF*steps/s"
+TTS_TOL = 1e-8
 FALLBACK_HBM_GBS = 6800.0
 STEP_KERNEL_SRC = os.path.join(ROOT, "paper_2402_08515_gb300", "csrc", "kernels_step.cu")
 BLOCK_KERNEL_SRC = os.path.join(ROOT, "paper_2402_08515_gb300", "csrc", "kernels_block.cu")
@@ -50,8 +51,10 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="cube128_fp64")
     ap.add_argument("--impl", default="kes", choices=["kes", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle sample")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--tts-repeats", type=int, default=3, help="timed converged solves of the tts field")
+    ap.add_argument("--no-tts", action="store_true", help="leave out the converged solve (tts, and e2e through it)")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle samples (1 core + all cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="solve", choices=["solve", "filter", "tts", "weights"],
                     help="filter: one filter application only (small profiling runs); tts: time to "
@@ -217,9 +220,134 @@ def oracle_sample(problem, tau, wl, seconds: float, interval=None):
     return problem.n * steps / dt / 1e9, steps, dt
 
 
-def cpu_cores_used() -> int:
-    # scipy's CSR matvec and numpy's elementwise ops run on one thread
-    return 1
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+# The all-core baseline: P processes (spawned: the parent holds a CUDA context) each run
+# the oracle's filter, as it stands, on the same matrix, mapped read-only from .npy files
+# so that the processes share one copy. Every process takes one job per round and waits
+# on a barrier of P parties before it starts, so the P samples of a round run at once.
+def _oracle_worker(path, barrier, jobs, results):
+    import numpy as np
+    import scipy.sparse as sp
+
+    import oracle as O
+    d = {k: np.load(os.path.join(path, k + ".npy"), mmap_mode="r")
+         for k in ("row_ptr", "col", "val", "m", "r")}
+    n = d["m"].shape[0]
+    S = sp.csr_matrix((d["val"], d["col"], d["row_ptr"]), shape=(n, n), copy=False)
+    m, r = np.array(d["m"]), np.array(d["r"])
+    while True:
+        job = jobs.get()
+        if job is None:
+            return
+        tau, wmin, wmax, steps = job
+        alpha = O.alpha_table(wmin, wmax, tau, steps)
+        barrier.wait(timeout=600)
+        t0 = time.time()
+        out = O.filter_apply(S, m, r, tau, alpha)
+        t1 = time.time()
+        results.put((n * steps, t0, t1, bool(np.isfinite(out).all())))
+
+
+class OraclePool:
+    """P oracle processes over one matrix; round(steps) runs `steps` leapfrog steps of the
+    oracle filter in every process at once and returns (dof-steps, wall seconds)."""
+
+    def __init__(self, problem, r, tau, interval, procs: int):
+        import multiprocessing as mp
+        import numpy as np
+        self.n_procs, self.tau, self.interval = procs, tau, interval
+        base = "/dev/shm" if os.path.isdir("/dev/shm") else None
+        self.dir = tempfile.mkdtemp(prefix="kes_oracle_", dir=base)
+        for k, a in (("row_ptr", problem.row_ptr.astype(np.int64)), ("col", problem.col.astype(np.int64)),
+                     ("val", problem.val), ("m", problem.m), ("r", r)):
+            np.save(os.path.join(self.dir, k + ".npy"), np.ascontiguousarray(a))
+        ctx = mp.get_context("spawn")
+        self.jobs = [ctx.Queue() for _ in range(procs)]
+        self.results = ctx.Queue()
+        self.barrier = ctx.Barrier(procs)      # kept alive while the processes use it
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"
+        try:
+            self.procs = [ctx.Process(target=_oracle_worker, args=(self.dir, self.barrier, q, self.results),
+                                      daemon=True)
+                          for q in self.jobs]
+            for pr in self.procs:
+                pr.start()
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+
+    def round(self, steps: int, timeout: float = 900.0):
+        import queue
+        job = (self.tau, self.interval[0], self.interval[1], int(steps))
+        for q in self.jobs:
+            q.put(job)
+        out, t_end = [], time.time() + timeout
+        while len(out) < self.n_procs:
+            try:
+                out.append(self.results.get(timeout=1.0))
+            except queue.Empty:
+                if time.time() > t_end or not all(pr.is_alive() for pr in self.procs):
+                    raise RuntimeError("an oracle process ended or timed out")
+        assert all(ok for *_, ok in out)
+        return sum(u for u, *_ in out), max(t1 for _, _, t1, _ in out) - min(t0 for _, t0, _, _ in out)
+
+    def close(self):
+        import shutil
+        for q in self.jobs:
+            q.put(None)
+        for pr in self.procs:
+            pr.join(timeout=30)
+            if pr.is_alive():
+                pr.terminate()
+        shutil.rmtree(self.dir, ignore_errors=True)
+
+
+def cpu_baseline(problem, tau, wl, seconds: float, interval) -> dict:
+    """The oracle on the host cores: one process (single core) and P processes (all cores),
+    each a bounded sample of the workload's filter."""
+    from fe_inputs import start_vectors
+    v1, steps1, dt1 = oracle_sample(problem, tau, wl, seconds / 2, interval)
+    P = host_cores()
+    per_step = dt1 / steps1
+    pool = OraclePool(problem, start_vectors(problem.n, 1, wl.seed)[0], tau, interval, P)
+    try:
+        pool.round(2)                                          # maps the matrix in every process
+        steps = int(max(3, min(wl.L, seconds / 2 / per_step)))
+        units, wall = pool.round(steps)
+    except Exception as e:                                     # report the one-core figure alone
+        return {"value": v1, "unit": METRIC, "cores": 1, "kind": "oracle",
+                "sample": f"{steps1} leapfrog steps of the FP64 oracle filter in one process, {dt1:.1f} s",
+                "all_cores_error": repr(e)[:200], "cpu_model": cpu_model()}
+    finally:
+        pool.close()
+    return {"value": units / wall / 1e9, "unit": METRIC, "cores": P, "kind": "oracle",
+            "sample": f"{P} processes, one per host core, each {steps} leapfrog steps of the FP64 oracle filter "
+                      f"(one vector) on {problem.name} ({problem.n} dofs) at once, {wall:.1f} s wall",
+            "cpu_model": cpu_model(),
+            "single_core": {"value": v1, "cores": 1,
+                            "sample": f"{steps1} leapfrog steps of the same filter in one process, {dt1:.1f} s"}}
 
 
 def workload_problems(wl):
@@ -289,10 +417,13 @@ def run_kes(args):
         ctx.close()
         return
 
-    def solve():
+    def solve_with(opts):
         if b == 1 and not batch:
-            return [K.kes_krylov_solve(h, R0_dev[0], so)]
-        return K.kes_block_krylov_solve(h, R0_dev, b, so)
+            return [K.kes_krylov_solve(h, R0_dev[0], opts)]
+        return K.kes_block_krylov_solve(h, R0_dev, b, opts)
+
+    def solve():
+        return solve_with(so)
 
     for _ in range(max(args.warmup, 0)):
         res = solve()
@@ -343,11 +474,51 @@ def run_kes(args):
                  "algorithmic_bytes_per_step": bF}
         K.kes_set_filters_batch(h, wmin1, wmax1, taus, wl.L)
 
+    # time to all eigenpairs of the interval at rel_res <= 1e-8: the FP64 solve at the Krylov
+    # dimension that accepts every distinct eigenvalue of the interval (one projection, at the
+    # end), inputs resident, CUDA events on the library's stream
+    tts = None
+    so_t = None
+    if wl.tts_kmax and not batch and b == 1 and not args.no_tts:
+        so_t = K.kes_solve_opts_default()
+        so_t.kmax, so_t.tol, so_t.check_every = wl.tts_kmax, TTS_TOL, wl.tts_kmax
+        res_t = solve_with(so_t)                                   # warm-up: sizes the basis
+        times = []
+        barrier(dist)
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk_t:
+            for _ in range(max(1, args.tts_repeats)):
+                with torch.cuda.stream(stream):
+                    e0.record(stream)
+                    res_t = solve_with(so_t)
+                    e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1) / 1e3)
+        barrier(dist)
+        exact = spectra.omega2_in(problems[0].cells, problems[0].h, wmin1[0, 0], wmax1[0, 0])
+        distinct, _ = spectra.cluster(exact)
+        found, _ = spectra.cluster(res_t[0]["omega2"])
+        t_med = max_over_ranks(dist, statistics.median(times), dev)
+        tts = {"value": t_med, "unit": "s", "higher_is_better": False, "repeats_s": times,
+               "kmax": wl.tts_kmax, "tol": TTS_TOL, "L": wl.L, "time_steps": res_t[0]["time_steps"],
+               "accepted_pairs": res_t[0]["n_pairs"], "accepted_distinct": len(found),
+               "distinct_in_interval": len(distinct), "eigenvalues_in_interval": len(exact),
+               "all_distinct_found": len(found) >= len(distinct),
+               "max_rel_res": float(res_t[0]["rel_res"].max()) if res_t[0]["n_pairs"] else None,
+               "max_eig_rel_err_vs_exact": max((float(np.min(np.abs(exact - t)) / t) for t in res_t[0]["omega2"]),
+                                               default=None),
+               "gdof_steps_per_s": sum_over_ranks(dist, n * res_t[0]["time_steps"], dev) / t_med / 1e9,
+               "kmax_source": "the smallest Krylov dimension (steps of 10) at which this solve accepts every "
+                              "distinct eigenvalue of the interval (bench.py --mode tts)",
+               "clocks": clk_t.summary()}
+
     # end to end through the C ABI with host buffers: start block from pinned memory in,
-    # accepted Ritz pairs (values and vectors) out, every step
+    # accepted Ritz pairs (values and vectors) out, every step; the converged solve when
+    # the workload has one, else the headline solve
     R0_pinned = torch.from_numpy(R0_host).pin_memory()
     so_e2e = K.kes_solve_opts_default()
-    so_e2e.kmax, so_e2e.tol, so_e2e.want_vectors, so_e2e.check_every = so.kmax, so.tol, 1, so.check_every
+    src = so_t if so_t is not None else so
+    so_e2e.kmax, so_e2e.tol, so_e2e.check_every, so_e2e.want_vectors = src.kmax, src.tol, src.check_every, 1
     e2e_steps = args.e2e_steps
     barrier(dist)
     torch.cuda.synchronize()
@@ -359,13 +530,17 @@ def run_kes(args):
             r = [K.kes_krylov_solve(h, R0_pinned.numpy()[0], so_e2e)]
         else:
             r = K.kes_block_krylov_solve(h, R0_pinned.numpy(), b, so_e2e)
-        out_bytes = sum((x["vectors"].nbytes if x["vectors"] is not None else 0) + 4 * x["n_pairs"] * 8 for x in r)
+        out_bytes = sum((x["vectors"].nbytes if x["vectors"] is not None else 0) + 4 * x["n_pairs"] * 8
+                        + 4 * x["n_pairs"] for x in r)
     torch.cuda.synchronize()
     e2e = None
     if e2e_steps > 0:
         e2e_s = max_over_ranks(dist, (time.perf_counter() - t0) / e2e_steps, dev)
         e2e = {"value": sum_over_ranks(dist, n * b * r[0]["time_steps"], dev) / e2e_s / 1e9, "unit": METRIC,
-               "h2d_bytes_per_step": 8 * n * b, "d2h_bytes_per_step": out_bytes}
+               "h2d_bytes_per_step": 8 * n * b, "d2h_bytes_per_step": out_bytes,
+               "solve": ("the converged solve of `tts` (kmax %d)" % so_e2e.kmax) if so_t is not None
+                        else "the timed solve", "seconds_per_step": e2e_s,
+               "accepted_pairs_returned": sum(x["n_pairs"] for x in r)}
 
     # accuracy of the accepted pairs against the exact spectrum (tensor grids)
     eig_err = None
@@ -379,10 +554,7 @@ def run_kes(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         big = max(range(len(problems)), key=lambda j: problems[j].n)
-        v, steps, dt = oracle_sample(problems[big], taus[big], wl, args.cpu_seconds, ivs[big][0])
-        cpu = {"value": v, "unit": METRIC, "cores": cpu_cores_used(), "kind": "oracle",
-               "sample": f"{steps} leapfrog steps of the FP64 oracle filter, one vector, on "
-                         f"{problems[big].name} ({problems[big].n} dofs, {dt:.1f} s)"}
+        cpu = cpu_baseline(problems[big], taus[big], wl, args.cpu_seconds, ivs[big][0])
 
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
@@ -407,6 +579,7 @@ def run_kes(args):
         "e2e": e2e,
         "gpu_launches": int(stats["kernel_launches"]),
         "clocks": clk.summary(),
+        "tts": tts,
         "solve": {"accepted_pairs": [x["n_pairs"] for x in res] if batch else res[0]["n_pairs"],
                   "k_used": res[0]["k_used"], "time_steps": steps_per_solve,
                   "max_rel_res": max((float(x["rel_res"].max()) for x in res if x["n_pairs"]), default=None),
@@ -425,6 +598,8 @@ def run_kes(args):
 # ----------------------------------------------------------------------------- reference arm
 
 def run_reference(args):
+    """The oracle, as it stands, on every host core: one process per core, each step one
+    bounded sample of the workload's filter in all of them at once (rank 0 only)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
@@ -436,26 +611,35 @@ def run_reference(args):
     problem = problems[big]
     iv = wl.mesh_intervals(problem)[0]
     S = problem.to_scipy()
-    omega_pow = O.power_iteration(S, problem.m, start_block([problem], 1, wl.seed)[0], wl.power_iters)
+    v0 = start_block([problem], 1, wl.seed)[0]
+    omega_pow = O.power_iteration(S, problem.m, v0, wl.power_iters)
     tau = wl.cfl * 2.0 / omega_pow
-    per_step_budget = max(1.0, 60.0 / max(args.steps + args.warmup, 1))
-    samples = []
-    for i in range(args.warmup + args.steps):
-        v, steps, dt = oracle_sample(problem, tau, wl, per_step_budget, iv)
-        if i >= args.warmup:
-            samples.append((v, steps, dt))
-    total_units = sum(problem.n * s for _, s, _ in samples)
-    total_s = sum(dt for _, _, dt in samples)
-    value = total_units / total_s / 1e9
+    P = host_cores()
+    t0 = time.perf_counter()
+    O.filter_apply(S, problem.m, v0, tau, O.alpha_table(iv[0], iv[1], tau, 3))
+    per_step = (time.perf_counter() - t0) / 3
+    # about 90 s of oracle work over all warm-up and timed steps
+    steps = int(max(2, min(wl.L, 90.0 / max(args.steps + args.warmup, 1) / per_step)))
+    pool = OraclePool(problem, v0, tau, iv, P)
+    units, secs = 0, 0.0
+    try:
+        for i in range(args.warmup + args.steps):
+            u, w = pool.round(steps)
+            if i >= args.warmup:
+                units += u
+                secs += w
+    finally:
+        pool.close()
+    value = units / secs / 1e9
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / max(len(samples), 1),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "dofs": problem.n, "nnz": problem.nnz,
                    "interval": list(iv), "L": wl.L, "kmax": wl.kmax, "tau": tau},
-        "cpu_baseline": {"value": value, "unit": METRIC, "cores": cpu_cores_used(), "kind": "oracle",
-                         "sample": f"each step = {samples[0][1] if samples else 0} leapfrog steps of the FP64 "
-                                   f"oracle filter on {problem.name}"},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": P, "kind": "oracle", "cpu_model": cpu_model(),
+                         "sample": f"each step = {steps} leapfrog steps of the FP64 oracle filter on {problem.name} "
+                                   f"in each of {P} processes (one per host core) at once"},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -465,21 +649,39 @@ TTS_FORMS = (
     # name, precision, block width, FP64 refinement sweeps, refinement filter length / L
     ("fp64", "fp64", 1, 0, 1.0),
     ("fp32+refine1", "fp32", 1, 1, 1.0),
-    ("fp32+refine1_L/4", "fp32", 1, 1, 0.25),
-    ("fp32+refine1_L/8", "fp32", 1, 1, 0.125),
+    ("fp64_b8", "fp64", 8, 0, 1.0),
+    ("fp32_b8+refine1", "fp32", 8, 1, 1.0),
+    ("fp32_b8+refine1_L/2", "fp32", 8, 1, 0.5),
 )
-TTS_KMAX = (160, 200, 240, 280, 320, 360, 400)   # coarse sweep; then steps of 10 below the first success
+# coarse Krylov dimensions of the search (single vector, block of 8) and the final resolution
+TTS_GRID = {1: (160, 200, 240, 280, 320, 360, 400), 8: (320, 384, 448, 512, 576, 640, 704, 768, 832, 896)}
+TTS_RES = {1: 10, 8: 16}
+
+
+def matched_pairs(exact, accepted) -> int:
+    """Accepted Ritz values matched to the exact spectrum with multiplicity: for every
+    distinct exact eigenvalue, min(multiplicity, accepted values within 1e-8 of it)."""
+    import numpy as np
+    from fe_inputs import spectra
+    vals, mult = spectra.cluster(exact)
+    acc = np.sort(np.asarray(accepted, dtype=np.float64))
+    got = 0
+    for v, m in zip(vals, mult):
+        got += min(int(m), int(np.count_nonzero(np.abs(acc - v) <= 1e-8 * v)))
+    return got
 
 
 def run_tts(args):
     """Time to all eigenpairs in the interval at rel_res <= 1e-8, on the 128^3 cube
     (eigenvalues of multiplicity up to 6) and on a box of the same size with simple
-    eigenvalues: for each form a sweep over the Krylov dimension kmax (one projection at
-    the end, so that every run costs what a solve of that size costs), reporting each
-    run's time and the distinct eigenvalues it accepted; a form's time to solution is
-    that of the smallest kmax (to within 10) that accepts every distinct eigenvalue.
-    The FP32 forms reach 1e-8 through FP64 refinement sweeps on their in-interval Ritz
-    vectors, filtered 8 at a time, with the full filter or its first L/4 or L/8 steps."""
+    eigenvalues, for each form: the FP64 and FP32 single-vector solvers and the block
+    solvers with b = 8 (Sec. 4, block version), the FP32 ones followed by one sweep of FP64
+    filtered subspace iteration over their in-interval Ritz vectors (8 columns at a time,
+    with the full filter or its first L/2 steps). A form's time to solution is that of the
+    smallest Krylov dimension (one projection, at the end) that accepts every distinct
+    eigenvalue of the interval, found by a coarse search and bisection; the block forms
+    are also timed to every eigenpair with multiplicity. Runs that reach neither report
+    the residual floor of their in-interval Ritz pairs."""
     import numpy as np
     import torch
 
@@ -487,58 +689,81 @@ def run_tts(args):
     from fe_inputs import WORKLOADS, start_vectors
     from fe_inputs import spectra
 
-    tol = 1e-8
     forms = [f for f in TTS_FORMS if not args.tts_forms or f[0] in args.tts_forms.split(",")]
     out = []
-    for wname in args.tts_workloads.split(","):
-        wl = WORKLOADS[wname]
-        p = wl.build()
-        exact = spectra.omega2_in(p.cells, p.h, wl.omega_min, wl.omega_max)
-        distinct, _ = spectra.cluster(exact)
-        v0 = start_vectors(p.n, 1, wl.seed)[0]
-        runs, summary = [], {}
-        for name, prec, b, refine, frac in forms:
-            summary[name] = None
-            with K.Context(p, precision=prec, block_b=8) as c:
-                w, _ = K.kes_estimate_omega_max(c.handle, wl.power_iters, v0)
-                K.kes_set_filter(c.handle, wl.omega_min, wl.omega_max, wl.cfl * 2 / w, wl.L)
-                R = start_vectors(p.n, b, wl.seed + 1)
+    with ClockSampler(0) as clk:
+        for wname in args.tts_workloads.split(","):
+            wl = WORKLOADS[wname]
+            p = wl.build()
+            exact = spectra.omega2_in(p.cells, p.h, wl.omega_min, wl.omega_max)
+            distinct, _ = spectra.cluster(exact)
+            v0 = start_vectors(p.n, 1, wl.seed)[0]
+            runs, summary = [], {}
+            for name, prec, b, refine, frac in forms:
+                with K.Context(p, precision=prec, block_b=8) as c:
+                    w, _ = K.kes_estimate_omega_max(c.handle, wl.power_iters, v0)
+                    K.kes_set_filter(c.handle, wl.omega_min, wl.omega_max, wl.cfl * 2 / w, wl.L)
+                    R = start_vectors(p.n, b, wl.seed + 1)
+                    cache = {}
 
-                def run(kmax):
-                    so = K.kes_solve_opts_default()
-                    so.kmax, so.tol, so.check_every, so.refine_sweeps = kmax, tol, kmax, refine
-                    so.refine_L = int(round(frac * wl.L)) if frac < 1.0 else 0
-                    torch.cuda.synchronize()
-                    t0 = time.perf_counter()
-                    res = K.kes_block_krylov_solve(c.handle, R, b, so)[0]
-                    dt = time.perf_counter() - t0
-                    found, _ = spectra.cluster(res["omega2"])
-                    err = max((float(np.min(np.abs(exact - t)) / t) for t in res["omega2"]), default=None)
-                    runs.append({"form": name, "b": b, "kmax": kmax, "refine_sweeps": refine,
-                                 "refine_L": so.refine_L or wl.L, "seconds": dt,
-                                 "accepted_pairs": res["n_pairs"], "accepted_distinct": len(found),
-                                 "max_rel_res": float(res["rel_res"].max()) if res["n_pairs"] else None,
-                                 "max_eig_rel_err_vs_exact": err, "leapfrog_steps": res["time_steps"],
-                                 "fp64_refine_steps": res["refine_steps"]})
-                    print(json.dumps({"workload": wname, **runs[-1]}), file=sys.stderr, flush=True)
-                    if len(found) >= len(distinct):
-                        summary[name] = {"seconds": dt, "kmax": kmax, "accepted_pairs": res["n_pairs"]}
-                        return True
-                    return False
+                    def run(kmax):
+                        if kmax in cache:
+                            return cache[kmax]
+                        so = K.kes_solve_opts_default()
+                        so.kmax, so.tol, so.check_every, so.refine_sweeps = kmax, TTS_TOL, kmax, refine
+                        so.refine_L = int(round(frac * wl.L)) if frac < 1.0 else 0
+                        torch.cuda.synchronize()
+                        t0 = time.perf_counter()
+                        res = K.kes_block_krylov_solve(c.handle, R, b, so)[0]
+                        dt = time.perf_counter() - t0
+                        found, _ = spectra.cluster(res["omega2"])
+                        inside = res["ritz_rel_res"][~np.isnan(res["ritz_rel_res"])]
+                        rec = {"form": name, "b": b, "kmax": kmax, "refine_sweeps": refine,
+                               "refine_L": so.refine_L or wl.L, "seconds": dt,
+                               "accepted_pairs": res["n_pairs"], "accepted_distinct": len(found),
+                               "matched_with_multiplicity": matched_pairs(exact, res["omega2"]),
+                               "max_rel_res": float(res["rel_res"].max()) if res["n_pairs"] else None,
+                               "ritz_rel_res_median_in_interval": float(np.median(inside)) if inside.size else None,
+                               "max_eig_rel_err_vs_exact": max((float(np.min(np.abs(exact - t)) / t)
+                                                                for t in res["omega2"]), default=None),
+                               "leapfrog_steps": res["time_steps"], "fp64_refine_steps": res["refine_steps"]}
+                        runs.append(rec)
+                        print(json.dumps({"workload": wname, **rec}), file=sys.stderr, flush=True)
+                        cache[kmax] = rec
+                        return rec
 
-                last_fail = None
-                for kmax in TTS_KMAX:
-                    if run(kmax):
-                        lo = (last_fail or kmax - 40) + 10
-                        for k in range(lo, kmax, 10):   # the coarse step overshoots by up to 30
-                            if run(k):
-                                break
-                        break
-                    last_fail = kmax
-        out.append({"workload": wname, "dofs": p.n, "interval": [wl.omega_min, wl.omega_max], "L": wl.L,
-                    "distinct_in_interval": len(distinct), "eigenvalues_in_interval": len(exact),
-                    "time_to_all_distinct": summary, "runs": runs})
-    print(json.dumps({"mode": "tts", "tol": tol, "workloads": out}), flush=True)
+                    def search(ok):
+                        """Smallest kmax (to TTS_RES[b]) of the grid's range with ok(run(kmax))."""
+                        lo = None
+                        for kmax in TTS_GRID[b]:
+                            if ok(run(kmax)):
+                                hi = kmax
+                                lo = lo if lo is not None else max(b, kmax - (TTS_GRID[b][1] - TTS_GRID[b][0]))
+                                while hi - lo > TTS_RES[b]:
+                                    mid = (lo + hi) // 2 // b * b
+                                    if mid <= lo or mid >= hi:
+                                        break
+                                    if ok(run(mid)):
+                                        hi = mid
+                                    else:
+                                        lo = mid
+                                r = run(hi)
+                                return {"seconds": r["seconds"], "kmax": hi, "accepted_pairs": r["accepted_pairs"],
+                                        "max_rel_res": r["max_rel_res"]}
+                            lo = kmax
+                        best = max(cache.values(), key=lambda r: r["accepted_distinct"])
+                        return {"reached": False, "up_to_kmax": TTS_GRID[b][-1],
+                                "best_accepted_distinct": best["accepted_distinct"],
+                                "ritz_rel_res_median_in_interval": best["ritz_rel_res_median_in_interval"]}
+
+                    summary[name] = {"all_distinct": search(lambda r: r["accepted_distinct"] >= len(distinct))}
+                    if b > 1:
+                        summary[name]["all_with_multiplicity"] = search(
+                            lambda r: r["matched_with_multiplicity"] >= len(exact))
+            out.append({"workload": wname, "dofs": p.n, "interval": [wl.omega_min, wl.omega_max], "L": wl.L,
+                        "distinct_in_interval": len(distinct), "eigenvalues_in_interval": len(exact),
+                        "time_to_solution": summary, "runs": runs})
+    print(json.dumps({"mode": "tts", "tol": TTS_TOL, "clocks": clk.summary(), "workloads": out}), flush=True)
 
 
 def run_weights(args):

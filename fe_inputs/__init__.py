@@ -307,6 +307,8 @@ class Workload:
     intervals: object = None      # (Problem) -> list of (wmin, wmax); None: [(omega_min, omega_max)]
     check_every: int = 5
     tol: float = 0.0              # acceptance; 0: 1e-8 (fp64) / 1e-5 (fp32)
+    tts_kmax: int = 0             # Krylov dimension at which the FP64 solve accepts every distinct
+                                  # eigenvalue of the interval at 1e-8 (0: not measured)
 
     def mesh_intervals(self, p: Problem):
         return self.intervals(p) if self.intervals else [(self.omega_min, self.omega_max)]
@@ -341,10 +343,10 @@ WORKLOADS = {
     # a box of the cube's size with incommensurate edges (2,005,965 dofs): every
     # eigenvalue is simple; [24, 28] holds 81 of them (smallest relative gap 1.9e-5)
     "box2m_fp64": Workload("box2m_fp64", lambda: box_grid((136, 128, 118), extent=(1.0, 0.91, 0.83)),
-                           24.0, 28.0, L=600, kmax=60),
+                           24.0, 28.0, L=600, kmax=60, tts_kmax=210),
     # 3D unit cube, Kuhn tets, 128^3 cells (2,048,383 dofs)
     "cube128_fp64": Workload("cube128_fp64", lambda: box_grid((128, 128, 128)),
-                             40.0, 45.0, L=600, kmax=60),
+                             40.0, 45.0, L=600, kmax=60, tts_kmax=250),
     "cube128_fp32": Workload("cube128_fp32", lambda: box_grid((128, 128, 128)),
                              40.0, 45.0, L=600, kmax=60, precision="fp32"),
     # 12 uneven boxes in one context, blocks of 8 start vectors, 4 intervals per mesh

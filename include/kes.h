@@ -44,7 +44,8 @@ typedef enum kes_status {
                                       stepper) or the time stepping produced Inf/NaN */
   KES_ERR_CUDA = -4,               /* a CUDA runtime call failed */
   KES_ERR_OOM = -5,                /* device or host allocation failed */
-  KES_ERR_TIMEOUT = -6,            /* a bounded device-side wait gave up */
+  KES_ERR_TIMEOUT = -6,            /* a bounded device-side wait gave up (reserved: no kernel of this
+                                      library waits on another thread block) */
   KES_ERR_STATE = -7,              /* call out of order (e.g. filter not set) */
   KES_ERR_UNSUPPORTED = -8         /* option combination not implemented */
 } kes_status;
@@ -88,7 +89,7 @@ typedef struct kes_opts {
   int32_t compact_cols; /* 1 (default): the step kernels read each stored entry's column as the 16-bit
                            difference column - row when every entry's fits (2 bytes instead of 4: tensor
                            grids up to about 180 x 180 nodes per plane), else as int32; 0: always int32.
-                           Results are the same either way. The bulk-copy launch shapes read int32. */
+                           Results are the same either way. */
 } kes_opts;
 
 /* Options of kes_krylov_solve. Initialise with kes_solve_opts_default(). */

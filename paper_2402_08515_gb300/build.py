@@ -23,7 +23,6 @@ SOURCES = [
     "csrc/kernels_step.cu",
     "csrc/kernels_blas.cu",
     "csrc/kernels_block.cu",
-    "csrc/kernels_tma.cu",
     "csrc/kes_api.cu",
     "csrc/noalloc.cu",
 ]

@@ -357,41 +357,15 @@ void step_f32_impl(int grid, int block, cudaStream_t st, bool first, bool last, 
 
 }  // namespace
 
-// TMA-staged shapes (G consumer warps, S stages, CTAs per SM), tried after the
-// register-staged variants.
-#define KES_TMA_SHAPES(X) X(0, 8, 4, 1) X(1, 8, 3, 2) X(2, 16, 3, 1) X(3, 4, 4, 3) X(4, 4, 4, 2) X(5, 8, 2, 2)
-
 int step_variant_count() {
   int n = 0;
 #define X(ID, B, M) ++n;
   KES_STEP_VARIANTS(X)
 #undef X
-  static_assert(kRegStepVariants == 8, "register-staged variant count");
-#define X(ID, G, S, C) ++n;
-  KES_TMA_SHAPES(X)
-#undef X
   return n;
 }
 
-TmaShape tma_variant_shape(int variant, int wmax) {
-  TmaShape sh;
-  sh.wmax = wmax;
-  switch (variant - kRegStepVariants) {
-#define X(ID, G_, S_, C_) \
-  case ID:                \
-    sh.G = G_;            \
-    sh.S = S_;            \
-    sh.ctas_per_sm = C_;  \
-    break;
-    KES_TMA_SHAPES(X)
-#undef X
-    default: break;
-  }
-  return sh;
-}
-
 int step_blocks_per_sm(bool fp32, int variant, int block) {
-  if (variant >= kRegStepVariants) return tma_variant_shape(variant, 1).ctas_per_sm;
   int nb = 0;
   cudaError_t e = cudaErrorInvalidValue;
   switch (variant) {
@@ -410,18 +384,6 @@ int step_blocks_per_sm(bool fp32, int variant, int block) {
 void launch_step_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bool first, const double* x,
                      const double* g, const double* prev, double* out, double* acc, int64_t acc_stride, int F,
                      const double* alpha, int L, int step, bool last, int* flag) {
-  if (cfg.variant >= kRegStepVariants && g != x) {  // the bulk-copy shapes gather from u_n only
-    LaunchCfg reg = cfg;
-    reg.variant = 3;
-    reg.grid_step = cfg.n_sm * step_blocks_per_sm(false, 3, cfg.block_step);
-    launch_step_f64(A, reg, st, first, x, g, prev, out, acc, acc_stride, F, alpha, L, step, last, flag);
-    return;
-  }
-  if (cfg.variant >= kRegStepVariants) {
-    launch_step_tma_f64(A, cfg.tma, cfg.n_sm, st, first, last, x, prev, out, acc, acc_stride, F, alpha, L, step,
-                        flag);
-    return;
-  }
   const int grid = grid_for(cfg, A.n_slices);
   switch (cfg.variant) {
 #define X(ID, B, M)                                                                                        \
@@ -440,19 +402,6 @@ void launch_step_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bo
                      const float* g, const float* prev, float* out, float* acc_s, float* acc_c, double* acc64,
                      int64_t acc_stride, int F, const float* alpha_hi, const float* alpha_lo, int L, int step,
                      int* flag) {
-  if (cfg.variant >= kRegStepVariants && g != x) {  // the bulk-copy shapes gather from u_n only
-    LaunchCfg reg = cfg;
-    reg.variant = 3;
-    reg.grid_step = cfg.n_sm * step_blocks_per_sm(true, 3, cfg.block_step);
-    launch_step_f32(A, reg, st, first, last, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, F, alpha_hi, alpha_lo,
-                    L, step, flag);
-    return;
-  }
-  if (cfg.variant >= kRegStepVariants) {
-    launch_step_tma_f32(A, cfg.tma, cfg.n_sm, st, first, last, x, prev, out, acc_s, acc_c, acc64, acc_stride, F,
-                        alpha_hi, alpha_lo, L, step, flag);
-    return;
-  }
   const int grid = grid_for(cfg, A.n_slices);
   switch (cfg.variant) {
 #define X(ID, B, M)                                                                                        \

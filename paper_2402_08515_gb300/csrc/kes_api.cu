@@ -424,7 +424,7 @@ kes_status check_flag(kes_ctx* c) {
   c->sync();
   if (flag) {
     KES_CUDA(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
-    return (flag & 2) ? KES_ERR_TIMEOUT : KES_ERR_UNSTABLE;
+    return KES_ERR_UNSTABLE;
   }
   return KES_OK;
 }
@@ -469,19 +469,11 @@ SellDev mesh_sell(const kes_ctx* c, const MeshInfo& m) {
   return a;
 }
 
-// Makes launch shape v of the single-vector step kernel current; false if it cannot run
-// on this matrix (a TMA shape whose stage would not fit in shared memory).
-bool select_variant(kes_ctx* c, int v) {
+// Makes launch shape v of the single-vector step kernel current.
+void select_variant(kes_ctx* c, int v) {
   const bool fp32 = c->opts.precision == KES_PREC_FP32;
-  if (v >= kRegStepVariants) {
-    const TmaShape sh = tma_variant_shape(v, c->cfg.tma.wmax);
-    if (!tma_shape_fits(fp32, sh)) return false;
-    KES_CUDA(tma_prepare(fp32, sh));
-    c->cfg.tma = sh;
-  }
   c->cfg.variant = v;
   c->cfg.grid_step = c->cfg.n_sm * step_blocks_per_sm(fp32, v, c->cfg.block_step);
-  return true;
 }
 
 // Times every launch shape of the step kernels on this matrix (a few steps on zeroed
@@ -512,10 +504,7 @@ void tune_steps(kes_ctx* c) {
   int best = 0;
   float best_ms = 3.0e38f;
   for (int v = 0; v < step_variant_count(); ++v) {
-    // the fourth-order step gathers from its stage and the compact index is read only by
-    // the register-staged shapes: the bulk-copy shapes take part in neither
-    if ((c->opts.stepper == KES_STEPPER_LEAPFROG4 || c->A.dcol) && v >= kRegStepVariants) continue;
-    if (!select_variant(c, v)) continue;
+    select_variant(c, v);
     const float ms = timed([&](int count) {
       for (int i = 0; i < count; ++i) {
         if (fp32)
@@ -645,9 +634,6 @@ void build_context(kes_ctx* c, int nm, const int64_t* n, const int64_t* const* r
     }
   }
   sp[n_slices] = at;
-  int64_t wmax = 0;
-  for (int64_t sl = 0; sl < n_slices; ++sl) wmax = std::max(wmax, (sp[sl + 1] - sp[sl]) / kSliceC);
-  c->cfg.tma.wmax = static_cast<int>(wmax);
   sells.clear();
   // the leapfrog's 2 u_n folds into the diagonal of the FP64 step values when each row of a
   // mesh has an entry at its own column (a stored diagonal, or SELL padding of a short row,
@@ -810,7 +796,7 @@ kes_status create_impl(kes_ctx** out, int32_t nm, const int64_t* n, const int64_
     const bool fp32 = c->opts.precision == KES_PREC_FP32;
     c->cfg.n_sm = n_sm;
     c->cfg.block_step = 256;
-    if (!select_variant(c, c->opts.step_variant)) throw KesError{KES_ERR_UNSUPPORTED};
+    select_variant(c, c->opts.step_variant);
     c->cfg.variant_blk = c->opts.blk_variant;
     c->cfg.grid_blk =
         n_sm * blk_blocks_per_sm(fp32, c->NBcap > 1 ? c->NBcap : 2, c->opts.blk_variant, c->cfg.block_step);
@@ -1106,7 +1092,7 @@ kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, co
       c->sync();
       if (flag) {
         KES_CUDA(cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
-        throw KesError{(flag & 2) ? KES_ERR_TIMEOUT : KES_ERR_UNSTABLE};
+        throw KesError{KES_ERR_UNSTABLE};
       }
       // phase 2 for the vectors that are not dependent: b_k = w / ||w||_M, S b_k (one
       // launch per interval over all meshes), the new column b_i^T S b_k of H

@@ -65,18 +65,11 @@ struct SellDev {
   const int32_t* slice_mesh = nullptr;
 };
 
-// Shape of the TMA-staged step kernel: G consumer warps (slices per chunk), S ring
-// stages, wmax = the widest slice of the matrix (entries per row), CTAs per SM.
-struct TmaShape {
-  int G = 8, S = 4, wmax = 0, ctas_per_sm = 1;
-};
-
 struct LaunchCfg {
   int grid_step = 0;   // blocks of the step / SpMV kernels (grid-stride over slices)
   int block_step = 256;
   int n_sm = 152;
   int variant = 0;     // step-kernel launch shape (load batch, register cap), see step_variant_count
-  TmaShape tma;        // used when variant >= kRegStepVariants
   int grid_blk = 0;    // blocks of the block (SpMM) step kernels
   int variant_blk = 0; // their launch shape (register cap), see blk_variant_count
 };
@@ -86,7 +79,7 @@ struct LaunchCfg {
 //   out = (2 x - prev) + A g;   acc_f += alpha_f[step+1] * out   (f < F)
 // (A.fold2: out = -prev + (A + 2I) x, the same sum with the 2 x in the diagonal values.)
 // g = x for the leapfrog; g = the stage v = x + A x / 12 (launch_stage4_*) for the
-// fourth-order scheme (bulk-copy shapes need g = x and fall back to a register shape).
+// fourth-order scheme.
 // first: prev = x and acc_f = alpha_f[0] * x + alpha_f[1] * out.
 // x, prev, out, acc: length n_pad; acc_f at acc + f * acc_stride; alpha of mesh m, table f at
 // alpha + (m * F + f) * (L+1). last: the state of the final step is not stored;
@@ -144,22 +137,8 @@ void launch_unpack_block(cudaStream_t st, const double* stage, int NB, double* W
 // Launch-shape variants of the step kernels (same arithmetic, different load batch and
 // register cap) and the resident blocks per SM of one variant (occupancy calculator);
 // the step grid is n_sm * that, so that the grid-stride loop runs in one wave.
-// Variants 0 .. kRegStepVariants-1 stage the matrix in registers; the TMA shapes follow.
-constexpr int kRegStepVariants = 8;
 int step_variant_count();
 int step_blocks_per_sm(bool fp32, int variant, int block);
-TmaShape tma_variant_shape(int variant, int wmax);  // variant >= kRegStepVariants
-
-// TMA-staged step kernels (same arithmetic as the register-staged ones; see kernels_tma.cu).
-bool tma_shape_fits(bool fp32, const TmaShape& sh);
-cudaError_t tma_prepare(bool fp32, const TmaShape& sh);  // dynamic shared memory attribute
-void launch_step_tma_f64(const SellDev& A, const TmaShape& sh, int n_sm, cudaStream_t st, bool first, bool last,
-                         const double* x, const double* prev, double* out, double* acc, int64_t acc_stride, int F,
-                         const double* alpha, int L, int step, int* flag);
-void launch_step_tma_f32(const SellDev& A, const TmaShape& sh, int n_sm, cudaStream_t st, bool first, bool last,
-                         const float* x, const float* prev, float* out, float* acc_s, float* acc_c, double* acc64,
-                         int64_t acc_stride, int F, const float* alpha_hi, const float* alpha_lo, int L, int step,
-                         int* flag);
 
 // Step values A = -tau^2 M^{-1} S from the values of S (A.val64) and tau^2/m per row:
 // out64[e] = -tau2m[row(e)] * val64[e] and/or out32[e] = (float) of the same (either may be null).

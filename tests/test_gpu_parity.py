@@ -222,24 +222,18 @@ def test_state_errors():
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_every_step_launch_shape_rounds_identically(problems, precision):
-    # the autotuner may pick any shape (register-staged or TMA-staged); all of them
-    # must give the bitwise same filter
+    # the autotuner may pick any shape; all of them must give the bitwise same filter
     p = problems["box_ragged"]
     tau = _tau_for(p)
     r = start_vectors(p.n, 1, 12)
     outs = []
     for v in range(K.kes_launch_shapes()[0]):
-        try:
-            c = K.Context(p, precision=precision, step_variant=v)
-        except K.KesError as e:            # a TMA shape that does not fit this matrix
-            assert e.status == -8
-            continue
-        with c:
+        with K.Context(p, precision=precision, step_variant=v) as c:
             K.kes_set_filter(c.handle, 10.0, 20.0, tau, 40)
             o = np.zeros((1, 1, p.n))
             K.kes_filter_apply(c.handle, r, o, 1)
             outs.append(o)
-    assert len(outs) >= 10
+    assert len(outs) == K.kes_launch_shapes()[0] >= 8
     for o in outs[1:]:
         np.testing.assert_array_equal(o, outs[0])
 
