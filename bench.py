@@ -54,15 +54,23 @@ def parse_args(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--tts-repeats", type=int, default=3, help="timed converged solves of the tts field")
     ap.add_argument("--no-tts", action="store_true", help="leave out the converged solve (tts, and e2e through it)")
+    ap.add_argument("--no-batch-filter", action="store_true", help="leave out the 12-mesh batched filter measurement")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle samples (1 core + all cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="solve", choices=["solve", "filter", "tts", "weights"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "filter", "tts", "weights", "certify"],
                     help="filter: one filter application only (small profiling runs); tts: time to "
                          "converged eigenpairs at residual 1e-8, FP64 form against the FP32 forms with FP64 "
                          "refinement")
     ap.add_argument("--tts-forms", default="", help="comma-separated subset of the --mode tts forms")
+    ap.add_argument("--tts-kmax", default="", help="comma-separated Krylov dimensions: run each form at these only "
+                                                   "(no search)")
     ap.add_argument("--tts-workloads", default="cube128_fp64,box2m_fp64", help="workloads of --mode tts")
-    ap.add_argument("--L", type=int, default=0, help="override the workload's time steps (--mode filter)")
+    ap.add_argument("--L", type=int, default=0, help="override the workload's time steps (--mode filter, certify)")
+    ap.add_argument("--kmax", type=int, default=0, help="override the workload's Krylov dimension (--mode certify)")
+    ap.add_argument("--interval", default="", help="override the filter interval as 'wmin,wmax' (--mode certify)")
+    ap.add_argument("--tol", type=float, default=0.0, help="override the acceptance tolerance (--mode certify)")
+    ap.add_argument("--refine-sweeps", type=int, default=0, help="FP64 refinement sweeps (--mode certify)")
+    ap.add_argument("--refine-extra", type=int, default=0, help="buffer Ritz vectors of the refinement (--mode certify)")
     ap.add_argument("--blk-variant", type=int, default=None,
                     help="fixed block step-kernel launch shape instead of the autotuner's choice")
     ap.add_argument("--variant", type=int, default=None,
@@ -365,6 +373,49 @@ def start_block(problems, b, seed):
 
 # ----------------------------------------------------------------------------- kes arm
 
+def batch_filter_measurement(dev, stream, reps: int = 3) -> dict:
+    """The batched SpMM step on the 12-mesh batch (3.14 M dofs, 8 FP32 columns per mesh, one
+    interval per mesh; and the four intervals of every mesh from one trajectory): one filter
+    application of L = 600 steps, warm, then `reps` timed by the library's CUDA events."""
+    import numpy as np
+    import torch
+
+    import paper_2402_08515_gb300 as K
+    from fe_inputs import WORKLOADS
+    wl = WORKLOADS["batch12_fp32"]
+    problems = wl.build()
+    n = sum(p.n for p in problems)
+    out = {"workload": "batch12_fp32", "meshes": len(problems), "dofs": n, "b": wl.b, "L": wl.L}
+    peak, _ = load_peak()
+    with K.Context(problems, precision=wl.precision, stream=stream, block_b=wl.b) as ctx:
+        h = ctx.handle
+        omega, _ = K.kes_estimate_omega_max_batch(h, wl.power_iters, start_block(problems, 1, wl.seed)[0])
+        taus = wl.cfl * 2.0 / omega
+        ivs = [wl.mesh_intervals(p) for p in problems]
+        R = torch.from_numpy(start_block(problems, wl.b, wl.seed + 1)).to(dev)
+        for F in (1, len(ivs[0])):
+            wmin = np.array([[a for a, _ in iv[:F]] for iv in ivs])
+            wmax = np.array([[c for _, c in iv[:F]] for iv in ivs])
+            K.kes_set_filters_batch(h, wmin, wmax, taus, wl.L)
+            res = torch.zeros((F, wl.b, n), dtype=torch.float64, device=dev)
+            K.kes_filter_apply(h, R, res, wl.b)
+            K.kes_sync(h)
+            K.kes_reset_stats(h)
+            for _ in range(reps):
+                K.kes_filter_apply(h, R, res, wl.b)
+            st = K.kes_get_stats(h)
+            step_us = 1e3 * st["filter_ms"] / max(st["filter_steps"], 1)
+            nbytes = K.kes_step_bytes(h, wl.b, F)
+            gbs = nbytes / (step_us / 1e6) / 1e9
+            out[f"F{F}"] = {"step_us": step_us, "algorithmic_bytes_per_step": nbytes, "achieved_gbs": gbs,
+                            "frac": gbs / peak, "gdof_steps_per_s": n * wl.b / (step_us / 1e6) / 1e9,
+                            "finite": bool(torch.isfinite(res).all())}
+        out["kernel"] = "k_step_blk<float,8>"
+        out["blk_variant"] = st["blk_variant"]
+        out["timing"] = f"{reps} filter applications of {wl.L} steps, CUDA events on the library stream, after one warm"
+    return out
+
+
 def run_kes(args):
     import numpy as np
     import torch
@@ -551,6 +602,11 @@ def run_kes(args):
                 e = float(np.min(np.abs(exact - t)) / t)
                 eig_err = e if eig_err is None else max(eig_err, e)
 
+    # the batched SpMM step of the 12-mesh batch (secondary: the default line's other kernel)
+    batch_filter = None
+    if args.workload == "cube128_fp64" and not args.no_batch_filter:
+        batch_filter = batch_filter_measurement(dev, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         big = max(range(len(problems)), key=lambda j: problems[j].n)
@@ -588,6 +644,8 @@ def run_kes(args):
     }
     if multi:
         line["filter_multi_interval"] = multi
+    if batch_filter:
+        line["batch12_filter"] = batch_filter
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -646,16 +704,19 @@ def run_reference(args):
 
 
 TTS_FORMS = (
-    # name, precision, block width, FP64 refinement sweeps, refinement filter length / L
-    ("fp64", "fp64", 1, 0, 1.0),
-    ("fp32+refine1", "fp32", 1, 1, 1.0),
-    ("fp64_b8", "fp64", 8, 0, 1.0),
-    ("fp32_b8+refine1", "fp32", 8, 1, 1.0),
-    ("fp32_b8+refine1_L/2", "fp32", 8, 1, 0.5),
+    # name, precision, block width, FP64 refinement sweeps, refinement filter length / L,
+    # Ritz vectors nearest outside the interval refined as a buffer
+    ("fp64", "fp64", 1, 0, 1.0, 0),
+    ("fp32+refine1", "fp32", 1, 1, 1.0, 0),
+    ("fp32+refine1_L/2", "fp32", 1, 1, 0.5, 0),
+    ("fp64_b8", "fp64", 8, 0, 1.0, 0),
+    ("fp32_b8+refine1", "fp32", 8, 1, 1.0, 0),
+    ("fp32_b8+refine1+16", "fp32", 8, 1, 1.0, 16),
+    ("fp32_b8+refine1_L/2", "fp32", 8, 1, 0.5, 0),
 )
 # coarse Krylov dimensions of the search (single vector, block of 8) and the final resolution
-TTS_GRID = {1: (160, 200, 240, 280, 320, 360, 400), 8: (320, 384, 448, 512, 576, 640, 704, 768, 832, 896)}
-TTS_RES = {1: 10, 8: 16}
+TTS_GRID = {1: (160, 200, 240, 280, 320, 360, 400), 8: (512, 640, 768, 896, 1024, 1152)}
+TTS_RES = {1: 10, 8: 32}
 
 
 def matched_pairs(exact, accepted) -> int:
@@ -699,7 +760,7 @@ def run_tts(args):
             distinct, _ = spectra.cluster(exact)
             v0 = start_vectors(p.n, 1, wl.seed)[0]
             runs, summary = [], {}
-            for name, prec, b, refine, frac in forms:
+            for name, prec, b, refine, frac, extra in forms:
                 with K.Context(p, precision=prec, block_b=8) as c:
                     w, _ = K.kes_estimate_omega_max(c.handle, wl.power_iters, v0)
                     K.kes_set_filter(c.handle, wl.omega_min, wl.omega_max, wl.cfl * 2 / w, wl.L)
@@ -712,13 +773,16 @@ def run_tts(args):
                         so = K.kes_solve_opts_default()
                         so.kmax, so.tol, so.check_every, so.refine_sweeps = kmax, TTS_TOL, kmax, refine
                         so.refine_L = int(round(frac * wl.L)) if frac < 1.0 else 0
+                        so.refine_extra = extra
+                        K.kes_reset_stats(c.handle)
                         torch.cuda.synchronize()
                         t0 = time.perf_counter()
                         res = K.kes_block_krylov_solve(c.handle, R, b, so)[0]
                         dt = time.perf_counter() - t0
+                        st = K.kes_get_stats(c.handle)
                         found, _ = spectra.cluster(res["omega2"])
                         inside = res["ritz_rel_res"][~np.isnan(res["ritz_rel_res"])]
-                        rec = {"form": name, "b": b, "kmax": kmax, "refine_sweeps": refine,
+                        rec = {"form": name, "b": b, "kmax": kmax, "refine_sweeps": refine, "refine_extra": extra,
                                "refine_L": so.refine_L or wl.L, "seconds": dt,
                                "accepted_pairs": res["n_pairs"], "accepted_distinct": len(found),
                                "matched_with_multiplicity": matched_pairs(exact, res["omega2"]),
@@ -726,7 +790,8 @@ def run_tts(args):
                                "ritz_rel_res_median_in_interval": float(np.median(inside)) if inside.size else None,
                                "max_eig_rel_err_vs_exact": max((float(np.min(np.abs(exact - t)) / t)
                                                                 for t in res["omega2"]), default=None),
-                               "leapfrog_steps": res["time_steps"], "fp64_refine_steps": res["refine_steps"]}
+                               "leapfrog_steps": res["time_steps"], "fp64_refine_steps": res["refine_steps"],
+                               "filter_s": st["filter_ms"] / 1e3, "other_kernels_s": st["solve_other_ms"] / 1e3}
                         runs.append(rec)
                         print(json.dumps({"workload": wname, **rec}), file=sys.stderr, flush=True)
                         cache[kmax] = rec
@@ -756,6 +821,10 @@ def run_tts(args):
                                 "best_accepted_distinct": best["accepted_distinct"],
                                 "ritz_rel_res_median_in_interval": best["ritz_rel_res_median_in_interval"]}
 
+                    if args.tts_kmax:                      # fixed Krylov dimensions, no search
+                        for kmax in (int(t) for t in args.tts_kmax.split(",")):
+                            run(kmax)
+                        continue
                     summary[name] = {"all_distinct": search(lambda r: r["accepted_distinct"] >= len(distinct))}
                     if b > 1:
                         summary[name]["all_with_multiplicity"] = search(
@@ -764,6 +833,77 @@ def run_tts(args):
                         "distinct_in_interval": len(distinct), "eigenvalues_in_interval": len(exact),
                         "time_to_solution": summary, "runs": runs})
     print(json.dumps({"mode": "tts", "tol": TTS_TOL, "clocks": clk.summary(), "workloads": out}), flush=True)
+
+
+def run_certify(args):
+    """One solve of the workload (block solver, every mesh) with the accepted Ritz vectors
+    copied back, each pair certified on the host from its vector alone: the FP64 residual
+    ||S x - theta M x||_2 / (theta ||M x||_2) of eq. (res) recomputed with the workload's
+    CSR matrix (scipy), and, on tensor grids, the eigenvalue against the closed form."""
+    import numpy as np
+    import torch
+
+    import paper_2402_08515_gb300 as K
+    from fe_inputs import WORKLOADS
+    from fe_inputs import spectra
+
+    wl = WORKLOADS[args.workload]
+    problems, batch = workload_problems(wl)
+    b = wl.b
+    L = args.L or wl.L
+    t_build = time.perf_counter()
+    with K.Context(problems if batch else problems[0], precision=wl.precision, block_b=b) as c:
+        v0 = start_block(problems, 1, wl.seed)[0]
+        omega_pow, _ = K.kes_estimate_omega_max_batch(c.handle, wl.power_iters, v0)
+        taus = wl.cfl * 2.0 / omega_pow
+        if args.interval:
+            a, z = (float(t) for t in args.interval.split(","))
+            ivs = [[(a, z)] for _ in problems]
+        else:
+            ivs = [wl.mesh_intervals(p)[:1] for p in problems]
+        K.kes_set_filters_batch(c.handle, np.array([[iv[0][0]] for iv in ivs]), np.array([[iv[0][1]] for iv in ivs]),
+                                taus, L)
+        so = K.kes_solve_opts_default()
+        so.kmax = args.kmax or wl.kmax
+        so.tol = args.tol or wl.acceptance()
+        so.check_every = so.kmax
+        so.refine_sweeps = args.refine_sweeps
+        so.refine_extra = args.refine_extra
+        so.want_vectors = 1
+        R0 = start_block(problems, b, wl.seed + 1)
+        setup_s = time.perf_counter() - t_build
+        torch.cuda.synchronize()
+        with ClockSampler(0) as clk:
+            t0 = time.perf_counter()
+            res = K.kes_block_krylov_solve(c.handle, R0, b, so)
+            solve_s = time.perf_counter() - t0
+        meshes = []
+        for p, r, iv, tau in zip(problems, res, ivs, taus):
+            S = p.to_scipy()
+            host_rel, eig_err = [], []
+            for th, x in zip(r["omega2"], r["vectors"] if r["vectors"] is not None else []):
+                mx = p.m * x
+                host_rel.append(float(np.linalg.norm(S @ x - th * mx) / (th * np.linalg.norm(mx))))
+                if p.cells and not p.meta.get("length"):
+                    exact = spectra.omega2_in(p.cells, p.h, iv[0][0], iv[0][1])
+                    eig_err.append(float(np.min(np.abs(exact - th)) / th) if exact.size else None)
+            inside = r["ritz_rel_res"][~np.isnan(r["ritz_rel_res"])]
+            meshes.append({"mesh": p.name, "dofs": p.n, "interval": list(iv[0]), "tau": float(tau),
+                           "accepted_pairs": r["n_pairs"],
+                           "omega": [float(w) for w in r["omega"]],
+                           "library_rel_res_max": float(r["rel_res"].max()) if r["n_pairs"] else None,
+                           "host_rel_res_max": max(host_rel) if host_rel else None,
+                           "host_rel_res_all_within_tol": bool(all(h <= so.tol * (1 + 1e-6) for h in host_rel)),
+                           "host_vs_library_rel_res_max_ratio": (max(h / l for h, l in zip(host_rel, r["rel_res"]))
+                                                                 if host_rel else None),
+                           "max_eig_rel_err_vs_exact": max((e for e in eig_err if e is not None), default=None),
+                           "in_interval_ritz_values": int(inside.size),
+                           "ritz_rel_res_median_in_interval": float(np.median(inside)) if inside.size else None,
+                           "k_used": r["k_used"], "leapfrog_steps": r["time_steps"],
+                           "fp64_refine_steps": r["refine_steps"]})
+    print(json.dumps({"mode": "certify", "workload": args.workload, "precision": wl.precision, "b": b, "L": L,
+                      "kmax": so.kmax, "tol": so.tol, "refine_sweeps": so.refine_sweeps, "setup_s": setup_s,
+                      "solve_s": solve_s, "clocks": clk.summary(), "meshes": meshes}), flush=True)
 
 
 def run_weights(args):
@@ -829,6 +969,9 @@ def main(argv=None):
         return
     if args.mode == "weights":
         run_weights(args)
+        return
+    if args.mode == "certify":
+        run_certify(args)
         return
     if args.impl == "reference":
         run_reference(args)

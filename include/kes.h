@@ -94,7 +94,9 @@ typedef struct kes_opts {
 
 /* Options of kes_krylov_solve. Initialise with kes_solve_opts_default(). */
 typedef struct kes_solve_opts {
-  int32_t kmax;         /* Krylov dimension: number of basis vectors b_0..b_{kmax-1} (kmax-1 filter applications) */
+  int32_t kmax;         /* Krylov dimension: number of basis vectors b_0..b_{kmax-1} (kmax-1 filter applications);
+                           at most 3584 (KES_ERR_UNSUPPORTED above: the projection kernels hold kmax x 8
+                           coefficients in one block's shared memory) */
   int32_t check_every;  /* solve the projected problem every this many new basis vectors (and at the end) */
   int32_t n_wanted;     /* stop as soon as this many pairs are accepted (0: run to kmax) */
   int32_t want_vectors; /* 1: return the accepted Ritz vectors B y (host, n x n_pairs col-major) */
@@ -105,6 +107,8 @@ typedef struct kes_solve_opts {
   int32_t refine_L;      /* leapfrog steps of the refinement filter: the first refine_L + 1 weights of the
                             installed tables, i.e. the same interval with end time refine_L * tau
                             (eq. weightf does not depend on T); 0 or >= L: L */
+  int32_t refine_extra;  /* the refinement sweeps also filter this many Ritz vectors whose Ritz values lie
+                            nearest outside the interval (a buffer; 0: the in-interval ones only) */
 } kes_solve_opts;
 
 /* Result of kes_krylov_solve; host memory owned by the library. */
@@ -361,19 +365,28 @@ kes_status kes_reset_stats(kes_ctx* ctx);
  * mid-run. kes_create allocates the context's state, so those callers use this
  * function: they own every input and the output, and the two leapfrog state
  * vectors live in a fixed array inside the library, 2 * KES_NOALLOC_MAX_N doubles
- * (16 MiB), which every GPU that loads the library holds until the process exits.
+ * (16 MiB), which every GPU where the library's module is loaded holds until the
+ * process exits.
  *   n        rows, 1 <= n <= KES_NOALLOC_MAX_N; a larger n returns KES_ERR_ARG and launches nothing
  *   row_ptr  device int64[n+1]; col device int32[nnz]; val device float64[nnz]: CSR of S
  *   tau2m    device float64[n], tau^2 / m_i
  *   alpha    device float64[L+1], the weights kes_alpha_table returns (L >= 1 steps)
  *   r_in     device float64[n]; r_out device float64[n] receives the filtered vector
  *   stream   cudaStream_t (NULL: the legacy default stream); the call only enqueues the work
- * The first call on a device looks up the array's device address (once per device,
- * with that device current); make that first call before any stream capture. Every
- * call shares the array, which keeps the last call's contents (each call writes every
- * entry before reading it, so nothing needs clearing); calls whose GPU work overlaps
- * race on it. A CFL violation is not detected here: it shows as huge or non-finite
- * values in r_out. Calls no cudaMalloc, cudaFree or other allocating routine.
+ * Preconditions that are NOT checked (the arrays stay on the device, unlike kes_create's):
+ * row_ptr[0] = 0, row_ptr non-decreasing, row_ptr[n] = nnz; every col entry in [0, n);
+ * every array of the stated length and on the current device. A violation is an
+ * out-of-bounds device access, not an error status.
+ * Set-up: the first call on a device loads the library's module there (CUDA loads
+ * modules lazily by default), which takes the 16 MiB array and the module's code from
+ * device memory, and looks up the array's address (once per device, with that device
+ * current). A caller that reserves all of its device memory must make one call before
+ * it does (or run with CUDA_MODULE_LOADING=EAGER); make that first call before any
+ * stream capture as well. Every call shares the array, which keeps the last call's
+ * contents (each call writes every entry before reading it, so nothing needs
+ * clearing); calls whose GPU work overlaps race on it. A CFL violation is not detected
+ * here: it shows as huge or non-finite values in r_out. Calls no cudaMalloc, cudaFree
+ * or other allocating routine.
  */
 #define KES_NOALLOC_MAX_N 1048576
 kes_status kes_filter_apply_noalloc(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val,

@@ -66,7 +66,7 @@ class KesOpts(C.Structure):
 class KesSolveOpts(C.Structure):
     _fields_ = [("kmax", C.c_int32), ("check_every", C.c_int32), ("n_wanted", C.c_int32),
                 ("want_vectors", C.c_int32), ("tol", C.c_double), ("refine_sweeps", C.c_int32),
-                ("refine_L", C.c_int32)]
+                ("refine_L", C.c_int32), ("refine_extra", C.c_int32)]
 
 
 class KesResult(C.Structure):
@@ -430,9 +430,28 @@ KES_NOALLOC_MAX_N = 1048576
 
 def kes_filter_apply_noalloc(n, row_ptr, col, val, tau2m, alpha, L, r_in, r_out, stream=None) -> None:
     """Allocation-free FP64 filter of one vector; every array argument is a CUDA tensor the
-    caller owns (int64 row_ptr, int32 col, float64 val / tau2m / alpha / r_in / r_out)."""
-    _check(lib.kes_filter_apply_noalloc(int(n), _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(tau2m), _ptr(alpha),
-                                        int(L), _ptr(r_in), _ptr(r_out), stream), "kes_filter_apply_noalloc")
+    caller owns (int64 row_ptr, int32 col, float64 val / tau2m / alpha / r_in / r_out), all
+    contiguous and on one device, which this call makes current. Shapes and dtypes are
+    checked here (KesError KES_ERR_ARG otherwise); the CSR contents are not (see kes.h)."""
+    import torch
+    n, L = int(n), int(L)
+    want = {"row_ptr": (row_ptr, torch.int64, n + 1), "col": (col, torch.int32, None),
+            "val": (val, torch.float64, None), "tau2m": (tau2m, torch.float64, n),
+            "alpha": (alpha, torch.float64, L + 1), "r_in": (r_in, torch.float64, n),
+            "r_out": (r_out, torch.float64, n)}
+    if 1 <= n <= KES_NOALLOC_MAX_N and L >= 1:
+        devs = set()
+        for name, (t, dt, size) in want.items():
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()
+                    and t.dim() == 1 and (size is None or t.numel() == size)):
+                raise KesError(-1, f"kes_filter_apply_noalloc: {name} must be a contiguous 1-D CUDA {dt} tensor"
+                               + (f" of {size} entries" if size is not None else ""))
+            devs.add(t.device)
+        if len(devs) != 1 or col.numel() != val.numel():
+            raise KesError(-1, "kes_filter_apply_noalloc: tensors on several devices, or col and val differ in length")
+        torch.cuda.set_device(devs.pop())
+    _check(lib.kes_filter_apply_noalloc(n, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(tau2m), _ptr(alpha),
+                                        L, _ptr(r_in), _ptr(r_out), stream), "kes_filter_apply_noalloc")
 
 
 # ------------------------------------------------------------------ convenience

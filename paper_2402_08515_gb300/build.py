@@ -24,9 +24,10 @@ SOURCES = [
     "csrc/kernels_blas.cu",
     "csrc/kernels_block.cu",
     "csrc/kes_api.cu",
+    "csrc/solver.cu",
     "csrc/noalloc.cu",
 ]
-HEADERS = ["csrc/kes_internal.h", os.path.join("..", "include", "kes.h")]
+HEADERS = ["csrc/kes_internal.h", "csrc/kes_ctx.h", os.path.join("..", "include", "kes.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -199,6 +199,25 @@ __global__ void k_scale(const double* __restrict__ src, double s, double* __rest
     dst[i] = src[i] * s;
 }
 
+// Kernels whose dynamic shared memory grows with the basis size k (k x 8 doubles of Ritz
+// coefficients, next to their static shared memory) may need more than the default 48 KB
+// per block: raise the kernel's limit
+// to what the launch asks for (up to the device's opt-in maximum, 227 KB on GB300, which
+// bounds k at kMaxProjected). Returns false if the launch cannot get that much; the launch
+// then fails and the caller's launch check reports it.
+bool allow_dynamic_smem(const void* fn, size_t bytes) {
+  cudaFuncAttributes attr{};
+  if (cudaFuncGetAttributes(&attr, fn) != cudaSuccess) return false;
+  if (bytes + attr.sharedSizeBytes <= 48 * 1024) return true;  // within the default limit
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return false;
+  if (bytes + attr.sharedSizeBytes > static_cast<size_t>(optin)) return false;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)) ==
+         cudaSuccess;
+}
+
 int rows_grid(int64_t n, int cap) {
   const int64_t b = (n + kThreads - 1) / kThreads;
   return static_cast<int>(b < cap ? (b > 0 ? b : 1) : cap);
@@ -218,27 +237,125 @@ __device__ __forceinline__ int job_of(const J* __restrict__ jobs, int njobs, int
   return lo;
 }
 
-__global__ void __launch_bounds__(kThreads) k_mdot_jobs(const DotJob* __restrict__ jobs, int njobs,
-                                                        double* __restrict__ partial) {
-  const DotJob jb = jobs[job_of(jobs, njobs, blockIdx.x)];
-  const int64_t local = blockIdx.x - jb.first;
-  const int blk = static_cast<int>(local % jb.nblk);
-  const int j0 = static_cast<int>(local / jb.nblk) * kGroup;
-  double acc[kGroup];
+// Batched M-inner products h_j = sum_i B[j*ldb + i] w_i v_i (Algorithm 2.5, the M-inner
+// product of the orthogonalisation). A block owns kBlockRows consecutive rows of its job
+// and each of its 8 warps kWarpRows of them (16 slabs of 32 rows). The warps sweep their
+// rows once per pass of up to 8 columns: the products w_i v_i are formed once, in the
+// first pass, and kept in shared memory, each lane reading back only what it wrote (no
+// barrier inside a pass); a pass issues exactly its columns' FMAs, one per basis element
+// read, two slabs of loads in flight per warp. A pass ends with one fold per warp (the 8
+// partial sums halved across the lanes), a barrier, and a fixed-order sum over the 8
+// warps; the block's sums go to partial[poff + j * nblk + blk]. The work of a job depends
+// only on that job (its rows, k and nblk), so batched and separate launches give the
+// same bits.
+constexpr int kMaxCpw = 8;                       // columns per pass
+constexpr int kWarpRows = 512;                   // rows per warp
+constexpr int kBlockRows = kWarpRows * (kThreads / 32);
+
+// Folds the 8 partial sums of every lane into warp totals: after the three halving steps
+// (offsets 16, 8, 4) lane l holds a partial of column 4 bit4(l) + 2 bit3(l) + bit2(l),
+// and two butterfly steps over lane bits 0-1 complete it. Fixed order: deterministic.
+__device__ __forceinline__ double warp_fold8(double (&a)[kMaxCpw], int lane) {
+  const unsigned full = 0xffffffffu;
+  {
+    const bool up = lane & 16;
 #pragma unroll
-  for (int g = 0; g < kGroup; ++g) acc[g] = 0.0;
-  const int ng = min(kGroup, jb.k - j0);
-  for (int64_t i = blk * static_cast<int64_t>(kThreads) + threadIdx.x; i < jb.n;
-       i += static_cast<int64_t>(jb.nblk) * kThreads) {
-    const double wv = jb.w ? jb.w[i] * jb.v[i] : jb.v[i];
-#pragma unroll
-    for (int g = 0; g < kGroup; ++g)
-      if (g < ng) acc[g] = fma(jb.B[(j0 + g) * jb.ldb + i], wv, acc[g]);
+    for (int q = 0; q < 4; ++q) {
+      const double send = up ? a[q] : a[q + 4];
+      const double keep = up ? a[q + 4] : a[q];
+      a[q] = keep + __shfl_xor_sync(full, send, 16);
+    }
   }
-  double tot[kGroup];
-  block_sum<kGroup>(acc, tot);
-  if (threadIdx.x == 0)
-    for (int g = 0; g < ng; ++g) partial[jb.poff + static_cast<int64_t>(j0 + g) * jb.nblk + blk] = tot[g];
+  {
+    const bool up = lane & 8;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const double send = up ? a[q] : a[q + 2];
+      const double keep = up ? a[q + 2] : a[q];
+      a[q] = keep + __shfl_xor_sync(full, send, 8);
+    }
+  }
+  {
+    const bool up = lane & 4;
+    const double send = up ? a[0] : a[1];
+    const double keep = up ? a[1] : a[0];
+    a[0] = keep + __shfl_xor_sync(full, send, 4);
+  }
+  double t = a[0];
+  t += __shfl_xor_sync(full, t, 2);
+  t += __shfl_xor_sync(full, t, 1);
+  return t;
+}
+__device__ __forceinline__ int fold8_column(int lane) {
+  return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+}
+
+// One pass of a warp over its rows for NC columns starting at Bc (column stride ldb).
+// FIRST: form x_i = w_i v_i and keep it in xs (this lane's 16 slots); later passes read it.
+template <int NC, bool FIRST>
+__device__ __forceinline__ void mdot_pass(const DotJob& jb, const double* __restrict__ Bc, int64_t row0, int lane,
+                                          double* xs, double (&acc)[kMaxCpw]) {
+#pragma unroll 2
+  for (int sl = 0; sl < kWarpRows / 32; ++sl) {
+    const int64_t row = row0 + sl * 32 + lane;
+    if (row < jb.n) {
+      double x;
+      if constexpr (FIRST) {
+        x = jb.w ? jb.w[row] * jb.v[row] : jb.v[row];
+        xs[sl * 32 + lane] = x;
+      } else {
+        x = xs[sl * 32 + lane];
+      }
+#pragma unroll
+      for (int g = 0; g < NC; ++g) acc[g] = fma(__ldcs(Bc + g * jb.ldb + row), x, acc[g]);
+    }
+  }
+}
+
+template <bool FIRST>
+__device__ __forceinline__ void mdot_pass_nc(int nc, const DotJob& jb, const double* __restrict__ Bc, int64_t row0,
+                                             int lane, double* xs, double (&acc)[kMaxCpw]) {
+  switch (nc) {
+    case 8: mdot_pass<8, FIRST>(jb, Bc, row0, lane, xs, acc); break;
+    case 7: mdot_pass<7, FIRST>(jb, Bc, row0, lane, xs, acc); break;
+    case 6: mdot_pass<6, FIRST>(jb, Bc, row0, lane, xs, acc); break;
+    case 5: mdot_pass<5, FIRST>(jb, Bc, row0, lane, xs, acc); break;
+    case 4: mdot_pass<4, FIRST>(jb, Bc, row0, lane, xs, acc); break;
+    case 3: mdot_pass<3, FIRST>(jb, Bc, row0, lane, xs, acc); break;
+    case 2: mdot_pass<2, FIRST>(jb, Bc, row0, lane, xs, acc); break;
+    default: mdot_pass<1, FIRST>(jb, Bc, row0, lane, xs, acc); break;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 4) k_mdot_jobs(const DotJob* __restrict__ jobs, int njobs,
+                                                           double* __restrict__ partial) {
+  __shared__ double s_x[kThreads / 32][kWarpRows];          // w_i v_i of each warp's rows
+  __shared__ double s_red[kThreads / 32][kMaxCpw];
+  const DotJob jb = jobs[job_of(jobs, njobs, blockIdx.x)];
+  const int blk = static_cast<int>(blockIdx.x - jb.first);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t row0 = static_cast<int64_t>(blk) * kBlockRows + warp * kWarpRows;
+  double* xs = s_x[warp];
+  for (int c0 = 0; c0 < jb.k; c0 += kMaxCpw) {
+    const int nc = min(kMaxCpw, jb.k - c0);
+    const double* Bc = jb.B + static_cast<int64_t>(c0) * jb.ldb;
+    double acc[kMaxCpw];
+#pragma unroll
+    for (int g = 0; g < kMaxCpw; ++g) acc[g] = 0.0;
+    if (c0 == 0) mdot_pass_nc<true>(nc, jb, Bc, row0, lane, xs, acc);
+    else mdot_pass_nc<false>(nc, jb, Bc, row0, lane, xs, acc);
+    const double t = warp_fold8(acc, lane);
+    const int g = fold8_column(lane);
+    if ((lane & 3) == 0 && g < nc) s_red[warp][g] = t;
+    __syncthreads();
+    if (threadIdx.x < nc) {
+      double sum = s_red[0][threadIdx.x];
+#pragma unroll
+      for (int wi = 1; wi < kThreads / 32; ++wi) sum += s_red[wi][threadIdx.x];
+      partial[jb.poff + static_cast<int64_t>(c0 + threadIdx.x) * jb.nblk + blk] = sum;
+    }
+    __syncthreads();  // s_red is rewritten by the next pass
+  }
 }
 
 __global__ void __launch_bounds__(kThreads) k_reduce_jobs(const DotJob* __restrict__ jobs,
@@ -304,10 +421,11 @@ __global__ void k_scale_jobs(const ScaleJob* __restrict__ jobs) {
 
 }  // namespace
 
-// Row blocks of the batched inner products: about 64 rows per thread, so that a block's
-// final reduction (8 sums over 256 threads) stays small next to its FMAs; at most
-// kDotBlocks per column group.
-int dot_blocks(int64_t n) { return rows_grid((n + 63) / 64, kDotBlocks); }
+// Row blocks of a batched inner-product job: kBlockRows rows each.
+int dot_blocks(int64_t n) {
+  const int64_t b = (n + kBlockRows - 1) / kBlockRows;
+  return static_cast<int>(b < 1 ? 1 : b);
+}
 int gemv_blocks(int64_t n) { return rows_grid(n, 2048); }
 
 void launch_mdot_jobs(cudaStream_t st, const DotJob* jobs, int njobs, int max_k, int64_t total_blocks,
@@ -367,7 +485,9 @@ void launch_ritz_residual(cudaStream_t st, const double* B, const double* SB, in
   if (p <= 0) return;
   const int nblk = rows_grid(n, kDotBlocks);
   dim3 grid(nblk, (p + kGroup - 1) / kGroup);
-  k_ritz_residual<<<grid, kThreads, k * kGroup * sizeof(double), st>>>(B, SB, ldb, k, Y, theta, p, m, n,
+  const size_t smem = static_cast<size_t>(k) * kGroup * sizeof(double);
+  allow_dynamic_smem(reinterpret_cast<const void*>(&k_ritz_residual), smem);  // else the launch fails, reported
+  k_ritz_residual<<<grid, kThreads, smem, st>>>(B, SB, ldb, k, Y, theta, p, m, n,
                                                                        partial);
   k_reduce_partial<<<2 * p, kThreads, 0, st>>>(partial, nblk, out);
   g_launches += 2;
@@ -377,7 +497,9 @@ void launch_gemm_bx(cudaStream_t st, const double* B, int64_t ldb, int k, const 
                     int64_t ldx, int64_t n) {
   if (p <= 0) return;
   dim3 grid(rows_grid(n, 2048), (p + kGroup - 1) / kGroup);
-  k_gemm_bx<<<grid, kThreads, k * kGroup * sizeof(double), st>>>(B, ldb, k, Y, p, X, ldx, n);
+  const size_t smem = static_cast<size_t>(k) * kGroup * sizeof(double);
+  allow_dynamic_smem(reinterpret_cast<const void*>(&k_gemm_bx), smem);
+  k_gemm_bx<<<grid, kThreads, smem, st>>>(B, ldb, k, Y, p, X, ldx, n);
   ++g_launches;
 }
 

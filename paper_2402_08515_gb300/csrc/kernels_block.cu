@@ -140,13 +140,53 @@ __device__ __forceinline__ void row_sums(T (&un)[NH], const T* __restrict__ vp, 
   }
 }
 
+// The same sums with the matrix stream software-pipelined: the columns and values of the
+// next PB entries are loaded while the PB rows of the current ones are gathered, so each
+// slice meets the HBM latency of its index stream about once instead of once per pair
+// of entries. The chain is still one FMA per entry in entry order (bitwise the sums of
+// row_sums). Entries past w (the last batch of a row) are neither loaded nor summed.
+template <typename T, int NB, int NH, int PB, typename I>
+__device__ __forceinline__ void row_sums_pipe(T (&un)[NH], const T* __restrict__ vp, const I* __restrict__ cp,
+                                              int base, int w, const T* __restrict__ g, int co) {
+  // entries past w read column `base` (a valid row) with value 0 and are not summed
+  int32_t cn[PB];
+  T vn[PB];
+#pragma unroll
+  for (int j = 0; j < PB; ++j) {
+    const bool ok = j < w;
+    cn[j] = base + (ok ? ld_idx(cp + j * kSliceC) : 0);
+    vn[j] = ok ? ld_cs(vp + j * kSliceC) : T(0);
+  }
+  for (int k = 0; k < w; k += PB) {
+    T xx[PB][NH];
+#pragma unroll
+    for (int j = 0; j < PB; ++j) load_row<NH>(g + static_cast<int64_t>(cn[j]) * NB + co, xx[j]);
+    T vv[PB];
+#pragma unroll
+    for (int j = 0; j < PB; ++j) vv[j] = vn[j];
+#pragma unroll
+    for (int j = 0; j < PB; ++j) {
+      const bool ok = k + PB + j < w;
+      cn[j] = base + (ok ? ld_idx(cp + (k + PB + j) * kSliceC) : 0);
+      vn[j] = ok ? ld_cs(vp + (k + PB + j) * kSliceC) : T(0);
+    }
+#pragma unroll
+    for (int j = 0; j < PB; ++j)
+      if (k + j < w) {
+#pragma unroll
+        for (int q = 0; q < NH; ++q) un[q] = fma(vv[j], xx[j][q], un[q]);
+      }
+  }
+}
+
 // g: the rows the sums gather from (x itself for the leapfrog, the fourth-order stage
 // otherwise); x seeds each row with 2 u_n - u_{n-1}.
 // LPR lanes share a row: LPR = 1 gives a lane a whole row of NB columns and a warp a
 // 32-row slice; LPR = 2 gives a lane NB / 2 columns and a warp half a slice (16 rows),
 // which halves the registers a thread needs for its columns. Either way every column is
-// the same FMA chain in entry order, so the shapes round identically.
-template <typename T, int NB, bool FIRST, bool LAST, int MINB, bool PF, int LPR>
+// the same FMA chain in entry order, so the shapes round identically. PB > 0 pipelines the
+// matrix stream PB entries ahead (row_sums_pipe); PB = 0 loads entries in pairs.
+template <typename T, int NB, bool FIRST, bool LAST, int MINB, bool PF, int LPR, int PB>
 __global__ void __launch_bounds__(256, MINB)
     k_step_blk(SellDev A, const T* __restrict__ x, const T* __restrict__ g, const T* prev, T* out, T* acc_s,
                T* acc_c, double* acc64, int64_t acc_stride, int F, const T* __restrict__ ahi,
@@ -216,8 +256,13 @@ __global__ void __launch_bounds__(256, MINB)
       if constexpr (kF32) un[j] = __fsub_rn(__fmul_rn(2.0f, xi[j]), pi[j]);
       else un[j] = A.fold2 ? -pi[j] : 2.0 * xi[j] - pi[j];  // A.fold2: 2 x_j is in the diagonal
     }
-    if (A.dcol) row_sums<T, NB, NH>(un, vp, A.dcol + beg + rs, static_cast<int>(row), w, g, co);
-    else row_sums<T, NB, NH>(un, vp, A.col + beg + rs, 0, w, g, co);
+    if constexpr (PB > 0) {
+      if (A.dcol) row_sums_pipe<T, NB, NH, PB>(un, vp, A.dcol + beg + rs, static_cast<int>(row), w, g, co);
+      else row_sums_pipe<T, NB, NH, PB>(un, vp, A.col + beg + rs, 0, w, g, co);
+    } else {
+      if (A.dcol) row_sums<T, NB, NH>(un, vp, A.dcol + beg + rs, static_cast<int>(row), w, g, co);
+      else row_sums<T, NB, NH>(un, vp, A.col + beg + rs, 0, w, g, co);
+    }
     if (!LAST) store_row<NH>(out + ro, un);
     bool bad = false;
     for (int f = 0; f < nacc; ++f) {
@@ -289,20 +334,24 @@ __global__ void __launch_bounds__(256, MINB)
 }
 
 // Launch shapes of the block kernels: minimum resident 256-thread blocks per SM, whether
-// the slices are prefetched into L2, lanes per row.
-#define KES_BLK_VARIANTS(X)                                                                                   \
-  X(0, 1, false, 1) X(1, 2, false, 1) X(2, 3, false, 1) X(3, 4, false, 1) X(4, 1, true, 1) X(5, 2, true, 1) \
-  X(6, 3, true, 1) X(7, 4, true, 1) X(8, 4, false, 2) X(9, 5, false, 2) X(10, 6, false, 2)
+// the slices are prefetched into L2, lanes per row, entries of the pipelined matrix stream
+// (0: pairs, not pipelined).
+#define KES_BLK_VARIANTS(X)                                                                         \
+  X(0, 1, false, 1, 0) X(1, 2, false, 1, 0) X(2, 3, false, 1, 0) X(3, 4, false, 1, 0)              \
+  X(4, 1, true, 1, 0) X(5, 2, true, 1, 0) X(6, 3, true, 1, 0) X(7, 4, true, 1, 0)                   \
+  X(8, 4, false, 2, 0) X(9, 5, false, 2, 0) X(10, 6, false, 2, 0) X(11, 4, false, 1, 2)             \
+  X(12, 3, false, 1, 4) X(13, 4, false, 1, 4) X(14, 2, false, 1, 8) X(15, 6, false, 2, 4)           \
+  X(16, 4, false, 2, 8)
 
-template <typename T, int NB, int MINB, bool PF, int LPR>
+template <typename T, int NB, int MINB, bool PF, int LPR, int PB>
 void blk_impl(int grid, int block, cudaStream_t st, bool first, bool last, const SellDev& A, const T* x,
               const T* g, const T* prev, T* out, T* acc_s, T* acc_c, double* acc64, int64_t acc_stride, int F, const T* ahi,
               const T* alo, int Lp1, int step, int cpt, int* flag) {
 #define KES_BLK_ARGS A, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, F, ahi, alo, Lp1, step, cpt, flag
-  if (first && last) k_step_blk<T, NB, true, true, MINB, PF, LPR><<<grid, block, 0, st>>>(KES_BLK_ARGS);
-  else if (first) k_step_blk<T, NB, true, false, MINB, PF, LPR><<<grid, block, 0, st>>>(KES_BLK_ARGS);
-  else if (last) k_step_blk<T, NB, false, true, MINB, PF, LPR><<<grid, block, 0, st>>>(KES_BLK_ARGS);
-  else k_step_blk<T, NB, false, false, MINB, PF, LPR><<<grid, block, 0, st>>>(KES_BLK_ARGS);
+  if (first && last) k_step_blk<T, NB, true, true, MINB, PF, LPR, PB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
+  else if (first) k_step_blk<T, NB, true, false, MINB, PF, LPR, PB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
+  else if (last) k_step_blk<T, NB, false, true, MINB, PF, LPR, PB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
+  else k_step_blk<T, NB, false, false, MINB, PF, LPR, PB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
 #undef KES_BLK_ARGS
 }
 
@@ -312,20 +361,20 @@ void blk_dispatch(const LaunchCfg& cfg, int NB, cudaStream_t st, bool first, boo
                   const T* ahi, const T* alo, int Lp1, int step, int cpt, int* flag) {
   // a block of 256 threads is 8 warps; a warp takes a slice (or half a slice, LPR = 2)
   int lpr = 1;
-#define X(ID, M, P, R) \
+#define X(ID, M, P, R, B) \
   if (cfg.variant_blk == ID) lpr = R;
   KES_BLK_VARIANTS(X)
 #undef X
   const int64_t need = (A.n_slices * lpr + 7) / 8;
   const int grid = static_cast<int>(need < cfg.grid_blk ? need : cfg.grid_blk);
-#define KES_CALL(NBV, M, P, R)                                                                             \
-  blk_impl<T, NBV, M, P, R>(grid, 256, st, first, last, A, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, F,  \
-                         ahi, alo, Lp1, step, cpt, flag)
-#define X(ID, M, P, R)                         \
-  case ID:                                     \
-    if (NB == 2) KES_CALL(2, M, P, R);         \
-    else if (NB == 4) KES_CALL(4, M, P, R);    \
-    else KES_CALL(8, M, P, R);                 \
+#define KES_CALL(NBV, M, P, R, B)                                                                             \
+  blk_impl<T, NBV, M, P, R, B>(grid, 256, st, first, last, A, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, F, \
+                               ahi, alo, Lp1, step, cpt, flag)
+#define X(ID, M, P, R, B)                         \
+  case ID:                                        \
+    if (NB == 2) KES_CALL(2, M, P, R, B);         \
+    else if (NB == 4) KES_CALL(4, M, P, R, B);    \
+    else KES_CALL(8, M, P, R, B);                 \
     break;
   switch (cfg.variant_blk) {
     KES_BLK_VARIANTS(X)
@@ -380,10 +429,10 @@ void stage4_dispatch(const SellDev& A, int n_sm, cudaStream_t st, int NB, const 
   else k_stage4<T, 8><<<grid, 256, 0, st>>>(A, x, v);
 }
 
-template <typename T, int NB, int M, bool P, int R>
+template <typename T, int NB, int M, bool P, int R, int B>
 int occ_one(int block) {
   int nb = 0;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_blk<T, NB, false, false, M, P, R>, block, 0) ==
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_blk<T, NB, false, false, M, P, R, B>, block, 0) ==
                  cudaSuccess
              ? nb
              : 0;
@@ -444,7 +493,7 @@ int elem_grid(int64_t count) {
 
 int blk_variant_count() {
   int n = 0;
-#define X(ID, M, P, R) ++n;
+#define X(ID, M, P, R, B) ++n;
   KES_BLK_VARIANTS(X)
 #undef X
   return n;
@@ -452,12 +501,12 @@ int blk_variant_count() {
 
 int blk_blocks_per_sm(bool fp32, int NB, int variant, int block) {
   int nb = 0;
-#define X(ID, M, P, R)                                                                                        \
-  case ID:                                                                                                    \
-    if (fp32) nb = NB == 2 ? occ_one<float, 2, M, P, R>(block) : NB == 4 ? occ_one<float, 4, M, P, R>(block)   \
-                                                                         : occ_one<float, 8, M, P, R>(block);  \
-    else nb = NB == 2 ? occ_one<double, 2, M, P, R>(block) : NB == 4 ? occ_one<double, 4, M, P, R>(block)      \
-                                                                     : occ_one<double, 8, M, P, R>(block);     \
+#define X(ID, M, P, R, B)                                                                                \
+  case ID:                                                                                                 \
+    if (fp32) nb = NB == 2 ? occ_one<float, 2, M, P, R, B>(block) : NB == 4 ? occ_one<float, 4, M, P, R, B>(block) \
+                                                                          : occ_one<float, 8, M, P, R, B>(block);  \
+    else nb = NB == 2 ? occ_one<double, 2, M, P, R, B>(block) : NB == 4 ? occ_one<double, 4, M, P, R, B>(block)    \
+                                                                      : occ_one<double, 8, M, P, R, B>(block);     \
     break;
   switch (variant) {
     KES_BLK_VARIANTS(X)

@@ -21,233 +21,11 @@
 #include <utility>
 #include <vector>
 
-#include "kes_internal.h"
+#include "kes_ctx.h"
 
 using namespace kes;
 
 namespace {
-
-struct KesError {
-  kes_status status;
-};
-
-#define KES_CUDA(call)                                                \
-  do {                                                                \
-    cudaError_t e_ = (call);                                          \
-    if (e_ != cudaSuccess) {                                          \
-      throw KesError{e_ == cudaErrorMemoryAllocation ? KES_ERR_OOM    \
-                                                     : KES_ERR_CUDA}; \
-    }                                                                 \
-  } while (0)
-
-#define KES_CHECK_LAUNCH() KES_CUDA(cudaGetLastError())
-
-template <typename F>
-kes_status guarded(F&& f) {
-  try {
-    return f();
-  } catch (const KesError& e) {
-    return e.status;
-  } catch (const std::bad_alloc&) {
-    return KES_ERR_OOM;
-  } catch (...) {
-    return KES_ERR_CUDA;
-  }
-}
-
-struct MeshInfo {
-  int64_t n = 0;          // dofs of this mesh
-  int64_t n_pad = 0;      // its padded rows (multiple of 32)
-  int64_t row_off = 0;    // first padded row in the context
-  int64_t src_off = 0;    // first row in the caller's concatenated vectors
-  int64_t slice_off = 0;  // first SELL slice
-  int64_t n_slices = 0;
-  int64_t nnz = 0;
-  double gershgorin = 0;  // sqrt(max_i sum_j |s_ij| / m_i) >= omega_max
-  double omega_est = 0;   // last power-iteration estimate (0: none)
-  double tau = 0;
-  std::vector<double> wmin, wmax;
-};
-
-// Adds the kernels launched while it lives (this thread) to the context's counter.
-struct LaunchCount {
-  kes_stats* stats;
-  int64_t start;
-  explicit LaunchCount(kes_stats* s) : stats(s), start(g_launches) {}
-  ~LaunchCount() { stats->kernel_launches += g_launches - start; }
-};
-
-struct GraphEntry {
-  int NB = 0;
-  bool fp64 = true;
-  int cpt = 0;
-  int steps = 0;
-  cudaGraphExec_t exec = nullptr;
-  int64_t nodes = 0;
-};
-
-int nb_for(int b) { return b <= 1 ? 1 : b <= 2 ? 2 : b <= 4 ? 4 : 8; }
-
-}  // namespace
-
-struct kes_ctx {
-  kes_opts opts{};
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  int device = 0;
-  std::vector<MeshInfo> meshes;
-  int64_t n = 0, n_pad = 0, nnz = 0, nnz_pad = 0;
-  std::vector<std::pair<void*, size_t>> allocs;
-  SellDev A;
-  LaunchCfg cfg;
-  int NBcap = 1;
-  int32_t* row_src = nullptr;     // padded row -> caller row (-1: padding); null: identity
-  int32_t* slice_mesh = nullptr;  // slice -> mesh (null: one mesh)
-  double* m64 = nullptr;          // lumped mass (n_pad, zero padded)
-  double* minv64 = nullptr;       // 1 / m
-  double* tau2m64 = nullptr;      // tau^2 / m with the tau of the row's mesh
-  double* step64 = nullptr;       // A = -tau^2 M^{-1} S, SELL layout (FP64 steps)
-  double* step64p = nullptr;      // the same in the pair layout (A.slice_ptr2); FP64 contexts with fold64
-  float* step32 = nullptr;        // the same in FP32 (FP32 steps)
-  float* step32p = nullptr;       // the FP32 ones in the pair layout (A.slice_ptr2), if built
-  int64_t nnz_pair = 0;           // entries of the pair layout (with its padding)
-  bool diag_in_rows = false;      // every row of the SELL layout stores its diagonal among its slice's
-                                  // width (a real entry or padding): the 2 u_n can fold into A
-  bool fold64 = false;            // the FP64 step values hold A + 2I (leapfrog and diag_in_rows)
-  SellDev step_A64() const {
-    SellDev a = A;
-    a.val64 = step64;
-    a.val64p = step64p;
-    a.fold2 = fold64 ? 1 : 0;
-    return a;
-  }
-  SellDev step_A32() const {
-    SellDev a = A;
-    a.val32 = step32;
-    a.val32p = step32p;
-    return a;
-  }
-  // filter
-  bool filter_set = false;
-  int F = 0, L = 0;
-  double* alpha64 = nullptr;  // [n_mesh][F][L+1]
-  float* alpha_hi = nullptr;
-  float* alpha_lo = nullptr;
-  size_t alpha_cap = 0;
-  // filter work (capacity NBcap columns)
-  double* stage_in = nullptr;   // n_pad x NB row-major: the start block of the trajectory
-  double* stage_out = nullptr;  // F x (n_pad x NB): filtered blocks (FP64)
-  int stage_out_F = 0;
-  double* U64[2] = {nullptr, nullptr};
-  float* U32[3] = {nullptr, nullptr, nullptr};
-  double* V64 = nullptr;  // fourth-order stage v = u + A u / 12 (n_pad x NBcap), allocated on first use
-  float* V32 = nullptr;
-  float* acc_s = nullptr;
-  float* acc_c = nullptr;
-  double* tmp_user = nullptr;  // n x NBcap, caller layout
-  int* d_flag = nullptr;
-  std::vector<GraphEntry> graphs;
-  int g_F = -1, g_L = -1;
-  // Krylov workspace
-  int kcap = 0, kF = 0;  // basis vectors per process, intervals (processes per mesh)
-  double* B = nullptr;   // n_pad x (kF * kcap), column-major: interval f owns columns f * kcap ..,
-                         // mesh j its rows row_off_j ..
-  double* SB = nullptr;
-  double* Hd = nullptr;  // (n_mesh * kF) x kcap x kcap; column k of process p holds b_i^T S b_k, i <= k
-  double* partial = nullptr;
-  double* scal = nullptr;  // per process: 2 * kcap + kScal device scalars
-  double* normd = nullptr; // per process: ||w||_M^2 before and after orthogonalisation
-  char* jobs = nullptr;    // job descriptors of the batched Gram-Schmidt stages
-  size_t jobs_bytes = 0;
-  double* Yd = nullptr;
-  double* thd = nullptr;
-  double* Xd = nullptr;
-  size_t Xd_cap = 0;
-  double* Wc = nullptr;       // n_pad x NBcap column-major (filtered block, unpacked)
-  int32_t* colsel = nullptr;  // n_mesh x 8
-  // stats
-  kes_stats stats{};
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_filter, ev_other;
-  std::vector<cudaEvent_t> ev_pool;
-
-  int n_mesh() const { return static_cast<int>(meshes.size()); }
-
-  void* dalloc(size_t bytes) {
-    if (bytes == 0) bytes = 16;
-    void* p = nullptr;
-    if (opts.dev_alloc) {
-      p = opts.dev_alloc(bytes, opts.alloc_user);
-      if (!p) throw KesError{KES_ERR_OOM};
-    } else {
-      cudaError_t e = cudaMalloc(&p, bytes);
-      if (e != cudaSuccess) {
-        cudaGetLastError();
-        throw KesError{KES_ERR_OOM};
-      }
-    }
-    allocs.emplace_back(p, bytes);
-    return p;
-  }
-  void dfree(void* p) {
-    if (!p) return;
-    for (size_t i = 0; i < allocs.size(); ++i)
-      if (allocs[i].first == p) {
-        if (opts.dev_free) opts.dev_free(p, allocs[i].second, opts.alloc_user);
-        else cudaFree(p);
-        allocs.erase(allocs.begin() + i);
-        return;
-      }
-  }
-  template <typename T>
-  T* dalloc_n(int64_t count) {
-    return static_cast<T*>(dalloc(static_cast<size_t>(count) * sizeof(T)));
-  }
-  template <typename T>
-  T* dzero_n(int64_t count) {
-    T* p = dalloc_n<T>(count);
-    KES_CUDA(cudaMemsetAsync(p, 0, static_cast<size_t>(count) * sizeof(T), stream));
-    return p;
-  }
-
-  cudaEvent_t get_event() {
-    if (!ev_pool.empty()) {
-      cudaEvent_t e = ev_pool.back();
-      ev_pool.pop_back();
-      return e;
-    }
-    cudaEvent_t e;
-    KES_CUDA(cudaEventCreate(&e));
-    return e;
-  }
-  // Completes pending event pairs (the stream must have been synchronised).
-  void harvest_events() {
-    for (auto* list : {&ev_filter, &ev_other}) {
-      for (auto& pr : *list) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) {
-          if (list == &ev_filter) stats.filter_ms += ms;
-          else stats.solve_other_ms += ms;
-        }
-        ev_pool.push_back(pr.first);
-        ev_pool.push_back(pr.second);
-      }
-      list->clear();
-    }
-  }
-  void sync() {
-    KES_CUDA(cudaStreamSynchronize(stream));
-    harvest_events();
-  }
-  void drop_graphs() {
-    for (auto& g : graphs)
-      if (g.exec) cudaGraphExecDestroy(g.exec);
-    graphs.clear();
-  }
-};
-
-namespace {
-
-constexpr int kScal = 16;  // device scalars per mesh ahead of the Gram-Schmidt coefficients
 
 void release(kes_ctx* c) {
   if (!c) return;
@@ -261,6 +39,10 @@ void release(kes_ctx* c) {
 }
 
 // --------------------------------------------------------------- transfers
+}  // namespace
+
+namespace kes {
+
 // Caller block (n x nb column-major, host or device) -> row-major n_pad x NB block.
 void block_in(kes_ctx* c, const double* src, int nb, int32_t mem, int NB, double* dst) {
   const size_t bytes = static_cast<size_t>(c->n) * nb * sizeof(double);
@@ -277,6 +59,10 @@ void block_out(kes_ctx* c, const double* src, int NB, int nb, double* dst, int32
   KES_CUDA(cudaMemcpyAsync(dst, c->tmp_user, static_cast<size_t>(c->n) * nb * sizeof(double),
                            mem == KES_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream));
 }
+
+}  // namespace kes
+
+namespace {
 
 // --------------------------------------------------------------- filter
 // Largest stable tau * omega of the context's stepper.
@@ -353,7 +139,11 @@ void ensure_fp64_state(kes_ctx* c) {
   }
 }
 
-void run_filter(kes_ctx* c, int NB, bool fp64, int cpt = 0, int steps = 0) {
+}  // namespace
+
+namespace kes {
+
+void run_filter(kes_ctx* c, int NB, bool fp64, int cpt, int steps) {
   if (cpt > 0 && NB < 2) throw KesError{KES_ERR_ARG};  // per-column tables live in the block kernels
   if (steps <= 0 || steps > c->L) steps = c->L;
   if (fp64) ensure_fp64_state(c);
@@ -403,6 +193,10 @@ void run_filter(kes_ctx* c, int NB, bool fp64, int cpt = 0, int steps = 0) {
   c->stats.filter_steps += steps;
 }
 
+}  // namespace kes
+
+namespace {
+
 void ensure_stage_out(kes_ctx* c, int F) {
   if (c->stage_out_F >= F) return;
   const int64_t cnt = static_cast<int64_t>(F) * c->n_pad * c->NBcap;
@@ -430,6 +224,10 @@ kes_status check_flag(kes_ctx* c) {
 }
 
 // --------------------------------------------------------------- Krylov workspace
+}  // namespace
+
+namespace kes {
+
 // A process is the Krylov iteration of one mesh on one interval (p = mesh * F + f).
 void ensure_krylov(kes_ctx* c, int kmax, int F) {
   if (c->kcap >= kmax && c->kF >= F) return;
@@ -443,8 +241,11 @@ void ensure_krylov(kes_ctx* c, int kmax, int F) {
   c->B = c->dzero_n<double>(static_cast<int64_t>(F) * kmax * c->n_pad);
   c->SB = c->dzero_n<double>(static_cast<int64_t>(F) * kmax * c->n_pad);
   c->Hd = c->dzero_n<double>(nproc * kmax * kmax);
-  // partial sums: every process's inner products of one batched stage at once
-  c->partial = c->dalloc_n<double>(nproc * kDotBlocks * (2 * kmax + 8));
+  // partial sums: every process's inner products of one batched stage at once (a process
+  // takes dot_blocks of its rows per column), and the single launches' kDotBlocks per column
+  int64_t dot_total = 0;
+  for (const MeshInfo& mi : c->meshes) dot_total += static_cast<int64_t>(F) * dot_blocks(mi.n_pad);
+  c->partial = c->dalloc_n<double>(std::max(nproc * kDotBlocks, dot_total) * (2 * kmax + 8));
   c->normd = c->dzero_n<double>(2 * nproc);
   // job descriptors of the batched Gram-Schmidt stages (see append_column)
   c->jobs_bytes = static_cast<size_t>(nproc) * (4 * sizeof(DotJob) + sizeof(GemvJob) + sizeof(ScaleJob)) +
@@ -455,19 +256,10 @@ void ensure_krylov(kes_ctx* c, int kmax, int F) {
   c->thd = c->dalloc_n<double>(nproc * kmax);
 }
 
-// Device scalars of process p (of mesh p outside the solver).
-double* proc_scal(kes_ctx* c, int p) { return c->scal + static_cast<int64_t>(p) * (2 * c->kcap + kScal); }
+}  // namespace kes
 
-// The slices of one mesh as a matrix of its own (columns stay global row indices).
-SellDev mesh_sell(const kes_ctx* c, const MeshInfo& m) {
-  SellDev a = c->A;
-  a.slice_ptr = c->A.slice_ptr + m.slice_off;
-  a.n_slices = m.n_slices;
-  a.n = m.n;
-  a.n_pad = m.n_pad;
-  a.slice_mesh = nullptr;
-  return a;
-}
+namespace {
+
 
 // Makes launch shape v of the single-vector step kernel current.
 void select_variant(kes_ctx* c, int v) {
@@ -938,615 +730,6 @@ kes_status omega_impl(kes_ctx* c, int32_t iters, const double* v0, double* omega
   });
 }
 
-// ------------------------------------------------------------------ block Krylov solver
-struct MeshSolve {
-  int k = 0;            // basis vectors
-  bool done = false;    // no further blocks for this process
-  bool breakdown = false;
-  int kproj = -1;       // basis size at the last projection
-  std::vector<double> last_theta, last_rel;
-  std::vector<double> acc_theta, acc_rel, acc_abs, acc_Y;
-};
-
-// Sets each job's first block of a batched launch (prefix sums in job order) and returns
-// the launch's total blocks.
-inline int64_t job_blocks(const DotJob& j) { return dot_job_blocks(j); }
-inline int64_t job_blocks(const GemvJob& j) { return gemv_job_blocks(j); }
-template <typename J>
-int64_t first_blocks(std::vector<J>& jobs) {
-  int64_t total = 0;
-  for (J& j : jobs) {
-    j.first = total;
-    total += job_blocks(j);
-  }
-  return total;
-}
-
-template <typename T>
-T* hdup(const std::vector<T>& v) {
-  T* d = static_cast<T*>(std::malloc(std::max<size_t>(1, v.size()) * sizeof(T)));
-  if (!d) throw std::bad_alloc();
-  if (!v.empty()) std::memcpy(d, v.data(), v.size() * sizeof(T));
-  return d;
-}
-
-
-// The block solver over every mesh and interval of the context. Process p = mesh * F + f
-// is the block Krylov iteration of mesh p / F on interval f from start columns
-// f * g .. f * g + g - 1 (g = b / F), with its own basis, Gram-Schmidt scalars and
-// projected matrix; the processes share only the b-column trajectory of each block step.
-// X0 (p0 caller vectors, n_total x p0 column-major) selects the fixed-dimension mode: no
-// Krylov phase; refine_sweeps sweeps of X <- C X, M-orthonormalisation and Rayleigh-Ritz
-// from X0, every Ritz vector fed back (the FEAST-like use of the filter in Sec. 4).
-kes_status block_solve_impl(kes_ctx* c, const double* R0, int b, int32_t mem, const kes_solve_opts& so,
-                            kes_result** out, const double* X0 = nullptr, int p0 = 0) {
-  const int nm = c->n_mesh();
-  const int F = c->F;
-  const int P = nm * F;
-  const int g = b / F;                // columns per process
-  const int cpt = F > 1 ? g : 0;      // column j of a block takes weight table j / g
-  const int kmax = so.kmax;
-  const int NB = nb_for(b);
-  std::vector<MeshSolve> ms(P);
-  std::vector<kes_result*> res(nm, nullptr);
-  for (int j = 0; j < nm; ++j) {
-    res[j] = static_cast<kes_result*>(std::calloc(1, sizeof(kes_result)));
-    if (!res[j]) {
-      for (auto* r : res) kes_result_free(r);
-      return KES_ERR_OOM;
-    }
-  }
-  const auto t_start = std::chrono::steady_clock::now();
-  LaunchCount lc(&c->stats);
-  kes_status st = guarded([&]() -> kes_status {
-    ensure_krylov(c, kmax, F);
-    const int64_t np = c->n_pad;
-    const int64_t kc = c->kcap;
-    cudaStream_t s = c->stream;
-    auto other_begin = [&]() {
-      cudaEvent_t e0 = c->get_event();
-      KES_CUDA(cudaEventRecord(e0, s));
-      return e0;
-    };
-    auto other_end = [&](cudaEvent_t e0) {
-      cudaEvent_t e1 = c->get_event();
-      KES_CUDA(cudaEventRecord(e1, s));
-      c->ev_other.emplace_back(e0, e1);
-    };
-    auto mesh_of = [&](int p) -> const MeshInfo& { return c->meshes[p / F]; };
-    // column 0 of process p's basis over all rows (SpMV input) and on its mesh's rows
-    auto Bfull = [&](int p) { return c->B + (p % F) * kc * np; };
-    auto Bp = [&](int p) { return Bfull(p) + mesh_of(p).row_off; };
-    auto SBp = [&](int p) { return c->SB + (p % F) * kc * np + mesh_of(p).row_off; };
-    auto Hcol = [&](int p, int k) { return c->Hd + (static_cast<int64_t>(p) * kc + k) * kc; };
-    // process that owns column jj of a block of mesh j (-1: a padding column)
-    auto owner = [&](int j, int jj) {
-      const int f = F > 1 ? jj / g : 0;
-      return f < F ? j * F + f : -1;
-    };
-
-    // Orthogonalise column jj of Wc against the basis of the process that owns it on
-    // each mesh (two classical passes in the M-inner product) and append the vectors
-    // that are not dependent (Algorithm 2.5).
-    std::vector<char> want(P, 1);  // processes taking part in the current block step
-    auto append_column = [&](int jj) {
-      std::vector<char> added(P, 0);
-      std::vector<int> act;  // processes that take column jj
-      for (int j = 0; j < nm; ++j) {
-        const int p = owner(j, jj);
-        if (p < 0 || !want[p] || ms[p].done || ms[p].k >= kmax) continue;
-        act.push_back(p);
-      }
-      if (act.empty()) return added;
-      const int na = static_cast<int>(act.size());
-      // phase 1, one launch per stage for all of them: ||w||_M^2, two passes of
-      // h = B^T M w and w -= B h, ||w||_M^2 again
-      std::vector<DotJob> nb_jobs(na), na_jobs(na), h_jobs;
-      std::vector<GemvJob> g_jobs;
-      int max_k = 0;
-      int64_t poff = 0, poff_h = 0;
-      for (int i = 0; i < na; ++i) {
-        const int p = act[i];
-        const MeshInfo& mi = mesh_of(p);
-        double* w = c->Wc + static_cast<int64_t>(jj) * np + mi.row_off;
-        const double* mj = c->m64 + mi.row_off;
-        const int nblk = dot_blocks(mi.n_pad), gblk = gemv_blocks(mi.n_pad);
-        nb_jobs[i] = DotJob{w, w, mj, c->normd + 2 * p, mi.n_pad, 0, poff, 0, 1, nblk};
-        na_jobs[i] = DotJob{w, w, mj, c->normd + 2 * p + 1, mi.n_pad, 0, poff, 0, 1, nblk};
-        poff += nblk;
-        const int k = ms[p].k;
-        if (k > 0) {
-          h_jobs.push_back(DotJob{Bp(p), w, mj, proc_scal(c, p) + kScal, mi.n_pad, np, poff_h, 0, k, nblk});
-          g_jobs.push_back(GemvJob{w, Bp(p), proc_scal(c, p) + kScal, mi.n_pad, np, 0, k, gblk});
-          poff_h += static_cast<int64_t>(k) * nblk;
-          max_k = std::max(max_k, k);
-        }
-      }
-      const int nh = static_cast<int>(h_jobs.size());
-      const int64_t nb_blocks = first_blocks(nb_jobs), na_blocks = first_blocks(na_jobs);
-      const int64_t h_blocks = first_blocks(h_jobs), g_blocks = first_blocks(g_jobs);
-      char* jb = c->jobs;
-      DotJob* d_nb = reinterpret_cast<DotJob*>(jb);
-      DotJob* d_na = d_nb + P;
-      DotJob* d_h = d_na + P;
-      GemvJob* d_g = reinterpret_cast<GemvJob*>(d_h + P);
-      cudaEvent_t ev = other_begin();
-      KES_CUDA(cudaMemcpyAsync(d_nb, nb_jobs.data(), na * sizeof(DotJob), cudaMemcpyHostToDevice, s));
-      KES_CUDA(cudaMemcpyAsync(d_na, na_jobs.data(), na * sizeof(DotJob), cudaMemcpyHostToDevice, s));
-      if (nh > 0) {
-        KES_CUDA(cudaMemcpyAsync(d_h, h_jobs.data(), nh * sizeof(DotJob), cudaMemcpyHostToDevice, s));
-        KES_CUDA(cudaMemcpyAsync(d_g, g_jobs.data(), nh * sizeof(GemvJob), cudaMemcpyHostToDevice, s));
-      }
-      launch_mdot_jobs(s, d_nb, na, 1, nb_blocks, c->partial);  // ||w||_M^2 before
-      for (int pass = 0; pass < 2 && nh > 0; ++pass) {
-        launch_mdot_jobs(s, d_h, nh, max_k, h_blocks, c->partial);  // h = B^T M w
-        launch_gemv_sub_jobs(s, d_g, nh, max_k, g_blocks);          // w -= B h
-      }
-      launch_mdot_jobs(s, d_na, na, 1, na_blocks, c->partial);  // ||w||_M^2 after
-      KES_CHECK_LAUNCH();
-      std::vector<double> nrm(2 * P, 0.0);
-      KES_CUDA(cudaMemcpyAsync(nrm.data(), c->normd, 2 * P * sizeof(double), cudaMemcpyDeviceToHost, s));
-      int flag = 0;
-      KES_CUDA(cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-      other_end(ev);
-      c->sync();
-      if (flag) {
-        KES_CUDA(cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
-        throw KesError{KES_ERR_UNSTABLE};
-      }
-      // phase 2 for the vectors that are not dependent: b_k = w / ||w||_M, S b_k (one
-      // launch per interval over all meshes), the new column b_i^T S b_k of H
-      std::vector<ScaleJob> s_jobs;
-      std::vector<DotJob> c_jobs;
-      std::vector<const double*> x_of(static_cast<size_t>(F) * nm, nullptr);
-      std::vector<double*> y_of(static_cast<size_t>(F) * nm, nullptr);
-      int max_k1 = 0, max_sblk = 1;
-      poff = 0;
-      for (int i = 0; i < na; ++i) {
-        const int p = act[i];
-        if (!(std::sqrt(nrm[2 * p + 1]) > 1e-10 * std::sqrt(nrm[2 * p]))) continue;  // dependent vector
-        const MeshInfo& mi = mesh_of(p);
-        const int k = ms[p].k;
-        double* w = c->Wc + static_cast<int64_t>(jj) * np + mi.row_off;
-        double* sbk = SBp(p) + k * np;
-        const int nblk = dot_blocks(mi.n_pad);
-        s_jobs.push_back(ScaleJob{w, c->normd + 2 * p + 1, Bp(p) + k * np, mi.n_pad});
-        max_sblk = std::max(max_sblk, gemv_blocks(mi.n_pad));
-        x_of[static_cast<size_t>(p % F) * nm + p / F] = Bfull(p) + k * np;
-        y_of[static_cast<size_t>(p % F) * nm + p / F] = c->SB + (p % F) * kc * np + k * np;
-        c_jobs.push_back(DotJob{Bp(p), sbk, nullptr, Hcol(p, k), mi.n_pad, np, poff, 0, k + 1, nblk});
-        poff += static_cast<int64_t>(k + 1) * nblk;
-        max_k1 = std::max(max_k1, k + 1);
-        ms[p].k = k + 1;
-        added[p] = 1;
-      }
-      const int ns = static_cast<int>(s_jobs.size());
-      const int64_t c_blocks = first_blocks(c_jobs);
-      if (ns > 0) {
-        ev = other_begin();
-        ScaleJob* d_s = reinterpret_cast<ScaleJob*>(d_g + P);
-        DotJob* d_c = reinterpret_cast<DotJob*>(d_s + P);
-        char* ptrs = reinterpret_cast<char*>(d_c + P);  // x_of, then y_of, F * nm pointers each
-        const double** d_x = reinterpret_cast<const double**>(ptrs);
-        double** d_y = reinterpret_cast<double**>(ptrs + static_cast<size_t>(F) * nm * sizeof(double*));
-        KES_CUDA(cudaMemcpyAsync(d_s, s_jobs.data(), ns * sizeof(ScaleJob), cudaMemcpyHostToDevice, s));
-        KES_CUDA(cudaMemcpyAsync(d_c, c_jobs.data(), ns * sizeof(DotJob), cudaMemcpyHostToDevice, s));
-        KES_CUDA(cudaMemcpyAsync(d_x, x_of.data(), x_of.size() * sizeof(double*), cudaMemcpyHostToDevice, s));
-        KES_CUDA(cudaMemcpyAsync(d_y, y_of.data(), y_of.size() * sizeof(double*), cudaMemcpyHostToDevice, s));
-        launch_scale_jobs(s, d_s, ns, max_sblk);
-        for (int f = 0; f < F; ++f) {
-          bool any = false;
-          for (int j = 0; j < nm; ++j) any |= x_of[static_cast<size_t>(f) * nm + j] != nullptr;
-          if (any) launch_spmv_f64_meshes(c->A, c->cfg, s, d_x + static_cast<size_t>(f) * nm,
-                                          d_y + static_cast<size_t>(f) * nm);
-        }
-        launch_mdot_jobs(s, d_c, ns, max_k1, c_blocks, c->partial);
-        KES_CHECK_LAUNCH();
-        other_end(ev);
-      }
-      return added;
-    };
-
-    // The projected matrix of process p mirrored into a full kk x kk array and its
-    // eigenpairs (theta ascending, clamped at 0).
-    auto projected_eig = [&](int p, std::vector<double>& theta, std::vector<double>& Y) {
-      const int kk = ms[p].k;
-      std::vector<double> Hh(static_cast<size_t>(kk) * kk, 0.0);
-      KES_CUDA(cudaMemcpy2DAsync(Hh.data(), kk * sizeof(double), Hcol(p, 0), kc * sizeof(double),
-                                 kk * sizeof(double), kk, cudaMemcpyDeviceToHost, s));
-      c->sync();
-      // column i holds rows 0..i (upper triangle); mirror it into the lower triangle
-      for (int i = 0; i < kk; ++i)
-        for (int r = i + 1; r < kk; ++r) Hh[static_cast<size_t>(i) * kk + r] = Hh[static_cast<size_t>(r) * kk + i];
-      theta.assign(kk, 0.0);
-      Y.assign(static_cast<size_t>(kk) * kk, 0.0);
-      if (!sym_eig(kk, Hh.data(), theta.data(), Y.data())) throw KesError{KES_ERR_CUDA};
-      for (double& t : theta) t = std::max(t, 0.0);
-    };
-
-    // Rayleigh-Ritz (eq. projevp) and the residual acceptance (eq. res) of several
-    // processes at once: their projected matrices come back with one synchronisation,
-    // the small eigenproblems are solved on host threads, and the residual kernels run
-    // back to back before one more synchronisation.
-    auto project_many = [&](const std::vector<int>& ps) {
-      const int np_ = static_cast<int>(ps.size());
-      if (np_ == 0) return;
-      std::vector<std::vector<double>> Hs(np_), th(np_), Ys(np_);
-      for (int i = 0; i < np_; ++i) {
-        const int kk = ms[ps[i]].k;
-        Hs[i].assign(static_cast<size_t>(kk) * kk, 0.0);
-        if (kk > 0)
-          KES_CUDA(cudaMemcpy2DAsync(Hs[i].data(), kk * sizeof(double), Hcol(ps[i], 0), kc * sizeof(double),
-                                     kk * sizeof(double), kk, cudaMemcpyDeviceToHost, s));
-      }
-      c->sync();
-      std::atomic<int> next{0};
-      std::atomic<bool> failed{false};
-      auto worker = [&]() {
-        for (int i = next++; i < np_; i = next++) {
-          const int kk = ms[ps[i]].k;
-          std::vector<double>& H = Hs[i];
-          // column i holds rows 0..i (upper triangle); mirror it into the lower triangle
-          for (int a = 0; a < kk; ++a)
-            for (int r = a + 1; r < kk; ++r) H[static_cast<size_t>(a) * kk + r] = H[static_cast<size_t>(r) * kk + a];
-          th[i].assign(kk, 0.0);
-          Ys[i].assign(static_cast<size_t>(kk) * kk, 0.0);
-          if (!sym_eig(kk, H.data(), th[i].data(), Ys[i].data())) failed = true;
-          for (double& t : th[i]) t = std::max(t, 0.0);
-        }
-      };
-      const int hw = static_cast<int>(std::thread::hardware_concurrency());
-      const int nt = std::min(np_, std::max(1, std::min(hw, 16)));
-      std::vector<std::thread> pool;
-      for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
-      worker();
-      for (auto& t : pool) t.join();
-      if (failed) throw KesError{KES_ERR_CUDA};
-      std::vector<std::vector<int>> inside(np_);
-      std::vector<std::vector<double>> Ysel(np_), thsel(np_), rr(np_);
-      cudaEvent_t ev = other_begin();
-      int64_t yo = 0, to = 0;
-      for (int i = 0; i < np_; ++i) {
-        const int p = ps[i];
-        MeshSolve& m = ms[p];
-        const MeshInfo& mi = mesh_of(p);
-        const int kk = m.k;
-        m.kproj = kk;
-        const double wmin = mi.wmin[p % F], wmax = mi.wmax[p % F];
-        for (int q = 0; q < kk; ++q) {
-          const double om = std::sqrt(th[i][q]);
-          if (om >= wmin && om <= wmax) inside[i].push_back(q);
-        }
-        const int np_in = static_cast<int>(inside[i].size());
-        m.last_theta = th[i];
-        m.last_rel.assign(kk, std::numeric_limits<double>::quiet_NaN());
-        m.acc_theta.clear();
-        m.acc_rel.clear();
-        m.acc_abs.clear();
-        m.acc_Y.clear();
-        if (np_in == 0) continue;
-        Ysel[i].resize(static_cast<size_t>(kk) * np_in);
-        thsel[i].resize(np_in);
-        for (int q = 0; q < np_in; ++q) {
-          thsel[i][q] = th[i][inside[i][q]];
-          std::memcpy(&Ysel[i][static_cast<size_t>(q) * kk], &Ys[i][static_cast<size_t>(inside[i][q]) * kk],
-                      kk * sizeof(double));
-        }
-        KES_CUDA(cudaMemcpyAsync(c->Yd + yo, Ysel[i].data(), Ysel[i].size() * sizeof(double), cudaMemcpyHostToDevice,
-                                 s));
-        KES_CUDA(cudaMemcpyAsync(c->thd + to, thsel[i].data(), np_in * sizeof(double), cudaMemcpyHostToDevice, s));
-        double* sc = proc_scal(c, p);
-        launch_ritz_residual(s, Bp(p), SBp(p), np, kk, c->Yd + yo, c->thd + to, np_in, c->m64 + mi.row_off,
-                             mi.n_pad, c->partial, sc + kScal);
-        KES_CHECK_LAUNCH();
-        rr[i].resize(2 * np_in);
-        KES_CUDA(cudaMemcpyAsync(rr[i].data(), sc + kScal, 2 * np_in * sizeof(double), cudaMemcpyDeviceToHost, s));
-        yo += static_cast<int64_t>(kk) * np_in;
-        to += np_in;
-      }
-      other_end(ev);
-      c->sync();
-      for (int i = 0; i < np_; ++i) {
-        MeshSolve& m = ms[ps[i]];
-        const int kk = m.k;
-        const int np_in = static_cast<int>(inside[i].size());
-        for (int q = 0; q < np_in; ++q) {
-          const double a = std::sqrt(std::max(rr[i][q], 0.0));
-          const double den = thsel[i][q] * std::sqrt(std::max(rr[i][np_in + q], 0.0));
-          const double rel = den > 0.0 ? a / den : std::numeric_limits<double>::infinity();
-          m.last_rel[inside[i][q]] = rel;
-          if (rel <= so.tol) {
-            m.acc_theta.push_back(thsel[i][q]);
-            m.acc_rel.push_back(rel);
-            m.acc_abs.push_back(a);
-            m.acc_Y.insert(m.acc_Y.end(), Ysel[i].begin() + static_cast<size_t>(q) * kk,
-                           Ysel[i].begin() + static_cast<size_t>(q + 1) * kk);
-          }
-        }
-      }
-    };
-
-    // a mesh that asked for n_wanted pairs stops once its intervals hold that many
-    auto check_wanted = [&]() {
-      if (so.n_wanted <= 0) return;
-      for (int j = 0; j < nm; ++j) {
-        int got = 0;
-        for (int f = 0; f < F; ++f) got += static_cast<int>(ms[j * F + f].acc_theta.size());
-        if (got >= so.n_wanted)
-          for (int f = 0; f < F; ++f) ms[j * F + f].done = true;
-      }
-    };
-
-    int64_t steps = 0;
-    // start block: the g start vectors of each process, M-orthonormalised in order
-    if (!X0) {
-      cudaEvent_t ev = other_begin();
-      block_in(c, R0, b, mem, NB, c->stage_in);
-      launch_unpack_block(s, c->stage_in, NB, c->Wc, np);
-      KES_CHECK_LAUNCH();
-      other_end(ev);
-      for (int jj = 0; jj < b; ++jj) append_column(jj);
-      for (int p = 0; p < P; ++p)
-        if (ms[p].k == 0) ms[p].done = ms[p].breakdown = true;
-    }
-    std::vector<int> next_check(P, so.check_every);
-    std::vector<int32_t> colsel(static_cast<size_t>(nm) * NB, -1);
-    for (; !X0;) {
-      bool any = false;
-      std::fill(colsel.begin(), colsel.end(), -1);
-      for (int p = 0; p < P; ++p) {
-        MeshSolve& m = ms[p];
-        if (m.done || m.k >= kmax) continue;
-        any = true;
-        // filter the g newest basis vectors of each process (Algorithm 2.5 filters the newest one)
-        const int j = p / F, f = p % F;
-        for (int i = 0; i < g; ++i) {
-          const int col = m.k - g + i;
-          colsel[j * NB + f * g + i] = col >= 0 ? static_cast<int32_t>(f * kc + col) : -1;
-        }
-      }
-      if (!any) break;
-      KES_CUDA(cudaMemcpyAsync(c->colsel, colsel.data(), colsel.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-      launch_pack_basis(s, c->B, np, c->colsel, c->slice_mesh, c->stage_in, NB, np);
-      KES_CHECK_LAUNCH();
-      run_filter(c, NB, c->opts.precision == KES_PREC_FP64, cpt);  // stage_in -> stage_out
-      steps += c->L;
-      launch_unpack_block(s, c->stage_out, NB, c->Wc, np);
-      KES_CHECK_LAUNCH();
-      std::vector<int> added(P, 0);
-      for (int jj = 0; jj < b; ++jj) {
-        std::vector<char> a = append_column(jj);
-        for (int p = 0; p < P; ++p) added[p] += a[p];
-      }
-      std::vector<int> due;
-      for (int p = 0; p < P; ++p) {
-        MeshSolve& m = ms[p];
-        if (m.done) continue;
-        if (added[p] == 0 && m.k < kmax) {  // the whole block was dependent: invariant subspace
-          m.done = m.breakdown = true;
-          continue;
-        }
-        if (m.k >= next_check[p] && m.k < kmax) {
-          while (next_check[p] <= m.k) next_check[p] += so.check_every;
-          due.push_back(p);
-        }
-      }
-      project_many(due);
-      check_wanted();
-    }
-    if (!X0) {
-      std::vector<int> due;
-      for (int p = 0; p < P; ++p)
-        if (ms[p].kproj != ms[p].k) due.push_back(p);
-      project_many(due);
-    }
-
-    // FP64 refinement: sweeps of filtered subspace iteration on the in-interval Ritz
-    // vectors of each process (Sec. 4 mentions fixed-dimension, FEAST-like use of the
-    // filter): X <- C X with the FP64 step kernels, M-orthonormalise, Rayleigh-Ritz,
-    // residuals. With F intervals the columns of a refinement block are grouped per
-    // interval like those of the Krylov blocks.
-    // In the fixed-dimension mode the sweeps filter in the context's precision and keep
-    // every Ritz vector; the refinement filters in FP64 and keeps the in-interval ones.
-    int64_t refine_steps = 0;
-    const int NBr = F > 1 ? NB : c->NBcap;  // columns of one refinement filter call
-    const int gr = F > 1 ? g : NBr;         // of them per interval
-    const bool sweep_fp64 = X0 ? c->opts.precision == KES_PREC_FP64 : true;
-    auto keep = [&](const MeshSolve& m, int q) { return X0 != nullptr || !std::isnan(m.last_rel[q]); };
-    for (int sweep = 0; sweep < so.refine_sweeps; ++sweep) {
-      const bool from_x0 = X0 && sweep == 0;
-      std::vector<int> pcount(P, 0);
-      std::vector<int64_t> xoff(F + 1, 0);  // interval f uses columns xoff[f] .. of Xd (meshes share them)
-      int rounds = 0;
-      for (int p = 0; p < P; ++p) {
-        if (from_x0) pcount[p] = p0;
-        else
-          for (size_t q = 0; q < ms[p].last_rel.size(); ++q) pcount[p] += keep(ms[p], static_cast<int>(q)) ? 1 : 0;
-        rounds = std::max(rounds, (pcount[p] + gr - 1) / gr);
-      }
-      for (int f = 0; f < F; ++f) {
-        int mx = 0;
-        for (int j = 0; j < nm; ++j) mx = std::max(mx, pcount[j * F + f]);
-        xoff[f + 1] = xoff[f] + mx;
-      }
-      if (xoff[F] == 0) break;
-      const size_t need = static_cast<size_t>(xoff[F]) * np;
-      if (need > c->Xd_cap) {
-        c->dfree(c->Xd);
-        c->Xd = c->dalloc_n<double>(need);
-        c->Xd_cap = need;
-      }
-      KES_CUDA(cudaMemsetAsync(c->Xd, 0, need * sizeof(double), s));
-      if (from_x0) {  // the caller's vectors, one column at a time into the padded row order
-        for (int q = 0; q < p0; ++q) {
-          const double* src = X0 + static_cast<int64_t>(q) * c->n;
-          if (mem == KES_MEM_HOST) {
-            KES_CUDA(cudaMemcpyAsync(c->tmp_user, src, static_cast<size_t>(c->n) * sizeof(double),
-                                     cudaMemcpyHostToDevice, s));
-            src = c->tmp_user;
-          }
-          launch_gather_rows(s, src, c->n, 1, c->row_src, c->n, c->Xd + static_cast<int64_t>(q) * np, 1, np);
-        }
-        KES_CHECK_LAUNCH();
-      }
-      // Ritz vectors (all of them, or those of in-interval Ritz values): X = B y_q
-      for (int p = 0; p < P && !from_x0; ++p) {
-        if (pcount[p] == 0) continue;
-        MeshSolve& m = ms[p];
-        const MeshInfo& mi = mesh_of(p);
-        const int kk = m.k;
-        std::vector<double> theta, Y, Ysel;
-        projected_eig(p, theta, Y);
-        for (int q = 0; q < kk; ++q)
-          if (keep(m, q))
-            Ysel.insert(Ysel.end(), Y.begin() + static_cast<size_t>(q) * kk, Y.begin() + static_cast<size_t>(q + 1) * kk);
-        KES_CUDA(cudaMemcpyAsync(c->Yd, Ysel.data(), Ysel.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-        launch_gemm_bx(s, Bp(p), np, kk, c->Yd, pcount[p], c->Xd + xoff[p % F] * np + mi.row_off, np, mi.n_pad);
-        KES_CHECK_LAUNCH();
-        c->sync();  // Yd is reused by the next process
-      }
-      // filter them with the FP64 kernels, a block of NBr columns at a time, into fresh bases
-      for (int p = 0; p < P; ++p) {
-        want[p] = pcount[p] > 0;
-        if (want[p]) {
-          ms[p].k = 0;
-          ms[p].done = false;
-        }
-      }
-      std::vector<int32_t> csel(static_cast<size_t>(nm) * NBr, -1);
-      for (int r = 0; r < rounds; ++r) {
-        std::fill(csel.begin(), csel.end(), -1);
-        for (int p = 0; p < P; ++p) {
-          const int j = p / F, f = p % F;
-          for (int i = 0; i < gr; ++i) {
-            const int q = r * gr + i;
-            if (q < pcount[p]) csel[j * NBr + f * gr + i] = static_cast<int32_t>(xoff[f] + q);
-          }
-        }
-        KES_CUDA(cudaMemcpyAsync(c->colsel, csel.data(), csel.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-        launch_pack_basis(s, c->Xd, np, c->colsel, c->slice_mesh, c->stage_in, NBr, np);
-        KES_CHECK_LAUNCH();
-        const int Lr = so.refine_L > 0 && so.refine_L < c->L ? so.refine_L : c->L;
-        run_filter(c, NBr, sweep_fp64, cpt, Lr);
-        refine_steps += Lr;
-        launch_unpack_block(s, c->stage_out, NBr, c->Wc, np);
-        KES_CHECK_LAUNCH();
-        for (int jj = 0; jj < NBr; ++jj) {
-          bool any = false;
-          for (int j = 0; j < nm; ++j) {
-            const int p = owner(j, jj);
-            if (p < 0) continue;
-            want[p] = csel[j * NBr + jj] >= 0;
-            any |= want[p] != 0;
-          }
-          if (any) append_column(jj);
-        }
-      }
-      std::vector<int> due;
-      for (int p = 0; p < P; ++p) {
-        if (pcount[p] > 0) due.push_back(p);
-        want[p] = 1;
-      }
-      project_many(due);
-    }
-
-    // results: the pairs of a mesh's processes merged in ascending theta
-    bool any_breakdown = false;
-    for (int j = 0; j < nm; ++j) {
-      const MeshInfo& mi = c->meshes[j];
-      kes_result* r = res[j];
-      struct Pair {
-        double theta;
-        int f, q;
-      };
-      std::vector<Pair> pairs;
-      std::vector<double> ritz_th, ritz_rel;
-      int k_used = 0;
-      bool brk = false;
-      for (int f = 0; f < F; ++f) {
-        const MeshSolve& m = ms[j * F + f];
-        for (size_t q = 0; q < m.acc_theta.size(); ++q) pairs.push_back({m.acc_theta[q], f, static_cast<int>(q)});
-        ritz_th.insert(ritz_th.end(), m.last_theta.begin(), m.last_theta.end());
-        ritz_rel.insert(ritz_rel.end(), m.last_rel.begin(), m.last_rel.end());
-        k_used += m.k;
-        brk |= m.breakdown;
-      }
-      std::stable_sort(pairs.begin(), pairs.end(), [](const Pair& x, const Pair& y) { return x.theta < y.theta; });
-      const int np_acc = static_cast<int>(pairs.size());
-      std::vector<double> th(np_acc), om(np_acc), rel(np_acc), ab(np_acc);
-      std::vector<int32_t> iv(np_acc);
-      for (int t = 0; t < np_acc; ++t) {
-        const MeshSolve& m = ms[j * F + pairs[t].f];
-        th[t] = pairs[t].theta;
-        om[t] = std::sqrt(th[t]);
-        rel[t] = m.acc_rel[pairs[t].q];
-        ab[t] = m.acc_abs[pairs[t].q];
-        iv[t] = pairs[t].f;
-      }
-      any_breakdown |= brk;
-      r->n = mi.n;
-      r->n_pairs = np_acc;
-      r->k_used = k_used;
-      r->breakdown = brk ? 1 : 0;
-      r->n_ritz = static_cast<int32_t>(ritz_th.size());
-      r->time_steps = steps;
-      r->refine_steps = refine_steps;
-      r->omega2 = hdup(th);
-      r->omega = hdup(om);
-      r->rel_res = hdup(rel);
-      r->abs_res = hdup(ab);
-      r->interval = hdup(iv);
-      r->ritz_omega2 = hdup(ritz_th);
-      r->ritz_rel_res = hdup(ritz_rel);
-      if (so.want_vectors && np_acc > 0) {
-        const size_t need = static_cast<size_t>(np_acc) * np;
-        if (need > c->Xd_cap) {
-          c->dfree(c->Xd);
-          c->Xd = c->dalloc_n<double>(need);
-          c->Xd_cap = need;
-        }
-        KES_CUDA(cudaMemsetAsync(c->Xd, 0, need * sizeof(double), s));
-        // interval f's accepted vectors go to columns xo[f] .. of Xd
-        std::vector<int> xo(F + 1, 0);
-        for (int f = 0; f < F; ++f) {
-          const MeshSolve& m = ms[j * F + f];
-          const int cnt = static_cast<int>(m.acc_theta.size());
-          xo[f + 1] = xo[f] + cnt;
-          if (cnt == 0) continue;
-          KES_CUDA(cudaMemcpyAsync(c->Yd, m.acc_Y.data(), m.acc_Y.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-          launch_gemm_bx(s, Bp(j * F + f), np, m.k, c->Yd, cnt, c->Xd + static_cast<int64_t>(xo[f]) * np + mi.row_off,
-                         np, mi.n_pad);
-          KES_CHECK_LAUNCH();
-          c->sync();  // Yd is reused by the next interval
-        }
-        r->vectors = static_cast<double*>(std::malloc(static_cast<size_t>(np_acc) * mi.n * sizeof(double)));
-        if (!r->vectors) throw std::bad_alloc();
-        // scatter each Ritz vector to the caller's order and keep this mesh's rows
-        for (int t = 0; t < np_acc; ++t) {
-          const int64_t col = xo[pairs[t].f] + pairs[t].q;
-          launch_scatter_rows(s, c->Xd + col * np, 1, 1, c->row_src, c->n, c->tmp_user, c->n, np);
-          KES_CHECK_LAUNCH();
-          KES_CUDA(cudaMemcpyAsync(r->vectors + static_cast<size_t>(t) * mi.n, c->tmp_user + mi.src_off,
-                                   mi.n * sizeof(double), cudaMemcpyDeviceToHost, s));
-        }
-        c->sync();
-      }
-    }
-    c->sync();
-    return any_breakdown ? KES_INFO_INVARIANT_SUBSPACE : KES_OK;
-  });
-  const double ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
-  if (st != KES_OK && st != KES_INFO_INVARIANT_SUBSPACE) {
-    for (auto* r : res) kes_result_free(r);
-    return st;
-  }
-  for (int j = 0; j < nm; ++j) {
-    res[j]->solve_ms = ms_total;
-    out[j] = res[j];
-  }
-  return st;
-}
-
 }  // namespace
 
 // =========================================================================
@@ -1772,8 +955,10 @@ kes_status kes_krylov_solve(kes_ctx* c, const double* r0, int32_t mem, const kes
   kes_solve_opts so;
   if (so_in) so = *so_in;
   else kes_solve_opts_default(&so);
-  if (so.kmax < 1 || so.check_every < 1 || !(so.tol > 0.0) || so.refine_sweeps < 0 || so.refine_L < 0)
+  if (so.kmax < 1 || so.check_every < 1 || !(so.tol > 0.0) || so.refine_sweeps < 0 || so.refine_L < 0 ||
+      so.refine_extra < 0)
     return KES_ERR_ARG;
+  if (so.kmax > kMaxProjected) return KES_ERR_UNSUPPORTED;
   return block_solve_impl(c, r0, 1, mem, so, out);
 }
 
@@ -1787,8 +972,10 @@ kes_status kes_block_krylov_solve(kes_ctx* c, const double* R0, int32_t b, int32
   kes_solve_opts so;
   if (so_in) so = *so_in;
   else kes_solve_opts_default(&so);
-  if (so.kmax < b / c->F || so.check_every < 1 || !(so.tol > 0.0) || so.refine_sweeps < 0 || so.refine_L < 0)
+  if (so.kmax < b / c->F || so.check_every < 1 || !(so.tol > 0.0) || so.refine_sweeps < 0 || so.refine_L < 0 ||
+      so.refine_extra < 0)
     return KES_ERR_ARG;
+  if (so.kmax > kMaxProjected) return KES_ERR_UNSUPPORTED;
   return block_solve_impl(c, R0, b, mem, so, out);
 }
 
@@ -1801,7 +988,9 @@ kes_status kes_subspace_solve(kes_ctx* c, const double* X0, int32_t p, int32_t m
   kes_solve_opts so;
   if (so_in) so = *so_in;
   else kes_solve_opts_default(&so);
-  if (so.kmax < p || so.refine_sweeps < 1 || !(so.tol > 0.0) || so.refine_L < 0) return KES_ERR_ARG;
+  if (so.kmax < p || so.refine_sweeps < 1 || !(so.tol > 0.0) || so.refine_L < 0 || so.refine_extra < 0)
+    return KES_ERR_ARG;
+  if (so.kmax > kMaxProjected) return KES_ERR_UNSUPPORTED;
   return block_solve_impl(c, nullptr, 1, mem, so, out, X0, p);
 }
 

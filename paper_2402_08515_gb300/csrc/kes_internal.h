@@ -183,7 +183,7 @@ struct GemvJob {       // v -= B h (k columns)
   int nblk;
 };
 // Blocks a job takes in a batched launch (the launch's grid is the sum over its jobs).
-inline int64_t dot_job_blocks(const DotJob& j) { return static_cast<int64_t>(j.nblk) * ((j.k + 7) / 8); }
+inline int64_t dot_job_blocks(const DotJob& j) { return j.nblk; }
 inline int64_t gemv_job_blocks(const GemvJob& j) { return j.nblk; }
 struct ScaleJob {      // dst = v / sqrt(nrm2[0])
   const double* v;
@@ -207,6 +207,9 @@ void launch_spmv_f64_meshes(const SellDev& A, const LaunchCfg& cfg, cudaStream_t
 // h_j = sum_i B[j*ldb + i] * w[i] * v[i] for j < k (w may be null); deterministic two-pass
 // reduction through `partial` (size >= k * kDotBlocks); result written to h (device).
 constexpr int kDotBlocks = 608;
+// Largest basis (Krylov dimension per process) the projection kernels take: their shared
+// memory holds k x 8 doubles, within the 227 KB a GB300 block may opt in to.
+constexpr int kMaxProjected = 3584;
 void launch_mdot(cudaStream_t st, const double* B, int64_t ldb, int k, const double* v, const double* w,
                  int64_t n, double* partial, double* h);
 // v[i] -= sum_j B[j*ldb + i] * h[j], j < k

@@ -7,14 +7,18 @@
 // fail nor fragment memory. kes_create allocates its own state, so those
 // callers get this entry point instead: they pass every input and the output
 // in device memory they already own, and the two leapfrog state vectors live
-// in the fixed array below, which is part of the library image.
+// in the fixed array below, a file-scope __device__ array of this module.
 //
-// The scratch array takes 2 * KES_NOALLOC_MAX_N doubles (16 MiB) on every GPU
-// that loads this module and keeps it until the process exits. Every call
-// shares it and it keeps the previous call's contents; calls whose GPU work
-// overlaps (two streams, two host threads) race on it and must be serialised
-// by the caller. Nothing has to start at zero: each call writes every state
-// entry it reads.
+// The array takes 2 * KES_NOALLOC_MAX_N doubles (16 MiB) on every device where
+// this module is loaded, until the process exits. Under CUDA's default lazy
+// module loading the module (and so the array) is loaded on a device by the
+// first call there, when the set-up looks up the array's address: a caller that
+// reserves all of its device memory must make one call first (or run with
+// CUDA_MODULE_LOADING=EAGER, which loads every module with the context).
+// Every call shares the array and it keeps the previous call's contents; calls
+// whose GPU work overlaps (two streams, two host threads) race on it and must
+// be serialised by the caller. Nothing has to start at zero: each call writes
+// every state entry it reads.
 #include <cuda_runtime.h>
 
 #include <mutex>

@@ -12,7 +12,7 @@ import oracle as O
 import paper_2402_08515_gb300 as K
 from fe_inputs import box_grid, flared_tube, square_grid, start_vectors
 from oracle import spectra
-from tests.tolerances import EIG_REL, elementwise_bound, filter_error, filter_tol
+from tests.tolerances import EIG_REL, elementwise_bound, filter_error, filter_tol, fp32_residual_floor
 
 pytestmark = pytest.mark.gpu
 
@@ -139,7 +139,9 @@ def test_krylov_solve_square64_matches_closed_form_and_oracle(problems, precisio
     S = p.to_scipy()
     tau = _tau_for(p)
     wmin, wmax, L, kmax = 20.0, 30.0, 300, 80
-    tol = 1e-8 if precision == "fp64" else 1e-5
+    # the FP32 form is accepted at 4x its residual floor (tests/tolerances.py, about 5e-6
+    # here), where the count of accepted pairs no longer hinges on pairs at the floor
+    tol = 1e-8 if precision == "fp64" else max(1e-5, 4 * fp32_residual_floor(S, p.m, wmin))
     r0 = start_vectors(p.n, 1, 0)[0]
     with _ctx(p, precision=precision) as c:
         K.kes_set_filter(c.handle, wmin, wmax, tau, L)

@@ -84,3 +84,17 @@ def elementwise_bound(tol: float, r: np.ndarray, m: np.ndarray, alpha: np.ndarra
     """Entry-wise bound implied by the M-norm bound: |e_i| <= ||e||_M / sqrt(min m)."""
     rm = np.sqrt(np.sum(np.atleast_2d(r) ** 2 * m, axis=-1)).max()
     return tol * np.abs(alpha).sum() * rm / np.sqrt(m.min())
+
+
+def fp32_residual_floor(S, m: np.ndarray, omega_min: float) -> float:
+    """Relative residual that Ritz pairs of the FP32 form cannot be expected to beat.
+
+    The FP32 form stores the step values A = -tau^2 M^-1 S rounded once to FP32, a relative
+    error of at most 2^-24 per entry, so its Krylov space belongs to the perturbed operator
+    K~ = K + dK with |dK| <= 2^-24 |K| entrywise (K = M^-1 S). An eigenvector x of K~ has
+    ||(K - theta) x||_inf <= 2^-24 G ||x||_inf, G = max_i sum_j |s_ij| / m_i (the Gershgorin
+    bound of |K|); relative to theta >= omega_min^2 that is at most 2^-24 G / omega_min^2.
+    Pairs near this level pass or fail an acceptance test by chance, so a count of accepted
+    pairs is only compared well above it."""
+    G = float(np.max(np.asarray(abs(S).sum(axis=1)).ravel() / m))
+    return EPS32 * G / (omega_min * omega_min)
