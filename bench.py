@@ -71,6 +71,9 @@ def parse_args(argv=None):
     ap.add_argument("--tol", type=float, default=0.0, help="override the acceptance tolerance (--mode certify)")
     ap.add_argument("--refine-sweeps", type=int, default=0, help="FP64 refinement sweeps (--mode certify)")
     ap.add_argument("--refine-extra", type=int, default=0, help="buffer Ritz vectors of the refinement (--mode certify)")
+    ap.add_argument("--precision", default="", choices=["", "fp64", "fp32"],
+                    help="override the workload's precision (--mode certify)")
+    ap.add_argument("--b", type=int, default=0, help="override the workload's block width (--mode certify)")
     ap.add_argument("--blk-variant", type=int, default=None,
                     help="fixed block step-kernel launch shape instead of the autotuner's choice")
     ap.add_argument("--variant", type=int, default=None,
@@ -849,10 +852,11 @@ def run_certify(args):
 
     wl = WORKLOADS[args.workload]
     problems, batch = workload_problems(wl)
-    b = wl.b
+    b = args.b or wl.b
+    precision = args.precision or wl.precision
     L = args.L or wl.L
     t_build = time.perf_counter()
-    with K.Context(problems if batch else problems[0], precision=wl.precision, block_b=b) as c:
+    with K.Context(problems if batch else problems[0], precision=precision, block_b=b) as c:
         v0 = start_block(problems, 1, wl.seed)[0]
         omega_pow, _ = K.kes_estimate_omega_max_batch(c.handle, wl.power_iters, v0)
         taus = wl.cfl * 2.0 / omega_pow
@@ -865,7 +869,7 @@ def run_certify(args):
                                 taus, L)
         so = K.kes_solve_opts_default()
         so.kmax = args.kmax or wl.kmax
-        so.tol = args.tol or wl.acceptance()
+        so.tol = args.tol or (1e-8 if precision == "fp64" else wl.acceptance())
         so.check_every = so.kmax
         so.refine_sweeps = args.refine_sweeps
         so.refine_extra = args.refine_extra
@@ -901,7 +905,7 @@ def run_certify(args):
                            "ritz_rel_res_median_in_interval": float(np.median(inside)) if inside.size else None,
                            "k_used": r["k_used"], "leapfrog_steps": r["time_steps"],
                            "fp64_refine_steps": r["refine_steps"]})
-    print(json.dumps({"mode": "certify", "workload": args.workload, "precision": wl.precision, "b": b, "L": L,
+    print(json.dumps({"mode": "certify", "workload": args.workload, "precision": precision, "b": b, "L": L,
                       "kmax": so.kmax, "tol": so.tol, "refine_sweeps": so.refine_sweeps, "setup_s": setup_s,
                       "solve_s": solve_s, "clocks": clk.summary(), "meshes": meshes}), flush=True)
 

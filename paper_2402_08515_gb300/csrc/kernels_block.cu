@@ -24,11 +24,18 @@ __device__ __forceinline__ T ld_cs(const T* p) { return __ldcs(p); }
 // registers, so a kernel computes the same with or without it.
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
-// NB contiguous values at p (16-byte aligned for NB * sizeof(T) >= 16) through the read-only path.
+// NB contiguous values at p (16-byte aligned for NB * sizeof(T) >= 16; 32-byte aligned for
+// 8 floats) through the read-only path. A row of 8 floats is one 32-byte sector, fetched by
+// one 256-bit load (sm_100 and later) instead of two 128-bit ones: the gathers of the SpMM
+// step issue half the L1 requests.
 template <int NB>
 __device__ __forceinline__ void load_row(const float* __restrict__ p, float (&v)[NB]) {
   if constexpr (NB == 1) {
     v[0] = __ldg(p);
+  } else if constexpr (NB == 8) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+        : "l"(p));
   } else if constexpr (NB >= 4) {
 #pragma unroll
     for (int q = 0; q < NB / 4; ++q) {
@@ -52,13 +59,18 @@ __device__ __forceinline__ void load_row(const double* __restrict__ p, double (&
     v[2 * q] = t.x; v[2 * q + 1] = t.y;
   }
 }
-// Coherent loads and stores of one row's NB contiguous values with 8- or 16-byte
-// vector accesses (rows are NB * sizeof(T) aligned): a lane moves its whole row in
+// Coherent loads and stores of one row's NB contiguous values with 8-, 16- or (8 floats)
+// 32-byte vector accesses (rows are NB * sizeof(T) aligned): a lane moves its whole row in
 // 1-4 instructions instead of NB scalar ones that each touch a separate sector.
 template <int NB>
 __device__ __forceinline__ void load_plain(const float* p, float (&v)[NB]) {
   if constexpr (NB == 1) {
     v[0] = *p;
+  } else if constexpr (NB == 8) {
+    asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+                 : "l"(p)
+                 : "memory");
   } else if constexpr (NB >= 4) {
 #pragma unroll
     for (int q = 0; q < NB / 4; ++q) {
@@ -86,6 +98,10 @@ template <int NB>
 __device__ __forceinline__ void store_row(float* p, const float (&v)[NB]) {
   if constexpr (NB == 1) {
     *p = v[0];
+  } else if constexpr (NB == 8) {
+    asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(v[0]), "f"(v[1]),
+                 "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+                 : "memory");
   } else if constexpr (NB >= 4) {
 #pragma unroll
     for (int q = 0; q < NB / 4; ++q)
@@ -110,6 +126,15 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
   const float ap = __fsub_rn(s, bp);
   t = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
 }
+
+// 16-byte asynchronous copy global -> shared (no registers held while in flight); the
+// copying thread reads the data back itself after cp_async_wait_all.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 __device__ __forceinline__ int32_t ld_idx(const int32_t* p) { return __ldcs(p); }
 __device__ __forceinline__ int32_t ld_idx(const int16_t* p) { return __ldcs(reinterpret_cast<const short*>(p)); }
@@ -185,8 +210,12 @@ __device__ __forceinline__ void row_sums_pipe(T (&un)[NH], const T* __restrict__
 // 32-row slice; LPR = 2 gives a lane NB / 2 columns and a warp half a slice (16 rows),
 // which halves the registers a thread needs for its columns. Either way every column is
 // the same FMA chain in entry order, so the shapes round identically. PB > 0 pipelines the
-// matrix stream PB entries ahead (row_sums_pipe); PB = 0 loads entries in pairs.
-template <typename T, int NB, bool FIRST, bool LAST, int MINB, bool PF, int LPR, int PB>
+// matrix stream PB entries ahead (row_sums_pipe); PB = 0 loads entries in pairs. AS (FP32,
+// at most kAsAcc accumulator pairs, 16-byte rows) copies the slice's accumulator rows into
+// shared memory asynchronously when the slice starts, so their latency overlaps the row
+// sums instead of following them; every thread reads back only its own copies.
+constexpr int kAsAcc = 2;
+template <typename T, int NB, bool FIRST, bool LAST, int MINB, bool PF, int LPR, int PB, bool AS>
 __global__ void __launch_bounds__(256, MINB)
     k_step_blk(SellDev A, const T* __restrict__ x, const T* __restrict__ g, const T* prev, T* out, T* acc_s,
                T* acc_c, double* acc64, int64_t acc_stride, int F, const T* __restrict__ ahi,
@@ -197,6 +226,9 @@ __global__ void __launch_bounds__(256, MINB)
   constexpr int NH = NB / LPR;            // columns of this lane
   constexpr int kRows = kSliceC / LPR;    // rows of a warp's unit
   static_assert(LPR == 1 || !PF, "the L2 prefetch shapes take whole slices");
+  constexpr bool kAS = AS && kF32 && (NH * 4) % 16 == 0;
+  constexpr int kChunks = kAS ? NH * 4 / 16 : 1;           // 16-byte pieces of one row of NH floats
+  __shared__ float4 s_acc[kAS ? kAsAcc * 2 * kChunks : 1][kAS ? 256 : 1];  // [piece][thread]
   const T* val;
   if constexpr (kF32) val = A.val32;
   else val = A.val64;
@@ -241,6 +273,21 @@ __global__ void __launch_bounds__(256, MINB)
     const T* vp = val + beg + rs;
     const int64_t row = s * kSliceC + rs;
     const int64_t ro = row * NB + co;  // this lane's values in a row-major block
+    const bool staged = kAS && (cpt ? 1 : F) <= kAsAcc;
+    if constexpr (kAS) {
+      if (staged) {
+        for (int f = 0; f < (cpt ? 1 : F); ++f) {
+          const float* gs = reinterpret_cast<const float*>(acc_s) + f * acc_stride + ro;
+          const float* gc = reinterpret_cast<const float*>(acc_c) + f * acc_stride + ro;
+#pragma unroll
+          for (int q = 0; q < kChunks; ++q) {
+            cp_async16(&s_acc[(2 * f) * kChunks + q][threadIdx.x], gs + 4 * q);
+            cp_async16(&s_acc[(2 * f + 1) * kChunks + q][threadIdx.x], gc + 4 * q);
+          }
+        }
+        cp_async_commit();
+      }
+    }
     T xi[NH], pi[NH], un[NH];
     load_plain<NH>(x + ro, xi);
     if constexpr (FIRST) {
@@ -264,6 +311,9 @@ __global__ void __launch_bounds__(256, MINB)
       else row_sums<T, NB, NH>(un, vp, A.col + beg + rs, 0, w, g, co);
     }
     if (!LAST) store_row<NH>(out + ro, un);
+    if constexpr (kAS) {
+      if (staged) cp_async_wait_all();
+    }
     bool bad = false;
     for (int f = 0; f < nacc; ++f) {
       const int64_t at = f * acc_stride + ro;
@@ -292,8 +342,18 @@ __global__ void __launch_bounds__(256, MINB)
       }
       if constexpr (kF32) {
         float as[NH], ac[NH];
-        load_plain<NH>(acc_s + at, as);
-        load_plain<NH>(acc_c + at, ac);
+        if (staged) {
+#pragma unroll
+          for (int q = 0; q < kChunks; ++q) {
+            const float4 ts = s_acc[(2 * f) * kChunks + q][threadIdx.x];
+            const float4 tc = s_acc[(2 * f + 1) * kChunks + q][threadIdx.x];
+            as[4 * q] = ts.x; as[4 * q + 1] = ts.y; as[4 * q + 2] = ts.z; as[4 * q + 3] = ts.w;
+            ac[4 * q] = tc.x; ac[4 * q + 1] = tc.y; ac[4 * q + 2] = tc.z; ac[4 * q + 3] = tc.w;
+          }
+        } else {
+          load_plain<NH>(acc_s + at, as);
+          load_plain<NH>(acc_c + at, ac);
+        }
         double v64[NH];
 #pragma unroll
         for (int j = 0; j < NH; ++j) {
@@ -335,23 +395,25 @@ __global__ void __launch_bounds__(256, MINB)
 
 // Launch shapes of the block kernels: minimum resident 256-thread blocks per SM, whether
 // the slices are prefetched into L2, lanes per row, entries of the pipelined matrix stream
-// (0: pairs, not pipelined).
-#define KES_BLK_VARIANTS(X)                                                                         \
-  X(0, 1, false, 1, 0) X(1, 2, false, 1, 0) X(2, 3, false, 1, 0) X(3, 4, false, 1, 0)              \
-  X(4, 1, true, 1, 0) X(5, 2, true, 1, 0) X(6, 3, true, 1, 0) X(7, 4, true, 1, 0)                   \
-  X(8, 4, false, 2, 0) X(9, 5, false, 2, 0) X(10, 6, false, 2, 0) X(11, 4, false, 1, 2)             \
-  X(12, 3, false, 1, 4) X(13, 4, false, 1, 4) X(14, 2, false, 1, 8) X(15, 6, false, 2, 4)           \
-  X(16, 4, false, 2, 8)
+// (0: pairs, not pipelined), accumulator rows staged by asynchronous copies (FP32).
+#define KES_BLK_VARIANTS(X)                                                                                    \
+  X(0, 1, false, 1, 0, false) X(1, 2, false, 1, 0, false) X(2, 3, false, 1, 0, false)                          \
+  X(3, 4, false, 1, 0, false) X(4, 1, true, 1, 0, false) X(5, 2, true, 1, 0, false)                            \
+  X(6, 3, true, 1, 0, false) X(7, 4, true, 1, 0, false) X(8, 4, false, 2, 0, false)                            \
+  X(9, 5, false, 2, 0, false) X(10, 6, false, 2, 0, false) X(11, 4, false, 1, 2, false)                        \
+  X(12, 3, false, 1, 4, false) X(13, 4, false, 1, 4, false) X(14, 2, false, 1, 8, false)                       \
+  X(15, 6, false, 2, 4, false) X(16, 4, false, 2, 8, false) X(17, 4, false, 1, 4, true)                        \
+  X(18, 3, false, 1, 4, true) X(19, 4, false, 1, 2, true) X(20, 6, false, 2, 4, true)
 
-template <typename T, int NB, int MINB, bool PF, int LPR, int PB>
+template <typename T, int NB, int MINB, bool PF, int LPR, int PB, bool AS>
 void blk_impl(int grid, int block, cudaStream_t st, bool first, bool last, const SellDev& A, const T* x,
               const T* g, const T* prev, T* out, T* acc_s, T* acc_c, double* acc64, int64_t acc_stride, int F, const T* ahi,
               const T* alo, int Lp1, int step, int cpt, int* flag) {
 #define KES_BLK_ARGS A, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, F, ahi, alo, Lp1, step, cpt, flag
-  if (first && last) k_step_blk<T, NB, true, true, MINB, PF, LPR, PB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
-  else if (first) k_step_blk<T, NB, true, false, MINB, PF, LPR, PB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
-  else if (last) k_step_blk<T, NB, false, true, MINB, PF, LPR, PB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
-  else k_step_blk<T, NB, false, false, MINB, PF, LPR, PB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
+  if (first && last) k_step_blk<T, NB, true, true, MINB, PF, LPR, PB, AS><<<grid, block, 0, st>>>(KES_BLK_ARGS);
+  else if (first) k_step_blk<T, NB, true, false, MINB, PF, LPR, PB, AS><<<grid, block, 0, st>>>(KES_BLK_ARGS);
+  else if (last) k_step_blk<T, NB, false, true, MINB, PF, LPR, PB, AS><<<grid, block, 0, st>>>(KES_BLK_ARGS);
+  else k_step_blk<T, NB, false, false, MINB, PF, LPR, PB, AS><<<grid, block, 0, st>>>(KES_BLK_ARGS);
 #undef KES_BLK_ARGS
 }
 
@@ -361,20 +423,20 @@ void blk_dispatch(const LaunchCfg& cfg, int NB, cudaStream_t st, bool first, boo
                   const T* ahi, const T* alo, int Lp1, int step, int cpt, int* flag) {
   // a block of 256 threads is 8 warps; a warp takes a slice (or half a slice, LPR = 2)
   int lpr = 1;
-#define X(ID, M, P, R, B) \
+#define X(ID, M, P, R, B, S) \
   if (cfg.variant_blk == ID) lpr = R;
   KES_BLK_VARIANTS(X)
 #undef X
   const int64_t need = (A.n_slices * lpr + 7) / 8;
   const int grid = static_cast<int>(need < cfg.grid_blk ? need : cfg.grid_blk);
-#define KES_CALL(NBV, M, P, R, B)                                                                             \
-  blk_impl<T, NBV, M, P, R, B>(grid, 256, st, first, last, A, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, F, \
-                               ahi, alo, Lp1, step, cpt, flag)
-#define X(ID, M, P, R, B)                         \
-  case ID:                                        \
-    if (NB == 2) KES_CALL(2, M, P, R, B);         \
-    else if (NB == 4) KES_CALL(4, M, P, R, B);    \
-    else KES_CALL(8, M, P, R, B);                 \
+#define KES_CALL(NBV, M, P, R, B, S)                                                                          \
+  blk_impl<T, NBV, M, P, R, B, S>(grid, 256, st, first, last, A, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, \
+                                  F, ahi, alo, Lp1, step, cpt, flag)
+#define X(ID, M, P, R, B, S)                         \
+  case ID:                                           \
+    if (NB == 2) KES_CALL(2, M, P, R, B, S);         \
+    else if (NB == 4) KES_CALL(4, M, P, R, B, S);    \
+    else KES_CALL(8, M, P, R, B, S);                 \
     break;
   switch (cfg.variant_blk) {
     KES_BLK_VARIANTS(X)
@@ -429,10 +491,11 @@ void stage4_dispatch(const SellDev& A, int n_sm, cudaStream_t st, int NB, const 
   else k_stage4<T, 8><<<grid, 256, 0, st>>>(A, x, v);
 }
 
-template <typename T, int NB, int M, bool P, int R, int B>
+template <typename T, int NB, int M, bool P, int R, int B, bool S>
 int occ_one(int block) {
   int nb = 0;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_blk<T, NB, false, false, M, P, R, B>, block, 0) ==
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_blk<T, NB, false, false, M, P, R, B, S>, block,
+                                                       0) ==
                  cudaSuccess
              ? nb
              : 0;
@@ -493,7 +556,7 @@ int elem_grid(int64_t count) {
 
 int blk_variant_count() {
   int n = 0;
-#define X(ID, M, P, R, B) ++n;
+#define X(ID, M, P, R, B, S) ++n;
   KES_BLK_VARIANTS(X)
 #undef X
   return n;
@@ -501,12 +564,14 @@ int blk_variant_count() {
 
 int blk_blocks_per_sm(bool fp32, int NB, int variant, int block) {
   int nb = 0;
-#define X(ID, M, P, R, B)                                                                                \
-  case ID:                                                                                                 \
-    if (fp32) nb = NB == 2 ? occ_one<float, 2, M, P, R, B>(block) : NB == 4 ? occ_one<float, 4, M, P, R, B>(block) \
-                                                                          : occ_one<float, 8, M, P, R, B>(block);  \
-    else nb = NB == 2 ? occ_one<double, 2, M, P, R, B>(block) : NB == 4 ? occ_one<double, 4, M, P, R, B>(block)    \
-                                                                      : occ_one<double, 8, M, P, R, B>(block);     \
+#define X(ID, M, P, R, B, S)                                                                      \
+  case ID:                                                                                          \
+    if (fp32)                                                                                       \
+      nb = NB == 2 ? occ_one<float, 2, M, P, R, B, S>(block)                                        \
+                   : NB == 4 ? occ_one<float, 4, M, P, R, B, S>(block) : occ_one<float, 8, M, P, R, B, S>(block); \
+    else                                                                                            \
+      nb = NB == 2 ? occ_one<double, 2, M, P, R, B, S>(block)                                       \
+                   : NB == 4 ? occ_one<double, 4, M, P, R, B, S>(block) : occ_one<double, 8, M, P, R, B, S>(block); \
     break;
   switch (variant) {
     KES_BLK_VARIANTS(X)
