@@ -127,15 +127,6 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
   t = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
 }
 
-// 16-byte asynchronous copy global -> shared (no registers held while in flight); the
-// copying thread reads the data back itself after cp_async_wait_all.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
 __device__ __forceinline__ int32_t ld_idx(const int32_t* p) { return __ldcs(p); }
 __device__ __forceinline__ int32_t ld_idx(const int16_t* p) { return __ldcs(reinterpret_cast<const short*>(p)); }
 
@@ -210,12 +201,8 @@ __device__ __forceinline__ void row_sums_pipe(T (&un)[NH], const T* __restrict__
 // 32-row slice; LPR = 2 gives a lane NB / 2 columns and a warp half a slice (16 rows),
 // which halves the registers a thread needs for its columns. Either way every column is
 // the same FMA chain in entry order, so the shapes round identically. PB > 0 pipelines the
-// matrix stream PB entries ahead (row_sums_pipe); PB = 0 loads entries in pairs. AS (FP32,
-// at most kAsAcc accumulator pairs, 16-byte rows) copies the slice's accumulator rows into
-// shared memory asynchronously when the slice starts, so their latency overlaps the row
-// sums instead of following them; every thread reads back only its own copies.
-constexpr int kAsAcc = 2;
-template <typename T, int NB, bool FIRST, bool LAST, int MINB, bool PF, int LPR, int PB, bool AS>
+// matrix stream PB entries ahead (row_sums_pipe); PB = 0 loads entries in pairs.
+template <typename T, int NB, bool FIRST, bool LAST, int MINB, bool PF, int LPR, int PB>
 __global__ void __launch_bounds__(256, MINB)
     k_step_blk(SellDev A, const T* __restrict__ x, const T* __restrict__ g, const T* prev, T* out, T* acc_s,
                T* acc_c, double* acc64, int64_t acc_stride, int F, const T* __restrict__ ahi,
@@ -226,9 +213,6 @@ __global__ void __launch_bounds__(256, MINB)
   constexpr int NH = NB / LPR;            // columns of this lane
   constexpr int kRows = kSliceC / LPR;    // rows of a warp's unit
   static_assert(LPR == 1 || !PF, "the L2 prefetch shapes take whole slices");
-  constexpr bool kAS = AS && kF32 && (NH * 4) % 16 == 0;
-  constexpr int kChunks = kAS ? NH * 4 / 16 : 1;           // 16-byte pieces of one row of NH floats
-  __shared__ float4 s_acc[kAS ? kAsAcc * 2 * kChunks : 1][kAS ? 256 : 1];  // [piece][thread]
   const T* val;
   if constexpr (kF32) val = A.val32;
   else val = A.val64;
@@ -273,21 +257,6 @@ __global__ void __launch_bounds__(256, MINB)
     const T* vp = val + beg + rs;
     const int64_t row = s * kSliceC + rs;
     const int64_t ro = row * NB + co;  // this lane's values in a row-major block
-    const bool staged = kAS && (cpt ? 1 : F) <= kAsAcc;
-    if constexpr (kAS) {
-      if (staged) {
-        for (int f = 0; f < (cpt ? 1 : F); ++f) {
-          const float* gs = reinterpret_cast<const float*>(acc_s) + f * acc_stride + ro;
-          const float* gc = reinterpret_cast<const float*>(acc_c) + f * acc_stride + ro;
-#pragma unroll
-          for (int q = 0; q < kChunks; ++q) {
-            cp_async16(&s_acc[(2 * f) * kChunks + q][threadIdx.x], gs + 4 * q);
-            cp_async16(&s_acc[(2 * f + 1) * kChunks + q][threadIdx.x], gc + 4 * q);
-          }
-        }
-        cp_async_commit();
-      }
-    }
     T xi[NH], pi[NH], un[NH];
     load_plain<NH>(x + ro, xi);
     if constexpr (FIRST) {
@@ -311,9 +280,6 @@ __global__ void __launch_bounds__(256, MINB)
       else row_sums<T, NB, NH>(un, vp, A.col + beg + rs, 0, w, g, co);
     }
     if (!LAST) store_row<NH>(out + ro, un);
-    if constexpr (kAS) {
-      if (staged) cp_async_wait_all();
-    }
     bool bad = false;
     for (int f = 0; f < nacc; ++f) {
       const int64_t at = f * acc_stride + ro;
@@ -342,18 +308,8 @@ __global__ void __launch_bounds__(256, MINB)
       }
       if constexpr (kF32) {
         float as[NH], ac[NH];
-        if (staged) {
-#pragma unroll
-          for (int q = 0; q < kChunks; ++q) {
-            const float4 ts = s_acc[(2 * f) * kChunks + q][threadIdx.x];
-            const float4 tc = s_acc[(2 * f + 1) * kChunks + q][threadIdx.x];
-            as[4 * q] = ts.x; as[4 * q + 1] = ts.y; as[4 * q + 2] = ts.z; as[4 * q + 3] = ts.w;
-            ac[4 * q] = tc.x; ac[4 * q + 1] = tc.y; ac[4 * q + 2] = tc.z; ac[4 * q + 3] = tc.w;
-          }
-        } else {
-          load_plain<NH>(acc_s + at, as);
-          load_plain<NH>(acc_c + at, ac);
-        }
+        load_plain<NH>(acc_s + at, as);
+        load_plain<NH>(acc_c + at, ac);
         double v64[NH];
 #pragma unroll
         for (int j = 0; j < NH; ++j) {
@@ -395,25 +351,25 @@ __global__ void __launch_bounds__(256, MINB)
 
 // Launch shapes of the block kernels: minimum resident 256-thread blocks per SM, whether
 // the slices are prefetched into L2, lanes per row, entries of the pipelined matrix stream
-// (0: pairs, not pipelined), accumulator rows staged by asynchronous copies (FP32).
-#define KES_BLK_VARIANTS(X)                                                                                    \
-  X(0, 1, false, 1, 0, false) X(1, 2, false, 1, 0, false) X(2, 3, false, 1, 0, false)                          \
-  X(3, 4, false, 1, 0, false) X(4, 1, true, 1, 0, false) X(5, 2, true, 1, 0, false)                            \
-  X(6, 3, true, 1, 0, false) X(7, 4, true, 1, 0, false) X(8, 4, false, 2, 0, false)                            \
-  X(9, 5, false, 2, 0, false) X(10, 6, false, 2, 0, false) X(11, 4, false, 1, 2, false)                        \
-  X(12, 3, false, 1, 4, false) X(13, 4, false, 1, 4, false) X(14, 2, false, 1, 8, false)                       \
-  X(15, 6, false, 2, 4, false) X(16, 4, false, 2, 8, false) X(17, 4, false, 1, 4, true)                        \
-  X(18, 3, false, 1, 4, true) X(19, 4, false, 1, 2, true) X(20, 6, false, 2, 4, true)
+// (0: pairs, not pipelined). (Copying each slice's accumulator rows into shared memory with
+// cp.async when the slice starts was measured as well: 186-201 us against 173 us for
+// shape 13 on the 12-mesh batch, so it is not offered.)
+#define KES_BLK_VARIANTS(X)                                                                         \
+  X(0, 1, false, 1, 0) X(1, 2, false, 1, 0) X(2, 3, false, 1, 0) X(3, 4, false, 1, 0)              \
+  X(4, 1, true, 1, 0) X(5, 2, true, 1, 0) X(6, 3, true, 1, 0) X(7, 4, true, 1, 0)                   \
+  X(8, 4, false, 2, 0) X(9, 5, false, 2, 0) X(10, 6, false, 2, 0) X(11, 4, false, 1, 2)             \
+  X(12, 3, false, 1, 4) X(13, 4, false, 1, 4) X(14, 2, false, 1, 8) X(15, 6, false, 2, 4)           \
+  X(16, 4, false, 2, 8)
 
-template <typename T, int NB, int MINB, bool PF, int LPR, int PB, bool AS>
+template <typename T, int NB, int MINB, bool PF, int LPR, int PB>
 void blk_impl(int grid, int block, cudaStream_t st, bool first, bool last, const SellDev& A, const T* x,
               const T* g, const T* prev, T* out, T* acc_s, T* acc_c, double* acc64, int64_t acc_stride, int F, const T* ahi,
               const T* alo, int Lp1, int step, int cpt, int* flag) {
 #define KES_BLK_ARGS A, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, F, ahi, alo, Lp1, step, cpt, flag
-  if (first && last) k_step_blk<T, NB, true, true, MINB, PF, LPR, PB, AS><<<grid, block, 0, st>>>(KES_BLK_ARGS);
-  else if (first) k_step_blk<T, NB, true, false, MINB, PF, LPR, PB, AS><<<grid, block, 0, st>>>(KES_BLK_ARGS);
-  else if (last) k_step_blk<T, NB, false, true, MINB, PF, LPR, PB, AS><<<grid, block, 0, st>>>(KES_BLK_ARGS);
-  else k_step_blk<T, NB, false, false, MINB, PF, LPR, PB, AS><<<grid, block, 0, st>>>(KES_BLK_ARGS);
+  if (first && last) k_step_blk<T, NB, true, true, MINB, PF, LPR, PB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
+  else if (first) k_step_blk<T, NB, true, false, MINB, PF, LPR, PB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
+  else if (last) k_step_blk<T, NB, false, true, MINB, PF, LPR, PB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
+  else k_step_blk<T, NB, false, false, MINB, PF, LPR, PB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
 #undef KES_BLK_ARGS
 }
 
@@ -423,20 +379,20 @@ void blk_dispatch(const LaunchCfg& cfg, int NB, cudaStream_t st, bool first, boo
                   const T* ahi, const T* alo, int Lp1, int step, int cpt, int* flag) {
   // a block of 256 threads is 8 warps; a warp takes a slice (or half a slice, LPR = 2)
   int lpr = 1;
-#define X(ID, M, P, R, B, S) \
+#define X(ID, M, P, R, B) \
   if (cfg.variant_blk == ID) lpr = R;
   KES_BLK_VARIANTS(X)
 #undef X
   const int64_t need = (A.n_slices * lpr + 7) / 8;
   const int grid = static_cast<int>(need < cfg.grid_blk ? need : cfg.grid_blk);
-#define KES_CALL(NBV, M, P, R, B, S)                                                                          \
-  blk_impl<T, NBV, M, P, R, B, S>(grid, 256, st, first, last, A, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, \
-                                  F, ahi, alo, Lp1, step, cpt, flag)
-#define X(ID, M, P, R, B, S)                         \
-  case ID:                                           \
-    if (NB == 2) KES_CALL(2, M, P, R, B, S);         \
-    else if (NB == 4) KES_CALL(4, M, P, R, B, S);    \
-    else KES_CALL(8, M, P, R, B, S);                 \
+#define KES_CALL(NBV, M, P, R, B)                                                                             \
+  blk_impl<T, NBV, M, P, R, B>(grid, 256, st, first, last, A, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, F, \
+                               ahi, alo, Lp1, step, cpt, flag)
+#define X(ID, M, P, R, B)                         \
+  case ID:                                        \
+    if (NB == 2) KES_CALL(2, M, P, R, B);         \
+    else if (NB == 4) KES_CALL(4, M, P, R, B);    \
+    else KES_CALL(8, M, P, R, B);                 \
     break;
   switch (cfg.variant_blk) {
     KES_BLK_VARIANTS(X)
@@ -491,11 +447,10 @@ void stage4_dispatch(const SellDev& A, int n_sm, cudaStream_t st, int NB, const 
   else k_stage4<T, 8><<<grid, 256, 0, st>>>(A, x, v);
 }
 
-template <typename T, int NB, int M, bool P, int R, int B, bool S>
+template <typename T, int NB, int M, bool P, int R, int B>
 int occ_one(int block) {
   int nb = 0;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_blk<T, NB, false, false, M, P, R, B, S>, block,
-                                                       0) ==
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_blk<T, NB, false, false, M, P, R, B>, block, 0) ==
                  cudaSuccess
              ? nb
              : 0;
@@ -556,7 +511,7 @@ int elem_grid(int64_t count) {
 
 int blk_variant_count() {
   int n = 0;
-#define X(ID, M, P, R, B, S) ++n;
+#define X(ID, M, P, R, B) ++n;
   KES_BLK_VARIANTS(X)
 #undef X
   return n;
@@ -564,14 +519,14 @@ int blk_variant_count() {
 
 int blk_blocks_per_sm(bool fp32, int NB, int variant, int block) {
   int nb = 0;
-#define X(ID, M, P, R, B, S)                                                                      \
+#define X(ID, M, P, R, B)                                                                           \
   case ID:                                                                                          \
     if (fp32)                                                                                       \
-      nb = NB == 2 ? occ_one<float, 2, M, P, R, B, S>(block)                                        \
-                   : NB == 4 ? occ_one<float, 4, M, P, R, B, S>(block) : occ_one<float, 8, M, P, R, B, S>(block); \
+      nb = NB == 2 ? occ_one<float, 2, M, P, R, B>(block)                                           \
+                   : NB == 4 ? occ_one<float, 4, M, P, R, B>(block) : occ_one<float, 8, M, P, R, B>(block); \
     else                                                                                            \
-      nb = NB == 2 ? occ_one<double, 2, M, P, R, B, S>(block)                                       \
-                   : NB == 4 ? occ_one<double, 4, M, P, R, B, S>(block) : occ_one<double, 8, M, P, R, B, S>(block); \
+      nb = NB == 2 ? occ_one<double, 2, M, P, R, B>(block)                                          \
+                   : NB == 4 ? occ_one<double, 4, M, P, R, B>(block) : occ_one<double, 8, M, P, R, B>(block); \
     break;
   switch (variant) {
     KES_BLK_VARIANTS(X)
