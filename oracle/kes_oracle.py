@@ -40,7 +40,7 @@ __all__ = [
     "filter_apply_multi", "power_iteration", "m_inner", "m_norm",
     "orthonormalize_cgs2", "rayleigh_ritz", "ritz_residuals", "krylov_solve",
     "block_krylov_solve", "multi_interval_krylov_solve", "subspace_iteration",
-    "refine_subspace", "gaussian_weight", "alpha_table_gaussian", "triangle_weight",
+    "refine_subspace", "refine_selection", "gaussian_weight", "alpha_table_gaussian", "triangle_weight",
     "alpha_table_triangle", "q_values_leapfrog4", "beta_tilde_leapfrog4",
     "filter_apply_leapfrog4",
     "KrylovResult", "BREAKDOWN_RATIO",
@@ -459,7 +459,7 @@ def block_krylov_solve(S, m: np.ndarray, R0: np.ndarray, omega_min: float,
 
 def multi_interval_krylov_solve(S, m: np.ndarray, R0: np.ndarray, intervals, tau: float,
                                 L: int, kmax: int, tol: float, check_every: int = 5,
-                                refine_sweeps: int = 0) -> KrylovResult:
+                                refine_sweeps: int = 0, refine_extra: int = 0) -> KrylovResult:
     """F intervals searched at once by F independent block Krylov processes.
 
     R0: (b, n) with b a multiple of F = len(intervals); g = b / F. Process f is the
@@ -467,8 +467,8 @@ def multi_interval_krylov_solve(S, m: np.ndarray, R0: np.ndarray, intervals, tau
     R0[f g : (f + 1) g], with its own basis of up to kmax vectors; the processes only
     share the time stepping (column j of the b-column trajectory belongs to process
     j // g), which does not change what any of them computes. With refine_sweeps > 0,
-    each process's in-interval Ritz vectors then go through refine_subspace on its
-    interval. The accepted pairs of all processes are merged in ascending theta with
+    each process's in-interval Ritz vectors (and the refine_extra nearest outside
+    its interval) then go through refine_subspace on its interval. The accepted pairs of all processes are merged in ascending theta with
     the index of the interval that found each (a pair in two overlapping intervals
     is reported by both); k_used adds up over the processes, time_steps is the length
     of the shared trajectory (the most steps any process took), and the Ritz values
@@ -484,12 +484,11 @@ def multi_interval_krylov_solve(S, m: np.ndarray, R0: np.ndarray, intervals, tau
         r = block_krylov_solve(S, m, R0[f * g:(f + 1) * g], lo, hi, tau, L, kmax, tol,
                                check_every, keep_basis=refine_sweeps > 0)
         if refine_sweeps > 0:
-            inside = ~np.isnan(r.ritz_rel_res)
             theta_r, Y = rayleigh_ritz(S, r.basis)
-            X = (Y.T @ r.basis)[inside]
+            X = (Y.T @ r.basis)[refine_selection(theta_r, lo, hi, refine_extra)]
             if len(X):
                 th, rel, Xa, thi, reli = refine_subspace(S, m, X, lo, hi, tau, L, tol,
-                                                         refine_sweeps)
+                                                         refine_sweeps, refine_extra)
                 X_acc, a_acc = Xa, np.array([np.linalg.norm(S @ x - t * (m * x))
                                              for t, x in zip(th, Xa)])
                 r = KrylovResult(omega2=th, omega=np.sqrt(th), rel_res=rel, abs_res=a_acc,
@@ -513,14 +512,28 @@ def multi_interval_krylov_solve(S, m: np.ndarray, R0: np.ndarray, intervals, tau
         basis=None, history=[r.history for r in parts], interval=label[order])
 
 
+def refine_selection(theta: np.ndarray, omega_min: float, omega_max: float, extra: int = 0) -> np.ndarray:
+    """Indices (ascending) of the Ritz values whose vectors a refinement sweep filters:
+    every one with omega = sqrt(theta) in [omega_min, omega_max], and the `extra` nearest
+    outside it (distance in omega to the interval, ties to the lower index), a buffer
+    like the one FEAST keeps beyond the wanted eigenvalues."""
+    omega = np.sqrt(np.maximum(np.asarray(theta, dtype=np.float64), 0.0))
+    inside = (omega >= omega_min) & (omega <= omega_max)
+    out = np.flatnonzero(~inside)
+    dist = np.where(omega[out] < omega_min, omega_min - omega[out], omega[out] - omega_max)
+    keep = out[np.argsort(dist, kind="stable")[:max(extra, 0)]]
+    return np.sort(np.concatenate([np.flatnonzero(inside), keep]))
+
+
 def refine_subspace(S, m: np.ndarray, X: np.ndarray, omega_min: float, omega_max: float,
-                    tau: float, L: int, tol: float, sweeps: int = 1):
+                    tau: float, L: int, tol: float, sweeps: int = 1, extra: int = 0):
     """Filtered subspace iteration on the rows of X (the fixed-dimension, FEAST-like
     use of the filter mentioned in Sec. 4): each sweep filters every vector (X <- C X),
     M-orthonormalises the result (CGS2, dependent vectors dropped), solves the
     projected problem (eq. projevp) and keeps the Ritz vectors with omega in the
-    interval for the next sweep. Returns (theta_acc, rel_acc, X_acc, theta_inside,
-    rel_inside) of the last sweep, acceptance rel_res <= tol."""
+    interval, and the `extra` nearest outside it (refine_selection), for the next
+    sweep. Returns (theta_acc, rel_acc, X_acc, theta_inside, rel_inside) of the last
+    sweep, acceptance rel_res <= tol."""
     alpha = alpha_table(omega_min, omega_max, tau, L)
     X = np.atleast_2d(np.asarray(X, dtype=np.float64))
     th_in = rel_in = np.zeros(0)
@@ -539,7 +552,7 @@ def refine_subspace(S, m: np.ndarray, X: np.ndarray, omega_min: float, omega_max
         th_in, rel_in = theta[inside], r
         acc = r <= tol
         th_acc, rel_acc, X_acc = th_in[acc], r[acc], Xi[acc]
-        X = Xi
+        X = (Y.T @ B)[refine_selection(theta, omega_min, omega_max, extra)]
     return th_acc, rel_acc, X_acc, th_in, rel_in
 
 

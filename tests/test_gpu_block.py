@@ -193,6 +193,49 @@ def test_fp32_solve_with_fp64_refinement_reaches_fp64_residuals(b, refine_L):
 
 
 
+@pytest.mark.parametrize("extra", [0, 6])
+def test_refinement_with_a_buffer_matches_oracle(extra):
+    # FP64 block solve, then one refinement sweep over the in-interval Ritz vectors and
+    # the `extra` nearest outside the interval (refine_extra): the refined subspace is
+    # the oracle's up to rounding, so its in-interval Ritz values agree with the oracle's
+    p = square_grid(32)
+    S = p.to_scipy()
+    tau = _tau(p)
+    lo, hi, L, kmax = 20.0, 30.0, 300, 100   # 36 eigenvalues (19 distinct), all accepted by kmax 100
+    R = start_vectors(p.n, 2, 5)
+    so = K.kes_solve_opts_default()
+    so.kmax, so.tol, so.check_every, so.want_vectors = kmax, 1e-8, kmax, 1
+    so.refine_sweeps, so.refine_extra = 1, extra
+    with K.Context(p, precision="fp64", block_b=2) as c:
+        K.kes_set_filter(c.handle, lo, hi, tau, L)
+        res = K.kes_block_krylov_solve(c.handle, R, 2, so)[0]
+    ref = O.multi_interval_krylov_solve(S, p.m, R, [(lo, hi)], tau, L, kmax, 1e-8, check_every=kmax,
+                                        refine_sweeps=1, refine_extra=extra)
+    inside = ~np.isnan(res["ritz_rel_res"])
+    got = np.sort(res["ritz_omega2"][inside])
+    exact = spectra.eigenvalues_in(p.cells, p.h, lo, hi)
+    assert res["refine_steps"] > 0
+    for th, x in zip(res["omega2"], res["vectors"]):
+        assert np.min(np.abs(exact - th)) <= 1e-10 * th
+        assert np.linalg.norm(S @ x - th * p.m * x) <= 1.01e-8 * th * np.linalg.norm(p.m * x)
+    # the refined in-interval Ritz values: the oracle's refinement of the same selection
+    _, _, _, th_ref, _ = O.refine_subspace(S, p.m, _selected_ritz_vectors(S, p.m, R, lo, hi, tau, L, kmax, extra),
+                                           lo, hi, tau, L, 1e-8, 1, extra)
+    th_ref = np.sort(th_ref)
+    print(f"extra={extra}: {got.size} in-interval Ritz values (oracle {th_ref.size}), {res['n_pairs']} accepted, "
+          f"{res['refine_steps']} refinement steps")
+    assert got.size == th_ref.size
+    np.testing.assert_allclose(got, th_ref, rtol=1e-9)
+    assert abs(res["n_pairs"] - len(ref.omega2)) <= 1
+
+
+def _selected_ritz_vectors(S, m, R, lo, hi, tau, L, kmax, extra):
+    """The oracle's Ritz vectors that a refinement with `extra` buffer vectors filters."""
+    r = O.block_krylov_solve(S, m, R, lo, hi, tau, L, kmax, 1e-8, check_every=kmax, keep_basis=True)
+    theta, Y = O.rayleigh_ritz(S, r.basis)
+    return (Y.T @ r.basis)[O.refine_selection(theta, lo, hi, extra)]
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("band", ["gaussian", "triangle"])
 def test_band_weights_filter_and_solve(precision, band):

@@ -214,3 +214,23 @@ def test_subspace_iteration_without_filter_is_caught(monkeypatch):
     _patch(monkeypatch, "filter_apply", no_filter)
     with pytest.raises(AssertionError):
         pins.test_subspace_iteration_finds_the_dominant_eigenvalues_of_the_filter()
+
+
+def test_refinement_buffer_farthest_instead_of_nearest_is_caught(monkeypatch):
+    def farthest(theta, omega_min, omega_max, extra=0):
+        omega = np.sqrt(np.maximum(np.asarray(theta, dtype=np.float64), 0.0))
+        inside = (omega >= omega_min) & (omega <= omega_max)
+        out = np.flatnonzero(~inside)
+        dist = np.where(omega[out] < omega_min, omega_min - omega[out], omega[out] - omega_max)
+        keep = out[np.argsort(-dist, kind="stable")[:max(extra, 0)]]
+        return np.sort(np.concatenate([np.flatnonzero(inside), keep]))
+    _patch(monkeypatch, "refine_selection", farthest)
+    with pytest.raises(AssertionError):
+        pins.test_refine_selection_keeps_the_interval_and_the_nearest_outside()
+
+
+def test_refinement_dropping_the_buffer_is_caught(monkeypatch):
+    real = K.refine_selection
+    _patch(monkeypatch, "refine_selection", lambda theta, lo, hi, extra=0: real(theta, lo, hi, 0))
+    with pytest.raises(AssertionError):
+        pins.test_refine_selection_keeps_the_interval_and_the_nearest_outside()

@@ -541,3 +541,36 @@ def test_subspace_iteration_finds_the_dominant_eigenvalues_of_the_filter():
         assert np.min(np.abs(exact - t)) <= 1e-10 * t
     for t in must:
         assert np.min(np.abs(th - t)) <= 1e-10 * t
+
+
+def test_refine_selection_keeps_the_interval_and_the_nearest_outside():
+    # omega = 1, 2, 3, 4, 5, 6 for the interval [2.5, 4.2]: inside 3 and 4; outside, by
+    # distance to the interval, 2 (0.5), 5 (0.8), 1 (1.5), 6 (1.8)
+    theta = np.array([1.0, 2.0, 3.0, 4.0, 5.0, 6.0]) ** 2
+    assert list(O.refine_selection(theta, 2.5, 4.2)) == [2, 3]
+    assert list(O.refine_selection(theta, 2.5, 4.2, 1)) == [1, 2, 3]
+    assert list(O.refine_selection(theta, 2.5, 4.2, 3)) == [0, 1, 2, 3, 4]
+    assert list(O.refine_selection(theta, 2.5, 4.2, 10)) == [0, 1, 2, 3, 4, 5]
+    # equal distances (omega = 0.5 and 4 to [1.5, 3]) go to the lower index
+    assert list(O.refine_selection(np.array([0.25, 4.0, 16.0]), 1.5, 3.0, 1)) == [0, 1]
+    # negative rounding noise counts as omega = 0
+    assert list(O.refine_selection(np.array([-1e-12, 4.0]), 1.0, 3.0, 1)) == [0, 1]
+
+
+def test_refinement_buffer_lets_rayleigh_ritz_remove_outside_noise():
+    # an eigenvector of the interval polluted along an eigenvector just outside it: a
+    # short filter only damps that component by its contrast, while with the outside
+    # direction in the refined subspace (the buffer) Rayleigh-Ritz removes it
+    p = square_grid(24)
+    S = p.to_scipy()
+    tau = 0.9 * 2 / math.sqrt(spectra.box_spectrum(p.cells, p.h).max())
+    v = spectra.box_eigenvector(p.cells, (3, 5))          # omega = 18.05
+    u = spectra.box_eigenvector(p.cells, (1, 6))          # omega = 18.64, outside [17.8, 18.3]
+    lam_u = 4 * 576 * (math.sin(1 * math.pi / 48) ** 2 + math.sin(6 * math.pi / 48) ** 2)
+    assert 18.3 < math.sqrt(lam_u) < 18.7
+    noisy = v + 1e-4 * (np.abs(v).max() / np.abs(u).max()) * u
+    lo, hi, L = 17.8, 18.3, 300
+    _, _, _, th0, rel0 = O.refine_subspace(S, p.m, noisy[None, :], lo, hi, tau, L, 1e-8)
+    _, _, _, th1, rel1 = O.refine_subspace(S, p.m, np.stack([noisy, u + 1e-3 * v]), lo, hi, tau, L, 1e-8)
+    assert len(th0) == 1 and len(th1) == 1
+    assert rel1[0] < 1e-11 and rel0[0] > 1e3 * rel1[0]
