@@ -68,9 +68,10 @@ def parse_args(argv=None):
     ap.add_argument("--L", type=int, default=0, help="override the workload's time steps (--mode filter, certify)")
     ap.add_argument("--kmax", type=int, default=0, help="override the workload's Krylov dimension (--mode certify)")
     ap.add_argument("--interval", default="", help="override the filter interval as 'wmin,wmax' (--mode certify)")
-    ap.add_argument("--tol", type=float, default=0.0, help="override the acceptance tolerance (--mode certify)")
-    ap.add_argument("--refine-sweeps", type=int, default=0, help="FP64 refinement sweeps (--mode certify)")
-    ap.add_argument("--refine-extra", type=int, default=0, help="buffer Ritz vectors of the refinement (--mode certify)")
+    ap.add_argument("--tol", type=float, default=0.0, help="override the acceptance tolerance (--mode solve, certify)")
+    ap.add_argument("--refine-sweeps", type=int, default=0, help="FP64 refinement sweeps (--mode solve, certify)")
+    ap.add_argument("--refine-extra", type=int, default=0,
+                    help="buffer Ritz vectors of the refinement (--mode solve, certify)")
     ap.add_argument("--precision", default="", choices=["", "fp64", "fp32"],
                     help="override the workload's precision (--mode certify)")
     ap.add_argument("--b", type=int, default=0, help="override the workload's block width (--mode certify)")
@@ -453,7 +454,8 @@ def run_kes(args):
     wmin1, wmax1 = wmin_all[:, :F_solve], wmax_all[:, :F_solve]
     K.kes_set_filters_batch(h, wmin1, wmax1, taus, wl.L)
     so = K.kes_solve_opts_default()
-    so.kmax, so.tol, so.check_every = wl.kmax, wl.acceptance(), wl.check_every
+    so.kmax, so.tol, so.check_every = wl.kmax, args.tol or wl.acceptance(), wl.check_every
+    so.refine_sweeps, so.refine_extra = args.refine_sweeps, args.refine_extra
     R0_host = start_block(problems, b, wl.seed + 1 + 1000 * rank)
     R0_dev = torch.from_numpy(R0_host).to(dev)
     torch.cuda.synchronize()
@@ -573,6 +575,7 @@ def run_kes(args):
     so_e2e = K.kes_solve_opts_default()
     src = so_t if so_t is not None else so
     so_e2e.kmax, so_e2e.tol, so_e2e.check_every, so_e2e.want_vectors = src.kmax, src.tol, src.check_every, 1
+    so_e2e.refine_sweeps, so_e2e.refine_extra = src.refine_sweeps, src.refine_extra
     e2e_steps = args.e2e_steps
     barrier(dist)
     torch.cuda.synchronize()
@@ -639,7 +642,8 @@ def run_kes(args):
         "gpu_launches": int(stats["kernel_launches"]),
         "clocks": clk.summary(),
         "tts": tts,
-        "solve": {"accepted_pairs": [x["n_pairs"] for x in res] if batch else res[0]["n_pairs"],
+        "solve": {"tol": so.tol, "refine_sweeps": so.refine_sweeps, "refine_extra": so.refine_extra,
+                  "accepted_pairs": [x["n_pairs"] for x in res] if batch else res[0]["n_pairs"],
                   "k_used": res[0]["k_used"], "time_steps": steps_per_solve,
                   "max_rel_res": max((float(x["rel_res"].max()) for x in res if x["n_pairs"]), default=None),
                   "max_eig_rel_err_vs_exact": eig_err, "filter_ms_share": stats["filter_ms"] / ms_local,

@@ -6,7 +6,8 @@ The oracle cannot produce single outputs of a 600-step filter one by one, so
 the full-length filter is checked through a property that holds at any size
 (Lemma 2.3: an eigenvector is scaled by beta~(omega)), element-wise parity is
 checked on a full-size trajectory of 60 steps, the Ritz pairs of the
-60-vector solve are checked by the residual bound, and the solve continued to
+60-vector solve (which accepts none yet) are checked by the residual bound, and
+the solve continued to
 the Krylov dimension that the time-to-solution measurement uses must accept
 every distinct eigenvalue of the interval, each pair certified on the host
 (FP64 residual from the returned vector, eigenvalue and eigenspace against the
@@ -99,7 +100,10 @@ def test_filter_elementwise_parity_full_size(cube, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_krylov_solve_full_size_matches_exact_spectrum(cube, precision):
+def test_krylov_solve_full_size_ritz_pairs_obey_the_residual_bound(cube, precision):
+    """The benchmarked solve (Krylov dimension 60): with 83 distinct eigenvalues in the
+    interval it accepts none yet (the converged solve below runs to 250 vectors), so the
+    check here is on every Ritz pair in the interval, converged or not."""
     p, v0, w_gpu = cube
     tau = WL.cfl * 2 / w_gpu
     tol = 1e-8 if precision == "fp64" else 1e-5
@@ -113,17 +117,17 @@ def test_krylov_solve_full_size_matches_exact_spectrum(cube, precision):
     print(f"{precision}: {res['n_pairs']} accepted of {exact.size} distinct, k={res['k_used']}, "
           f"{res['solve_ms']:.0f} ms")
     assert res["k_used"] == WL.kmax and res["time_steps"] == (WL.kmax - 1) * WL.L
-    assert np.all(res["rel_res"] <= tol)
-    for th in res["omega2"]:
-        assert np.min(np.abs(exact - th) / th) <= EIG_REL[precision]
-    # Every Ritz pair in the interval, converged or not, obeys the residual bound of a
-    # symmetric definite pencil: some eigenvalue lies within ||(S - theta M) x||_{M^-1}
-    # of theta (||x||_M = 1); with M = h^3 I that radius is rel_res * theta.
+    # Every Ritz pair in the interval obeys the residual bound of a symmetric definite
+    # pencil: some eigenvalue lies within ||(S - theta M) x||_{M^-1} of theta (||x||_M = 1);
+    # with M = h^3 I that radius is rel_res * theta.
     inside = ~np.isnan(res["ritz_rel_res"])
     assert inside.any()
     for th, rel in zip(res["ritz_omega2"][inside], res["ritz_rel_res"][inside]):
         gap = np.min(np.abs(everything - th))
         assert gap <= rel * th * (1 + 1e-6) + 1e-12 * th, (th, rel, gap)
+    # whatever it accepts (nothing at this dimension on this build) is an exact eigenvalue
+    for th in res["omega2"]:
+        assert np.min(np.abs(exact - th) / th) <= EIG_REL[precision]
 
 
 def _modes_of(cells, lam, rel=1e-10):
