@@ -13,6 +13,7 @@ from __future__ import annotations
 import ctypes as C
 import os
 import re
+import weakref
 
 import numpy as np
 
@@ -318,7 +319,11 @@ def _arr(p, k):
 
 
 def _result_dict(rp, st) -> dict:
+    """The result as a dict of numpy arrays. The small arrays are copied; the Ritz vectors
+    (often gigabytes) are not: their array views the library's buffer, and the result is
+    released when that array is garbage collected (or at once when there are none)."""
     r = rp.contents
+    keep = False
     try:
         p = r.n_pairs
         out = dict(status=st, n=r.n, n_pairs=p, k_used=r.k_used, breakdown=bool(r.breakdown),
@@ -329,9 +334,13 @@ def _result_dict(rp, st) -> dict:
                    interval=(np.ctypeslib.as_array(r.interval, shape=(p,)).astype(np.int64) if p > 0
                              else np.zeros(0, dtype=np.int64)))
         if r.vectors and p > 0:
-            out["vectors"] = np.ctypeslib.as_array(r.vectors, shape=(p * r.n,)).copy().reshape(p, r.n)
+            flat = np.ctypeslib.as_array(r.vectors, shape=(p * r.n,))
+            weakref.finalize(flat, lib.kes_result_free, rp)
+            keep = True
+            out["vectors"] = flat.reshape(p, r.n)
     finally:
-        lib.kes_result_free(rp)
+        if not keep:
+            lib.kes_result_free(rp)
     return out
 
 
