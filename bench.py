@@ -336,9 +336,33 @@ class OraclePool:
         shutil.rmtree(self.dir, ignore_errors=True)
 
 
-def cpu_baseline(problem, tau, wl, seconds: float, interval) -> dict:
+def small_solve_oracle(small: dict | None) -> dict | None:
+    """The oracle's whole eigensolve (Algorithm 2.5 with the same start vector, tau and
+    sizes) on the small case the GPU solved (small_solve_gpu), in one process."""
+    if not small:
+        return None
+    import numpy as np
+    import oracle as O
+    from fe_inputs import WORKLOADS, start_vectors
+    wl = WORKLOADS[small["workload"]]
+    p = wl.build()
+    r0 = start_vectors(p.n, 1, wl.seed + 1)[0]
+    t0 = time.perf_counter()
+    res = O.krylov_solve(p.to_scipy(), p.m, r0, wl.omega_min, wl.omega_max, small["tau"], wl.L, wl.kmax, 1e-8,
+                         check_every=wl.check_every, keep_basis=False)
+    dt = time.perf_counter() - t0
+    gpu = np.asarray(small["gpu_omega2"])
+    worst = max((float(np.min(np.abs(res.omega2 - t)) / t) for t in gpu), default=None) if res.omega2.size else None
+    out = {k: v for k, v in small.items() if k != "gpu_omega2"}
+    out.update(oracle_s=dt, oracle_cores=1, oracle_accepted=int(res.omega2.size),
+               max_rel_diff_gpu_vs_oracle_eigenvalues=worst)
+    return out
+
+
+def cpu_baseline(problem, tau, wl, seconds: float, interval, small: dict | None = None) -> dict:
     """The oracle on the host cores: one process (single core) and P processes (all cores),
-    each a bounded sample of the workload's filter."""
+    each a bounded sample of the workload's filter; and the oracle's whole solve of the
+    small case beside the GPU's."""
     from fe_inputs import start_vectors
     v1, steps1, dt1 = oracle_sample(problem, tau, wl, seconds / 2, interval)
     P = host_cores()
@@ -357,6 +381,7 @@ def cpu_baseline(problem, tau, wl, seconds: float, interval) -> dict:
     return {"value": units / wall / 1e9, "unit": METRIC, "cores": P, "kind": "oracle",
             "sample": f"{P} processes, one per host core, each {steps} leapfrog steps of the FP64 oracle filter "
                       f"(one vector) on {problem.name} ({problem.n} dofs) at once, {wall:.1f} s wall",
+            "small_case_solve": small_solve_oracle(small),
             "cpu_model": cpu_model(),
             "single_core": {"value": v1, "cores": 1,
                             "sample": f"{steps1} leapfrog steps of the same filter in one process, {dt1:.1f} s"}}
@@ -418,6 +443,32 @@ def batch_filter_measurement(dev, stream, reps: int = 3) -> dict:
         out["blk_variant"] = st["blk_variant"]
         out["timing"] = f"{reps} filter applications of {wl.L} steps, CUDA events on the library stream, after one warm"
     return out
+
+
+def small_solve_gpu(stream) -> dict:
+    """The small case (64^2 square, [20, 30], L = 300, Krylov dimension 40, FP64) solved on
+    the GPU: wall time of the call, accepted pairs (compared with the oracle's solve of the
+    same problem in the CPU baseline)."""
+    import torch
+
+    import paper_2402_08515_gb300 as K
+    from fe_inputs import WORKLOADS, start_vectors
+    wl = WORKLOADS["square64_fp64"]
+    p = wl.build()
+    with K.Context(p, precision="fp64", stream=stream) as c:
+        w, _ = K.kes_estimate_omega_max(c.handle, wl.power_iters, start_vectors(p.n, 1, wl.seed)[0])
+        tau = wl.cfl * 2.0 / w
+        K.kes_set_filter(c.handle, wl.omega_min, wl.omega_max, tau, wl.L)
+        so = K.kes_solve_opts_default()
+        so.kmax, so.tol, so.check_every = wl.kmax, 1e-8, wl.check_every
+        r0 = start_vectors(p.n, 1, wl.seed + 1)[0]
+        K.kes_krylov_solve(c.handle, r0, so)                    # warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = K.kes_krylov_solve(c.handle, r0, so)
+        dt = time.perf_counter() - t0
+    return {"workload": "square64_fp64", "dofs": p.n, "kmax": wl.kmax, "L": wl.L, "tau": tau,
+            "gpu_s": dt, "gpu_accepted": res["n_pairs"], "gpu_omega2": [float(t) for t in res["omega2"]]}
 
 
 def run_kes(args):
@@ -616,7 +667,8 @@ def run_kes(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         big = max(range(len(problems)), key=lambda j: problems[j].n)
-        cpu = cpu_baseline(problems[big], taus[big], wl, args.cpu_seconds, ivs[big][0])
+        small = small_solve_gpu(stream) if args.workload == "cube128_fp64" else None
+        cpu = cpu_baseline(problems[big], taus[big], wl, args.cpu_seconds, ivs[big][0], small)
 
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,

@@ -30,3 +30,20 @@ def test_matched_pairs_counts_multiplicity_once_per_copy():
     assert bench.matched_pairs(exact, [2.0, 2.0 * (1 + 1e-12), 3.0]) == 3
     assert bench.matched_pairs(exact, [2.0] * 5 + [1.0]) == 4          # at most the multiplicity
     assert bench.matched_pairs(exact, [2.5, 1.0 + 1e-6]) == 0          # not within 1e-8
+
+
+def test_small_case_oracle_solve_reports_beside_the_gpu_fields():
+    from fe_inputs import WORKLOADS
+    wl = WORKLOADS["square64_fp64"]
+    p = wl.build()
+    tau = 0.9 * 2 / np.sqrt(spectra.grid_omega2(p.cells, p.h).max())
+    exact = spectra.omega2_in(p.cells, p.h, wl.omega_min, wl.omega_max)
+    small = {"workload": "square64_fp64", "dofs": p.n, "kmax": wl.kmax, "L": wl.L, "tau": tau,
+             "gpu_s": 0.0, "gpu_accepted": 0, "gpu_omega2": []}
+    assert bench.small_solve_oracle(None) is None
+    out = bench.small_solve_oracle(small)
+    assert "gpu_omega2" not in out and out["oracle_accepted"] >= 1 and out["oracle_s"] > 0
+    assert out["max_rel_diff_gpu_vs_oracle_eigenvalues"] is None
+    small["gpu_omega2"] = list(exact[:1])          # an exact eigenvalue the oracle finds
+    out = bench.small_solve_oracle(small)
+    assert out["max_rel_diff_gpu_vs_oracle_eigenvalues"] is not None
