@@ -352,10 +352,16 @@ def small_solve_oracle(small: dict | None) -> dict | None:
                          check_every=wl.check_every, keep_basis=False)
     dt = time.perf_counter() - t0
     gpu = np.asarray(small["gpu_omega2"])
-    worst = max((float(np.min(np.abs(res.omega2 - t)) / t) for t in gpu), default=None) if res.omega2.size else None
+    # pairs near the acceptance threshold may be accepted on one side only; the ones both
+    # accept (within 1e-10) are compared
+    diffs = [float(np.min(np.abs(res.omega2 - t)) / t) for t in gpu] if res.omega2.size else []
+    common = [d for d in diffs if d <= 1e-10]
     out = {k: v for k, v in small.items() if k != "gpu_omega2"}
     out.update(oracle_s=dt, oracle_cores=1, oracle_accepted=int(res.omega2.size),
-               max_rel_diff_gpu_vs_oracle_eigenvalues=worst)
+               accepted_by_both=len(common),
+               max_rel_diff_of_pairs_both_accept=max(common, default=None),
+               gpu_accepted_omega=[float(np.sqrt(t)) for t in gpu],
+               oracle_accepted_omega=[float(w) for w in res.omega])
     return out
 
 

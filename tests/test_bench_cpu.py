@@ -43,7 +43,7 @@ def test_small_case_oracle_solve_reports_beside_the_gpu_fields():
     assert bench.small_solve_oracle(None) is None
     out = bench.small_solve_oracle(small)
     assert "gpu_omega2" not in out and out["oracle_accepted"] >= 1 and out["oracle_s"] > 0
-    assert out["max_rel_diff_gpu_vs_oracle_eigenvalues"] is None
-    small["gpu_omega2"] = list(exact[:1])          # an exact eigenvalue the oracle finds
+    assert out["accepted_by_both"] == 0 and out["max_rel_diff_of_pairs_both_accept"] is None
+    small["gpu_omega2"] = [out["oracle_accepted_omega"][0] ** 2]   # a value the oracle accepts
     out = bench.small_solve_oracle(small)
-    assert out["max_rel_diff_gpu_vs_oracle_eigenvalues"] is not None
+    assert out["accepted_by_both"] == 1 and out["max_rel_diff_of_pairs_both_accept"] <= 1e-15
