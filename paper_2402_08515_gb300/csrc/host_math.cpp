@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <limits>
 #include <vector>
 
 #include "kes_internal.h"
@@ -79,6 +80,9 @@ void weights_response(const double* alpha, double tau, int L, const double* omeg
 // Householder tridiagonalisation, then implicit symmetric QR steps with the
 // Wilkinson shift, eigenvectors accumulated).
 // ---------------------------------------------------------------------------
+// Blocks of at least this many rows or columns run their loops on OpenMP threads.
+constexpr int kParallelEig = 256;
+
 bool sym_eig(int k, const double* Ain, double* w, double* Vout) {
   if (k <= 0) return true;
   // full symmetric copy from the lower triangle
@@ -115,15 +119,21 @@ bool sym_eig(int k, const double* Ain, double* w, double* Vout) {
     const double beta = 2.0 / vtv;
     e[j] = -sgn * nrm;
     // p = beta * A22 v ; q = p - (beta/2)(p.v) v ; A22 -= v q^T + q v^T
-    double pv = 0.0;
+    // (the loops over independent rows or columns run on host threads for large blocks;
+    // nothing is reduced across threads, so the result does not depend on their number)
+#pragma omp parallel for schedule(static) if (m >= kParallelEig)
     for (int r = 0; r < m; ++r) {
+      // row r of the trailing block read down its column (the block stays exactly
+      // symmetric: both triangles get the same rank-2 update)
       double s = 0.0;
-      for (int c = 0; c < m; ++c) s += a(j + 1 + r, j + 1 + c) * v[c];
+      for (int c = 0; c < m; ++c) s += a(j + 1 + c, j + 1 + r) * v[c];
       p[r] = beta * s;
-      pv += p[r] * v[r];
     }
+    double pv = 0.0;
+    for (int r = 0; r < m; ++r) pv += p[r] * v[r];
     const double K = 0.5 * beta * pv;
     for (int r = 0; r < m; ++r) q[r] = p[r] - K * v[r];
+#pragma omp parallel for schedule(static) if (m >= kParallelEig)
     for (int c = 0; c < m; ++c)
       for (int r = 0; r < m; ++r) a(j + 1 + r, j + 1 + c) -= v[r] * q[c] + q[r] * v[c];
     hv.push_back(std::move(v));
@@ -140,6 +150,7 @@ bool sym_eig(int k, const double* Ain, double* w, double* Vout) {
     if (hbeta[j] == 0.0) continue;
     const std::vector<double>& v = hv[j];
     const int m = k - j - 1;
+#pragma omp parallel for schedule(static) if (m >= kParallelEig)
     for (int c = j + 1; c < k; ++c) {
       double s = 0.0;
       for (int r = 0; r < m; ++r) s += v[r] * z(j + 1 + r, c);
@@ -148,7 +159,30 @@ bool sym_eig(int k, const double* Ain, double* w, double* Vout) {
     }
   }
 
-  // implicit QR on the tridiagonal (d, e), e[i] couples i and i+1
+  // implicit QR on the tridiagonal (d, e), e[i] couples i and i+1. The rotations of each
+  // sweep are recorded and applied to the eigenvector matrix Z in batches of sweeps, its
+  // rows in blocks of 32 over host threads for large k: every row sees the same rotations in
+  // the same order as a row-by-row application, so the result does not depend on the split.
+  struct Rot {
+    int i;
+    double c, s;
+  };
+  std::vector<Rot> rots;
+  auto apply_rots = [&]() {
+    if (rots.empty()) return;
+#pragma omp parallel for schedule(static) if (k >= kParallelEig)
+    for (int r0 = 0; r0 < k; r0 += 32) {
+      const int r1 = std::min(k, r0 + 32);
+      for (const Rot& q : rots)
+        for (int row = r0; row < r1; ++row) {
+          const double zi = z(row, q.i), zi1 = z(row, q.i + 1);
+          z(row, q.i) = q.c * zi - q.s * zi1;
+          z(row, q.i + 1) = q.s * zi + q.c * zi1;
+        }
+    }
+    rots.clear();
+  };
+  const size_t batch = static_cast<size_t>(std::max(64, 8 * k));  // rotations per application
   const double eps = std::numeric_limits<double>::epsilon();
   int hi = k - 1;
   int iters = 0;
@@ -190,13 +224,11 @@ bool sym_eig(int k, const double* Ain, double* w, double* Vout) {
         x = e[i];
         zz = bulge;
       }
-      for (int row = 0; row < k; ++row) {
-        const double zi = z(row, i), zi1 = z(row, i + 1);
-        z(row, i) = c * zi - s * zi1;
-        z(row, i + 1) = s * zi + c * zi1;
-      }
+      rots.push_back({i, c, s});
     }
+    if (rots.size() >= batch) apply_rots();
   }
+  apply_rots();
   // sort ascending
   std::vector<int> order(k);
   std::iota(order.begin(), order.end(), 0);
