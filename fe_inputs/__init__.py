@@ -308,7 +308,8 @@ class Workload:
     check_every: int = 5
     tol: float = 0.0              # acceptance; 0: 1e-8 (fp64) / 1e-5 (fp32)
     tts_kmax: int = 0             # Krylov dimension at which the FP64 solve accepts every distinct
-                                  # eigenvalue of the interval at 1e-8 (0: not measured)
+                                  # eigenvalue of the interval at 1e-8, and so does the next
+                                  # larger one in steps of 10 (0: not measured)
 
     def mesh_intervals(self, p: Problem):
         return self.intervals(p) if self.intervals else [(self.omega_min, self.omega_max)]
@@ -346,7 +347,7 @@ WORKLOADS = {
                            24.0, 28.0, L=600, kmax=60, tts_kmax=210),
     # 3D unit cube, Kuhn tets, 128^3 cells (2,048,383 dofs)
     "cube128_fp64": Workload("cube128_fp64", lambda: box_grid((128, 128, 128)),
-                             40.0, 45.0, L=600, kmax=60, tts_kmax=250),
+                             40.0, 45.0, L=600, kmax=60, tts_kmax=260),
     "cube128_fp32": Workload("cube128_fp32", lambda: box_grid((128, 128, 128)),
                              40.0, 45.0, L=600, kmax=60, precision="fp32"),
     # 12 uneven boxes in one context, blocks of 8 start vectors, 4 intervals per mesh

@@ -193,6 +193,31 @@ def test_fp32_solve_with_fp64_refinement_reaches_fp64_residuals(b, refine_L):
 
 
 
+def test_large_krylov_dimension_projects_and_certifies():
+    # 800 basis vectors: the projection kernels then hold more than 48 KB of Ritz
+    # coefficients per block (k x 8 doubles) and take the opted-in shared memory; the solve
+    # must still return exact eigenvalues with host-verified residuals, and a Krylov
+    # dimension beyond the kernels' limit is refused
+    p = box_grid((21, 17, 15), extent=(1.0, 0.85, 0.75))      # 4,480 dofs
+    S = p.to_scipy()
+    tau = _tau(p)
+    R = start_vectors(p.n, 8, 41)
+    exact = spectra.eigenvalues_in(p.cells, p.h, 10.0, 14.0)
+    so = K.kes_solve_opts_default()
+    so.kmax, so.tol, so.check_every, so.want_vectors = 800, 1e-8, 800, 1
+    with K.Context(p, precision="fp64", block_b=8) as c:
+        K.kes_set_filter(c.handle, 10.0, 14.0, tau, 40)
+        res = K.kes_block_krylov_solve(c.handle, R, 8, so)[0]
+        so.kmax = 4000
+        with pytest.raises(K.KesError) as e:
+            K.kes_block_krylov_solve(c.handle, R, 8, so)
+        assert e.value.status == -8
+    assert res["k_used"] > 768 and res["n_pairs"] > 0
+    for th, x in zip(res["omega2"], res["vectors"]):
+        assert np.min(np.abs(exact - th)) <= 1e-10 * th
+        assert np.linalg.norm(S @ x - th * p.m * x) <= 1.01e-8 * th * np.linalg.norm(p.m * x)
+
+
 @pytest.mark.parametrize("extra", [0, 6])
 def test_refinement_with_a_buffer_matches_oracle(extra):
     # FP64 block solve, then one refinement sweep over the in-interval Ritz vectors and

@@ -102,7 +102,7 @@ def test_filter_elementwise_parity_full_size(cube, precision):
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_krylov_solve_full_size_ritz_pairs_obey_the_residual_bound(cube, precision):
     """The benchmarked solve (Krylov dimension 60): with 83 distinct eigenvalues in the
-    interval it accepts none yet (the converged solve below runs to 250 vectors), so the
+    interval it accepts none yet (the converged solve below runs to 260 vectors), so the
     check here is on every Ritz pair in the interval, converged or not."""
     p, v0, w_gpu = cube
     tau = WL.cfl * 2 / w_gpu
