@@ -120,6 +120,25 @@ __device__ __forceinline__ void store_row(double* p, const double (&v)[NB]) {
   for (int q = 0; q < NB / 2; ++q) reinterpret_cast<double2*>(p)[q] = make_double2(v[2 * q], v[2 * q + 1]);
 }
 
+// One row's NB values read again through an opaque (volatile) load: the accumulation of a
+// step re-reads u_{n-1} and u_n after the row sums instead of keeping them in registers
+// across the gather loop (the compiler may not merge it with the first read). The rows were
+// read a moment before and are normally still in L1 or L2.
+template <int NB>
+__device__ __forceinline__ void reload_row(const float* p, float (&v)[NB]) {
+  if constexpr (NB == 8) {
+    load_plain<8>(p, v);  // a volatile 256-bit load already
+  } else {
+#pragma unroll
+    for (int q = 0; q < NB; ++q) asm volatile("ld.global.f32 %0, [%1];" : "=f"(v[q]) : "l"(p + q) : "memory");
+  }
+}
+template <int NB>
+__device__ __forceinline__ void reload_row(const double* p, double (&v)[NB]) {
+#pragma unroll
+  for (int q = 0; q < NB; ++q) asm volatile("ld.global.f64 %0, [%1];" : "=d"(v[q]) : "l"(p + q) : "memory");
+}
+
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
   s = __fadd_rn(a, b);
   const float bp = __fsub_rn(s, a);
@@ -202,17 +221,27 @@ __device__ __forceinline__ void row_sums_pipe(T (&un)[NH], const T* __restrict__
 // which halves the registers a thread needs for its columns. Either way every column is
 // the same FMA chain in entry order, so the shapes round identically. PB > 0 pipelines the
 // matrix stream PB entries ahead (row_sums_pipe); PB = 0 loads entries in pairs.
-template <typename T, int NB, bool FIRST, bool LAST, int MINB, bool PF, int LPR, int PB>
+//
+// Accumulation (eq. disc_filtercoeff): a step holds u_{n-1}, u_n and u_{n+1} of its rows in
+// registers, so the weighted terms need not reach the accumulators every step. With ACC the
+// step adds the last nterm (1-3) of alpha_{n-1} u_{n-1}, alpha_n u_n, alpha_{n+1} u_{n+1}, in
+// that order (init: the accumulator starts at the first of them, FP64 form); without ACC it
+// leaves the accumulator rows alone. The host runs the accumulation every third step and at
+// the last: each term is still added once, in index order, with the same operations, so the
+// sums are bitwise those of one term per step, and the accumulator rows (for 8 FP32 columns
+// 128 of the step's ~320 bytes per row) move every third step only.
+template <typename T, int NB, bool FIRST, bool LAST, bool ACC, int MINB, bool PF, int LPR, int PB>
 __global__ void __launch_bounds__(256, MINB)
     k_step_blk(SellDev A, const T* __restrict__ x, const T* __restrict__ g, const T* prev, T* out, T* acc_s,
                T* acc_c, double* acc64, int64_t acc_stride, int F, const T* __restrict__ ahi,
-               const T* __restrict__ alo, int Lp1, int step, int cpt, int* flag) {
+               const T* __restrict__ alo, int Lp1, int step, int cpt, int nterm, int init, int* flag) {
   // cpt == 0: every column accumulates with all F weight tables (F accumulators);
   // cpt > 0: column j accumulates only with table min(j / cpt, F - 1) (one accumulator)
   constexpr bool kF32 = std::is_same<T, float>::value;
   constexpr int NH = NB / LPR;            // columns of this lane
   constexpr int kRows = kSliceC / LPR;    // rows of a warp's unit
   static_assert(LPR == 1 || !PF, "the L2 prefetch shapes take whole slices");
+  static_assert(ACC || !LAST, "the last step completes the sums");
   const T* val;
   if constexpr (kF32) val = A.val32;
   else val = A.val64;
@@ -221,10 +250,11 @@ __global__ void __launch_bounds__(256, MINB)
   const int co = (lane % LPR) * NH;       // first column of this lane
   const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
   const int64_t n_units = A.n_slices * LPR;
-  // PF: L2 prefetch of a slice's streamed lines (column indices, values, u_{n-1} and
-  // accumulator rows), the warp's first slice up front and each next slice while the
-  // current one is gathered, so that the dependent index -> gather -> FMA chain meets
-  // L2 instead of HBM latency. Every address lies inside the slice's own entries/rows.
+  // PF: L2 prefetch of a slice's streamed lines (column indices, values, u_{n-1} and, when
+  // this step reads them, the accumulator rows), the warp's first slice up front and each
+  // next slice while the current one is gathered, so that the dependent index -> gather ->
+  // FMA chain meets L2 instead of HBM latency. Every address lies inside the slice's own
+  // entries/rows.
   const int nacc = cpt ? 1 : F;
   auto prefetch_slice = [&](int64_t sn) {
     if (sn >= A.n_slices) return;
@@ -238,7 +268,7 @@ __global__ void __launch_bounds__(256, MINB)
     if (lane < kRowLines) {
       const int64_t off = sn * kSliceC * NB + lane * (128 / static_cast<int>(sizeof(T)));
       if (!FIRST) prefetch_l2(prev + off);
-      if (kF32 || !FIRST)
+      if (ACC && !init)
         for (int f = 0; f < nacc; ++f) {
           prefetch_l2(acc_s + f * acc_stride + off);
           if (kF32) prefetch_l2(acc_c + f * acc_stride + off);
@@ -279,73 +309,88 @@ __global__ void __launch_bounds__(256, MINB)
       if (A.dcol) row_sums<T, NB, NH>(un, vp, A.dcol + beg + rs, static_cast<int>(row), w, g, co);
       else row_sums<T, NB, NH>(un, vp, A.col + beg + rs, 0, w, g, co);
     }
-    if (!LAST) store_row<NH>(out + ro, un);
-    bool bad = false;
-    for (int f = 0; f < nacc; ++f) {
-      const int64_t at = f * acc_stride + ro;
-      // this step's weights per column (the start weight alpha_0 too on the first step)
-      T ah[NH], al[NH], a0[NH];
-      if (cpt) {
+    if constexpr (!ACC) store_row<NH>(out + ro, un);
+    if constexpr (ACC) {
+      bool bad = false;
+      const int tf = static_cast<int>(mesh) * F;
+      for (int f = 0; f < nacc; ++f) {
+        const int64_t at = f * acc_stride + ro;
+        // term t = 0, 1, 2 is alpha_m u_m, m = step - 1 + t, with u_{n-1}, u_n read again
+        // (not kept in registers across the gather loop) and u_{n+1} from the row sums;
+        // column j's weight comes from its table (cpt > 0: the column's; padding columns
+        // take the last one). One term at a time, so that only one term's weights are live.
+        auto term_row = [&](int t, T (&uu)[NH]) {
+          if (t == 0) {
+            if constexpr (FIRST) reload_row<NH>(x + ro, uu);
+            else reload_row<NH>(prev + ro, uu);
+          } else if (t == 1) {
+            reload_row<NH>(x + ro, uu);
+          } else {
 #pragma unroll
-        for (int j = 0; j < NH; ++j) {
-          const int64_t ai = (mesh * F + min((co + j) / cpt, F - 1)) * Lp1;  // padding columns: last table
-          ah[j] = ahi[ai + step + 1];
-          if constexpr (kF32) al[j] = alo[ai + step + 1];
-          if constexpr (FIRST && !kF32) a0[j] = ahi[ai];
-        }
-      } else {
-        const int64_t ai = (mesh * F + f) * Lp1;
-        const T h = ahi[ai + step + 1];
-        T l = T(0), z = T(0);
-        if constexpr (kF32) l = alo[ai + step + 1];
-        if constexpr (FIRST && !kF32) z = ahi[ai];
+            for (int j = 0; j < NH; ++j) uu[j] = un[j];
+          }
+        };
+        auto weight_at = [&](int j, int m) { return (tf + (cpt ? min((co + j) / cpt, F - 1) : f)) * Lp1 + m; };
+        if constexpr (kF32) {
+          float as[NH], ac[NH];
+          load_plain<NH>(acc_s + at, as);
+          load_plain<NH>(acc_c + at, ac);
+          // (s, c) += alpha_m u_m with alpha_m = hi + lo: the sum's rounding error (Knuth's
+          // two-sum), the product's (an FMA) and the low weight's term go to c
+#pragma unroll 1
+          for (int t = 3 - nterm; t < 3; ++t) {
+            float uu[NH];
+            term_row(t, uu);
 #pragma unroll
-        for (int j = 0; j < NH; ++j) {
-          ah[j] = h;
-          al[j] = l;
-          a0[j] = z;
+            for (int j = 0; j < NH; ++j) {
+              const int ai = weight_at(j, step - 1 + t);
+              const float h = ahi[ai], l = alo[ai];
+              const float p = __fmul_rn(h, uu[j]);
+              const float pe = fmaf(l, uu[j], fmaf(h, uu[j], -p));
+              float sn, e;
+              two_sum(as[j], p, sn, e);
+              ac[j] = __fadd_rn(ac[j], __fadd_rn(e, pe));
+              as[j] = sn;
+            }
+          }
+          if constexpr (LAST) {
+            double v64[NH];
+#pragma unroll
+            for (int j = 0; j < NH; ++j) {
+              v64[j] = static_cast<double>(as[j]) + static_cast<double>(ac[j]);
+              bad |= !isfinite(v64[j]);
+            }
+            store_row<NH>(acc64 + at, v64);
+          } else {
+            store_row<NH>(acc_s + at, as);
+            store_row<NH>(acc_c + at, ac);
+          }
+        } else {
+          double na[NH];
+          const int t0 = 3 - nterm;
+          if (!init) load_plain<NH>(acc_s + at, na);
+#pragma unroll 1
+          for (int t = t0; t < 3; ++t) {
+            double uu[NH];
+            term_row(t, uu);
+            const bool fresh = init && t == t0;  // the accumulator starts at its first term's product
+#pragma unroll
+            for (int j = 0; j < NH; ++j) {
+              const double h = ahi[weight_at(j, step - 1 + t)];
+              na[j] = fresh ? h * uu[j] : fma(h, uu[j], na[j]);
+            }
+          }
+          if constexpr (LAST) {
+#pragma unroll
+            for (int j = 0; j < NH; ++j) bad |= !isfinite(na[j]);
+          }
+          store_row<NH>(acc_s + at, na);
         }
       }
-      if constexpr (kF32) {
-        float as[NH], ac[NH];
-        load_plain<NH>(acc_s + at, as);
-        load_plain<NH>(acc_c + at, ac);
-        double v64[NH];
-#pragma unroll
-        for (int j = 0; j < NH; ++j) {
-          const float p = __fmul_rn(ah[j], un[j]);
-          const float pe = fmaf(al[j], un[j], fmaf(ah[j], un[j], -p));
-          float sn, e;
-          two_sum(as[j], p, sn, e);
-          const float cn = __fadd_rn(ac[j], __fadd_rn(e, pe));
-          as[j] = sn;
-          ac[j] = cn;
-          v64[j] = static_cast<double>(sn) + static_cast<double>(cn);
-          if (LAST) bad |= !isfinite(v64[j]);
-        }
-        if (LAST) {
-          store_row<NH>(acc64 + at, v64);
-        } else {
-          store_row<NH>(acc_s + at, as);
-          store_row<NH>(acc_c + at, ac);
-        }
-      } else {
-        double na[NH];
-        if constexpr (FIRST) {
-#pragma unroll
-          for (int j = 0; j < NH; ++j) na[j] = a0[j] * xi[j];
-        } else {
-          load_plain<NH>(acc_s + at, na);
-        }
-#pragma unroll
-        for (int j = 0; j < NH; ++j) {
-          na[j] = fma(ah[j], un[j], na[j]);
-          if (LAST) bad |= !isfinite(na[j]);
-        }
-        store_row<NH>(acc_s + at, na);
-      }
+      // after every read of u_{n-1}: out may share its storage
+      if constexpr (!LAST) store_row<NH>(out + ro, un);
+      if (LAST && bad) atomicOr(flag, 1);
     }
-    if (LAST && bad) atomicOr(flag, 1);
   }
 }
 
@@ -364,19 +409,23 @@ __global__ void __launch_bounds__(256, MINB)
 template <typename T, int NB, int MINB, bool PF, int LPR, int PB>
 void blk_impl(int grid, int block, cudaStream_t st, bool first, bool last, const SellDev& A, const T* x,
               const T* g, const T* prev, T* out, T* acc_s, T* acc_c, double* acc64, int64_t acc_stride, int F, const T* ahi,
-              const T* alo, int Lp1, int step, int cpt, int* flag) {
-#define KES_BLK_ARGS A, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, F, ahi, alo, Lp1, step, cpt, flag
-  if (first && last) k_step_blk<T, NB, true, true, MINB, PF, LPR, PB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
-  else if (first) k_step_blk<T, NB, true, false, MINB, PF, LPR, PB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
-  else if (last) k_step_blk<T, NB, false, true, MINB, PF, LPR, PB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
-  else k_step_blk<T, NB, false, false, MINB, PF, LPR, PB><<<grid, block, 0, st>>>(KES_BLK_ARGS);
+              const T* alo, int Lp1, int step, int cpt, int nterm, int init, int* flag) {
+#define KES_BLK_ARGS A, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, F, ahi, alo, Lp1, step, cpt, nterm, init, flag
+#define KES_BLK(FI, LA, AC) k_step_blk<T, NB, FI, LA, AC, MINB, PF, LPR, PB><<<grid, block, 0, st>>>(KES_BLK_ARGS)
+  if (first && last) KES_BLK(true, true, true);
+  else if (last) KES_BLK(false, true, true);
+  else if (first && nterm) KES_BLK(true, false, true);
+  else if (first) KES_BLK(true, false, false);
+  else if (nterm) KES_BLK(false, false, true);
+  else KES_BLK(false, false, false);
+#undef KES_BLK
 #undef KES_BLK_ARGS
 }
 
 template <typename T>
 void blk_dispatch(const LaunchCfg& cfg, int NB, cudaStream_t st, bool first, bool last, const SellDev& A,
                   const T* x, const T* g, const T* prev, T* out, T* acc_s, T* acc_c, double* acc64, int64_t acc_stride, int F,
-                  const T* ahi, const T* alo, int Lp1, int step, int cpt, int* flag) {
+                  const T* ahi, const T* alo, int Lp1, int step, int cpt, int nterm, int init, int* flag) {
   // a block of 256 threads is 8 warps; a warp takes a slice (or half a slice, LPR = 2)
   int lpr = 1;
 #define X(ID, M, P, R, B) \
@@ -387,7 +436,7 @@ void blk_dispatch(const LaunchCfg& cfg, int NB, cudaStream_t st, bool first, boo
   const int grid = static_cast<int>(need < cfg.grid_blk ? need : cfg.grid_blk);
 #define KES_CALL(NBV, M, P, R, B)                                                                             \
   blk_impl<T, NBV, M, P, R, B>(grid, 256, st, first, last, A, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, F, \
-                               ahi, alo, Lp1, step, cpt, flag)
+                               ahi, alo, Lp1, step, cpt, nterm, init, flag)
 #define X(ID, M, P, R, B)                         \
   case ID:                                        \
     if (NB == 2) KES_CALL(2, M, P, R, B);         \
@@ -450,7 +499,7 @@ void stage4_dispatch(const SellDev& A, int n_sm, cudaStream_t st, int NB, const 
 template <typename T, int NB, int M, bool P, int R, int B>
 int occ_one(int block) {
   int nb = 0;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_blk<T, NB, false, false, M, P, R, B>, block, 0) ==
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_blk<T, NB, false, false, true, M, P, R, B>, block, 0) ==
                  cudaSuccess
              ? nb
              : 0;
@@ -538,18 +587,19 @@ int blk_blocks_per_sm(bool fp32, int NB, int variant, int block) {
 
 void launch_step_blk_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, int NB, bool first, bool last,
                          const double* x, const double* g, const double* prev, double* out, double* acc,
-                         int64_t acc_stride, int F, const double* alpha, int L, int step, int cpt, int* flag) {
+                         int64_t acc_stride, int F, const double* alpha, int L, int step, int cpt, int nterm,
+                         bool init, int* flag) {
   blk_dispatch<double>(cfg, NB, st, first, last, A, x, g, prev, out, acc, nullptr, nullptr, acc_stride, F, alpha,
-                       nullptr, L + 1, step, cpt, flag);
+                       nullptr, L + 1, step, cpt, nterm, init ? 1 : 0, flag);
   ++g_launches;
 }
 
 void launch_step_blk_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, int NB, bool first, bool last,
                          const float* x, const float* g, const float* prev, float* out, float* acc_s, float* acc_c,
                          double* acc64, int64_t acc_stride, int F, const float* alpha_hi, const float* alpha_lo,
-                         int L, int step, int cpt, int* flag) {
+                         int L, int step, int cpt, int nterm, int* flag) {
   blk_dispatch<float>(cfg, NB, st, first, last, A, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, F, alpha_hi,
-                      alpha_lo, L + 1, step, cpt, flag);
+                      alpha_lo, L + 1, step, cpt, nterm, 0, flag);
   ++g_launches;
 }
 

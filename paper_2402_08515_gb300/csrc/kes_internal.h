@@ -105,14 +105,30 @@ void launch_init_f32(cudaStream_t st, const SellDev& A, int nb, const double* r6
 // (row i's NB values contiguous). Same arithmetic per column as the single-vector
 // kernels; acc_stride = n_pad * NB elements per accumulator set. cpt = 0: every column
 // accumulates with all F weight tables; cpt > 0: column j only with table j / cpt (the
-// columns of several intervals share the matrix stream).
+// columns of several intervals share the matrix stream). nterm = 0: the step leaves the
+// accumulators alone; 1-3: it adds the last nterm of alpha_{s-1} u_{s-1}, alpha_s u_s,
+// alpha_{s+1} u_{s+1} in that order (step s computes u_{s+1}; the last step needs
+// nterm >= 1). init (FP64): the accumulator starts at the first of them (the FP32 form's
+// accumulators start from launch_init_f32). acc_plan gives the schedule.
 void launch_step_blk_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, int NB, bool first, bool last,
                          const double* x, const double* g, const double* prev, double* out, double* acc,
-                         int64_t acc_stride, int F, const double* alpha, int L, int step, int cpt, int* flag);
+                         int64_t acc_stride, int F, const double* alpha, int L, int step, int cpt, int nterm,
+                         bool init, int* flag);
 void launch_step_blk_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, int NB, bool first, bool last,
                          const float* x, const float* g, const float* prev, float* out, float* acc_s, float* acc_c,
                          double* acc64, int64_t acc_stride, int F, const float* alpha_hi, const float* alpha_lo,
-                         int L, int step, int cpt, int* flag);
+                         int L, int step, int cpt, int nterm, int* flag);
+// Accumulation schedule of a filter application of `steps` block steps: the weighted terms
+// reach the accumulators every third step and at the last. next is the index of the first
+// term not yet added (0 for the FP64 form, 1 for the FP32 form, whose initialisation adds
+// alpha_0 u_0); returns the step's nterm and advances next.
+inline int acc_plan(int s, int steps, int& next, bool& init) {
+  const int pending = s + 2 - next;  // terms u_next .. u_{s+1}
+  if (pending < 3 && s != steps - 1) return 0;
+  init = next == 0;
+  next = s + 2;
+  return pending;
+}
 // Stage of the fourth-order modified-equation leapfrog: v = x + A x / 12 over NB row-major
 // columns (NB in {1, 2, 4, 8}; n_pad x NB).
 void launch_stage4_f64(const SellDev& A, int n_sm, cudaStream_t st, int NB, const double* x, double* v);

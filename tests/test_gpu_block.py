@@ -59,6 +59,29 @@ def test_block_columns_equal_single_vector_runs(meshes):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("L", [1, 2, 3, 4, 5, 7, 30])
+def test_block_accumulation_schedule_equals_single_vector_runs(meshes, precision, L):
+    # the block kernels add the weighted terms every third step and at the last, the
+    # single-vector kernels every step: the same terms in the same order with the same
+    # operations, so every column of every weight table agrees bit for bit at any length
+    p = meshes[2]
+    tau = _tau(p)
+    R = start_vectors(p.n, 4, 5 + L)
+    with K.Context(p, precision=precision, block_b=4) as c:
+        K.kes_set_filters(c.handle, [8.0, 14.0], [12.0, 18.0], tau, L)
+        blk = np.zeros((2, 4, p.n))
+        K.kes_filter_apply(c.handle, R, blk, 4)
+        for j in range(4):
+            one = np.zeros((2, 1, p.n))
+            K.kes_filter_apply(c.handle, R[j:j + 1], one, 1)
+            np.testing.assert_array_equal(one[:, 0], blk[:, j])
+        cols = np.zeros((4, p.n))                  # columns 0-1 with table 0, 2-3 with table 1
+        K.kes_filter_apply_columns(c.handle, R, cols, 4)
+    np.testing.assert_array_equal(cols[:2], blk[0, :2])
+    np.testing.assert_array_equal(cols[2:], blk[1, 2:])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("b", [2, 4, 8])
 def test_every_block_launch_shape_rounds_identically(meshes, precision, b):
     # lane-per-row and two-lanes-per-row shapes, with and without L2 prefetch: every
