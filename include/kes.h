@@ -261,9 +261,9 @@ void kes_launch_shapes(int32_t* n_step, int32_t* n_block);
    and F intervals (every matrix entry, row pointer and per-row vector read or written once; an
    entry is its value plus a 2-byte column difference when the compact index is in use, else a
    4-byte column; the fourth-order stepper adds its stage pass and the read of the stage). The
-   block form (b >= 2) adds the weighted terms of eq. (disc_filtercoeff) to its accumulators every
-   third step and at the last (a step holds u_{n-1}, u_n, u_{n+1}), so the accumulator bytes count
-   with that share of a filter application of the context's filter length L (the average step). */
+   step kernels add the weighted terms of eq. (disc_filtercoeff) to their accumulators every third
+   step and at the last (a step holds u_{n-1}, u_n, u_{n+1}), so the accumulator bytes count with
+   that share of a filter application of the context's filter length L (the average step). */
 int64_t kes_step_bytes(const kes_ctx* ctx, int32_t b, int32_t F);
 
 /*

@@ -121,12 +121,19 @@ __device__ __forceinline__ T row_dot_pairs(T acc, const typename Pair2<T>::type*
 // 2 u_n of eq. 2stepmethod folded into the diagonal; only for the leapfrog, where g = x) and
 // the row seeds with -u_{n-1} alone: one FP64 operation less per row. The pair values are
 // built only in that form, so IDX 2 implies it.
-template <bool FIRST, bool LAST, int BATCH, int MINB, int IDX>
+//
+// Accumulation: with ACC the step adds the last nterm (1-3) of alpha_{n-1} u_{n-1},
+// alpha_n u_n, alpha_{n+1} u_{n+1} (all three are in registers) in that order, the first of
+// them as a product when init (the accumulator's first terms); without ACC it leaves the
+// accumulators alone. The host runs the accumulation every third step and at the last, so
+// every term is added once, in index order, with the operations of adding one per step.
+template <bool FIRST, bool LAST, bool ACC, int BATCH, int MINB, int IDX>
 __global__ void __launch_bounds__(256, MINB) k_step_f64(SellDev A, const double* __restrict__ x,
                                                   const double* __restrict__ g, const double* prev,
                                                   double* out, double* acc, int64_t acc_stride, int F,
                                                   const double* __restrict__ alpha, int Lp1, int step,
-                                                  int* flag) {
+                                                  int nterm, int init, int* flag) {
+  static_assert(ACC || !LAST, "the last step completes the sums");
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
   for (int64_t s = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; s < A.n_slices;
@@ -150,16 +157,25 @@ __global__ void __launch_bounds__(256, MINB) k_step_f64(SellDev A, const double*
       un = row_dot<double, BATCH>(seed, A.val64 + beg + lane, A.col + beg + lane, 0, w, g);
     }
     if (!LAST) out[row] = un;
-    bool bad = false;
-    for (int f = 0; f < F; ++f) {
-      const double* al = alpha + (mesh * F + f) * Lp1;
-      double* a = acc + f * acc_stride + row;
-      const double prev_acc = FIRST ? al[0] * xi : *a;
-      const double na = fma(al[step + 1], un, prev_acc);
-      *a = na;
-      if (LAST) bad |= !isfinite(na);
+    if constexpr (ACC) {
+      bool bad = false;
+      const int t0 = 3 - nterm;  // term t is alpha_m u_m, m = step - 1 + t
+      for (int f = 0; f < F; ++f) {
+        const int64_t ab = (mesh * F + f) * Lp1 + step - 1;
+        double* a = acc + f * acc_stride + row;
+        double na = init ? 0.0 : *a;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+          if (t < t0) continue;
+          const double u = t == 0 ? pi : (t == 1 ? xi : un);
+          const double h = alpha[ab + t];
+          na = (init && t == t0) ? h * u : fma(h, u, na);
+        }
+        *a = na;
+        if (LAST) bad |= !isfinite(na);
+      }
+      if (LAST && bad) atomicOr(flag, 1);
     }
-    if (LAST && bad) atomicOr(flag, 1);
   }
 }
 
@@ -172,13 +188,15 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
 }
 
 // IDX: 0 int32 columns, 1 the compact 16-bit differences, 2 the pair layout.
-template <bool FIRST, bool LAST, int BATCH, int MINB, int IDX>
+// ACC and nterm as in k_step_f64 (the accumulators start from k_init_f32).
+template <bool FIRST, bool LAST, bool ACC, int BATCH, int MINB, int IDX>
 __global__ void __launch_bounds__(256, MINB) k_step_f32(SellDev A, const float* __restrict__ x,
                                                   const float* __restrict__ g, const float* prev,
                                                   float* out, float* acc_s, float* acc_c, double* acc64,
                                                   int64_t acc_stride, int F, const float* __restrict__ ahi,
                                                   const float* __restrict__ alo, int Lp1, int step,
-                                                  int* flag) {
+                                                  int nterm, int* flag) {
+  static_assert(ACC || !LAST, "the last step completes the sums");
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
   for (int64_t s = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; s < A.n_slices;
@@ -202,27 +220,37 @@ __global__ void __launch_bounds__(256, MINB) k_step_f32(SellDev A, const float* 
       un = row_dot<float, BATCH>(seed, A.val32 + beg + lane, A.col + beg + lane, 0, w, g);
     }
     if (!LAST) out[row] = un;
-    bool bad = false;
-    for (int f = 0; f < F; ++f) {
-      const int64_t ai = (mesh * F + f) * Lp1 + step + 1;
-      const float a_hi = ahi[ai], a_lo = alo[ai];
-      const int64_t at = f * acc_stride + row;
-      // alpha * un = p + pe, p = fl(a_hi * un), pe = (a_hi * un - p) + a_lo * un
-      const float p = __fmul_rn(a_hi, un);
-      const float pe = fmaf(a_lo, un, fmaf(a_hi, un, -p));
-      float sn, e;
-      two_sum(acc_s[at], p, sn, e);
-      const float cn = __fadd_rn(acc_c[at], __fadd_rn(e, pe));
-      if (LAST) {
-        const double v = static_cast<double>(sn) + static_cast<double>(cn);
-        acc64[at] = v;
-        bad |= !isfinite(v);
-      } else {
-        acc_s[at] = sn;
-        acc_c[at] = cn;
+    if constexpr (ACC) {
+      bool bad = false;
+      const int t0 = 3 - nterm;  // term t is alpha_m u_m, m = step - 1 + t
+      for (int f = 0; f < F; ++f) {
+        const int64_t ab = (mesh * F + f) * Lp1 + step - 1;
+        const int64_t at = f * acc_stride + row;
+        float sa = acc_s[at], ca = acc_c[at];
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+          if (t < t0) continue;
+          const float u = t == 0 ? pi : (t == 1 ? xi : un);
+          const float a_hi = ahi[ab + t], a_lo = alo[ab + t];
+          // alpha * u = p + pe, p = fl(a_hi * u), pe = (a_hi * u - p) + a_lo * u
+          const float p = __fmul_rn(a_hi, u);
+          const float pe = fmaf(a_lo, u, fmaf(a_hi, u, -p));
+          float sn, e;
+          two_sum(sa, p, sn, e);
+          ca = __fadd_rn(ca, __fadd_rn(e, pe));
+          sa = sn;
+        }
+        if (LAST) {
+          const double v = static_cast<double>(sa) + static_cast<double>(ca);
+          acc64[at] = v;
+          bad |= !isfinite(v);
+        } else {
+          acc_s[at] = sa;
+          acc_c[at] = ca;
+        }
       }
+      if (LAST && bad) atomicOr(flag, 1);
     }
-    if (LAST && bad) atomicOr(flag, 1);
   }
 }
 
@@ -313,16 +341,26 @@ int grid_for(const LaunchCfg& cfg, int64_t n_slices) {
 #define KES_STEP_VARIANTS(X) \
   X(0, 8, 1) X(1, 8, 3) X(2, 8, 4) X(3, 4, 4) X(4, 4, 5) X(5, 4, 6) X(6, 2, 6) X(7, 2, 8)
 
+// first / last / accumulating forms of one instantiation (the first step accumulates only
+// when it is the last as well: it holds at most two of the pending terms)
+#define KES_STEP_FORMS(KERNEL, I, ARGS)                                                                   \
+  if (last) {                                                                                             \
+    if (first) KERNEL<true, true, true, BATCH, MINB, I><<<grid, block, 0, st>>>(ARGS);                    \
+    else KERNEL<false, true, true, BATCH, MINB, I><<<grid, block, 0, st>>>(ARGS);                         \
+  } else if (first) {                                                                                     \
+    KERNEL<true, false, false, BATCH, MINB, I><<<grid, block, 0, st>>>(ARGS);                             \
+  } else if (nterm) {                                                                                     \
+    KERNEL<false, false, true, BATCH, MINB, I><<<grid, block, 0, st>>>(ARGS);                             \
+  } else {                                                                                                \
+    KERNEL<false, false, false, BATCH, MINB, I><<<grid, block, 0, st>>>(ARGS);                            \
+  }
+
 template <int BATCH, int MINB>
 void step_f64_impl(int grid, int block, cudaStream_t st, bool first, bool last, const SellDev& A, const double* x,
                    const double* g, const double* prev, double* out, double* acc, int64_t acc_stride, int F, const double* alpha,
-                   int Lp1, int step, int* flag) {
-#define KES_F64_ARGS A, x, g, prev, out, acc, acc_stride, F, alpha, Lp1, step, flag
-#define KES_F64_LAUNCH(I)                                                                        \
-  if (first && last) k_step_f64<true, true, BATCH, MINB, I><<<grid, block, 0, st>>>(KES_F64_ARGS);    \
-  else if (first) k_step_f64<true, false, BATCH, MINB, I><<<grid, block, 0, st>>>(KES_F64_ARGS);      \
-  else if (last) k_step_f64<false, true, BATCH, MINB, I><<<grid, block, 0, st>>>(KES_F64_ARGS);       \
-  else k_step_f64<false, false, BATCH, MINB, I><<<grid, block, 0, st>>>(KES_F64_ARGS);
+                   int Lp1, int step, int nterm, int init, int* flag) {
+#define KES_F64_ARGS A, x, g, prev, out, acc, acc_stride, F, alpha, Lp1, step, nterm, init, flag
+#define KES_F64_LAUNCH(I) KES_STEP_FORMS(k_step_f64, I, KES_F64_ARGS)
   if (A.val64p && A.fold2) {  // the pair form seeds with -u_{n-1}: the values must hold A + 2I
     KES_F64_LAUNCH(2)
   } else if (A.dcol) {
@@ -337,13 +375,9 @@ void step_f64_impl(int grid, int block, cudaStream_t st, bool first, bool last, 
 template <int BATCH, int MINB>
 void step_f32_impl(int grid, int block, cudaStream_t st, bool first, bool last, const SellDev& A, const float* x,
                    const float* g, const float* prev, float* out, float* acc_s, float* acc_c, double* acc64, int64_t acc_stride,
-                   int F, const float* ahi, const float* alo, int Lp1, int step, int* flag) {
-#define KES_F32_ARGS A, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, F, ahi, alo, Lp1, step, flag
-#define KES_F32_LAUNCH(I)                                                                        \
-  if (first && last) k_step_f32<true, true, BATCH, MINB, I><<<grid, block, 0, st>>>(KES_F32_ARGS);    \
-  else if (first) k_step_f32<true, false, BATCH, MINB, I><<<grid, block, 0, st>>>(KES_F32_ARGS);      \
-  else if (last) k_step_f32<false, true, BATCH, MINB, I><<<grid, block, 0, st>>>(KES_F32_ARGS);       \
-  else k_step_f32<false, false, BATCH, MINB, I><<<grid, block, 0, st>>>(KES_F32_ARGS);
+                   int F, const float* ahi, const float* alo, int Lp1, int step, int nterm, int* flag) {
+#define KES_F32_ARGS A, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, F, ahi, alo, Lp1, step, nterm, flag
+#define KES_F32_LAUNCH(I) KES_STEP_FORMS(k_step_f32, I, KES_F32_ARGS)
   if (A.val32p) {
     KES_F32_LAUNCH(2)
   } else if (A.dcol) {
@@ -354,6 +388,7 @@ void step_f32_impl(int grid, int block, cudaStream_t st, bool first, bool last, 
 #undef KES_F32_LAUNCH
 #undef KES_F32_ARGS
 }
+#undef KES_STEP_FORMS
 
 }  // namespace
 
@@ -371,8 +406,8 @@ int step_blocks_per_sm(bool fp32, int variant, int block) {
   switch (variant) {
 #define X(ID, B, M)                                                                                      \
   case ID:                                                                                               \
-    e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_f32<false, false, B, M, 2>, block, 0) \
-             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_f64<false, false, B, M, 2>, block, 0); \
+    e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_f32<false, false, true, B, M, 2>, block, 0) \
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_f64<false, false, true, B, M, 2>, block, 0); \
     break;
     KES_STEP_VARIANTS(X)
 #undef X
@@ -383,13 +418,13 @@ int step_blocks_per_sm(bool fp32, int variant, int block) {
 
 void launch_step_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bool first, const double* x,
                      const double* g, const double* prev, double* out, double* acc, int64_t acc_stride, int F,
-                     const double* alpha, int L, int step, bool last, int* flag) {
+                     const double* alpha, int L, int step, bool last, int nterm, bool init, int* flag) {
   const int grid = grid_for(cfg, A.n_slices);
   switch (cfg.variant) {
 #define X(ID, B, M)                                                                                        \
   case ID:                                                                                                 \
     step_f64_impl<B, M>(grid, cfg.block_step, st, first, last, A, x, g, prev, out, acc, acc_stride, F,     \
-                        alpha, L + 1, step, flag);                                                         \
+                        alpha, L + 1, step, nterm, init ? 1 : 0, flag);                                    \
     break;
     KES_STEP_VARIANTS(X)
 #undef X
@@ -401,13 +436,13 @@ void launch_step_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bo
 void launch_step_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bool first, bool last, const float* x,
                      const float* g, const float* prev, float* out, float* acc_s, float* acc_c, double* acc64,
                      int64_t acc_stride, int F, const float* alpha_hi, const float* alpha_lo, int L, int step,
-                     int* flag) {
+                     int nterm, int* flag) {
   const int grid = grid_for(cfg, A.n_slices);
   switch (cfg.variant) {
 #define X(ID, B, M)                                                                                        \
   case ID:                                                                                                 \
     step_f32_impl<B, M>(grid, cfg.block_step, st, first, last, A, x, g, prev, out, acc_s, acc_c, acc64,     \
-                        acc_stride, F, alpha_hi, alpha_lo, L + 1, step, flag);                             \
+                        acc_stride, F, alpha_hi, alpha_lo, L + 1, step, nterm, flag);                      \
     break;
     KES_STEP_VARIANTS(X)
 #undef X

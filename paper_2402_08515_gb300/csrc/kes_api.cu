@@ -87,7 +87,7 @@ int64_t issue_filter_steps(kes_ctx* c, int NB, bool fp64, int cpt, int steps) {
       cfg.variant = 3;
       cfg.grid_step = cfg.n_sm * step_blocks_per_sm(false, 3, cfg.block_step);
     }
-    int next = 0;  // first weighted term not yet in the block accumulators
+    int next = 0;  // first weighted term not yet in the accumulators
     for (int s = 0; s < steps; ++s) {
       const bool first = s == 0, last = s == steps - 1;
       const double* x = s == 0 ? c->stage_in : c->U64[(s - 1) & 1];
@@ -98,12 +98,12 @@ int64_t issue_filter_steps(kes_ctx* c, int NB, bool fp64, int cpt, int steps) {
         launch_stage4_f64(A64, cfg.n_sm, c->stream, NB, x, c->V64);
         g = c->V64;
       }
-      if (NB == 1)
+      bool init = false;
+      const int nterm = acc_plan(s, steps, next, init);
+      if (NB == 1) {
         launch_step_f64(A64, cfg, c->stream, first, x, g, prev, out, c->stage_out, stride, F, c->alpha64, L, s,
-                        last, c->d_flag);
-      else {
-        bool init = false;
-        const int nterm = acc_plan(s, steps, next, init);
+                        last, nterm, init, c->d_flag);
+      } else {
         launch_step_blk_f64(A64, cfg, c->stream, NB, first, last, x, g, prev, out, c->stage_out, stride, F,
                             c->alpha64, L, s, cpt, nterm, init, c->d_flag);
       }
@@ -122,12 +122,12 @@ int64_t issue_filter_steps(kes_ctx* c, int NB, bool fp64, int cpt, int steps) {
         launch_stage4_f32(A32, c->cfg.n_sm, c->stream, NB, x, c->V32);
         g = c->V32;
       }
-      if (NB == 1)
+      bool init = false;
+      const int nterm = acc_plan(s, steps, next, init);
+      if (NB == 1) {
         launch_step_f32(A32, c->cfg, c->stream, first, last, x, g, prev, out, c->acc_s, c->acc_c, c->stage_out,
-                        stride, F, c->alpha_hi, c->alpha_lo, L, s, c->d_flag);
-      else {
-        bool init = false;
-        const int nterm = acc_plan(s, steps, next, init);
+                        stride, F, c->alpha_hi, c->alpha_lo, L, s, nterm, c->d_flag);
+      } else {
         launch_step_blk_f32(A32, c->cfg, c->stream, NB, first, last, x, g, prev, out, c->acc_s, c->acc_c,
                             c->stage_out, stride, F, c->alpha_hi, c->alpha_lo, L, s, cpt, nterm, c->d_flag);
       }
@@ -300,19 +300,21 @@ void tune_steps(kes_ctx* c) {
     KES_CHECK_LAUNCH();
     return best;
   };
-  // single-vector kernel
+  // single-vector kernel, over the middle steps of a filter application: two that leave
+  // the accumulators alone, one that adds three terms
   int best = 0;
   float best_ms = 3.0e38f;
   for (int v = 0; v < step_variant_count(); ++v) {
     select_variant(c, v);
     const float ms = timed([&](int count) {
       for (int i = 0; i < count; ++i) {
+        const int nterm = i % 3 == 2 ? 3 : 0;
         if (fp32)
           launch_step_f32(c->step_A32(), c->cfg, c->stream, false, false, c->U32[0], c->U32[0], c->U32[1], c->U32[1],
-                          c->acc_s, c->acc_c, c->stage_out, c->n_pad, 1, a32, a32, 7, 1, c->d_flag);
+                          c->acc_s, c->acc_c, c->stage_out, c->n_pad, 1, a32, a32, 7, 1, nterm, c->d_flag);
         else
           launch_step_f64(c->step_A64(), c->cfg, c->stream, false, c->U64[0], c->U64[0], c->U64[1], c->U64[1],
-                          c->stage_out, c->n_pad, 1, a64, 7, 1, false, c->d_flag);
+                          c->stage_out, c->n_pad, 1, a64, 7, 1, false, nterm, false, c->d_flag);
       }
     });
     if (ms < best_ms) {
@@ -819,14 +821,14 @@ int64_t kes_step_bytes(const kes_ctx* c, int32_t b, int32_t F) {
   // The fourth-order stepper adds a stage pass (matrix and row pointers again, u_n gathered,
   // the stage written) and the step reads the stage (gathered) besides u_n. With the
   // compact index a stored entry's column takes 2 bytes instead of 4.
-  // The block kernels (b >= 2) read and write the accumulators only in the steps that add
-  // the weighted terms (every third step and the last, acc_plan): their 16 F bytes count with
-  // that share of a filter application of the context's L steps.
+  // The step kernels read and write the accumulators only in the steps that add the weighted
+  // terms (every third step and the last, acc_plan): their 16 F bytes count with that share of
+  // a filter application of the context's L steps.
   const int64_t vs = c->opts.precision == KES_PREC_FP64 ? 8 : 4;
   const int64_t is = c->A.dcol ? 2 : 4;
   const int64_t mat = (vs + is) * c->nnz + 4 * (c->n + 1);
   int64_t acc = c->n * int64_t(b) * 16 * F;
-  if (b >= 2 && c->L > 0) {
+  if (c->L > 0) {
     int next = vs == 8 ? 0 : 1, n_acc = 0;
     bool init = false;
     for (int s = 0; s < c->L; ++s) n_acc += acc_plan(s, c->L, next, init) > 0;

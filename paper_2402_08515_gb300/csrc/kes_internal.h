@@ -83,18 +83,19 @@ struct LaunchCfg {
 // first: prev = x and acc_f = alpha_f[0] * x + alpha_f[1] * out.
 // x, prev, out, acc: length n_pad; acc_f at acc + f * acc_stride; alpha of mesh m, table f at
 // alpha + (m * F + f) * (L+1). last: the state of the final step is not stored;
-// flag[0] |= 1 if any acc entry is not finite.
+// flag[0] |= 1 if any acc entry is not finite. nterm / init: the accumulation of this step
+// (acc_plan; the last step needs nterm >= 1).
 void launch_step_f64(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bool first,
                      const double* x, const double* g, const double* prev, double* out,
                      double* acc, int64_t acc_stride, int F, const double* alpha, int L, int step,
-                     bool last, int* flag);
+                     bool last, int nterm, bool init, int* flag);
 
 // FP32 form: values/state FP32, accumulator as an unevaluated FP32 sum (s + c) kept by
 // error-free transformations; alpha as FP32 pairs (hi + lo). last: writes acc64 = s + c in FP64.
 void launch_step_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, bool first, bool last,
                      const float* x, const float* g, const float* prev, float* out, float* acc_s,
                      float* acc_c, double* acc64, int64_t acc_stride, int F, const float* alpha_hi,
-                     const float* alpha_lo, int L, int step, int* flag);
+                     const float* alpha_lo, int L, int step, int nterm, int* flag);
 // FP32 start over n_pad x nb row-major values: x32 = (float) r64; s_f = fl(alpha_f[0] r),
 // c_f = alpha_f[0] r - s_f (rounded), with the weight table of each row's mesh (cpt > 0:
 // column j has one accumulator, with table j / cpt).
@@ -118,8 +119,8 @@ void launch_step_blk_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st
                          const float* x, const float* g, const float* prev, float* out, float* acc_s, float* acc_c,
                          double* acc64, int64_t acc_stride, int F, const float* alpha_hi, const float* alpha_lo,
                          int L, int step, int cpt, int nterm, int* flag);
-// Accumulation schedule of a filter application of `steps` block steps: the weighted terms
-// reach the accumulators every third step and at the last. next is the index of the first
+// Accumulation schedule of a filter application of `steps` fused steps (single-vector and
+// block kernels): the weighted terms reach the accumulators every third step and at the last. next is the index of the first
 // term not yet added (0 for the FP64 form, 1 for the FP32 form, whose initialisation adds
 // alpha_0 u_0); returns the step's nterm and advances next.
 inline int acc_plan(int s, int steps, int& next, bool& init) {
