@@ -256,6 +256,11 @@ __global__ void __launch_bounds__(256, MINB)
   // FMA chain meets L2 instead of HBM latency. Every address lies inside the slice's own
   // entries/rows.
   const int nacc = cpt ? 1 : F;
+  // cpt > 0: the weight table of each of this lane's columns, 4 bits each (cpt > 0 means
+  // at most one table per column, so F <= NB <= 8), computed once instead of per row
+  uint32_t col_tab = 0;
+  if (cpt)
+    for (int j = 0; j < NH; ++j) col_tab |= static_cast<uint32_t>(min((co + j) / cpt, F - 1)) << (4 * j);
   auto prefetch_slice = [&](int64_t sn) {
     if (sn >= A.n_slices) return;
     const int64_t bn = A.slice_ptr[sn];
@@ -330,7 +335,9 @@ __global__ void __launch_bounds__(256, MINB)
             for (int j = 0; j < NH; ++j) uu[j] = un[j];
           }
         };
-        auto weight_at = [&](int j, int m) { return (tf + (cpt ? min((co + j) / cpt, F - 1) : f)) * Lp1 + m; };
+        // table of column j; the columns of one table are contiguous, so a term's weights are
+        // loaded once per table the lane's columns meet (once when cpt == 0)
+        auto table_of = [&](int j) { return cpt ? static_cast<int>((col_tab >> (4 * j)) & 15u) : f; };
         if constexpr (kF32) {
           float as[NH], ac[NH];
           load_plain<NH>(acc_s + at, as);
@@ -341,10 +348,16 @@ __global__ void __launch_bounds__(256, MINB)
           for (int t = 3 - nterm; t < 3; ++t) {
             float uu[NH];
             term_row(t, uu);
+            int tb = -1;
+            float h = 0.f, l = 0.f;
 #pragma unroll
             for (int j = 0; j < NH; ++j) {
-              const int ai = weight_at(j, step - 1 + t);
-              const float h = ahi[ai], l = alo[ai];
+              if (table_of(j) != tb) {
+                tb = table_of(j);
+                const int ai = (tf + tb) * Lp1 + step - 1 + t;
+                h = ahi[ai];
+                l = alo[ai];
+              }
               const float p = __fmul_rn(h, uu[j]);
               const float pe = fmaf(l, uu[j], fmaf(h, uu[j], -p));
               float sn, e;
@@ -374,9 +387,14 @@ __global__ void __launch_bounds__(256, MINB)
             double uu[NH];
             term_row(t, uu);
             const bool fresh = init && t == t0;  // the accumulator starts at its first term's product
+            int tb = -1;
+            double h = 0.0;
 #pragma unroll
             for (int j = 0; j < NH; ++j) {
-              const double h = ahi[weight_at(j, step - 1 + t)];
+              if (table_of(j) != tb) {
+                tb = table_of(j);
+                h = ahi[(tf + tb) * Lp1 + step - 1 + t];
+              }
               na[j] = fresh ? h * uu[j] : fma(h, uu[j], na[j]);
             }
           }
