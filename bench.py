@@ -784,6 +784,7 @@ TTS_FORMS = (
     ("fp32_b8+refine1", "fp32", 8, 1, 1.0, 0),
     ("fp32_b8+refine1+16", "fp32", 8, 1, 1.0, 16),
     ("fp32_b8+refine1_L/2", "fp32", 8, 1, 0.5, 0),
+    ("fp32_b8+refine1_L/2+16", "fp32", 8, 1, 0.5, 16),
 )
 # coarse Krylov dimensions of the search (single vector, block of 8) and the final resolution
 TTS_GRID = {1: (160, 200, 240, 280, 320, 360, 400), 8: (512, 640, 768, 896, 1024, 1152)}

@@ -10,6 +10,7 @@
 // same order as the single-vector kernel forms it.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "kes_internal.h"
@@ -234,7 +235,8 @@ template <typename T, int NB, bool FIRST, bool LAST, bool ACC, int MINB, bool PF
 __global__ void __launch_bounds__(256, MINB)
     k_step_blk(SellDev A, const T* __restrict__ x, const T* __restrict__ g, const T* prev, T* out, T* acc_s,
                T* acc_c, double* acc64, int64_t acc_stride, int F, const T* __restrict__ ahi,
-               const T* __restrict__ alo, int Lp1, int step, int cpt, int nterm, int init, int* flag) {
+               const T* __restrict__ alo, int Lp1, int step, int cpt, uint32_t coltab, int nterm, int init,
+               int* flag) {
   // cpt == 0: every column accumulates with all F weight tables (F accumulators);
   // cpt > 0: column j accumulates only with table min(j / cpt, F - 1) (one accumulator)
   constexpr bool kF32 = std::is_same<T, float>::value;
@@ -256,11 +258,6 @@ __global__ void __launch_bounds__(256, MINB)
   // FMA chain meets L2 instead of HBM latency. Every address lies inside the slice's own
   // entries/rows.
   const int nacc = cpt ? 1 : F;
-  // cpt > 0: the weight table of each of this lane's columns, 4 bits each (cpt > 0 means
-  // at most one table per column, so F <= NB <= 8), computed once instead of per row
-  uint32_t col_tab = 0;
-  if (cpt)
-    for (int j = 0; j < NH; ++j) col_tab |= static_cast<uint32_t>(min((co + j) / cpt, F - 1)) << (4 * j);
   auto prefetch_slice = [&](int64_t sn) {
     if (sn >= A.n_slices) return;
     const int64_t bn = A.slice_ptr[sn];
@@ -337,7 +334,7 @@ __global__ void __launch_bounds__(256, MINB)
         };
         // table of column j; the columns of one table are contiguous, so a term's weights are
         // loaded once per table the lane's columns meet (once when cpt == 0)
-        auto table_of = [&](int j) { return cpt ? static_cast<int>((col_tab >> (4 * j)) & 15u) : f; };
+        auto table_of = [&](int j) { return cpt ? static_cast<int>((coltab >> (4 * (co + j))) & 15u) : f; };
         if constexpr (kF32) {
           float as[NH], ac[NH];
           load_plain<NH>(acc_s + at, as);
@@ -427,8 +424,9 @@ __global__ void __launch_bounds__(256, MINB)
 template <typename T, int NB, int MINB, bool PF, int LPR, int PB>
 void blk_impl(int grid, int block, cudaStream_t st, bool first, bool last, const SellDev& A, const T* x,
               const T* g, const T* prev, T* out, T* acc_s, T* acc_c, double* acc64, int64_t acc_stride, int F, const T* ahi,
-              const T* alo, int Lp1, int step, int cpt, int nterm, int init, int* flag) {
-#define KES_BLK_ARGS A, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, F, ahi, alo, Lp1, step, cpt, nterm, init, flag
+              const T* alo, int Lp1, int step, int cpt, uint32_t coltab, int nterm, int init, int* flag) {
+#define KES_BLK_ARGS \
+  A, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, F, ahi, alo, Lp1, step, cpt, coltab, nterm, init, flag
 #define KES_BLK(FI, LA, AC) k_step_blk<T, NB, FI, LA, AC, MINB, PF, LPR, PB><<<grid, block, 0, st>>>(KES_BLK_ARGS)
   if (first && last) KES_BLK(true, true, true);
   else if (last) KES_BLK(false, true, true);
@@ -444,6 +442,11 @@ template <typename T>
 void blk_dispatch(const LaunchCfg& cfg, int NB, cudaStream_t st, bool first, bool last, const SellDev& A,
                   const T* x, const T* g, const T* prev, T* out, T* acc_s, T* acc_c, double* acc64, int64_t acc_stride, int F,
                   const T* ahi, const T* alo, int Lp1, int step, int cpt, int nterm, int init, int* flag) {
+  // cpt > 0: weight table min(c / cpt, F - 1) of each column c, 4 bits per column (at most
+  // one table per column there, so F <= NB <= 8), passed as a kernel parameter
+  uint32_t coltab = 0;
+  if (cpt > 0)
+    for (int c = 0; c < NB; ++c) coltab |= static_cast<uint32_t>(std::min(c / cpt, F - 1)) << (4 * c);
   // a block of 256 threads is 8 warps; a warp takes a slice (or half a slice, LPR = 2)
   int lpr = 1;
 #define X(ID, M, P, R, B) \
@@ -454,7 +457,7 @@ void blk_dispatch(const LaunchCfg& cfg, int NB, cudaStream_t st, bool first, boo
   const int grid = static_cast<int>(need < cfg.grid_blk ? need : cfg.grid_blk);
 #define KES_CALL(NBV, M, P, R, B)                                                                             \
   blk_impl<T, NBV, M, P, R, B>(grid, 256, st, first, last, A, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, F, \
-                               ahi, alo, Lp1, step, cpt, nterm, init, flag)
+                               ahi, alo, Lp1, step, cpt, coltab, nterm, init, flag)
 #define X(ID, M, P, R, B)                         \
   case ID:                                        \
     if (NB == 2) KES_CALL(2, M, P, R, B);         \
