@@ -191,7 +191,14 @@ def load_peak():
 
 
 def kernel_source_hash(src: str = STEP_KERNEL_SRC) -> str:
-    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    """Hash of the kernel source without its // comments and blank lines: a profile
+    stays valid across comment edits and goes stale when any code changes."""
+    code = []
+    for line in open(src, encoding="utf-8").read().splitlines():
+        line = re.sub(r"//.*$", "", line).strip()
+        if line:
+            code.append(line)
+    return hashlib.sha256("\n".join(code).encode()).hexdigest()[:16]
 
 
 def profiled_traffic(workload: str, src: str = STEP_KERNEL_SRC):

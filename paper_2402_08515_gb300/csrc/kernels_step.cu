@@ -9,8 +9,9 @@
 // (lane = row); the slice's values and column indices stream from HBM in
 // 256-byte (FP64) / 128-byte (FP32) coalesced warp loads marked evict-first, u_n
 // is gathered through the read-only path (it stays L2-resident across the step),
-// and each row is one FMA chain seeded with 2 u_n - u_{n-1}, followed by the
-// weighted accumulation in registers.
+// and each row is one FMA chain seeded with 2 u_n - u_{n-1}. The weighted terms
+// alpha_f[m] u_m reach the accumulators in every third step (and the last), which
+// adds the pending ones of u_{n-1}, u_n, u_{n+1} from registers in index order.
 // No tensor cores: the step is a sparse gather, not a dense contraction.
 #include <cuda_runtime.h>
 
