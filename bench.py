@@ -72,6 +72,8 @@ def parse_args(argv=None):
     ap.add_argument("--refine-sweeps", type=int, default=0, help="FP64 refinement sweeps (--mode solve, certify)")
     ap.add_argument("--refine-extra", type=int, default=0,
                     help="buffer Ritz vectors of the refinement (--mode solve, certify)")
+    ap.add_argument("--refine-x2", action="store_true",
+                    help="refinement filter in FP32 pairs instead of FP64 (--mode solve, certify; FP32 form)")
     ap.add_argument("--precision", default="", choices=["", "fp64", "fp32"],
                     help="override the workload's precision (--mode certify)")
     ap.add_argument("--b", type=int, default=0, help="override the workload's block width (--mode certify)")
@@ -520,6 +522,7 @@ def run_kes(args):
     so = K.kes_solve_opts_default()
     so.kmax, so.tol, so.check_every = wl.kmax, args.tol or wl.acceptance(), wl.check_every
     so.refine_sweeps, so.refine_extra = args.refine_sweeps, args.refine_extra
+    so.refine_precision = K.KES_REFINE_F32X2 if args.refine_x2 else K.KES_REFINE_FP64
     R0_host = start_block(problems, b, wl.seed + 1 + 1000 * rank)
     R0_dev = torch.from_numpy(R0_host).to(dev)
     torch.cuda.synchronize()
@@ -714,6 +717,7 @@ def run_kes(args):
         "clocks": clk.summary(),
         "tts": tts,
         "solve": {"tol": so.tol, "refine_sweeps": so.refine_sweeps, "refine_extra": so.refine_extra,
+                  "refine_precision": ("fp64", "fp32x2")[so.refine_precision],
                   "accepted_pairs": [x["n_pairs"] for x in res] if batch else res[0]["n_pairs"],
                   "k_used": res[0]["k_used"], "time_steps": steps_per_solve,
                   "max_rel_res": max((float(x["rel_res"].max()) for x in res if x["n_pairs"]), default=None),
@@ -782,16 +786,19 @@ def run_reference(args):
 
 
 TTS_FORMS = (
-    # name, precision, block width, FP64 refinement sweeps, refinement filter length / L,
-    # Ritz vectors nearest outside the interval refined as a buffer
-    ("fp64", "fp64", 1, 0, 1.0, 0),
-    ("fp32+refine1", "fp32", 1, 1, 1.0, 0),
-    ("fp32+refine1_L/2", "fp32", 1, 1, 0.5, 0),
-    ("fp64_b8", "fp64", 8, 0, 1.0, 0),
-    ("fp32_b8+refine1", "fp32", 8, 1, 1.0, 0),
-    ("fp32_b8+refine1+16", "fp32", 8, 1, 1.0, 16),
-    ("fp32_b8+refine1_L/2", "fp32", 8, 1, 0.5, 0),
-    ("fp32_b8+refine1_L/2+16", "fp32", 8, 1, 0.5, 16),
+    # name, precision, block width, refinement sweeps, refinement filter length / L, Ritz
+    # vectors nearest outside the interval refined as a buffer, arithmetic of the refinement
+    # filter (0 FP64, 1 FP32 pairs: the "x2" forms)
+    ("fp64", "fp64", 1, 0, 1.0, 0, 0),
+    ("fp32+refine1", "fp32", 1, 1, 1.0, 0, 0),
+    ("fp32+refine1_L/2", "fp32", 1, 1, 0.5, 0, 0),
+    ("fp32+refine1x2_L/2", "fp32", 1, 1, 0.5, 0, 1),
+    ("fp64_b8", "fp64", 8, 0, 1.0, 0, 0),
+    ("fp32_b8+refine1", "fp32", 8, 1, 1.0, 0, 0),
+    ("fp32_b8+refine1+16", "fp32", 8, 1, 1.0, 16, 0),
+    ("fp32_b8+refine1x2+16", "fp32", 8, 1, 1.0, 16, 1),
+    ("fp32_b8+refine1_L/2", "fp32", 8, 1, 0.5, 0, 0),
+    ("fp32_b8+refine1_L/2+16", "fp32", 8, 1, 0.5, 16, 0),
 )
 # coarse Krylov dimensions of the search (single vector, block of 8) and the final resolution
 TTS_GRID = {1: (160, 200, 240, 280, 320, 360, 400), 8: (512, 640, 768, 896, 1024, 1152)}
@@ -839,7 +846,7 @@ def run_tts(args):
             distinct, _ = spectra.cluster(exact)
             v0 = start_vectors(p.n, 1, wl.seed)[0]
             runs, summary = [], {}
-            for name, prec, b, refine, frac, extra in forms:
+            for name, prec, b, refine, frac, extra, rprec in forms:
                 with K.Context(p, precision=prec, block_b=8) as c:
                     w, _ = K.kes_estimate_omega_max(c.handle, wl.power_iters, v0)
                     K.kes_set_filter(c.handle, wl.omega_min, wl.omega_max, wl.cfl * 2 / w, wl.L)
@@ -852,7 +859,7 @@ def run_tts(args):
                         so = K.kes_solve_opts_default()
                         so.kmax, so.tol, so.check_every, so.refine_sweeps = kmax, TTS_TOL, kmax, refine
                         so.refine_L = int(round(frac * wl.L)) if frac < 1.0 else 0
-                        so.refine_extra = extra
+                        so.refine_extra, so.refine_precision = extra, rprec
                         K.kes_reset_stats(c.handle)
                         torch.cuda.synchronize()
                         t0 = time.perf_counter()
@@ -862,6 +869,7 @@ def run_tts(args):
                         found, _ = spectra.cluster(res["omega2"])
                         inside = res["ritz_rel_res"][~np.isnan(res["ritz_rel_res"])]
                         rec = {"form": name, "b": b, "kmax": kmax, "refine_sweeps": refine, "refine_extra": extra,
+                               "refine_precision": ("fp64", "fp32x2")[rprec],
                                "refine_L": so.refine_L or wl.L, "seconds": dt,
                                "accepted_pairs": res["n_pairs"], "accepted_distinct": len(found),
                                "matched_with_multiplicity": matched_pairs(exact, res["omega2"]),
@@ -869,7 +877,7 @@ def run_tts(args):
                                "ritz_rel_res_median_in_interval": float(np.median(inside)) if inside.size else None,
                                "max_eig_rel_err_vs_exact": max((float(np.min(np.abs(exact - t)) / t)
                                                                 for t in res["omega2"]), default=None),
-                               "leapfrog_steps": res["time_steps"], "fp64_refine_steps": res["refine_steps"],
+                               "leapfrog_steps": res["time_steps"], "refine_steps": res["refine_steps"],
                                "filter_s": st["filter_ms"] / 1e3, "other_kernels_s": st["solve_other_ms"] / 1e3}
                         runs.append(rec)
                         print(json.dumps({"workload": wname, **rec}), file=sys.stderr, flush=True)
@@ -949,6 +957,7 @@ def run_certify(args):
         so.check_every = so.kmax
         so.refine_sweeps = args.refine_sweeps
         so.refine_extra = args.refine_extra
+        so.refine_precision = K.KES_REFINE_F32X2 if args.refine_x2 else K.KES_REFINE_FP64
         so.want_vectors = 1
         R0 = start_block(problems, b, wl.seed + 1)
         setup_s = time.perf_counter() - t_build
@@ -980,9 +989,10 @@ def run_certify(args):
                            "in_interval_ritz_values": int(inside.size),
                            "ritz_rel_res_median_in_interval": float(np.median(inside)) if inside.size else None,
                            "k_used": r["k_used"], "leapfrog_steps": r["time_steps"],
-                           "fp64_refine_steps": r["refine_steps"]})
+                           "refine_steps": r["refine_steps"]})
     print(json.dumps({"mode": "certify", "workload": args.workload, "precision": precision, "b": b, "L": L,
-                      "kmax": so.kmax, "tol": so.tol, "refine_sweeps": so.refine_sweeps, "setup_s": setup_s,
+                      "kmax": so.kmax, "tol": so.tol, "refine_sweeps": so.refine_sweeps,
+                      "refine_precision": ("fp64", "fp32x2")[so.refine_precision], "setup_s": setup_s,
                       "solve_s": solve_s, "clocks": clk.summary(), "meshes": meshes}), flush=True)
 
 

@@ -109,7 +109,21 @@ typedef struct kes_solve_opts {
                             (eq. weightf does not depend on T); 0 or >= L: L */
   int32_t refine_extra;  /* the refinement sweeps also filter this many Ritz vectors whose Ritz values lie
                             nearest outside the interval (a buffer; 0: the in-interval ones only) */
+  int32_t refine_precision; /* arithmetic of the refinement sweeps' filter (enum kes_refine_precision):
+                            KES_REFINE_FP64 (default) or KES_REFINE_F32X2; the latter in contexts of the
+                            FP32 form with the leapfrog stepper and block_b >= 2 (KES_ERR_UNSUPPORTED
+                            otherwise); contexts of the FP64 form filter in FP64 either way */
 } kes_solve_opts;
+
+/* Arithmetic of the refinement sweeps' filter steps. KES_REFINE_F32X2 keeps step values,
+   states and row sums as unevaluated sums hi + lo of two FP32 numbers (double-float
+   arithmetic: error-free products by FMA and Knuth's two-sum, a significand of about 48
+   bits) on the FP32 units, with the compensated FP32 accumulator of the FP32 form; on GB300,
+   whose FP64 units issue about two FMAs per clock per SM, it runs the block steps at the
+   memory system's rate instead of the FP64 pipe's. Its step values carry the FP64 values to
+   about 2^-48 relative, far below the level a 1e-8 residual needs (the FP32 form's floor,
+   about 2^-24 G / omega^2 with G = max_i sum_j |s_ij| / m_i, drops by 2^24). */
+enum kes_refine_precision { KES_REFINE_FP64 = 0, KES_REFINE_F32X2 = 1 };
 
 /* Result of kes_krylov_solve; host memory owned by the library. */
 typedef struct kes_result {
@@ -128,7 +142,7 @@ typedef struct kes_result {
                             intervals: each interval's projection in turn) */
   double* ritz_rel_res;  /* [n_ritz] relative residual of the in-interval ones, NaN elsewhere */
   double solve_ms;       /* wall time of the call */
-  int64_t refine_steps;  /* FP64 leapfrog steps of the refinement sweeps (per filtered block) */
+  int64_t refine_steps;  /* leapfrog steps of the refinement sweeps (per filtered block; FP64 or FP32 pairs) */
   int32_t* interval;     /* [n_pairs] the filter interval whose process found each pair (0 for one interval) */
 } kes_result;
 

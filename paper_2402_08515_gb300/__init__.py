@@ -20,7 +20,7 @@ import numpy as np
 __all__ = [
     "KesError", "KesOpts", "KesSolveOpts", "KesResult", "KesStats", "lib", "LIB_PATH",
     "KES_PREC_FP64", "KES_PREC_FP32", "KES_MEM_DEVICE", "KES_MEM_HOST", "KES_STEPPER_LEAPFROG",
-    "KES_STEPPER_LEAPFROG4",
+    "KES_STEPPER_LEAPFROG4", "KES_REFINE_FP64", "KES_REFINE_F32X2",
     "kes_opts_default", "kes_solve_opts_default", "kes_strerror", "kes_create", "kes_destroy",
     "kes_size", "kes_sync", "kes_estimate_omega_max", "kes_set_filter", "kes_set_filters",
     "kes_alpha_table", "kes_filter_response", "kes_sym_eig", "kes_step_bytes",
@@ -44,6 +44,7 @@ KES_OK, KES_INFO_INVARIANT_SUBSPACE = 0, 1
 KES_PREC_FP64, KES_PREC_FP32 = 0, 1
 KES_MEM_DEVICE, KES_MEM_HOST = 0, 1
 KES_STEPPER_LEAPFROG, KES_STEPPER_LEAPFROG4 = 0, 1
+KES_REFINE_FP64, KES_REFINE_F32X2 = 0, 1
 
 
 class KesError(RuntimeError):
@@ -67,7 +68,7 @@ class KesOpts(C.Structure):
 class KesSolveOpts(C.Structure):
     _fields_ = [("kmax", C.c_int32), ("check_every", C.c_int32), ("n_wanted", C.c_int32),
                 ("want_vectors", C.c_int32), ("tol", C.c_double), ("refine_sweeps", C.c_int32),
-                ("refine_L", C.c_int32), ("refine_extra", C.c_int32)]
+                ("refine_L", C.c_int32), ("refine_extra", C.c_int32), ("refine_precision", C.c_int32)]
 
 
 class KesResult(C.Structure):

@@ -409,6 +409,231 @@ __global__ void __launch_bounds__(256, MINB)
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Block step in FP32 pairs (double-float arithmetic): every step value, state value and
+// row sum is an unevaluated sum hi + lo of two FP32 numbers. A product a x of two pairs is
+// taken as ph = fl(a_hi x_hi) plus the error of that product (an FMA gives it exactly) and
+// the cross terms a_hi x_lo + a_lo x_hi; the row sum adds ph by Knuth's two-sum and keeps
+// the rounding errors and the small terms in a compensation word, normalised at the end of
+// the row. This carries a significand of about 48 bits with FP32 instructions only (the
+// FP64 units of GB300 issue about two FMAs per clock per SM). Same recurrence and order as
+// the other step kernels (eq. 2stepmethod; the values hold A + 2I when fold2), the weighted
+// terms added to the compensated FP32 accumulator every third step like k_step_blk.
+// Two lanes per row (LPR = 2): a lane owns NH = NB / 2 columns, a warp half a slice.
+// NH (hi, lo) pairs of one row: coherent and read-only-path loads, and the store
+template <int NH>
+__device__ __forceinline__ void load_pairs(const float2* p, float (&h)[NH], float (&l)[NH]) {
+  float v[2 * NH];
+  load_plain<2 * NH>(reinterpret_cast<const float*>(p), v);
+#pragma unroll
+  for (int j = 0; j < NH; ++j) {
+    h[j] = v[2 * j];
+    l[j] = v[2 * j + 1];
+  }
+}
+template <int NH>
+__device__ __forceinline__ void load_pairs_nc(const float2* __restrict__ p, float (&h)[NH], float (&l)[NH]) {
+  float v[2 * NH];
+  load_row<2 * NH>(reinterpret_cast<const float*>(p), v);
+#pragma unroll
+  for (int j = 0; j < NH; ++j) {
+    h[j] = v[2 * j];
+    l[j] = v[2 * j + 1];
+  }
+}
+template <int NH>
+__device__ __forceinline__ void store_pairs(float2* p, const float (&h)[NH], const float (&l)[NH]) {
+  float v[2 * NH];
+#pragma unroll
+  for (int j = 0; j < NH; ++j) {
+    v[2 * j] = h[j];
+    v[2 * j + 1] = l[j];
+  }
+  store_row<2 * NH>(reinterpret_cast<float*>(p), v);
+}
+
+// (sh, sl) += (ah + al)(xh + xl), the product's low-order terms and the sum's rounding error
+// into sl
+__device__ __forceinline__ void pair_fma(float ah, float al, float xh, float xl, float& sh, float& sl) {
+  const float ph = __fmul_rn(ah, xh);
+  float pe = fmaf(ah, xh, -ph);
+  pe = fmaf(ah, xl, pe);
+  pe = fmaf(al, xh, pe);
+  float t, e;
+  two_sum(sh, ph, t, e);
+  sh = t;
+  sl = __fadd_rn(sl, __fadd_rn(e, pe));
+}
+
+template <int NB, bool FIRST, bool LAST, bool ACC>
+__global__ void __launch_bounds__(256, 4)
+    k_step_x2(SellDev A, const float2* __restrict__ val2, const float2* __restrict__ x, const float2* prev,
+              float2* out, float* acc_s, float* acc_c, double* acc64, int64_t acc_stride, int F,
+              const float* __restrict__ ahi, const float* __restrict__ alo, int Lp1, int step, int cpt,
+              uint32_t coltab, int nterm, int* flag) {
+  constexpr int NH = NB / 2;              // columns of this lane
+  static_assert(ACC || !LAST, "the last step completes the sums");
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / 2;               // row within the half slice
+  const int co = (lane % 2) * NH;         // first column of this lane
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  const int64_t n_units = A.n_slices * 2;
+  const int nacc = cpt ? 1 : F;
+  for (int64_t u = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; u < n_units; u += nwarps) {
+    const int64_t s = u / 2;
+    const int rs = static_cast<int>(u % 2) * 16 + sub;  // row within the slice
+    const int64_t beg = A.slice_ptr[s];
+    const int w = static_cast<int>((A.slice_ptr[s + 1] - beg) >> 5);
+    const int64_t mesh = A.slice_mesh ? A.slice_mesh[s] : 0;
+    const int64_t row = s * kSliceC + rs;
+    const int64_t ro = row * NB + co;
+    float sh[NH], sl[NH];
+    {
+      float xh[NH], xl[NH], ph[NH], pl[NH];
+      load_pairs<NH>(x + ro, xh, xl);
+      if constexpr (FIRST) {
+#pragma unroll
+        for (int j = 0; j < NH; ++j) {
+          ph[j] = xh[j];
+          pl[j] = xl[j];
+        }
+      } else {
+        load_pairs<NH>(prev + ro, ph, pl);
+      }
+      // seed: -u_{n-1} when the values hold A + 2I, else 2 u_n - u_{n-1} (2 x is exact)
+#pragma unroll
+      for (int j = 0; j < NH; ++j) {
+        if (A.fold2) {
+          sh[j] = -ph[j];
+          sl[j] = -pl[j];
+        } else {
+          float t, e;
+          two_sum(__fmul_rn(2.0f, xh[j]), -ph[j], t, e);
+          sh[j] = t;
+          sl[j] = __fadd_rn(e, __fsub_rn(__fmul_rn(2.0f, xl[j]), pl[j]));
+        }
+      }
+    }
+    // the row's entries in order, two at a time
+    const float2* vp = val2 + beg + rs;
+    const int base = A.dcol ? static_cast<int>(row) : 0;
+    int k = 0;
+    for (; k + 2 <= w; k += 2) {
+      const int32_t c0 = base + (A.dcol ? ld_idx(A.dcol + beg + rs + k * kSliceC) : ld_idx(A.col + beg + rs + k * kSliceC));
+      const int32_t c1 = base + (A.dcol ? ld_idx(A.dcol + beg + rs + (k + 1) * kSliceC)
+                                        : ld_idx(A.col + beg + rs + (k + 1) * kSliceC));
+      const float2 v0 = __ldcs(vp + k * kSliceC), v1 = __ldcs(vp + (k + 1) * kSliceC);
+      float h0[NH], l0[NH], h1[NH], l1[NH];
+      load_pairs_nc<NH>(x + static_cast<int64_t>(c0) * NB + co, h0, l0);
+      load_pairs_nc<NH>(x + static_cast<int64_t>(c1) * NB + co, h1, l1);
+#pragma unroll
+      for (int j = 0; j < NH; ++j) {
+        pair_fma(v0.x, v0.y, h0[j], l0[j], sh[j], sl[j]);
+        pair_fma(v1.x, v1.y, h1[j], l1[j], sh[j], sl[j]);
+      }
+    }
+    if (k < w) {
+      const int32_t c0 = base + (A.dcol ? ld_idx(A.dcol + beg + rs + k * kSliceC) : ld_idx(A.col + beg + rs + k * kSliceC));
+      const float2 v0 = __ldcs(vp + k * kSliceC);
+      float h0[NH], l0[NH];
+      load_pairs_nc<NH>(x + static_cast<int64_t>(c0) * NB + co, h0, l0);
+#pragma unroll
+      for (int j = 0; j < NH; ++j) pair_fma(v0.x, v0.y, h0[j], l0[j], sh[j], sl[j]);
+    }
+    // u_{n+1} normalised: hi = fl(sh + sl), lo = the rest
+    float uh[NH], ul[NH];
+#pragma unroll
+    for (int j = 0; j < NH; ++j) two_sum(sh[j], sl[j], uh[j], ul[j]);
+    if constexpr (!ACC) store_pairs<NH>(out + ro, uh, ul);
+    if constexpr (ACC) {
+      bool bad = false;
+      for (int f = 0; f < nacc; ++f) {
+        const int64_t at = f * acc_stride + ro;
+        auto table_of = [&](int j) { return cpt ? static_cast<int>((coltab >> (4 * (co + j))) & 15u) : f; };
+        float as[NH], ac[NH];
+        load_plain<NH>(acc_s + at, as);
+        load_plain<NH>(acc_c + at, ac);
+#pragma unroll 1
+        for (int t = 3 - nterm; t < 3; ++t) {
+          float th[NH], tl[NH];
+          if (t == 0) {
+            if constexpr (FIRST) load_pairs<NH>(x + ro, th, tl);
+            else load_pairs<NH>(prev + ro, th, tl);
+          } else if (t == 1) {
+            load_pairs<NH>(x + ro, th, tl);
+          } else {
+#pragma unroll
+            for (int j = 0; j < NH; ++j) {
+              th[j] = uh[j];
+              tl[j] = ul[j];
+            }
+          }
+          int tb = -1;
+          float h = 0.f, l = 0.f;
+#pragma unroll
+          for (int j = 0; j < NH; ++j) {
+            if (table_of(j) != tb) {
+              tb = table_of(j);
+              const int ai = (static_cast<int>(mesh) * F + tb) * Lp1 + step - 1 + t;
+              h = ahi[ai];
+              l = alo[ai];
+            }
+            pair_fma(h, l, th[j], tl[j], as[j], ac[j]);
+          }
+        }
+        if constexpr (LAST) {
+          double v64[NH];
+#pragma unroll
+          for (int j = 0; j < NH; ++j) {
+            v64[j] = static_cast<double>(as[j]) + static_cast<double>(ac[j]);
+            bad |= !isfinite(v64[j]);
+          }
+          store_row<NH>(acc64 + at, v64);
+        } else {
+          store_row<NH>(acc_s + at, as);
+          store_row<NH>(acc_c + at, ac);
+        }
+      }
+      // after every read of u_{n-1}: out may share its storage
+      if constexpr (!LAST) store_pairs<NH>(out + ro, uh, ul);
+      if (LAST && bad) atomicOr(flag, 1);
+    }
+  }
+}
+
+// FP32-pair start for nb columns: x2 = r split as hi + lo, and the compensated accumulators
+// set to alpha_f[0] r as k_init_f32 sets them.
+__global__ void k_init_x2(int64_t count, int nb, const double* __restrict__ r, float2* __restrict__ x2,
+                          float* __restrict__ acc_s, float* __restrict__ acc_c, int64_t acc_stride, int F,
+                          const double* __restrict__ alpha, int Lp1, const int32_t* __restrict__ slice_mesh,
+                          int cpt) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < count;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const double ri = r[i];
+    const float hi = static_cast<float>(ri);
+    x2[i] = make_float2(hi, static_cast<float>(ri - static_cast<double>(hi)));
+    const int64_t mesh = slice_mesh ? slice_mesh[(i / nb) / kSliceC] : 0;
+    const int nacc = cpt ? 1 : F;
+    for (int f = 0; f < nacc; ++f) {
+      const int table = cpt ? min(static_cast<int>(i % nb) / cpt, F - 1) : f;
+      const double t = alpha[(mesh * F + table) * Lp1] * ri;
+      const float s = static_cast<float>(t);
+      acc_s[f * acc_stride + i] = s;
+      acc_c[f * acc_stride + i] = static_cast<float>(t - static_cast<double>(s));
+    }
+  }
+}
+
+// FP64 step values split into FP32 pairs, hi = fl(v), lo = fl(v - hi)
+__global__ void k_split_values(int64_t count, const double* __restrict__ v, float2* __restrict__ v2) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < count;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const double a = v[i];
+    const float hi = static_cast<float>(a);
+    v2[i] = make_float2(hi, static_cast<float>(a - static_cast<double>(hi)));
+  }
+}
+
 // Launch shapes of the block kernels: minimum resident 256-thread blocks per SM, whether
 // the slices are prefetched into L2, lanes per row, entries of the pipelined matrix stream
 // (0: pairs, not pipelined). (Copying each slice's accumulator rows into shared memory with
@@ -621,6 +846,56 @@ void launch_step_blk_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st
                          int L, int step, int cpt, int nterm, int* flag) {
   blk_dispatch<float>(cfg, NB, st, first, last, A, x, g, prev, out, acc_s, acc_c, acc64, acc_stride, F, alpha_hi,
                       alpha_lo, L + 1, step, cpt, nterm, 0, flag);
+  ++g_launches;
+}
+
+void launch_step_x2(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, int NB, bool first, bool last,
+                    const float2* val2, const float2* x, const float2* prev, float2* out, float* acc_s, float* acc_c,
+                    double* acc64, int64_t acc_stride, int F, const float* alpha_hi, const float* alpha_lo, int L,
+                    int step, int cpt, int nterm, int* flag) {
+  uint32_t coltab = 0;
+  if (cpt > 0)
+    for (int c = 0; c < NB; ++c) coltab |= static_cast<uint32_t>(std::min(c / cpt, F - 1)) << (4 * c);
+  const int64_t need = (A.n_slices * 2 + 7) / 8;  // 8 warps per block, half a slice each
+  const int64_t cap = static_cast<int64_t>(cfg.n_sm) * 4;
+  const int grid = static_cast<int>(need < cap ? (need > 0 ? need : 1) : cap);
+#define KES_X2_ARGS A, val2, x, prev, out, acc_s, acc_c, acc64, acc_stride, F, alpha_hi, alpha_lo, L + 1, step, cpt, coltab, nterm, flag
+#define KES_X2(NBV)                                                                               \
+  if (last) {                                                                                     \
+    if (first) k_step_x2<NBV, true, true, true><<<grid, 256, 0, st>>>(KES_X2_ARGS);               \
+    else k_step_x2<NBV, false, true, true><<<grid, 256, 0, st>>>(KES_X2_ARGS);                    \
+  } else if (first) {                                                                             \
+    if (nterm) k_step_x2<NBV, true, false, true><<<grid, 256, 0, st>>>(KES_X2_ARGS);              \
+    else k_step_x2<NBV, true, false, false><<<grid, 256, 0, st>>>(KES_X2_ARGS);                   \
+  } else if (nterm) {                                                                             \
+    k_step_x2<NBV, false, false, true><<<grid, 256, 0, st>>>(KES_X2_ARGS);                        \
+  } else {                                                                                        \
+    k_step_x2<NBV, false, false, false><<<grid, 256, 0, st>>>(KES_X2_ARGS);                       \
+  }
+  if (NB == 2) {
+    KES_X2(2)
+  } else if (NB == 4) {
+    KES_X2(4)
+  } else {
+    KES_X2(8)
+  }
+#undef KES_X2
+#undef KES_X2_ARGS
+  ++g_launches;
+}
+
+void launch_init_x2(cudaStream_t st, const SellDev& A, int nb, const double* r64, float2* x2, float* acc_s,
+                    float* acc_c, int64_t acc_stride, int F, const double* alpha64, int L, int cpt) {
+  const int64_t count = A.n_pad * nb;
+  const int64_t blocks = (count + 255) / 256;
+  k_init_x2<<<static_cast<int>(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(
+      count, nb, r64, x2, acc_s, acc_c, acc_stride, F, alpha64, L + 1, A.slice_mesh, cpt);
+  ++g_launches;
+}
+
+void launch_split_values(cudaStream_t st, int64_t count, const double* v, float2* v2) {
+  const int64_t blocks = (count + 255) / 256;
+  k_split_values<<<static_cast<int>(blocks < 4096 ? (blocks > 0 ? blocks : 1) : 4096), 256, 0, st>>>(count, v, v2);
   ++g_launches;
 }
 

@@ -73,12 +73,27 @@ double cfl_bound(const kes_ctx* c) { return c->opts.stepper == KES_STEPPER_LEAPF
 // weight table; cpt > 0: one block, column j with table min(j / cpt, F - 1)). steps <= L
 // runs the first steps + 1 weights of the tables: alpha(t) of eq. (weightf) does not
 // depend on T, so that is the filter of end time steps * tau.
-int64_t issue_filter_steps(kes_ctx* c, int NB, bool fp64, int cpt, int steps) {
+int64_t issue_filter_steps(kes_ctx* c, int NB, bool fp64, int cpt, int steps, bool x2) {
   const int64_t before = g_launches;
   const bool ho = c->opts.stepper == KES_STEPPER_LEAPFROG4;
   const int L = c->L, F = c->F;  // L: the tables' length (their stride is L + 1)
   const int64_t stride = c->n_pad * NB;
-  if (fp64) {
+  if (x2) {
+    // FP32 pairs: the FP64 step values (fold64 as for the FP64 steps) split once per filter
+    const SellDev A64 = c->step_A64();
+    launch_init_x2(c->stream, c->A, NB, c->stage_in, c->U2[2], c->acc_s, c->acc_c, stride, F, c->alpha64, L, cpt);
+    int next = 1;  // the initialisation added alpha_0 u_0
+    for (int s = 0; s < steps; ++s) {
+      const bool first = s == 0, last = s == steps - 1;
+      const float2* x = s == 0 ? c->U2[2] : c->U2[(s - 1) & 1];
+      const float2* prev = s <= 1 ? c->U2[2] : c->U2[s & 1];
+      float2* out = c->U2[s & 1];
+      bool init = false;
+      const int nterm = acc_plan(s, steps, next, init);
+      launch_step_x2(A64, c->cfg, c->stream, NB, first, last, c->step2, x, prev, out, c->acc_s, c->acc_c,
+                     c->stage_out, stride, F, c->alpha_hi, c->alpha_lo, L, s, cpt, nterm, c->d_flag);
+    }
+  } else if (fp64) {
     // in a context of the FP32 form the launch shape was tuned for the FP32 kernels:
     // the FP64 steps of the refinement take a fixed register-staged shape
     const SellDev A64 = c->step_A64();
@@ -147,14 +162,31 @@ void ensure_fp64_state(kes_ctx* c) {
   }
 }
 
+// The FP32-pair steps in a context of the FP32 form: step values split from the FP64 ones
+// (again after a filter change rescaled those) and the pair state.
+void ensure_x2_state(kes_ctx* c) {
+  ensure_fp64_state(c);
+  if (!c->step2) c->step2 = c->dzero_n<float2>(c->nnz_pad);
+  if (!c->step2_fresh) {
+    launch_split_values(c->stream, c->nnz_pad, c->step64, c->step2);
+    KES_CHECK_LAUNCH();
+    c->step2_fresh = true;
+  }
+  if (!c->U2[0])
+    for (int j = 0; j < 3; ++j) c->U2[j] = c->dzero_n<float2>(c->n_pad * c->NBcap);
+}
+
 }  // namespace
 
 namespace kes {
 
-void run_filter(kes_ctx* c, int NB, bool fp64, int cpt, int steps) {
+void run_filter(kes_ctx* c, int NB, bool fp64, int cpt, int steps, bool x2) {
   if (cpt > 0 && NB < 2) throw KesError{KES_ERR_ARG};  // per-column tables live in the block kernels
+  if (x2 && (NB < 2 || c->opts.precision != KES_PREC_FP32 || c->opts.stepper != KES_STEPPER_LEAPFROG))
+    throw KesError{KES_ERR_UNSUPPORTED};
   if (steps <= 0 || steps > c->L) steps = c->L;
-  if (fp64) ensure_fp64_state(c);
+  if (x2) ensure_x2_state(c);
+  else if (fp64) ensure_fp64_state(c);
   if (c->opts.stepper == KES_STEPPER_LEAPFROG4) {  // stage buffers before any graph captures them
     if (fp64 && !c->V64) c->V64 = c->dzero_n<double>(c->n_pad * c->NBcap);
     if (!fp64 && !c->V32) c->V32 = c->dzero_n<float>(c->n_pad * c->NBcap);
@@ -169,17 +201,18 @@ void run_filter(kes_ctx* c, int NB, bool fp64, int cpt, int steps) {
     }
     GraphEntry* ge = nullptr;
     for (auto& g : c->graphs)
-      if (g.NB == NB && g.fp64 == fp64 && g.cpt == cpt && g.steps == steps) ge = &g;
+      if (g.NB == NB && g.fp64 == fp64 && g.x2 == x2 && g.cpt == cpt && g.steps == steps) ge = &g;
     if (!ge) {
       cudaGraph_t graph;
       KES_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-      const int64_t nodes = issue_filter_steps(c, NB, fp64, cpt, steps);
+      const int64_t nodes = issue_filter_steps(c, NB, fp64, cpt, steps, x2);
       cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
       g_launches -= nodes;  // captured, not launched
       KES_CUDA(ce);
       GraphEntry g;
       g.NB = NB;
       g.fp64 = fp64;
+      g.x2 = x2;
       g.cpt = cpt;
       g.steps = steps;
       g.nodes = nodes;
@@ -192,7 +225,7 @@ void run_filter(kes_ctx* c, int NB, bool fp64, int cpt, int steps) {
     KES_CUDA(cudaGraphLaunch(ge->exec, c->stream));
     g_launches += ge->nodes;  // every node of the replayed graph is a kernel launch
   } else {
-    issue_filter_steps(c, NB, fp64, cpt, steps);
+    issue_filter_steps(c, NB, fp64, cpt, steps, x2);
     KES_CHECK_LAUNCH();
   }
   KES_CUDA(cudaEventRecord(e1, c->stream));
@@ -682,6 +715,7 @@ kes_status set_weights_impl(kes_ctx* c, int32_t F, const double* alpha, const do
     if (c->step64 || c->step32)
       launch_scale_values(c->A, c->cfg, c->stream, c->tau2m64, c->step64, c->step32, c->step64p, c->step32p,
                           c->fold64);
+    c->step2_fresh = false;  // the FP32-pair values follow step64 at their next use
     KES_CHECK_LAUNCH();
     ensure_stage_out(c, F);
     c->sync();
@@ -978,7 +1012,8 @@ kes_status kes_krylov_solve(kes_ctx* c, const double* r0, int32_t mem, const kes
   if (so_in) so = *so_in;
   else kes_solve_opts_default(&so);
   if (so.kmax < 1 || so.check_every < 1 || !(so.tol > 0.0) || so.refine_sweeps < 0 || so.refine_L < 0 ||
-      so.refine_extra < 0)
+      so.refine_extra < 0 ||
+      (so.refine_precision != KES_REFINE_FP64 && so.refine_precision != KES_REFINE_F32X2))
     return KES_ERR_ARG;
   if (so.kmax > kMaxProjected) return KES_ERR_UNSUPPORTED;
   return block_solve_impl(c, r0, 1, mem, so, out);
@@ -995,7 +1030,8 @@ kes_status kes_block_krylov_solve(kes_ctx* c, const double* R0, int32_t b, int32
   if (so_in) so = *so_in;
   else kes_solve_opts_default(&so);
   if (so.kmax < b / c->F || so.check_every < 1 || !(so.tol > 0.0) || so.refine_sweeps < 0 || so.refine_L < 0 ||
-      so.refine_extra < 0)
+      so.refine_extra < 0 ||
+      (so.refine_precision != KES_REFINE_FP64 && so.refine_precision != KES_REFINE_F32X2))
     return KES_ERR_ARG;
   if (so.kmax > kMaxProjected) return KES_ERR_UNSUPPORTED;
   return block_solve_impl(c, R0, b, mem, so, out);
@@ -1010,7 +1046,8 @@ kes_status kes_subspace_solve(kes_ctx* c, const double* X0, int32_t p, int32_t m
   kes_solve_opts so;
   if (so_in) so = *so_in;
   else kes_solve_opts_default(&so);
-  if (so.kmax < p || so.refine_sweeps < 1 || !(so.tol > 0.0) || so.refine_L < 0 || so.refine_extra < 0)
+  if (so.kmax < p || so.refine_sweeps < 1 || !(so.tol > 0.0) || so.refine_L < 0 || so.refine_extra < 0 ||
+      (so.refine_precision != KES_REFINE_FP64 && so.refine_precision != KES_REFINE_F32X2))
     return KES_ERR_ARG;
   if (so.kmax > kMaxProjected) return KES_ERR_UNSUPPORTED;
   return block_solve_impl(c, nullptr, 1, mem, so, out, X0, p);

@@ -68,6 +68,7 @@ struct LaunchCount {
 struct GraphEntry {
   int NB = 0;
   bool fp64 = true;
+  bool x2 = false;
   int cpt = 0;
   int steps = 0;
   cudaGraphExec_t exec = nullptr;
@@ -129,6 +130,11 @@ struct kes_ctx {
   double* U64[2] = {nullptr, nullptr};
   float* U32[3] = {nullptr, nullptr, nullptr};
   double* V64 = nullptr;  // fourth-order stage v = u + A u / 12 (n_pad x NBcap), allocated on first use
+  // FP32-pair refinement filter (allocated on first use): step values split from step64,
+  // state ping-pong [0], [1] and start [2] (n_pad x NBcap pairs each)
+  float2* step2 = nullptr;
+  bool step2_fresh = false;  // step2 holds the current step64
+  float2* U2[3] = {nullptr, nullptr, nullptr};
   float* V32 = nullptr;
   float* acc_s = nullptr;
   float* acc_c = nullptr;
@@ -245,7 +251,8 @@ void block_out(kes_ctx* c, const double* src, int NB, int nb, double* dst, int32
 // One filter application of an NB-column block on the context stream: stage_in ->
 // stage_out (cpt = 0: F filtered blocks; cpt > 0: column j with weight table j / cpt),
 // the first `steps` steps of the installed tables (0: all L), as a CUDA graph if enabled.
-void run_filter(kes_ctx* c, int NB, bool fp64, int cpt = 0, int steps = 0);
+// x2: in FP32 pairs (FP32-form contexts, NB >= 2, leapfrog; fp64 is then ignored).
+void run_filter(kes_ctx* c, int NB, bool fp64, int cpt = 0, int steps = 0, bool x2 = false);
 // Krylov workspace for kmax basis vectors per process and F intervals per mesh.
 void ensure_krylov(kes_ctx* c, int kmax, int F);
 // Device scalars of process p (of mesh p outside the solver).

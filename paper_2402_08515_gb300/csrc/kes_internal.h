@@ -119,6 +119,19 @@ void launch_step_blk_f32(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st
                          const float* x, const float* g, const float* prev, float* out, float* acc_s, float* acc_c,
                          double* acc64, int64_t acc_stride, int F, const float* alpha_hi, const float* alpha_lo,
                          int L, int step, int cpt, int nterm, int* flag);
+// Block step in FP32 pairs (hi + lo, double-float arithmetic) for NB in {2, 4, 8} columns:
+// state rows of NB float2 (n_pad x NB row-major), step values val2 (the FP64 step values split,
+// SELL order of val64), the compensated FP32 accumulators and weights of the FP32 form;
+// nterm as for launch_step_blk_f32.
+void launch_step_x2(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, int NB, bool first, bool last,
+                    const float2* val2, const float2* x, const float2* prev, float2* out, float* acc_s, float* acc_c,
+                    double* acc64, int64_t acc_stride, int F, const float* alpha_hi, const float* alpha_lo, int L,
+                    int step, int cpt, int nterm, int* flag);
+// Start of a filter application in FP32 pairs: x2 = r64 split, accumulators as launch_init_f32.
+void launch_init_x2(cudaStream_t st, const SellDev& A, int nb, const double* r64, float2* x2, float* acc_s,
+                    float* acc_c, int64_t acc_stride, int F, const double* alpha64, int L, int cpt);
+// v2[i] = (fl(v[i]), fl(v[i] - fl(v[i]))) for count values
+void launch_split_values(cudaStream_t st, int64_t count, const double* v, float2* v2);
 // Accumulation schedule of a filter application of `steps` fused steps (single-vector and
 // block kernels): the weighted terms reach the accumulators every third step and at the last. next is the index of the first
 // term not yet added (0 for the FP64 form, 1 for the FP32 form, whose initialisation adds

@@ -445,6 +445,9 @@ void BlockSolver::refine(int32_t mem) {
   const int NBr = F_ > 1 ? NB_ : c_->NBcap;  // columns of one refinement filter call
   const int gr = F_ > 1 ? g_ : NBr;          // of them per interval
   const bool sweep_fp64 = X0_ ? c_->opts.precision == KES_PREC_FP64 : true;
+  // FP32-form contexts may take the sweeps' filter in FP32 pairs instead (same recurrence and
+  // weights, a ~48-bit significand on the FP32 units)
+  const bool sweep_x2 = so_.refine_precision == KES_REFINE_F32X2 && c_->opts.precision == KES_PREC_FP32;
   // the Ritz vectors a sweep filters: all of them (fixed-dimension mode), or those with Ritz
   // values in the interval plus the refine_extra nearest outside it (a buffer, as FEAST
   // keeps more vectors than eigenvalues wanted)
@@ -544,7 +547,7 @@ void BlockSolver::refine(int32_t mem) {
       launch_pack_basis(s_, c_->Xd, np_, c_->colsel, c_->slice_mesh, c_->stage_in, NBr, np_);
       KES_CHECK_LAUNCH();
       const int Lr = so_.refine_L > 0 && so_.refine_L < c_->L ? so_.refine_L : c_->L;
-      run_filter(c_, NBr, sweep_fp64, cpt_, Lr);
+      run_filter(c_, NBr, sweep_fp64, cpt_, Lr, sweep_x2);
       refine_steps_ += Lr;
       launch_unpack_block(s_, c_->stage_out, NBr, c_->Wc, np_);
       KES_CHECK_LAUNCH();

@@ -216,6 +216,58 @@ def test_fp32_solve_with_fp64_refinement_reaches_fp64_residuals(b, refine_L):
 
 
 
+@pytest.mark.parametrize("b,block_b,refine_L", [(1, 8, 0), (2, 2, 0), (2, 4, 100)])
+def test_fp32_pair_refinement_reaches_fp64_residuals(b, block_b, refine_L):
+    # the refinement sweep's filter in FP32 pairs (double-float arithmetic on the FP32
+    # units): the same pairs as the FP64 sweep, eigenvalues to 1e-10 of the closed form and
+    # host-computed residuals within the 1e-8 acceptance
+    p = square_grid(32)
+    S = p.to_scipy()
+    tau = _tau(p)
+    exact = spectra.eigenvalues_in(p.cells, p.h, 20.0, 30.0)
+    R = start_vectors(p.n, b, 3)
+    out = {}
+    for prec in (K.KES_REFINE_FP64, K.KES_REFINE_F32X2):
+        so = K.kes_solve_opts_default()
+        so.kmax, so.tol, so.want_vectors, so.refine_sweeps, so.refine_L = 100, 1e-8, 1, 2, refine_L
+        so.refine_precision = prec
+        with K.Context(p, precision="fp32", block_b=block_b) as c:
+            K.kes_set_filter(c.handle, 20.0, 30.0, tau, 300)
+            out[prec] = K.kes_block_krylov_solve(c.handle, R, b, so)[0]
+    r64, rx2 = out[K.KES_REFINE_FP64], out[K.KES_REFINE_F32X2]
+    print(f"b={b}: FP64 sweep {r64['n_pairs']} pairs, FP32-pair sweep {rx2['n_pairs']} pairs")
+    assert rx2["refine_steps"] == r64["refine_steps"] > 0
+    assert abs(rx2["n_pairs"] - r64["n_pairs"]) <= 1 and rx2["n_pairs"] >= 1
+    for th, x in zip(rx2["omega2"], rx2["vectors"]):
+        assert np.min(np.abs(exact - th)) <= 1e-10 * th
+        r = S @ x - th * p.m * x
+        assert np.linalg.norm(r) <= 1.01e-8 * th * np.linalg.norm(p.m * x)
+    for th in rx2["omega2"]:                       # the pairs both sweeps accept agree
+        d = np.abs(r64["omega2"] - th)
+        if d.size and d.min() <= 1e-9 * th:
+            assert d.min() <= 1e-11 * th
+
+
+def test_fp32_pair_refinement_needs_a_block_context():
+    p = square_grid(16)
+    tau = _tau(p)
+    so = K.kes_solve_opts_default()
+    so.kmax, so.refine_sweeps, so.refine_precision = 20, 1, K.KES_REFINE_F32X2
+    with K.Context(p, precision="fp32", block_b=1) as c:
+        K.kes_set_filter(c.handle, 20.0, 30.0, tau, 100)
+        with pytest.raises(K.KesError) as e:
+            K.kes_block_krylov_solve(c.handle, start_vectors(p.n, 1, 1), 1, so)
+        assert e.value.status == -8
+        so.refine_precision = 7
+        with pytest.raises(K.KesError) as e:
+            K.kes_block_krylov_solve(c.handle, start_vectors(p.n, 1, 1), 1, so)
+        assert e.value.status == -1
+    with K.Context(p, precision="fp64", block_b=1) as c:   # FP64 contexts refine in FP64
+        K.kes_set_filter(c.handle, 20.0, 30.0, tau, 100)
+        so.refine_precision = K.KES_REFINE_F32X2
+        K.kes_block_krylov_solve(c.handle, start_vectors(p.n, 1, 1), 1, so)
+
+
 def test_large_krylov_dimension_projects_and_certifies():
     # 800 basis vectors: the projection kernels then hold more than 48 KB of Ritz
     # coefficients per block (k x 8 doubles) and take the opted-in shared memory; the solve
