@@ -54,6 +54,8 @@ def parse_args(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--tts-repeats", type=int, default=3, help="timed converged solves of the tts field")
     ap.add_argument("--no-tts", action="store_true", help="leave out the converged solve (tts, and e2e through it)")
+    ap.add_argument("--no-precision-compare", action="store_true",
+                    help="leave out the FP32-form against FP64 time to converged pairs (box2m)")
     ap.add_argument("--no-batch-filter", action="store_true", help="leave out the 12-mesh batched filter measurement")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle samples (1 core + all cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -417,6 +419,61 @@ def start_block(problems, b, seed):
 
 # ----------------------------------------------------------------------------- kes arm
 
+def precision_comparison(dev, stream) -> dict:
+    """The FP32 form against plain FP64, time to every eigenpair of an interval at
+    rel_res <= 1e-8 on a workload whose interval holds simple eigenvalues (box2m, [24, 28],
+    81 of them): the FP64 single-vector solve at its Krylov dimension, and the FP32 solve
+    followed by one refinement sweep of half length in FP32 pairs over its in-interval Ritz
+    vectors (8 columns per SpMM step), each one solve on a fresh context with the input
+    resident, CUDA events on the library stream around the synchronous call. The Krylov
+    dimensions are those of `--mode tts` (the smallest that accept all 81, to within 10)."""
+    import numpy as np
+    import torch
+
+    import paper_2402_08515_gb300 as K
+    from fe_inputs import WORKLOADS, start_vectors
+    from fe_inputs import spectra
+    wl = WORKLOADS["box2m_fp64"]
+    p = wl.build()
+    exact = spectra.omega2_in(p.cells, p.h, wl.omega_min, wl.omega_max)
+    distinct, _ = spectra.cluster(exact)
+    v0 = start_vectors(p.n, 1, wl.seed)[0]
+    r0 = torch.from_numpy(start_vectors(p.n, 1, wl.seed + 1)[0]).to(dev)
+    forms = (("fp64", "fp64", 1, wl.tts_kmax, 0, 0, K.KES_REFINE_FP64),
+             ("fp32+refine1x2_L/2", "fp32", 8, 240, 1, wl.L // 2, K.KES_REFINE_F32X2))
+    out = {"workload": "box2m_fp64", "dofs": p.n, "interval": [wl.omega_min, wl.omega_max], "L": wl.L,
+           "tol": TTS_TOL, "distinct_in_interval": len(distinct), "forms": {}}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index or 0) as clk:
+        for name, prec, bb, kmax, sweeps, refine_L, rprec in forms:
+            with K.Context(p, precision=prec, stream=stream, block_b=bb) as ctx:
+                h = ctx.handle
+                w, _ = K.kes_estimate_omega_max(h, wl.power_iters, v0)
+                K.kes_set_filter(h, wl.omega_min, wl.omega_max, wl.cfl * 2 / w, wl.L)
+                so = K.kes_solve_opts_default()
+                so.kmax, so.tol, so.check_every = kmax, TTS_TOL, kmax
+                so.refine_sweeps, so.refine_L, so.refine_precision = sweeps, refine_L, rprec
+                torch.cuda.synchronize()
+                with torch.cuda.stream(stream):
+                    e0.record(stream)
+                    res = K.kes_krylov_solve(h, r0, so)
+                    e1.record(stream)
+                torch.cuda.synchronize()
+                found, _ = spectra.cluster(res["omega2"])
+                out["forms"][name] = {
+                    "seconds": e0.elapsed_time(e1) / 1e3, "kmax": kmax, "refine_sweeps": sweeps,
+                    "refine_L": refine_L, "refine_precision": ("fp64", "fp32x2")[rprec],
+                    "accepted_pairs": res["n_pairs"], "accepted_distinct": len(found),
+                    "all_distinct_found": len(found) >= len(distinct),
+                    "max_rel_res": float(res["rel_res"].max()) if res["n_pairs"] else None,
+                    "max_eig_rel_err_vs_exact": max((float(np.min(np.abs(exact - t)) / t) for t in res["omega2"]),
+                                                    default=None)}
+    f64, f32 = out["forms"]["fp64"], out["forms"]["fp32+refine1x2_L/2"]
+    out["fp64_over_fp32_time"] = f64["seconds"] / f32["seconds"]
+    out["clocks"] = clk.summary()
+    return out
+
+
 def batch_filter_measurement(dev, stream, reps: int = 3) -> dict:
     """The batched SpMM step on the 12-mesh batch (3.14 M dofs, 8 FP32 columns per mesh, one
     interval per mesh; and the four intervals of every mesh from one trajectory): one filter
@@ -686,6 +743,11 @@ def run_kes(args):
     if args.workload == "cube128_fp64" and not args.no_batch_filter:
         batch_filter = batch_filter_measurement(dev, stream)
 
+    # the FP32 form against plain FP64 to converged pairs at 1e-8 (simple eigenvalues)
+    prec_cmp = None
+    if args.workload == "cube128_fp64" and not args.no_precision_compare:
+        prec_cmp = precision_comparison(dev, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         big = max(range(len(problems)), key=lambda j: problems[j].n)
@@ -716,6 +778,7 @@ def run_kes(args):
         "gpu_launches": int(stats["kernel_launches"]),
         "clocks": clk.summary(),
         "tts": tts,
+        "precision_comparison": prec_cmp,
         "solve": {"tol": so.tol, "refine_sweeps": so.refine_sweeps, "refine_extra": so.refine_extra,
                   "refine_precision": ("fp64", "fp32x2")[so.refine_precision],
                   "accepted_pairs": [x["n_pairs"] for x in res] if batch else res[0]["n_pairs"],
