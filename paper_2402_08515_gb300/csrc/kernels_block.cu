@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(256, MINB)
 // FP64 units of GB300 issue about two FMAs per clock per SM). Same recurrence and order as
 // the other step kernels (eq. 2stepmethod; the values hold A + 2I when fold2), the weighted
 // terms added to the compensated FP32 accumulator every third step like k_step_blk.
-// Two lanes per row (LPR = 2): a lane owns NH = NB / 2 columns, a warp half a slice.
+// kX2Lpr lanes per row: a lane owns NH = NB / kX2Lpr columns, a warp 32 / kX2Lpr rows.
 // NH (hi, lo) pairs of one row: coherent and read-only-path loads, and the store
 template <int NH>
 __device__ __forceinline__ void load_pairs(const float2* p, float (&h)[NH], float (&l)[NH]) {
@@ -465,23 +465,28 @@ __device__ __forceinline__ void pair_fma(float ah, float al, float xh, float xl,
   sl = __fadd_rn(sl, __fadd_rn(e, pe));
 }
 
+// Lanes per row and resident blocks per SM of the FP32-pair step.
+constexpr int kX2Lpr = 2, kX2MinBlocks = 4;
+
 template <int NB, bool FIRST, bool LAST, bool ACC>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, kX2MinBlocks)
     k_step_x2(SellDev A, const float2* __restrict__ val2, const float2* __restrict__ x, const float2* prev,
               float2* out, float* acc_s, float* acc_c, double* acc64, int64_t acc_stride, int F,
               const float* __restrict__ ahi, const float* __restrict__ alo, int Lp1, int step, int cpt,
               uint32_t coltab, int nterm, int* flag) {
-  constexpr int NH = NB / 2;              // columns of this lane
+  constexpr int LPR = NB >= kX2Lpr ? kX2Lpr : NB;
+  constexpr int NH = NB / LPR;            // columns of this lane
+  constexpr int kRows = kSliceC / LPR;    // rows of a warp's unit
   static_assert(ACC || !LAST, "the last step completes the sums");
   const int lane = threadIdx.x & 31;
-  const int sub = lane / 2;               // row within the half slice
-  const int co = (lane % 2) * NH;         // first column of this lane
+  const int sub = lane / LPR;             // row within the unit
+  const int co = (lane % LPR) * NH;       // first column of this lane
   const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-  const int64_t n_units = A.n_slices * 2;
+  const int64_t n_units = A.n_slices * LPR;
   const int nacc = cpt ? 1 : F;
   for (int64_t u = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; u < n_units; u += nwarps) {
-    const int64_t s = u / 2;
-    const int rs = static_cast<int>(u % 2) * 16 + sub;  // row within the slice
+    const int64_t s = u / LPR;
+    const int rs = static_cast<int>(u % LPR) * kRows + sub;  // row within the slice
     const int64_t beg = A.slice_ptr[s];
     const int w = static_cast<int>((A.slice_ptr[s + 1] - beg) >> 5);
     const int64_t mesh = A.slice_mesh ? A.slice_mesh[s] : 0;
@@ -856,8 +861,9 @@ void launch_step_x2(const SellDev& A, const LaunchCfg& cfg, cudaStream_t st, int
   uint32_t coltab = 0;
   if (cpt > 0)
     for (int c = 0; c < NB; ++c) coltab |= static_cast<uint32_t>(std::min(c / cpt, F - 1)) << (4 * c);
-  const int64_t need = (A.n_slices * 2 + 7) / 8;  // 8 warps per block, half a slice each
-  const int64_t cap = static_cast<int64_t>(cfg.n_sm) * 4;
+  const int lpr = NB >= kX2Lpr ? kX2Lpr : NB;
+  const int64_t need = (A.n_slices * lpr + 7) / 8;  // 8 warps per block, 32 / lpr rows each
+  const int64_t cap = static_cast<int64_t>(cfg.n_sm) * kX2MinBlocks;
   const int grid = static_cast<int>(need < cap ? (need > 0 ? need : 1) : cap);
 #define KES_X2_ARGS A, val2, x, prev, out, acc_s, acc_c, acc64, acc_stride, F, alpha_hi, alpha_lo, L + 1, step, cpt, coltab, nterm, flag
 #define KES_X2(NBV)                                                                               \
