@@ -47,3 +47,32 @@ def test_small_case_oracle_solve_reports_beside_the_gpu_fields():
     small["gpu_omega2"] = [out["oracle_accepted_omega"][0] ** 2]   # a value the oracle accepts
     out = bench.small_solve_oracle(small)
     assert out["accepted_by_both"] == 1 and out["max_rel_diff_of_pairs_both_accept"] <= 1e-15
+
+
+def test_kernel_source_hash_ignores_comments_and_sees_code(tmp_path):
+    # a committed profile's traffic figure stays attached to the kernel code it was taken on:
+    # comment edits keep the hash, any code change alters it
+    a = tmp_path / "a.cu"
+    a.write_text("// header\n__global__ void k(int* p) {\n  p[0] = 1;  // store\n}\n")
+    b = tmp_path / "b.cu"
+    b.write_text("// another header\n\n__global__ void k(int* p) {\n  p[0] = 1;\n}\n")
+    c = tmp_path / "c.cu"
+    c.write_text("__global__ void k(int* p) {\n  p[0] = 2;\n}\n")
+    assert bench.kernel_source_hash(str(a)) == bench.kernel_source_hash(str(b))
+    assert bench.kernel_source_hash(str(a)) != bench.kernel_source_hash(str(c))
+
+
+def test_committed_step_profiles_match_the_current_kernels():
+    # the profiles the bench line's `traffic` comes from were taken on the current code
+    assert bench.profiled_traffic("cube128_fp64", bench.STEP_KERNEL_SRC) is not None
+    assert bench.profiled_traffic("cube128_fp32", bench.STEP_KERNEL_SRC) is not None
+    assert bench.profiled_traffic("batch12_fp32", bench.BLOCK_KERNEL_SRC) is not None
+
+
+def test_time_to_solution_forms_are_well_formed():
+    names = [f[0] for f in bench.TTS_FORMS]
+    assert len(names) == len(set(names))
+    for name, prec, b, sweeps, frac, extra, rprec in bench.TTS_FORMS:
+        assert prec in ("fp64", "fp32") and b in (1, 8) and 0 < frac <= 1.0 and extra >= 0
+        assert (sweeps > 0) == (prec == "fp32")        # the FP32 forms are refined, FP64 ones not
+        assert rprec in (0, 1) and ("x2" in name) == (rprec == 1)
