@@ -568,22 +568,27 @@ def test_meshes_times_intervals_equal_separate_solves(meshes):
 
 # ---------------------------------------------------------------- fixed-dimension iteration (Sec. 4)
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32x2"])
 def test_subspace_solve_matches_oracle(precision):
+    # fp32x2: a context of the FP32 form whose sweeps filter in FP32 pairs: held to the
+    # FP64 form's tolerances against the FP64 oracle
     p = square_grid(24)
     S = p.to_scipy()
     tau = _tau(p)
     lo, hi, L, dim, sweeps = 15.0, 22.0, 200, 36, 14
     X0 = start_vectors(p.n, dim, 5)
+    x2, label = precision == "fp32x2", precision
+    precision = "fp64" if x2 else precision       # the tolerances it is held to
     tol = 1e-8 if precision == "fp64" else 1e-5
     so = K.kes_solve_opts_default()
     so.kmax, so.tol, so.refine_sweeps, so.want_vectors = dim, tol, sweeps, 1
-    with K.Context(p, precision=precision, block_b=8) as c:
+    so.refine_precision = K.KES_REFINE_F32X2 if x2 else K.KES_REFINE_FP64
+    with K.Context(p, precision="fp32" if x2 else precision, block_b=8) as c:
         K.kes_set_filter(c.handle, lo, hi, tau, L)
         res = K.kes_subspace_solve(c.handle, X0, so)[0]
     th, rel, X, tha, rela = O.subspace_iteration(S, p.m, X0, lo, hi, tau, L, tol, sweeps)
     exact = spectra.eigenvalues_in(p.cells, p.h, lo, hi)
-    print(f"{precision}: GPU accepted {res['n_pairs']}, oracle {len(th)} of {len(exact)}; "
+    print(f"{label}: GPU accepted {res['n_pairs']}, oracle {len(th)} of {len(exact)}; "
           f"{res['refine_steps']} steps")
     assert res["time_steps"] == 0 and res["refine_steps"] > 0 and res["k_used"] <= dim
     for t in res["omega2"]:
