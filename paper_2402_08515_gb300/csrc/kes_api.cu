@@ -1002,6 +1002,14 @@ void kes_result_free(kes_result* r) {
   std::free(r);
 }
 
+// Refinement sweeps in FP32 pairs need a context of the FP32 form with block columns (the
+// sweep's filter is a block kernel) and the leapfrog stepper; checked before the Krylov phase.
+static bool refine_precision_supported(const kes_ctx* c, const kes_solve_opts& so) {
+  if (so.refine_precision != KES_REFINE_F32X2 || so.refine_sweeps == 0 || c->opts.precision != KES_PREC_FP32)
+    return true;
+  return c->opts.stepper == KES_STEPPER_LEAPFROG && (c->F > 1 || c->NBcap >= 2);
+}
+
 kes_status kes_krylov_solve(kes_ctx* c, const double* r0, int32_t mem, const kes_solve_opts* so_in,
                             kes_result** out) {
   if (!c || !r0 || !out || (mem != KES_MEM_HOST && mem != KES_MEM_DEVICE)) return KES_ERR_ARG;
@@ -1015,7 +1023,7 @@ kes_status kes_krylov_solve(kes_ctx* c, const double* r0, int32_t mem, const kes
       so.refine_extra < 0 ||
       (so.refine_precision != KES_REFINE_FP64 && so.refine_precision != KES_REFINE_F32X2))
     return KES_ERR_ARG;
-  if (so.kmax > kMaxProjected) return KES_ERR_UNSUPPORTED;
+  if (so.kmax > kMaxProjected || !refine_precision_supported(c, so)) return KES_ERR_UNSUPPORTED;
   return block_solve_impl(c, r0, 1, mem, so, out);
 }
 
@@ -1033,7 +1041,7 @@ kes_status kes_block_krylov_solve(kes_ctx* c, const double* R0, int32_t b, int32
       so.refine_extra < 0 ||
       (so.refine_precision != KES_REFINE_FP64 && so.refine_precision != KES_REFINE_F32X2))
     return KES_ERR_ARG;
-  if (so.kmax > kMaxProjected) return KES_ERR_UNSUPPORTED;
+  if (so.kmax > kMaxProjected || !refine_precision_supported(c, so)) return KES_ERR_UNSUPPORTED;
   return block_solve_impl(c, R0, b, mem, so, out);
 }
 
@@ -1049,7 +1057,7 @@ kes_status kes_subspace_solve(kes_ctx* c, const double* X0, int32_t p, int32_t m
   if (so.kmax < p || so.refine_sweeps < 1 || !(so.tol > 0.0) || so.refine_L < 0 || so.refine_extra < 0 ||
       (so.refine_precision != KES_REFINE_FP64 && so.refine_precision != KES_REFINE_F32X2))
     return KES_ERR_ARG;
-  if (so.kmax > kMaxProjected) return KES_ERR_UNSUPPORTED;
+  if (so.kmax > kMaxProjected || !refine_precision_supported(c, so)) return KES_ERR_UNSUPPORTED;
   return block_solve_impl(c, nullptr, 1, mem, so, out, X0, p);
 }
 
