@@ -101,9 +101,10 @@ typedef struct kes_solve_opts {
   int32_t n_wanted;     /* stop as soon as this many pairs are accepted (0: run to kmax) */
   int32_t want_vectors; /* 1: return the accepted Ritz vectors B y (host, n x n_pairs col-major) */
   double tol;           /* acceptance: rel_res = ||S x - theta M x||_2 / (theta ||M x||_2) <= tol */
-  int32_t refine_sweeps; /* after the Krylov phase: sweeps of FP64 filtered subspace iteration on the
-                            in-interval Ritz vectors (X <- C X with the FP64 step kernels, then
-                            Rayleigh-Ritz); lifts FP32-form pairs to FP64 residuals. 0: none */
+  int32_t refine_sweeps; /* after the Krylov phase: sweeps of filtered subspace iteration on the
+                            in-interval Ritz vectors (X <- C X with the FP64 step kernels, or in FP32
+                            pairs per refine_precision, then FP64 Gram-Schmidt and Rayleigh-Ritz, Sec. 4);
+                            lifts FP32-form pairs to FP64 residuals. 0: none */
   int32_t refine_L;      /* leapfrog steps of the refinement filter: the first refine_L + 1 weights of the
                             installed tables, i.e. the same interval with end time refine_L * tau
                             (eq. weightf does not depend on T); 0 or >= L: L */
