@@ -20,18 +20,19 @@ def _patch(monkeypatch, name, fn):
 
 
 def _leapfrog(S, m, r, tau, alpha, *, start_prev=None, sign=-1.0, shift=1,
-              use_mass=True):
+              use_mass=True, first_term=True, last_term=True):
     """filter_apply with one configurable slip."""
     L = len(alpha) - 1
     y_prev = np.array(r if start_prev is None else start_prev(r), dtype=np.float64)
     y = np.array(r, dtype=np.float64)
-    acc = alpha[0] * y
+    acc = alpha[0] * y if first_term else np.zeros_like(y)
     for l in range(L):
         sy = S @ y
         if use_mass:
             sy = sy / m
         y_next = sign * tau * tau * sy + 2.0 * y - y_prev
-        acc = acc + alpha[min(l + shift, L)] * y_next
+        if last_term or l < L - 1:
+            acc = acc + alpha[min(l + shift, L)] * y_next
         y_prev, y = y, y_next
     return acc
 
@@ -41,6 +42,10 @@ MUTANTS_FILTER = {
     "wrong_sign_of_stiffness_term": dict(sign=+1.0),
     "weights_shifted_by_one_step": dict(shift=0),
     "mass_inverse_dropped": dict(use_mass=False),
+    # the first or the last weighted term left out of the sum (eq. disc_filtercoeff runs
+    # over n = 0..L): the slips a regrouped accumulation could make at either end
+    "first_term_dropped": dict(first_term=False),
+    "last_term_dropped": dict(last_term=False),
 }
 
 
