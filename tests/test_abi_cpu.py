@@ -157,3 +157,41 @@ def test_struct_layouts_match_the_header(tmp_path):
 def test_launch_shape_counts():
     n_step, n_block = K.kes_launch_shapes()
     assert n_step >= 8 and n_block >= 4
+
+
+def test_sym_eig_threaded_size_is_accurate_and_independent_of_the_thread_count(tmp_path):
+    # k >= 256 runs the Householder and rotation loops on OpenMP threads over independent
+    # rows and columns: the result must be backward stable on a graded spectrum like that of
+    # a projected stiffness matrix (eigenvalues from 0 to 2e5 with an interior cluster) and
+    # bitwise the same with one thread as with several (the matrix is made once, here: the
+    # BLAS that builds it rounds differently with other thread counts)
+    import os
+    import subprocess
+    import sys
+    k = 300
+    rng = np.random.default_rng(7)
+    lam = 2e5 * rng.random(k) ** 3
+    lam[:20] = 1600 + 400 * rng.random(20)
+    lam[20] = lam[0] * (1 + 1e-13)
+    Q, _ = np.linalg.qr(rng.standard_normal((k, k)))
+    A = (Q * lam) @ Q.T
+    A = 0.5 * (A + A.T)
+    np.save(tmp_path / "A.npy", A)
+    code = ("import numpy as np, sys\n"
+            "import paper_2402_08515_gb300 as K\n"
+            "w, V = K.kes_sym_eig(np.load(sys.argv[1]))\n"
+            "np.save(sys.argv[2], np.concatenate([w, V.ravel()]))\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = {}
+    for threads in ("1", "4"):
+        path = tmp_path / f"t{threads}.npy"
+        env = dict(os.environ, OMP_NUM_THREADS=threads)
+        subprocess.run([sys.executable, "-c", code, str(tmp_path / "A.npy"), str(path)], check=True, env=env,
+                       cwd=root)
+        out[threads] = np.load(path)
+    np.testing.assert_array_equal(out["1"], out["4"])
+    w, V = out["1"][:k], out["1"][k:].reshape(k, k)
+    norm = np.abs(lam).max()
+    assert np.abs(A @ V - V * w).max() <= 1e-13 * norm
+    assert np.abs(V.T @ V - np.eye(k)).max() <= 1e-12
+    np.testing.assert_allclose(w, np.sort(lam), atol=1e-13 * norm)
